@@ -1,0 +1,261 @@
+/*
+ * riga.h -- C ABI of the GB300 shift-and-invert eigensolver for B-spline (IGA)
+ * and refined-IGA (rIGA) discretizations of the Laplace eigenproblem.
+ *
+ * Problem (Sec. 2.1, Eq. helmholtz / Eq. GHEP of arXiv 2009.08167): find
+ * (lambda, u) with K u = lambda M u, K and M the stiffness and mass matrices
+ * of a tensor-product B-spline space of degree p on (0,1)^d with homogeneous
+ * Dirichlet conditions.  The solution path is the paper's (Sec. 4): an LDL^T
+ * factorization of K - sigma M (multifrontal, in the nested-dissection order
+ * whose separators are the rIGA C0 hyperplanes of Sec. 3.2), forward/backward
+ * solves and M mat-vecs inside a Lanczos iteration in the M-inner product
+ * (Eq. LanczosAlphaBeta), Rayleigh-Ritz on T_m (Eq. RitzValues), and the
+ * Sylvester inertia of D (Remark on inertia) to place shifts and to confirm
+ * that no eigenvalue was missed.
+ *
+ * Conventions for every entry point
+ *  - Return value: RIGA_OK (0) or a negative RIGA_E* code; no exception or
+ *    signal crosses the ABI.  riga_strerror() names a code;
+ *    riga_last_error() gives a human-readable message for the last failing
+ *    call on a context.
+ *  - Arrays are owned by the caller.  A pointer argument may address host or
+ *    device memory of the context's device; the library detects which.
+ *    Device arrays are accessed on the context's stream in stream order; host
+ *    arrays are copied synchronously (the call returns after the copy).
+ *  - The context owns its internal device allocations (matrices, fronts,
+ *    Lanczos basis) until riga_destroy().
+ *  - Global DOF numbering is x-fastest: g = i + n_x (j + n_y k), where n_a is
+ *    the number of DOFs in direction a after the two Dirichlet functions of
+ *    each direction are removed (Eq. dofs).  Element numbering is x-fastest
+ *    likewise: e = e_x + ne_x (e_y + ne_y e_z).
+ *  - Vectors and matrices of several columns are column-major with leading
+ *    dimension N (one eigenvector per column).
+ */
+#ifndef RIGA_H
+#define RIGA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+#define RIGA_OK 0
+#define RIGA_EINVAL (-1)   /* bad argument (sizes, NULL pointer, unsupported option) */
+#define RIGA_ESTATE (-2)   /* call order (e.g. riga_solve before riga_factor) */
+#define RIGA_EPIVOT (-3)   /* zero or non-finite pivot in LDL^T (sigma at an eigenvalue) */
+#define RIGA_ENOCONV (-4)  /* Lanczos did not converge; outputs valid for *nconv pairs */
+#define RIGA_EREFINE (-5)  /* iterative refinement stagnated above the tolerance */
+#define RIGA_ETIMEOUT (-6) /* a bounded device-side wait expired */
+#define RIGA_ECUDA (-7)    /* a CUDA runtime call failed */
+#define RIGA_ENOMEM (-8)   /* device allocation failed */
+
+/* ---------------------------------------------------- factor precisions */
+#define RIGA_FP64 0 /* fronts in FP64 */
+#define RIGA_FP32 1 /* fronts in FP32, solves refined to FP64 accuracy */
+
+typedef struct riga_ctx riga_ctx;
+
+/*
+ * Mesh description (Sec. 3.1 Eq. U, Sec. 3.2): uniform open knot vectors on
+ * [0,1] with ne[a] elements in direction a and degree p in every direction.
+ * mult[a] points to ne[a]-1 interior knot multiplicities in 1..p (p makes the
+ * knot a C0 separator, Fig. 2); NULL means all 1 (maximum continuity C^{p-1}).
+ * dirichlet must be 1 (homogeneous Dirichlet on all faces, Eq. helmholtz).
+ * leaf_extent bounds the DOF extent of a leaf box of the nested dissection
+ * (0 selects 8); see riga_assemble.
+ */
+typedef struct {
+    int dim;         /* 1, 2 or 3 */
+    int ne[3];       /* elements per direction, >= 1 */
+    int p;           /* degree, 1..6 */
+    const int* mult[3];
+    int dirichlet;   /* must be 1 */
+    int leaf_extent; /* >= 1, or 0 for the default 8 */
+} riga_mesh;
+
+/*
+ * riga_create: make a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * stream must outlive the context.  Errors: RIGA_EINVAL, RIGA_ECUDA.
+ */
+int riga_create(riga_ctx** out, int device, void* cuda_stream);
+
+/*
+ * riga_create with device = -1 makes a host-only context: it accepts
+ * riga_analyze, riga_query, riga_get_symbolic, riga_strerror and
+ * riga_last_error (no CUDA call is made); every other call returns
+ * RIGA_ESTATE.
+ */
+
+/* riga_destroy: free every device allocation of the context.  NULL is a no-op. */
+void riga_destroy(riga_ctx* ctx);
+
+/*
+ * riga_assemble: build K and M (Eq. 1Dmatrix, Eq. 2Dmatrix) on the device.
+ *  - Symbolic analysis (host, integer, once per mesh pattern): C0 DOFs,
+ *    nested-dissection order (separators = C0 hyperplanes first, then p-thick
+ *    slabs down to leaf boxes of extent <= max(leaf_extent, p+1)), assembly
+ *    tree, fronts, scatter and extend-add maps.  A second call with the same
+ *    mesh reuses it and only recomputes values.
+ *  - Numeric assembly (device): Cox-de Boor basis and derivatives at p+1
+ *    Gauss points per element, 1D element matrices, then CSR values of K and
+ *    M in elimination order.
+ *  coefK, coefM: NULL for constant coefficients (Kronecker construction of
+ *    Eq. 2Dmatrix), else n_elem factors c_e so that K = sum_e coefK[e] K_e and
+ *    M = sum_e coefM[e] M_e (either may be NULL = all ones).
+ * Errors: RIGA_EINVAL (bad mesh), RIGA_ENOMEM, RIGA_ECUDA.  Invalidates any
+ * factorization held by the context.
+ */
+int riga_assemble(riga_ctx* ctx, const riga_mesh* mesh, const double* coefK, const double* coefM);
+
+/*
+ * riga_analyze: the symbolic half of riga_assemble alone (host, integer):
+ * C0 DOFs, elimination order, assembly tree and fronts for `mesh`, without
+ * touching a device.  Makes riga_query and riga_get_symbolic available.
+ * Errors: RIGA_EINVAL (bad mesh).
+ */
+int riga_analyze(riga_ctx* ctx, const riga_mesh* mesh);
+
+/*
+ * riga_factor: numeric LDL^T of A = K - sigma M in the context's elimination
+ * order (Sec. 4.2 and its Remark on inertia), 1x1 pivots without pivoting.
+ * precision: RIGA_FP64 or RIGA_FP32 (fronts stored and updated in FP32; the
+ *   assembled A is rounded from FP64).
+ * n_neg (may be NULL): receives the inertia nu(K - sigma M), the number of
+ *   negative entries of D = the number of eigenvalues below sigma (Sylvester).
+ * Errors: RIGA_ESTATE (no riga_assemble), RIGA_EPIVOT (a zero or non-finite
+ * pivot: sigma is at, or numerically indistinguishable from, an eigenvalue),
+ * RIGA_EINVAL, RIGA_ECUDA.
+ */
+int riga_factor(riga_ctx* ctx, double sigma, int precision, long long* n_neg);
+
+/*
+ * riga_solve: x = (K - sigma M)^{-1} b for nrhs right-hand sides (columns of
+ * length N, x-fastest numbering) with the last factorization: forward
+ * elimination, D^{-1}, backward elimination over the assembly tree.  With an
+ * FP32 factor (or tol > 0) the FP64 residual b - (K - sigma M) x drives
+ * iterative refinement until ||r||_2 <= tol ||b||_2 (tol <= 0 with an FP32
+ * factor selects 1e-13); iters_out (may be NULL) receives the refinement
+ * sweeps of the last column.  b and x may alias.  Errors: RIGA_ESTATE,
+ * RIGA_EREFINE (no progress, x holds the best iterate), RIGA_EINVAL, RIGA_ECUDA.
+ */
+int riga_solve(riga_ctx* ctx, const double* b, double* x, int nrhs, double tol, int* iters_out);
+
+/*
+ * riga_eigs: the k smallest eigenvalues lambda > sigma of K u = lambda M u
+ * and M-orthonormal eigenvectors, by shift-and-invert Lanczos (Sec. 4).
+ *  - The first shift is sigma.  When slice > 0 and slice < k, the interval is
+ *    covered by spectrum slicing: after each shift's `slice` pairs are
+ *    accepted, the next shift is placed midway between the last accepted
+ *    eigenvalue and the next Ritz value (Sec. 4.1, Remark on inertia).
+ *  - Each shift: factorization at `precision`, Lanczos with full
+ *    reorthogonalization (two classical Gram-Schmidt passes against the
+ *    basis and all locked vectors), Rayleigh-Ritz on T_m, locking of pairs
+ *    whose residual estimate is below tol, restarts from a fresh random vector
+ *    M-orthogonal to the locked ones until the inertia difference between the
+ *    shift and a check shift confirms the count (degenerate eigenvalues).
+ *  - evals[k] ascending; evecs (N x k, may be NULL) M-normalised, sign fixed
+ *    so that the entry of largest magnitude is positive (lowest index on
+ *    ties); resid[k] (may be NULL) the residuals
+ *    ||K u - lambda M u||_2 / (|lambda| ||M u||_2) evaluated in FP64.
+ *  - nconv (may be NULL): pairs delivered.
+ * Errors: RIGA_ESTATE, RIGA_ENOCONV (first *nconv outputs valid), RIGA_EPIVOT,
+ * RIGA_EINVAL, RIGA_ECUDA.
+ */
+int riga_eigs(riga_ctx* ctx, int k, double sigma, double tol, double* evals, double* evecs,
+              double* resid, int* nconv);
+
+/*
+ * riga_set_eig_options: options of riga_eigs (not in the SURVEY-level
+ * signature, kept separate so that riga_eigs stays short).
+ *  slice      eigenpairs accepted per shift (0 = k, a single shift);
+ *  precision  RIGA_FP64 or RIGA_FP32 factor inside riga_eigs;
+ *  max_steps  Lanczos steps per run (0 = automatic: min(N, max(3 w, w + 40))
+ *             for w wanted pairs);
+ *  extra      additional pairs computed beyond the wanted ones so that the
+ *             completeness check shift can sit in a gap (0 selects 2);
+ *  seed       start-vector seed (SplitMix64 stream).
+ */
+int riga_set_eig_options(riga_ctx* ctx, int slice, int precision, int max_steps, int extra,
+                         unsigned long long seed);
+
+/*
+ * riga_eig_grad: gradient of L = sum_i dL_dlambda[i] lambda_i over the k
+ * eigenpairs of the last riga_eigs with respect to the log-coefficients a_e,
+ * b_e (coefK[e] = exp(a_e), coefM[e] = exp(b_e) of riga_assemble):
+ *   dL/da_e =  sum_i w_i coefK[e] u_ie^T K_e u_ie,
+ *   dL/db_e = -sum_i w_i lambda_i coefM[e] u_ie^T M_e u_ie,
+ * with K_e, M_e the unit-coefficient element matrices (tensor products of 1D
+ * element matrices) and u_ie the element's coefficients of eigenvector i.
+ * Not in the paper; valid for simple eigenvalues (or symmetric functions of a
+ * complete degenerate set).  grad_a, grad_b: n_elem each (either may be NULL).
+ * Errors: RIGA_ESTATE (no eigenpairs), RIGA_EINVAL (k larger than computed),
+ * RIGA_ECUDA.
+ */
+int riga_eig_grad(riga_ctx* ctx, int k, const double* dL_dlambda, double* grad_a, double* grad_b);
+
+/*
+ * riga_query: sizes of the current problem (any pointer may be NULL):
+ * N DOFs, nnz of K (= nnz of M, full symmetric pattern), nnzL entries held by
+ * the dense fronts' factor (lower trapezoids incl. diagonal), flops_fact the
+ * factorization flop count sum_F sum_{i<k_F} (n_F-i)(n_F-i-1).
+ */
+int riga_query(riga_ctx* ctx, long long* N, long long* nnz, long long* nnzL, double* flops_fact);
+
+/*
+ * riga_get_symbolic: the elimination order and assembly tree (integers,
+ * bit-exact comparable).  Query sizes first with all arrays NULL:
+ *  n_nodes, total_idx (sum of front sizes).
+ *  perm[N]: perm[pos] = global DOF eliminated at position pos;
+ *  node_ptr[n_nodes+1]: node F owns positions node_ptr[F]..node_ptr[F+1]-1;
+ *  parent[n_nodes]: parent node (-1 for a root), nodes are post-ordered;
+ *  front_ptr[n_nodes+1], front_idx[total_idx]: the front of F as global DOFs,
+ *  own variables first then the border in elimination order.
+ * Host arrays only.  Errors: RIGA_ESTATE, RIGA_EINVAL.
+ */
+int riga_get_symbolic(riga_ctx* ctx, int* n_nodes, long long* total_idx, int* perm, int* node_ptr,
+                      int* parent, long long* front_ptr, int* front_idx);
+
+/*
+ * riga_get_matrices: CSR of K and M in global (x-fastest) numbering, rows and
+ * columns ascending: row_ptr[N+1], col[nnz], kval[nnz], mval[nnz] (any may be
+ * NULL).  Host or device arrays.  Errors: RIGA_ESTATE, RIGA_ECUDA.
+ */
+int riga_get_matrices(riga_ctx* ctx, long long* row_ptr, int* col, double* kval, double* mval);
+
+/*
+ * riga_get_factor: D[N] (in elimination order) of the last factorization and,
+ * if L is non-NULL, the dense-front factor: for node F the column-major
+ * n_F x k_F block of L (unit diagonal implied, strictly lower part valid)
+ * stored at L + Lptr[F] with leading dimension n_F, Lptr[n_nodes+1] the
+ * offsets (query with L = NULL first).  Values are converted to double.
+ * Host arrays only.  Errors: RIGA_ESTATE, RIGA_ECUDA.
+ */
+int riga_get_factor(riga_ctx* ctx, double* D, long long* Lptr, double* L);
+
+/*
+ * riga_spmv: y = A x with A = M (which = 0), K (1) or K - sigma M (2, sigma of
+ * the last factorization), x and y of length N in global numbering, FP64.
+ * Host or device arrays.  Errors: RIGA_ESTATE, RIGA_EINVAL, RIGA_ECUDA.
+ */
+int riga_spmv(riga_ctx* ctx, int which, const double* x, double* y);
+
+/*
+ * riga_stats: counters of the last riga_eigs (any may be NULL):
+ * n_fact factorizations (N_fa of Table 1), n_solve f/b eliminations (N_fb),
+ * n_matvec M mat-vecs (N_mv), lanczos_steps total steps over all runs,
+ * t_fact_ms / t_solve_ms device time in factorizations / Lanczos loops.
+ */
+int riga_stats(riga_ctx* ctx, long long* n_fact, long long* n_solve, long long* n_matvec,
+               long long* lanczos_steps, double* t_fact_ms, double* t_lanczos_ms);
+
+/* riga_strerror: static name of a status code. */
+const char* riga_strerror(int status);
+
+/* riga_last_error: message of the last failing call on ctx ("" if none). */
+const char* riga_last_error(riga_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIGA_H */

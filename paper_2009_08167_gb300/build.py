@@ -1,0 +1,81 @@
+"""Build libriga.so in-tree for sm_103a (nvcc, no cmake).
+
+    python -m paper_2009_08167_gb300.build
+
+Compiles every translation unit of csrc/ in parallel into _build/ and links
+paper_2009_08167_gb300/libriga.so.  Only what changed is recompiled.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libriga.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def _newer(src, deps, obj):
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(p) > t for p in [src] + deps)
+
+
+def build(verbose=False, jobs=None):
+    os.makedirs(OUT, exist_ok=True)
+    nvcc = _nvcc()
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(os.path.dirname(HERE), "include", "riga.h"))
+    srcs = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+    cmds = []
+    objs = []
+    for f in srcs:
+        src = os.path.join(CSRC, f)
+        obj = os.path.join(OUT, f + ".o")
+        objs.append(obj)
+        if not _newer(src, headers, obj):
+            continue
+        cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"] + ARCH
+        if f.endswith(".cu"):
+            cmd += ["-Xptxas", "-O3"]
+        else:
+            cmd += ["-x", "cu"]
+        cmds.append(cmd)
+
+    def run(cmd):
+        p = subprocess.run(cmd, capture_output=True, text=True)
+        return cmd, p
+
+    failed = []
+    with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 4)) as ex:
+        for cmd, p in ex.map(run, cmds):
+            if verbose or p.returncode:
+                sys.stderr.write(" ".join(cmd) + "\n" + p.stdout + p.stderr)
+            if p.returncode:
+                failed.append(cmd[2])
+    if failed:
+        raise RuntimeError("compilation failed: " + ", ".join(failed))
+    if cmds or not os.path.exists(LIB):
+        tmp = LIB + ".tmp"
+        link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+        p = subprocess.run(link, capture_output=True, text=True)
+        if p.returncode:
+            sys.stderr.write(" ".join(link) + "\n" + p.stdout + p.stderr)
+            raise RuntimeError("link failed")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv))

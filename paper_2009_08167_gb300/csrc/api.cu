@@ -1,0 +1,563 @@
+// C ABI entry points (include/riga.h).  Argument checking, host/device
+// pointer handling, and the order of the device phases; every numeric step
+// runs in the kernels of assemble.cu, factor.cu, solve.cu, lanczos.cu and
+// adjoint.cu (the tridiagonal Rayleigh-Ritz step of tridiag.cpp runs on the
+// host, inside this library).
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+namespace riga {
+
+int set_error(riga_ctx* c, int code, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+void sign_fix(riga_ctx* c, double* U, int ncols);
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy n values between a user pointer (host or device) and a device buffer
+template <typename T>
+int to_device(riga_ctx* c, const T* user, T* dev, size_t n) {
+    if (n == 0) return RIGA_OK;
+    cudaMemcpyKind kind = is_device_ptr(user) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(dev, user, n * sizeof(T), kind, c->stream));
+    if (kind == cudaMemcpyHostToDevice) RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RIGA_OK;
+}
+
+template <typename T>
+int to_user(riga_ctx* c, const T* dev, T* user, size_t n) {
+    if (n == 0) return RIGA_OK;
+    cudaMemcpyKind kind = is_device_ptr(user) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(user, dev, n * sizeof(T), kind, c->stream));
+    if (kind == cudaMemcpyDeviceToHost) RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RIGA_OK;
+}
+
+int upload_symbolic(riga_ctx* c) {
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    RIGA_CUDA_TRY(c, c->rowptr.upload(S.rowptr, st));
+    RIGA_CUDA_TRY(c, c->col.upload(S.col, st));
+    RIGA_CUDA_TRY(c, c->perm.upload(S.perm, st));
+    RIGA_CUDA_TRY(c, c->ipos.upload(S.ipos, st));
+    RIGA_CUDA_TRY(c, c->node_ptr.upload(S.node_ptr, st));
+    RIGA_CUDA_TRY(c, c->kk.upload(S.k, st));
+    RIGA_CUDA_TRY(c, c->nn.upload(S.n, st));
+    RIGA_CUDA_TRY(c, c->parent.upload(S.parent, st));
+    RIGA_CUDA_TRY(c, c->front_off.upload(S.front_off, st));
+    RIGA_CUDA_TRY(c, c->front_ptr.upload(S.front_ptr, st));
+    RIGA_CUDA_TRY(c, c->front_pos.upload(S.front_pos, st));
+    RIGA_CUDA_TRY(c, c->child_ptr.upload(S.child_ptr, st));
+    RIGA_CUDA_TRY(c, c->child_list.upload(S.child_list.empty() ? std::vector<int>{0} : S.child_list, st));
+    RIGA_CUDA_TRY(c, c->rel.upload(S.rel.empty() ? std::vector<int>{0} : S.rel, st));
+    RIGA_CUDA_TRY(c, c->rel_ptr.upload(S.rel_ptr, st));
+    RIGA_CUDA_TRY(c, c->upd_off.upload(S.upd_off, st));
+    RIGA_CUDA_TRY(c, c->scatter.upload(S.scatter, st));
+    RIGA_CUDA_TRY(c, c->perm_to_glob.upload(S.perm_to_glob, st));
+    RIGA_CUDA_TRY(c, c->glob_rowptr.upload(S.glob_rowptr, st));
+    std::vector<int> ln;
+    c->level_nodes_off.assign(S.n_levels + 1, 0);
+    for (int l = 0; l < S.n_levels; ++l) {
+        c->level_nodes_off[l] = (int)ln.size();
+        for (int f : S.levels[l].nodes) ln.push_back(f);
+    }
+    c->level_nodes_off[S.n_levels] = (int)ln.size();
+    RIGA_CUDA_TRY(c, c->level_nodes.upload(ln, st));
+    RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
+    RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
+    RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return RIGA_OK;
+}
+
+__global__ void scatter_glob_kernel(long long nnz, const long long* __restrict__ p2g, const double* __restrict__ src,
+                                    double* __restrict__ dst) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) dst[p2g[e]] = src[e];
+}
+
+__global__ void glob_col_kernel(long long N, const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const int* __restrict__ perm, const long long* __restrict__ p2g,
+                                int* __restrict__ gcol) {
+    long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    for (long long e = rowptr[row]; e < rowptr[row + 1]; ++e) gcol[p2g[e]] = perm[col[e]];
+}
+
+__global__ void resid_partial_kernel(long long N, const double* __restrict__ Ku, const double* __restrict__ Mu,
+                                     double lam, double* __restrict__ partial) {
+    __shared__ double sa[8], sb[8];
+    double xa = 0.0, xb = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        double r = Ku[i] - lam * Mu[i];
+        xa += r * r;
+        xb += Mu[i] * Mu[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        xa += __shfl_xor_sync(0xffffffffu, xa, o);
+        xb += __shfl_xor_sync(0xffffffffu, xb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = xa;
+        sb[threadIdx.x >> 5] = xb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        partial[2 * blockIdx.x] = ta;
+        partial[2 * blockIdx.x + 1] = tb;
+    }
+}
+
+std::vector<int> mesh_key(const riga_mesh* m) {
+    std::vector<int> key{m->dim, m->p, m->leaf_extent > 0 ? m->leaf_extent : 8};
+    for (int a = 0; a < m->dim; ++a) {
+        key.push_back(m->ne[a]);
+        for (int i = 0; i + 1 < m->ne[a]; ++i) key.push_back(m->mult[a] ? m->mult[a][i] : 1);
+    }
+    return key;
+}
+
+}  // namespace
+}  // namespace riga
+
+using namespace riga;
+
+extern "C" {
+
+int riga_create(riga_ctx** out, int device, void* cuda_stream) {
+    if (!out) return RIGA_EINVAL;
+    *out = nullptr;
+    if (device == -1) {
+        riga_ctx* h = new (std::nothrow) riga_ctx();
+        if (!h) return RIGA_ENOMEM;
+        h->device = -1;
+        *out = h;
+        return RIGA_OK;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return RIGA_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return RIGA_ECUDA;
+    riga_ctx* c = new (std::nothrow) riga_ctx();
+    if (!c) return RIGA_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    return RIGA_OK;
+}
+
+void riga_destroy(riga_ctx* c) {
+    if (!c) return;
+    if (c->device < 0) {
+        delete c;
+        return;
+    }
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+const char* riga_strerror(int s) {
+    switch (s) {
+        case RIGA_OK: return "RIGA_OK";
+        case RIGA_EINVAL: return "RIGA_EINVAL";
+        case RIGA_ESTATE: return "RIGA_ESTATE";
+        case RIGA_EPIVOT: return "RIGA_EPIVOT";
+        case RIGA_ENOCONV: return "RIGA_ENOCONV";
+        case RIGA_EREFINE: return "RIGA_EREFINE";
+        case RIGA_ETIMEOUT: return "RIGA_ETIMEOUT";
+        case RIGA_ECUDA: return "RIGA_ECUDA";
+        case RIGA_ENOMEM: return "RIGA_ENOMEM";
+        default: return "RIGA_UNKNOWN";
+    }
+}
+
+const char* riga_last_error(riga_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+static int check_mesh(riga_ctx* c, const riga_mesh* m) {
+    if (m->dim < 1 || m->dim > 3) return set_error(c, RIGA_EINVAL, "dim must be 1, 2 or 3");
+    if (m->dirichlet != 1) return set_error(c, RIGA_EINVAL, "only homogeneous Dirichlet (dirichlet = 1) is supported");
+    if (m->p < 1 || m->p > 6) return set_error(c, RIGA_EINVAL, "p must be in 1..6");
+    if (m->leaf_extent < 0) return set_error(c, RIGA_EINVAL, "leaf_extent must be >= 0");
+    for (int a = 0; a < m->dim; ++a)
+        if (m->ne[a] < 1 || m->ne[a] > (1 << 20)) return set_error(c, RIGA_EINVAL, "ne out of range");
+    return RIGA_OK;
+}
+
+int riga_analyze(riga_ctx* c, const riga_mesh* m) {
+    if (!c || !m) return RIGA_EINVAL;
+    c->last_error.clear();
+    int rc = check_mesh(c, m);
+    if (rc) return rc;
+    c->assembled = false;
+    c->factored = false;
+    c->nev = 0;
+    c->mesh_key.clear();
+    std::string err = build_symbolic(c->S, m->dim, m->ne, m->p, m->mult, m->leaf_extent);
+    if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
+    c->analyzed_only = true;
+    return RIGA_OK;
+}
+
+int riga_assemble(riga_ctx* c, const riga_mesh* m, const double* coefK, const double* coefM) {
+    if (!c || !m) return RIGA_EINVAL;
+    c->last_error.clear();
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    cudaSetDevice(c->device);
+    {
+        int rc0 = check_mesh(c, m);
+        if (rc0) return rc0;
+    }
+    c->analyzed_only = false;
+    c->assembled = false;
+    c->factored = false;
+    c->nev = 0;
+    std::vector<int> key = mesh_key(m);
+    if (key != c->mesh_key) {
+        std::string err = build_symbolic(c->S, m->dim, m->ne, m->p, m->mult, m->leaf_extent);
+        if (!err.empty()) {
+            c->mesh_key.clear();
+            return set_error(c, RIGA_EINVAL, err);
+        }
+        int rc = upload_symbolic(c);
+        if (rc) {
+            c->mesh_key.clear();
+            return rc;
+        }
+        c->mesh_key = key;
+    }
+    const long long ne_tot = c->S.n_elem;
+    c->coefK.clear();
+    c->coefM.clear();
+    if (coefK) {
+        c->coefK.resize(ne_tot);
+        DevBuf<double> tmp;
+        RIGA_CUDA_TRY(c, tmp.alloc(ne_tot));
+        int rc = to_device(c, coefK, tmp.ptr, ne_tot);
+        if (rc) return rc;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->coefK.data(), tmp.ptr, ne_tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (coefM) {
+        c->coefM.resize(ne_tot);
+        DevBuf<double> tmp;
+        RIGA_CUDA_TRY(c, tmp.alloc(ne_tot));
+        int rc = to_device(c, coefM, tmp.ptr, ne_tot);
+        if (rc) return rc;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->coefM.data(), tmp.ptr, ne_tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (double v : c->coefK)
+        if (!(v > 0.0) || !std::isfinite(v)) return set_error(c, RIGA_EINVAL, "coefK must be positive and finite");
+    for (double v : c->coefM)
+        if (!(v > 0.0) || !std::isfinite(v)) return set_error(c, RIGA_EINVAL, "coefM must be positive and finite");
+    int rc = assemble_device(c);
+    if (rc) return rc;
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->assembled = true;
+    return RIGA_OK;
+}
+
+int riga_factor(riga_ctx* c, double sigma, int precision, long long* n_neg) {
+    if (!c) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (precision != RIGA_FP64 && precision != RIGA_FP32) return set_error(c, RIGA_EINVAL, "unknown precision");
+    if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
+    c->sigma = sigma;
+    c->precision = precision;
+    c->factored = false;
+    int rc = enqueue_factor(c);
+    if (rc) return rc;
+    rc = finish_factor(c);
+    if (n_neg) *n_neg = c->inertia;
+    return rc;
+}
+
+int riga_solve(riga_ctx* c, const double* b, double* x, int nrhs, double tol, int* iters_out) {
+    if (!c || !b || !x || nrhs < 1) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->factored) return set_error(c, RIGA_ESTATE, "riga_factor first");
+    const long long N = c->S.N;
+    for (int i = 0; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    double* g = c->vwork[0].ptr;
+    double* y = c->vwork[1].ptr;
+    int status = RIGA_OK;
+    for (int col = 0; col < nrhs; ++col) {
+        int rc = to_device(c, b + (long long)col * N, g, N);
+        if (rc) return rc;
+        enqueue_permute(c, g, y, 1, 1);
+        const bool refine = (c->precision != RIGA_FP64) || tol > 0.0;
+        double t = tol > 0.0 ? tol : 1e-13;
+        int sweeps = 1;
+        rc = solve_refined(c, y, c->vwork[2].ptr, c->vwork[3].ptr, t, refine ? 30 : 1, refine ? 1 : 0, &sweeps);
+        if (rc == RIGA_EREFINE) status = rc;
+        else if (rc) return rc;
+        if (iters_out) *iters_out = sweeps;
+        enqueue_permute(c, y, g, 0, 1);
+        rc = to_user(c, g, x + (long long)col * N, N);
+        if (rc) return rc;
+    }
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return status;
+}
+
+int riga_set_eig_options(riga_ctx* c, int slice, int precision, int max_steps, int extra, unsigned long long seed) {
+    if (!c) return RIGA_EINVAL;
+    if (slice < 0 || max_steps < 0 || extra < 0) return set_error(c, RIGA_EINVAL, "negative option");
+    if (precision != RIGA_FP64 && precision != RIGA_FP32) return set_error(c, RIGA_EINVAL, "unknown precision");
+    c->opt_slice = slice;
+    c->opt_precision = precision;
+    c->opt_max_steps = max_steps;
+    c->opt_extra = extra;
+    c->opt_seed = seed;
+    return RIGA_OK;
+}
+
+int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, double* evecs, double* resid, int* nconv) {
+    if (!c || !evals) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (!(tol > 0.0)) return set_error(c, RIGA_EINVAL, "tol must be positive");
+    if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
+    int got = 0;
+    int status = run_eigs(c, k, sigma, tol, &got);
+    if (nconv) *nconv = got;
+    if (status != RIGA_OK && status != RIGA_ENOCONV) return status;
+    const long long N = c->S.N;
+    // eigenvalues
+    if (got > 0) {
+        if (is_device_ptr(evals)) {
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(evals, c->evals.data(), got * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        } else {
+            std::memcpy(evals, c->evals.data(), got * sizeof(double));
+        }
+    }
+    // residuals rho_i = ||K u - lambda M u|| / (|lambda| ||M u||)
+    if (resid && got > 0) {
+        std::vector<double> rh(got);
+        RIGA_CUDA_TRY(c, c->vwork[4].alloc(N));
+        RIGA_CUDA_TRY(c, c->vwork[5].alloc(N));
+        RIGA_CUDA_TRY(c, c->red.alloc(2 * 304));
+        std::vector<double> part(2 * 152);
+        for (int q = 0; q < got; ++q) {
+            const double* u = c->evec_perm.ptr + (long long)q * N;
+            enqueue_spmv(c, 1, u, c->vwork[4].ptr, 0.0);
+            enqueue_spmv(c, 0, u, c->vwork[5].ptr, 0.0);
+            c->stats.n_matvec--;  // reporting, not part of the iteration count
+            resid_partial_kernel<<<152, 256, 0, c->stream>>>(N, c->vwork[4].ptr, c->vwork[5].ptr, c->evals[q], c->red.ptr);
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), c->red.ptr, 2 * 152 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            double ra = 0.0, rb = 0.0;
+            for (int i = 0; i < 152; ++i) {
+                ra += part[2 * i];
+                rb += part[2 * i + 1];
+            }
+            rh[q] = std::sqrt(ra) / (std::fabs(c->evals[q]) * std::sqrt(rb));
+        }
+        if (is_device_ptr(resid)) {
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(resid, rh.data(), got * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        } else {
+            std::memcpy(resid, rh.data(), got * sizeof(double));
+        }
+    }
+    // eigenvectors: back to global numbering, sign convention
+    if (evecs && got > 0) {
+        DevBuf<double> tmp;
+        RIGA_CUDA_TRY(c, tmp.alloc((size_t)N * got));
+        enqueue_permute(c, c->evec_perm.ptr, tmp.ptr, 0, got);
+        sign_fix(c, tmp.ptr, got);
+        int r2 = to_user(c, tmp.ptr, evecs, (size_t)N * got);
+        if (r2) return r2;
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    RIGA_CUDA_TRY(c, cudaGetLastError());
+    return status;
+}
+
+int riga_eig_grad(riga_ctx* c, int k, const double* dL, double* grad_a, double* grad_b) {
+    if (!c || !dL || k < 1) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (c->nev < 1) return set_error(c, RIGA_ESTATE, "riga_eigs first");
+    if (k > c->nev) return set_error(c, RIGA_EINVAL, "k exceeds the computed eigenpairs");
+    const long long ne = c->S.n_elem;
+    DevBuf<double> w, ga, gb;
+    RIGA_CUDA_TRY(c, w.alloc(k));
+    RIGA_CUDA_TRY(c, ga.alloc(ne));
+    RIGA_CUDA_TRY(c, gb.alloc(ne));
+    int rc = to_device(c, dL, w.ptr, k);
+    if (rc) return rc;
+    rc = eig_grad_device(c, k, w.ptr, ga.ptr, gb.ptr);
+    if (rc) return rc;
+    if (grad_a) {
+        rc = to_user(c, ga.ptr, grad_a, ne);
+        if (rc) return rc;
+    }
+    if (grad_b) {
+        rc = to_user(c, gb.ptr, grad_b, ne);
+        if (rc) return rc;
+    }
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RIGA_OK;
+}
+
+int riga_query(riga_ctx* c, long long* N, long long* nnz, long long* nnzL, double* flops) {
+    if (!c) return RIGA_EINVAL;
+    if (c->mesh_key.empty() && !c->analyzed_only) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (N) *N = c->S.N;
+    if (nnz) *nnz = c->S.nnz;
+    if (nnzL) *nnzL = c->S.nnzL;
+    if (flops) *flops = c->S.flops;
+    return RIGA_OK;
+}
+
+int riga_get_symbolic(riga_ctx* c, int* n_nodes, long long* total_idx, int* perm, int* node_ptr, int* parent,
+                      long long* front_ptr, int* front_idx) {
+    if (!c) return RIGA_EINVAL;
+    if (c->mesh_key.empty() && !c->analyzed_only) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    const Symbolic& S = c->S;
+    if (n_nodes) *n_nodes = S.n_nodes;
+    if (total_idx) *total_idx = (long long)S.front_pos.size();
+    if (perm) std::memcpy(perm, S.perm.data(), S.perm.size() * sizeof(int));
+    if (node_ptr) std::memcpy(node_ptr, S.node_ptr.data(), S.node_ptr.size() * sizeof(int));
+    if (parent) std::memcpy(parent, S.parent.data(), S.parent.size() * sizeof(int));
+    if (front_ptr) std::memcpy(front_ptr, S.front_ptr.data(), S.front_ptr.size() * sizeof(long long));
+    if (front_idx)
+        for (size_t i = 0; i < S.front_pos.size(); ++i) front_idx[i] = S.perm[S.front_pos[i]];
+    return RIGA_OK;
+}
+
+int riga_get_matrices(riga_ctx* c, long long* row_ptr, int* col, double* kval, double* mval) {
+    if (!c) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    const Symbolic& S = c->S;
+    if (row_ptr) {
+        DevBuf<long long> t;
+        RIGA_CUDA_TRY(c, t.alloc(S.N + 1));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(t.ptr, S.glob_rowptr.data(), (S.N + 1) * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+        int rc = to_user(c, t.ptr, row_ptr, S.N + 1);
+        if (rc) return rc;
+    }
+    if (col) {
+        DevBuf<int> t;
+        RIGA_CUDA_TRY(c, t.alloc(S.nnz));
+        glob_col_kernel<<<(unsigned)((S.N + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
+                                                                             c->perm_to_glob.ptr, t.ptr);
+        int rc = to_user(c, t.ptr, col, S.nnz);
+        if (rc) return rc;
+    }
+    const double* srcs[2] = {c->Kval.ptr, c->Mval.ptr};
+    double* dsts[2] = {kval, mval};
+    for (int i = 0; i < 2; ++i) {
+        if (!dsts[i]) continue;
+        DevBuf<double> t;
+        RIGA_CUDA_TRY(c, t.alloc(S.nnz));
+        scatter_glob_kernel<<<(unsigned)((S.nnz + 255) / 256), 256, 0, c->stream>>>(S.nnz, c->perm_to_glob.ptr, srcs[i], t.ptr);
+        int rc = to_user(c, t.ptr, dsts[i], S.nnz);
+        if (rc) return rc;
+    }
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RIGA_OK;
+}
+
+int riga_get_factor(riga_ctx* c, double* D, long long* Lptr, double* L) {
+    if (!c) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->factored) return set_error(c, RIGA_ESTATE, "riga_factor first");
+    const Symbolic& S = c->S;
+    if (Lptr) {
+        long long at = 0;
+        for (int f = 0; f < S.n_nodes; ++f) {
+            Lptr[f] = at;
+            at += (long long)S.n[f] * S.k[f];
+        }
+        Lptr[S.n_nodes] = at;
+    }
+    if (D) RIGA_CUDA_TRY(c, cudaMemcpy(D, c->D.ptr, S.N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (L) {
+        long long at = 0;
+        for (int f = 0; f < S.n_nodes; ++f) {
+            long long cnt = (long long)S.n[f] * S.k[f];  // first k columns, leading dimension n
+            if (c->precision == RIGA_FP64) {
+                RIGA_CUDA_TRY(c, cudaMemcpy(L + at, c->pool64.ptr + S.front_off[f], cnt * sizeof(double), cudaMemcpyDeviceToHost));
+            } else {
+                std::vector<float> tmp(cnt);
+                RIGA_CUDA_TRY(c, cudaMemcpy(tmp.data(), c->pool32.ptr + S.front_off[f], cnt * sizeof(float), cudaMemcpyDeviceToHost));
+                for (long long i = 0; i < cnt; ++i) L[at + i] = tmp[i];
+            }
+            at += cnt;
+        }
+    }
+    return RIGA_OK;
+}
+
+int riga_spmv(riga_ctx* c, int which, const double* x, double* y) {
+    if (!c || !x || !y) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (which < 0 || which > 2) return set_error(c, RIGA_EINVAL, "which must be 0 (M), 1 (K) or 2 (K - sigma M)");
+    const long long N = c->S.N;
+    for (int i = 0; i < 3; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    int rc = to_device(c, x, c->vwork[0].ptr, N);
+    if (rc) return rc;
+    enqueue_permute(c, c->vwork[0].ptr, c->vwork[1].ptr, 1, 1);
+    rc = enqueue_spmv(c, which, c->vwork[1].ptr, c->vwork[2].ptr, c->sigma);
+    if (rc) return rc;
+    enqueue_permute(c, c->vwork[2].ptr, c->vwork[0].ptr, 0, 1);
+    rc = to_user(c, c->vwork[0].ptr, y, N);
+    if (rc) return rc;
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RIGA_OK;
+}
+
+int riga_stats(riga_ctx* c, long long* n_fact, long long* n_solve, long long* n_matvec, long long* steps,
+               double* t_fact_ms, double* t_lanczos_ms) {
+    if (!c) return RIGA_EINVAL;
+    if (n_fact) *n_fact = c->stats.n_fact;
+    if (n_solve) *n_solve = c->stats.n_solve;
+    if (n_matvec) *n_matvec = c->stats.n_matvec;
+    if (steps) *steps = c->stats.steps;
+    if (t_fact_ms) *t_fact_ms = c->stats.t_fact_ms;
+    if (t_lanczos_ms) *t_lanczos_ms = c->stats.t_lanczos_ms;
+    return RIGA_OK;
+}
+
+}  // extern "C"

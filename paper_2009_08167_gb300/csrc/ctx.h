@@ -1,0 +1,139 @@
+// Internal context of the riga library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/riga.h"
+#include "symbolic.h"
+
+namespace riga {
+
+// Owning device buffer (cudaMalloc/cudaFree).
+template <typename T>
+struct DevBuf {
+    T* ptr = nullptr;
+    size_t count = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        count = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        if (ptr && n <= count) return cudaSuccess;  // grow-only
+        release();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc((void**)&ptr, n * sizeof(T));
+        if (e == cudaSuccess) count = n;
+        else ptr = nullptr;
+        return e;
+    }
+    cudaError_t upload(const std::vector<T>& v, cudaStream_t s) {
+        cudaError_t e = alloc(v.size());
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpyAsync(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+};
+
+struct Stats {
+    long long n_fact = 0, n_solve = 0, n_matvec = 0, steps = 0;
+    double t_fact_ms = 0.0, t_lanczos_ms = 0.0;
+};
+
+}  // namespace riga
+
+struct riga_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+
+    // ------------------------------------------------------------ problem
+    bool assembled = false;
+    bool analyzed_only = false;
+    bool factored = false;
+    std::vector<int> mesh_key;
+    riga::Symbolic S;
+    std::vector<double> coefK, coefM;  // host copies (empty = constant)
+
+    // symbolic arrays on the device
+    riga::DevBuf<long long> rowptr, front_off, front_ptr, rel_ptr, upd_off, scatter, perm_to_glob, glob_rowptr;
+    riga::DevBuf<int> col, perm, ipos, node_ptr, kk, nn, front_pos, child_ptr, child_list, rel, level_nodes, parent;
+    std::vector<int> level_nodes_off;  // offsets of each level in level_nodes
+    riga::DevBuf<riga::PanelItem> pitems;
+    riga::DevBuf<riga::TileItem> titems;
+    riga::DevBuf<riga::ExtItem> eitems;
+    // per-direction 1D data
+    riga::DevBuf<int> kv[3], elem_first[3];
+    riga::DevBuf<double> Ke1[3], Me1[3], Kb1[3], Mb1[3];
+    riga::DevBuf<double> dcoefK, dcoefM;
+
+    // matrices in elimination order (CSR of rowptr/col)
+    riga::DevBuf<double> Kval, Mval;
+
+    // --------------------------------------------------------------- factor
+    int precision = RIGA_FP64;
+    double sigma = 0.0;
+    riga::DevBuf<double> pool64;
+    riga::DevBuf<float> pool32;
+    riga::DevBuf<double> D;      // pivots in elimination order
+    riga::DevBuf<int> flag;      // device error word (bit 0: pivot breakdown)
+    riga::DevBuf<long long> neg; // inertia counter
+    long long inertia = -1;
+
+    // ---------------------------------------------------------------- solve
+    riga::DevBuf<double> upd;          // forward-solve update vectors
+    riga::DevBuf<double> vwork[6];     // N-vectors (permuted order)
+    riga::DevBuf<double> hostbuf_dev;  // staging for host arrays
+    riga::DevBuf<double> red;          // reduction scratch
+    int ir_sweeps = 4;                 // refinement sweeps per solve inside Lanczos (FP32 factor)
+
+    // -------------------------------------------------------------- Lanczos
+    int opt_slice = 0, opt_precision = RIGA_FP64, opt_max_steps = 0, opt_extra = 2;
+    unsigned long long opt_seed = 1;
+    riga::DevBuf<double> V, MV;        // basis storage: locked vectors, then the run's vectors
+    riga::DevBuf<double> coef;         // Gram-Schmidt coefficients
+    riga::DevBuf<double> partial;      // per-chunk partial dots
+    riga::DevBuf<double> ab;           // alpha / beta of the current run
+    riga::DevBuf<double> Wd;           // Ritz coefficient matrix
+    riga::DevBuf<double> evec_perm;    // final eigenvectors, permuted order, N x nev
+    std::vector<double> evals;         // final eigenvalues
+    int nev = 0;
+    riga::Stats stats;
+};
+
+namespace riga {
+
+// error helpers
+int set_error(riga_ctx* c, int code, const std::string& msg);
+#define RIGA_CUDA_TRY(ctx, call)                                                                 \
+    do {                                                                                         \
+        cudaError_t _e = (call);                                                                 \
+        if (_e != cudaSuccess)                                                                   \
+            return ::riga::set_error((ctx), RIGA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// assemble.cu
+int assemble_device(riga_ctx* c);
+// factor.cu
+int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
+int finish_factor(riga_ctx* c);   // sync, read flag and inertia
+// solve.cu
+int enqueue_solve(riga_ctx* c, double* y);  // y := A^{-1} y in permuted order (one pass)
+int enqueue_spmv(riga_ctx* c, int which, const double* x, double* y, double alpha_shift);
+void enqueue_permute(riga_ctx* c, const double* in, double* out, int to_perm, int ncols);
+int solve_refined(riga_ctx* c, double* y, double* work_x, double* work_r, double tol, int max_sweeps,
+                  int check, int* sweeps_out);
+// lanczos.cu
+int run_eigs(riga_ctx* c, int k, double sigma, double tol, int* nconv);
+// adjoint.cu
+int eig_grad_device(riga_ctx* c, int k, const double* w_dev, double* ga_dev, double* gb_dev);
+// tridiag.cpp
+void tridiag_eig(int m, const double* alpha, const double* beta, double* theta, double* Z, bool vectors);
+
+}  // namespace riga

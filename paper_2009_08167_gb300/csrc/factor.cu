@@ -1,0 +1,264 @@
+// Multifrontal LDL^T of A = K - sigma M (Sec. 4.2 and its Remark on inertia),
+// fronts in FP64 or FP32, 1x1 pivots without pivoting.
+//
+// The fronts live side by side in one pool (column-major, leading dimension
+// n_F, lower triangle used).  Per assembly-tree level, leaves to root:
+//   extend_add_kernel  children's Schur complements into the parents
+//                      (child rank 0, then rank 1: deterministic, no atomics);
+//   for each panel step s (panel columns [s*nb, s*nb+kb)):
+//     diag_kernel      LDL^T of the kb x kb diagonal block in shared memory,
+//                      pivots to D and the front diagonal, breakdown flag;
+//     trsm_kernel      L21 = A21 L11^{-T} D^{-1}, one thread per row;
+//     update_kernel    A22 -= L21 D L21^T on 64x64 lower tiles of the
+//                      trailing matrix (remaining fully summed part and the
+//                      Schur complement).
+// All items of one launch span every front of the level.  The original
+// entries are scattered into all fronts once, before the first level.
+#include "ctx.h"
+
+namespace riga {
+
+constexpr int NB = 32;    // panel width
+constexpr int TILE = 64;  // update tile
+constexpr int RB = 64;    // TRSM rows per block
+
+template <typename T>
+__global__ void scatter_kernel(long long nnz, const long long* __restrict__ scatter, const double* __restrict__ K,
+                               const double* __restrict__ M, double sigma, T* __restrict__ pool) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    long long off = scatter[e];
+    if (off >= 0) pool[off] = (T)(K[e] - sigma * M[e]);
+}
+
+template <typename T>
+__global__ void extend_add_kernel(const ExtItem* __restrict__ items, const int* __restrict__ parent,
+                                  const long long* __restrict__ front_off, const int* __restrict__ kk,
+                                  const int* __restrict__ nn, const int* __restrict__ rel,
+                                  const long long* __restrict__ rel_ptr, T* __restrict__ pool) {
+    const ExtItem it = items[blockIdx.x];
+    const int c = it.child, P = parent[c];
+    const int kc = kk[c], nc = nn[c], np = nn[P];
+    const int m = nc - kc;
+    const T* src = pool + front_off[c] + (long long)kc * nc + kc;
+    T* dst = pool + front_off[P];
+    const int* r = rel + rel_ptr[c];
+    for (int j = it.c0; j < it.c1; ++j) {
+        const long long cj = (long long)r[j] * np;
+        for (int i = j + threadIdx.x; i < m; i += blockDim.x) dst[cj + r[i]] += src[(long long)j * nc + i];
+    }
+}
+
+// LDL^T of one kb x kb diagonal block per front (block of 256 threads).
+template <typename T>
+__global__ void diag_kernel(const PanelItem* __restrict__ items, const int* __restrict__ kk,
+                            const int* __restrict__ nn, const long long* __restrict__ front_off,
+                            const int* __restrict__ node_ptr, T* __restrict__ pool, double* __restrict__ D,
+                            int* __restrict__ flag) {
+    __shared__ T Ls[NB][NB + 1];
+    const PanelItem it = items[blockIdx.x];
+    const int F = it.front, k = kk[F], n = nn[F], j0 = it.r0;
+    const int kb = min(NB, k - j0);
+    T* A = pool + front_off[F];
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int r = idx % kb, cc = idx / kb;
+        Ls[r][cc] = (r >= cc) ? A[(long long)(j0 + cc) * n + j0 + r] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        const T d = Ls[j][j];
+        if (threadIdx.x == 0 && !(d != T(0) && isfinite((double)d))) atomicOr(flag, 1);
+        // trailing update of the block: a_rc -= a_rj a_cj / d, j < c <= r
+        const int m = kb - j - 1;
+        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+            int r = j + 1 + idx % m, cc = j + 1 + idx / m;
+            if (r >= cc) Ls[r][cc] -= Ls[r][j] * Ls[cc][j] / d;
+        }
+        __syncthreads();
+        for (int r = j + 1 + threadIdx.x; r < kb; r += blockDim.x) Ls[r][j] /= d;
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int r = idx % kb, cc = idx / kb;
+        if (r >= cc) A[(long long)(j0 + cc) * n + j0 + r] = Ls[r][cc];
+    }
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) D[node_ptr[F] + j0 + t] = (double)Ls[t][t];
+}
+
+// Rows r0..r0+RB-1 of the panel below the diagonal block (blockDim = RB).
+template <typename T>
+__global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const int* __restrict__ kk,
+                            const int* __restrict__ nn, const long long* __restrict__ front_off,
+                            T* __restrict__ pool) {
+    __shared__ T Ls[NB][NB + 1];
+    __shared__ T ds[NB];
+    const PanelItem it = items[blockIdx.x];
+    const int F = it.front, k = kk[F], n = nn[F];
+    const int kb = min(NB, k - j0);
+    T* A = pool + front_off[F];
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int r = idx % kb, cc = idx / kb;
+        if (r > cc) Ls[r][cc] = A[(long long)(j0 + cc) * n + j0 + r];
+        if (r == cc) ds[r] = A[(long long)(j0 + cc) * n + j0 + r];
+    }
+    __syncthreads();
+    const int r = it.r0 + threadIdx.x;
+    if (r >= n) return;
+    T x[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+        if (t < kb) x[t] = A[(long long)(j0 + t) * n + r];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        if (t < kb) {
+            T s = x[t];
+#pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (u < t) s -= x[u] * ds[u] * Ls[t][u];
+            x[t] = s / ds[t];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+        if (t < kb) A[(long long)(j0 + t) * n + r] = x[t];
+}
+
+// C[i0:i0+64, j0:j0+64] -= L[:, panel] D L[:, panel]^T (256 threads, 4x4 each)
+template <typename T>
+__global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict__ items, int p0,
+                                                     const int* __restrict__ kk, const int* __restrict__ nn,
+                                                     const long long* __restrict__ front_off,
+                                                     const int* __restrict__ node_ptr, const double* __restrict__ D,
+                                                     T* __restrict__ pool) {
+    __shared__ T As[NB][TILE];
+    __shared__ T Bs[NB][TILE];
+    const TileItem it = items[blockIdx.x];
+    const int F = it.front, k = kk[F], n = nn[F];
+    const int kb = min(NB, k - p0);
+    T* A = pool + front_off[F];
+    const double* d = D + node_ptr[F] + p0;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < NB * TILE; idx += 256) {
+        int rr = idx % TILE, t = idx / TILE;
+        T a = T(0), b = T(0);
+        if (t < kb) {
+            int gi = it.i0 + rr, gj = it.j0 + rr;
+            if (gi < n) a = A[(long long)(p0 + t) * n + gi];
+            if (gj < n) b = A[(long long)(p0 + t) * n + gj] * (T)d[t];
+        }
+        As[t][rr] = a;
+        Bs[t][rr] = b;
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int t = 0; t < kb; ++t) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[t][tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[t][ty + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int gj = it.j0 + ty + 16 * b;
+        if (gj >= n) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int gi = it.i0 + tx + 16 * a;
+            if (gi < n && gi >= gj) A[(long long)gj * n + gi] -= acc[a][b];
+        }
+    }
+}
+
+__global__ void inertia_kernel(long long N, const double* __restrict__ D, long long* __restrict__ neg) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int local = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        local += (D[i] < 0.0) ? 1 : 0;
+    if (local) atomicAdd(&cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt) atomicAdd((unsigned long long*)neg, (unsigned long long)cnt);
+}
+
+template <typename T>
+static int enqueue_factor_t(riga_ctx* c, T* pool) {
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(pool, 0, (size_t)S.pool_size * sizeof(T), st));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), st));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
+    if (S.nnz > 0)
+        scatter_kernel<T><<<(unsigned)((S.nnz + 255) / 256), 256, 0, st>>>(S.nnz, c->scatter.ptr, c->Kval.ptr,
+                                                                          c->Mval.ptr, c->sigma, pool);
+    for (int l = 0; l < S.n_levels; ++l) {
+        const LevelPlan& P = S.levels[l];
+        for (int rank = 0; rank < 2; ++rank) {
+            int cnt = P.ext_end[rank] - P.ext_begin[rank];
+            if (cnt > 0)
+                extend_add_kernel<T><<<cnt, 128, 0, st>>>(c->eitems.ptr + P.ext_begin[rank], c->parent.ptr,
+                                                          c->front_off.ptr, c->kk.ptr, c->nn.ptr, c->rel.ptr,
+                                                          c->rel_ptr.ptr, pool);
+        }
+        for (const StepRange& R : P.steps) {
+            const int j0 = R.s * NB;
+            if (R.d_end > R.d_begin)
+                diag_kernel<T><<<R.d_end - R.d_begin, 256, 0, st>>>(c->pitems.ptr + R.d_begin, c->kk.ptr, c->nn.ptr,
+                                                                    c->front_off.ptr, c->node_ptr.ptr, pool, c->D.ptr,
+                                                                    c->flag.ptr);
+            if (R.p_end > R.p_begin)
+                trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
+                                                                   c->nn.ptr, c->front_off.ptr, pool);
+            if (R.t_end > R.t_begin)
+                update_kernel<T><<<R.t_end - R.t_begin, 256, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
+                                                                      c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr,
+                                                                      c->D.ptr, pool);
+        }
+    }
+    inertia_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->neg.ptr);
+    RIGA_CUDA_TRY(c, cudaGetLastError());
+    return RIGA_OK;
+}
+
+int enqueue_factor(riga_ctx* c) {
+    Symbolic& S = c->S;
+    if (S.nb != NB || S.tile != TILE || S.rowblk != RB) return set_error(c, RIGA_EINVAL, "schedule/kernel tile mismatch");
+    RIGA_CUDA_TRY(c, c->D.alloc(S.N));
+    RIGA_CUDA_TRY(c, c->flag.alloc(1));
+    RIGA_CUDA_TRY(c, c->neg.alloc(1));
+    if (c->precision == RIGA_FP64) {
+        c->pool32.release();
+        if (c->pool64.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp64)");
+        return enqueue_factor_t<double>(c, c->pool64.ptr);
+    }
+    c->pool64.release();
+    if (c->pool32.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp32)");
+    return enqueue_factor_t<float>(c, c->pool32.ptr);
+}
+
+int finish_factor(riga_ctx* c) {
+    int flag = 0;
+    long long neg = 0;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(&neg, c->neg.ptr, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->inertia = neg;
+    if (flag & 1) {
+        c->factored = false;
+        return set_error(c, RIGA_EPIVOT, "zero or non-finite pivot in LDL^T (shift at an eigenvalue?)");
+    }
+    c->factored = true;
+    return RIGA_OK;
+}
+
+}  // namespace riga

@@ -1,0 +1,542 @@
+// Shift-and-invert Lanczos in the M-inner product (Sec. 4.1-4.2 of arXiv
+// 2009.08167) on H = (K - sigma M)^{-1} M, vectors in elimination order.
+//
+// Per step j (Eq. LanczosAlphaBeta): w = H v_j = A^{-1} (M v_j) with the
+// stored M v_j; full reorthogonalization (Sec. 4.2, "with respect to all
+// previously stored Lanczos vectors") by two classical Gram-Schmidt passes in
+// the M-inner product against [Y V_j] (Y = locked eigenvectors of this and
+// earlier shifts: deflation); alpha_j = v_j^T M w (first-pass coefficient plus
+// its correction); beta_{j+1} = ||w||_M; v_{j+1} = w / beta_{j+1}; M v_{j+1}
+// stored from the same SpMV.  Rayleigh-Ritz on T_m (Eq. RitzValues) on the
+// host every few steps with the last eigenvector row only (residual
+// estimates |beta_{m+1} w_m|), Ritz vectors V_m W by a device GEMM.
+// Converged pairs are locked; runs restart from a fresh random vector until
+// the Sylvester inertia at a check shift in a spectral gap equals the number
+// of locked eigenvalues below it (Remark on inertia); with spectrum slicing
+// that check shift becomes the next shift.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "ctx.h"
+
+namespace riga {
+
+constexpr int CH = 256;  // rows per chunk of the tall-skinny kernels
+
+__global__ void __launch_bounds__(256) gemvT_partial_kernel(const double* __restrict__ B, long long ld, int J,
+                                                            const double* __restrict__ w, long long N,
+                                                            double* __restrict__ partial, int pstride) {
+    __shared__ double ws[CH];
+    const long long r0 = (long long)blockIdx.x * CH;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    ws[tid] = (r0 + tid < N) ? w[r0 + tid] : 0.0;
+    __syncthreads();
+    const int rows = (int)min((long long)CH, N - r0);
+    for (int j = warp; j < J; j += 8) {
+        const double* Bc = B + (long long)j * ld + r0;
+        double s = 0.0;
+        for (int r = lane; r < rows; r += 32) s += Bc[r] * ws[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) partial[(long long)blockIdx.x * pstride + j] = s;
+    }
+}
+
+__global__ void reduce_cols_kernel(const double* __restrict__ partial, int nch, int J, int pstride,
+                                   double* __restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += partial[(long long)c * pstride + j];
+    out[j] = s;
+}
+
+// w -= V c1 on this chunk, then partial dots MV^T w
+__global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restrict__ V, const double* __restrict__ MV,
+                                                           long long ld, int J, const double* __restrict__ c1,
+                                                           double* __restrict__ w, long long N,
+                                                           double* __restrict__ partial, int pstride) {
+    extern __shared__ double sh[];
+    double* cs = sh;       // J
+    double* ws = sh + J;   // CH
+    const long long r0 = (long long)blockIdx.x * CH;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < J; j += blockDim.x) cs[j] = c1[j];
+    __syncthreads();
+    const long long r = r0 + tid;
+    double v = 0.0;
+    if (r < N) {
+        v = w[r];
+        for (int j = 0; j < J; ++j) v -= V[(long long)j * ld + r] * cs[j];
+        w[r] = v;
+    }
+    ws[tid] = v;
+    __syncthreads();
+    const int rows = (int)min((long long)CH, N - r0);
+    for (int j = warp; j < J; j += 8) {
+        const double* Bc = MV + (long long)j * ld + r0;
+        double s = 0.0;
+        for (int q = lane; q < rows; q += 32) s += Bc[q] * ws[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) partial[(long long)blockIdx.x * pstride + j] = s;
+    }
+}
+
+__global__ void gemv_update_kernel(const double* __restrict__ V, long long ld, int J, const double* __restrict__ c,
+                                   double* __restrict__ w, long long N) {
+    extern __shared__ double cs[];
+    for (int j = threadIdx.x; j < J; j += blockDim.x) cs[j] = c[j];
+    __syncthreads();
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    double v = w[r];
+    for (int j = 0; j < J; ++j) v -= V[(long long)j * ld + r] * cs[j];
+    w[r] = v;
+}
+
+// y = M x over the permuted CSR (16 lanes per row) and per-block partial x.y
+__global__ void __launch_bounds__(256) spmv_dot_kernel(long long N, const long long* __restrict__ rowptr,
+                                                       const int* __restrict__ col, const double* __restrict__ Mv,
+                                                       const double* __restrict__ x, double* __restrict__ y,
+                                                       double* __restrict__ partial) {
+    __shared__ double red[16];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long row = t / 16;
+    const int lane = (int)(t % 16);
+    double s = 0.0;
+    if (row < N)
+        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Mv[e] * x[col[e]];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+    double d = 0.0;
+    if (row < N && lane == 0) {
+        y[row] = s;
+        d = s * x[row];
+    }
+    if (lane == 0) red[threadIdx.x / 16] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (int)(blockDim.x / 16); ++i) tot += red[i];
+        partial[blockIdx.x] = tot;
+    }
+}
+
+__global__ void finalize_kernel(const double* __restrict__ partial, int nb, const double* __restrict__ c1,
+                                const double* __restrict__ c2, int col, int j, double* __restrict__ alpha,
+                                double* __restrict__ beta) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (j >= 0) alpha[j] = c1[col] + c2[col];
+        beta[j + 1] = sqrt(fmax(sh[0], 0.0));
+    }
+}
+
+__global__ void normalize_kernel(long long N, const double* __restrict__ w, const double* __restrict__ Mw,
+                                 const double* __restrict__ bptr, double* __restrict__ v, double* __restrict__ mv) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const double b = *bptr;
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    v[r] = w[r] * inv;
+    mv[r] = Mw[r] * inv;
+}
+
+// U[:, i] = sum_j V[:, j] W[j, i] for i < nsel (rows by threads, 16 outputs each)
+__global__ void __launch_bounds__(256) gemm_ritz_kernel(const double* __restrict__ V, long long ld, int J,
+                                                        const double* __restrict__ W, int ldw, int nsel,
+                                                        double* __restrict__ U, long long ldu, long long N) {
+    __shared__ double Ws[128][16];
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = blockIdx.y * 16;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int j0 = 0; j0 < J; j0 += 128) {
+        const int jn = min(128, J - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 128 * 16; t += blockDim.x) {
+            int jj = t / 16, q = t % 16;
+            Ws[jj][q] = (jj < jn && i0 + q < nsel) ? W[(long long)(i0 + q) * ldw + j0 + jj] : 0.0;
+        }
+        __syncthreads();
+        if (r < N) {
+            for (int jj = 0; jj < jn; ++jj) {
+                double v = V[(long long)(j0 + jj) * ld + r];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] += v * Ws[jj][q];
+            }
+        }
+    }
+    if (r < N)
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (i0 + q < nsel) U[(long long)(i0 + q) * ldu + r] = acc[q];
+}
+
+// sign convention: largest |u| positive, lowest index on ties (global numbering)
+__global__ void sign_fix_kernel(long long N, double* __restrict__ U, long long ldu) {
+    __shared__ double bv[256];
+    __shared__ long long bi[256];
+    double* u = U + (long long)blockIdx.x * ldu;
+    double best = -1.0;
+    long long idx = 0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+        double a = fabs(u[i]);
+        if (a > best) {
+            best = a;
+            idx = i;
+        }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            double a = bv[threadIdx.x + o];
+            long long ia = bi[threadIdx.x + o];
+            if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) {
+                bv[threadIdx.x] = a;
+                bi[threadIdx.x] = ia;
+            }
+        }
+        __syncthreads();
+    }
+    const bool flip = u[bi[0]] < 0.0;
+    __syncthreads();
+    if (flip)
+        for (long long i = threadIdx.x; i < N; i += blockDim.x) u[i] = -u[i];
+}
+
+__global__ void copy_cols_kernel(long long N, int ncols, const double* __restrict__ src, long long lds,
+                                 double* __restrict__ dst, long long ldd) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * ncols) return;
+    long long cidx = t / N, r = t % N;
+    dst[cidx * ldd + r] = src[cidx * lds + r];
+}
+
+// --------------------------------------------------------------- host side
+namespace {
+
+struct Run {
+    riga_ctx* c;
+    long long N, ld;
+    int cap;       // columns of V / MV
+    int nch;       // chunks
+    double* w;
+    double* Mw;
+    double* xw;
+    double* rw;
+    double* c1;
+    double* c2;
+    double* alpha;
+    double* beta;
+};
+
+uint64_t splitmix(uint64_t& s) {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+int ortho_pass(Run& R, int col0, int J, double* w) {
+    riga_ctx* c = R.c;
+    cudaStream_t st = c->stream;
+    if (J <= 0) return RIGA_OK;
+    gemvT_partial_kernel<<<R.nch, 256, 0, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap);
+    reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1);
+    size_t sm = (size_t)(J + CH) * sizeof(double);
+    update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, c->MV.ptr + col0 * R.ld, R.ld, J, R.c1, w,
+                                                R.N, c->partial.ptr, R.cap);
+    reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2);
+    gemv_update_kernel<<<(unsigned)((R.N + 255) / 256), 256, (size_t)J * sizeof(double), st>>>(
+        c->V.ptr + col0 * R.ld, R.ld, J, R.c2, w, R.N);
+    return RIGA_OK;
+}
+
+// w -> M-normalised into column `col` of V / MV; beta slot receives the norm
+void normalize_into(Run& R, double* w, int col, int jslot) {
+    riga_ctx* c = R.c;
+    cudaStream_t st = c->stream;
+    const unsigned nbs = (unsigned)((R.N * 16 + 255) / 256);
+    spmv_dot_kernel<<<nbs, 256, 0, st>>>(R.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, R.Mw, c->red.ptr);
+    c->stats.n_matvec++;
+    finalize_kernel<<<1, 256, 0, st>>>(c->red.ptr, (int)nbs, R.c1, R.c2, col - 1, jslot, R.alpha, R.beta);
+    normalize_kernel<<<(unsigned)((R.N + 255) / 256), 256, 0, st>>>(R.N, w, R.Mw, R.beta + jslot + 1,
+                                                                     c->V.ptr + col * R.ld, c->MV.ptr + col * R.ld);
+}
+
+int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    c->sigma = sigma;
+    c->precision = precision;
+    cudaEventRecord(e0, c->stream);
+    int rc = enqueue_factor(c);
+    if (rc == RIGA_OK) {
+        cudaEventRecord(e1, c->stream);
+        rc = finish_factor(c);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->stats.t_fact_ms += ms;
+        c->stats.n_fact++;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (nu) *nu = c->inertia;
+    return rc;
+}
+
+}  // namespace
+
+int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    const long long N = S.N;
+    if (k < 1 || k >= N) return set_error(c, RIGA_EINVAL, "k must be in 1..N-1");
+    const int slice = (c->opt_slice > 0 && c->opt_slice < k) ? c->opt_slice : k;
+    const int extra = c->opt_extra > 0 ? c->opt_extra : 2;
+    const int prec = c->opt_precision;
+    const double tol_est = 1e-2 * tol;
+    const double gap_rel = 1e-6;
+    int wmax = slice + extra;
+    int m_cap = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(3 * wmax, wmax + 40);
+    m_cap = (int)std::min<long long>(m_cap, N - 1);
+    const int lock_cap = k + extra + 64;
+    Run R;
+    R.c = c;
+    R.N = N;
+    R.ld = N;
+    R.cap = lock_cap + m_cap + 1;
+    R.nch = (int)((N + CH - 1) / CH);
+    if (c->V.alloc((size_t)N * R.cap) != cudaSuccess || c->MV.alloc((size_t)N * R.cap) != cudaSuccess)
+        return set_error(c, RIGA_ENOMEM, "Lanczos basis");
+    RIGA_CUDA_TRY(c, c->partial.alloc((size_t)R.nch * R.cap));
+    RIGA_CUDA_TRY(c, c->coef.alloc(2 * (size_t)R.cap));
+    RIGA_CUDA_TRY(c, c->ab.alloc(2 * (size_t)m_cap + 4));
+    RIGA_CUDA_TRY(c, c->red.alloc((size_t)((N * 16 + 255) / 256) + 1024));
+    for (int i = 0; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    R.w = c->vwork[0].ptr;
+    R.Mw = c->vwork[1].ptr;
+    R.xw = c->vwork[2].ptr;
+    R.rw = c->vwork[3].ptr;
+    R.c1 = c->coef.ptr;
+    R.c2 = c->coef.ptr + R.cap;
+    R.alpha = c->ab.ptr;
+    R.beta = c->ab.ptr + m_cap + 2;
+    c->stats = Stats();
+
+    std::vector<double> lam;      // locked eigenvalues, in column order of V
+    int nlock = 0;
+    long long nu0 = 0, nu_chk = 0;
+    int rc = factor_at(c, sigma0, prec, &nu0);
+    if (rc) return rc;
+    double cur_sigma = sigma0;
+    double factored_sigma = sigma0;
+    int confirmed = 0;
+    int target = std::min(k, slice);
+    int need = target + extra;  // locked pairs above sigma0 wanted before the next check
+    uint64_t seed = c->opt_seed ? c->opt_seed : 1;
+    int runs = 0, fruitless = 0;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    std::vector<double> h_ab, theta, zl, Zf, Wsel;
+    std::vector<double> hv(N);
+    int status = RIGA_OK;
+
+    while (true) {
+        if (nlock >= need) {
+            // completeness check by inertia at a gap after the target count
+            std::vector<double> sl(lam);
+            std::sort(sl.begin(), sl.end());
+            int gi = -1;
+            for (int i = std::max(target, 1); i < (int)sl.size(); ++i)
+                if (sl[i] - sl[i - 1] > gap_rel * std::fabs(sl[i])) { gi = i; break; }
+            if (gi < 0) {
+                need = nlock + extra;
+                continue;
+            }
+            const double sp = 0.5 * (sl[gi - 1] + sl[gi]);
+            rc = factor_at(c, sp, prec, &nu_chk);
+            if (rc) { status = rc; break; }
+            factored_sigma = sp;
+            const long long found = gi;  // locked eigenvalues below sp (all are > sigma0)
+            if (nu_chk - nu0 == found) {
+                confirmed = gi;
+                if (confirmed >= k) break;
+                target = std::min(k, confirmed + slice);
+                need = std::max(need, target + extra);
+                cur_sigma = sp;  // next slice starts at the check shift (already factored)
+            } else if (nu_chk - nu0 > found) {
+                // eigenvalues missing below sp (degenerate copies): restart at the current shift
+                need = nlock + (int)(nu_chk - nu0 - found);
+            } else {
+                status = set_error(c, RIGA_ENOCONV, "more locked pairs than the inertia allows");
+                break;
+            }
+            continue;
+        }
+        if (++runs > 60 || fruitless > 4) {
+            status = RIGA_ENOCONV;
+            break;
+        }
+        if (factored_sigma != cur_sigma) {
+            rc = factor_at(c, cur_sigma, prec, nullptr);
+            if (rc) { status = rc; break; }
+            factored_sigma = cur_sigma;
+        }
+        const int want_run = std::max(need - nlock, 1);
+        int m_max = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(3 * want_run, want_run + 40);
+        m_max = std::min(m_max, m_cap);
+        m_max = (int)std::min<long long>(m_max, N - nlock - 1);
+        if (m_max < 1) { status = RIGA_ENOCONV; break; }
+        if (nlock + m_max + 1 > R.cap) { status = set_error(c, RIGA_ENOMEM, "Lanczos basis capacity"); break; }
+        const int col0 = nlock;
+        cudaEventRecord(ev0, st);
+        // random start vector, M-orthogonal to the locked ones
+        for (long long i = 0; i < N; ++i) {
+            uint64_t u = splitmix(seed);
+            hv[i] = ((double)(u >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+        }
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(R.w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (nlock > 0) ortho_pass(R, 0, nlock, R.w);
+        normalize_into(R, R.w, col0, -1);
+        int m = 0;
+        bool converged = false;
+        for (int j = 0; j < m_max; ++j) {
+            const int col = col0 + j;
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(R.w, c->MV.ptr + (long long)col * R.ld, N * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, st));
+            rc = solve_refined(c, R.w, R.xw, R.rw, 0.0, c->ir_sweeps, 0, nullptr);
+            if (rc) { status = rc; break; }
+            ortho_pass(R, 0, col + 1, R.w);
+            normalize_into(R, R.w, col + 1, j);
+            c->stats.steps++;
+            m = j + 1;
+            if (m % 10 == 0 || m == m_max) {
+                h_ab.resize(2 * (size_t)m_cap + 4);
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_ab.data(), c->ab.ptr, h_ab.size() * sizeof(double),
+                                                 cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+                const double* a = h_ab.data();
+                const double* b = h_ab.data() + m_cap + 2;  // b[i] = beta_i (b[0] = start norm)
+                theta.assign(m, 0.0);
+                zl.assign(m, 0.0);
+                tridiag_eig(m, a, b + 1, theta.data(), zl.data(), false);
+                const double bm = b[m];
+                // acceptable Ritz values: lambda above sigma0, by decreasing |theta|
+                std::vector<int> ord;
+                for (int i = 0; i < m; ++i)
+                    if (theta[i] != 0.0 && cur_sigma + 1.0 / theta[i] > sigma0) ord.push_back(i);
+                std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+                int ok = 0;
+                bool all = (int)ord.size() >= want_run;
+                for (int q = 0; q < (int)ord.size() && q < want_run; ++q) {
+                    int i = ord[q];
+                    if (std::fabs(bm * zl[i]) <= tol_est * std::fabs(theta[i])) ++ok;
+                    else all = false;
+                }
+                if ((all && ok >= want_run) || bm <= 1e-300) {
+                    converged = true;
+                    break;
+                }
+            }
+        }
+        if (status) break;
+        // Rayleigh-Ritz with vectors, select converged acceptable pairs
+        h_ab.resize(2 * (size_t)m_cap + 4);
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_ab.data(), c->ab.ptr, h_ab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        const double* a = h_ab.data();
+        const double* b = h_ab.data() + m_cap + 2;
+        theta.assign(m, 0.0);
+        Zf.assign((size_t)m * m, 0.0);
+        tridiag_eig(m, a, b + 1, theta.data(), Zf.data(), true);
+        const double bm = b[m];
+        std::vector<int> sel;
+        for (int i = 0; i < m; ++i) {
+            if (theta[i] == 0.0) continue;
+            double l = cur_sigma + 1.0 / theta[i];
+            if (!(l > sigma0)) continue;
+            double est = std::fabs(bm * Zf[(size_t)i * m + (m - 1)]);
+            if (est <= tol_est * std::fabs(theta[i])) sel.push_back(i);
+        }
+        std::sort(sel.begin(), sel.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+        int room = lock_cap - nlock;
+        if ((int)sel.size() > room) sel.resize(room);
+        const int nsel = (int)sel.size();
+        if (nsel > 0) {
+            Wsel.assign((size_t)m * nsel, 0.0);
+            for (int q = 0; q < nsel; ++q)
+                for (int r = 0; r < m; ++r) Wsel[(size_t)q * m + r] = Zf[(size_t)sel[q] * m + r];
+            RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel));
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, Wsel.data(), Wsel.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
+            double* U = c->evec_perm.ptr;
+            double* MU = c->evec_perm.ptr + (size_t)N * nsel;
+            dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
+            gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N);
+            gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N);
+            long long t = N * nsel;
+            copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, U, N, c->V.ptr + (long long)nlock * R.ld, R.ld);
+            copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, MU, N, c->MV.ptr + (long long)nlock * R.ld, R.ld);
+            for (int q = 0; q < nsel; ++q) lam.push_back(cur_sigma + 1.0 / theta[sel[q]]);
+            nlock += nsel;
+            fruitless = 0;
+        } else {
+            ++fruitless;
+        }
+        cudaEventRecord(ev1, st);
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        c->stats.t_lanczos_ms += ms;
+        (void)converged;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+
+    // output: the k smallest locked eigenvalues, ascending, vectors in permuted order
+    std::vector<int> ord(nlock);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return lam[x] < lam[y]; });
+    const int nout = std::min(k, nlock);
+    const int limit = (status == RIGA_OK) ? nout : std::min(nout, confirmed);
+    c->evals.assign(limit, 0.0);
+    RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * std::max(limit, 1)));
+    for (int q = 0; q < limit; ++q) {
+        c->evals[q] = lam[ord[q]];
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->evec_perm.ptr + (long long)q * N, c->V.ptr + (long long)ord[q] * R.ld,
+                                         N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    c->nev = limit;
+    if (nconv) *nconv = limit;
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (status) {
+        if (status == RIGA_ENOCONV && c->last_error.empty()) set_error(c, status, "Lanczos did not converge");
+        return status;
+    }
+    return RIGA_OK;
+}
+
+// exported helpers for api.cu
+void sign_fix(riga_ctx* c, double* U, int ncols) {
+    if (ncols > 0) sign_fix_kernel<<<ncols, 256, 0, c->stream>>>(c->S.N, U, c->S.N);
+}
+
+}  // namespace riga

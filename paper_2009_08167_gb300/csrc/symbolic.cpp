@@ -1,0 +1,407 @@
+// Host symbolic analysis (integer only, once per mesh pattern).
+//
+// * Knot vectors in element units and C0 DOFs (Sec. 3.1 Eq. U, Sec. 3.2).
+// * Nested dissection whose first cuts are the rIGA C0 hyperplanes and whose
+//   remaining cuts are p-thick slabs (a reading of the "blocks first, then
+//   separators" cost model of Sec. 5.1 Eq. flopsFact; the paper itself orders
+//   with METIS, Sec. 6).  Rule, per box of DOF intervals [lo,hi):
+//     leaf        if every extent <= max(leaf_extent, p+1);
+//     C0 cut      else if a direction has a C0 DOF c with lo < c < hi-1: the
+//                 direction of largest extent among those (lowest axis on
+//                 ties), the c minimising |2c-(lo+hi-1)| (lower c on ties),
+//                 separator [c, c+1);
+//     p-thick cut else: direction of largest extent (lowest axis on ties),
+//                 separator [s, s+p), s = lo + floor((hi-lo-p)/2).
+//   Post-order: left subtree, right subtree, separator; DOFs inside a node
+//   ascending in global (x-fastest) numbering.
+// * Multifrontal structure: each node's front = own DOFs + border (later DOFs
+//   adjacent to the node's DOFs or in a child's border), scatter map of A's
+//   lower entries into fronts, extend-add maps, solve update offsets, and the
+//   per-level panel/tile work lists of the blocked partial LDL^T.
+#include "symbolic.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+
+namespace riga {
+
+static std::string build_dir(Dir1D& D, int ne, int p, const int* mult) {
+    if (ne < 1) return "ne must be >= 1";
+    D.ne = ne;
+    D.p = p;
+    D.mult.assign(ne > 1 ? ne - 1 : 0, 1);
+    if (mult) {
+        for (int i = 0; i < ne - 1; ++i) {
+            if (mult[i] < 1 || mult[i] > p) return "knot multiplicity outside 1..p";
+            D.mult[i] = mult[i];
+        }
+    }
+    D.kv.clear();
+    for (int i = 0; i <= p; ++i) D.kv.push_back(0);
+    for (int t = 1; t < ne; ++t)
+        for (int m = 0; m < D.mult[t - 1]; ++m) D.kv.push_back(t);
+    for (int i = 0; i <= p; ++i) D.kv.push_back(ne);
+    D.nfun = (int)D.kv.size() - p - 1;
+    D.ndof = D.nfun - 2;
+    if (D.ndof < 1) return "fewer than one interior DOF in a direction";
+    // first non-zero function on each element: the span index sp with
+    // kv[sp] <= e < kv[sp+1], minus p
+    D.elem_first.assign(ne, 0);
+    for (int e = 0; e < ne; ++e) {
+        int sp = -1;
+        for (int i = 0; i + 1 < (int)D.kv.size(); ++i)
+            if (D.kv[i] <= e && e < D.kv[i + 1]) sp = i;
+        if (sp < p) return "internal: bad span";
+        D.elem_first[e] = sp - p;
+    }
+    // C0 DOFs: the function B_{s-1}, s the first occurrence of a knot of
+    // multiplicity p; after removing function 0 its DOF index is s-2
+    D.c0.clear();
+    for (int t = 1; t < ne; ++t) {
+        if (D.mult[t - 1] != p) continue;
+        int s = -1;
+        for (int i = 0; i < (int)D.kv.size(); ++i)
+            if (D.kv[i] == t) { s = i; break; }
+        D.c0.push_back(s - 2);
+    }
+    // DOF adjacency: supports [kv[f], kv[f+p+1]) share an element
+    D.adj_ptr.assign(D.ndof + 1, 0);
+    D.adj.clear();
+    for (int a = 0; a < D.ndof; ++a) {
+        int f = a + 1;
+        for (int b = std::max(0, a - p); b <= std::min(D.ndof - 1, a + p); ++b) {
+            int g = b + 1;
+            int lo = std::max(D.kv[f], D.kv[g]);
+            int hi = std::min(D.kv[f + p + 1], D.kv[g + p + 1]);
+            if (lo < hi) D.adj.push_back(b);
+        }
+        D.adj_ptr[a + 1] = (int)D.adj.size();
+    }
+    return "";
+}
+
+namespace {
+struct Box {
+    int lo[3], hi[3];
+};
+}  // namespace
+
+std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int* const* mult,
+                           int leaf_extent) {
+    if (dim < 1 || dim > 3) return "dim must be 1, 2 or 3";
+    if (p < 1 || p > 6) return "p must be in 1..6";
+    S = Symbolic();
+    S.dim = dim;
+    S.p = p;
+    S.leaf_extent = leaf_extent > 0 ? leaf_extent : 8;
+    S.N = 1;
+    S.n_elem = 1;
+    for (int a = 0; a < 3; ++a) S.n1[a] = 1;
+    for (int a = 0; a < dim; ++a) {
+        std::string err = build_dir(S.dir[a], ne[a], p, mult ? mult[a] : nullptr);
+        if (!err.empty()) return err;
+        S.n1[a] = S.dir[a].ndof;
+        S.N *= S.n1[a];
+        S.n_elem *= ne[a];
+    }
+    if (S.N > 2000000000LL) return "problem too large for 32-bit DOF indices";
+    const int N = (int)S.N;
+    const int nx = S.n1[0], ny = S.n1[1];
+
+    // ------------------------------------------------------------ dissection
+    std::vector<std::vector<int>> own;
+    std::vector<std::vector<int>> kids;
+    const int limit = std::max(S.leaf_extent, p + 1);
+    auto box_vars = [&](const Box& b) {
+        std::vector<int> v;
+        for (int z = b.lo[2]; z < b.hi[2]; ++z)
+            for (int y = b.lo[1]; y < b.hi[1]; ++y)
+                for (int x = b.lo[0]; x < b.hi[0]; ++x) v.push_back(x + nx * (y + ny * z));
+        return v;
+    };
+    std::function<int(const Box&)> rec = [&](const Box& b) -> int {
+        int ext[3], maxext = 0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = b.hi[a] - b.lo[a];
+            if (a < dim) maxext = std::max(maxext, ext[a]);
+        }
+        if (maxext <= limit) {
+            own.push_back(box_vars(b));
+            kids.push_back({});
+            return (int)own.size() - 1;
+        }
+        int axis = -1;
+        for (int a = 0; a < dim; ++a) {
+            bool has = false;
+            for (int c : S.dir[a].c0)
+                if (b.lo[a] < c && c < b.hi[a] - 1) has = true;
+            if (has && (axis < 0 || ext[a] > ext[axis])) axis = a;
+        }
+        int s, t;
+        if (axis >= 0) {
+            const int lo = b.lo[axis], hi = b.hi[axis];
+            int best = -1;
+            long long bestd = 0;
+            for (int c : S.dir[axis].c0) {
+                if (!(lo < c && c < hi - 1)) continue;
+                long long d = std::llabs(2LL * c - (lo + hi - 1));
+                if (best < 0 || d < bestd) { best = c; bestd = d; }
+            }
+            s = best;
+            t = best + 1;
+        } else {
+            axis = 0;
+            for (int a = 1; a < dim; ++a)
+                if (ext[a] > ext[axis]) axis = a;
+            s = b.lo[axis] + (ext[axis] - p) / 2;
+            t = s + p;
+        }
+        Box L = b, R = b, Sep = b;
+        L.hi[axis] = s;
+        R.lo[axis] = t;
+        Sep.lo[axis] = s;
+        Sep.hi[axis] = t;
+        int l = rec(L);
+        int r = rec(R);
+        own.push_back(box_vars(Sep));
+        kids.push_back({l, r});
+        return (int)own.size() - 1;
+    };
+    Box root;
+    for (int a = 0; a < 3; ++a) {
+        root.lo[a] = 0;
+        root.hi[a] = S.n1[a];
+    }
+    rec(root);
+
+    const int F = (int)own.size();
+    S.n_nodes = F;
+    S.node_ptr.assign(F + 1, 0);
+    S.perm.clear();
+    S.perm.reserve(N);
+    for (int f = 0; f < F; ++f) {
+        S.node_ptr[f] = (int)S.perm.size();
+        for (int g : own[f]) S.perm.push_back(g);
+    }
+    S.node_ptr[F] = (int)S.perm.size();
+    if ((int)S.perm.size() != N) return "internal: dissection does not cover all DOFs";
+    S.ipos.assign(N, -1);
+    for (int i = 0; i < N; ++i) S.ipos[S.perm[i]] = i;
+    for (int g = 0; g < N; ++g)
+        if (S.ipos[g] < 0) return "internal: dissection repeats a DOF";
+    S.node_of.assign(N, 0);
+    for (int f = 0; f < F; ++f)
+        for (int i = S.node_ptr[f]; i < S.node_ptr[f + 1]; ++i) S.node_of[i] = f;
+    S.parent.assign(F, -1);
+    S.child_ptr.assign(F + 1, 0);
+    S.child_list.clear();
+    for (int f = 0; f < F; ++f) {
+        S.child_ptr[f] = (int)S.child_list.size();
+        for (int c : kids[f]) {
+            S.child_list.push_back(c);
+            S.parent[c] = f;
+        }
+    }
+    S.child_ptr[F] = (int)S.child_list.size();
+
+    // ------------------------------------------------------- CSR patterns
+    // global numbering first (rows and columns ascending)
+    S.glob_rowptr.assign(N + 1, 0);
+    std::vector<int> gcol;
+    gcol.reserve((size_t)N * 27);
+    {
+        const Dir1D& X = S.dir[0];
+        for (int g = 0; g < N; ++g) {
+            int ix = g % nx, rem = g / nx;
+            int iy = dim > 1 ? rem % ny : 0;
+            int iz = dim > 2 ? rem / ny : 0;
+            int zb = 0, ze = 1, yb = 0, ye = 1;
+            const int* zadj = nullptr;
+            const int* yadj = nullptr;
+            if (dim > 2) { zb = S.dir[2].adj_ptr[iz]; ze = S.dir[2].adj_ptr[iz + 1]; zadj = S.dir[2].adj.data(); }
+            if (dim > 1) { yb = S.dir[1].adj_ptr[iy]; ye = S.dir[1].adj_ptr[iy + 1]; yadj = S.dir[1].adj.data(); }
+            for (int zz = zb; zz < ze; ++zz) {
+                int jz = zadj ? zadj[zz] : 0;
+                for (int yy = yb; yy < ye; ++yy) {
+                    int jy = yadj ? yadj[yy] : 0;
+                    for (int xx = X.adj_ptr[ix]; xx < X.adj_ptr[ix + 1]; ++xx)
+                        gcol.push_back(X.adj[xx] + nx * (jy + ny * jz));
+                }
+            }
+            S.glob_rowptr[g + 1] = (long long)gcol.size();
+        }
+    }
+    S.nnz = (long long)gcol.size();
+    // permuted CSR: row = pos, columns = positions ascending
+    S.rowptr.assign(N + 1, 0);
+    S.col.resize(S.nnz);
+    S.perm_to_glob.resize(S.nnz);
+    {
+        std::vector<std::pair<int, long long>> tmp;
+        long long at = 0;
+        for (int i = 0; i < N; ++i) {
+            int g = S.perm[i];
+            tmp.clear();
+            for (long long e = S.glob_rowptr[g]; e < S.glob_rowptr[g + 1]; ++e)
+                tmp.push_back({S.ipos[gcol[e]], e});
+            std::sort(tmp.begin(), tmp.end());
+            for (auto& pr : tmp) {
+                S.col[at] = pr.first;
+                S.perm_to_glob[at] = pr.second;
+                ++at;
+            }
+            S.rowptr[i + 1] = at;
+        }
+    }
+
+    // ------------------------------------------------------------- fronts
+    S.k.assign(F, 0);
+    S.n.assign(F, 0);
+    S.front_ptr.assign(F + 1, 0);
+    S.front_pos.clear();
+    std::vector<int> stamp(N, -1);
+    std::vector<int> cand;
+    for (int f = 0; f < F; ++f) {
+        const int b0 = S.node_ptr[f], b1 = S.node_ptr[f + 1];
+        cand.clear();
+        for (int i = b0; i < b1; ++i)
+            for (long long e = S.rowptr[i]; e < S.rowptr[i + 1]; ++e) {
+                int q = S.col[e];
+                if (q >= b1 && stamp[q] != f) { stamp[q] = f; cand.push_back(q); }
+            }
+        for (int ci = S.child_ptr[f]; ci < S.child_ptr[f + 1]; ++ci) {
+            int c = S.child_list[ci];
+            for (long long e = S.front_ptr[c] + S.k[c]; e < S.front_ptr[c] + S.n[c]; ++e) {
+                int q = S.front_pos[e];
+                if (q < b0) return "internal: child border precedes parent";
+                if (q >= b1 && stamp[q] != f) { stamp[q] = f; cand.push_back(q); }
+            }
+        }
+        std::sort(cand.begin(), cand.end());
+        S.front_ptr[f] = (long long)S.front_pos.size();
+        for (int i = b0; i < b1; ++i) S.front_pos.push_back(i);
+        for (int q : cand) S.front_pos.push_back(q);
+        S.k[f] = b1 - b0;
+        S.n[f] = S.k[f] + (int)cand.size();
+    }
+    S.front_ptr[F] = (long long)S.front_pos.size();
+
+    auto local_index = [&](int f, int q) -> int {
+        if (q >= S.node_ptr[f] && q < S.node_ptr[f + 1]) return q - S.node_ptr[f];
+        const int* bb = S.front_pos.data() + S.front_ptr[f] + S.k[f];
+        const int* be = S.front_pos.data() + S.front_ptr[f + 1];
+        const int* it = std::lower_bound(bb, be, q);
+        if (it == be || *it != q) return -1;
+        return S.k[f] + (int)(it - bb);
+    };
+
+    S.front_off.assign(F + 1, 0);
+    for (int f = 0; f < F; ++f) S.front_off[f + 1] = S.front_off[f] + (long long)S.n[f] * S.n[f];
+    S.pool_size = S.front_off[F];
+
+    S.scatter.assign(S.nnz, -1);
+    for (int i = 0; i < N; ++i)
+        for (long long e = S.rowptr[i]; e < S.rowptr[i + 1]; ++e) {
+            int j = S.col[e];
+            if (j > i) continue;
+            int f = S.node_of[j];
+            int lc = j - S.node_ptr[f];
+            int lr = local_index(f, i);
+            if (lr < 0) return "internal: matrix entry outside its front";
+            S.scatter[e] = S.front_off[f] + (long long)lc * S.n[f] + lr;
+        }
+
+    S.rel_ptr.assign(F + 1, 0);
+    S.upd_off.assign(F + 1, 0);
+    S.rel.clear();
+    for (int f = 0; f < F; ++f) {
+        S.rel_ptr[f] = (long long)S.rel.size();
+        S.upd_off[f + 1] = S.upd_off[f] + (S.n[f] - S.k[f]);
+        int par = S.parent[f];
+        for (long long e = S.front_ptr[f] + S.k[f]; e < S.front_ptr[f + 1]; ++e) {
+            if (par < 0) return "internal: root front with a border";
+            int li = local_index(par, S.front_pos[e]);
+            if (li < 0) return "internal: child border not in parent front";
+            S.rel.push_back(li);
+        }
+    }
+    S.rel_ptr[F] = (long long)S.rel.size();
+    S.upd_size = S.upd_off[F];
+
+    // heights and counts
+    S.height.assign(F, 0);
+    int maxh = 0;
+    for (int f = 0; f < F; ++f) {
+        int h = 0;
+        for (int ci = S.child_ptr[f]; ci < S.child_ptr[f + 1]; ++ci)
+            h = std::max(h, S.height[S.child_list[ci]] + 1);
+        S.height[f] = h;
+        maxh = std::max(maxh, h);
+    }
+    S.n_levels = maxh + 1;
+    S.nnzL = 0;
+    S.flops = 0.0;
+    for (int f = 0; f < F; ++f) {
+        long long kk = S.k[f], nn = S.n[f];
+        S.nnzL += kk * (kk + 1) / 2 + kk * (nn - kk);
+        for (long long i = 0; i < kk; ++i) S.flops += (double)(nn - i) * (double)(nn - i - 1);
+    }
+
+    // ---------------------------------------------------- level schedule
+    S.levels.assign(S.n_levels, LevelPlan());
+    for (int f = 0; f < F; ++f) S.levels[S.height[f]].nodes.push_back(f);
+    S.pitems.clear();
+    S.titems.clear();
+    S.eitems.clear();
+    const int nb = S.nb, tile = S.tile, rb = S.rowblk;
+    const int ext_cols = 32;
+    for (int l = 0; l < S.n_levels; ++l) {
+        LevelPlan& P = S.levels[l];
+        for (int f : P.nodes) {
+            P.max_n = std::max(P.max_n, S.n[f]);
+            P.max_k = std::max(P.max_k, S.k[f]);
+        }
+        for (int rank = 0; rank < 2; ++rank) {
+            P.ext_begin[rank] = (int)S.eitems.size();
+            for (int f : P.nodes) {
+                int nc = S.child_ptr[f + 1] - S.child_ptr[f];
+                if (rank >= nc) continue;
+                int c = S.child_list[S.child_ptr[f] + rank];
+                int m = S.n[c] - S.k[c];
+                for (int c0 = 0; c0 < m; c0 += ext_cols)
+                    S.eitems.push_back({c, c0, std::min(m, c0 + ext_cols)});
+            }
+            P.ext_end[rank] = (int)S.eitems.size();
+        }
+        for (int s = 0; s * nb < P.max_k; ++s) {
+            StepRange R;
+            R.s = s;
+            R.d_begin = (int)S.pitems.size();
+            for (int f : P.nodes)
+                if (S.k[f] > s * nb) S.pitems.push_back({f, s * nb});
+            R.d_end = (int)S.pitems.size();
+            R.p_begin = (int)S.pitems.size();
+            R.t_begin = (int)S.titems.size();
+            for (int f : P.nodes) {
+                int kf = S.k[f], nf = S.n[f];
+                if (kf <= s * nb) continue;
+                int kb = std::min(nb, kf - s * nb);
+                for (int r0 = s * nb + kb; r0 < nf; r0 += rb) S.pitems.push_back({f, r0});
+                int c0 = s * nb + kb;
+                if (c0 < nf) {
+                    int T = (nf - c0 + tile - 1) / tile;
+                    for (int bi = 0; bi < T; ++bi)
+                        for (int bj = 0; bj <= bi; ++bj)
+                            S.titems.push_back({f, c0 + bi * tile, c0 + bj * tile});
+                }
+            }
+            R.p_end = (int)S.pitems.size();
+            R.t_end = (int)S.titems.size();
+            P.steps.push_back(R);
+        }
+    }
+    return "";
+}
+
+}  // namespace riga

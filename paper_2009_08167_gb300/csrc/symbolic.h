@@ -1,0 +1,101 @@
+// Host-side symbolic analysis: B-spline index structure, separator-induced
+// nested dissection, assembly tree, fronts and all integer maps the device
+// kernels consume.  Integer only; computed once per mesh pattern.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace riga {
+
+// One direction of the tensor-product space (Sec. 3.1 Eq. U, Sec. 3.2).
+struct Dir1D {
+    int ne = 0, p = 0;
+    std::vector<int> mult;      // interior knot multiplicities (ne-1)
+    std::vector<int> kv;        // knot vector in element units (value * ne)
+    int nfun = 0;               // functions before Dirichlet removal
+    int ndof = 0;               // nfun - 2
+    std::vector<int> elem_first;  // first non-zero function on element e (pre-Dirichlet)
+    std::vector<int> c0;        // C0 DOFs (after Dirichlet removal), ascending
+    // adjacency of DOFs: adj_ptr[a]..adj_ptr[a+1] in adj (ascending)
+    std::vector<int> adj_ptr, adj;
+};
+
+// Factorization work items (precomputed per level and panel step).
+struct PanelItem { int front; int r0; };            // TRSM row block of a front
+struct TileItem { int front; int i0; int j0; };     // trailing-update tile
+struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
+
+struct StepRange {   // one panel step of one level
+    int s;           // step index (panel columns s*nb .. )
+    int d_begin, d_end;   // PanelItem range: one diagonal-block item per active front (r0 = s*nb)
+    int p_begin, p_end;   // PanelItem range: row blocks below the diagonal block
+    int t_begin, t_end;   // TileItem range
+};
+
+struct LevelPlan {
+    std::vector<int> nodes;          // nodes of this level
+    int max_n = 0, max_k = 0;
+    int ext_begin[2], ext_end[2];    // ExtItem ranges per child rank
+    std::vector<StepRange> steps;
+};
+
+struct Symbolic {
+    int dim = 0, p = 0, leaf_extent = 8;
+    Dir1D dir[3];
+    int n1[3] = {1, 1, 1};
+    long long N = 0;
+
+    // elimination order
+    std::vector<int> perm;  // perm[pos] = global DOF
+    std::vector<int> ipos;  // ipos[g] = pos
+
+    // nodes, post-ordered
+    int n_nodes = 0;
+    std::vector<int> node_ptr;     // own positions [node_ptr[F], node_ptr[F+1])
+    std::vector<int> parent;
+    std::vector<int> child_ptr, child_list;  // children in order (left, right)
+    std::vector<int> node_of;      // node_of[pos]
+    std::vector<int> k, n;         // fully summed / front size
+    std::vector<long long> front_ptr;  // index lists (positions) at front_ptr[F]
+    std::vector<int> front_pos;        // own positions then border positions
+    std::vector<int> height;
+    int n_levels = 0;
+
+    // CSR pattern in elimination order (row = pos, cols = pos ascending)
+    std::vector<long long> rowptr;
+    std::vector<int> col;
+    long long nnz = 0;
+    // the same entries in global numbering: csr_perm_to_glob[e] = index of
+    // entry e of the permuted CSR inside the global CSR (rows/cols ascending)
+    std::vector<long long> glob_rowptr;
+    std::vector<long long> perm_to_glob;
+
+    // front pool (column-major, leading dimension n_F)
+    std::vector<long long> front_off;
+    long long pool_size = 0;
+    std::vector<long long> scatter;   // per permuted CSR entry: pool offset or -1 (upper)
+    std::vector<int> rel;             // extend-add: local index in parent, per border entry
+    std::vector<long long> rel_ptr;   // rel of node F at rel_ptr[F] (length n_F - k_F)
+    std::vector<long long> upd_off;   // solve update vector offsets (length n_F - k_F)
+    long long upd_size = 0;
+
+    // factorization schedule
+    int nb = 32, tile = 64, rowblk = 64;
+    std::vector<LevelPlan> levels;
+    std::vector<PanelItem> pitems;
+    std::vector<TileItem> titems;
+    std::vector<ExtItem> eitems;
+
+    // element structure (for assembly with coefficients and the adjoint)
+    long long n_elem = 0;
+
+    long long nnzL = 0;
+    double flops = 0.0;
+};
+
+// Builds everything above.  Returns an empty string on success, else a message.
+std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int* const* mult,
+                           int leaf_extent);
+
+}  // namespace riga
