@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the shift-and-invert eigensolution on one GB300 per rank.
+
+Workload (the 2D configuration of Table 3's 256^2 p=3 row, with rIGA blocks
+of 16 elements): Laplace on the unit square, Dirichlet, B-spline degree 3,
+256x256 elements, C0 separator lines every 16 elements (N = 82,369), lowest
+100 eigenpairs in two spectrum slices of 50 (sigma = 0, then the check shift
+after the 50th), FP64 fronts.  One step = numeric assembly of K and M +
+riga_eigs (factorizations, Lanczos, Rayleigh-Ritz, inertia checks,
+residuals); the symbolic analysis is once per mesh pattern and not timed.
+Metric: converged eigenpairs per second at residual <= 1e-10.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl riga|reference]
+                    [--precision fp64|fp32] [--mesh riga|iga]
+
+Under torchrun each rank solves its own copy (replicas: the single eigenproblem
+does not shard); value = pairs of all ranks / max step time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/s at resid<=1e-10 (2D p=3 256^2 rIGA bs16, 100 pairs, 2 slices)"
+RESID_TOL = 1e-10
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="riga", choices=["riga", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--mesh", default="riga", choices=["riga", "iga"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(mesh_kind):
+    from paper_2009_08167_gb300.inputs import config_c2
+    cfg = config_c2(riga=(mesh_kind == "riga"))
+    return cfg
+
+
+def config_dict(args, cfg, extra=None):
+    m = cfg["mesh"]
+    d = {
+        "workload": f"laplace2d_p{m.p}_{m.ne[0]}x{m.ne[1]}_{'riga_bs%d' % m.bs if m.bs else 'iga'}_k{cfg['k']}_slices{cfg['k'] // cfg['slice']}",
+        "dim": m.dim, "elements_per_side": m.ne[0], "degree": m.p, "block_size": m.bs, "leaf_extent": m.leaf_extent,
+        "pairs": cfg["k"], "slice": cfg["slice"], "factor_precision": args.precision,
+        "l2": "flushed between timed steps (512 MiB write)",
+        "parallelism": f"replicas{args.gpus}",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(phase):
+    """DRAM bytes per invocation of a phase from the committed ncu summary
+    (profiles/ncu_traffic.txt: '<phase> <bytes_per_call> <source commit>'),
+    or None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split("#")[0].split()
+        if len(parts) >= 2 and parts[0] == phase:
+            return float(parts[1])
+    return None
+
+
+# ------------------------------------------------------------- oracle leg
+def oracle_sample():
+    """The FP64 oracle as it stands (shift-invert Lanczos with banded LDL^T)
+    on a bounded sample: the same 2D p=3 rIGA family (C0 lines every 16
+    elements) at 48x48 elements, 100 eigenpairs.  Returns (pairs/s, seconds,
+    description)."""
+    import numpy as np
+    from oracle import assembly, eigen
+    from paper_2009_08167_gb300.inputs import Mesh
+    m = Mesh(2, 48, 3, 16)
+    t0 = time.perf_counter()
+    K, M = assembly.assemble_kron(2, m.ne, m.p, m.mults)
+    lam, U, info = eigen.lanczos_shift_invert(K, M, 100, 0.0, tol=1e-12, seed=1)
+    rho = eigen.residual_rho(K, M, lam, U)
+    dt = time.perf_counter() - t0
+    ok = int(np.sum(rho <= RESID_TOL))
+    desc = (f"oracle shift-invert Lanczos + banded LDL^T, 2D p=3 rIGA bs16 at 48x48 elements (N={K.n}), "
+            f"{ok} of 100 pairs at resid<=1e-10, {dt:.1f} s, 1 thread of numpy/BLAS")
+    return ok / dt, dt, desc
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    cfg = workload(args.mesh)
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals, secs = [], []
+    desc = ""
+    for _ in range(args.steps):
+        v, dt, desc = oracle_sample()
+        vals.append(v)
+        secs.append(dt)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, cfg),
+        "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ riga leg
+def run_riga(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2009_08167_gb300 import riga
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    prec = riga.RIGA_FP64 if args.precision == "fp64" else riga.RIGA_FP32
+    cfg = workload(args.mesh)
+    mesh, k = cfg["mesh"], cfg["k"]
+    R = riga.Riga(local_rank, stream)
+    R.set_eig_options(slice=cfg["slice"], precision=prec, extra=2, seed=11)
+    R.assemble(mesh)  # symbolic analysis: once per pattern, untimed
+    q = R.query()
+    N = q["N"]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step_device():
+        R.assemble(mesh)
+        return R.eigs(k, cfg["sigma"], RESID_TOL, vectors=True, device_out=True)
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    clk = Clocks(local_rank)
+    launches0 = R.launches()
+    times = []
+    rs = None
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, U, rs = step_device()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    launches = (R.launches() - launches0) // max(1, args.steps)
+    rs_h = rs.cpu().numpy()
+    pairs = int(np.sum(rs_h <= RESID_TOL))
+    ms = statistics.mean(times)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * pairs / (ms_max / 1e3)
+    st = R.stats()
+
+    # end to end through the public API with host buffers: mesh description
+    # in, eigenvalues, eigenvectors and residuals out (pageable host memory)
+    h2d = int(sum(np.asarray(mm, dtype=np.int32).nbytes for mm in mesh.mults))
+    d2h = 8 * (k + N * k + k)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R.assemble(mesh)
+        evh, Uh, rsh = R.eigs(k, cfg["sigma"], RESID_TOL, vectors=True, device_out=False)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_pairs = int(np.sum(rsh <= RESID_TOL))
+    e2e_val = world * e2e_pairs / statistics.mean(e2e_times)
+
+    # roofline: one profiled step (phase timing with CUDA events on the
+    # library's stream), dominant phase by device time
+    R.profile(True)
+    step_device()
+    prof = R.profile_get()
+    R.profile(False)
+    pk, pk_kind = peaks()
+    dom = max(prof, key=lambda p: prof[p]["ms"])
+    pr = prof[dom]
+    if pr["flops"] > 0 and pr["bytes"] == 0:
+        ach = pr["flops"] / (pr["ms"] / 1e3) / 1e12
+        peak = 1.25  # FP64 FFMA: nominal GB300 FP64 rate (no measured FP64 peak in the peaks file)
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "phase": dom, "peak_source": "nominal fp64"}
+    else:
+        gbs = pr["bytes"] / (pr["ms"] / 1e3) / 1e9
+        per_call = ncu_traffic(dom)
+        roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                "traffic": per_call, "phase": dom, "peak_source": pk_kind,
+                "algorithmic_bytes_per_call": pr["bytes"] / max(1, pr["calls"]),
+                "ms_per_call": pr["ms"] / max(1, pr["calls"])}
+    phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        v, dt, desc = oracle_sample()
+        cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-fronts/f64",
+            "data": "synthetic (deterministic mesh; seeded Lanczos start vectors)",
+            "config": config_dict(args, cfg, {"N": N, "nnz": q["nnz"], "nnzL": q["nnzL"],
+                                              "flops_fact": q["flops_fact"]}),
+            "converged_pairs": pairs, "max_resid": float(np.max(rs_h)),
+            "e2e": {"value": e2e_val, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "phases_ms_one_step": phases,
+            "counts_per_step": {"n_fact": st["n_fact"], "n_solve": st["n_solve"], "n_matvec": st["n_matvec"],
+                                "lanczos_steps": st["lanczos_steps"]},
+            "clocks": clocks,
+            "wall_s_timed": t_wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    R.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_riga(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -249,6 +249,28 @@ int riga_spmv(riga_ctx* ctx, int which, const double* x, double* y);
 int riga_stats(riga_ctx* ctx, long long* n_fact, long long* n_solve, long long* n_matvec,
                long long* lanczos_steps, double* t_fact_ms, double* t_lanczos_ms);
 
+/*
+ * riga_profile: enable (1) or disable (0) device timing of the library's
+ * phases and reset all phase counters (launch counts keep running).  While
+ * enabled, every phase invocation is bracketed by CUDA events on the
+ * context's stream (a small per-invocation cost).
+ */
+int riga_profile(riga_ctx* ctx, int enable);
+
+/*
+ * riga_profile_get: counters of phase `phase` since the last riga_profile
+ * call: 0 assemble, 1 factor (numeric LDL^T), 2 solve (one forward/backward
+ * elimination), 3 reorth (Gram-Schmidt passes), 4 spmv (M mat-vec and
+ * normalisation), 5 ritz (Ritz-vector GEMM), 6 other.  phase = -1 gives the
+ * total kernel launches since riga_create in *launches.  Outputs (any may be
+ * NULL): name (static string), launches (kernel launches), calls (phase
+ * invocations), ms (summed device time, profiling on), bytes and flops
+ * (algorithmic work: factor entries read twice per solve, basis columns read
+ * four times per reorthogonalization, and so on).  Synchronizes the stream.
+ */
+int riga_profile_get(riga_ctx* ctx, int phase, const char** name, long long* launches, long long* calls,
+                     double* ms, double* bytes, double* flops);
+
 /* riga_strerror: static name of a status code. */
 const char* riga_strerror(int status);
 

@@ -96,9 +96,9 @@ int eig_grad_device(riga_ctx* c, int k, const double* w_dev, double* ga_dev, dou
     DevBuf<double> lam;
     std::vector<double> l(c->evals.begin(), c->evals.begin() + k);
     RIGA_CUDA_TRY(c, lam.upload(l, c->stream));
-    adjoint_kernel<<<(unsigned)((S.n_elem + 127) / 128), 128, 0, c->stream>>>(
+    { count_launch(c); adjoint_kernel<<<(unsigned)((S.n_elem + 127) / 128), 128, 0, c->stream>>>(
         S.dim, S.p, S.n_elem, d[0], d[1], d[2], S.n1[0], S.n1[1], c->ipos.ptr, k, c->evec_perm.ptr, S.N, lam.ptr,
-        w_dev, c->coefK.empty() ? nullptr : c->dcoefK.ptr, c->coefM.empty() ? nullptr : c->dcoefM.ptr, ga_dev, gb_dev);
+        w_dev, c->coefK.empty() ? nullptr : c->dcoefK.ptr, c->coefM.empty() ? nullptr : c->dcoefM.ptr, ga_dev, gb_dev); }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return RIGA_OK;

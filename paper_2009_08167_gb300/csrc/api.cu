@@ -373,7 +373,7 @@ int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, doubl
             enqueue_spmv(c, 1, u, c->vwork[4].ptr, 0.0);
             enqueue_spmv(c, 0, u, c->vwork[5].ptr, 0.0);
             c->stats.n_matvec--;  // reporting, not part of the iteration count
-            resid_partial_kernel<<<152, 256, 0, c->stream>>>(N, c->vwork[4].ptr, c->vwork[5].ptr, c->evals[q], c->red.ptr);
+            { count_launch(c); resid_partial_kernel<<<152, 256, 0, c->stream>>>(N, c->vwork[4].ptr, c->vwork[5].ptr, c->evals[q], c->red.ptr); }
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), c->red.ptr, 2 * 152 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
             RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
             double ra = 0.0, rb = 0.0;
@@ -475,8 +475,8 @@ int riga_get_matrices(riga_ctx* c, long long* row_ptr, int* col, double* kval, d
     if (col) {
         DevBuf<int> t;
         RIGA_CUDA_TRY(c, t.alloc(S.nnz));
-        glob_col_kernel<<<(unsigned)((S.N + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
-                                                                             c->perm_to_glob.ptr, t.ptr);
+        { count_launch(c); glob_col_kernel<<<(unsigned)((S.N + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
+                                                                             c->perm_to_glob.ptr, t.ptr); }
         int rc = to_user(c, t.ptr, col, S.nnz);
         if (rc) return rc;
     }
@@ -486,7 +486,7 @@ int riga_get_matrices(riga_ctx* c, long long* row_ptr, int* col, double* kval, d
         if (!dsts[i]) continue;
         DevBuf<double> t;
         RIGA_CUDA_TRY(c, t.alloc(S.nnz));
-        scatter_glob_kernel<<<(unsigned)((S.nnz + 255) / 256), 256, 0, c->stream>>>(S.nnz, c->perm_to_glob.ptr, srcs[i], t.ptr);
+        { count_launch(c); scatter_glob_kernel<<<(unsigned)((S.nnz + 255) / 256), 256, 0, c->stream>>>(S.nnz, c->perm_to_glob.ptr, srcs[i], t.ptr); }
         int rc = to_user(c, t.ptr, dsts[i], S.nnz);
         if (rc) return rc;
     }
@@ -557,6 +557,50 @@ int riga_stats(riga_ctx* c, long long* n_fact, long long* n_solve, long long* n_
     if (steps) *steps = c->stats.steps;
     if (t_fact_ms) *t_fact_ms = c->stats.t_fact_ms;
     if (t_lanczos_ms) *t_lanczos_ms = c->stats.t_lanczos_ms;
+    return RIGA_OK;
+}
+
+static void resolve_profile(riga_ctx* c) {
+    if (c->device >= 0) cudaStreamSynchronize(c->stream);
+    for (int p = 0; p < PH_COUNT; ++p) {
+        PhaseRec& r = c->prof.ph[p];
+        for (auto& e : r.ev) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) r.ms += ms;
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        r.ev.clear();
+    }
+    cudaGetLastError();
+}
+
+int riga_profile(riga_ctx* c, int enable) {
+    if (!c) return RIGA_EINVAL;
+    resolve_profile(c);
+    for (int p = 0; p < PH_COUNT; ++p) c->prof.ph[p] = PhaseRec();
+    c->prof.on = enable != 0;
+    return RIGA_OK;
+}
+
+int riga_profile_get(riga_ctx* c, int phase, const char** name, long long* launches, long long* calls, double* ms,
+                     double* bytes, double* flops) {
+    static const char* names[PH_COUNT] = {"assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"};
+    if (!c) return RIGA_EINVAL;
+    if (phase == -1) {
+        if (name) *name = "total";
+        if (launches) *launches = c->prof.launches;
+        return RIGA_OK;
+    }
+    if (phase < 0 || phase >= PH_COUNT) return set_error(c, RIGA_EINVAL, "phase out of range");
+    resolve_profile(c);
+    const PhaseRec& r = c->prof.ph[phase];
+    if (name) *name = names[phase];
+    if (launches) *launches = r.launches;
+    if (calls) *calls = r.calls;
+    if (ms) *ms = r.ms;
+    if (bytes) *bytes = r.bytes;
+    if (flops) *flops = r.flops;
     return RIGA_OK;
 }
 

@@ -255,6 +255,7 @@ __global__ void csr_coef_kernel(int dim, int p, long long N, const long long* __
 int assemble_device(riga_ctx* c) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_ASSEMBLE, (double)S.nnz * 16.0);
     DirDev dd[3];
     for (int a = 0; a < 3; ++a) {
         dd[a] = DirDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, 1};
@@ -267,11 +268,11 @@ int assemble_device(riga_ctx* c) {
         RIGA_CUDA_TRY(c, c->Me1[a].alloc((size_t)D.ne * q * q));
         RIGA_CUDA_TRY(c, c->Kb1[a].alloc((size_t)D.ndof * w));
         RIGA_CUDA_TRY(c, c->Mb1[a].alloc((size_t)D.ndof * w));
-        elem1d_kernel<<<(D.ne + 127) / 128, 128, 0, st>>>(D.ne, S.p, c->kv[a].ptr, c->elem_first[a].ptr,
-                                                          c->Ke1[a].ptr, c->Me1[a].ptr);
-        band1d_kernel<<<(D.ndof * w + 127) / 128, 128, 0, st>>>(D.ndof, S.p, c->kv[a].ptr, c->elem_first[a].ptr,
+        { count_launch(c); elem1d_kernel<<<(D.ne + 127) / 128, 128, 0, st>>>(D.ne, S.p, c->kv[a].ptr, c->elem_first[a].ptr,
+                                                          c->Ke1[a].ptr, c->Me1[a].ptr); }
+        { count_launch(c); band1d_kernel<<<(D.ndof * w + 127) / 128, 128, 0, st>>>(D.ndof, S.p, c->kv[a].ptr, c->elem_first[a].ptr,
                                                                 c->Ke1[a].ptr, c->Me1[a].ptr, c->Kb1[a].ptr,
-                                                                c->Mb1[a].ptr);
+                                                                c->Mb1[a].ptr); }
         dd[a] = DirDev{c->kv[a].ptr, c->elem_first[a].ptr, c->Ke1[a].ptr, c->Me1[a].ptr,
                        c->Kb1[a].ptr, c->Mb1[a].ptr, D.ndof, D.ne};
     }
@@ -280,8 +281,8 @@ int assemble_device(riga_ctx* c) {
     long long threads = S.N * 32;
     int blocks = (int)((threads + 255) / 256);
     if (c->coefK.empty() && c->coefM.empty()) {
-        csr_kron_kernel<<<blocks, 256, 0, st>>>(S.dim, S.p, S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, dd[0],
-                                                dd[1], dd[2], c->Kval.ptr, c->Mval.ptr);
+        { count_launch(c); csr_kron_kernel<<<blocks, 256, 0, st>>>(S.dim, S.p, S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, dd[0],
+                                                dd[1], dd[2], c->Kval.ptr, c->Mval.ptr); }
     } else {
         const double* cK = nullptr;
         const double* cM = nullptr;
@@ -293,8 +294,8 @@ int assemble_device(riga_ctx* c) {
             RIGA_CUDA_TRY(c, c->dcoefM.upload(c->coefM, st));
             cM = c->dcoefM.ptr;
         }
-        csr_coef_kernel<<<blocks, 256, 0, st>>>(S.dim, S.p, S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, dd[0],
-                                                dd[1], dd[2], cK, cM, c->Kval.ptr, c->Mval.ptr);
+        { count_launch(c); csr_coef_kernel<<<blocks, 256, 0, st>>>(S.dim, S.p, S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, dd[0],
+                                                dd[1], dd[2], cK, cM, c->Kval.ptr, c->Mval.ptr); }
     }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     return RIGA_OK;

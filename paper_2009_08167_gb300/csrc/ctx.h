@@ -46,6 +46,21 @@ struct Stats {
     double t_fact_ms = 0.0, t_lanczos_ms = 0.0;
 };
 
+// Per-phase device timing (CUDA events around each phase's launches, only
+// while profiling is on), launch counts and algorithmic work.
+enum Phase { PH_ASSEMBLE = 0, PH_FACTOR, PH_SOLVE, PH_REORTH, PH_SPMV, PH_RITZ, PH_OTHER, PH_COUNT };
+struct PhaseRec {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    long long launches = 0, calls = 0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+};
+struct Profile {
+    bool on = false;
+    int cur = PH_OTHER;
+    long long launches = 0;  // every kernel launch, profiling on or off
+    PhaseRec ph[PH_COUNT];
+};
+
 }  // namespace riga
 
 struct riga_ctx {
@@ -105,6 +120,7 @@ struct riga_ctx {
     std::vector<double> evals;         // final eigenvalues
     int nev = 0;
     riga::Stats stats;
+    riga::Profile prof;
 };
 
 namespace riga {
@@ -117,6 +133,39 @@ int set_error(riga_ctx* c, int code, const std::string& msg);
         if (_e != cudaSuccess)                                                                   \
             return ::riga::set_error((ctx), RIGA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
     } while (0)
+
+// one kernel launch, attributed to the current phase
+inline void count_launch(riga_ctx* c) {
+    c->prof.launches++;
+    c->prof.ph[c->prof.cur].launches++;
+}
+// RAII phase scope: events around the enclosed launches when profiling is on
+struct PhaseScope {
+    riga_ctx* c;
+    int prev;
+    int p;
+    cudaEvent_t a = nullptr;
+    PhaseScope(riga_ctx* c_, int p_, double bytes = 0.0, double flops = 0.0) : c(c_), prev(c_->prof.cur), p(p_) {
+        c->prof.cur = p;
+        PhaseRec& r = c->prof.ph[p];
+        r.calls++;
+        r.bytes += bytes;
+        r.flops += flops;
+        if (c->prof.on) {
+            cudaEventCreate(&a);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~PhaseScope() {
+        if (c->prof.on && a) {
+            cudaEvent_t b;
+            cudaEventCreate(&b);
+            cudaEventRecord(b, c->stream);
+            c->prof.ph[p].ev.push_back({a, b});
+        }
+        c->prof.cur = prev;
+    }
+};
 
 // assemble.cu
 int assemble_device(riga_ctx* c);

@@ -195,37 +195,38 @@ template <typename T>
 static int enqueue_factor_t(riga_ctx* c, T* pool) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_FACTOR, 0.0, S.flops);
     RIGA_CUDA_TRY(c, cudaMemsetAsync(pool, 0, (size_t)S.pool_size * sizeof(T), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
     if (S.nnz > 0)
-        scatter_kernel<T><<<(unsigned)((S.nnz + 255) / 256), 256, 0, st>>>(S.nnz, c->scatter.ptr, c->Kval.ptr,
-                                                                          c->Mval.ptr, c->sigma, pool);
+        { count_launch(c); scatter_kernel<T><<<(unsigned)((S.nnz + 255) / 256), 256, 0, st>>>(S.nnz, c->scatter.ptr, c->Kval.ptr,
+                                                                          c->Mval.ptr, c->sigma, pool); }
     for (int l = 0; l < S.n_levels; ++l) {
         const LevelPlan& P = S.levels[l];
         for (int rank = 0; rank < 2; ++rank) {
             int cnt = P.ext_end[rank] - P.ext_begin[rank];
             if (cnt > 0)
-                extend_add_kernel<T><<<cnt, 128, 0, st>>>(c->eitems.ptr + P.ext_begin[rank], c->parent.ptr,
+                { count_launch(c); extend_add_kernel<T><<<cnt, 128, 0, st>>>(c->eitems.ptr + P.ext_begin[rank], c->parent.ptr,
                                                           c->front_off.ptr, c->kk.ptr, c->nn.ptr, c->rel.ptr,
-                                                          c->rel_ptr.ptr, pool);
+                                                          c->rel_ptr.ptr, pool); }
         }
         for (const StepRange& R : P.steps) {
             const int j0 = R.s * NB;
             if (R.d_end > R.d_begin)
-                diag_kernel<T><<<R.d_end - R.d_begin, 256, 0, st>>>(c->pitems.ptr + R.d_begin, c->kk.ptr, c->nn.ptr,
+                { count_launch(c); diag_kernel<T><<<R.d_end - R.d_begin, 256, 0, st>>>(c->pitems.ptr + R.d_begin, c->kk.ptr, c->nn.ptr,
                                                                     c->front_off.ptr, c->node_ptr.ptr, pool, c->D.ptr,
-                                                                    c->flag.ptr);
+                                                                    c->flag.ptr); }
             if (R.p_end > R.p_begin)
-                trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
-                                                                   c->nn.ptr, c->front_off.ptr, pool);
+                { count_launch(c); trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
+                                                                   c->nn.ptr, c->front_off.ptr, pool); }
             if (R.t_end > R.t_begin)
-                update_kernel<T><<<R.t_end - R.t_begin, 256, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
+                { count_launch(c); update_kernel<T><<<R.t_end - R.t_begin, 256, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
                                                                       c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr,
-                                                                      c->D.ptr, pool);
+                                                                      c->D.ptr, pool); }
         }
     }
-    inertia_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->neg.ptr);
+    { count_launch(c); inertia_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->neg.ptr); }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     return RIGA_OK;
 }

@@ -16,6 +16,8 @@
 // that check shift becomes the next shift.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <numeric>
 
 #include "ctx.h"
@@ -256,14 +258,16 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
     riga_ctx* c = R.c;
     cudaStream_t st = c->stream;
     if (J <= 0) return RIGA_OK;
-    gemvT_partial_kernel<<<R.nch, 256, 0, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap);
-    reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1);
+    // two Gram-Schmidt passes read MV twice and V twice
+    PhaseScope scope(c, PH_REORTH, 4.0 * (double)R.N * J * sizeof(double));
+    { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, 0, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
+    { count_launch(c); reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }
     size_t sm = (size_t)(J + CH) * sizeof(double);
-    update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, c->MV.ptr + col0 * R.ld, R.ld, J, R.c1, w,
-                                                R.N, c->partial.ptr, R.cap);
-    reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2);
-    gemv_update_kernel<<<(unsigned)((R.N + 255) / 256), 256, (size_t)J * sizeof(double), st>>>(
-        c->V.ptr + col0 * R.ld, R.ld, J, R.c2, w, R.N);
+    { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, c->MV.ptr + col0 * R.ld, R.ld, J, R.c1, w,
+                                                R.N, c->partial.ptr, R.cap); }
+    { count_launch(c); reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2); }
+    { count_launch(c); gemv_update_kernel<<<(unsigned)((R.N + 255) / 256), 256, (size_t)J * sizeof(double), st>>>(
+        c->V.ptr + col0 * R.ld, R.ld, J, R.c2, w, R.N); }
     return RIGA_OK;
 }
 
@@ -271,12 +275,13 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
 void normalize_into(Run& R, double* w, int col, int jslot) {
     riga_ctx* c = R.c;
     cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)R.N * 8.0 * 6.0);
     const unsigned nbs = (unsigned)((R.N * 16 + 255) / 256);
-    spmv_dot_kernel<<<nbs, 256, 0, st>>>(R.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, R.Mw, c->red.ptr);
+    { count_launch(c); spmv_dot_kernel<<<nbs, 256, 0, st>>>(R.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, R.Mw, c->red.ptr); }
     c->stats.n_matvec++;
-    finalize_kernel<<<1, 256, 0, st>>>(c->red.ptr, (int)nbs, R.c1, R.c2, col - 1, jslot, R.alpha, R.beta);
-    normalize_kernel<<<(unsigned)((R.N + 255) / 256), 256, 0, st>>>(R.N, w, R.Mw, R.beta + jslot + 1,
-                                                                     c->V.ptr + col * R.ld, c->MV.ptr + col * R.ld);
+    { count_launch(c); finalize_kernel<<<1, 256, 0, st>>>(c->red.ptr, (int)nbs, R.c1, R.c2, col - 1, jslot, R.alpha, R.beta); }
+    { count_launch(c); normalize_kernel<<<(unsigned)((R.N + 255) / 256), 256, 0, st>>>(R.N, w, R.Mw, R.beta + jslot + 1,
+                                                                     c->V.ptr + col * R.ld, c->MV.ptr + col * R.ld); }
 }
 
 int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
@@ -304,6 +309,7 @@ int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
 }  // namespace
 
 int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
+    static const bool dbg = std::getenv("RIGA_DEBUG") != nullptr;
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     const long long N = S.N;
@@ -314,7 +320,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     const double tol_est = 1e-2 * tol;
     const double gap_rel = 1e-6;
     int wmax = slice + extra;
-    int m_cap = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(3 * wmax, wmax + 40);
+    int m_cap = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * wmax, wmax + 60);
     m_cap = (int)std::min<long long>(m_cap, N - 1);
     const int lock_cap = k + extra + 64;
     Run R;
@@ -373,6 +379,9 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             }
             const double sp = 0.5 * (sl[gi - 1] + sl[gi]);
             rc = factor_at(c, sp, prec, &nu_chk);
+            if (dbg)
+                std::fprintf(stderr, "[riga] check: nlock=%d target=%d gap_index=%d shift=%.12g inertia=%lld-%lld found=%d rc=%d\n",
+                             nlock, target, gi, sp, nu_chk, nu0, gi, rc);
             if (rc) { status = rc; break; }
             factored_sigma = sp;
             const long long found = gi;  // locked eigenvalues below sp (all are > sigma0)
@@ -401,7 +410,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             factored_sigma = cur_sigma;
         }
         const int want_run = std::max(need - nlock, 1);
-        int m_max = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(3 * want_run, want_run + 40);
+        int m_max = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * want_run, want_run + 60);
         m_max = std::min(m_max, m_cap);
         m_max = (int)std::min<long long>(m_max, N - nlock - 1);
         if (m_max < 1) { status = RIGA_ENOCONV; break; }
@@ -489,18 +498,22 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
             double* U = c->evec_perm.ptr;
             double* MU = c->evec_perm.ptr + (size_t)N * nsel;
+            PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * nsel) * sizeof(double));
             dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
-            gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N);
-            gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N);
+            { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N); }
+            { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N); }
             long long t = N * nsel;
-            copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, U, N, c->V.ptr + (long long)nlock * R.ld, R.ld);
-            copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, MU, N, c->MV.ptr + (long long)nlock * R.ld, R.ld);
+            { count_launch(c); copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, U, N, c->V.ptr + (long long)nlock * R.ld, R.ld); }
+            { count_launch(c); copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, MU, N, c->MV.ptr + (long long)nlock * R.ld, R.ld); }
             for (int q = 0; q < nsel; ++q) lam.push_back(cur_sigma + 1.0 / theta[sel[q]]);
             nlock += nsel;
             fruitless = 0;
         } else {
             ++fruitless;
         }
+        if (dbg)
+            std::fprintf(stderr, "[riga] run %d: shift=%.12g want=%d steps=%d/%d converged=%d locked=%d total=%d\n", runs,
+                         cur_sigma, want_run, m, m_max, (int)converged, nsel, nlock);
         cudaEventRecord(ev1, st);
         RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
         float ms = 0.f;
@@ -536,7 +549,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
 
 // exported helpers for api.cu
 void sign_fix(riga_ctx* c, double* U, int ncols) {
-    if (ncols > 0) sign_fix_kernel<<<ncols, 256, 0, c->stream>>>(c->S.N, U, c->S.N);
+    if (ncols > 0) { count_launch(c); sign_fix_kernel<<<ncols, 256, 0, c->stream>>>(c->S.N, U, c->S.N); }
 }
 
 }  // namespace riga

@@ -193,19 +193,22 @@ template <typename T>
 static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
+    // algorithmic bytes: every factor entry read twice (forward, backward),
+    // the vector read and written in each sweep
+    PhaseScope scope(c, PH_SOLVE, 2.0 * (double)S.nnzL * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
     for (int l = 0; l < S.n_levels; ++l) {
         const LevelPlan& P = S.levels[l];
         size_t sm = level_smem(P, sizeof(T));
-        fwd_kernel<T><<<(unsigned)P.nodes.size(), 256, sm, st>>>(
+        { count_launch(c); fwd_kernel<T><<<(unsigned)P.nodes.size(), 256, sm, st>>>(
             c->level_nodes.ptr + c->level_nodes_off[l], pool, c->front_off.ptr, c->node_ptr.ptr, c->kk.ptr, c->nn.ptr,
-            c->child_ptr.ptr, c->child_list.ptr, c->rel.ptr, c->rel_ptr.ptr, c->upd_off.ptr, c->upd.ptr, y);
+            c->child_ptr.ptr, c->child_list.ptr, c->rel.ptr, c->rel_ptr.ptr, c->upd_off.ptr, c->upd.ptr, y); }
     }
     for (int l = S.n_levels - 1; l >= 0; --l) {
         const LevelPlan& P = S.levels[l];
         size_t sm = level_smem(P, sizeof(T));
-        bwd_kernel<T><<<(unsigned)P.nodes.size(), 256, sm, st>>>(
+        { count_launch(c); bwd_kernel<T><<<(unsigned)P.nodes.size(), 256, sm, st>>>(
             c->level_nodes.ptr + c->level_nodes_off[l], pool, c->front_off.ptr, c->node_ptr.ptr, c->kk.ptr, c->nn.ptr,
-            c->front_ptr.ptr, c->front_pos.ptr, c->D.ptr, y);
+            c->front_ptr.ptr, c->front_pos.ptr, c->D.ptr, y); }
     }
     return RIGA_OK;
 }
@@ -245,9 +248,9 @@ int enqueue_solve(riga_ctx* c, double* y) {
 int enqueue_spmv(riga_ctx* c, int which, const double* x, double* y, double shift) {
     Symbolic& S = c->S;
     long long threads = S.N * 16;
-    spmv_kernel<16><<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr,
+    { count_launch(c); spmv_kernel<16><<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr,
                                                                                c->Kval.ptr, c->Mval.ptr, which, shift,
-                                                                               x, y);
+                                                                               x, y); }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     if (which == 0) c->stats.n_matvec++;
     return RIGA_OK;
@@ -255,7 +258,7 @@ int enqueue_spmv(riga_ctx* c, int which, const double* x, double* y, double shif
 
 void enqueue_permute(riga_ctx* c, const double* in, double* out, int to_perm, int ncols) {
     long long t = c->S.N * ncols;
-    permute_kernel<<<(unsigned)((t + 255) / 256), 256, 0, c->stream>>>(c->S.N, ncols, c->perm.ptr, in, out, to_perm);
+    { count_launch(c); permute_kernel<<<(unsigned)((t + 255) / 256), 256, 0, c->stream>>>(c->S.N, ncols, c->perm.ptr, in, out, to_perm); }
 }
 
 // y := (K - sigma M)^{-1} y (permuted order).  With an FP32 factor, or check
@@ -281,12 +284,12 @@ int solve_refined(riga_ctx* c, double* y, double* x, double* r, double tol, int 
     for (sweeps = 1; sweeps <= max_sweeps; ++sweeps) {
         int rc = enqueue_solve(c, r);  // r := A^{-1} r (correction)
         if (rc) return rc;
-        axpy_kernel<<<gb, 256, 0, st>>>(N, 1.0, r, x);
+        { count_launch(c); axpy_kernel<<<gb, 256, 0, st>>>(N, 1.0, r, x); }
         long long threads = N * 16;
-        residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
-                                                                            c->Mval.ptr, c->sigma, x, y, r);
+        { count_launch(c); residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
+                                                                            c->Mval.ptr, c->sigma, x, y, r); }
         if (check) {
-            norm2_partial_kernel<<<304, 256, 0, st>>>(N, r, y, c->red.ptr);
+            { count_launch(c); norm2_partial_kernel<<<304, 256, 0, st>>>(N, r, y, c->red.ptr); }
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), c->red.ptr, 2 * 304 * sizeof(double), cudaMemcpyDeviceToHost, st));
             RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
             double rn = 0.0, bn = 0.0;

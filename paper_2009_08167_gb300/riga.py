@@ -32,8 +32,10 @@ RIGA_FP32 = 1
 EXPORTED = [
     "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_factor", "riga_solve", "riga_eigs",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
-    "riga_get_factor", "riga_spmv", "riga_stats", "riga_strerror", "riga_last_error",
+    "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_strerror",
+    "riga_last_error",
 ]
+PHASES = ["assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"]
 
 
 class RigaError(RuntimeError):
@@ -84,6 +86,9 @@ def load_library(path=LIB_PATH):
     lib.riga_get_factor.argtypes = [P, P, P, P]
     lib.riga_spmv.argtypes = [P, I, P, P]
     lib.riga_stats.argtypes = [P] + [ctypes.POINTER(LL)] * 4 + [ctypes.POINTER(D)] * 2
+    lib.riga_profile.argtypes = [P, I]
+    lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
+                                     ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.riga_strerror.argtypes = [I]
     lib.riga_strerror.restype = ctypes.c_char_p
     lib.riga_last_error.argtypes = [P]
@@ -294,3 +299,22 @@ class Riga:
         self._check(self.lib.riga_stats(self.ctx, *[ctypes.byref(t) for t in v]))
         keys = ["n_fact", "n_solve", "n_matvec", "lanczos_steps", "t_fact_ms", "t_lanczos_ms"]
         return {k: t.value for k, t in zip(keys, v)}
+
+    # ------------------------------------------------------------ profiling
+    def profile(self, enable=True):
+        self._check(self.lib.riga_profile(self.ctx, 1 if enable else 0))
+
+    def launches(self):
+        n = ctypes.c_longlong()
+        self._check(self.lib.riga_profile_get(self.ctx, -1, None, ctypes.byref(n), None, None, None, None))
+        return n.value
+
+    def profile_get(self):
+        out = {}
+        for i, name in enumerate(PHASES):
+            la, ca = ctypes.c_longlong(), ctypes.c_longlong()
+            ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.riga_profile_get(self.ctx, i, None, ctypes.byref(la), ctypes.byref(ca), ctypes.byref(ms),
+                                                  ctypes.byref(by), ctypes.byref(fl)))
+            out[name] = dict(launches=la.value, calls=ca.value, ms=ms.value, bytes=by.value, flops=fl.value)
+        return out

@@ -33,16 +33,18 @@ def clusters(lam, rel=1e-8):
     return groups
 
 
-def compare_eigvecs(U_ref, U, M, lam_ref, rel=1e-8, tol=1e-9):
+def compare_eigvecs(U_ref, U, M, lam_ref, rel=1e-8, tol=1e-9, lam_next=None):
     """Eigenvectors agree as cluster subspaces: the singular values of
     U_ref^T M U over each cluster are all >= 1 - tol.  Simple eigenvalues
-    reduce to |u_ref^T M u| >= 1 - tol.  Clusters cut by the end of the
-    range are skipped (their subspace is not determined)."""
+    reduce to |u_ref^T M u| >= 1 - tol.  A cluster cut by the end of the
+    range (its next member, lam_next, lies beyond it) is skipped: the
+    computed vectors span an undetermined part of that subspace."""
     MU = M.matvec(U)
     worst = 1.0
     k = lam_ref.size
     for g in clusters(lam_ref, rel):
-        if g[-1] == k - 1 and len(g) > 1:
+        cut = g[-1] == k - 1 and (lam_next is None or lam_next - lam_ref[-1] <= rel * abs(lam_next))
+        if cut:
             continue
         S = U_ref[:, g].T @ MU[:, g]
         s = np.linalg.svd(S, compute_uv=False)
