@@ -271,6 +271,15 @@ int riga_profile(riga_ctx* ctx, int enable);
 int riga_profile_get(riga_ctx* ctx, int phase, const char** name, long long* launches, long long* calls,
                      double* ms, double* bytes, double* flops);
 
+/*
+ * riga_set_wait_limit: budget of every device-side dependency wait of the
+ * persistent tree solve, in polls of about 64 ns (default 2^24, about a
+ * second).  A wait that exhausts it sets the context's device error word, the
+ * kernel returns, and the next host check reports RIGA_ETIMEOUT; the context
+ * stays usable.  limit >= 0.  Errors: RIGA_EINVAL.
+ */
+int riga_set_wait_limit(riga_ctx* ctx, long long limit);
+
 /* riga_strerror: static name of a status code. */
 const char* riga_strerror(int status);
 

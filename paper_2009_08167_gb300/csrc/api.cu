@@ -78,6 +78,12 @@ int upload_symbolic(riga_ctx* c) {
     }
     c->level_nodes_off[S.n_levels] = (int)ln.size();
     RIGA_CUDA_TRY(c, c->level_nodes.upload(ln, st));
+    // persistent-solve work order: forward by ascending height, backward by descending
+    std::vector<int> order(ln);
+    for (int l = S.n_levels - 1; l >= 0; --l)
+        for (int f : S.levels[l].nodes) order.push_back(f);
+    RIGA_CUDA_TRY(c, c->solve_order.upload(order, st));
+    c->solve_flags.release();
     RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
@@ -324,7 +330,10 @@ int riga_solve(riga_ctx* c, const double* b, double* x, int nrhs, double tol, in
         rc = to_user(c, g, x + (long long)col * N, N);
         if (rc) return rc;
     }
+    int dflag = 0;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (dflag & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
     return status;
 }
 
@@ -601,6 +610,12 @@ int riga_profile_get(riga_ctx* c, int phase, const char** name, long long* launc
     if (ms) *ms = r.ms;
     if (bytes) *bytes = r.bytes;
     if (flops) *flops = r.flops;
+    return RIGA_OK;
+}
+
+int riga_set_wait_limit(riga_ctx* c, long long limit) {
+    if (!c || limit < 0) return RIGA_EINVAL;
+    c->wait_limit = limit;
     return RIGA_OK;
 }
 

@@ -103,6 +103,11 @@ struct riga_ctx {
 
     // ---------------------------------------------------------------- solve
     riga::DevBuf<double> upd;          // forward-solve update vectors
+    riga::DevBuf<int> solve_order;     // 2F work items of the persistent solve
+    riga::DevBuf<int> solve_flags;     // per-front done flags (epoch-valued)
+    riga::DevBuf<int> solve_counter;   // work counter of the persistent solve
+    int solve_epoch = 0;
+    long long wait_limit = 1LL << 24;  // device dependency-wait budget (polls)
     riga::DevBuf<double> vwork[6];     // N-vectors (permuted order)
     riga::DevBuf<double> hostbuf_dev;  // staging for host arrays
     riga::DevBuf<double> red;          // reduction scratch

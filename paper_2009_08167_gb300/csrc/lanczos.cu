@@ -439,9 +439,15 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             m = j + 1;
             if (m % 10 == 0 || m == m_max) {
                 h_ab.resize(2 * (size_t)m_cap + 4);
+                int dflag = 0;
                 RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_ab.data(), c->ab.ptr, h_ab.size() * sizeof(double),
                                                  cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
                 RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+                if (dflag & 2) {
+                    status = set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+                    break;
+                }
                 const double* a = h_ab.data();
                 const double* b = h_ab.data() + m_cap + 2;  // b[i] = beta_i (b[0] = start norm)
                 theta.assign(m, 0.0);

@@ -2,108 +2,178 @@
 // (Sec. 4.2: one f/b elimination and the M mat-vecs per Lanczos step;
 // Sec. 5.1 Eq. flopsFb).  Vectors are in elimination order.
 //
-// fwd_kernel (one CTA per front of a level, leaves to root): the front's
-//   local vector w = [b(own); 0] plus the children's update vectors, then
-//   L11 z = w(own) by 32-column blocks (warp-shuffle triangle + row updates
-//   of every row below), w(border) -= L21 z.  z goes back to the vector, the
-//   border part becomes this front's update vector for its parent.
-// bwd_kernel (root to leaves): x(own) = L11^{-T} (D^{-1} z - L21^T x(border))
-//   by 32-column blocks (warp-per-column dot products + warp-shuffle
-//   triangle); x(border) belongs to ancestors and is already final.
-// Both read every factor entry exactly once per solve.
+// tree_solve_kernel: one persistent launch per solve, one CTA per front at a
+// time, fronts taken in dependency order (forward leaves to root, then
+// backward root to leaves) with bounded waits on per-front done flags.
+//   forward:  w = [b(own); 0] plus the children's update vectors, then
+//             L11 z = w(own) by 32-column blocks (diagonal block staged in
+//             shared memory, warp-shuffle triangle, row updates of all rows
+//             below), w(border) -= L21 z; z goes back to the vector, the
+//             border part is this front's update vector for its parent.
+//   backward: x(own) = L11^{-T} (D^{-1} z - L21^T x(border)) by 32-column
+//             blocks (warp-per-column dots, shuffle triangle); x(border)
+//             belongs to ancestors and is final.
+// Every factor entry is read exactly once per sweep.
+#include <algorithm>
+
 #include "ctx.h"
 
 namespace riga {
 
-template <typename T>
-__global__ void __launch_bounds__(256) fwd_kernel(const int* __restrict__ nodes, const T* __restrict__ pool,
-                                                  const long long* __restrict__ front_off,
-                                                  const int* __restrict__ node_ptr, const int* __restrict__ kk,
-                                                  const int* __restrict__ nn, const int* __restrict__ child_ptr,
-                                                  const int* __restrict__ child_list, const int* __restrict__ rel,
-                                                  const long long* __restrict__ rel_ptr,
-                                                  const long long* __restrict__ upd_off, double* __restrict__ upd,
-                                                  double* __restrict__ y) {
-    extern __shared__ unsigned char smem_raw[];
-    T* w = reinterpret_cast<T*>(smem_raw);
-    const int F = nodes[blockIdx.x];
-    const int k = kk[F], n = nn[F], b0 = node_ptr[F];
-    const T* L = pool + front_off[F];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < n; i += blockDim.x) w[i] = (i < k) ? (T)y[b0 + i] : T(0);
-    __syncthreads();
-    for (int ci = child_ptr[F]; ci < child_ptr[F + 1]; ++ci) {
-        const int c = child_list[ci];
-        const int m = nn[c] - kk[c];
-        const int* r = rel + rel_ptr[c];
-        const double* u = upd + upd_off[c];
-        for (int i = tid; i < m; i += blockDim.x) w[r[i]] += (T)u[i];
-        __syncthreads();
-    }
-    for (int jb = 0; jb < k; jb += 32) {
-        const int kb = min(32, k - jb);
-        if (warp == 0) {
-            T v = (lane < kb) ? w[jb + lane] : T(0);
-            for (int u = 0; u < kb; ++u) {
-                T zu = __shfl_sync(0xffffffffu, v, u);
-                if (lane > u && lane < kb) v -= L[(long long)(jb + u) * n + jb + lane] * zu;
-            }
-            if (lane < kb) w[jb + lane] = v;
+
+struct TreeArgs {
+    const long long* front_off;
+    const int* node_ptr;
+    const int* kk;
+    const int* nn;
+    const int* child_ptr;
+    const int* child_list;
+    const int* parent;
+    const int* rel;
+    const long long* rel_ptr;
+    const long long* upd_off;
+    const long long* front_ptr;
+    const int* front_pos;
+    const double* D;
+    const int* order;  // 2F work items: forward sweep (ascending height), then backward (descending)
+    int F;
+    double* upd;
+    double* y;
+    int* flags;        // [0,F) forward done, [F,2F) backward done: equal to epoch when done
+    int* counter;      // next work item (zeroed before the launch)
+    int* err;          // bit 1: a dependency wait gave up
+    int epoch;
+    long long spin_limit;  // polls (64 ns back-off each) before a wait gives up
+};
+
+__device__ __forceinline__ bool wait_flag(const int* f, int epoch, int* err, long long limit) {
+    long long it = 0;
+    while (*(volatile const int*)f != epoch) {
+        if (++it > limit) {
+            atomicOr(err, 2);
+            return false;
         }
-        __syncthreads();
-        for (int i = jb + kb + tid; i < n; i += blockDim.x) {
-            T acc = w[i];
-            for (int u = 0; u < kb; ++u) acc -= L[(long long)(jb + u) * n + i] * w[jb + u];
-            w[i] = acc;
-        }
-        __syncthreads();
+        __nanosleep(64);
     }
-    for (int i = tid; i < n; i += blockDim.x) {
-        if (i < k) y[b0 + i] = (double)w[i];
-        else upd[upd_off[F] + i - k] = (double)w[i];
-    }
-    (void)warp;
+    return true;
 }
 
+// One persistent launch per solve.  CTAs claim work items in order from a
+// global counter; an item waits (bounded) until its dependencies are done:
+// forward: the children's forward items; backward: its own forward item and
+// the parent's backward item.  Dependencies always have lower item indices,
+// so they were claimed by CTAs that are already running: no deadlock.
 template <typename T>
-__global__ void __launch_bounds__(256) bwd_kernel(const int* __restrict__ nodes, const T* __restrict__ pool,
-                                                  const long long* __restrict__ front_off,
-                                                  const int* __restrict__ node_ptr, const int* __restrict__ kk,
-                                                  const int* __restrict__ nn, const long long* __restrict__ front_ptr,
-                                                  const int* __restrict__ front_pos, const double* __restrict__ D,
-                                                  double* __restrict__ y) {
-    extern __shared__ unsigned char smem_raw[];
+__global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ pool, TreeArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* w = reinterpret_cast<T*>(smem_raw);
-    const int F = nodes[blockIdx.x];
-    const int k = kk[F], n = nn[F], b0 = node_ptr[F];
-    const T* L = pool + front_off[F];
-    const int* idx = front_pos + front_ptr[F];
+    __shared__ T Lb[32][33];
+    __shared__ int s_item, s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    for (int i = tid; i < n; i += blockDim.x) w[i] = (i < k) ? (T)(y[b0 + i] / D[b0 + i]) : (T)y[idx[i]];
-    __syncthreads();
-    const int last = ((k - 1) / 32) * 32;
-    for (int jb = last; jb >= 0; jb -= 32) {
-        const int kb = min(32, k - jb);
-        for (int j = jb + warp; j < jb + kb; j += nwarp) {
-            T s = T(0);
-            const T* Lc = L + (long long)j * n;
-            for (int i = jb + kb + lane; i < n; i += 32) s += Lc[i] * w[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) w[j] -= s;
-        }
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.counter, 1);
         __syncthreads();
-        if (warp == 0) {
-            T v = (lane < kb) ? w[jb + lane] : T(0);
-            for (int u = kb - 1; u >= 0; --u) {
-                T xu = __shfl_sync(0xffffffffu, v, u);
-                if (lane < u) v -= L[(long long)(jb + lane) * n + jb + u] * xu;
+        const int item = s_item;
+        if (item >= 2 * a.F) return;
+        const bool fwd = item < a.F;
+        const int F = a.order[item];
+        if (tid == 0) {
+            bool ok = true;
+            if (fwd) {
+                for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1] && ok; ++ci)
+                    ok = wait_flag(&a.flags[a.child_list[ci]], a.epoch, a.err, a.spin_limit);
+            } else {
+                ok = wait_flag(&a.flags[F], a.epoch, a.err, a.spin_limit);
+                const int par = a.parent[F];
+                if (ok && par >= 0) ok = wait_flag(&a.flags[a.F + par], a.epoch, a.err, a.spin_limit);
             }
-            if (lane < kb) w[jb + lane] = v;
+            __threadfence();
+            s_ok = ok;
         }
         __syncthreads();
+        if (!s_ok) return;
+        const int k = a.kk[F], n = a.nn[F], b0 = a.node_ptr[F];
+        const T* L = pool + a.front_off[F];
+        if (fwd) {
+            for (int i = tid; i < n; i += blockDim.x) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
+            __syncthreads();
+            for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1]; ++ci) {
+                const int c = a.child_list[ci];
+                const int m = a.nn[c] - a.kk[c];
+                const int* r = a.rel + a.rel_ptr[c];
+                const double* u = a.upd + a.upd_off[c];
+                for (int i = tid; i < m; i += blockDim.x) w[r[i]] += (T)__ldcg(&u[i]);
+                __syncthreads();
+            }
+            for (int jb = 0; jb < k; jb += 32) {
+                const int kb = min(32, k - jb);
+                for (int q = tid; q < 1024; q += blockDim.x) {
+                    const int r = q & 31, cc = q >> 5;
+                    Lb[r][cc] = (r < kb && cc < r) ? L[(long long)(jb + cc) * n + jb + r] : T(0);
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    T v = (lane < kb) ? w[jb + lane] : T(0);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const T zu = __shfl_sync(0xffffffffu, v, u);
+                        v -= Lb[lane][u] * zu;
+                    }
+                    if (lane < kb) w[jb + lane] = v;
+                }
+                __syncthreads();
+                for (int i = jb + kb + tid; i < n; i += blockDim.x) {
+                    T acc = w[i];
+#pragma unroll
+                    for (int u = 0; u < 32; ++u)
+                        if (u < kb) acc -= L[(long long)(jb + u) * n + i] * w[jb + u];
+                    w[i] = acc;
+                }
+                __syncthreads();
+            }
+            for (int i = tid; i < n; i += blockDim.x) {
+                if (i < k) a.y[b0 + i] = (double)w[i];
+                else a.upd[a.upd_off[F] + i - k] = (double)w[i];
+            }
+        } else {
+            const int* idx = a.front_pos + a.front_ptr[F];
+            for (int i = tid; i < n; i += blockDim.x)
+                w[i] = (i < k) ? (T)(__ldcg(&a.y[b0 + i]) / a.D[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
+            __syncthreads();
+            for (int jb = ((k - 1) / 32) * 32; jb >= 0; jb -= 32) {
+                const int kb = min(32, k - jb);
+                for (int j = jb + warp; j < jb + kb; j += nwarp) {
+                    T s = T(0);
+                    const T* Lc = L + (long long)j * n;
+                    for (int i = jb + kb + lane; i < n; i += 32) s += Lc[i] * w[i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) w[j] -= s;
+                }
+                for (int q = tid; q < 1024; q += blockDim.x) {
+                    const int r = q & 31, cc = q >> 5;
+                    Lb[r][cc] = (r < kb && cc < r) ? L[(long long)(jb + cc) * n + jb + r] : T(0);
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    T v = (lane < kb) ? w[jb + lane] : T(0);
+#pragma unroll
+                    for (int u = 31; u >= 0; --u) {
+                        const T xu = __shfl_sync(0xffffffffu, v, u);
+                        if (lane < u) v -= Lb[u][lane] * xu;
+                    }
+                    if (lane < kb) w[jb + lane] = v;
+                }
+                __syncthreads();
+            }
+            for (int i = tid; i < k; i += blockDim.x) a.y[b0 + i] = (double)w[i];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicExch(&a.flags[fwd ? F : a.F + F], a.epoch);
+        }
     }
-    for (int i = tid; i < k; i += blockDim.x) y[b0 + i] = (double)w[i];
 }
 
 // y = (A1 - shift A2) x over the permuted CSR, `lanes` threads per row.
@@ -187,8 +257,6 @@ __global__ void norm2_partial_kernel(long long N, const double* __restrict__ a, 
     }
 }
 
-static size_t level_smem(const LevelPlan& P, size_t elt) { return (size_t)P.max_n * elt; }
-
 template <typename T>
 static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     Symbolic& S = c->S;
@@ -196,47 +264,58 @@ static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     // algorithmic bytes: every factor entry read twice (forward, backward),
     // the vector read and written in each sweep
     PhaseScope scope(c, PH_SOLVE, 2.0 * (double)S.nnzL * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
-    for (int l = 0; l < S.n_levels; ++l) {
-        const LevelPlan& P = S.levels[l];
-        size_t sm = level_smem(P, sizeof(T));
-        { count_launch(c); fwd_kernel<T><<<(unsigned)P.nodes.size(), 256, sm, st>>>(
-            c->level_nodes.ptr + c->level_nodes_off[l], pool, c->front_off.ptr, c->node_ptr.ptr, c->kk.ptr, c->nn.ptr,
-            c->child_ptr.ptr, c->child_list.ptr, c->rel.ptr, c->rel_ptr.ptr, c->upd_off.ptr, c->upd.ptr, y); }
-    }
-    for (int l = S.n_levels - 1; l >= 0; --l) {
-        const LevelPlan& P = S.levels[l];
-        size_t sm = level_smem(P, sizeof(T));
-        { count_launch(c); bwd_kernel<T><<<(unsigned)P.nodes.size(), 256, sm, st>>>(
-            c->level_nodes.ptr + c->level_nodes_off[l], pool, c->front_off.ptr, c->node_ptr.ptr, c->kk.ptr, c->nn.ptr,
-            c->front_ptr.ptr, c->front_pos.ptr, c->D.ptr, y); }
-    }
-    return RIGA_OK;
-}
-
-static int configure_smem(riga_ctx* c) {
-    static int done_dev = -1;
-    if (done_dev == c->device) return RIGA_OK;
-    int maxopt = 0;
+    int max_n = 0;
+    for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
+    const size_t smem = (size_t)max_n * sizeof(T);
+    int maxopt = 0, nsm = 0, per_sm = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt));
-    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt));
-    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt));
-    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxopt));
-    done_dev = c->device;
+    RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    if (smem + 32 * 33 * sizeof(T) + 64 > (size_t)maxopt)
+        return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
+    if (smem > 48 * 1024)
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tree_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_solve_kernel<T>, 256, smem));
+    const int grid = std::max(1, std::min(2 * S.n_nodes, std::max(1, per_sm) * nsm));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_counter.ptr, 0, sizeof(int), st));
+    TreeArgs a;
+    a.front_off = c->front_off.ptr;
+    a.node_ptr = c->node_ptr.ptr;
+    a.kk = c->kk.ptr;
+    a.nn = c->nn.ptr;
+    a.child_ptr = c->child_ptr.ptr;
+    a.child_list = c->child_list.ptr;
+    a.parent = c->parent.ptr;
+    a.rel = c->rel.ptr;
+    a.rel_ptr = c->rel_ptr.ptr;
+    a.upd_off = c->upd_off.ptr;
+    a.front_ptr = c->front_ptr.ptr;
+    a.front_pos = c->front_pos.ptr;
+    a.D = c->D.ptr;
+    a.order = c->solve_order.ptr;
+    a.F = S.n_nodes;
+    a.upd = c->upd.ptr;
+    a.y = y;
+    a.flags = c->solve_flags.ptr;
+    a.counter = c->solve_counter.ptr;
+    a.err = c->flag.ptr;
+    a.epoch = ++c->solve_epoch;
+    a.spin_limit = c->wait_limit;
+    { count_launch(c); tree_solve_kernel<T><<<grid, 256, smem, st>>>(pool, a); }
     return RIGA_OK;
 }
 
 int enqueue_solve(riga_ctx* c, double* y) {
     if (!c->factored) return set_error(c, RIGA_ESTATE, "no factorization");
-    int rc = configure_smem(c);
-    if (rc) return rc;
     Symbolic& S = c->S;
-    int maxopt = 0;
-    cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    size_t elt = c->precision == RIGA_FP64 ? sizeof(double) : sizeof(float);
-    for (const LevelPlan& P : S.levels)
-        if (level_smem(P, elt) > (size_t)maxopt) return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
     RIGA_CUDA_TRY(c, c->upd.alloc(S.upd_size > 0 ? S.upd_size : 1));
+    if (c->solve_flags.count < (size_t)(2 * S.n_nodes)) {
+        c->solve_flags.release();
+        RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes));
+        RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, 2 * (size_t)S.n_nodes * sizeof(int), c->stream));
+        c->solve_epoch = 0;
+    }
+    RIGA_CUDA_TRY(c, c->solve_counter.alloc(1));
+    int rc;
     if (c->precision == RIGA_FP64) rc = enqueue_solve_t<double>(c, c->pool64.ptr, y);
     else rc = enqueue_solve_t<float>(c, c->pool32.ptr, y);
     if (rc) return rc;

@@ -32,7 +32,8 @@ RIGA_FP32 = 1
 EXPORTED = [
     "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_factor", "riga_solve", "riga_eigs",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
-    "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_strerror",
+    "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_set_wait_limit",
+    "riga_strerror",
     "riga_last_error",
 ]
 PHASES = ["assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"]
@@ -87,6 +88,7 @@ def load_library(path=LIB_PATH):
     lib.riga_spmv.argtypes = [P, I, P, P]
     lib.riga_stats.argtypes = [P] + [ctypes.POINTER(LL)] * 4 + [ctypes.POINTER(D)] * 2
     lib.riga_profile.argtypes = [P, I]
+    lib.riga_set_wait_limit.argtypes = [P, LL]
     lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
                                      ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.riga_strerror.argtypes = [I]
@@ -299,6 +301,9 @@ class Riga:
         self._check(self.lib.riga_stats(self.ctx, *[ctypes.byref(t) for t in v]))
         keys = ["n_fact", "n_solve", "n_matvec", "lanczos_steps", "t_fact_ms", "t_lanczos_ms"]
         return {k: t.value for k, t in zip(keys, v)}
+
+    def set_wait_limit(self, limit):
+        self._check(self.lib.riga_set_wait_limit(self.ctx, int(limit)))
 
     # ------------------------------------------------------------ profiling
     def profile(self, enable=True):

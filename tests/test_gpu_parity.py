@@ -245,3 +245,24 @@ def test_spmv_parity(R):
     x = np.random.default_rng(9).normal(size=K.n)
     assert np.allclose(R.spmv(0, x), M.matvec(x), rtol=1e-13, atol=1e-15)
     assert np.allclose(R.spmv(1, x), K.matvec(x), rtol=1e-12, atol=1e-12)
+
+
+def test_wait_budget_exhaustion_reports_timeout(R):
+    # a zero wait budget makes the persistent solve's dependency waits give up:
+    # the kernel returns, the host reports RIGA_ETIMEOUT, and the context stays
+    # usable with the default budget
+    from paper_2009_08167_gb300.riga import RigaError, RIGA_ETIMEOUT
+    mesh = Mesh(2, 32, 3, 8, 8)
+    R.assemble(mesh)
+    K, M = oracle_matrices(mesh)
+    R.factor(0.0)
+    b = np.random.default_rng(13).normal(size=K.n)
+    R.set_wait_limit(0)
+    with pytest.raises(RigaError) as e:
+        R.solve(b)
+    assert e.value.code == RIGA_ETIMEOUT
+    R.set_wait_limit(1 << 24)
+    R.factor(0.0)
+    x, _ = R.solve(b)
+    xr = np.linalg.solve(K.todense(), b)
+    assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
