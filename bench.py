@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the phase-timing pass")
+    ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor"],
+                    help="eigs: the benchmark; solve / factor: a short program (one factorization and "
+                         "--steps solves, or --steps factorizations) of the same workload, for profilers")
     return ap.parse_args()
 
 
@@ -327,8 +330,43 @@ def run_riga(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_kernel_mode(args, local_rank):
+    """Short program for profilers: the benchmark's mesh, one numeric
+    assembly, then --steps factorizations (mode factor) or one factorization
+    and --steps solves (mode solve) through the C ABI; prints one JSON line
+    with device times."""
+    import numpy as np
+    import torch
+    from paper_2009_08167_gb300 import riga
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    prec = riga.RIGA_FP64 if args.precision == "fp64" else riga.RIGA_FP32
+    cfg = workload(args.mesh)
+    R = riga.Riga(local_rank, stream)
+    R.assemble(cfg["mesh"])
+    N = R.query()["N"]
+    b = torch.randn(N, dtype=torch.float64, device="cuda")
+    x = torch.empty_like(b)
+    R.profile(True)
+    R.factor(0.0, prec)
+    for _ in range(args.steps):
+        if args.mode == "factor":
+            R.factor(0.0, prec)
+        else:
+            R.solve(b, out=x)
+    prof = R.profile_get()
+    R.profile(False)
+    q = R.query()
+    print(json.dumps({"mode": args.mode, "steps": args.steps, "N": N, "nnzL": q["nnzL"], "flops_fact": q["flops_fact"],
+                      "phases": prof}), flush=True)
+    R.close()
+
+
 def main():
     args = parse()
+    if args.mode != "eigs":
+        run_kernel_mode(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
