@@ -522,12 +522,16 @@ int riga_get_factor(riga_ctx* c, double* D, long long* Lptr, double* L) {
     if (L) {
         long long at = 0;
         for (int f = 0; f < S.n_nodes; ++f) {
-            long long cnt = (long long)S.n[f] * S.k[f];  // first k columns, leading dimension n
+            // first k columns, rows 0..n-1 of the augmented front (leading dimension n + k)
+            const long long n = S.n[f], k = S.k[f], ld = S.ld[f];
+            const long long cnt = n * k;
             if (c->precision == RIGA_FP64) {
-                RIGA_CUDA_TRY(c, cudaMemcpy(L + at, c->pool64.ptr + S.front_off[f], cnt * sizeof(double), cudaMemcpyDeviceToHost));
+                RIGA_CUDA_TRY(c, cudaMemcpy2D(L + at, n * sizeof(double), c->pool64.ptr + S.front_off[f], ld * sizeof(double),
+                                              n * sizeof(double), k, cudaMemcpyDeviceToHost));
             } else {
                 std::vector<float> tmp(cnt);
-                RIGA_CUDA_TRY(c, cudaMemcpy(tmp.data(), c->pool32.ptr + S.front_off[f], cnt * sizeof(float), cudaMemcpyDeviceToHost));
+                RIGA_CUDA_TRY(c, cudaMemcpy2D(tmp.data(), n * sizeof(float), c->pool32.ptr + S.front_off[f], ld * sizeof(float),
+                                              n * sizeof(float), k, cudaMemcpyDeviceToHost));
                 for (long long i = 0; i < cnt; ++i) L[at + i] = tmp[i];
             }
             at += cnt;

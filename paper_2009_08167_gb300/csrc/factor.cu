@@ -1,8 +1,13 @@
 // Multifrontal LDL^T of A = K - sigma M (Sec. 4.2 and its Remark on inertia),
 // fronts in FP64 or FP32, 1x1 pivots without pivoting.
 //
-// The fronts live side by side in one pool (column-major, leading dimension
-// n_F, lower triangle used).  Per assembly-tree level, leaves to root:
+// The fronts live side by side in one pool (column-major, lower triangle
+// used).  Each front is augmented by k_F extra rows coupled to its own
+// variables by the identity (ld_F = n_F + k_F rows): after the own block is
+// eliminated, the extra rows' Schur complement holds -A11^{-1} A12 and
+// -A11^{-1}, the operators of the GEMV-only tree solve (solve.cu); the
+// regular rows, D and the inertia are those of the plain factorization.
+// Per assembly-tree level, leaves to root:
 //   extend_add_kernel  children's Schur complements into the parents
 //                      (child rank 0, then rank 1: deterministic, no atomics);
 //   for each panel step s (panel columns [s*nb, s*nb+kb)):
@@ -32,20 +37,30 @@ __global__ void scatter_kernel(long long nnz, const long long* __restrict__ scat
 }
 
 template <typename T>
+__global__ void identity_kernel(int F, const int* __restrict__ kk, const int* __restrict__ nn,
+                                const long long* __restrict__ front_off, T* __restrict__ pool) {
+    const int f = blockIdx.x;
+    if (f >= F) return;
+    const int k = kk[f], n = nn[f], ld = n + k;
+    T* A = pool + front_off[f];
+    for (int r = threadIdx.x; r < k; r += blockDim.x) A[(long long)r * ld + n + r] = T(1);
+}
+
+template <typename T>
 __global__ void extend_add_kernel(const ExtItem* __restrict__ items, const int* __restrict__ parent,
                                   const long long* __restrict__ front_off, const int* __restrict__ kk,
                                   const int* __restrict__ nn, const int* __restrict__ rel,
                                   const long long* __restrict__ rel_ptr, T* __restrict__ pool) {
     const ExtItem it = items[blockIdx.x];
     const int c = it.child, P = parent[c];
-    const int kc = kk[c], nc = nn[c], np = nn[P];
+    const int kc = kk[c], nc = nn[c], ldc = nc + kc, ldp = nn[P] + kk[P];
     const int m = nc - kc;
-    const T* src = pool + front_off[c] + (long long)kc * nc + kc;
+    const T* src = pool + front_off[c] + (long long)kc * ldc + kc;
     T* dst = pool + front_off[P];
     const int* r = rel + rel_ptr[c];
     for (int j = it.c0; j < it.c1; ++j) {
-        const long long cj = (long long)r[j] * np;
-        for (int i = j + threadIdx.x; i < m; i += blockDim.x) dst[cj + r[i]] += src[(long long)j * nc + i];
+        const long long cj = (long long)r[j] * ldp;
+        for (int i = j + threadIdx.x; i < m; i += blockDim.x) dst[cj + r[i]] += src[(long long)j * ldc + i];
     }
 }
 
@@ -57,12 +72,12 @@ __global__ void diag_kernel(const PanelItem* __restrict__ items, const int* __re
                             int* __restrict__ flag) {
     __shared__ T Ls[NB][NB + 1];
     const PanelItem it = items[blockIdx.x];
-    const int F = it.front, k = kk[F], n = nn[F], j0 = it.r0;
+    const int F = it.front, k = kk[F], ld = nn[F] + k, j0 = it.r0;
     const int kb = min(NB, k - j0);
     T* A = pool + front_off[F];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, cc = idx / kb;
-        Ls[r][cc] = (r >= cc) ? A[(long long)(j0 + cc) * n + j0 + r] : T(0);
+        Ls[r][cc] = (r >= cc) ? A[(long long)(j0 + cc) * ld + j0 + r] : T(0);
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
@@ -80,7 +95,7 @@ __global__ void diag_kernel(const PanelItem* __restrict__ items, const int* __re
     }
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, cc = idx / kb;
-        if (r >= cc) A[(long long)(j0 + cc) * n + j0 + r] = Ls[r][cc];
+        if (r >= cc) A[(long long)(j0 + cc) * ld + j0 + r] = Ls[r][cc];
     }
     for (int t = threadIdx.x; t < kb; t += blockDim.x) D[node_ptr[F] + j0 + t] = (double)Ls[t][t];
 }
@@ -93,21 +108,21 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
     __shared__ T Ls[NB][NB + 1];
     __shared__ T ds[NB];
     const PanelItem it = items[blockIdx.x];
-    const int F = it.front, k = kk[F], n = nn[F];
+    const int F = it.front, k = kk[F], ld = nn[F] + k;
     const int kb = min(NB, k - j0);
     T* A = pool + front_off[F];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, cc = idx / kb;
-        if (r > cc) Ls[r][cc] = A[(long long)(j0 + cc) * n + j0 + r];
-        if (r == cc) ds[r] = A[(long long)(j0 + cc) * n + j0 + r];
+        if (r > cc) Ls[r][cc] = A[(long long)(j0 + cc) * ld + j0 + r];
+        if (r == cc) ds[r] = A[(long long)(j0 + cc) * ld + j0 + r];
     }
     __syncthreads();
     const int r = it.r0 + threadIdx.x;
-    if (r >= n) return;
+    if (r >= ld) return;
     T x[NB];
 #pragma unroll
     for (int t = 0; t < NB; ++t)
-        if (t < kb) x[t] = A[(long long)(j0 + t) * n + r];
+        if (t < kb) x[t] = A[(long long)(j0 + t) * ld + r];
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
         if (t < kb) {
@@ -120,7 +135,7 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
     }
 #pragma unroll
     for (int t = 0; t < NB; ++t)
-        if (t < kb) A[(long long)(j0 + t) * n + r] = x[t];
+        if (t < kb) A[(long long)(j0 + t) * ld + r] = x[t];
 }
 
 // C[i0:i0+64, j0:j0+64] -= L[:, panel] D L[:, panel]^T (256 threads, 4x4 each)
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
     __shared__ T As[NB][TILE];
     __shared__ T Bs[NB][TILE];
     const TileItem it = items[blockIdx.x];
-    const int F = it.front, k = kk[F], n = nn[F];
+    const int F = it.front, k = kk[F], n = nn[F], ld = n + k;
     const int kb = min(NB, k - p0);
     T* A = pool + front_off[F];
     const double* d = D + node_ptr[F] + p0;
@@ -143,8 +158,8 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
         T a = T(0), b = T(0);
         if (t < kb) {
             int gi = it.i0 + rr, gj = it.j0 + rr;
-            if (gi < n) a = A[(long long)(p0 + t) * n + gi];
-            if (gj < n) b = A[(long long)(p0 + t) * n + gj] * (T)d[t];
+            if (gi < ld) a = A[(long long)(p0 + t) * ld + gi];
+            if (gj < ld) b = A[(long long)(p0 + t) * ld + gj] * (T)d[t];
         }
         As[t][rr] = a;
         Bs[t][rr] = b;
@@ -170,11 +185,12 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         int gj = it.j0 + ty + 16 * b;
-        if (gj >= n) continue;
+        if (gj >= ld) continue;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             int gi = it.i0 + tx + 16 * a;
-            if (gi < n && gi >= gj) A[(long long)gj * n + gi] -= acc[a][b];
+            // lower triangle, plus the whole extra x extra block
+            if (gi < ld && (gi >= gj || (gi >= n && gj >= n))) A[(long long)gj * ld + gi] -= acc[a][b];
         }
     }
 }
@@ -195,10 +211,11 @@ template <typename T>
 static int enqueue_factor_t(riga_ctx* c, T* pool) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
-    PhaseScope scope(c, PH_FACTOR, 0.0, S.flops);
+    PhaseScope scope(c, PH_FACTOR, 0.0, S.flops + S.flops_aug);
     RIGA_CUDA_TRY(c, cudaMemsetAsync(pool, 0, (size_t)S.pool_size * sizeof(T), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
+    { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
     if (S.nnz > 0)
         { count_launch(c); scatter_kernel<T><<<(unsigned)((S.nnz + 255) / 256), 256, 0, st>>>(S.nnz, c->scatter.ptr, c->Kval.ptr,
                                                                           c->Mval.ptr, c->sigma, pool); }

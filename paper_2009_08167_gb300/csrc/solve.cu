@@ -5,15 +5,17 @@
 // tree_solve_kernel: one persistent launch per solve, one CTA per front at a
 // time, fronts taken in dependency order (forward leaves to root, then
 // backward root to leaves) with bounded waits on per-front done flags.
-//   forward:  w = [b(own); 0] plus the children's update vectors, then
-//             L11 z = w(own) by 32-column blocks (diagonal block staged in
-//             shared memory, warp-shuffle triangle, row updates of all rows
-//             below), w(border) -= L21 z; z goes back to the vector, the
-//             border part is this front's update vector for its parent.
-//   backward: x(own) = L11^{-T} (D^{-1} z - L21^T x(border)) by 32-column
-//             blocks (warp-per-column dots, shuffle triangle); x(border)
-//             belongs to ancestors and is final.
-// Every factor entry is read exactly once per sweep.
+// The factorization leaves in each augmented front's extra rows the block
+// elimination operators of the front, -A11^{-1} A12 and -A11^{-1}, so that
+// the forward/backward elimination of Sec. 4.2 (L y = b, D, L^T x = z) is,
+// front by front, one GEMV each way:
+//   forward:  w = [b(own); 0] plus the children's update vectors;
+//             u = w(border) - A21 A11^{-1} w(own) is this front's update
+//             vector for its parent; w(own) is kept in the vector.
+//   backward: x(own) = A11^{-1} w(own) - A11^{-1} A12 x(border), with
+//             x(border) owned by ancestors and already final.
+// No sequential triangular chain remains inside a front; every operator
+// entry is read once per sweep.
 #include <algorithm>
 
 #include "ctx.h"
@@ -67,7 +69,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ pool, TreeArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* w = reinterpret_cast<T*>(smem_raw);
-    __shared__ T Lb[32][33];
+    __shared__ T red[8][33];
     __shared__ int s_item, s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     for (;;) {
@@ -92,9 +94,12 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
         }
         __syncthreads();
         if (!s_ok) return;
-        const int k = a.kk[F], n = a.nn[F], b0 = a.node_ptr[F];
-        const T* L = pool + a.front_off[F];
+        const int k = a.kk[F], n = a.nn[F], ld = n + k, b0 = a.node_ptr[F];
+        // extra rows of the augmented front: E[r][c] = Fr[(n + r) + c * ld],
+        // columns [k, n): -A11^{-1} A12, columns [n, n + k): -A11^{-1}
+        const T* E = pool + a.front_off[F] + n;
         if (fwd) {
+            // w = [b(own); 0] + children's update vectors
             for (int i = tid; i < n; i += blockDim.x) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
             __syncthreads();
             for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1]; ++ci) {
@@ -105,68 +110,40 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
                 for (int i = tid; i < m; i += blockDim.x) w[r[i]] += (T)__ldcg(&u[i]);
                 __syncthreads();
             }
-            for (int jb = 0; jb < k; jb += 32) {
-                const int kb = min(32, k - jb);
-                for (int q = tid; q < 1024; q += blockDim.x) {
-                    const int r = q & 31, cc = q >> 5;
-                    Lb[r][cc] = (r < kb && cc < r) ? L[(long long)(jb + cc) * n + jb + r] : T(0);
-                }
-                __syncthreads();
-                if (warp == 0) {
-                    T v = (lane < kb) ? w[jb + lane] : T(0);
+            // keep w1 = w(own) for the backward sweep; u = w2 - A21 A11^{-1} w1
+            for (int i = tid; i < k; i += blockDim.x) a.y[b0 + i] = (double)w[i];
+            double* u = a.upd + a.upd_off[F] - k;
+            for (int cc = k + warp; cc < n; cc += nwarp) {
+                const T* col = E + (long long)cc * ld;
+                T s = T(0);
+                for (int r = lane; r < k; r += 32) s += col[r] * w[r];
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        const T zu = __shfl_sync(0xffffffffu, v, u);
-                        v -= Lb[lane][u] * zu;
-                    }
-                    if (lane < kb) w[jb + lane] = v;
-                }
-                __syncthreads();
-                for (int i = jb + kb + tid; i < n; i += blockDim.x) {
-                    T acc = w[i];
-#pragma unroll
-                    for (int u = 0; u < 32; ++u)
-                        if (u < kb) acc -= L[(long long)(jb + u) * n + i] * w[jb + u];
-                    w[i] = acc;
-                }
-                __syncthreads();
-            }
-            for (int i = tid; i < n; i += blockDim.x) {
-                if (i < k) a.y[b0 + i] = (double)w[i];
-                else a.upd[a.upd_off[F] + i - k] = (double)w[i];
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) u[cc] = (double)(w[cc] + s);
             }
         } else {
+            // v = [-w1; x(border)], x(own) = A11^{-1} w1 - A11^{-1} A12 x2 = E v
             const int* idx = a.front_pos + a.front_ptr[F];
             for (int i = tid; i < n; i += blockDim.x)
-                w[i] = (i < k) ? (T)(__ldcg(&a.y[b0 + i]) / a.D[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
+                w[i] = (i < k) ? -(T)__ldcg(&a.y[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
             __syncthreads();
-            for (int jb = ((k - 1) / 32) * 32; jb >= 0; jb -= 32) {
-                const int kb = min(32, k - jb);
-                for (int j = jb + warp; j < jb + kb; j += nwarp) {
-                    T s = T(0);
-                    const T* Lc = L + (long long)j * n;
-                    for (int i = jb + kb + lane; i < n; i += 32) s += Lc[i] * w[i];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) w[j] -= s;
-                }
-                for (int q = tid; q < 1024; q += blockDim.x) {
-                    const int r = q & 31, cc = q >> 5;
-                    Lb[r][cc] = (r < kb && cc < r) ? L[(long long)(jb + cc) * n + jb + r] : T(0);
-                }
+            for (int r0 = 0; r0 < k; r0 += 32) {
+                const int r = r0 + lane;
+                T acc = T(0);
+                if (r < k)
+                    for (int j = warp; j < n; j += nwarp) {
+                        const int colj = (j < k) ? n + j : j;
+                        acc += E[(long long)colj * ld + r] * w[j];
+                    }
+                red[warp][lane] = acc;
                 __syncthreads();
                 if (warp == 0) {
-                    T v = (lane < kb) ? w[jb + lane] : T(0);
-#pragma unroll
-                    for (int u = 31; u >= 0; --u) {
-                        const T xu = __shfl_sync(0xffffffffu, v, u);
-                        if (lane < u) v -= Lb[u][lane] * xu;
-                    }
-                    if (lane < kb) w[jb + lane] = v;
+                    T sum = T(0);
+                    for (int q = 0; q < nwarp; ++q) sum += red[q][lane];
+                    if (r < k) a.y[b0 + r] = (double)sum;
                 }
                 __syncthreads();
             }
-            for (int i = tid; i < k; i += blockDim.x) a.y[b0 + i] = (double)w[i];
         }
         __syncthreads();
         if (tid == 0) {
@@ -263,14 +240,16 @@ static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     cudaStream_t st = c->stream;
     // algorithmic bytes: every factor entry read twice (forward, backward),
     // the vector read and written in each sweep
-    PhaseScope scope(c, PH_SOLVE, 2.0 * (double)S.nnzL * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
+    // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
+    // and the vector read and written in each sweep
+    PhaseScope scope(c, PH_SOLVE, (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
     int max_n = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
     const size_t smem = (size_t)max_n * sizeof(T);
     int maxopt = 0, nsm = 0, per_sm = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    if (smem + 32 * 33 * sizeof(T) + 64 > (size_t)maxopt)
+    if (smem + 8 * 33 * sizeof(T) + 64 > (size_t)maxopt)
         return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
     if (smem > 48 * 1024)
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tree_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -296,8 +296,13 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
         return S.k[f] + (int)(it - bb);
     };
 
+    // Augmented fronts: k extra rows below the n front rows, coupled to the own
+    // variables by the identity.  Eliminating the own block leaves -A11^{-1} A12
+    // and -A11^{-1} in the extra rows' Schur complement: the solve operators.
+    S.ld.assign(F, 0);
+    for (int f = 0; f < F; ++f) S.ld[f] = S.n[f] + S.k[f];
     S.front_off.assign(F + 1, 0);
-    for (int f = 0; f < F; ++f) S.front_off[f + 1] = S.front_off[f] + (long long)S.n[f] * S.n[f];
+    for (int f = 0; f < F; ++f) S.front_off[f + 1] = S.front_off[f] + (long long)S.ld[f] * S.ld[f];
     S.pool_size = S.front_off[F];
 
     S.scatter.assign(S.nnz, -1);
@@ -309,7 +314,7 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
             int lc = j - S.node_ptr[f];
             int lr = local_index(f, i);
             if (lr < 0) return "internal: matrix entry outside its front";
-            S.scatter[e] = S.front_off[f] + (long long)lc * S.n[f] + lr;
+            S.scatter[e] = S.front_off[f] + (long long)lc * S.ld[f] + lr;
         }
 
     S.rel_ptr.assign(F + 1, 0);
@@ -341,11 +346,19 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
     }
     S.n_levels = maxh + 1;
     S.nnzL = 0;
+    S.nnzQ = 0;
+    S.nnzL_own2 = 0;
     S.flops = 0.0;
+    S.flops_aug = 0.0;
     for (int f = 0; f < F; ++f) {
         long long kk = S.k[f], nn = S.n[f];
         S.nnzL += kk * (kk + 1) / 2 + kk * (nn - kk);
-        for (long long i = 0; i < kk; ++i) S.flops += (double)(nn - i) * (double)(nn - i - 1);
+        S.nnzQ += kk * nn;
+        S.nnzL_own2 += kk * kk;
+        for (long long i = 0; i < kk; ++i) {
+            S.flops += (double)(nn - i) * (double)(nn - i - 1);
+            S.flops_aug += (double)(nn + kk - i) * (double)(nn + kk - i - 1) - (double)(nn - i) * (double)(nn - i - 1);
+        }
     }
 
     // ---------------------------------------------------- level schedule
@@ -384,17 +397,22 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
             R.p_begin = (int)S.pitems.size();
             R.t_begin = (int)S.titems.size();
             for (int f : P.nodes) {
-                int kf = S.k[f], nf = S.n[f];
+                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 int kb = std::min(nb, kf - s * nb);
-                for (int r0 = s * nb + kb; r0 < nf; r0 += rb) S.pitems.push_back({f, r0});
+                for (int r0 = s * nb + kb; r0 < lf; r0 += rb) S.pitems.push_back({f, r0});
                 int c0 = s * nb + kb;
-                if (c0 < nf) {
-                    int T = (nf - c0 + tile - 1) / tile;
-                    for (int bi = 0; bi < T; ++bi)
-                        for (int bj = 0; bj <= bi; ++bj)
-                            S.titems.push_back({f, c0 + bi * tile, c0 + bj * tile});
-                }
+                // trailing update: lower tiles of the augmented front, plus the
+                // upper tiles of the extra x extra block so that -A11^{-1} is
+                // stored in full
+                int T = (lf - c0 + tile - 1) / tile;
+                for (int bi = 0; bi < T; ++bi)
+                    for (int bj = 0; bj < T; ++bj) {
+                        int i0 = c0 + bi * tile, j0 = c0 + bj * tile;
+                        bool lower = bj <= bi;
+                        bool extra_upper = (i0 + tile > nf) && (j0 + tile > nf);
+                        if (lower || extra_upper) S.titems.push_back({f, i0, j0});
+                    }
             }
             R.p_end = (int)S.pitems.size();
             R.t_end = (int)S.titems.size();

@@ -56,7 +56,8 @@ struct Symbolic {
     std::vector<int> parent;
     std::vector<int> child_ptr, child_list;  // children in order (left, right)
     std::vector<int> node_of;      // node_of[pos]
-    std::vector<int> k, n;         // fully summed / front size
+    std::vector<int> k, n;         // fully summed / front size (own + border)
+    std::vector<int> ld;           // rows of the augmented front: n + k
     std::vector<long long> front_ptr;  // index lists (positions) at front_ptr[F]
     std::vector<int> front_pos;        // own positions then border positions
     std::vector<int> height;
@@ -71,7 +72,7 @@ struct Symbolic {
     std::vector<long long> glob_rowptr;
     std::vector<long long> perm_to_glob;
 
-    // front pool (column-major, leading dimension n_F)
+    // front pool (column-major, leading dimension ld_F = n_F + k_F)
     std::vector<long long> front_off;
     long long pool_size = 0;
     std::vector<long long> scatter;   // per permuted CSR entry: pool offset or -1 (upper)
@@ -90,8 +91,11 @@ struct Symbolic {
     // element structure (for assembly with coefficients and the adjoint)
     long long n_elem = 0;
 
-    long long nnzL = 0;
-    double flops = 0.0;
+    long long nnzL = 0;   // factor entries (lower trapezoids of the n x k panels)
+    long long nnzQ = 0;   // solve-operator entries (k x n extra-row blocks)
+    long long nnzL_own2 = 0;  // sum k^2: the -A11^{-1} part, read only by the backward sweep
+    double flops = 0.0;   // LDL^T flops of the fronts
+    double flops_aug = 0.0;  // additional flops of the extra rows
 };
 
 // Builds everything above.  Returns an empty string on success, else a message.
