@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the phase-timing pass")
-    ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor"],
+    ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor", "trace"],
                     help="eigs: the benchmark; solve / factor: a short program (one factorization and "
                          "--steps solves, or --steps factorizations) of the same workload, for profilers")
     return ap.parse_args()
@@ -347,6 +347,18 @@ def run_kernel_mode(args, local_rank):
     N = R.query()["N"]
     b = torch.randn(N, dtype=torch.float64, device="cuda")
     x = torch.empty_like(b)
+    if args.mode == "trace":
+        R.factor(0.0, prec)
+        for _ in range(3):
+            R.solve(b, out=x)
+        tr, order = R.trace_solve(b.cpu().numpy())
+        sym = R.get_symbolic()
+        np.savez(os.path.join(ROOT, "gpurun_out", "solve_trace.npz"), trace=tr, order=order, parent=sym["parent"],
+                 node_ptr=sym["node_ptr"], front_ptr=sym["front_ptr"])
+        t0 = tr[:, 1].min()
+        print(json.dumps({"mode": "trace", "items": int(tr.shape[0]), "span_us": float((tr[:, 3].max() - t0) / 1e3)}))
+        R.close()
+        return
     R.profile(True)
     R.factor(0.0, prec)
     for _ in range(args.steps):

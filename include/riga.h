@@ -280,6 +280,19 @@ int riga_profile_get(riga_ctx* ctx, int phase, const char** name, long long* lau
  */
 int riga_set_wait_limit(riga_ctx* ctx, long long limit);
 
+/*
+ * riga_trace_solve: one forward/backward elimination of b (as riga_solve with
+ * tol = 0, FP64 or FP32 factor, no refinement) that also records, for each of
+ * the 2 n_nodes work items of the persistent tree solve (forward items in
+ * ascending tree height, then backward items in descending height), four
+ * int64 values in trace[4*item ..]: the SM that ran it, the global-timer
+ * nanoseconds when it was claimed, when its dependencies were satisfied, and
+ * when it completed.  trace: host array of 8 n_nodes int64; order (may be
+ * NULL): host array of 2 n_nodes ints receiving the node of each item.
+ * Errors: RIGA_ESTATE, RIGA_ETIMEOUT, RIGA_ECUDA.
+ */
+int riga_trace_solve(riga_ctx* ctx, const double* b, long long* trace, int* order);
+
 /* riga_strerror: static name of a status code. */
 const char* riga_strerror(int status);
 

@@ -623,4 +623,33 @@ int riga_set_wait_limit(riga_ctx* c, long long limit) {
     return RIGA_OK;
 }
 
+int riga_trace_solve(riga_ctx* c, const double* b, long long* trace, int* order) {
+    if (!c || !b || !trace) return RIGA_EINVAL;
+    c->last_error.clear();
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    cudaSetDevice(c->device);
+    if (!c->factored) return set_error(c, RIGA_ESTATE, "riga_factor first");
+    const Symbolic& S = c->S;
+    const long long N = S.N;
+    const size_t nt = 8 * (size_t)S.n_nodes;
+    DevBuf<long long> tb;
+    RIGA_CUDA_TRY(c, tb.alloc(nt));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(tb.ptr, 0, nt * sizeof(long long), c->stream));
+    for (int i = 0; i < 2; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    int rc = to_device(c, b, c->vwork[0].ptr, N);
+    if (rc) return rc;
+    enqueue_permute(c, c->vwork[0].ptr, c->vwork[1].ptr, 1, 1);
+    c->trace_buf = tb.ptr;
+    rc = enqueue_solve(c, c->vwork[1].ptr);
+    c->trace_buf = nullptr;
+    if (rc) return rc;
+    int dflag = 0;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(trace, tb.ptr, nt * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (order) RIGA_CUDA_TRY(c, cudaMemcpyAsync(order, c->solve_order.ptr, 2 * (size_t)S.n_nodes * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (dflag & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+    return RIGA_OK;
+}
+
 }  // extern "C"

@@ -108,6 +108,7 @@ struct riga_ctx {
     riga::DevBuf<int> solve_counter;   // work counter of the persistent solve
     int solve_epoch = 0;
     long long wait_limit = 1LL << 24;  // device dependency-wait budget (polls)
+    long long* trace_buf = nullptr;    // device trace of the next solve (riga_trace_solve)
     riga::DevBuf<double> vwork[6];     // N-vectors (permuted order)
     riga::DevBuf<double> hostbuf_dev;  // staging for host arrays
     riga::DevBuf<double> red;          // reduction scratch

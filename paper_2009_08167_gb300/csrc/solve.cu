@@ -46,7 +46,20 @@ struct TreeArgs {
     int* err;          // bit 1: a dependency wait gave up
     int epoch;
     long long spin_limit;  // polls (64 ns back-off each) before a wait gives up
+    long long* trace;      // optional: per item {sm, claim ns, deps-ready ns, done ns}
 };
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int sm_id() {
+    int id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
 
 __device__ __forceinline__ bool wait_flag(const int* f, int epoch, int* err, long long limit) {
     long long it = 0;
@@ -80,6 +93,10 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
         const bool fwd = item < a.F;
         const int F = a.order[item];
         if (tid == 0) {
+            if (a.trace) {
+                a.trace[4 * item] = sm_id();
+                a.trace[4 * item + 1] = global_ns();
+            }
             bool ok = true;
             if (fwd) {
                 for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1] && ok; ++ci)
@@ -91,6 +108,7 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
             }
             __threadfence();
             s_ok = ok;
+            if (a.trace) a.trace[4 * item + 2] = global_ns();
         }
         __syncthreads();
         if (!s_ok) return;
@@ -149,6 +167,7 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
         if (tid == 0) {
             __threadfence();
             atomicExch(&a.flags[fwd ? F : a.F + F], a.epoch);
+            if (a.trace) a.trace[4 * item + 3] = global_ns();
         }
     }
 }
@@ -279,6 +298,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     a.err = c->flag.ptr;
     a.epoch = ++c->solve_epoch;
     a.spin_limit = c->wait_limit;
+    a.trace = c->trace_buf;
     { count_launch(c); tree_solve_kernel<T><<<grid, 256, smem, st>>>(pool, a); }
     return RIGA_OK;
 }

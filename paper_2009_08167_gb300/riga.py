@@ -33,7 +33,7 @@ EXPORTED = [
     "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_factor", "riga_solve", "riga_eigs",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
     "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_set_wait_limit",
-    "riga_strerror",
+    "riga_trace_solve", "riga_strerror",
     "riga_last_error",
 ]
 PHASES = ["assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"]
@@ -89,6 +89,7 @@ def load_library(path=LIB_PATH):
     lib.riga_stats.argtypes = [P] + [ctypes.POINTER(LL)] * 4 + [ctypes.POINTER(D)] * 2
     lib.riga_profile.argtypes = [P, I]
     lib.riga_set_wait_limit.argtypes = [P, LL]
+    lib.riga_trace_solve.argtypes = [P, P, P, P]
     lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
                                      ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.riga_strerror.argtypes = [I]
@@ -301,6 +302,15 @@ class Riga:
         self._check(self.lib.riga_stats(self.ctx, *[ctypes.byref(t) for t in v]))
         keys = ["n_fact", "n_solve", "n_matvec", "lanczos_steps", "t_fact_ms", "t_lanczos_ms"]
         return {k: t.value for k, t in zip(keys, v)}
+
+    def trace_solve(self, b):
+        """One traced solve: per work item (sm, claim ns, ready ns, done ns) and its node."""
+        F = self.get_symbolic()["parent"].size
+        tr = np.zeros((2 * F, 4), dtype=np.int64)
+        order = np.zeros(2 * F, dtype=np.int32)
+        bb = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b
+        self._check(self.lib.riga_trace_solve(self.ctx, _ptr(bb), _ptr(tr), _ptr(order)))
+        return tr, order
 
     def set_wait_limit(self, limit):
         self._check(self.lib.riga_set_wait_limit(self.ctx, int(limit)))
