@@ -70,6 +70,9 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->scatter.upload(S.scatter, st));
     RIGA_CUDA_TRY(c, c->perm_to_glob.upload(S.perm_to_glob, st));
     RIGA_CUDA_TRY(c, c->glob_rowptr.upload(S.glob_rowptr, st));
+    RIGA_CUDA_TRY(c, c->ldq.upload(S.ldq, st));
+    RIGA_CUDA_TRY(c, c->qoff.upload(S.qoff, st));
+    RIGA_CUDA_TRY(c, c->qitems.upload(S.qitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.qitems, st));
     std::vector<int> ln;
     c->level_nodes_off.assign(S.n_levels + 1, 0);
     for (int l = 0; l < S.n_levels; ++l) {

@@ -77,6 +77,9 @@ struct riga_ctx {
     std::vector<double> coefK, coefM;  // host copies (empty = constant)
 
     // symbolic arrays on the device
+    riga::DevBuf<long long> qoff;
+    riga::DevBuf<int> ldq;
+    riga::DevBuf<riga::PanelItem> qitems;
     riga::DevBuf<long long> rowptr, front_off, front_ptr, rel_ptr, upd_off, scatter, perm_to_glob, glob_rowptr;
     riga::DevBuf<int> col, perm, ipos, node_ptr, kk, nn, front_pos, child_ptr, child_list, rel, level_nodes, parent;
     std::vector<int> level_nodes_off;  // offsets of each level in level_nodes
@@ -96,6 +99,8 @@ struct riga_ctx {
     double sigma = 0.0;
     riga::DevBuf<double> pool64;
     riga::DevBuf<float> pool32;
+    riga::DevBuf<double> q64;    // packed solve operators (see Symbolic::qoff)
+    riga::DevBuf<float> q32;
     riga::DevBuf<double> D;      // pivots in elimination order
     riga::DevBuf<int> flag;      // device error word (bit 0: pivot breakdown)
     riga::DevBuf<long long> neg; // inertia counter

@@ -195,6 +195,25 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
     }
 }
 
+// Q[qoff + j*ldq + r] = extra-row entry (n + r, col_j) of the front, col_j =
+// n + j for j < k (-A11^{-1}), j for j >= k (-A11^{-1} A12); rows k..ldq zero.
+template <typename T>
+__global__ void pack_q_kernel(const PanelItem* __restrict__ items, const int* __restrict__ kk,
+                              const int* __restrict__ nn, const long long* __restrict__ front_off,
+                              const int* __restrict__ ldq, const long long* __restrict__ qoff,
+                              const T* __restrict__ pool, T* __restrict__ Q) {
+    const PanelItem it = items[blockIdx.x];
+    const int F = it.front, k = kk[F], n = nn[F], ld = n + k, lq = ldq[F];
+    const T* E = pool + front_off[F] + n;
+    T* q = Q + qoff[F];
+    const int j1 = min(n, it.r0 + 32);
+    for (int j = it.r0; j < j1; ++j) {
+        const int col = (j < k) ? n + j : j;
+        for (int r = threadIdx.x; r < lq; r += blockDim.x)
+            q[(long long)j * lq + r] = (r < k) ? E[(long long)col * ld + r] : T(0);
+    }
+}
+
 __global__ void inertia_kernel(long long N, const double* __restrict__ D, long long* __restrict__ neg) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -208,7 +227,7 @@ __global__ void inertia_kernel(long long N, const double* __restrict__ D, long l
 }
 
 template <typename T>
-static int enqueue_factor_t(riga_ctx* c, T* pool) {
+static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_FACTOR, 0.0, S.flops + S.flops_aug);
@@ -243,6 +262,10 @@ static int enqueue_factor_t(riga_ctx* c, T* pool) {
                                                                       c->D.ptr, pool); }
         }
     }
+    if (!S.qitems.empty())
+        { count_launch(c); pack_q_kernel<T><<<(unsigned)S.qitems.size(), 128, 0, st>>>(c->qitems.ptr, c->kk.ptr, c->nn.ptr,
+                                                                                      c->front_off.ptr, c->ldq.ptr,
+                                                                                      c->qoff.ptr, pool, Q); }
     { count_launch(c); inertia_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->neg.ptr); }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     return RIGA_OK;
@@ -256,12 +279,16 @@ int enqueue_factor(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->neg.alloc(1));
     if (c->precision == RIGA_FP64) {
         c->pool32.release();
+        c->q32.release();
         if (c->pool64.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp64)");
-        return enqueue_factor_t<double>(c, c->pool64.ptr);
+        if (c->q64.alloc(S.q_size + 4) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "solve operators (fp64)");
+        return enqueue_factor_t<double>(c, c->pool64.ptr, c->q64.ptr);
     }
     c->pool64.release();
+    c->q64.release();
     if (c->pool32.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp32)");
-    return enqueue_factor_t<float>(c, c->pool32.ptr);
+    if (c->q32.alloc(S.q_size + 4) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "solve operators (fp32)");
+    return enqueue_factor_t<float>(c, c->pool32.ptr, c->q32.ptr);
 }
 
 int finish_factor(riga_ctx* c) {

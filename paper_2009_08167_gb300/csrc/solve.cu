@@ -14,8 +14,10 @@
 //             vector for its parent; w(own) is kept in the vector.
 //   backward: x(own) = A11^{-1} w(own) - A11^{-1} A12 x(border), with
 //             x(border) owned by ancestors and already final.
-// No sequential triangular chain remains inside a front; every operator
-// entry is read once per sweep.
+// No sequential triangular chain remains inside a front.  The operators are
+// packed per front (factor.cu) and stream through shared memory by bulk
+// copies (cp.async.bulk + mbarrier, double buffered), issued before the
+// item waits on its dependencies; every operator entry is read once per sweep.
 #include <algorithm>
 
 #include "ctx.h"
@@ -24,7 +26,6 @@ namespace riga {
 
 
 struct TreeArgs {
-    const long long* front_off;
     const int* node_ptr;
     const int* kk;
     const int* nn;
@@ -36,14 +37,17 @@ struct TreeArgs {
     const long long* upd_off;
     const long long* front_ptr;
     const int* front_pos;
-    const double* D;
+    const int* ldq;
+    const long long* qoff;
     const int* order;  // 2F work items: forward sweep (ascending height), then backward (descending)
     int F;
+    int chunk_elems;   // elements per shared-memory chunk buffer (two buffers)
+    int max_n, max_k;
     double* upd;
     double* y;
     int* flags;        // [0,F) forward done, [F,2F) backward done: equal to epoch when done
     int* counter;      // next work item (zeroed before the launch)
-    int* err;          // bit 1: a dependency wait gave up
+    int* err;          // bit 1: a dependency or copy wait gave up
     int epoch;
     long long spin_limit;  // polls (64 ns back-off each) before a wait gives up
     long long* trace;      // optional: per item {sm, claim ns, deps-ready ns, done ns}
@@ -73,18 +77,72 @@ __device__ __forceinline__ bool wait_flag(const int* f, int epoch, int* err, lon
     return true;
 }
 
+// ---- bulk (TMA) copies global -> shared with mbarrier completion (PTX) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err, long long limit) {
+    long long it = 0;
+    while (!mbar_test(bar, parity)) {
+        if (++it > limit) {
+            atomicOr(err, 2);
+            return false;
+        }
+    }
+    return true;
+}
+
 // One persistent launch per solve.  CTAs claim work items in order from a
 // global counter; an item waits (bounded) until its dependencies are done:
 // forward: the children's forward items; backward: its own forward item and
 // the parent's backward item.  Dependencies always have lower item indices,
 // so they were claimed by CTAs that are already running: no deadlock.
+// The item's operator block streams through two shared-memory buffers by
+// bulk copies issued before the dependency wait.
 template <typename T>
-__global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ pool, TreeArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* w = reinterpret_cast<T*>(smem_raw);
-    __shared__ T red[8][33];
+__global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* buf[2];
+    buf[0] = reinterpret_cast<T*>(smem_raw);
+    buf[1] = buf[0] + a.chunk_elems;
+    T* w = buf[1] + a.chunk_elems;  // local vector (n)
+    T* xs = w + a.max_n;            // backward accumulators (k)
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_item, s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    unsigned parity[2] = {0u, 0u};
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
         __syncthreads();
@@ -92,10 +150,21 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
         if (item >= 2 * a.F) return;
         const bool fwd = item < a.F;
         const int F = a.order[item];
+        const int k = a.kk[F], n = a.nn[F], b0 = a.node_ptr[F], lq = a.ldq[F];
+        const T* q = Q + a.qoff[F];
+        // forward streams columns [k, n) (-A11^{-1} A12), backward all n
+        const int jbeg = fwd ? k : 0;
+        const int cpc = max(1, a.chunk_elems / lq);
+        const int nchunks = (n - jbeg + cpc - 1) / cpc;
+        const int issued = min(2, nchunks);
         if (tid == 0) {
             if (a.trace) {
                 a.trace[4 * item] = sm_id();
                 a.trace[4 * item + 1] = global_ns();
+            }
+            for (int c = 0; c < issued; ++c) {
+                const int j0 = jbeg + c * cpc, jn = min(cpc, n - j0);
+                bulk_load(buf[c], q + (long long)j0 * lq, (unsigned)(jn * lq * sizeof(T)), &mbar[c]);
             }
             bool ok = true;
             if (fwd) {
@@ -111,11 +180,12 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
             if (a.trace) a.trace[4 * item + 2] = global_ns();
         }
         __syncthreads();
-        if (!s_ok) return;
-        const int k = a.kk[F], n = a.nn[F], ld = n + k, b0 = a.node_ptr[F];
-        // extra rows of the augmented front: E[r][c] = Fr[(n + r) + c * ld],
-        // columns [k, n): -A11^{-1} A12, columns [n, n + k): -A11^{-1}
-        const T* E = pool + a.front_off[F] + n;
+        if (!s_ok) {
+            // drain the copies in flight (bounded) before leaving
+            for (int c = 0; c < issued; ++c) mbar_wait(&mbar[c], parity[c], a.err, a.spin_limit);
+            __syncthreads();
+            return;
+        }
         if (fwd) {
             // w = [b(own); 0] + children's update vectors
             for (int i = tid; i < n; i += blockDim.x) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
@@ -128,41 +198,60 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ p
                 for (int i = tid; i < m; i += blockDim.x) w[r[i]] += (T)__ldcg(&u[i]);
                 __syncthreads();
             }
-            // keep w1 = w(own) for the backward sweep; u = w2 - A21 A11^{-1} w1
+            // keep w1 = w(own) for the backward sweep
             for (int i = tid; i < k; i += blockDim.x) a.y[b0 + i] = (double)w[i];
-            double* u = a.upd + a.upd_off[F] - k;
-            for (int cc = k + warp; cc < n; cc += nwarp) {
-                const T* col = E + (long long)cc * ld;
-                T s = T(0);
-                for (int r = lane; r < k; r += 32) s += col[r] * w[r];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) u[cc] = (double)(w[cc] + s);
-            }
         } else {
-            // v = [-w1; x(border)], x(own) = A11^{-1} w1 - A11^{-1} A12 x2 = E v
+            // v = [-w1; x(border)]
             const int* idx = a.front_pos + a.front_ptr[F];
             for (int i = tid; i < n; i += blockDim.x)
                 w[i] = (i < k) ? -(T)__ldcg(&a.y[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
-            __syncthreads();
-            for (int r0 = 0; r0 < k; r0 += 32) {
-                const int r = r0 + lane;
-                T acc = T(0);
-                if (r < k)
-                    for (int j = warp; j < n; j += nwarp) {
-                        const int colj = (j < k) ? n + j : j;
-                        acc += E[(long long)colj * ld + r] * w[j];
+            for (int r = tid; r < k; r += blockDim.x) xs[r] = T(0);
+        }
+        __syncthreads();
+        double* u = a.upd + a.upd_off[F] - k;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            const bool good = mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
+            if (__syncthreads_or(!good)) {
+                // a copy did not complete within the budget: wait once more
+                // (bounded) for it and for the next one, then leave
+                mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
+                if (c + 1 < nchunks) mbar_wait(&mbar[b ^ 1], parity[b ^ 1], a.err, a.spin_limit);
+                __syncthreads();
+                return;
+            }
+            parity[b] ^= 1u;
+            const int j0 = jbeg + c * cpc, jn = min(cpc, n - j0);
+            const T* qb = buf[b];
+            {
+                if (fwd) {
+                    // u(j) = w(j) - (A21 A11^{-1} w1)(j) = w(j) + sum_r Q[r, j] w1[r]
+                    for (int jj = warp; jj < jn; jj += nwarp) {
+                        const T* col = qb + (long long)jj * lq;
+                        T s = T(0);
+                        for (int r = lane; r < k; r += 32) s += col[r] * w[r];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        if (lane == 0) u[j0 + jj] = (double)(w[j0 + jj] + s);
                     }
-                red[warp][lane] = acc;
-                __syncthreads();
-                if (warp == 0) {
-                    T sum = T(0);
-                    for (int q = 0; q < nwarp; ++q) sum += red[q][lane];
-                    if (r < k) a.y[b0 + r] = (double)sum;
+                } else {
+                    // x(own) += Q[:, j0:j0+jn] v[j0:j0+jn]
+                    for (int r = tid; r < k; r += blockDim.x) {
+                        T acc = xs[r];
+                        for (int jj = 0; jj < jn; ++jj) acc += qb[(long long)jj * lq + r] * w[j0 + jj];
+                        xs[r] = acc;
+                    }
                 }
-                __syncthreads();
+            }
+            __syncthreads();
+            if (tid == 0 && c + 2 < nchunks) {
+                fence_proxy_async();
+                const int j2 = jbeg + (c + 2) * cpc, jn2 = min(cpc, n - j2);
+                bulk_load(buf[b], q + (long long)j2 * lq, (unsigned)(jn2 * lq * sizeof(T)), &mbar[b]);
             }
         }
+        if (!fwd)
+            for (int r = tid; r < k; r += blockDim.x) a.y[b0 + r] = (double)xs[r];
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -254,29 +343,32 @@ __global__ void norm2_partial_kernel(long long N, const double* __restrict__ a, 
 }
 
 template <typename T>
-static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
+static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
-    // algorithmic bytes: every factor entry read twice (forward, backward),
-    // the vector read and written in each sweep
     // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
     // and the vector read and written in each sweep
     PhaseScope scope(c, PH_SOLVE, (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
-    int max_n = 0;
-    for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
-    const size_t smem = (size_t)max_n * sizeof(T);
+    int max_n = 0, max_k = 0, max_ldq = 0;
+    for (int f = 0; f < S.n_nodes; ++f) {
+        max_n = std::max(max_n, S.n[f]);
+        max_k = std::max(max_k, S.k[f]);
+        max_ldq = std::max(max_ldq, S.ldq[f]);
+    }
+    int chunk = (int)(32768 / sizeof(T));
+    chunk = std::max(chunk, max_ldq);
+    chunk = (chunk + 3) / 4 * 4;
+    const size_t smem = (2 * (size_t)chunk + max_n + max_k + 8) * sizeof(T);
     int maxopt = 0, nsm = 0, per_sm = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    if (smem + 8 * 33 * sizeof(T) + 64 > (size_t)maxopt)
-        return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
+    if (smem + 256 > (size_t)maxopt) return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
     if (smem > 48 * 1024)
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tree_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_solve_kernel<T>, 256, smem));
     const int grid = std::max(1, std::min(2 * S.n_nodes, std::max(1, per_sm) * nsm));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_counter.ptr, 0, sizeof(int), st));
     TreeArgs a;
-    a.front_off = c->front_off.ptr;
     a.node_ptr = c->node_ptr.ptr;
     a.kk = c->kk.ptr;
     a.nn = c->nn.ptr;
@@ -288,9 +380,13 @@ static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     a.upd_off = c->upd_off.ptr;
     a.front_ptr = c->front_ptr.ptr;
     a.front_pos = c->front_pos.ptr;
-    a.D = c->D.ptr;
+    a.ldq = c->ldq.ptr;
+    a.qoff = c->qoff.ptr;
     a.order = c->solve_order.ptr;
     a.F = S.n_nodes;
+    a.chunk_elems = chunk;
+    a.max_n = max_n;
+    a.max_k = max_k;
     a.upd = c->upd.ptr;
     a.y = y;
     a.flags = c->solve_flags.ptr;
@@ -299,7 +395,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* pool, double* y) {
     a.epoch = ++c->solve_epoch;
     a.spin_limit = c->wait_limit;
     a.trace = c->trace_buf;
-    { count_launch(c); tree_solve_kernel<T><<<grid, 256, smem, st>>>(pool, a); }
+    { count_launch(c); tree_solve_kernel<T><<<grid, 256, smem, st>>>(Q, a); }
     return RIGA_OK;
 }
 
@@ -315,8 +411,8 @@ int enqueue_solve(riga_ctx* c, double* y) {
     }
     RIGA_CUDA_TRY(c, c->solve_counter.alloc(1));
     int rc;
-    if (c->precision == RIGA_FP64) rc = enqueue_solve_t<double>(c, c->pool64.ptr, y);
-    else rc = enqueue_solve_t<float>(c, c->pool32.ptr, y);
+    if (c->precision == RIGA_FP64) rc = enqueue_solve_t<double>(c, c->q64.ptr, y);
+    else rc = enqueue_solve_t<float>(c, c->q32.ptr, y);
     if (rc) return rc;
     RIGA_CUDA_TRY(c, cudaGetLastError());
     c->stats.n_solve++;

@@ -334,6 +334,16 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
     S.rel_ptr[F] = (long long)S.rel.size();
     S.upd_size = S.upd_off[F];
 
+    S.ldq.assign(F, 0);
+    S.qoff.assign(F + 1, 0);
+    S.qitems.clear();
+    for (int f = 0; f < F; ++f) {
+        S.ldq[f] = (S.k[f] + 3) / 4 * 4;
+        S.qoff[f + 1] = S.qoff[f] + (long long)S.ldq[f] * S.n[f];
+        for (int j0 = 0; j0 < S.n[f]; j0 += 32) S.qitems.push_back({f, j0});
+    }
+    S.q_size = S.qoff[F];
+
     // heights and counts
     S.height.assign(F, 0);
     int maxh = 0;

@@ -79,6 +79,13 @@ struct Symbolic {
     std::vector<int> rel;             // extend-add: local index in parent, per border entry
     std::vector<long long> rel_ptr;   // rel of node F at rel_ptr[F] (length n_F - k_F)
     std::vector<long long> upd_off;   // solve update vector offsets (length n_F - k_F)
+    // packed solve operators: per front a column-major ldq_F x n_F block
+    // (ldq_F = k_F rounded up to 4, zero padded), columns [0,k): -A11^{-1},
+    // columns [k,n): -A11^{-1} A12; offsets 16-byte aligned for bulk copies
+    std::vector<int> ldq;
+    std::vector<long long> qoff;
+    long long q_size = 0;
+    std::vector<PanelItem> qitems;    // pack work: (front, first column) per 32 columns
     long long upd_size = 0;
 
     // factorization schedule
