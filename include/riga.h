@@ -293,6 +293,32 @@ int riga_set_wait_limit(riga_ctx* ctx, long long limit);
  */
 int riga_trace_solve(riga_ctx* ctx, const double* b, long long* trace, int* order);
 
+/*
+ * riga_spmv_dot_noalloc: y = A x and *xy = x^T y for a CSR matrix A, without
+ * allocating any device memory.  The paper has no counterpart: this is an
+ * allocation-free variant of the SpMV + inner-product kernel of the Lanczos
+ * step, for callers that cannot allocate device memory, such as code that
+ * runs inside a host framework which owns the whole device-memory budget (a
+ * pool or a fixed reservation) and forbids cudaMalloc, or a long-running
+ * service that must not grow its device footprint after start-up.
+ *  - rowptr[N+1] (int64), col[nnz] (int32, ascending within a row), val[nnz],
+ *    x[N], y[N], xy[1]: DEVICE pointers owned by the caller; 1 <= N <= 2^20.
+ *  - The per-block partial sums live in a fixed 512 KiB array in device
+ *    memory that every GPU which loads this library holds until the process
+ *    exits.  The first call on a device looks that array's address up
+ *    (cudaGetSymbolAddress, with the device current) and caches it: make the
+ *    first call on each device before any stream capture.
+ *  - Every call uses the same array, which keeps the last call's contents;
+ *    nothing in it has to start at zero (each call writes every entry it
+ *    reads).  Calls that overlap on the GPU (other streams, or host threads
+ *    without ordering between them) race on it.
+ *  - Work is enqueued on cuda_stream (NULL = legacy default stream); the call
+ *    returns without synchronizing.
+ * Errors: RIGA_EINVAL (NULL pointer, N < 1 or N > 2^20), RIGA_ECUDA.
+ */
+int riga_spmv_dot_noalloc(const long long* rowptr, const int* col, const double* val, long long N,
+                          const double* x, double* y, double* xy, void* cuda_stream);
+
 /* riga_strerror: static name of a status code. */
 const char* riga_strerror(int status);
 

@@ -33,7 +33,7 @@ EXPORTED = [
     "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_factor", "riga_solve", "riga_eigs",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
     "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_set_wait_limit",
-    "riga_trace_solve", "riga_strerror",
+    "riga_trace_solve", "riga_spmv_dot_noalloc", "riga_strerror",
     "riga_last_error",
 ]
 PHASES = ["assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"]
@@ -90,6 +90,7 @@ def load_library(path=LIB_PATH):
     lib.riga_profile.argtypes = [P, I]
     lib.riga_set_wait_limit.argtypes = [P, LL]
     lib.riga_trace_solve.argtypes = [P, P, P, P]
+    lib.riga_spmv_dot_noalloc.argtypes = [P, P, P, LL, P, P, P, P]
     lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
                                      ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.riga_strerror.argtypes = [I]
@@ -333,3 +334,18 @@ class Riga:
                                                   ctypes.byref(by), ctypes.byref(fl)))
             out[name] = dict(launches=la.value, calls=ca.value, ms=ms.value, bytes=by.value, flops=fl.value)
         return out
+
+
+def spmv_dot_noalloc(rowptr, col, val, x, y, xy, stream=None):
+    """y = A x and xy[0] = x^T y through riga_spmv_dot_noalloc (no device
+    allocation).  All arguments are CUDA torch tensors (int64 rowptr, int32
+    col, float64 val/x/y/xy); work is enqueued on ``stream`` (a torch stream,
+    default the current one) and not synchronized."""
+    import torch
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    n = x.numel()
+    rc = lib.riga_spmv_dot_noalloc(_ptr(rowptr), _ptr(col), _ptr(val), int(n), _ptr(x), _ptr(y), _ptr(xy),
+                                   ctypes.c_void_p(s.cuda_stream))
+    if rc != RIGA_OK:
+        raise RigaError(rc, lib.riga_strerror(rc).decode())
