@@ -282,16 +282,17 @@ int riga_set_wait_limit(riga_ctx* ctx, long long limit);
 
 /*
  * riga_trace_solve: one forward/backward elimination of b (as riga_solve with
- * tol = 0, FP64 or FP32 factor, no refinement) that also records, for each of
- * the 2 n_nodes work items of the persistent tree solve (forward items in
- * ascending tree height, then backward items in descending height), four
+ * tol = 0, FP64 or FP32 factor, no refinement) that also records, for each
+ * work item of the persistent tree solve (forward parts in ascending tree
+ * height, then backward parts in descending height; *n_items of them), four
  * int64 values in trace[4*item ..]: the SM that ran it, the global-timer
  * nanoseconds when it was claimed, when its dependencies were satisfied, and
- * when it completed.  trace: host array of 8 n_nodes int64; order (may be
- * NULL): host array of 2 n_nodes ints receiving the node of each item.
+ * when it completed.  Call with trace = NULL first to get *n_items.
+ * trace: host array of 4 *n_items int64; order (may be NULL): host array of
+ * *n_items ints receiving the node of each item.
  * Errors: RIGA_ESTATE, RIGA_ETIMEOUT, RIGA_ECUDA.
  */
-int riga_trace_solve(riga_ctx* ctx, const double* b, long long* trace, int* order);
+int riga_trace_solve(riga_ctx* ctx, const double* b, int* n_items, long long* trace, int* order);
 
 /*
  * riga_spmv_dot_noalloc: y = A x and *xy = x^T y for a CSR matrix A, without

@@ -70,8 +70,9 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->scatter.upload(S.scatter, st));
     RIGA_CUDA_TRY(c, c->perm_to_glob.upload(S.perm_to_glob, st));
     RIGA_CUDA_TRY(c, c->glob_rowptr.upload(S.glob_rowptr, st));
-    RIGA_CUDA_TRY(c, c->ldq.upload(S.ldq, st));
-    RIGA_CUDA_TRY(c, c->qoff.upload(S.qoff, st));
+    RIGA_CUDA_TRY(c, c->sitems.upload(S.sitems, st));
+    RIGA_CUDA_TRY(c, c->parts_f.upload(S.parts_f, st));
+    RIGA_CUDA_TRY(c, c->parts_b.upload(S.parts_b, st));
     RIGA_CUDA_TRY(c, c->qitems.upload(S.qitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.qitems, st));
     std::vector<int> ln;
     c->level_nodes_off.assign(S.n_levels + 1, 0);
@@ -81,10 +82,9 @@ int upload_symbolic(riga_ctx* c) {
     }
     c->level_nodes_off[S.n_levels] = (int)ln.size();
     RIGA_CUDA_TRY(c, c->level_nodes.upload(ln, st));
-    // persistent-solve work order: forward by ascending height, backward by descending
-    std::vector<int> order(ln);
-    for (int l = S.n_levels - 1; l >= 0; --l)
-        for (int f : S.levels[l].nodes) order.push_back(f);
+    // front of each persistent-solve work item (for traces)
+    std::vector<int> order;
+    for (const SolveItem& it : S.sitems) order.push_back(it.front);
     RIGA_CUDA_TRY(c, c->solve_order.upload(order, st));
     c->solve_flags.release();
     RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
@@ -626,15 +626,17 @@ int riga_set_wait_limit(riga_ctx* c, long long limit) {
     return RIGA_OK;
 }
 
-int riga_trace_solve(riga_ctx* c, const double* b, long long* trace, int* order) {
-    if (!c || !b || !trace) return RIGA_EINVAL;
+int riga_trace_solve(riga_ctx* c, const double* b, int* n_items, long long* trace, int* order) {
+    if (!c || !b || !n_items) return RIGA_EINVAL;
     c->last_error.clear();
     if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
     cudaSetDevice(c->device);
     if (!c->factored) return set_error(c, RIGA_ESTATE, "riga_factor first");
     const Symbolic& S = c->S;
+    *n_items = (int)S.sitems.size();
+    if (!trace) return RIGA_OK;
     const long long N = S.N;
-    const size_t nt = 8 * (size_t)S.n_nodes;
+    const size_t nt = 4 * S.sitems.size();
     DevBuf<long long> tb;
     RIGA_CUDA_TRY(c, tb.alloc(nt));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(tb.ptr, 0, nt * sizeof(long long), c->stream));
@@ -649,7 +651,7 @@ int riga_trace_solve(riga_ctx* c, const double* b, long long* trace, int* order)
     int dflag = 0;
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(trace, tb.ptr, nt * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    if (order) RIGA_CUDA_TRY(c, cudaMemcpyAsync(order, c->solve_order.ptr, 2 * (size_t)S.n_nodes * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (order) RIGA_CUDA_TRY(c, cudaMemcpyAsync(order, c->solve_order.ptr, S.sitems.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (dflag & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
     return RIGA_OK;

@@ -77,8 +77,8 @@ struct riga_ctx {
     std::vector<double> coefK, coefM;  // host copies (empty = constant)
 
     // symbolic arrays on the device
-    riga::DevBuf<long long> qoff;
-    riga::DevBuf<int> ldq;
+    riga::DevBuf<riga::SolveItem> sitems;
+    riga::DevBuf<int> parts_f, parts_b;
     riga::DevBuf<riga::PanelItem> qitems;
     riga::DevBuf<long long> rowptr, front_off, front_ptr, rel_ptr, upd_off, scatter, perm_to_glob, glob_rowptr;
     riga::DevBuf<int> col, perm, ipos, node_ptr, kk, nn, front_pos, child_ptr, child_list, rel, level_nodes, parent;
@@ -109,7 +109,8 @@ struct riga_ctx {
     // ---------------------------------------------------------------- solve
     riga::DevBuf<double> upd;          // forward-solve update vectors
     riga::DevBuf<int> solve_order;     // 2F work items of the persistent solve
-    riga::DevBuf<int> solve_flags;     // per-front done flags (epoch-valued)
+    riga::DevBuf<int> solve_flags;     // per-front completed parts, forward then backward
+    riga::DevBuf<double> w1buf;        // assembled own right-hand sides of the forward sweep
     riga::DevBuf<int> solve_counter;   // work counter of the persistent solve
     int solve_epoch = 0;
     long long wait_limit = 1LL << 24;  // device dependency-wait budget (polls)

@@ -195,22 +195,35 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
     }
 }
 
-// Q[qoff + j*ldq + r] = extra-row entry (n + r, col_j) of the front, col_j =
-// n + j for j < k (-A11^{-1}), j for j >= k (-A11^{-1} A12); rows k..ldq zero.
+// Packs the solve operators from the extra rows E (rows n..n+k of the
+// augmented front) into the panels of the solve items:
+//   forward item  (columns [lo,hi) of k..n): row-major k x ldp, P[r*ldp + j-lo] = E[r][j];
+//   backward item (rows [lo,hi) of 0..k):    column-major ldp x n,
+//                 P[jq*ldp + r-lo] = E[r][col(jq)], col(jq) = n + jq (jq < k), jq (jq >= k).
+// Padding entries are zero.
 template <typename T>
-__global__ void pack_q_kernel(const PanelItem* __restrict__ items, const int* __restrict__ kk,
-                              const int* __restrict__ nn, const long long* __restrict__ front_off,
-                              const int* __restrict__ ldq, const long long* __restrict__ qoff,
-                              const T* __restrict__ pool, T* __restrict__ Q) {
-    const PanelItem it = items[blockIdx.x];
-    const int F = it.front, k = kk[F], n = nn[F], ld = n + k, lq = ldq[F];
+__global__ void pack_q_kernel(const PanelItem* __restrict__ qitems, const SolveItem* __restrict__ sitems, int n_fwd,
+                              const int* __restrict__ kk, const int* __restrict__ nn,
+                              const long long* __restrict__ front_off, const T* __restrict__ pool,
+                              T* __restrict__ Q) {
+    const PanelItem pi = qitems[blockIdx.x];
+    const SolveItem it = sitems[pi.front];
+    const bool fwd = pi.front < n_fwd;
+    const int F = it.front, k = kk[F], n = nn[F], ld = n + k;
     const T* E = pool + front_off[F] + n;
-    T* q = Q + qoff[F];
-    const int j1 = min(n, it.r0 + 32);
-    for (int j = it.r0; j < j1; ++j) {
-        const int col = (j < k) ? n + j : j;
-        for (int r = threadIdx.x; r < lq; r += blockDim.x)
-            q[(long long)j * lq + r] = (r < k) ? E[(long long)col * ld + r] : T(0);
+    T* q = Q + it.off;
+    const long long cnt = (long long)it.ldp * (fwd ? k : n);
+    const long long e1 = min(cnt, (long long)pi.r0 + 4096);
+    for (long long e = pi.r0 + threadIdx.x; e < e1; e += blockDim.x) {
+        T v = T(0);
+        if (fwd) {
+            const int r = (int)(e / it.ldp), j = it.lo + (int)(e % it.ldp);
+            if (j < it.hi) v = E[(long long)j * ld + r];
+        } else {
+            const int jq = (int)(e / it.ldp), r = it.lo + (int)(e % it.ldp);
+            if (r < it.hi) v = E[(long long)(jq < k ? n + jq : jq) * ld + r];
+        }
+        q[e] = v;
     }
 }
 
@@ -263,9 +276,9 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
         }
     }
     if (!S.qitems.empty())
-        { count_launch(c); pack_q_kernel<T><<<(unsigned)S.qitems.size(), 128, 0, st>>>(c->qitems.ptr, c->kk.ptr, c->nn.ptr,
-                                                                                      c->front_off.ptr, c->ldq.ptr,
-                                                                                      c->qoff.ptr, pool, Q); }
+        { count_launch(c); pack_q_kernel<T><<<(unsigned)S.qitems.size(), 256, 0, st>>>(c->qitems.ptr, c->sitems.ptr, S.n_fwd_items,
+                                                                                      c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                                                                      pool, Q); }
     { count_launch(c); inertia_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->neg.ptr); }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     return RIGA_OK;

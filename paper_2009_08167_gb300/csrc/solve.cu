@@ -2,9 +2,10 @@
 // (Sec. 4.2: one f/b elimination and the M mat-vecs per Lanczos step;
 // Sec. 5.1 Eq. flopsFb).  Vectors are in elimination order.
 //
-// tree_solve_kernel: one persistent launch per solve, one CTA per front at a
-// time, fronts taken in dependency order (forward leaves to root, then
-// backward root to leaves) with bounded waits on per-front done flags.
+// tree_solve_kernel: one persistent launch per solve; work items (parts of a
+// front's forward or backward sweep) are taken in dependency order (forward
+// leaves to root, then backward root to leaves) with bounded waits on
+// per-front completed-part counters.
 // The factorization leaves in each augmented front's extra rows the block
 // elimination operators of the front, -A11^{-1} A12 and -A11^{-1}, so that
 // the forward/backward elimination of Sec. 4.2 (L y = b, D, L^T x = z) is,
@@ -37,18 +38,19 @@ struct TreeArgs {
     const long long* upd_off;
     const long long* front_ptr;
     const int* front_pos;
-    const int* ldq;
-    const long long* qoff;
-    const int* order;  // 2F work items: forward sweep (ascending height), then backward (descending)
-    int F;
+    const int* parts_f;
+    const int* parts_b;
+    const SolveItem* items;  // forward parts (ascending height), then backward parts
+    int n_items, n_fwd;
     int chunk_elems;   // elements per shared-memory chunk buffer (two buffers)
-    int max_n, max_k;
+    int max_n;
     double* upd;
     double* y;
-    int* flags;        // [0,F) forward done, [F,2F) backward done: equal to epoch when done
+    double* w1;        // assembled own right-hand sides (forward -> backward)
+    int* done_f;       // completed forward parts per front (zeroed before the launch)
+    int* done_b;       // completed backward parts per front
     int* counter;      // next work item (zeroed before the launch)
     int* err;          // bit 1: a dependency or copy wait gave up
-    int epoch;
     long long spin_limit;  // polls (64 ns back-off each) before a wait gives up
     long long* trace;      // optional: per item {sm, claim ns, deps-ready ns, done ns}
 };
@@ -65,9 +67,9 @@ __device__ __forceinline__ int sm_id() {
     return id;
 }
 
-__device__ __forceinline__ bool wait_flag(const int* f, int epoch, int* err, long long limit) {
+__device__ __forceinline__ bool wait_count(const int* f, int target, int* err, long long limit) {
     long long it = 0;
-    while (*(volatile const int*)f != epoch) {
+    while (*(volatile const int*)f < target) {
         if (++it > limit) {
             atomicOr(err, 2);
             return false;
@@ -120,22 +122,28 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 
 // One persistent launch per solve.  CTAs claim work items in order from a
 // global counter; an item waits (bounded) until its dependencies are done:
-// forward: the children's forward items; backward: its own forward item and
-// the parent's backward item.  Dependencies always have lower item indices,
-// so they were claimed by CTAs that are already running: no deadlock.
-// The item's operator block streams through two shared-memory buffers by
-// bulk copies issued before the dependency wait.
+// forward part: every forward part of every child; backward part: every
+// forward part of its own front and every backward part of the parent.
+// Dependencies always have lower item indices, so they were claimed by CTAs
+// that are already running: no deadlock.  The item's operator panel streams
+// through two shared-memory buffers by bulk copies issued before the
+// dependency wait.  A forward part owns border columns [lo,hi): u(j) =
+// w(j) + sum_r P[r][j] w1(r); a backward part owns rows [lo,hi) of the front's
+// own variables: x(r) = sum_j P[j][r] v(j), v = [-w1; x(border)].  Both are
+// the same loop: stream units (forward: rows r; backward: columns j) times a
+// multiplier (w1(r), v(j)) accumulated into the part's outputs; threads split
+// the outputs and interleave the units, then reduce through shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* buf[2];
     buf[0] = reinterpret_cast<T*>(smem_raw);
     buf[1] = buf[0] + a.chunk_elems;
-    T* w = buf[1] + a.chunk_elems;  // local vector (n)
-    T* xs = w + a.max_n;            // backward accumulators (k)
+    T* w = buf[1] + a.chunk_elems;  // front vector (n)
+    T* red = w + a.max_n;           // 256 partial sums
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_item, s_ok;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     unsigned parity[2] = {0u, 0u};
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
@@ -147,15 +155,15 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
         __syncthreads();
         const int item = s_item;
-        if (item >= 2 * a.F) return;
-        const bool fwd = item < a.F;
-        const int F = a.order[item];
-        const int k = a.kk[F], n = a.nn[F], b0 = a.node_ptr[F], lq = a.ldq[F];
-        const T* q = Q + a.qoff[F];
-        // forward streams columns [k, n) (-A11^{-1} A12), backward all n
-        const int jbeg = fwd ? k : 0;
-        const int cpc = max(1, a.chunk_elems / lq);
-        const int nchunks = (n - jbeg + cpc - 1) / cpc;
+        if (item >= a.n_items) return;
+        const SolveItem it = a.items[item];
+        const bool fwd = item < a.n_fwd;
+        const int F = it.front, k = a.kk[F], n = a.nn[F], b0 = a.node_ptr[F];
+        const int lo = it.lo, cnt = it.hi - it.lo, ldp = it.ldp;
+        const T* q = Q + it.off;
+        const int units = fwd ? k : n;          // rows (forward) or columns (backward) of the panel
+        const int upc = max(1, a.chunk_elems / ldp);
+        const int nchunks = (cnt > 0) ? (units + upc - 1) / upc : 0;
         const int issued = min(2, nchunks);
         if (tid == 0) {
             if (a.trace) {
@@ -163,17 +171,19 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
                 a.trace[4 * item + 1] = global_ns();
             }
             for (int c = 0; c < issued; ++c) {
-                const int j0 = jbeg + c * cpc, jn = min(cpc, n - j0);
-                bulk_load(buf[c], q + (long long)j0 * lq, (unsigned)(jn * lq * sizeof(T)), &mbar[c]);
+                const int ua = c * upc, un = min(upc, units - ua);
+                bulk_load(buf[c], q + (long long)ua * ldp, (unsigned)(un * ldp * sizeof(T)), &mbar[c]);
             }
             bool ok = true;
             if (fwd) {
-                for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1] && ok; ++ci)
-                    ok = wait_flag(&a.flags[a.child_list[ci]], a.epoch, a.err, a.spin_limit);
+                for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1] && ok; ++ci) {
+                    const int ch = a.child_list[ci];
+                    ok = wait_count(&a.done_f[ch], a.parts_f[ch], a.err, a.spin_limit);
+                }
             } else {
-                ok = wait_flag(&a.flags[F], a.epoch, a.err, a.spin_limit);
+                ok = wait_count(&a.done_f[F], a.parts_f[F], a.err, a.spin_limit);
                 const int par = a.parent[F];
-                if (ok && par >= 0) ok = wait_flag(&a.flags[a.F + par], a.epoch, a.err, a.spin_limit);
+                if (ok && par >= 0) ok = wait_count(&a.done_b[par], a.parts_b[par], a.err, a.spin_limit);
             }
             __threadfence();
             s_ok = ok;
@@ -198,17 +208,23 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
                 for (int i = tid; i < m; i += blockDim.x) w[r[i]] += (T)__ldcg(&u[i]);
                 __syncthreads();
             }
-            // keep w1 = w(own) for the backward sweep
-            for (int i = tid; i < k; i += blockDim.x) a.y[b0 + i] = (double)w[i];
+            if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
+                for (int i = tid; i < k; i += blockDim.x) a.w1[b0 + i] = (double)w[i];
         } else {
-            // v = [-w1; x(border)]
             const int* idx = a.front_pos + a.front_ptr[F];
             for (int i = tid; i < n; i += blockDim.x)
-                w[i] = (i < k) ? -(T)__ldcg(&a.y[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
-            for (int r = tid; r < k; r += blockDim.x) xs[r] = T(0);
+                w[i] = (i < k) ? -(T)__ldcg(&a.w1[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
         }
         __syncthreads();
-        double* u = a.upd + a.upd_off[F] - k;
+        // thread layout: outputs l (columns or rows of the part) x unit groups g
+        const int cp = max(1, min(cnt, 256));
+        const int G = max(1, 256 / cp);
+        const int li = tid % cp, g = tid / cp;
+        const bool active = cnt > 0 && g < G;
+        const int na = (cnt + 255) / 256;  // outputs per thread when cnt > 256 (G = 1)
+        T acc[8];
+#pragma unroll
+        for (int q2 = 0; q2 < 8; ++q2) acc[q2] = T(0);
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             const bool good = mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
@@ -221,41 +237,55 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
                 return;
             }
             parity[b] ^= 1u;
-            const int j0 = jbeg + c * cpc, jn = min(cpc, n - j0);
-            const T* qb = buf[b];
-            {
-                if (fwd) {
-                    // u(j) = w(j) - (A21 A11^{-1} w1)(j) = w(j) + sum_r Q[r, j] w1[r]
-                    for (int jj = warp; jj < jn; jj += nwarp) {
-                        const T* col = qb + (long long)jj * lq;
-                        T s = T(0);
-                        for (int r = lane; r < k; r += 32) s += col[r] * w[r];
+            const int ua = c * upc, ub = min(units, ua + upc);
+            const T* P = buf[b];
+            if (active) {
+                for (int u = ua + g; u < ub; u += G) {
+                    const T* row = P + (long long)(u - ua) * ldp;
+                    const T x = w[u];
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if (lane == 0) u[j0 + jj] = (double)(w[j0 + jj] + s);
-                    }
-                } else {
-                    // x(own) += Q[:, j0:j0+jn] v[j0:j0+jn]
-                    for (int r = tid; r < k; r += blockDim.x) {
-                        T acc = xs[r];
-                        for (int jj = 0; jj < jn; ++jj) acc += qb[(long long)jj * lq + r] * w[j0 + jj];
-                        xs[r] = acc;
+                    for (int q2 = 0; q2 < 8; ++q2) {
+                        const int l = li + q2 * 256;
+                        if (q2 < na && l < cnt) acc[q2] += row[l] * x;
                     }
                 }
             }
             __syncthreads();
             if (tid == 0 && c + 2 < nchunks) {
                 fence_proxy_async();
-                const int j2 = jbeg + (c + 2) * cpc, jn2 = min(cpc, n - j2);
-                bulk_load(buf[b], q + (long long)j2 * lq, (unsigned)(jn2 * lq * sizeof(T)), &mbar[b]);
+                const int u2 = (c + 2) * upc, un2 = min(upc, units - u2);
+                bulk_load(buf[b], q + (long long)u2 * ldp, (unsigned)(un2 * ldp * sizeof(T)), &mbar[b]);
             }
         }
-        if (!fwd)
-            for (int r = tid; r < k; r += blockDim.x) a.y[b0 + r] = (double)xs[r];
+        if (cnt > 0) {
+            if (G > 1) {
+                if (active) red[g * cp + li] = acc[0];
+                __syncthreads();
+                if (g == 0 && li < cnt) {
+                    T s = T(0);
+                    for (int g2 = 0; g2 < G; ++g2) s += red[g2 * cp + li];
+                    acc[0] = s;
+                }
+            }
+            if (g == 0) {
+#pragma unroll
+                for (int q2 = 0; q2 < 8; ++q2) {
+                    const int l = li + q2 * 256;
+                    if (q2 < na && l < cnt) {
+                        if (fwd) {
+                            const int j = lo + l;
+                            a.upd[a.upd_off[F] + j - k] = (double)(w[j] + acc[q2]);
+                        } else {
+                            a.y[b0 + lo + l] = (double)acc[q2];
+                        }
+                    }
+                }
+            }
+        }
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            atomicExch(&a.flags[fwd ? F : a.F + F], a.epoch);
+            atomicAdd(fwd ? &a.done_f[F] : &a.done_b[F], 1);
             if (a.trace) a.trace[4 * item + 3] = global_ns();
         }
     }
@@ -349,16 +379,13 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
     // and the vector read and written in each sweep
     PhaseScope scope(c, PH_SOLVE, (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
-    int max_n = 0, max_k = 0, max_ldq = 0;
-    for (int f = 0; f < S.n_nodes; ++f) {
-        max_n = std::max(max_n, S.n[f]);
-        max_k = std::max(max_k, S.k[f]);
-        max_ldq = std::max(max_ldq, S.ldq[f]);
-    }
+    int max_n = 0, max_ldp = 0;
+    for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
+    for (const SolveItem& it : S.sitems) max_ldp = std::max(max_ldp, it.ldp);
     int chunk = (int)(32768 / sizeof(T));
-    chunk = std::max(chunk, max_ldq);
+    chunk = std::max(chunk, max_ldp);
     chunk = (chunk + 3) / 4 * 4;
-    const size_t smem = (2 * (size_t)chunk + max_n + max_k + 8) * sizeof(T);
+    const size_t smem = (2 * (size_t)chunk + max_n + 256 + 8) * sizeof(T);
     int maxopt = 0, nsm = 0, per_sm = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
@@ -366,8 +393,9 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     if (smem > 48 * 1024)
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tree_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_solve_kernel<T>, 256, smem));
-    const int grid = std::max(1, std::min(2 * S.n_nodes, std::max(1, per_sm) * nsm));
-    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_counter.ptr, 0, sizeof(int), st));
+    const int n_items = (int)S.sitems.size();
+    const int grid = std::max(1, std::min(n_items, std::max(1, per_sm) * nsm));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, (2 * (size_t)S.n_nodes + 1) * sizeof(int), st));
     TreeArgs a;
     a.node_ptr = c->node_ptr.ptr;
     a.kk = c->kk.ptr;
@@ -380,19 +408,20 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     a.upd_off = c->upd_off.ptr;
     a.front_ptr = c->front_ptr.ptr;
     a.front_pos = c->front_pos.ptr;
-    a.ldq = c->ldq.ptr;
-    a.qoff = c->qoff.ptr;
-    a.order = c->solve_order.ptr;
-    a.F = S.n_nodes;
+    a.parts_f = c->parts_f.ptr;
+    a.parts_b = c->parts_b.ptr;
+    a.items = c->sitems.ptr;
+    a.n_items = n_items;
+    a.n_fwd = S.n_fwd_items;
     a.chunk_elems = chunk;
     a.max_n = max_n;
-    a.max_k = max_k;
     a.upd = c->upd.ptr;
     a.y = y;
-    a.flags = c->solve_flags.ptr;
-    a.counter = c->solve_counter.ptr;
+    a.w1 = c->w1buf.ptr;
+    a.done_f = c->solve_flags.ptr;
+    a.done_b = c->solve_flags.ptr + S.n_nodes;
+    a.counter = c->solve_flags.ptr + 2 * S.n_nodes;
     a.err = c->flag.ptr;
-    a.epoch = ++c->solve_epoch;
     a.spin_limit = c->wait_limit;
     a.trace = c->trace_buf;
     { count_launch(c); tree_solve_kernel<T><<<grid, 256, smem, st>>>(Q, a); }
@@ -403,13 +432,8 @@ int enqueue_solve(riga_ctx* c, double* y) {
     if (!c->factored) return set_error(c, RIGA_ESTATE, "no factorization");
     Symbolic& S = c->S;
     RIGA_CUDA_TRY(c, c->upd.alloc(S.upd_size > 0 ? S.upd_size : 1));
-    if (c->solve_flags.count < (size_t)(2 * S.n_nodes)) {
-        c->solve_flags.release();
-        RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes));
-        RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, 2 * (size_t)S.n_nodes * sizeof(int), c->stream));
-        c->solve_epoch = 0;
-    }
-    RIGA_CUDA_TRY(c, c->solve_counter.alloc(1));
+    RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes + 1));
+    RIGA_CUDA_TRY(c, c->w1buf.alloc(S.N));
     int rc;
     if (c->precision == RIGA_FP64) rc = enqueue_solve_t<double>(c, c->q64.ptr, y);
     else rc = enqueue_solve_t<float>(c, c->q32.ptr, y);

@@ -334,15 +334,7 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
     S.rel_ptr[F] = (long long)S.rel.size();
     S.upd_size = S.upd_off[F];
 
-    S.ldq.assign(F, 0);
-    S.qoff.assign(F + 1, 0);
-    S.qitems.clear();
-    for (int f = 0; f < F; ++f) {
-        S.ldq[f] = (S.k[f] + 3) / 4 * 4;
-        S.qoff[f + 1] = S.qoff[f] + (long long)S.ldq[f] * S.n[f];
-        for (int j0 = 0; j0 < S.n[f]; j0 += 32) S.qitems.push_back({f, j0});
-    }
-    S.q_size = S.qoff[F];
+    // (solve items are built after the heights, below)
 
     // heights and counts
     S.height.assign(F, 0);
@@ -369,6 +361,57 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
             S.flops += (double)(nn - i) * (double)(nn - i - 1);
             S.flops_aug += (double)(nn + kk - i) * (double)(nn + kk - i - 1) - (double)(nn - i) * (double)(nn - i - 1);
         }
+    }
+
+    // ------------------------------------------------------- solve items
+    // parts of about SOLVE_PART_FMA multiply-adds each (up to 32 per sweep)
+    const long long SOLVE_PART_FMA = 12288;
+    S.parts_f.assign(F, 1);
+    S.parts_b.assign(F, 1);
+    for (int f = 0; f < F; ++f) {
+        const long long kk = S.k[f], mm = S.n[f] - S.k[f], nn = S.n[f];
+        long long pf = (kk * mm + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
+        pf = std::max(1LL, std::min({pf, 32LL, std::max(1LL, mm)}));
+        pf = std::max(pf, (mm + 2047) / 2048);  // at most 2048 columns per part
+        long long pb = (kk * nn + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
+        pb = std::max(1LL, std::min({pb, 32LL, std::max(1LL, kk / 8)}));
+        pb = std::max(pb, (kk + 2047) / 2048);  // at most 2048 rows per part
+        if (pf > 64 || pb > 64) return "front too large for the tree solve";
+        S.parts_f[f] = (int)pf;
+        S.parts_b[f] = (int)pb;
+    }
+    {
+        std::vector<int> byh(F);
+        for (int f = 0; f < F; ++f) byh[f] = f;
+        std::stable_sort(byh.begin(), byh.end(), [&](int a, int b) { return S.height[a] < S.height[b]; });
+        S.sitems.clear();
+        S.qitems.clear();
+        long long off = 0;
+        auto add = [&](int f, int lo, int hi, long long elems_per_ld_unit, bool) {
+            SolveItem it;
+            it.front = f;
+            it.lo = lo;
+            it.hi = hi;
+            it.ldp = std::max(4, (hi - lo + 3) / 4 * 4);
+            it.off = off;
+            const long long cnt = (long long)it.ldp * elems_per_ld_unit;
+            const int idx = (int)S.sitems.size();
+            for (long long e0 = 0; e0 < cnt; e0 += 4096) S.qitems.push_back({idx, (int)e0});
+            off += cnt;
+            S.sitems.push_back(it);
+        };
+        for (int f : byh) {  // forward, ascending height
+            const int kk = S.k[f], mm = S.n[f] - S.k[f], P = S.parts_f[f];
+            for (int q = 0; q < P; ++q)
+                add(f, kk + (int)((long long)mm * q / P), kk + (int)((long long)mm * (q + 1) / P), kk, true);
+        }
+        S.n_fwd_items = (int)S.sitems.size();
+        for (int i = F - 1; i >= 0; --i) {  // backward, descending height
+            const int f = byh[i], kk = S.k[f], P = S.parts_b[f];
+            for (int q = 0; q < P; ++q)
+                add(f, (int)((long long)kk * q / P), (int)((long long)kk * (q + 1) / P), S.n[f], false);
+        }
+        S.q_size = off;
     }
 
     // ---------------------------------------------------- level schedule

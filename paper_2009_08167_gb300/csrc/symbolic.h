@@ -26,6 +26,13 @@ struct PanelItem { int front; int r0; };            // TRSM row block of a front
 struct TileItem { int front; int i0; int j0; };     // trailing-update tile
 struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
 
+struct SolveItem {   // one work item of the persistent tree solve
+    int front;
+    int lo, hi;       // forward: border columns [lo,hi) (front numbering, k <= lo); backward: own rows [lo,hi)
+    int ldp;          // panel leading dimension, multiple of 4
+    long long off;    // panel offset in the Q pool (elements, multiple of 4)
+};
+
 struct StepRange {   // one panel step of one level
     int s;           // step index (panel columns s*nb .. )
     int d_begin, d_end;   // PanelItem range: one diagonal-block item per active front (r0 = s*nb)
@@ -79,13 +86,18 @@ struct Symbolic {
     std::vector<int> rel;             // extend-add: local index in parent, per border entry
     std::vector<long long> rel_ptr;   // rel of node F at rel_ptr[F] (length n_F - k_F)
     std::vector<long long> upd_off;   // solve update vector offsets (length n_F - k_F)
-    // packed solve operators: per front a column-major ldq_F x n_F block
-    // (ldq_F = k_F rounded up to 4, zero padded), columns [0,k): -A11^{-1},
-    // columns [k,n): -A11^{-1} A12; offsets 16-byte aligned for bulk copies
-    std::vector<int> ldq;
-    std::vector<long long> qoff;
+    // Tree-solve work items and their packed operator panels.  A front's
+    // forward sweep is split into parts by border columns, its backward sweep
+    // by own rows; every part has one panel in the Q pool (16-byte aligned):
+    //   forward part  [lo,hi) of columns k..n: row-major k x ldp panel of
+    //                 -A11^{-1} A12 (ldp = hi-lo rounded up to 4);
+    //   backward part [lo,hi) of rows 0..k: column-major ldp x n panel of
+    //                 [-A11^{-1} | -A11^{-1} A12] (ldp = hi-lo rounded up to 4).
+    std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
+    int n_fwd_items = 0;
+    std::vector<int> parts_f, parts_b;
     long long q_size = 0;
-    std::vector<PanelItem> qitems;    // pack work: (front, first column) per 32 columns
+    std::vector<PanelItem> qitems;    // pack work: (solve item, first element) per 4096 elements
     long long upd_size = 0;
 
     // factorization schedule

@@ -89,7 +89,7 @@ def load_library(path=LIB_PATH):
     lib.riga_stats.argtypes = [P] + [ctypes.POINTER(LL)] * 4 + [ctypes.POINTER(D)] * 2
     lib.riga_profile.argtypes = [P, I]
     lib.riga_set_wait_limit.argtypes = [P, LL]
-    lib.riga_trace_solve.argtypes = [P, P, P, P]
+    lib.riga_trace_solve.argtypes = [P, P, ctypes.POINTER(I), P, P]
     lib.riga_spmv_dot_noalloc.argtypes = [P, P, P, LL, P, P, P, P]
     lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
                                      ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -306,11 +306,12 @@ class Riga:
 
     def trace_solve(self, b):
         """One traced solve: per work item (sm, claim ns, ready ns, done ns) and its node."""
-        F = self.get_symbolic()["parent"].size
-        tr = np.zeros((2 * F, 4), dtype=np.int64)
-        order = np.zeros(2 * F, dtype=np.int32)
         bb = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b
-        self._check(self.lib.riga_trace_solve(self.ctx, _ptr(bb), _ptr(tr), _ptr(order)))
+        ni = ctypes.c_int(0)
+        self._check(self.lib.riga_trace_solve(self.ctx, _ptr(bb), ctypes.byref(ni), None, None))
+        tr = np.zeros((ni.value, 4), dtype=np.int64)
+        order = np.zeros(ni.value, dtype=np.int32)
+        self._check(self.lib.riga_trace_solve(self.ctx, _ptr(bb), ctypes.byref(ni), _ptr(tr), _ptr(order)))
         return tr, order
 
     def set_wait_limit(self, limit):
