@@ -120,6 +120,27 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return true;
 }
 
+// acc[q] += sum over units u = ua+g, ua+g+G, ... < ub of P[u-ua][li + 256 q] * w[u]
+// for the NA output slots of this thread (an exact count: predicated-off FP64
+// instructions still occupy GB300's narrow FP64 pipe).
+template <typename T, int NA>
+__device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ldp, int ua, int ub, int g, int G,
+                                                 int li, int cnt, const T* __restrict__ w, T* acc) {
+    for (int u = ua + g; u < ub; u += G) {
+        const T* row = P + (long long)(u - ua) * ldp;
+        const T x = w[u];
+        if (NA == 1) {
+            acc[0] += row[li] * x;
+        } else {
+#pragma unroll
+            for (int q2 = 0; q2 < NA; ++q2) {
+                const int l = li + q2 * 256;
+                if (l < cnt) acc[q2] += row[l] * x;
+            }
+        }
+    }
+}
+
 // One persistent launch per solve.  CTAs claim work items in order from a
 // global counter; an item waits (bounded) until its dependencies are done:
 // forward part: every forward part of every child; backward part: every
@@ -240,14 +261,15 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
             const int ua = c * upc, ub = min(units, ua + upc);
             const T* P = buf[b];
             if (active) {
-                for (int u = ua + g; u < ub; u += G) {
-                    const T* row = P + (long long)(u - ua) * ldp;
-                    const T x = w[u];
-#pragma unroll
-                    for (int q2 = 0; q2 < 8; ++q2) {
-                        const int l = li + q2 * 256;
-                        if (q2 < na && l < cnt) acc[q2] += row[l] * x;
-                    }
+                switch (na) {
+                    case 1: accumulate_chunk<T, 1>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 2: accumulate_chunk<T, 2>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 3: accumulate_chunk<T, 3>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 4: accumulate_chunk<T, 4>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 5: accumulate_chunk<T, 5>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 6: accumulate_chunk<T, 6>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 7: accumulate_chunk<T, 7>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    default: accumulate_chunk<T, 8>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
                 }
             }
             __syncthreads();
