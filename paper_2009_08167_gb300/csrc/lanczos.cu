@@ -26,23 +26,65 @@ namespace riga {
 
 constexpr int CH = 256;  // rows per chunk of the tall-skinny kernels
 
+constexpr int TJ = 32;  // basis columns per shared-memory tile
+
+// Partial dots out[j] = sum_{r in chunk} B[j][r] ws[r] for j < J over one
+// chunk of CH rows.  Each 32-column tile is staged through shared memory by
+// coalesced column loads; thread (column jl, row group g) then sums rows
+// g, g+8, ... with one FP64 FMA per element (GB300's FP64 pipe is the bound of
+// these tall-skinny products), and the 8 row groups are added through shared
+// memory.
+__device__ __forceinline__ void chunk_dots(const double* __restrict__ B, long long ld, int J, long long r0, int rows,
+                                           const double* __restrict__ ws, double* __restrict__ Vs,
+                                           double* __restrict__ red, double* __restrict__ out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j0 = 0; j0 < J; j0 += TJ) {
+        const int jn = min(TJ, J - j0);
+#pragma unroll
+        for (int q = 0; q < TJ / 8; ++q) {
+            const int jl = warp + 8 * q;
+            if (jl < jn) {
+                const double* col = B + (long long)(j0 + jl) * ld + r0;
+#pragma unroll
+                for (int i = 0; i < CH / 32; ++i) {
+                    const int r = lane + 32 * i;
+                    Vs[jl * (CH + 1) + r] = (r < rows) ? col[r] : 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        const int jl = lane, g = warp;
+        double s = 0.0;
+        if (jl < jn) {
+            const double* vc = Vs + jl * (CH + 1);
+#pragma unroll 8
+            for (int r = g; r < CH; r += 8) s += vc[r] * ws[r];
+        }
+        red[g * TJ + jl] = s;
+        __syncthreads();
+        if (tid < jn) {
+            double t = 0.0;
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg) t += red[gg * TJ + tid];
+            out[j0 + tid] = t;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) gemvT_partial_kernel(const double* __restrict__ B, long long ld, int J,
                                                             const double* __restrict__ w, long long N,
                                                             double* __restrict__ partial, int pstride) {
-    __shared__ double ws[CH];
+    extern __shared__ double sh[];
+    double* ws = sh;                    // CH
+    double* red = ws + CH;              // 8 * TJ
+    double* Vs = red + 8 * TJ;          // TJ * (CH + 1)
     const long long r0 = (long long)blockIdx.x * CH;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     ws[tid] = (r0 + tid < N) ? w[r0 + tid] : 0.0;
     __syncthreads();
     const int rows = (int)min((long long)CH, N - r0);
-    for (int j = warp; j < J; j += 8) {
-        const double* Bc = B + (long long)j * ld + r0;
-        double s = 0.0;
-        for (int r = lane; r < rows; r += 32) s += Bc[r] * ws[r];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) partial[(long long)blockIdx.x * pstride + j] = s;
-    }
+    chunk_dots(B, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
 __global__ void reduce_cols_kernel(const double* __restrict__ partial, int nch, int J, int pstride,
@@ -60,10 +102,12 @@ __global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restr
                                                            double* __restrict__ w, long long N,
                                                            double* __restrict__ partial, int pstride) {
     extern __shared__ double sh[];
-    double* cs = sh;       // J
-    double* ws = sh + J;   // CH
+    double* ws = sh;                    // CH
+    double* red = ws + CH;              // 8 * TJ
+    double* Vs = red + 8 * TJ;          // TJ * (CH + 1)
+    double* cs = Vs + TJ * (CH + 1);    // J
     const long long r0 = (long long)blockIdx.x * CH;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     for (int j = tid; j < J; j += blockDim.x) cs[j] = c1[j];
     __syncthreads();
     const long long r = r0 + tid;
@@ -76,14 +120,7 @@ __global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restr
     ws[tid] = v;
     __syncthreads();
     const int rows = (int)min((long long)CH, N - r0);
-    for (int j = warp; j < J; j += 8) {
-        const double* Bc = MV + (long long)j * ld + r0;
-        double s = 0.0;
-        for (int q = lane; q < rows; q += 32) s += Bc[q] * ws[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) partial[(long long)blockIdx.x * pstride + j] = s;
-    }
+    chunk_dots(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
 __global__ void gemv_update_kernel(const double* __restrict__ V, long long ld, int J, const double* __restrict__ c,
@@ -260,9 +297,10 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
     if (J <= 0) return RIGA_OK;
     // two Gram-Schmidt passes read MV twice and V twice
     PhaseScope scope(c, PH_REORTH, 4.0 * (double)R.N * J * sizeof(double));
-    { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, 0, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
+    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
+    { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }
-    size_t sm = (size_t)(J + CH) * sizeof(double);
+    size_t sm = sm_dots + (size_t)J * sizeof(double);
     { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, c->MV.ptr + col0 * R.ld, R.ld, J, R.c1, w,
                                                 R.N, c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2); }
@@ -308,6 +346,14 @@ int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
 
 }  // namespace
 
+static int configure_reorth(riga_ctx* c, int cap) {
+    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
+    const size_t sm_upd = sm_dots + (size_t)cap * sizeof(double);
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(gemvT_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dots));
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(update_gemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_upd));
+    return RIGA_OK;
+}
+
 int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     static const bool dbg = std::getenv("RIGA_DEBUG") != nullptr;
     Symbolic& S = c->S;
@@ -342,6 +388,10 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     R.rw = c->vwork[3].ptr;
     R.c1 = c->coef.ptr;
     R.c2 = c->coef.ptr + R.cap;
+    {
+        int rc0 = configure_reorth(c, R.cap);
+        if (rc0) return rc0;
+    }
     R.alpha = c->ab.ptr;
     R.beta = c->ab.ptr + m_cap + 2;
     c->stats = Stats();
