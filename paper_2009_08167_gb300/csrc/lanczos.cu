@@ -87,13 +87,41 @@ __global__ void __launch_bounds__(256) gemvT_partial_kernel(const double* __rest
     chunk_dots(B, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
-__global__ void reduce_cols_kernel(const double* __restrict__ partial, int nch, int J, int pstride,
-                                   double* __restrict__ out) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= J) return;
+// out[j] = sum over chunks of partial[c][j]: 32 columns per block, 8 chunk
+// groups per column, fixed summation order (deterministic)
+__global__ void __launch_bounds__(256) reduce_cols_kernel(const double* __restrict__ partial, int nch, int J,
+                                                          int pstride, double* __restrict__ out) {
+    __shared__ double red[8][33];
+    const int jl = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + jl;
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += partial[(long long)c * pstride + j];
-    out[j] = s;
+    if (j < J) {
+#pragma unroll 4
+        for (int c = g; c < nch; c += 8) s += partial[(long long)c * pstride + j];
+    }
+    red[g][jl] = s;
+    __syncthreads();
+    if (g == 0 && j < J) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][jl];
+        out[j] = t;
+    }
+}
+
+// v - sum_j V[j][r] c[j] with the loads issued eight at a time
+__device__ __forceinline__ double row_update(const double* __restrict__ V, long long ld, int J, long long r,
+                                             const double* __restrict__ cs, double v) {
+    int j = 0;
+    for (; j + 8 <= J; j += 8) {
+        double b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = V[(long long)(j + q) * ld + r];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v -= b[q] * cs[j + q];
+    }
+    for (; j < J; ++j) v -= V[(long long)j * ld + r] * cs[j];
+    return v;
 }
 
 // w -= V c1 on this chunk, then partial dots MV^T w
@@ -113,8 +141,7 @@ __global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restr
     const long long r = r0 + tid;
     double v = 0.0;
     if (r < N) {
-        v = w[r];
-        for (int j = 0; j < J; ++j) v -= V[(long long)j * ld + r] * cs[j];
+        v = row_update(V, ld, J, r, cs, w[r]);
         w[r] = v;
     }
     ws[tid] = v;
@@ -130,9 +157,7 @@ __global__ void gemv_update_kernel(const double* __restrict__ V, long long ld, i
     __syncthreads();
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
-    double v = w[r];
-    for (int j = 0; j < J; ++j) v -= V[(long long)j * ld + r] * cs[j];
-    w[r] = v;
+    w[r] = row_update(V, ld, J, r, cs, w[r]);
 }
 
 // y = M x over the permuted CSR (16 lanes per row) and per-block partial x.y
@@ -223,6 +248,51 @@ __global__ void __launch_bounds__(256) gemm_ritz_kernel(const double* __restrict
             if (i0 + q < nsel) U[(long long)(i0 + q) * ldu + r] = acc[q];
 }
 
+// Residuals of candidate Ritz pairs: for column q of U (with M U in MU),
+// partial sums of ||K u - lam_q M u||^2 and ||M u||^2 over this block's rows
+// (16 lanes per row; every thread runs the same number of iterations).
+__global__ void __launch_bounds__(256) resid_cols_kernel(long long N, const long long* __restrict__ rowptr,
+                                                         const int* __restrict__ col, const double* __restrict__ Kv,
+                                                         const double* __restrict__ U, const double* __restrict__ MU,
+                                                         long long ld, const double* __restrict__ lam,
+                                                         double* __restrict__ partial) {
+    __shared__ double sa[16], sb[16];
+    const int q = blockIdx.y;
+    const double l = lam[q];
+    const double* u = U + (long long)q * ld;
+    const double* mu = MU + (long long)q * ld;
+    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    double sr = 0.0, sm = 0.0;
+    for (long long it = blockIdx.x; it * 16 < N; it += gridDim.x) {
+        const long long row = it * 16 + grp;
+        double s = 0.0;
+        if (row < N)
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Kv[e] * u[col[e]];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+        if (lane == 0 && row < N) {
+            const double m = mu[row];
+            const double r = s - l * m;
+            sr += r * r;
+            sm += m * m;
+        }
+    }
+    if (lane == 0) {
+        sa[grp] = sr;
+        sb[grp] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < 16; ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        partial[((long long)q * gridDim.x + blockIdx.x) * 2] = ta;
+        partial[((long long)q * gridDim.x + blockIdx.x) * 2 + 1] = tb;
+    }
+}
+
 // sign convention: largest |u| positive, lowest index on ties (global numbering)
 __global__ void sign_fix_kernel(long long N, double* __restrict__ U, long long ldu) {
     __shared__ double bv[256];
@@ -299,11 +369,11 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
     PhaseScope scope(c, PH_REORTH, 4.0 * (double)R.N * J * sizeof(double));
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
     { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
-    { count_launch(c); reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }
+    { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }
     size_t sm = sm_dots + (size_t)J * sizeof(double);
     { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, c->MV.ptr + col0 * R.ld, R.ld, J, R.c1, w,
                                                 R.N, c->partial.ptr, R.cap); }
-    { count_launch(c); reduce_cols_kernel<<<(J + 127) / 128, 128, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2); }
+    { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2); }
     { count_launch(c); gemv_update_kernel<<<(unsigned)((R.N + 255) / 256), 256, (size_t)J * sizeof(double), st>>>(
         c->V.ptr + col0 * R.ld, R.ld, J, R.c2, w, R.N); }
     return RIGA_OK;
@@ -364,6 +434,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     const int extra = c->opt_extra > 0 ? c->opt_extra : 2;
     const int prec = c->opt_precision;
     const double tol_est = 1e-2 * tol;
+    const double lock_tol = 0.5 * tol;  // true-residual bar for locking
     const double gap_rel = 1e-6;
     int wmax = slice + extra;
     int m_cap = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * wmax, wmax + 60);
@@ -549,7 +620,8 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             Wsel.assign((size_t)m * nsel, 0.0);
             for (int q = 0; q < nsel; ++q)
                 for (int r = 0; r < m; ++r) Wsel[(size_t)q * m + r] = Zf[(size_t)sel[q] * m + r];
-            RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel));
+            // W, then candidate eigenvalues and residual partial sums (304 blocks)
+            RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel + nsel + (size_t)2 * 304 * nsel));
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, Wsel.data(), Wsel.size() * sizeof(double), cudaMemcpyHostToDevice, st));
             RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
             double* U = c->evec_perm.ptr;
@@ -558,12 +630,37 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
             { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N); }
             { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N); }
-            long long t = N * nsel;
-            { count_launch(c); copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, U, N, c->V.ptr + (long long)nlock * R.ld, R.ld); }
-            { count_launch(c); copy_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(N, nsel, MU, N, c->MV.ptr + (long long)nlock * R.ld, R.ld); }
-            for (int q = 0; q < nsel; ++q) lam.push_back(cur_sigma + 1.0 / theta[sel[q]]);
-            nlock += nsel;
-            fruitless = 0;
+            // lock only the candidates whose FP64 residual
+            // ||K u - lam M u|| / (|lam| ||M u||) meets the tolerance
+            std::vector<double> lcand(nsel);
+            for (int q = 0; q < nsel; ++q) lcand[q] = cur_sigma + 1.0 / theta[sel[q]];
+            const int gx = 304;
+            double* dlam = c->Wd.ptr + (size_t)m * nsel;
+            double* dpart = dlam + nsel;
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lcand.data(), nsel * sizeof(double), cudaMemcpyHostToDevice, st));
+            { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
+            std::vector<double> part((size_t)2 * gx * nsel);
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+            int acc_n = 0;
+            for (int q = 0; q < nsel; ++q) {
+                double ra = 0.0, rb = 0.0;
+                for (int b = 0; b < gx; ++b) {
+                    ra += part[((size_t)q * gx + b) * 2];
+                    rb += part[((size_t)q * gx + b) * 2 + 1];
+                }
+                const double rho = std::sqrt(ra) / (std::fabs(lcand[q]) * std::sqrt(rb));
+                if (!(rho <= lock_tol)) continue;
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->V.ptr + (long long)(nlock + acc_n) * R.ld, U + (long long)q * N,
+                                                 N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->MV.ptr + (long long)(nlock + acc_n) * R.ld, MU + (long long)q * N,
+                                                 N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                lam.push_back(lcand[q]);
+                ++acc_n;
+            }
+            nlock += acc_n;
+            if (acc_n > 0) fruitless = 0;
+            else ++fruitless;
         } else {
             ++fruitless;
         }
