@@ -44,6 +44,8 @@ struct DevBuf {
 struct Stats {
     long long n_fact = 0, n_solve = 0, n_matvec = 0, steps = 0;
     double t_fact_ms = 0.0, t_lanczos_ms = 0.0;
+    int ir_sweeps = 0;        // refinement sweeps per Lanczos solve (FP32 fronts)
+    long long n_fallback = 0; // shifts refactored with FP64 fronts after refinement stalled
 };
 
 // Per-phase device timing (CUDA events around each phase's launches, only

@@ -414,6 +414,30 @@ int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
     return rc;
 }
 
+// FP32 fronts: measure how many refinement sweeps one solve needs to reach a
+// relative residual of 1e-13 (a seeded random right-hand side, residuals read
+// back after every sweep); Lanczos then runs that many plus one without host
+// checks.  If refinement stalls, the shift is refactored with FP64 fronts.
+int calibrate_refinement(riga_ctx* c, uint64_t seed) {
+    const long long N = c->S.N;
+    for (int i = 2; i < 6; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    std::vector<double> hb(N);
+    uint64_t st = seed ^ 0x5DEECE66DULL;
+    for (long long i = 0; i < N; ++i) hb[i] = ((double)(splitmix(st) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->vwork[4].ptr, hb.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int sweeps = 0;
+    int rc = solve_refined(c, c->vwork[4].ptr, c->vwork[2].ptr, c->vwork[3].ptr, 1e-13, 20, 1, &sweeps);
+    if (rc == RIGA_OK) {
+        c->ir_sweeps = std::min(sweeps + 1, 20);
+        c->stats.ir_sweeps = c->ir_sweeps;
+        return RIGA_OK;
+    }
+    if (rc != RIGA_EREFINE) return rc;
+    c->last_error.clear();
+    c->stats.n_fallback++;
+    return factor_at(c, c->sigma, RIGA_FP64, nullptr);
+}
+
 }  // namespace
 
 static int configure_reorth(riga_ctx* c, int cap) {
@@ -470,10 +494,11 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     std::vector<double> lam;      // locked eigenvalues, in column order of V
     int nlock = 0;
     long long nu0 = 0, nu_chk = 0;
-    int rc = factor_at(c, sigma0, prec, &nu0);
+    int rc = factor_at(c, sigma0, RIGA_FP64, &nu0);
     if (rc) return rc;
     double cur_sigma = sigma0;
     double factored_sigma = sigma0;
+    double calibrated_sigma = std::nan("");
     int confirmed = 0;
     int target = std::min(k, slice);
     int need = target + extra;  // locked pairs above sigma0 wanted before the next check
@@ -499,7 +524,8 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
                 continue;
             }
             const double sp = 0.5 * (sl[gi - 1] + sl[gi]);
-            rc = factor_at(c, sp, prec, &nu_chk);
+            // the inertia that certifies completeness always comes from FP64 fronts
+            rc = factor_at(c, sp, RIGA_FP64, &nu_chk);
             if (dbg)
                 std::fprintf(stderr, "[riga] check: nlock=%d target=%d gap_index=%d shift=%.12g inertia=%lld-%lld found=%d rc=%d\n",
                              nlock, target, gi, sp, nu_chk, nu0, gi, rc);
@@ -525,10 +551,16 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             status = RIGA_ENOCONV;
             break;
         }
-        if (factored_sigma != cur_sigma) {
+        if (factored_sigma != cur_sigma || (c->precision != prec && c->stats.n_fallback == 0)) {
             rc = factor_at(c, cur_sigma, prec, nullptr);
             if (rc) { status = rc; break; }
             factored_sigma = cur_sigma;
+        }
+        if (c->precision == RIGA_FP32 && calibrated_sigma != cur_sigma) {
+            rc = calibrate_refinement(c, seed + (uint64_t)runs);
+            if (rc) { status = rc; break; }
+            calibrated_sigma = cur_sigma;
+            if (dbg) std::fprintf(stderr, "[riga] refinement sweeps per solve: %d (precision now %d)\n", c->ir_sweeps, c->precision);
         }
         const int want_run = std::max(need - nlock, 1);
         int m_max = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * want_run, want_run + 60);

@@ -244,10 +244,17 @@ class Riga:
         return ev, U, rs
 
     def eig_grad(self, k, weights):
+        """Gradients (grad_a, grad_b) of sum_i weights[i] lambda_i; numpy in ->
+        numpy out, CUDA tensor in -> CUDA tensors out."""
         ne = self.mesh.n_elem
-        w = np.ascontiguousarray(weights, dtype=np.float64)
-        ga = np.zeros(ne)
-        gb = np.zeros(ne)
+        if _is_torch(weights):
+            w = weights.contiguous()
+            ga = w.new_zeros(ne)
+            gb = w.new_zeros(ne)
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float64)
+            ga = np.zeros(ne)
+            gb = np.zeros(ne)
         self._check(self.lib.riga_eig_grad(self.ctx, int(k), _ptr(w), _ptr(ga), _ptr(gb)))
         return ga, gb
 
