@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
-METRIC = "eigenpairs/s at resid<=1e-10 (2D p=3 256^2 rIGA bs16, 100 pairs, 2 slices)"
+METRIC = "eigenpairs/s at resid<=1e-10"
 RESID_TOL = 1e-10
 
 
@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="riga", choices=["riga", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--mesh", default="riga", choices=["riga", "iga"])
+    ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3"],
+                    help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, 50 pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-front (mixed) leg")
@@ -58,7 +59,11 @@ def parse():
 
 
 def workload(mesh_kind):
-    from paper_2009_08167_gb300.inputs import config_c2
+    from paper_2009_08167_gb300.inputs import config_c2, config_c3
+    if mesh_kind == "c3":
+        cfg = config_c3()
+        cfg["slice"] = cfg["k"]
+        return cfg
     cfg = config_c2(riga=(mesh_kind == "riga"))
     return cfg
 
@@ -66,7 +71,7 @@ def workload(mesh_kind):
 def config_dict(args, cfg, extra=None):
     m = cfg["mesh"]
     d = {
-        "workload": f"laplace2d_p{m.p}_{m.ne[0]}x{m.ne[1]}_{'riga_bs%d' % m.bs if m.bs else 'iga'}_k{cfg['k']}_slices{cfg['k'] // cfg['slice']}",
+        "workload": f"laplace{m.dim}d_p{m.p}_{'x'.join(str(v) for v in m.ne)}_{'riga_bs%d' % m.bs if m.bs else 'iga'}_k{cfg['k']}_slices{cfg['k'] // cfg['slice']}",
         "dim": m.dim, "elements_per_side": m.ne[0], "degree": m.p, "block_size": m.bs, "leaf_extent": m.leaf_extent,
         "pairs": cfg["k"], "slice": cfg["slice"], "factor_precision": args.precision,
         "l2": "flushed between timed steps (512 MiB write)",
