@@ -99,6 +99,7 @@ struct riga_ctx {
     // --------------------------------------------------------------- factor
     int precision = RIGA_FP64;
     double sigma = 0.0;
+    bool inertia_only = false;   // next factorization skips the solve operators (extra rows)
     riga::DevBuf<double> pool64;
     riga::DevBuf<float> pool32;
     riga::DevBuf<double> q64;    // packed solve operators (see Symbolic::qoff)

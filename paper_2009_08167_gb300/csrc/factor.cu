@@ -104,11 +104,13 @@ __global__ void diag_kernel(const PanelItem* __restrict__ items, const int* __re
 template <typename T>
 __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const int* __restrict__ kk,
                             const int* __restrict__ nn, const long long* __restrict__ front_off,
-                            T* __restrict__ pool) {
+                            T* __restrict__ pool, int plain) {
     __shared__ T Ls[NB][NB + 1];
     __shared__ T ds[NB];
     const PanelItem it = items[blockIdx.x];
     const int F = it.front, k = kk[F], ld = nn[F] + k;
+    const int rmax = plain ? nn[F] : ld;  // plain: skip the extra rows
+    if (it.r0 >= rmax) return;
     const int kb = min(NB, k - j0);
     T* A = pool + front_off[F];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
@@ -118,7 +120,7 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
     }
     __syncthreads();
     const int r = it.r0 + threadIdx.x;
-    if (r >= ld) return;
+    if (r >= rmax) return;
     T x[NB];
 #pragma unroll
     for (int t = 0; t < NB; ++t)
@@ -144,11 +146,12 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
                                                      const int* __restrict__ kk, const int* __restrict__ nn,
                                                      const long long* __restrict__ front_off,
                                                      const int* __restrict__ node_ptr, const double* __restrict__ D,
-                                                     T* __restrict__ pool) {
+                                                     T* __restrict__ pool, int plain) {
     __shared__ T As[NB][TILE];
     __shared__ T Bs[NB][TILE];
     const TileItem it = items[blockIdx.x];
     const int F = it.front, k = kk[F], n = nn[F], ld = n + k;
+    if (plain && (it.i0 >= n || it.j0 >= n)) return;  // plain: tiles touching only extra rows
     const int kb = min(NB, k - p0);
     T* A = pool + front_off[F];
     const double* d = D + node_ptr[F] + p0;
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
         for (int a = 0; a < 4; ++a) {
             int gi = it.i0 + tx + 16 * a;
             // lower triangle, plus the whole extra x extra block
-            if (gi < ld && (gi >= gj || (gi >= n && gj >= n))) A[(long long)gj * ld + gi] -= acc[a][b];
+            if (gi < ld && (gi >= gj || (gi >= n && gj >= n)) && !(plain && gi >= n)) A[(long long)gj * ld + gi] -= acc[a][b];
         }
     }
 }
@@ -243,11 +246,12 @@ template <typename T>
 static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
-    PhaseScope scope(c, PH_FACTOR, 0.0, S.flops + S.flops_aug);
+    PhaseScope scope(c, PH_FACTOR, 0.0, c->inertia_only ? S.flops : S.flops + S.flops_aug);
     RIGA_CUDA_TRY(c, cudaMemsetAsync(pool, 0, (size_t)S.pool_size * sizeof(T), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
-    { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
+    const int plain = c->inertia_only ? 1 : 0;
+    if (!plain) { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
     if (S.nnz > 0)
         { count_launch(c); scatter_kernel<T><<<(unsigned)((S.nnz + 255) / 256), 256, 0, st>>>(S.nnz, c->scatter.ptr, c->Kval.ptr,
                                                                           c->Mval.ptr, c->sigma, pool); }
@@ -268,14 +272,14 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
                                                                     c->flag.ptr); }
             if (R.p_end > R.p_begin)
                 { count_launch(c); trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
-                                                                   c->nn.ptr, c->front_off.ptr, pool); }
+                                                                   c->nn.ptr, c->front_off.ptr, pool, plain); }
             if (R.t_end > R.t_begin)
                 { count_launch(c); update_kernel<T><<<R.t_end - R.t_begin, 256, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
                                                                       c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr,
-                                                                      c->D.ptr, pool); }
+                                                                      c->D.ptr, pool, plain); }
         }
     }
-    if (!S.qitems.empty())
+    if (!S.qitems.empty() && !plain)
         { count_launch(c); pack_q_kernel<T><<<(unsigned)S.qitems.size(), 256, 0, st>>>(c->qitems.ptr, c->sitems.ptr, S.n_fwd_items,
                                                                                       c->kk.ptr, c->nn.ptr, c->front_off.ptr,
                                                                                       pool, Q); }
@@ -291,14 +295,10 @@ int enqueue_factor(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->flag.alloc(1));
     RIGA_CUDA_TRY(c, c->neg.alloc(1));
     if (c->precision == RIGA_FP64) {
-        c->pool32.release();
-        c->q32.release();
         if (c->pool64.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp64)");
         if (c->q64.alloc(S.q_size + 4) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "solve operators (fp64)");
         return enqueue_factor_t<double>(c, c->pool64.ptr, c->q64.ptr);
     }
-    c->pool64.release();
-    c->q64.release();
     if (c->pool32.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp32)");
     if (c->q32.alloc(S.q_size + 4) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "solve operators (fp32)");
     return enqueue_factor_t<float>(c, c->pool32.ptr, c->q32.ptr);
@@ -315,7 +315,7 @@ int finish_factor(riga_ctx* c) {
         c->factored = false;
         return set_error(c, RIGA_EPIVOT, "zero or non-finite pivot in LDL^T (shift at an eigenvalue?)");
     }
-    c->factored = true;
+    c->factored = !c->inertia_only;  // an inertia-only factorization cannot solve
     return RIGA_OK;
 }
 

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <numeric>
 
 #include "ctx.h"
@@ -392,12 +393,19 @@ void normalize_into(Run& R, double* w, int col, int jslot) {
                                                                      c->V.ptr + col * R.ld, c->MV.ptr + col * R.ld); }
 }
 
-int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
+// Numeric factorization at sigma.  An inertia-only factorization leaves the
+// packed solve operators (Q pool) untouched, so the solve state of the
+// previous factorization (shift, precision) is restored afterwards.
+int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool inertia_only = false) {
+    const double keep_sigma = c->sigma;
+    const int keep_prec = c->precision;
+    const bool keep_factored = c->factored;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     c->sigma = sigma;
     c->precision = precision;
+    c->inertia_only = inertia_only;
     cudaEventRecord(e0, c->stream);
     int rc = enqueue_factor(c);
     if (rc == RIGA_OK) {
@@ -411,6 +419,12 @@ int factor_at(riga_ctx* c, double sigma, int precision, long long* nu) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (nu) *nu = c->inertia;
+    if (inertia_only) {
+        c->sigma = keep_sigma;
+        c->precision = keep_prec;
+        c->factored = keep_factored;
+    }
+    c->inertia_only = false;
     return rc;
 }
 
@@ -494,10 +508,12 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     std::vector<double> lam;      // locked eigenvalues, in column order of V
     int nlock = 0;
     long long nu0 = 0, nu_chk = 0;
-    int rc = factor_at(c, sigma0, RIGA_FP64, &nu0);
+    std::map<double, long long> inertia_cache;
+    int rc = factor_at(c, sigma0, RIGA_FP64, &nu0, prec != RIGA_FP64);
     if (rc) return rc;
+    inertia_cache[sigma0] = nu0;
     double cur_sigma = sigma0;
-    double factored_sigma = sigma0;
+    double factored_sigma = (prec == RIGA_FP64) ? sigma0 : std::nan("");
     double calibrated_sigma = std::nan("");
     int confirmed = 0;
     int target = std::min(k, slice);
@@ -524,13 +540,25 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
                 continue;
             }
             const double sp = 0.5 * (sl[gi - 1] + sl[gi]);
-            // the inertia that certifies completeness always comes from FP64 fronts
-            rc = factor_at(c, sp, RIGA_FP64, &nu_chk);
+            // the inertia that certifies completeness always comes from FP64
+            // fronts; it is cached per shift.  The solve operators are only
+            // built when this shift may carry the next slice's Lanczos run.
+            auto hit = inertia_cache.find(sp);
+            if (hit != inertia_cache.end()) {
+                nu_chk = hit->second;
+                rc = RIGA_OK;
+            } else {
+                const bool reuse = (prec == RIGA_FP64) && (target < k);
+                rc = factor_at(c, sp, RIGA_FP64, &nu_chk, !reuse);
+                if (rc == RIGA_OK) {
+                    inertia_cache[sp] = nu_chk;
+                    if (reuse) factored_sigma = sp;
+                }
+            }
             if (dbg)
-                std::fprintf(stderr, "[riga] check: nlock=%d target=%d gap_index=%d shift=%.12g inertia=%lld-%lld found=%d rc=%d\n",
-                             nlock, target, gi, sp, nu_chk, nu0, gi, rc);
+                std::fprintf(stderr, "[riga] check: nlock=%d target=%d gap_index=%d shift=%.12g inertia=%lld-%lld found=%d rc=%d cached=%d\n",
+                             nlock, target, gi, sp, nu_chk, nu0, gi, rc, (int)(hit != inertia_cache.end()));
             if (rc) { status = rc; break; }
-            factored_sigma = sp;
             const long long found = gi;  // locked eigenvalues below sp (all are > sigma0)
             if (nu_chk - nu0 == found) {
                 confirmed = gi;
@@ -551,7 +579,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             status = RIGA_ENOCONV;
             break;
         }
-        if (factored_sigma != cur_sigma || (c->precision != prec && c->stats.n_fallback == 0)) {
+        if (!(factored_sigma == cur_sigma)) {
             rc = factor_at(c, cur_sigma, prec, nullptr);
             if (rc) { status = rc; break; }
             factored_sigma = cur_sigma;
