@@ -543,7 +543,9 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             // the inertia that certifies completeness always comes from FP64
             // fronts; it is cached per shift.  The solve operators are only
             // built when this shift may carry the next slice's Lanczos run.
-            auto hit = inertia_cache.find(sp);
+            auto hit = inertia_cache.end();
+            for (auto it2 = inertia_cache.begin(); it2 != inertia_cache.end(); ++it2)
+                if (std::fabs(it2->first - sp) <= 1e-10 * std::fabs(sp)) hit = it2;
             if (hit != inertia_cache.end()) {
                 nu_chk = hit->second;
                 rc = RIGA_OK;
