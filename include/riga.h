@@ -166,8 +166,8 @@ int riga_eigs(riga_ctx* ctx, int k, double sigma, double tol, double* evals, dou
               double* resid, int* nconv);
 
 /*
- * riga_set_eig_options: options of riga_eigs (not in the SURVEY-level
- * signature, kept separate so that riga_eigs stays short).
+ * riga_set_eig_options: options of riga_eigs and riga_eigs_batch, kept
+ * separate so that their signatures stay short.
  *  slice      eigenpairs accepted per shift (0 = k, a single shift);
  *  precision  RIGA_FP64 or RIGA_FP32 factor inside riga_eigs;
  *  max_steps  Lanczos steps per run (0 = automatic: min(N, max(3 w, w + 40))
@@ -178,6 +178,48 @@ int riga_eigs(riga_ctx* ctx, int k, double sigma, double tol, double* evals, dou
  */
 int riga_set_eig_options(riga_ctx* ctx, int slice, int precision, int max_steps, int extra,
                          unsigned long long seed);
+
+/*
+ * riga_assemble_batch: assembles nprob independent problems (each a mesh as
+ * in riga_assemble, Sec. 2-3; meshes may differ in dim, p, elements and
+ * separators) into one context.  Their elimination trees (Sec. 4.2) are merged
+ * into a forest: every later factorization processes one tree level of all
+ * problems per launch, and one persistent solve serves all of them.
+ *  coefK[b], coefM[b] (the arrays themselves and each entry may be NULL):
+ *    HOST arrays of per-element coefficients of problem b as in
+ *    riga_assemble; NULL selects constant coefficients.
+ * The context then holds a batch: riga_eigs and riga_eig_grad answer
+ * RIGA_ESTATE, riga_factor factors all problems at one shift (n_neg = the
+ * inertia summed over the problems), riga_solve and riga_spmv act on the
+ * concatenated vectors (problem b's rows follow problem b-1's), and
+ * riga_get_matrices returns the block-diagonal K and M.  A later
+ * riga_assemble replaces the batch by a single problem.
+ * Errors: RIGA_EINVAL (bad mesh, with its index in riga_last_error),
+ * RIGA_ENOMEM, RIGA_ECUDA.
+ */
+int riga_assemble_batch(riga_ctx* ctx, int nprob, const riga_mesh* meshes, const double* const* coefK,
+                        const double* const* coefM);
+
+/*
+ * riga_eigs_batch: for every problem of the batch, the k smallest eigenvalues
+ * lambda > sigma of K u = lambda M u by shift-and-invert Lanczos (Sec. 4) in
+ * FP64, all problems advancing together: one factorization of the forest, one
+ * persistent solve and one M-SpMV per Lanczos step for the whole batch, with
+ * each problem's recurrence, reorthogonalisation, Rayleigh-Ritz step, locking
+ * and inertia-certified completeness check (its own check shift, in one
+ * factorization of the forest with per-problem shifts) kept separate.
+ *  evals[nprob * k]: HOST, problem-major, ascending within each problem;
+ *    NaN where a problem did not converge.
+ *  resid[nprob * k] (may be NULL): HOST, FP64 residuals
+ *    ||K u - lambda M u||_2 / (|lambda| ||M u||_2) of the accepted pairs.
+ *  nconv[nprob] (may be NULL): HOST, pairs delivered per problem (k or 0).
+ * Uses the slice-free options of riga_set_eig_options (max_steps, extra,
+ * seed); the precision is always FP64.
+ * Errors: RIGA_ESTATE (no riga_assemble_batch), RIGA_EINVAL (k too large for
+ * the smallest problem), RIGA_ENOCONV (outputs of the converged problems
+ * valid), RIGA_EPIVOT, RIGA_ENOMEM, RIGA_ECUDA.
+ */
+int riga_eigs_batch(riga_ctx* ctx, int k, double sigma, double tol, double* evals, double* resid, int* nconv);
 
 /*
  * riga_eig_grad: gradient of L = sum_i dL_dlambda[i] lambda_i over the k

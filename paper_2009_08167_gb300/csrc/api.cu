@@ -48,6 +48,8 @@ int to_user(riga_ctx* c, const T* dev, T* user, size_t n) {
     return RIGA_OK;
 }
 
+}  // namespace
+
 int upload_symbolic(riga_ctx* c) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
@@ -90,9 +92,12 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
+    if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     return RIGA_OK;
 }
+
+namespace {
 
 __global__ void scatter_glob_kernel(long long nnz, const long long* __restrict__ p2g, const double* __restrict__ src,
                                     double* __restrict__ dst) {
@@ -298,6 +303,7 @@ int riga_factor(riga_ctx* c, double sigma, int precision, long long* n_neg) {
     if (precision != RIGA_FP64 && precision != RIGA_FP32) return set_error(c, RIGA_EINVAL, "unknown precision");
     if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
     c->sigma = sigma;
+    c->sigma_prob.clear();
     c->precision = precision;
     c->factored = false;
     int rc = enqueue_factor(c);
@@ -358,6 +364,7 @@ int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, doubl
     c->last_error.clear();
     cudaSetDevice(c->device);
     if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (c->S.dim == 0) return set_error(c, RIGA_ESTATE, "a batch context: use riga_eigs_batch");
     if (!(tol > 0.0)) return set_error(c, RIGA_EINVAL, "tol must be positive");
     if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
     int got = 0;

@@ -148,19 +148,21 @@ struct DirDev {
     int ne;
 };
 
-__global__ void csr_kron_kernel(int dim, int p, long long N, const long long* __restrict__ rowptr,
-                                const int* __restrict__ col, const int* __restrict__ perm, DirDev X, DirDev Y,
-                                DirDev Z, double* __restrict__ Kv, double* __restrict__ Mv) {
+__global__ void csr_kron_kernel(int dim, int p, long long N, long long row0, long long goff,
+                                const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const int* __restrict__ perm, DirDev X, DirDev Y, DirDev Z, double* __restrict__ Kv,
+                                double* __restrict__ Mv) {
     const int lane = threadIdx.x & 31;
     long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= N) return;
+    row += row0;
     const int w = 2 * p + 1;
-    int g = perm[row];
+    int g = (int)(perm[row] - goff);
     int ix = g % X.n, rem = g / X.n;
     int iy = dim > 1 ? rem % Y.n : 0;
     int iz = dim > 2 ? rem / Y.n : 0;
     for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
-        int h = perm[col[e]];
+        int h = (int)(perm[col[e]] - goff);
         int jx = h % X.n, r2 = h / X.n;
         int jy = dim > 1 ? r2 % Y.n : 0;
         int jz = dim > 2 ? r2 / Y.n : 0;
@@ -190,20 +192,22 @@ __device__ __forceinline__ void elem_range(const DirDev& D, int p, int i, int j,
     hi = min(D.kv[f + p + 1], D.kv[g + p + 1]);
 }
 
-__global__ void csr_coef_kernel(int dim, int p, long long N, const long long* __restrict__ rowptr,
-                                const int* __restrict__ col, const int* __restrict__ perm, DirDev X, DirDev Y,
-                                DirDev Z, const double* __restrict__ cK, const double* __restrict__ cM,
-                                double* __restrict__ Kv, double* __restrict__ Mv) {
+__global__ void csr_coef_kernel(int dim, int p, long long N, long long row0, long long goff,
+                                const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const int* __restrict__ perm, DirDev X, DirDev Y, DirDev Z,
+                                const double* __restrict__ cK, const double* __restrict__ cM, double* __restrict__ Kv,
+                                double* __restrict__ Mv) {
     const int lane = threadIdx.x & 31;
     long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= N) return;
+    row += row0;
     const int q = p + 1, qq = q * q;
-    int g = perm[row];
+    int g = (int)(perm[row] - goff);
     int ix = g % X.n, rem = g / X.n;
     int iy = dim > 1 ? rem % Y.n : 0;
     int iz = dim > 2 ? rem / Y.n : 0;
     for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
-        int h = perm[col[e]];
+        int h = (int)(perm[col[e]] - goff);
         int jx = h % X.n, r2 = h / X.n;
         int jy = dim > 1 ? r2 % Y.n : 0;
         int jz = dim > 2 ? r2 / Y.n : 0;
@@ -252,52 +256,69 @@ __global__ void csr_coef_kernel(int dim, int p, long long N, const long long* __
     }
 }
 
-int assemble_device(riga_ctx* c) {
-    Symbolic& S = c->S;
+// Assembles one problem (its 1D data in P) into rows [row0, row0 + P.N) of the
+// context's CSR; goff is the problem's first global DOF.  cK / cM: device
+// coefficient arrays of the problem (NULL = constant).
+int assemble_problem(riga_ctx* c, const Symbolic& P, long long row0, long long goff, const double* cK,
+                     const double* cM) {
     cudaStream_t st = c->stream;
-    PhaseScope scope(c, PH_ASSEMBLE, (double)S.nnz * 16.0);
     DirDev dd[3];
     for (int a = 0; a < 3; ++a) {
         dd[a] = DirDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, 1};
-        if (a >= S.dim) continue;
-        const Dir1D& D = S.dir[a];
-        const int q = S.p + 1, w = 2 * S.p + 1;
+        if (a >= P.dim) continue;
+        const Dir1D& D = P.dir[a];
+        const int q = P.p + 1, w = 2 * P.p + 1;
         RIGA_CUDA_TRY(c, c->kv[a].upload(D.kv, st));
         RIGA_CUDA_TRY(c, c->elem_first[a].upload(D.elem_first, st));
         RIGA_CUDA_TRY(c, c->Ke1[a].alloc((size_t)D.ne * q * q));
         RIGA_CUDA_TRY(c, c->Me1[a].alloc((size_t)D.ne * q * q));
         RIGA_CUDA_TRY(c, c->Kb1[a].alloc((size_t)D.ndof * w));
         RIGA_CUDA_TRY(c, c->Mb1[a].alloc((size_t)D.ndof * w));
-        { count_launch(c); elem1d_kernel<<<(D.ne + 127) / 128, 128, 0, st>>>(D.ne, S.p, c->kv[a].ptr, c->elem_first[a].ptr,
+        { count_launch(c); elem1d_kernel<<<(D.ne + 127) / 128, 128, 0, st>>>(D.ne, P.p, c->kv[a].ptr, c->elem_first[a].ptr,
                                                           c->Ke1[a].ptr, c->Me1[a].ptr); }
-        { count_launch(c); band1d_kernel<<<(D.ndof * w + 127) / 128, 128, 0, st>>>(D.ndof, S.p, c->kv[a].ptr, c->elem_first[a].ptr,
+        { count_launch(c); band1d_kernel<<<(D.ndof * w + 127) / 128, 128, 0, st>>>(D.ndof, P.p, c->kv[a].ptr, c->elem_first[a].ptr,
                                                                 c->Ke1[a].ptr, c->Me1[a].ptr, c->Kb1[a].ptr,
                                                                 c->Mb1[a].ptr); }
         dd[a] = DirDev{c->kv[a].ptr, c->elem_first[a].ptr, c->Ke1[a].ptr, c->Me1[a].ptr,
                        c->Kb1[a].ptr, c->Mb1[a].ptr, D.ndof, D.ne};
     }
-    RIGA_CUDA_TRY(c, c->Kval.alloc(S.nnz));
-    RIGA_CUDA_TRY(c, c->Mval.alloc(S.nnz));
-    long long threads = S.N * 32;
+    long long threads = P.N * 32;
     int blocks = (int)((threads + 255) / 256);
-    if (c->coefK.empty() && c->coefM.empty()) {
-        { count_launch(c); csr_kron_kernel<<<blocks, 256, 0, st>>>(S.dim, S.p, S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, dd[0],
-                                                dd[1], dd[2], c->Kval.ptr, c->Mval.ptr); }
+    if (!cK && !cM) {
+        { count_launch(c); csr_kron_kernel<<<blocks, 256, 0, st>>>(P.dim, P.p, P.N, row0, goff, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
+                                                dd[0], dd[1], dd[2], c->Kval.ptr, c->Mval.ptr); }
     } else {
-        const double* cK = nullptr;
-        const double* cM = nullptr;
-        if (!c->coefK.empty()) {
-            RIGA_CUDA_TRY(c, c->dcoefK.upload(c->coefK, st));
-            cK = c->dcoefK.ptr;
-        }
-        if (!c->coefM.empty()) {
-            RIGA_CUDA_TRY(c, c->dcoefM.upload(c->coefM, st));
-            cM = c->dcoefM.ptr;
-        }
-        { count_launch(c); csr_coef_kernel<<<blocks, 256, 0, st>>>(S.dim, S.p, S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, dd[0],
-                                                dd[1], dd[2], cK, cM, c->Kval.ptr, c->Mval.ptr); }
+        { count_launch(c); csr_coef_kernel<<<blocks, 256, 0, st>>>(P.dim, P.p, P.N, row0, goff, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
+                                                dd[0], dd[1], dd[2], cK, cM, c->Kval.ptr, c->Mval.ptr); }
     }
     RIGA_CUDA_TRY(c, cudaGetLastError());
+    return RIGA_OK;
+}
+
+int assemble_device(riga_ctx* c) {
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_ASSEMBLE, (double)S.nnz * 16.0);
+    RIGA_CUDA_TRY(c, c->Kval.alloc(S.nnz));
+    RIGA_CUDA_TRY(c, c->Mval.alloc(S.nnz));
+    const double* cK = nullptr;
+    const double* cM = nullptr;
+    if (!c->coefK.empty()) {
+        RIGA_CUDA_TRY(c, c->dcoefK.upload(c->coefK, st));
+        cK = c->dcoefK.ptr;
+    }
+    if (!c->coefM.empty()) {
+        RIGA_CUDA_TRY(c, c->dcoefM.upload(c->coefM, st));
+        cM = c->dcoefM.ptr;
+    }
+    if (S.dim > 0) return assemble_problem(c, S, 0, 0, cK, cM);
+    // batch: one problem at a time into its rows of the merged CSR
+    for (size_t b = 0; b < c->probs.size(); ++b) {
+        const long long e0 = S.prob_elem[b];
+        int rc = assemble_problem(c, c->probs[b], S.prob_pos[b], S.prob_pos[b], cK ? cK + e0 : nullptr,
+                                  cM ? cM + e0 : nullptr);
+        if (rc) return rc;
+    }
     return RIGA_OK;
 }
 

@@ -1,0 +1,741 @@
+// Batched shift-and-invert Lanczos over many independent eigenproblems
+// (Sec. 4.2 applied to each problem of a batch at once).
+//
+// The problems are merged into one forest (symbolic.cpp merge_symbolic): one
+// factorization launch per tree level and one persistent tree solve serve all
+// of them, and the SpMV runs on the block-diagonal merged CSR.  Each problem
+// keeps its own Lanczos recurrence: all reductions (Gram-Schmidt coefficients,
+// M-norms, residuals) are segmented by problem over row chunks that never
+// straddle two problems, and every problem has its own alpha, beta, Ritz
+// values, locked vectors and completeness check.  Check shifts are per
+// problem in one factorization of the forest (per-position shifts), and the
+// Sylvester inertia is counted per problem.  FP64 fronts.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <numeric>
+
+#include "ctx.h"
+
+namespace riga {
+
+constexpr int BCH = 256;  // rows per chunk
+constexpr int BTJ = 32;   // basis columns per shared-memory tile
+
+struct Chunks {
+    const long long* row0;
+    const int* rows;
+    const int* prob;
+};
+
+// partial dots over one chunk (same scheme as the single-problem kernels)
+__device__ __forceinline__ void bchunk_dots(const double* __restrict__ B, long long ld, int J, long long r0, int rows,
+                                            const double* __restrict__ ws, double* __restrict__ Vs,
+                                            double* __restrict__ red, double* __restrict__ out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j0 = 0; j0 < J; j0 += BTJ) {
+        const int jn = min(BTJ, J - j0);
+#pragma unroll
+        for (int q = 0; q < BTJ / 8; ++q) {
+            const int jl = warp + 8 * q;
+            if (jl < jn) {
+                const double* col = B + (long long)(j0 + jl) * ld + r0;
+#pragma unroll
+                for (int i = 0; i < BCH / 32; ++i) {
+                    const int r = lane + 32 * i;
+                    Vs[jl * (BCH + 1) + r] = (r < rows) ? col[r] : 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        double s = 0.0;
+        if (lane < jn) {
+            const double* vc = Vs + lane * (BCH + 1);
+#pragma unroll 8
+            for (int r = warp; r < BCH; r += 8) s += vc[r] * ws[r];
+        }
+        red[warp * BTJ + lane] = s;
+        __syncthreads();
+        if (tid < jn) {
+            double t = 0.0;
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg) t += red[gg * BTJ + tid];
+            out[j0 + tid] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) bgemvT_kernel(const double* __restrict__ B, long long ld, int J,
+                                                     const double* __restrict__ w, Chunks ch,
+                                                     double* __restrict__ partial, int pstride) {
+    extern __shared__ double sh[];
+    double* ws = sh;
+    double* red = ws + BCH;
+    double* Vs = red + 8 * BTJ;
+    const long long r0 = ch.row0[blockIdx.x];
+    const int rows = ch.rows[blockIdx.x];
+    ws[threadIdx.x] = (threadIdx.x < rows) ? w[r0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    bchunk_dots(B, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+}
+
+__device__ __forceinline__ double brow_update(const double* __restrict__ V, long long ld, int J, long long r,
+                                              const double* __restrict__ cs, double v) {
+    int j = 0;
+    for (; j + 8 <= J; j += 8) {
+        double b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = V[(long long)(j + q) * ld + r];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v -= b[q] * cs[j + q];
+    }
+    for (; j < J; ++j) v -= V[(long long)j * ld + r] * cs[j];
+    return v;
+}
+
+// w -= V c(problem) on this chunk, then partial dots MV^T w
+__global__ void __launch_bounds__(256) bupdate_gemvT_kernel(const double* __restrict__ V, const double* __restrict__ MV,
+                                                            long long ld, int J, const double* __restrict__ coef,
+                                                            double* __restrict__ w, Chunks ch,
+                                                            double* __restrict__ partial, int pstride) {
+    extern __shared__ double sh[];
+    double* ws = sh;
+    double* red = ws + BCH;
+    double* Vs = red + 8 * BTJ;
+    double* cs = Vs + BTJ * (BCH + 1);
+    const long long r0 = ch.row0[blockIdx.x];
+    const int rows = ch.rows[blockIdx.x];
+    const double* c = coef + (long long)ch.prob[blockIdx.x] * J;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) cs[j] = c[j];
+    __syncthreads();
+    double v = 0.0;
+    if ((int)threadIdx.x < rows) {
+        const long long r = r0 + threadIdx.x;
+        v = brow_update(V, ld, J, r, cs, w[r]);
+        w[r] = v;
+    }
+    ws[threadIdx.x] = v;
+    __syncthreads();
+    bchunk_dots(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+}
+
+__global__ void __launch_bounds__(256) bgemv_update_kernel(const double* __restrict__ V, long long ld, int J,
+                                                           const double* __restrict__ coef, double* __restrict__ w,
+                                                           Chunks ch) {
+    extern __shared__ double cs[];
+    const double* c = coef + (long long)ch.prob[blockIdx.x] * J;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) cs[j] = c[j];
+    __syncthreads();
+    if ((int)threadIdx.x < ch.rows[blockIdx.x]) {
+        const long long r = ch.row0[blockIdx.x] + threadIdx.x;
+        w[r] = brow_update(V, ld, J, r, cs, w[r]);
+    }
+}
+
+// out[b][j] = sum over problem b's chunks of partial[c][j]
+__global__ void __launch_bounds__(256) bseg_reduce_kernel(const double* __restrict__ partial, const int* __restrict__ cbeg,
+                                                          const int* __restrict__ cend, int J, int pstride,
+                                                          double* __restrict__ out) {
+    __shared__ double red[8][33];
+    const int b = blockIdx.y;
+    const int jl = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + jl;
+    double s = 0.0;
+    if (j < J)
+        for (int c = cbeg[b] + g; c < cend[b]; c += 8) s += partial[(long long)c * pstride + j];
+    red[g][jl] = s;
+    __syncthreads();
+    if (g == 0 && j < J) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][jl];
+        out[(long long)b * J + j] = t;
+    }
+}
+
+// y = M x over a chunk (16 lanes per row) and the chunk's partial x.y
+__global__ void __launch_bounds__(256) bspmv_dot_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                                        const double* __restrict__ Mv, const double* __restrict__ x,
+                                                        double* __restrict__ y, Chunks ch,
+                                                        double* __restrict__ partial) {
+    __shared__ double red[16];
+    const long long r0 = ch.row0[blockIdx.x];
+    const int rows = ch.rows[blockIdx.x];
+    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    double d = 0.0;
+    for (int base = 0; base < BCH; base += 16) {
+        const int rl = base + grp;
+        double s = 0.0;
+        if (rl < rows) {
+            const long long row = r0 + rl;
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Mv[e] * x[col[e]];
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+        if (lane == 0 && rl < rows) {
+            const long long row = r0 + rl;
+            y[row] = s;
+            d += s * x[row];
+        }
+    }
+    if (lane == 0) red[grp] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 16; ++i) t += red[i];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// per problem: alpha[b][j] = c1[b][col] + c2[b][col], beta[b][j+1] = sqrt(sum of its chunk partials)
+__global__ void bfinalize_kernel(int P, const double* __restrict__ partial, const int* __restrict__ cbeg,
+                                 const int* __restrict__ cend, const double* __restrict__ c1,
+                                 const double* __restrict__ c2, int J, int col, int j, double* __restrict__ alpha,
+                                 double* __restrict__ beta, double* __restrict__ inv, int mstride) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= P) return;
+    double s = 0.0;
+    for (int c = cbeg[b]; c < cend[b]; ++c) s += partial[c];
+    const double bt = sqrt(fmax(s, 0.0));
+    if (j >= 0) alpha[(long long)b * mstride + j] = c1[(long long)b * J + col] + c2[(long long)b * J + col];
+    beta[(long long)b * (mstride + 1) + j + 1] = bt;
+    inv[b] = bt > 0.0 ? 1.0 / bt : 0.0;
+}
+
+__global__ void bnormalize_kernel(long long N, const int* __restrict__ prob, const double* __restrict__ inv,
+                                  const double* __restrict__ w, const double* __restrict__ Mw, double* __restrict__ v,
+                                  double* __restrict__ mv) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const double s = inv[prob[r]];
+    v[r] = w[r] * s;
+    mv[r] = Mw[r] * s;
+}
+
+// U[r][q] = sum_j V[r][j] W_b[j][q] over a chunk of problem b (W padded to qmax columns)
+__global__ void __launch_bounds__(256) bgemm_ritz_kernel(const double* __restrict__ V, long long ld, int J,
+                                                         const double* __restrict__ W, int qmax, Chunks ch,
+                                                         double* __restrict__ U, long long ldu) {
+    __shared__ double Ws[128][16];
+    const int b = ch.prob[blockIdx.x];
+    const long long r = ch.row0[blockIdx.x] + threadIdx.x;
+    const bool ok = (int)threadIdx.x < ch.rows[blockIdx.x];
+    const int i0 = blockIdx.y * 16;
+    const double* Wb = W + (long long)b * J * qmax;  // column-major J x qmax per problem
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int j0 = 0; j0 < J; j0 += 128) {
+        const int jn = min(128, J - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 128 * 16; t += blockDim.x) {
+            const int jj = t / 16, q = t % 16;
+            Ws[jj][q] = (jj < jn && i0 + q < qmax) ? Wb[(long long)(i0 + q) * J + j0 + jj] : 0.0;
+        }
+        __syncthreads();
+        if (ok)
+            for (int jj = 0; jj < jn; ++jj) {
+                const double v = V[(long long)(j0 + jj) * ld + r];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] += v * Ws[jj][q];
+            }
+    }
+    if (ok)
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (i0 + q < qmax) U[(long long)(i0 + q) * ldu + r] = acc[q];
+}
+
+// residual partial sums per (chunk, candidate q): ||K u - lam M u||^2, ||M u||^2
+__global__ void __launch_bounds__(256) bresid_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                                     const double* __restrict__ Kv, const double* __restrict__ U,
+                                                     const double* __restrict__ MU, long long ld,
+                                                     const double* __restrict__ lam, int qmax, Chunks ch,
+                                                     double* __restrict__ partial) {
+    __shared__ double sa[16], sb[16];
+    const int q = blockIdx.y;
+    const int b = ch.prob[blockIdx.x];
+    const double l = lam[(long long)b * qmax + q];
+    const double* u = U + (long long)q * ld;
+    const double* mu = MU + (long long)q * ld;
+    const long long r0 = ch.row0[blockIdx.x];
+    const int rows = ch.rows[blockIdx.x];
+    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    double sr = 0.0, sm = 0.0;
+    for (int base = 0; base < BCH; base += 16) {
+        const int rl = base + grp;
+        double s = 0.0;
+        if (rl < rows) {
+            const long long row = r0 + rl;
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Kv[e] * u[col[e]];
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+        if (lane == 0 && rl < rows) {
+            const double m = mu[r0 + rl];
+            const double rr = s - l * m;
+            sr += rr * rr;
+            sm += m * m;
+        }
+    }
+    if (lane == 0) {
+        sa[grp] = sr;
+        sb[grp] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int i = 0; i < 16; ++i) {
+            ta += sa[i];
+            tb += sb[i];
+        }
+        partial[((long long)q * gridDim.x + blockIdx.x) * 2] = ta;
+        partial[((long long)q * gridDim.x + blockIdx.x) * 2 + 1] = tb;
+    }
+}
+
+// dst column dcol[b*qmax + q] (if >= 0) of V / MV receives candidate q of
+// problem b, on that problem's rows only
+__global__ void bscatter_cols_kernel(long long N, int qmax, const int* __restrict__ prob, const int* __restrict__ dcol,
+                                     const double* __restrict__ U, const double* __restrict__ MU, long long ldu,
+                                     double* __restrict__ V, double* __restrict__ MV, long long ld) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * qmax) return;
+    const int q = (int)(t / N);
+    const long long r = t % N;
+    const int d = dcol[(long long)prob[r] * qmax + q];
+    if (d < 0) return;
+    V[(long long)d * ld + r] = U[(long long)q * ldu + r];
+    MV[(long long)d * ld + r] = MU[(long long)q * ldu + r];
+}
+
+// columns [nlock(problem), L) of V / MV are zero on each problem's rows, so
+// that a problem is orthogonalised only against its own locked vectors
+__global__ void bzero_tail_kernel(long long N, int L, const int* __restrict__ prob, const int* __restrict__ nlock,
+                                  double* __restrict__ V, double* __restrict__ MV, long long ld) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * L) return;
+    const int j = (int)(t / N);
+    const long long r = t % N;
+    if (j < nlock[prob[r]]) return;
+    V[(long long)j * ld + r] = 0.0;
+    MV[(long long)j * ld + r] = 0.0;
+}
+
+// ------------------------------------------------------------------ host side
+namespace {
+
+uint64_t bsplitmix(uint64_t& s) {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+struct BatchState {
+    riga_ctx* c;
+    int P;
+    long long N, ld;
+    int cap;
+    int nch;
+    Chunks ch;
+    DevBuf<long long> ch_row0;
+    DevBuf<int> ch_rows, ch_prob, cbeg, cend;
+    std::vector<int> h_cbeg, h_cend;
+    DevBuf<double> c1, c2, partial, ab_alpha, ab_beta, inv, W, lam, rpart;
+    DevBuf<int> dcol, nlock;
+    int mcap;
+};
+
+void bortho(BatchState& B, int J, double* w) {
+    riga_ctx* c = B.c;
+    cudaStream_t st = c->stream;
+    if (J <= 0) return;
+    PhaseScope scope(c, PH_REORTH, 4.0 * (double)B.N * J * sizeof(double));
+    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
+    dim3 rg((J + 31) / 32, B.P);
+    { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr, B.ld, J, w, B.ch, B.partial.ptr, B.cap); }
+    { count_launch(c); bseg_reduce_kernel<<<rg, 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, J, B.cap, B.c1.ptr); }
+    { count_launch(c); bupdate_gemvT_kernel<<<B.nch, 256, sm_dots + (size_t)J * sizeof(double), st>>>(
+        c->V.ptr, c->MV.ptr, B.ld, J, B.c1.ptr, w, B.ch, B.partial.ptr, B.cap); }
+    { count_launch(c); bseg_reduce_kernel<<<rg, 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, J, B.cap, B.c2.ptr); }
+    { count_launch(c); bgemv_update_kernel<<<B.nch, 256, (size_t)J * sizeof(double), st>>>(c->V.ptr, B.ld, J, B.c2.ptr, w, B.ch); }
+}
+
+// w -> M-normalised per problem into column col of V / MV; beta slot jslot+1
+void bnormalize(BatchState& B, double* w, double* Mw, int col, int jslot, int J) {
+    riga_ctx* c = B.c;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)B.N * 8.0 * 6.0);
+    { count_launch(c); bspmv_dot_kernel<<<B.nch, 256, 0, st>>>(c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, Mw, B.ch, B.partial.ptr); }
+    c->stats.n_matvec++;
+    { count_launch(c); bfinalize_kernel<<<(B.P + 127) / 128, 128, 0, st>>>(B.P, B.partial.ptr, B.cbeg.ptr, B.cend.ptr, B.c1.ptr,
+                                                                       B.c2.ptr, J, col - 1, jslot, B.ab_alpha.ptr,
+                                                                       B.ab_beta.ptr, B.inv.ptr, B.mcap); }
+    { count_launch(c); bnormalize_kernel<<<(unsigned)((B.N + 255) / 256), 256, 0, st>>>(
+        B.N, c->prob_of_pos.ptr, B.inv.ptr, w, Mw, c->V.ptr + (long long)col * B.ld, c->MV.ptr + (long long)col * B.ld); }
+}
+
+}  // namespace
+
+int factor_batch(riga_ctx* c, const std::vector<double>& sig, bool inertia_only) {
+    c->sigma_prob = sig;
+    c->sigma = sig.empty() ? 0.0 : sig[0];
+    c->precision = RIGA_FP64;
+    c->inertia_only = inertia_only;
+    const bool keep = c->factored;
+    int rc = enqueue_factor(c);
+    if (rc == RIGA_OK) rc = finish_factor(c);
+    if (inertia_only) c->factored = keep;
+    c->inertia_only = false;
+    c->stats.n_fact++;
+    return rc;
+}
+
+// The k smallest eigenvalues above sigma0 of every problem of the batch.
+// Outputs in c->batch_evals / batch_resid / batch_nconv (problem-major).
+int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
+    static const bool dbg = std::getenv("RIGA_DEBUG") != nullptr;
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    const int P = (int)S.prob_pos.size() - 1;
+    const long long N = S.N;
+    const int extra = c->opt_extra > 0 ? c->opt_extra : 2;
+    const int want = k + extra;
+    long long minN = N;
+    for (int b = 0; b < P; ++b) minN = std::min(minN, S.prob_pos[b + 1] - S.prob_pos[b]);
+    if (k < 1 || want >= minN) return set_error(c, RIGA_EINVAL, "k too large for the smallest problem of the batch");
+    const double tol_est = 1e-2 * tol, lock_tol = 0.5 * tol, gap_rel = 1e-6;
+    int m_cap = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * want, want + 60);
+    m_cap = (int)std::min<long long>(m_cap, minN - 1);
+    const int lock_cap = want + 32;
+    BatchState B;
+    B.c = c;
+    B.P = P;
+    B.N = N;
+    B.ld = N;
+    B.cap = lock_cap + m_cap + 1;
+    B.mcap = m_cap;
+    // row chunks inside problems
+    std::vector<long long> r0;
+    std::vector<int> rw, pb;
+    B.h_cbeg.assign(P, 0);
+    B.h_cend.assign(P, 0);
+    for (int b = 0; b < P; ++b) {
+        B.h_cbeg[b] = (int)r0.size();
+        for (long long r = S.prob_pos[b]; r < S.prob_pos[b + 1]; r += BCH) {
+            r0.push_back(r);
+            rw.push_back((int)std::min<long long>(BCH, S.prob_pos[b + 1] - r));
+            pb.push_back(b);
+        }
+        B.h_cend[b] = (int)r0.size();
+    }
+    B.nch = (int)r0.size();
+    RIGA_CUDA_TRY(c, B.ch_row0.upload(r0, st));
+    RIGA_CUDA_TRY(c, B.ch_rows.upload(rw, st));
+    RIGA_CUDA_TRY(c, B.ch_prob.upload(pb, st));
+    RIGA_CUDA_TRY(c, B.cbeg.upload(B.h_cbeg, st));
+    RIGA_CUDA_TRY(c, B.cend.upload(B.h_cend, st));
+    B.ch = Chunks{B.ch_row0.ptr, B.ch_rows.ptr, B.ch_prob.ptr};
+    if (c->V.alloc((size_t)N * B.cap) != cudaSuccess || c->MV.alloc((size_t)N * B.cap) != cudaSuccess)
+        return set_error(c, RIGA_ENOMEM, "batched Lanczos basis");
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->V.ptr, 0, (size_t)N * B.cap * sizeof(double), st));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->MV.ptr, 0, (size_t)N * B.cap * sizeof(double), st));
+    RIGA_CUDA_TRY(c, B.partial.alloc((size_t)B.nch * B.cap));
+    RIGA_CUDA_TRY(c, B.c1.alloc((size_t)P * B.cap));
+    RIGA_CUDA_TRY(c, B.c2.alloc((size_t)P * B.cap));
+    RIGA_CUDA_TRY(c, B.ab_alpha.alloc((size_t)P * m_cap));
+    RIGA_CUDA_TRY(c, B.ab_beta.alloc((size_t)P * (m_cap + 1)));
+    RIGA_CUDA_TRY(c, B.inv.alloc(P));
+    RIGA_CUDA_TRY(c, B.dcol.alloc((size_t)P * want));
+    for (int i = 0; i < 2; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bgemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dots));
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_gemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sm_dots + (size_t)B.cap * sizeof(double))));
+    double* w = c->vwork[0].ptr;
+    double* Mw = c->vwork[1].ptr;
+    c->stats = Stats();
+
+    // per-problem state
+    std::vector<std::vector<double>> lam(P), res(P);
+    std::vector<int> nlock(P, 0);
+    std::vector<char> done(P, 0);
+    std::vector<int> need(P, want);
+    std::vector<double> sig0(P, sigma0);
+    int rc = factor_batch(c, sig0, false);
+    if (rc) return rc;
+    std::vector<long long> nu0 = c->inertia_prob;
+    uint64_t seed = c->opt_seed ? c->opt_seed : 1;
+    std::vector<double> h_alpha, h_beta, theta, zl, Zf, hv(N);
+    int status = RIGA_OK;
+    for (int run = 1; run <= 4; ++run) {
+        int active = 0;
+        for (int b = 0; b < P; ++b) active += !done[b];
+        if (active == 0) break;
+        int Lmax = 0;
+        for (int b = 0; b < P; ++b) Lmax = std::max(Lmax, nlock[b]);
+        int maxw = 1;
+        for (int b = 0; b < P; ++b)
+            if (!done[b]) maxw = std::max(maxw, need[b] - nlock[b]);
+        int m_max = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * maxw, maxw + 60);
+        m_max = std::min(m_max, m_cap);
+        if (Lmax + m_max + 1 > B.cap) m_max = B.cap - Lmax - 1;
+        if (m_max < 1) {
+            status = RIGA_ENOCONV;
+            break;
+        }
+        const int col0 = Lmax;
+        if (Lmax > 0) {
+            RIGA_CUDA_TRY(c, B.nlock.upload(nlock, st));
+            { count_launch(c); bzero_tail_kernel<<<(unsigned)((N * Lmax + 255) / 256), 256, 0, st>>>(
+                N, Lmax, c->prob_of_pos.ptr, B.nlock.ptr, c->V.ptr, c->MV.ptr, B.ld); }
+        }
+        // start vectors: random on active problems, zero on the others
+        for (int b = 0; b < P; ++b)
+            for (long long r = S.prob_pos[b]; r < S.prob_pos[b + 1]; ++r)
+                hv[r] = done[b] ? 0.0 : ((double)(bsplitmix(seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (Lmax > 0) bortho(B, Lmax, w);
+        bnormalize(B, w, Mw, col0, -1, Lmax > 0 ? Lmax : 1);
+        int m = 0;
+        for (int j = 0; j < m_max; ++j) {
+            const int col = col0 + j;
+            RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, c->MV.ptr + (long long)col * B.ld, N * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, st));
+            rc = enqueue_solve(c, w);
+            if (rc) {
+                status = rc;
+                break;
+            }
+            bortho(B, col + 1, w);
+            bnormalize(B, w, Mw, col + 1, j, col + 1);
+            c->stats.steps++;
+            m = j + 1;
+            if (m % 10 == 0 || m == m_max) {
+                h_alpha.resize((size_t)P * m_cap);
+                h_beta.resize((size_t)P * (m_cap + 1));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_alpha.data(), B.ab_alpha.ptr, h_alpha.size() * sizeof(double),
+                                                 cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_beta.data(), B.ab_beta.ptr, h_beta.size() * sizeof(double),
+                                                 cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+                bool all = true;
+                for (int b = 0; b < P && all; ++b) {
+                    if (done[b]) continue;
+                    const double* a = h_alpha.data() + (size_t)b * m_cap;
+                    const double* bt = h_beta.data() + (size_t)b * (m_cap + 1);
+                    theta.assign(m, 0.0);
+                    zl.assign(m, 0.0);
+                    tridiag_eig(m, a, bt + 1, theta.data(), zl.data(), false);
+                    const int wb = need[b] - nlock[b];
+                    int ok = 0;
+                    for (int i = m - 1; i >= 0 && ok < wb; --i) {
+                        if (!(theta[i] > 0.0)) break;
+                        if (std::fabs(bt[m] * zl[i]) <= tol_est * theta[i]) ++ok;
+                        else break;
+                    }
+                    if (ok < wb && bt[m] > 1e-300) all = false;
+                }
+                if (all) break;
+            }
+        }
+        if (status) break;
+        // Rayleigh-Ritz per problem, candidates = converged largest theta
+        h_alpha.resize((size_t)P * m_cap);
+        h_beta.resize((size_t)P * (m_cap + 1));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_alpha.data(), B.ab_alpha.ptr, h_alpha.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_beta.data(), B.ab_beta.ptr, h_beta.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        const int qmax = want;
+        std::vector<double> hW((size_t)P * m * qmax, 0.0), hl((size_t)P * qmax, 0.0);
+        std::vector<int> nsel(P, 0);
+        for (int b = 0; b < P; ++b) {
+            if (done[b]) continue;
+            const double* a = h_alpha.data() + (size_t)b * m_cap;
+            const double* bt = h_beta.data() + (size_t)b * (m_cap + 1);
+            theta.assign(m, 0.0);
+            Zf.assign((size_t)m * m, 0.0);
+            tridiag_eig(m, a, bt + 1, theta.data(), Zf.data(), true);
+            const int room = std::min(qmax, lock_cap - nlock[b]);
+            for (int i = m - 1; i >= 0 && nsel[b] < room; --i) {
+                if (!(theta[i] > 0.0)) break;
+                if (std::fabs(bt[m] * Zf[(size_t)i * m + m - 1]) > tol_est * theta[i]) continue;
+                const int q = nsel[b]++;
+                for (int r = 0; r < m; ++r) hW[((size_t)b * qmax + q) * m + r] = Zf[(size_t)i * m + r];
+                hl[(size_t)b * qmax + q] = sigma0 + 1.0 / theta[i];
+            }
+        }
+        RIGA_CUDA_TRY(c, B.W.upload(hW, st));
+        RIGA_CUDA_TRY(c, B.lam.upload(hl, st));
+        RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * qmax * 2));
+        double* U = c->evec_perm.ptr;
+        double* MU = c->evec_perm.ptr + (size_t)N * qmax;
+        {
+            PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * qmax) * sizeof(double));
+            dim3 g(B.nch, (qmax + 15) / 16);
+            { count_launch(c); bgemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, U, N); }
+            { count_launch(c); bgemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, MU, N); }
+            RIGA_CUDA_TRY(c, B.rpart.alloc((size_t)2 * B.nch * qmax));
+            { count_launch(c); bresid_kernel<<<dim3(B.nch, qmax), 256, 0, st>>>(c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N,
+                                                                               B.lam.ptr, qmax, B.ch, B.rpart.ptr); }
+        }
+        std::vector<double> part((size_t)2 * B.nch * qmax);
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), B.rpart.ptr, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        std::vector<int> dcol((size_t)P * qmax, -1);
+        for (int b = 0; b < P; ++b) {
+            for (int q = 0; q < nsel[b]; ++q) {
+                double ra = 0.0, rb = 0.0;
+                for (int cc = B.h_cbeg[b]; cc < B.h_cend[b]; ++cc) {
+                    ra += part[((size_t)q * B.nch + cc) * 2];
+                    rb += part[((size_t)q * B.nch + cc) * 2 + 1];
+                }
+                const double l = hl[(size_t)b * qmax + q];
+                const double rho = std::sqrt(ra) / (std::fabs(l) * std::sqrt(rb));
+                if (!(rho <= lock_tol)) continue;
+                dcol[(size_t)b * qmax + q] = nlock[b];
+                lam[b].push_back(l);
+                res[b].push_back(rho);
+                ++nlock[b];
+            }
+        }
+        RIGA_CUDA_TRY(c, B.dcol.upload(dcol, st));
+        { count_launch(c); bscatter_cols_kernel<<<(unsigned)((N * qmax + 255) / 256), 256, 0, st>>>(
+            N, qmax, c->prob_of_pos.ptr, B.dcol.ptr, U, MU, N, c->V.ptr, c->MV.ptr, B.ld); }
+        // completeness per problem: check shift in a gap after the k-th eigenvalue
+        std::vector<double> sig_chk(P, sigma0);
+        std::vector<int> gi(P, -1);
+        int checks = 0;
+        for (int b = 0; b < P; ++b) {
+            if (done[b]) continue;
+            std::vector<double> sl(lam[b]);
+            std::sort(sl.begin(), sl.end());
+            for (int i = k; i < (int)sl.size(); ++i)
+                if (sl[i] - sl[i - 1] > gap_rel * std::fabs(sl[i])) {
+                    gi[b] = i;
+                    break;
+                }
+            if (gi[b] < 0) {
+                need[b] = nlock[b] + extra;
+                continue;
+            }
+            sig_chk[b] = 0.5 * (sl[gi[b] - 1] + sl[gi[b]]);
+            ++checks;
+        }
+        if (checks > 0) {
+            rc = factor_batch(c, sig_chk, true);
+            if (rc) {
+                status = rc;
+                break;
+            }
+            for (int b = 0; b < P; ++b) {
+                if (done[b] || gi[b] < 0) continue;
+                const long long inside = c->inertia_prob[b] - nu0[b];
+                if (inside == gi[b]) done[b] = 1;
+                else if (inside > gi[b]) need[b] = nlock[b] + (int)(inside - gi[b]);
+                else status = set_error(c, RIGA_ENOCONV, "more locked pairs than the inertia allows");
+            }
+        }
+        int nd = 0;
+        for (int b = 0; b < P; ++b) nd += done[b];
+        if (dbg) std::fprintf(stderr, "[riga] batch run %d: steps=%d, problems complete %d/%d\n", run, m, nd, P);
+        if (status) break;
+    }
+    // outputs: the k smallest locked eigenvalues per problem
+    c->batch_evals.assign((size_t)P * k, std::nan(""));
+    c->batch_resid.assign((size_t)P * k, std::nan(""));
+    c->batch_nconv.assign(P, 0);
+    bool all_done = true;
+    for (int b = 0; b < P; ++b) {
+        std::vector<int> ord(lam[b].size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int x, int y) { return lam[b][x] < lam[b][y]; });
+        const int nout = done[b] ? std::min(k, (int)ord.size()) : 0;
+        for (int q = 0; q < nout; ++q) {
+            c->batch_evals[(size_t)b * k + q] = lam[b][ord[q]];
+            c->batch_resid[(size_t)b * k + q] = res[b][ord[q]];
+        }
+        c->batch_nconv[b] = nout;
+        all_done = all_done && done[b] && nout == k;
+    }
+    if (status) return status;
+    if (!all_done) return set_error(c, RIGA_ENOCONV, "some problems of the batch did not converge");
+    return RIGA_OK;
+}
+
+}  // namespace riga
+
+using namespace riga;
+
+extern "C" int riga_assemble_batch(riga_ctx* c, int nprob, const riga_mesh* meshes, const double* const* coefK,
+                                   const double* const* coefM) {
+    if (!c || nprob < 1 || !meshes) return RIGA_EINVAL;
+    c->last_error.clear();
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    cudaSetDevice(c->device);
+    c->assembled = false;
+    c->factored = false;
+    c->nev = 0;
+    c->mesh_key.clear();
+    c->probs.assign(nprob, Symbolic());
+    for (int b = 0; b < nprob; ++b) {
+        const riga_mesh* m = &meshes[b];
+        if (m->dim < 1 || m->dim > 3 || m->dirichlet != 1 || m->p < 1 || m->p > 6 || m->leaf_extent < 0)
+            return set_error(c, RIGA_EINVAL, "bad mesh in the batch");
+        std::string err = build_symbolic(c->probs[b], m->dim, m->ne, m->p, m->mult, m->leaf_extent);
+        if (!err.empty()) return set_error(c, RIGA_EINVAL, "problem " + std::to_string(b) + ": " + err);
+    }
+    std::string err = merge_symbolic(c->S, c->probs);
+    if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
+    int rc = upload_symbolic(c);
+    if (rc) return rc;
+    // coefficients: host pointers, concatenated (NULL per problem = ones)
+    bool anyK = false, anyM = false;
+    for (int b = 0; b < nprob; ++b) {
+        anyK = anyK || (coefK && coefK[b]);
+        anyM = anyM || (coefM && coefM[b]);
+    }
+    c->coefK.clear();
+    c->coefM.clear();
+    if (anyK) c->coefK.assign(c->S.n_elem, 1.0);
+    if (anyM) c->coefM.assign(c->S.n_elem, 1.0);
+    for (int b = 0; b < nprob; ++b) {
+        const long long e0 = c->S.prob_elem[b], ne = c->probs[b].n_elem;
+        for (long long e = 0; e < ne; ++e) {
+            if (anyK && coefK[b]) {
+                if (!(coefK[b][e] > 0.0) || !std::isfinite(coefK[b][e])) return set_error(c, RIGA_EINVAL, "coefK must be positive");
+                c->coefK[e0 + e] = coefK[b][e];
+            }
+            if (anyM && coefM[b]) {
+                if (!(coefM[b][e] > 0.0) || !std::isfinite(coefM[b][e])) return set_error(c, RIGA_EINVAL, "coefM must be positive");
+                c->coefM[e0 + e] = coefM[b][e];
+            }
+        }
+    }
+    rc = assemble_device(c);
+    if (rc) return rc;
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->assembled = true;
+    return RIGA_OK;
+}
+
+extern "C" int riga_eigs_batch(riga_ctx* c, int k, double sigma, double tol, double* evals, double* resid, int* nconv) {
+    if (!c || !evals) return RIGA_EINVAL;
+    c->last_error.clear();
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    cudaSetDevice(c->device);
+    if (!c->assembled || c->S.dim != 0) return set_error(c, RIGA_ESTATE, "riga_assemble_batch first");
+    if (!(tol > 0.0) || !std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "bad tol or sigma");
+    int status = run_eigs_batch(c, k, sigma, tol);
+    if (status != RIGA_OK && status != RIGA_ENOCONV) return status;
+    const size_t P = c->batch_nconv.size();
+    std::copy(c->batch_evals.begin(), c->batch_evals.end(), evals);
+    if (resid) std::copy(c->batch_resid.begin(), c->batch_resid.end(), resid);
+    if (nconv) std::copy(c->batch_nconv.begin(), c->batch_nconv.end(), nconv);
+    (void)P;
+    return status;
+}

@@ -75,8 +75,10 @@ struct riga_ctx {
     bool analyzed_only = false;
     bool factored = false;
     std::vector<int> mesh_key;
-    riga::Symbolic S;
-    std::vector<double> coefK, coefM;  // host copies (empty = constant)
+    riga::Symbolic S;                  // the problem, or the merged forest of a batch
+    std::vector<riga::Symbolic> probs; // batch: the problems (1D data, sizes)
+    std::vector<double> coefK, coefM;  // host copies (empty = constant); batch: concatenated
+    std::vector<double> sigma_prob;    // batch: per-problem shifts of the next factorization (empty = sigma)
 
     // symbolic arrays on the device
     riga::DevBuf<riga::SolveItem> sitems;
@@ -106,7 +108,10 @@ struct riga_ctx {
     riga::DevBuf<float> q32;
     riga::DevBuf<double> D;      // pivots in elimination order
     riga::DevBuf<int> flag;      // device error word (bit 0: pivot breakdown)
-    riga::DevBuf<long long> neg; // inertia counter
+    riga::DevBuf<long long> neg; // inertia counter(s): one, or one per problem of a batch
+    riga::DevBuf<int> prob_of_pos;  // batch: problem of each position
+    riga::DevBuf<double> sig_pos;   // batch: shift of each position's problem
+    std::vector<long long> inertia_prob;  // batch: inertia per problem
     long long inertia = -1;
 
     // ---------------------------------------------------------------- solve
@@ -133,6 +138,8 @@ struct riga_ctx {
     riga::DevBuf<double> Wd;           // Ritz coefficient matrix
     riga::DevBuf<double> evec_perm;    // final eigenvectors, permuted order, N x nev
     std::vector<double> evals;         // final eigenvalues
+    std::vector<double> batch_evals, batch_resid;  // batch: k per problem, problem-major
+    std::vector<int> batch_nconv;
     int nev = 0;
     riga::Stats stats;
     riga::Profile prof;
@@ -182,6 +189,8 @@ struct PhaseScope {
     }
 };
 
+// api.cu
+int upload_symbolic(riga_ctx* c);  // symbolic arrays of c->S to the device
 // assemble.cu
 int assemble_device(riga_ctx* c);
 // factor.cu
@@ -195,6 +204,8 @@ int solve_refined(riga_ctx* c, double* y, double* work_x, double* work_r, double
                   int check, int* sweeps_out);
 // lanczos.cu
 int run_eigs(riga_ctx* c, int k, double sigma, double tol, int* nconv);
+// batch.cu
+int run_eigs_batch(riga_ctx* c, int k, double sigma, double tol);
 // adjoint.cu
 int eig_grad_device(riga_ctx* c, int k, const double* w_dev, double* ga_dev, double* gb_dev);
 // tridiag.cpp

@@ -36,6 +36,30 @@ __global__ void scatter_kernel(long long nnz, const long long* __restrict__ scat
     if (off >= 0) pool[off] = (T)(K[e] - sigma * M[e]);
 }
 
+// batch: per-position shifts (each problem of the forest has its own sigma);
+// one warp per row, entry (i, j) with j <= i shares row i's problem
+template <typename T>
+__global__ void scatter_rows_kernel(long long N, const long long* __restrict__ rowptr,
+                                    const long long* __restrict__ scatter, const double* __restrict__ K,
+                                    const double* __restrict__ M, const double* __restrict__ sig_pos,
+                                    T* __restrict__ pool) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= N) return;
+    const double sg = sig_pos[row];
+    for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+        const long long off = scatter[e];
+        if (off >= 0) pool[off] = (T)(K[e] - sg * M[e]);
+    }
+}
+
+// batch: negative pivots per problem
+__global__ void inertia_prob_kernel(long long N, const double* __restrict__ D, const int* __restrict__ prob,
+                                    long long* __restrict__ neg) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        if (D[i] < 0.0) atomicAdd((unsigned long long*)&neg[prob[i]], 1ULL);
+}
+
 template <typename T>
 __global__ void identity_kernel(int F, const int* __restrict__ kk, const int* __restrict__ nn,
                                 const long long* __restrict__ front_off, T* __restrict__ pool) {
@@ -252,9 +276,18 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
     const int plain = c->inertia_only ? 1 : 0;
     if (!plain) { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
-    if (S.nnz > 0)
+    const bool per_problem = (S.dim == 0) && !c->sigma_prob.empty();
+    if (per_problem) {
+        std::vector<double> sp(S.N);
+        for (size_t b = 0; b + 1 < S.prob_pos.size(); ++b)
+            for (long long i = S.prob_pos[b]; i < S.prob_pos[b + 1]; ++i) sp[i] = c->sigma_prob[b];
+        RIGA_CUDA_TRY(c, c->sig_pos.upload(sp, st));
+        { count_launch(c); scatter_rows_kernel<T><<<(unsigned)((S.N * 32 + 255) / 256), 256, 0, st>>>(
+            S.N, c->rowptr.ptr, c->scatter.ptr, c->Kval.ptr, c->Mval.ptr, c->sig_pos.ptr, pool); }
+    } else if (S.nnz > 0) {
         { count_launch(c); scatter_kernel<T><<<(unsigned)((S.nnz + 255) / 256), 256, 0, st>>>(S.nnz, c->scatter.ptr, c->Kval.ptr,
                                                                           c->Mval.ptr, c->sigma, pool); }
+    }
     for (int l = 0; l < S.n_levels; ++l) {
         const LevelPlan& P = S.levels[l];
         for (int rank = 0; rank < 2; ++rank) {
@@ -284,6 +317,11 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
                                                                                       c->kk.ptr, c->nn.ptr, c->front_off.ptr,
                                                                                       pool, Q); }
     { count_launch(c); inertia_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->neg.ptr); }
+    if (S.dim == 0) {
+        const size_t np = S.prob_pos.size() - 1;
+        RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr + 1, 0, np * sizeof(long long), st));
+        { count_launch(c); inertia_prob_kernel<<<152, 256, 0, st>>>(S.N, c->D.ptr, c->prob_of_pos.ptr, c->neg.ptr + 1); }
+    }
     RIGA_CUDA_TRY(c, cudaGetLastError());
     return RIGA_OK;
 }
@@ -293,7 +331,7 @@ int enqueue_factor(riga_ctx* c) {
     if (S.nb != NB || S.tile != TILE || S.rowblk != RB) return set_error(c, RIGA_EINVAL, "schedule/kernel tile mismatch");
     RIGA_CUDA_TRY(c, c->D.alloc(S.N));
     RIGA_CUDA_TRY(c, c->flag.alloc(1));
-    RIGA_CUDA_TRY(c, c->neg.alloc(1));
+    RIGA_CUDA_TRY(c, c->neg.alloc(S.dim == 0 ? S.prob_pos.size() : 1));
     if (c->precision == RIGA_FP64) {
         if (c->pool64.alloc(S.pool_size) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "front pool (fp64)");
         if (c->q64.alloc(S.q_size + 4) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "solve operators (fp64)");
@@ -309,6 +347,11 @@ int finish_factor(riga_ctx* c) {
     long long neg = 0;
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(&neg, c->neg.ptr, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    if (c->S.dim == 0) {
+        c->inertia_prob.assign(c->S.prob_pos.size() - 1, 0);
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->inertia_prob.data(), c->neg.ptr + 1, c->inertia_prob.size() * sizeof(long long),
+                                         cudaMemcpyDeviceToHost, c->stream));
+    }
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->inertia = neg;
     if (flag & 1) {

@@ -87,6 +87,150 @@ struct Box {
 };
 }  // namespace
 
+
+// Heights, counts, factorization schedule and tree-solve items of a
+// (possibly merged) symbolic structure whose nodes, fronts and maps are set.
+std::string finish_symbolic(Symbolic& S) {
+    const int F = S.n_nodes;
+    // heights and counts
+    S.height.assign(F, 0);
+    int maxh = 0;
+    for (int f = 0; f < F; ++f) {
+        int h = 0;
+        for (int ci = S.child_ptr[f]; ci < S.child_ptr[f + 1]; ++ci)
+            h = std::max(h, S.height[S.child_list[ci]] + 1);
+        S.height[f] = h;
+        maxh = std::max(maxh, h);
+    }
+    S.n_levels = maxh + 1;
+    S.nnzL = 0;
+    S.nnzQ = 0;
+    S.nnzL_own2 = 0;
+    S.flops = 0.0;
+    S.flops_aug = 0.0;
+    for (int f = 0; f < F; ++f) {
+        long long kk = S.k[f], nn = S.n[f];
+        S.nnzL += kk * (kk + 1) / 2 + kk * (nn - kk);
+        S.nnzQ += kk * nn;
+        S.nnzL_own2 += kk * kk;
+        for (long long i = 0; i < kk; ++i) {
+            S.flops += (double)(nn - i) * (double)(nn - i - 1);
+            S.flops_aug += (double)(nn + kk - i) * (double)(nn + kk - i - 1) - (double)(nn - i) * (double)(nn - i - 1);
+        }
+    }
+
+    // ------------------------------------------------------- solve items
+    // parts of about SOLVE_PART_FMA multiply-adds each (up to 32 per sweep)
+    const long long SOLVE_PART_FMA = 12288;
+    S.parts_f.assign(F, 1);
+    S.parts_b.assign(F, 1);
+    for (int f = 0; f < F; ++f) {
+        const long long kk = S.k[f], mm = S.n[f] - S.k[f], nn = S.n[f];
+        long long pf = (kk * mm + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
+        pf = std::max(1LL, std::min({pf, 32LL, std::max(1LL, mm)}));
+        pf = std::max(pf, (mm + 2047) / 2048);  // at most 2048 columns per part
+        long long pb = (kk * nn + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
+        pb = std::max(1LL, std::min({pb, 32LL, std::max(1LL, kk / 8)}));
+        pb = std::max(pb, (kk + 2047) / 2048);  // at most 2048 rows per part
+        if (pf > 64 || pb > 64) return "front too large for the tree solve";
+        S.parts_f[f] = (int)pf;
+        S.parts_b[f] = (int)pb;
+    }
+    {
+        std::vector<int> byh(F);
+        for (int f = 0; f < F; ++f) byh[f] = f;
+        std::stable_sort(byh.begin(), byh.end(), [&](int a, int b) { return S.height[a] < S.height[b]; });
+        S.sitems.clear();
+        S.qitems.clear();
+        long long off = 0;
+        auto add = [&](int f, int lo, int hi, long long elems_per_ld_unit, bool) {
+            SolveItem it;
+            it.front = f;
+            it.lo = lo;
+            it.hi = hi;
+            it.ldp = std::max(4, (hi - lo + 3) / 4 * 4);
+            it.off = off;
+            const long long cnt = (long long)it.ldp * elems_per_ld_unit;
+            const int idx = (int)S.sitems.size();
+            for (long long e0 = 0; e0 < cnt; e0 += 4096) S.qitems.push_back({idx, (int)e0});
+            off += cnt;
+            S.sitems.push_back(it);
+        };
+        for (int f : byh) {  // forward, ascending height
+            const int kk = S.k[f], mm = S.n[f] - S.k[f], P = S.parts_f[f];
+            for (int q = 0; q < P; ++q)
+                add(f, kk + (int)((long long)mm * q / P), kk + (int)((long long)mm * (q + 1) / P), kk, true);
+        }
+        S.n_fwd_items = (int)S.sitems.size();
+        for (int i = F - 1; i >= 0; --i) {  // backward, descending height
+            const int f = byh[i], kk = S.k[f], P = S.parts_b[f];
+            for (int q = 0; q < P; ++q)
+                add(f, (int)((long long)kk * q / P), (int)((long long)kk * (q + 1) / P), S.n[f], false);
+        }
+        S.q_size = off;
+    }
+
+    // ---------------------------------------------------- level schedule
+    S.levels.assign(S.n_levels, LevelPlan());
+    for (int f = 0; f < F; ++f) S.levels[S.height[f]].nodes.push_back(f);
+    S.pitems.clear();
+    S.titems.clear();
+    S.eitems.clear();
+    const int nb = S.nb, tile = S.tile, rb = S.rowblk;
+    const int ext_cols = 32;
+    for (int l = 0; l < S.n_levels; ++l) {
+        LevelPlan& P = S.levels[l];
+        for (int f : P.nodes) {
+            P.max_n = std::max(P.max_n, S.n[f]);
+            P.max_k = std::max(P.max_k, S.k[f]);
+        }
+        for (int rank = 0; rank < 2; ++rank) {
+            P.ext_begin[rank] = (int)S.eitems.size();
+            for (int f : P.nodes) {
+                int nc = S.child_ptr[f + 1] - S.child_ptr[f];
+                if (rank >= nc) continue;
+                int c = S.child_list[S.child_ptr[f] + rank];
+                int m = S.n[c] - S.k[c];
+                for (int c0 = 0; c0 < m; c0 += ext_cols)
+                    S.eitems.push_back({c, c0, std::min(m, c0 + ext_cols)});
+            }
+            P.ext_end[rank] = (int)S.eitems.size();
+        }
+        for (int s = 0; s * nb < P.max_k; ++s) {
+            StepRange R;
+            R.s = s;
+            R.d_begin = (int)S.pitems.size();
+            for (int f : P.nodes)
+                if (S.k[f] > s * nb) S.pitems.push_back({f, s * nb});
+            R.d_end = (int)S.pitems.size();
+            R.p_begin = (int)S.pitems.size();
+            R.t_begin = (int)S.titems.size();
+            for (int f : P.nodes) {
+                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
+                if (kf <= s * nb) continue;
+                int kb = std::min(nb, kf - s * nb);
+                for (int r0 = s * nb + kb; r0 < lf; r0 += rb) S.pitems.push_back({f, r0});
+                int c0 = s * nb + kb;
+                // trailing update: lower tiles of the augmented front, plus the
+                // upper tiles of the extra x extra block so that -A11^{-1} is
+                // stored in full
+                int T = (lf - c0 + tile - 1) / tile;
+                for (int bi = 0; bi < T; ++bi)
+                    for (int bj = 0; bj < T; ++bj) {
+                        int i0 = c0 + bi * tile, j0 = c0 + bj * tile;
+                        bool lower = bj <= bi;
+                        bool extra_upper = (i0 + tile > nf) && (j0 + tile > nf);
+                        if (lower || extra_upper) S.titems.push_back({f, i0, j0});
+                    }
+            }
+            R.p_end = (int)S.pitems.size();
+            R.t_end = (int)S.titems.size();
+            P.steps.push_back(R);
+        }
+    }
+    return "";
+}
+
 std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int* const* mult,
                            int leaf_extent) {
     if (dim < 1 || dim > 3) return "dim must be 1, 2 or 3";
@@ -336,143 +480,101 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
 
     // (solve items are built after the heights, below)
 
-    // heights and counts
-    S.height.assign(F, 0);
-    int maxh = 0;
-    for (int f = 0; f < F; ++f) {
-        int h = 0;
-        for (int ci = S.child_ptr[f]; ci < S.child_ptr[f + 1]; ++ci)
-            h = std::max(h, S.height[S.child_list[ci]] + 1);
-        S.height[f] = h;
-        maxh = std::max(maxh, h);
-    }
-    S.n_levels = maxh + 1;
-    S.nnzL = 0;
-    S.nnzQ = 0;
-    S.nnzL_own2 = 0;
-    S.flops = 0.0;
-    S.flops_aug = 0.0;
-    for (int f = 0; f < F; ++f) {
-        long long kk = S.k[f], nn = S.n[f];
-        S.nnzL += kk * (kk + 1) / 2 + kk * (nn - kk);
-        S.nnzQ += kk * nn;
-        S.nnzL_own2 += kk * kk;
-        for (long long i = 0; i < kk; ++i) {
-            S.flops += (double)(nn - i) * (double)(nn - i - 1);
-            S.flops_aug += (double)(nn + kk - i) * (double)(nn + kk - i - 1) - (double)(nn - i) * (double)(nn - i - 1);
-        }
-    }
+    return finish_symbolic(S);
+}
 
-    // ------------------------------------------------------- solve items
-    // parts of about SOLVE_PART_FMA multiply-adds each (up to 32 per sweep)
-    const long long SOLVE_PART_FMA = 12288;
-    S.parts_f.assign(F, 1);
-    S.parts_b.assign(F, 1);
-    for (int f = 0; f < F; ++f) {
-        const long long kk = S.k[f], mm = S.n[f] - S.k[f], nn = S.n[f];
-        long long pf = (kk * mm + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
-        pf = std::max(1LL, std::min({pf, 32LL, std::max(1LL, mm)}));
-        pf = std::max(pf, (mm + 2047) / 2048);  // at most 2048 columns per part
-        long long pb = (kk * nn + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
-        pb = std::max(1LL, std::min({pb, 32LL, std::max(1LL, kk / 8)}));
-        pb = std::max(pb, (kk + 2047) / 2048);  // at most 2048 rows per part
-        if (pf > 64 || pb > 64) return "front too large for the tree solve";
-        S.parts_f[f] = (int)pf;
-        S.parts_b[f] = (int)pb;
-    }
-    {
-        std::vector<int> byh(F);
-        for (int f = 0; f < F; ++f) byh[f] = f;
-        std::stable_sort(byh.begin(), byh.end(), [&](int a, int b) { return S.height[a] < S.height[b]; });
-        S.sitems.clear();
-        S.qitems.clear();
-        long long off = 0;
-        auto add = [&](int f, int lo, int hi, long long elems_per_ld_unit, bool) {
-            SolveItem it;
-            it.front = f;
-            it.lo = lo;
-            it.hi = hi;
-            it.ldp = std::max(4, (hi - lo + 3) / 4 * 4);
-            it.off = off;
-            const long long cnt = (long long)it.ldp * elems_per_ld_unit;
-            const int idx = (int)S.sitems.size();
-            for (long long e0 = 0; e0 < cnt; e0 += 4096) S.qitems.push_back({idx, (int)e0});
-            off += cnt;
-            S.sitems.push_back(it);
-        };
-        for (int f : byh) {  // forward, ascending height
-            const int kk = S.k[f], mm = S.n[f] - S.k[f], P = S.parts_f[f];
-            for (int q = 0; q < P; ++q)
-                add(f, kk + (int)((long long)mm * q / P), kk + (int)((long long)mm * (q + 1) / P), kk, true);
-        }
-        S.n_fwd_items = (int)S.sitems.size();
-        for (int i = F - 1; i >= 0; --i) {  // backward, descending height
-            const int f = byh[i], kk = S.k[f], P = S.parts_b[f];
-            for (int q = 0; q < P; ++q)
-                add(f, (int)((long long)kk * q / P), (int)((long long)kk * (q + 1) / P), S.n[f], false);
-        }
-        S.q_size = off;
-    }
 
-    // ---------------------------------------------------- level schedule
-    S.levels.assign(S.n_levels, LevelPlan());
-    for (int f = 0; f < F; ++f) S.levels[S.height[f]].nodes.push_back(f);
-    S.pitems.clear();
-    S.titems.clear();
-    S.eitems.clear();
-    const int nb = S.nb, tile = S.tile, rb = S.rowblk;
-    const int ext_cols = 32;
-    for (int l = 0; l < S.n_levels; ++l) {
-        LevelPlan& P = S.levels[l];
-        for (int f : P.nodes) {
-            P.max_n = std::max(P.max_n, S.n[f]);
-            P.max_k = std::max(P.max_k, S.k[f]);
-        }
-        for (int rank = 0; rank < 2; ++rank) {
-            P.ext_begin[rank] = (int)S.eitems.size();
-            for (int f : P.nodes) {
-                int nc = S.child_ptr[f + 1] - S.child_ptr[f];
-                if (rank >= nc) continue;
-                int c = S.child_list[S.child_ptr[f] + rank];
-                int m = S.n[c] - S.k[c];
-                for (int c0 = 0; c0 < m; c0 += ext_cols)
-                    S.eitems.push_back({c, c0, std::min(m, c0 + ext_cols)});
-            }
-            P.ext_end[rank] = (int)S.eitems.size();
-        }
-        for (int s = 0; s * nb < P.max_k; ++s) {
-            StepRange R;
-            R.s = s;
-            R.d_begin = (int)S.pitems.size();
-            for (int f : P.nodes)
-                if (S.k[f] > s * nb) S.pitems.push_back({f, s * nb});
-            R.d_end = (int)S.pitems.size();
-            R.p_begin = (int)S.pitems.size();
-            R.t_begin = (int)S.titems.size();
-            for (int f : P.nodes) {
-                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
-                if (kf <= s * nb) continue;
-                int kb = std::min(nb, kf - s * nb);
-                for (int r0 = s * nb + kb; r0 < lf; r0 += rb) S.pitems.push_back({f, r0});
-                int c0 = s * nb + kb;
-                // trailing update: lower tiles of the augmented front, plus the
-                // upper tiles of the extra x extra block so that -A11^{-1} is
-                // stored in full
-                int T = (lf - c0 + tile - 1) / tile;
-                for (int bi = 0; bi < T; ++bi)
-                    for (int bj = 0; bj < T; ++bj) {
-                        int i0 = c0 + bi * tile, j0 = c0 + bj * tile;
-                        bool lower = bj <= bi;
-                        bool extra_upper = (i0 + tile > nf) && (j0 + tile > nf);
-                        if (lower || extra_upper) S.titems.push_back({f, i0, j0});
-                    }
-            }
-            R.p_end = (int)S.pitems.size();
-            R.t_end = (int)S.titems.size();
-            P.steps.push_back(R);
-        }
+// Concatenates independent problems into one forest: positions, DOFs, nodes,
+// CSR entries, fronts and maps are offset per problem; the schedule and the
+// solve items are then built for the whole forest (one launch per level and
+// one persistent solve serve every problem).
+std::string merge_symbolic(Symbolic& M, const std::vector<Symbolic>& P) {
+    M = Symbolic();
+    M.dim = 0;  // a batch: per-problem data stay in P
+    long long N = 0, nnz = 0, pool = 0, fpos = 0, rel = 0, upd = 0, nel = 0;
+    int F = 0, nch = 0;
+    for (const Symbolic& S : P) {
+        N += S.N;
+        nnz += S.nnz;
+        F += S.n_nodes;
     }
-    return "";
+    if (N > 2000000000LL) return "batch too large for 32-bit DOF indices";
+    M.N = N;
+    M.nnz = nnz;
+    M.n_nodes = F;
+    M.perm.reserve(N);
+    M.ipos.reserve(N);
+    M.node_of.reserve(N);
+    M.rowptr.assign(1, 0);
+    M.glob_rowptr.assign(1, 0);
+    M.node_ptr.clear();
+    M.front_ptr.clear();
+    M.child_ptr.clear();
+    M.rel_ptr.clear();
+    M.upd_off.clear();
+    M.front_off.clear();
+    long long pos0 = 0;
+    int node0 = 0;
+    for (const Symbolic& S : P) {
+        M.prob_pos.push_back(pos0);
+        M.prob_nnz.push_back(M.col.size());
+        M.prob_elem.push_back(nel);
+        M.prob_node.push_back(node0);
+        for (int i = 0; i < S.N; ++i) {
+            M.perm.push_back((int)(S.perm[i] + pos0));
+            M.ipos.push_back((int)(S.ipos[i] + pos0));
+            M.node_of.push_back(S.node_of[i] + node0);
+            M.prob_of_pos.push_back((int)M.prob_pos.size() - 1);
+        }
+        const long long e0 = (long long)M.col.size();
+        for (int i = 0; i < S.N; ++i) {
+            M.rowptr.push_back(S.rowptr[i + 1] + e0);
+            M.glob_rowptr.push_back(S.glob_rowptr[i + 1] + e0);
+        }
+        for (long long e = 0; e < S.nnz; ++e) {
+            M.col.push_back((int)(S.col[e] + pos0));
+            M.perm_to_glob.push_back(S.perm_to_glob[e] + e0);
+            M.scatter.push_back(S.scatter[e] >= 0 ? S.scatter[e] + pool : -1);
+        }
+        for (int f = 0; f < S.n_nodes; ++f) {
+            M.node_ptr.push_back((int)(S.node_ptr[f] + pos0));
+            M.parent.push_back(S.parent[f] >= 0 ? S.parent[f] + node0 : -1);
+            M.child_ptr.push_back((int)M.child_list.size() + S.child_ptr[f] - S.child_ptr[0]);
+            M.k.push_back(S.k[f]);
+            M.n.push_back(S.n[f]);
+            M.ld.push_back(S.ld[f]);
+            M.front_ptr.push_back(S.front_ptr[f] + fpos);
+            M.front_off.push_back(S.front_off[f] + pool);
+            M.rel_ptr.push_back(S.rel_ptr[f] + rel);
+            M.upd_off.push_back(S.upd_off[f] + upd);
+        }
+        for (int c : S.child_list) M.child_list.push_back(c + node0);
+        for (int q : S.front_pos) M.front_pos.push_back((int)(q + pos0));
+        for (int r : S.rel) M.rel.push_back(r);
+        pos0 += S.N;
+        node0 += S.n_nodes;
+        pool += S.pool_size;
+        fpos += (long long)S.front_pos.size();
+        rel += (long long)S.rel.size();
+        upd += S.upd_size;
+        nel += S.n_elem;
+        ++nch;
+    }
+    M.node_ptr.push_back((int)N);
+    M.front_ptr.push_back(fpos);
+    M.front_off.push_back(pool);
+    M.child_ptr.push_back((int)M.child_list.size());
+    M.rel_ptr.push_back(rel);
+    M.upd_off.push_back(upd);
+    M.prob_pos.push_back(N);
+    M.prob_nnz.push_back((long long)M.col.size());
+    M.prob_elem.push_back(nel);
+    M.prob_node.push_back(F);
+    M.pool_size = pool;
+    M.upd_size = upd;
+    M.n_elem = nel;
+    (void)nch;
+    return finish_symbolic(M);
 }
 
 }  // namespace riga

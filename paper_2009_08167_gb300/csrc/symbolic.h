@@ -110,6 +110,12 @@ struct Symbolic {
     // element structure (for assembly with coefficients and the adjoint)
     long long n_elem = 0;
 
+    // batch (merged forest of independent problems): per-problem offsets of
+    // positions / DOFs, CSR entries, elements and nodes (size problems + 1)
+    std::vector<long long> prob_pos, prob_nnz, prob_elem;
+    std::vector<int> prob_node;
+    std::vector<int> prob_of_pos;   // problem of each position
+
     long long nnzL = 0;   // factor entries (lower trapezoids of the n x k panels)
     long long nnzQ = 0;   // solve-operator entries (k x n extra-row blocks)
     long long nnzL_own2 = 0;  // sum k^2: the -A11^{-1} part, read only by the backward sweep
@@ -120,5 +126,9 @@ struct Symbolic {
 // Builds everything above.  Returns an empty string on success, else a message.
 std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int* const* mult,
                            int leaf_extent);
+// Heights, counts, schedule and solve items from nodes, fronts and maps.
+std::string finish_symbolic(Symbolic& S);
+// Merges independent problems into one forest (dim = 0 marks a batch).
+std::string merge_symbolic(Symbolic& M, const std::vector<Symbolic>& P);
 
 }  // namespace riga

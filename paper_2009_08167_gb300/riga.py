@@ -81,6 +81,8 @@ def load_library(path=LIB_PATH):
     lib.riga_eigs.argtypes = [P, I, D, D, P, P, P, ctypes.POINTER(I)]
     lib.riga_set_eig_options.argtypes = [P, I, I, I, I, ctypes.c_ulonglong]
     lib.riga_eig_grad.argtypes = [P, I, P, P, P]
+    lib.riga_assemble_batch.argtypes = [P, I, ctypes.POINTER(_MeshC), P, P]
+    lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
     lib.riga_get_symbolic.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(LL), P, P, P, P, P]
     lib.riga_get_matrices.argtypes = [P, P, P, P, P]
@@ -191,6 +193,41 @@ class Riga:
         self._check(self.lib.riga_assemble(self.ctx, ctypes.byref(m), _ptr(coefK), _ptr(coefM)))
         self.mesh = mesh
         self._mult_keep = keep
+
+    def assemble_batch(self, meshes, coefK=None, coefM=None):
+        """Assembles independent problems into one batch context; coefK /
+        coefM: None or a list with one array (or None) per problem."""
+        n = len(meshes)
+        arr = (_MeshC * n)()
+        keep = []
+        for b, mesh in enumerate(meshes):
+            m, kp = self._mesh_c(mesh)
+            arr[b] = m
+            keep.append(kp)
+        ptrs = []
+        for coefs in (coefK, coefM):
+            if coefs is None:
+                ptrs.append((None, None))
+                continue
+            hold = [None if c is None else np.ascontiguousarray(c, dtype=np.float64) for c in coefs]
+            pa = (ctypes.c_void_p * n)(*[None if h is None else h.ctypes.data for h in hold])
+            ptrs.append((pa, hold))
+        self._check(self.lib.riga_assemble_batch(self.ctx, n, arr, ptrs[0][0], ptrs[1][0]))
+        self.meshes = list(meshes)
+        self.mesh = None
+        self._mult_keep = keep
+
+    def eigs_batch(self, k, sigma=0.0, tol=1e-10, check=True):
+        """(evals, resid, nconv) of every problem of the batch: arrays of
+        shape (nprob, k), (nprob, k), (nprob,)."""
+        n = len(self.meshes)
+        ev = np.zeros((n, k))
+        rs = np.zeros((n, k))
+        nc = np.zeros(n, dtype=np.int32)
+        rc = self.lib.riga_eigs_batch(self.ctx, int(k), float(sigma), float(tol), _ptr(ev), _ptr(rs), _ptr(nc))
+        if check or rc != RIGA_ENOCONV:
+            self._check(rc)
+        return ev, rs, nc
 
     # ------------------------------------------------------------ riga_factor
     def factor(self, sigma, precision=RIGA_FP64):
