@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="riga", choices=["riga", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3"],
-                    help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, 50 pairs")
+    ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c4"],
+                    help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, "
+                         "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-front (mixed) leg")
@@ -59,7 +60,12 @@ def parse():
 
 
 def workload(mesh_kind):
-    from paper_2009_08167_gb300.inputs import config_c2, config_c3
+    from paper_2009_08167_gb300.inputs import config_c2, config_c3, config_c4
+    if mesh_kind == "c4":
+        import numpy as np
+        probs = config_c4()
+        return {"batch": True, "meshes": [p["mesh"] for p in probs], "coefK": [np.exp(p["a"]) for p in probs],
+                "k": probs[0]["k"], "slice": probs[0]["k"], "sigma": 0.0}
     if mesh_kind == "c3":
         cfg = config_c3()
         cfg["slice"] = cfg["k"]
@@ -69,6 +75,18 @@ def workload(mesh_kind):
 
 
 def config_dict(args, cfg, extra=None):
+    if cfg.get("batch"):
+        ms = cfg["meshes"]
+        d = {
+            "workload": f"batch{len(ms)}_laplace2d_riga_ne32-128_p2-3_bs8-16_lognormal-coef_k{cfg['k']}",
+            "problems": len(ms), "pairs_per_problem": cfg["k"], "elements_per_side": "U{32..128}",
+            "degree": "{2,3}", "block_size": "{8,16}", "coefficient": "exp(a_e), a_e~N(0,0.5^2)",
+            "factor_precision": "fp64", "l2": "flushed between timed steps (512 MiB write)",
+            "parallelism": f"replicas{args.gpus}",
+        }
+        if extra:
+            d.update(extra)
+        return d
     m = cfg["mesh"]
     d = {
         "workload": f"laplace{m.dim}d_p{m.p}_{'x'.join(str(v) for v in m.ne)}_{'riga_bs%d' % m.bs if m.bs else 'iga'}_k{cfg['k']}_slices{cfg['k'] // cfg['slice']}",
@@ -166,6 +184,30 @@ def oracle_sample():
     return ok / dt, dt, desc
 
 
+def oracle_sample_batch(cfg, budget_s=15.0):
+    """The oracle as it stands on a bounded sample of the batch: its problems
+    from the smallest up until about budget_s seconds of CPU work (larger
+    problems take the banded oracle up to ~100 s each, so the sample favours
+    the oracle).  Returns (pairs/s, seconds, description)."""
+    import numpy as np
+    from oracle import assembly, eigen
+    t0 = time.perf_counter()
+    ok = done = 0
+    order = sorted(range(len(cfg["meshes"])), key=lambda i: (int(np.prod(cfg["meshes"][i].ne)), i))
+    for i in order:
+        m, c = cfg["meshes"][i], cfg["coefK"][i]
+        K, M = assembly.assemble_coef(m.dim, m.ne, m.p, m.mults, c, None)
+        lam, U, info = eigen.lanczos_shift_invert(K, M, cfg["k"], cfg["sigma"], tol=1e-12, seed=1)
+        ok += int(np.sum(eigen.residual_rho(K, M, lam, U) <= RESID_TOL))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    desc = (f"oracle shift-invert Lanczos + banded LDL^T on the {done} smallest problems of the batch, "
+            f"{ok} pairs at resid<=1e-10, {dt:.1f} s, 1 thread of numpy/BLAS")
+    return ok / dt, dt, desc
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -178,12 +220,13 @@ def run_reference(args, rank, world):
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     cfg = workload(args.mesh)
+    sample = (lambda: oracle_sample_batch(cfg)) if cfg.get("batch") else oracle_sample
     for _ in range(args.warmup):
-        oracle_sample()
+        sample()
     vals, secs = [], []
     desc = ""
     for _ in range(args.steps):
-        v, dt, desc = oracle_sample()
+        v, dt, desc = sample()
         vals.append(v)
         secs.append(dt)
     value = statistics.mean(vals)
@@ -198,7 +241,129 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def roofline(prof):
+    """Roofline of the dominant phase of one profiled step (device time of
+    the phase's launches, CUDA events on the library's stream)."""
+    pk, pk_kind = peaks()
+    dom = max(prof, key=lambda p: prof[p]["ms"])
+    pr = prof[dom]
+    if pr["ms"] <= 0:
+        return None
+    if pr["flops"] > 0 and pr["bytes"] == 0:
+        ach = pr["flops"] / (pr["ms"] / 1e3) / 1e12
+        peak = 1.25  # FP64 FFMA: nominal GB300 FP64 rate (no measured FP64 peak in the peaks file)
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "phase": dom, "peak_source": "nominal fp64"}
+    gbs = pr["bytes"] / (pr["ms"] / 1e3) / 1e9
+    per_call = ncu_traffic(dom)
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "traffic": per_call, "phase": dom, "peak_source": pk_kind,
+            "algorithmic_bytes_per_call": pr["bytes"] / max(1, pr["calls"]),
+            "ms_per_call": pr["ms"] / max(1, pr["calls"])}
+
+
 # ------------------------------------------------------------------ riga leg
+def run_riga_batch(args, rank, world, local_rank, cfg):
+    """The batch workload: one step = numeric assembly of every problem +
+    riga_eigs_batch (FP64)."""
+    import numpy as np
+    import torch
+    from paper_2009_08167_gb300 import riga
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    meshes, cK, k = cfg["meshes"], cfg["coefK"], cfg["k"]
+    R = riga.Riga(local_rank, stream)
+    R.set_eig_options(extra=2, seed=11)
+    R.assemble_batch(meshes, cK)  # symbolic analysis of every pattern: once, untimed
+    q = R.query()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        R.assemble_batch(meshes, cK)
+        return R.eigs_batch(k, cfg["sigma"], RESID_TOL)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clk = Clocks(local_rank)
+    launches0 = R.launches()
+    times = []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, rs, nc = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    launches = (R.launches() - launches0) // max(1, args.steps)
+    pairs = int(np.sum(rs <= RESID_TOL))
+    ms = statistics.mean(times)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * pairs / (ms_max / 1e3)
+    st = R.stats()
+    # end to end: host wall clock around the same public calls (coefficients
+    # host -> device inside assembly, eigenvalues and residuals back)
+    h2d = int(sum(c.nbytes for c in cK) + sum(np.asarray(mm, dtype=np.int32).nbytes for m in meshes for mm in m.mults))
+    d2h = 8 * 2 * len(meshes) * k + 4 * len(meshes)
+    e2e_times = []
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rsh, _ = step()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_val = world * int(np.sum(rsh <= RESID_TOL)) / statistics.mean(e2e_times) if e2e_times else None
+    R.profile(True)
+    if not args.no_profile_pass:
+        step()
+    prof = R.profile_get()
+    R.profile(False)
+    roof = roofline(prof)
+    phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_sample_batch(cfg)
+        cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded meshes and coefficients)",
+            "config": config_dict(args, cfg, {"N_total": q["N"], "nnz_total": q["nnz"], "nnzL_total": q["nnzL"],
+                                              "flops_fact": q["flops_fact"]}),
+            "converged_pairs": pairs, "max_resid": float(np.nanmax(rs)),
+            "e2e": {"value": e2e_val, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "roofline": roof, "phases_ms_one_step": phases,
+            "counts_per_step": {"n_fact": st["n_fact"], "n_solve": st["n_solve"], "n_matvec": st["n_matvec"],
+                                "lanczos_steps": st["lanczos_steps"]},
+            "clocks": clocks, "wall_s_timed": t_wall, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    R.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_riga(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -213,6 +378,8 @@ def run_riga(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     prec = riga.RIGA_FP64 if args.precision == "fp64" else riga.RIGA_FP32
     cfg = workload(args.mesh)
+    if cfg.get("batch"):
+        return run_riga_batch(args, rank, world, local_rank, cfg)
     mesh, k = cfg["mesh"], cfg["k"]
     R = riga.Riga(local_rank, stream)
     R.set_eig_options(slice=cfg["slice"], precision=prec, extra=2, seed=11)
@@ -286,23 +453,7 @@ def run_riga(args, rank, world, local_rank):
         step_device()
     prof = R.profile_get()
     R.profile(False)
-    pk, pk_kind = peaks()
-    dom = max(prof, key=lambda p: prof[p]["ms"])
-    pr = prof[dom]
-    if pr["ms"] <= 0:
-        roof = None
-    elif pr["flops"] > 0 and pr["bytes"] == 0:
-        ach = pr["flops"] / (pr["ms"] / 1e3) / 1e12
-        peak = 1.25  # FP64 FFMA: nominal GB300 FP64 rate (no measured FP64 peak in the peaks file)
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "phase": dom, "peak_source": "nominal fp64"}
-    else:
-        gbs = pr["bytes"] / (pr["ms"] / 1e3) / 1e9
-        per_call = ncu_traffic(dom)
-        roof = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
-                "traffic": per_call, "phase": dom, "peak_source": pk_kind,
-                "algorithmic_bytes_per_call": pr["bytes"] / max(1, pr["calls"]),
-                "ms_per_call": pr["ms"] / max(1, pr["calls"])}
+    roof = roofline(prof)
     phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
 
     # the mixed path (FP32 fronts, FP64 refinement, residuals, Lanczos and

@@ -680,19 +680,38 @@ extern "C" int riga_assemble_batch(riga_ctx* c, int nprob, const riga_mesh* mesh
     c->assembled = false;
     c->factored = false;
     c->nev = 0;
-    c->mesh_key.clear();
-    c->probs.assign(nprob, Symbolic());
+    c->analyzed_only = false;
+    // key of the batch's patterns: the symbolic phase is skipped when the
+    // meshes repeat (numeric re-assembly only, as for a single problem)
+    std::vector<int> key{-1, nprob};
     for (int b = 0; b < nprob; ++b) {
         const riga_mesh* m = &meshes[b];
         if (m->dim < 1 || m->dim > 3 || m->dirichlet != 1 || m->p < 1 || m->p > 6 || m->leaf_extent < 0)
-            return set_error(c, RIGA_EINVAL, "bad mesh in the batch");
-        std::string err = build_symbolic(c->probs[b], m->dim, m->ne, m->p, m->mult, m->leaf_extent);
-        if (!err.empty()) return set_error(c, RIGA_EINVAL, "problem " + std::to_string(b) + ": " + err);
+            return set_error(c, RIGA_EINVAL, "bad mesh in the batch: problem " + std::to_string(b));
+        key.push_back(m->dim);
+        key.push_back(m->p);
+        key.push_back(m->leaf_extent > 0 ? m->leaf_extent : 8);
+        for (int a = 0; a < m->dim; ++a) {
+            if (m->ne[a] < 1 || m->ne[a] > (1 << 20))
+                return set_error(c, RIGA_EINVAL, "ne out of range: problem " + std::to_string(b));
+            key.push_back(m->ne[a]);
+            for (int i = 0; i + 1 < m->ne[a]; ++i) key.push_back(m->mult[a] ? m->mult[a][i] : 1);
+        }
     }
-    std::string err = merge_symbolic(c->S, c->probs);
-    if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
-    int rc = upload_symbolic(c);
-    if (rc) return rc;
+    if (key != c->mesh_key) {
+        c->mesh_key.clear();
+        c->probs.assign(nprob, Symbolic());
+        for (int b = 0; b < nprob; ++b) {
+            const riga_mesh* m = &meshes[b];
+            std::string err = build_symbolic(c->probs[b], m->dim, m->ne, m->p, m->mult, m->leaf_extent);
+            if (!err.empty()) return set_error(c, RIGA_EINVAL, "problem " + std::to_string(b) + ": " + err);
+        }
+        std::string err = merge_symbolic(c->S, c->probs);
+        if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
+        int rc0 = upload_symbolic(c);
+        if (rc0) return rc0;
+        c->mesh_key = key;  // starts with -1: never equal to a single mesh's key
+    }
     // coefficients: host pointers, concatenated (NULL per problem = ones)
     bool anyK = false, anyM = false;
     for (int b = 0; b < nprob; ++b) {
@@ -716,7 +735,7 @@ extern "C" int riga_assemble_batch(riga_ctx* c, int nprob, const riga_mesh* mesh
             }
         }
     }
-    rc = assemble_device(c);
+    int rc = assemble_device(c);
     if (rc) return rc;
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->assembled = true;
