@@ -73,6 +73,7 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->perm_to_glob.upload(S.perm_to_glob, st));
     RIGA_CUDA_TRY(c, c->glob_rowptr.upload(S.glob_rowptr, st));
     RIGA_CUDA_TRY(c, c->sitems.upload(S.sitems, st));
+    RIGA_CUDA_TRY(c, c->crec.upload(S.crec.empty() ? std::vector<ChildRec>{ChildRec{0, 0, 0, 0, 0, 0}} : S.crec, st));
     RIGA_CUDA_TRY(c, c->parts_f.upload(S.parts_f, st));
     RIGA_CUDA_TRY(c, c->parts_b.upload(S.parts_b, st));
     RIGA_CUDA_TRY(c, c->qitems.upload(S.qitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.qitems, st));

@@ -82,6 +82,7 @@ struct riga_ctx {
 
     // symbolic arrays on the device
     riga::DevBuf<riga::SolveItem> sitems;
+    riga::DevBuf<riga::ChildRec> crec;
     riga::DevBuf<int> parts_f, parts_b;
     riga::DevBuf<riga::PanelItem> qitems;
     riga::DevBuf<long long> rowptr, front_off, front_ptr, rel_ptr, upd_off, scatter, perm_to_glob, glob_rowptr;

@@ -41,6 +41,7 @@ struct TreeArgs {
     const int* parts_f;
     const int* parts_b;
     const SolveItem* items;  // forward parts (ascending height), then backward parts
+    const ChildRec* crec;    // children records (see Symbolic::crec)
     int n_items, n_fwd;
     int chunk_elems;   // elements per shared-memory chunk buffer (two buffers)
     int max_n;
@@ -120,10 +121,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return true;
 }
 
-// acc[q] += sum over units u = ua+g, ua+g+G, ... < ub of P[u-ua][li + 256 q] * w[u]
+// acc[q] += sum over units u = ua+g, ua+g+G, ... < ub of P[u-ua][li + NT q] * w[u]
 // for the NA output slots of this thread (an exact count: predicated-off FP64
 // instructions still occupy GB300's narrow FP64 pipe).
-template <typename T, int NA>
+template <typename T, int NA, int NT>
 __device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ldp, int ua, int ub, int g, int G,
                                                  int li, int cnt, const T* __restrict__ w, T* acc) {
     for (int u = ua + g; u < ub; u += G) {
@@ -134,7 +135,7 @@ __device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ld
         } else {
 #pragma unroll
             for (int q2 = 0; q2 < NA; ++q2) {
-                const int l = li + q2 * 256;
+                const int l = li + q2 * NT;
                 if (l < cnt) acc[q2] += row[l] * x;
             }
         }
@@ -146,22 +147,27 @@ __device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ld
 // forward part: every forward part of every child; backward part: every
 // forward part of its own front and every backward part of the parent.
 // Dependencies always have lower item indices, so they were claimed by CTAs
-// that are already running: no deadlock.  The item's operator panel streams
-// through two shared-memory buffers by bulk copies issued before the
-// dependency wait.  A forward part owns border columns [lo,hi): u(j) =
-// w(j) + sum_r P[r][j] w1(r); a backward part owns rows [lo,hi) of the front's
-// own variables: x(r) = sum_j P[j][r] v(j), v = [-w1; x(border)].  Both are
-// the same loop: stream units (forward: rows r; backward: columns j) times a
-// multiplier (w1(r), v(j)) accumulated into the part's outputs; threads split
-// the outputs and interleave the units, then reduce through shared memory.
-template <typename T>
-__global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
+// that are already running: no deadlock.  The item's operator panel is
+// copied into shared memory by bulk copies issued before the dependency
+// wait: in one copy when it fits the whole buffer (the usual case: parts are
+// sized for that), else streamed through the two halves of the buffer.  A
+// forward part owns border columns [lo,hi): u(j) = w(j) + sum_r P[r][j]
+// w1(r); a backward part owns rows [lo,hi) of the front's own variables:
+// x(r) = sum_j P[j][r] v(j), v = [-w1; x(border)].  Both are the same loop:
+// stream units (forward: rows r; backward: columns j) times a multiplier
+// (w1(r), v(j)) accumulated into the part's outputs; threads split the
+// outputs and interleave the units, then reduce through shared memory.
+// Everything an item needs to know about its front comes packed in the item
+// (and, for its children, in one record each), so that few dependent global
+// loads separate a claim from the arithmetic.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* buf[2];
     buf[0] = reinterpret_cast<T*>(smem_raw);
     buf[1] = buf[0] + a.chunk_elems;
     T* w = buf[1] + a.chunk_elems;  // front vector (n)
-    T* red = w + a.max_n;           // 256 partial sums
+    T* red = w + a.max_n;           // NT partial sums
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_item, s_ok;
     const int tid = threadIdx.x;
@@ -179,11 +185,13 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
         if (item >= a.n_items) return;
         const SolveItem it = a.items[item];
         const bool fwd = item < a.n_fwd;
-        const int F = it.front, k = a.kk[F], n = a.nn[F], b0 = a.node_ptr[F];
+        const int F = it.front, k = it.k, n = it.n, b0 = it.b0;
         const int lo = it.lo, cnt = it.hi - it.lo, ldp = it.ldp;
         const T* q = Q + it.off;
-        const int units = fwd ? k : n;          // rows (forward) or columns (backward) of the panel
-        const int upc = max(1, a.chunk_elems / ldp);
+        const int units = fwd ? k : n;  // rows (forward) or columns (backward) of the panel
+        // one copy into the whole buffer, or chunks through its halves
+        const bool whole = (long long)units * ldp <= 2LL * a.chunk_elems;
+        const int upc = whole ? max(1, units) : max(1, a.chunk_elems / ldp);
         const int nchunks = (cnt > 0) ? (units + upc - 1) / upc : 0;
         const int issued = min(2, nchunks);
         if (tid == 0) {
@@ -197,14 +205,13 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
             }
             bool ok = true;
             if (fwd) {
-                for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1] && ok; ++ci) {
-                    const int ch = a.child_list[ci];
-                    ok = wait_count(&a.done_f[ch], a.parts_f[ch], a.err, a.spin_limit);
+                for (int ci = it.c0; ci < it.c1 && ok; ++ci) {
+                    const ChildRec cr = a.crec[ci];
+                    ok = wait_count(&a.done_f[cr.child], cr.parts, a.err, a.spin_limit);
                 }
             } else {
-                ok = wait_count(&a.done_f[F], a.parts_f[F], a.err, a.spin_limit);
-                const int par = a.parent[F];
-                if (ok && par >= 0) ok = wait_count(&a.done_b[par], a.parts_b[par], a.err, a.spin_limit);
+                ok = wait_count(&a.done_f[F], it.wait_parts, a.err, a.spin_limit);
+                if (ok && it.parent >= 0) ok = wait_count(&a.done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
             }
             __threadfence();
             s_ok = ok;
@@ -219,30 +226,29 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
         }
         if (fwd) {
             // w = [b(own); 0] + children's update vectors
-            for (int i = tid; i < n; i += blockDim.x) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
+            for (int i = tid; i < n; i += NT) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
             __syncthreads();
-            for (int ci = a.child_ptr[F]; ci < a.child_ptr[F + 1]; ++ci) {
-                const int c = a.child_list[ci];
-                const int m = a.nn[c] - a.kk[c];
-                const int* r = a.rel + a.rel_ptr[c];
-                const double* u = a.upd + a.upd_off[c];
-                for (int i = tid; i < m; i += blockDim.x) w[r[i]] += (T)__ldcg(&u[i]);
+            for (int ci = it.c0; ci < it.c1; ++ci) {
+                const ChildRec cr = a.crec[ci];
+                const int* r = a.rel + cr.rel_off;
+                const double* u = a.upd + cr.upd_off;
+                for (int i = tid; i < cr.m; i += NT) w[r[i]] += (T)__ldcg(&u[i]);
                 __syncthreads();
             }
             if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
-                for (int i = tid; i < k; i += blockDim.x) a.w1[b0 + i] = (double)w[i];
+                for (int i = tid; i < k; i += NT) a.w1[b0 + i] = (double)w[i];
         } else {
-            const int* idx = a.front_pos + a.front_ptr[F];
-            for (int i = tid; i < n; i += blockDim.x)
+            const int* idx = a.front_pos + it.fpos;
+            for (int i = tid; i < n; i += NT)
                 w[i] = (i < k) ? -(T)__ldcg(&a.w1[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
         }
         __syncthreads();
         // thread layout: outputs l (columns or rows of the part) x unit groups g
-        const int cp = max(1, min(cnt, 256));
-        const int G = max(1, 256 / cp);
+        const int cp = max(1, min(cnt, NT));
+        const int G = max(1, NT / cp);
         const int li = tid % cp, g = tid / cp;
         const bool active = cnt > 0 && g < G;
-        const int na = (cnt + 255) / 256;  // outputs per thread when cnt > 256 (G = 1)
+        const int na = (cnt + NT - 1) / NT;  // outputs per thread when cnt > NT (G = 1)
         T acc[8];
 #pragma unroll
         for (int q2 = 0; q2 < 8; ++q2) acc[q2] = T(0);
@@ -262,14 +268,14 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
             const T* P = buf[b];
             if (active) {
                 switch (na) {
-                    case 1: accumulate_chunk<T, 1>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 2: accumulate_chunk<T, 2>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 3: accumulate_chunk<T, 3>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 4: accumulate_chunk<T, 4>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 5: accumulate_chunk<T, 5>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 6: accumulate_chunk<T, 6>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 7: accumulate_chunk<T, 7>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    default: accumulate_chunk<T, 8>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 1: accumulate_chunk<T, 1, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 2: accumulate_chunk<T, 2, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 3: accumulate_chunk<T, 3, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 4: accumulate_chunk<T, 4, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 5: accumulate_chunk<T, 5, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 6: accumulate_chunk<T, 6, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    case 7: accumulate_chunk<T, 7, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                    default: accumulate_chunk<T, 8, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
                 }
             }
             __syncthreads();
@@ -292,14 +298,10 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
             if (g == 0) {
 #pragma unroll
                 for (int q2 = 0; q2 < 8; ++q2) {
-                    const int l = li + q2 * 256;
+                    const int l = li + q2 * NT;
                     if (q2 < na && l < cnt) {
-                        if (fwd) {
-                            const int j = lo + l;
-                            a.upd[a.upd_off[F] + j - k] = (double)(w[j] + acc[q2]);
-                        } else {
-                            a.y[b0 + lo + l] = (double)acc[q2];
-                        }
+                        if (fwd) a.upd[it.upd_off + lo + l - k] = (double)(w[lo + l] + acc[q2]);
+                        else a.y[b0 + lo + l] = (double)acc[q2];
                     }
                 }
             }
@@ -310,6 +312,154 @@ __global__ void __launch_bounds__(256) tree_solve_kernel(const T* __restrict__ Q
             atomicAdd(fwd ? &a.done_f[F] : &a.done_b[F], 1);
             if (a.trace) a.trace[4 * item + 3] = global_ns();
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-item variant for batches of many small trees, where the solve is
+// bound by how many items are in flight rather than by a critical path:
+// every warp is an independent worker with its own front vector in shared
+// memory, so that dozens of items per SM overlap their dependency waits and
+// gathers.  The item's panel is prefetched into L2 by one bulk prefetch when
+// the item is claimed (before its dependency wait) and then read once with
+// streaming loads straight into registers.  Parts hold at most 256 outputs
+// (8 per lane), in widths that are multiples of 32.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// acc[q] += sum over units u = g, g+G, ... < units of P[u][li + 32 q] * w[u];
+// U units per round, so that U * NA loads are in flight per lane
+template <typename T, int NA, int U>
+__device__ __forceinline__ void warp_accumulate(const T* __restrict__ P, int ldp, int units, int g, int G, int li,
+                                                int cnt, const T* __restrict__ w, T* acc) {
+    int u = g;
+    for (; u + (U - 1) * G < units; u += U * G) {
+        T v[U][NA];
+#pragma unroll
+        for (int s = 0; s < U; ++s) {
+            const T* row = P + (long long)(u + s * G) * ldp;
+#pragma unroll
+            for (int q2 = 0; q2 < NA; ++q2) {
+                const int l = li + 32 * q2;
+                v[s][q2] = (l < cnt) ? __ldcs(row + l) : T(0);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < U; ++s) {
+            const T x = w[u + s * G];
+#pragma unroll
+            for (int q2 = 0; q2 < NA; ++q2)
+                if (li + 32 * q2 < cnt) acc[q2] += v[s][q2] * x;
+        }
+    }
+    for (; u < units; u += G) {
+        const T* row = P + (long long)u * ldp;
+        const T x = w[u];
+#pragma unroll
+        for (int q2 = 0; q2 < NA; ++q2) {
+            const int l = li + 32 * q2;
+            if (l < cnt) acc[q2] += __ldcs(row + l) * x;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restrict__ Q, TreeArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    T* w = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * a.max_n;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= a.n_items) return;
+        const SolveItem it = a.items[item];
+        const bool fwd = item < a.n_fwd;
+        const int F = it.front, k = it.k, n = it.n, b0 = it.b0;
+        const int lo = it.lo, cnt = it.hi - it.lo, ldp = it.ldp;
+        const T* q = Q + it.off;
+        const int units = fwd ? k : n;  // rows (forward) or columns (backward) of the panel
+        if (lane == 0) {
+            if (a.trace) {
+                a.trace[4 * item] = sm_id();
+                a.trace[4 * item + 1] = global_ns();
+            }
+            if (cnt > 0 && units > 0) bulk_prefetch_l2(q, (unsigned)((long long)units * ldp * sizeof(T)));
+        }
+        // dependency waits: forward, every forward part of every child (one
+        // lane per child); backward, this front's forward parts and the
+        // parent's backward parts
+        bool ok = true;
+        if (fwd) {
+            for (int ci = it.c0 + lane; ci < it.c1; ci += 32) {
+                const ChildRec cr = a.crec[ci];
+                ok = ok && wait_count(&a.done_f[cr.child], cr.parts, a.err, a.spin_limit);
+            }
+        } else if (lane == 0) {
+            ok = wait_count(&a.done_f[F], it.wait_parts, a.err, a.spin_limit);
+            if (ok && it.parent >= 0) ok = wait_count(&a.done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
+        }
+        if (!__all_sync(FULL, ok)) return;
+        __threadfence();
+        if (a.trace && lane == 0) a.trace[4 * item + 2] = global_ns();
+        if (fwd) {
+            // w = [b(own); 0] + children's update vectors
+            for (int i = lane; i < n; i += 32) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
+            __syncwarp();
+            for (int ci = it.c0; ci < it.c1; ++ci) {
+                const ChildRec cr = a.crec[ci];
+                const int* r = a.rel + cr.rel_off;
+                const double* u = a.upd + cr.upd_off;
+                for (int i = lane; i < cr.m; i += 32) w[r[i]] += (T)__ldcg(&u[i]);
+                __syncwarp();
+            }
+            if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
+                for (int i = lane; i < k; i += 32) a.w1[b0 + i] = (double)w[i];
+        } else {
+            const int* idx = a.front_pos + it.fpos;
+            for (int i = lane; i < n; i += 32)
+                w[i] = (i < k) ? -(T)__ldcg(&a.w1[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
+        }
+        __syncwarp();
+        // lanes: outputs li (cp per unit group) x unit groups g (G = 32 / cp)
+        const int cp = cnt > 16 ? 32 : (cnt > 8 ? 16 : (cnt > 4 ? 8 : 4));
+        const int G = 32 / cp, li = lane % cp, g = lane / cp;
+        const int na = (cnt + 31) / 32;
+        T acc[8];
+#pragma unroll
+        for (int q2 = 0; q2 < 8; ++q2) acc[q2] = T(0);
+        if (cnt > 0) {
+            switch (na) {
+                case 1: warp_accumulate<T, 1, 16>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 2: warp_accumulate<T, 2, 8>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 3: warp_accumulate<T, 3, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 4: warp_accumulate<T, 4, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 5: warp_accumulate<T, 5, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 6: warp_accumulate<T, 6, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 7: warp_accumulate<T, 7, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                default: warp_accumulate<T, 8, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+            }
+            for (int o = cp; o < 32; o <<= 1) acc[0] += __shfl_xor_sync(FULL, acc[0], o);
+            if (g == 0) {
+#pragma unroll
+                for (int q2 = 0; q2 < 8; ++q2) {
+                    const int l = li + 32 * q2;
+                    if (q2 < na && l < cnt) {
+                        if (fwd) a.upd[it.upd_off + lo + l - k] = (double)(w[lo + l] + acc[q2]);
+                        else a.y[b0 + lo + l] = (double)acc[q2];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd(fwd ? &a.done_f[F] : &a.done_b[F], 1);
+            if (a.trace) a.trace[4 * item + 3] = global_ns();
+        }
+        __syncwarp();
     }
 }
 
@@ -404,19 +554,32 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     int max_n = 0, max_ldp = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
     for (const SolveItem& it : S.sitems) max_ldp = std::max(max_ldp, it.ldp);
-    int chunk = (int)(32768 / sizeof(T));
-    chunk = std::max(chunk, max_ldp);
-    chunk = (chunk + 3) / 4 * 4;
-    const size_t smem = (2 * (size_t)chunk + max_n + 256 + 8) * sizeof(T);
+    // batches of many small trees: one item per warp (tree_solve_warp_kernel);
+    // small fronts: 128 threads and a 32 KiB (FP64) panel buffer per CTA, so
+    // that many items per SM overlap their waits; large fronts: 256 threads
+    // and two 32 KiB halves
+    const int n_items = (int)S.sitems.size();
     int maxopt = 0, nsm = 0, per_sm = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    const int nt = S.solve_mode == SOLVE_CTA256 ? 256 : 128;
+    // (small: halves of 2048..3072 elements, so that every part's panel
+    // usually arrives in one copy)
+    int chunk = S.solve_mode == SOLVE_CTA128
+                    ? (int)std::min<long long>(3072, std::max<long long>(2048, (S.max_panel + 1) / 2))
+                    : (int)(32768 / sizeof(T));
+    chunk = std::max(chunk, max_ldp);
+    chunk = (chunk + 3) / 4 * 4;
+    const bool warp = S.solve_mode == SOLVE_WARP;
+    const size_t smem = warp ? 4 * (size_t)max_n * sizeof(T) : (2 * (size_t)chunk + max_n + nt + 8) * sizeof(T);
     if (smem + 256 > (size_t)maxopt) return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
+    auto kern = warp ? tree_solve_warp_kernel<T>
+                     : (S.solve_mode == SOLVE_CTA128 ? tree_solve_kernel<T, 128> : tree_solve_kernel<T, 256>);
     if (smem > 48 * 1024)
-        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tree_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_solve_kernel<T>, 256, smem));
-    const int n_items = (int)S.sitems.size();
-    const int grid = std::max(1, std::min(n_items, std::max(1, per_sm) * nsm));
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+    const int per_block = warp ? 4 : 1;  // concurrent items per block
+    const int grid = std::max(1, std::min((n_items + per_block - 1) / per_block, std::max(1, per_sm) * nsm));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, (2 * (size_t)S.n_nodes + 1) * sizeof(int), st));
     TreeArgs a;
     a.node_ptr = c->node_ptr.ptr;
@@ -433,6 +596,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     a.parts_f = c->parts_f.ptr;
     a.parts_b = c->parts_b.ptr;
     a.items = c->sitems.ptr;
+    a.crec = c->crec.ptr;
     a.n_items = n_items;
     a.n_fwd = S.n_fwd_items;
     a.chunk_elems = chunk;
@@ -446,7 +610,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     a.err = c->flag.ptr;
     a.spin_limit = c->wait_limit;
     a.trace = c->trace_buf;
-    { count_launch(c); tree_solve_kernel<T><<<grid, 256, smem, st>>>(Q, a); }
+    { count_launch(c); kern<<<grid, nt, smem, st>>>(Q, a); }
     return RIGA_OK;
 }
 

@@ -120,37 +120,87 @@ std::string finish_symbolic(Symbolic& S) {
     }
 
     // ------------------------------------------------------- solve items
-    // parts of about SOLVE_PART_FMA multiply-adds each (up to 32 per sweep)
-    const long long SOLVE_PART_FMA = 12288;
+    // Parts of about part_fma multiply-adds each (at most 32 per sweep), of at
+    // most 8 outputs per thread of the solve CTA (per lane for the warp
+    // kernel).  When every front has at most SMALL_MAX_N variables (2D
+    // meshes), parts are smaller, so that the fronts near the root (the
+    // critical path of the solve) spread over more SMs and each part's panel
+    // fits one shared-memory copy; a forest of many such trees (a batch) is
+    // solved one warp per item.
+    const int SMALL_MAX_N = 1536;
+    int max_n = 0;
+    for (int f = 0; f < F; ++f) max_n = std::max(max_n, S.n[f]);
+    int n_trees = 0;
+    for (int f = 0; f < F; ++f) n_trees += S.parent[f] < 0;
+    S.solve_mode = max_n > SMALL_MAX_N ? SOLVE_CTA256 : (n_trees >= 16 ? SOLVE_WARP : SOLVE_CTA128);
+    const bool warp = S.solve_mode == SOLVE_WARP;
+    const long long part_fma = S.solve_mode == SOLVE_CTA256 ? 12288 : 4096;
+    const long long max_width = warp ? 256 : (S.solve_mode == SOLVE_CTA128 ? 8 * 128 : 8 * 256);
+    // split `len` outputs into at least `want` parts of at most max_width
+    // (warp kernel: widths a multiple of 32 except the last)
+    auto split = [&](long long len, long long want) -> long long {
+        long long P = std::max({1LL, want, (len + max_width - 1) / max_width});
+        if (warp && len > 32) {
+            const long long wdt = ((len + P - 1) / P + 31) / 32 * 32;
+            P = (len + wdt - 1) / wdt;
+        }
+        return P;
+    };
     S.parts_f.assign(F, 1);
     S.parts_b.assign(F, 1);
     for (int f = 0; f < F; ++f) {
         const long long kk = S.k[f], mm = S.n[f] - S.k[f], nn = S.n[f];
-        long long pf = (kk * mm + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
+        long long pf = (kk * mm + part_fma - 1) / part_fma;
         pf = std::max(1LL, std::min({pf, 32LL, std::max(1LL, mm)}));
-        pf = std::max(pf, (mm + 2047) / 2048);  // at most 2048 columns per part
-        long long pb = (kk * nn + SOLVE_PART_FMA - 1) / SOLVE_PART_FMA;
+        pf = split(mm, pf);
+        long long pb = (kk * nn + part_fma - 1) / part_fma;
         pb = std::max(1LL, std::min({pb, 32LL, std::max(1LL, kk / 8)}));
-        pb = std::max(pb, (kk + 2047) / 2048);  // at most 2048 rows per part
+        pb = split(kk, pb);
         if (pf > 64 || pb > 64) return "front too large for the tree solve";
         S.parts_f[f] = (int)pf;
         S.parts_b[f] = (int)pb;
     }
+    // part q of P over len outputs: [bound(q), bound(q+1))
+    auto bound = [&](long long len, long long P, long long q) -> int {
+        if (warp && len > 32) {
+            const long long wdt = ((len + P - 1) / P + 31) / 32 * 32;
+            return (int)std::min(len, wdt * q);
+        }
+        return (int)(len * q / P);
+    };
+    S.crec.resize(S.child_list.size());
+    for (int f = 0; f < F; ++f)
+        for (int ci = S.child_ptr[f]; ci < S.child_ptr[f + 1]; ++ci) {
+            const int c = S.child_list[ci];
+            S.crec[ci] = ChildRec{c, S.parts_f[c], S.n[c] - S.k[c], 0, S.rel_ptr[c], S.upd_off[c]};
+        }
     {
         std::vector<int> byh(F);
         for (int f = 0; f < F; ++f) byh[f] = f;
         std::stable_sort(byh.begin(), byh.end(), [&](int a, int b) { return S.height[a] < S.height[b]; });
         S.sitems.clear();
         S.qitems.clear();
+        S.max_panel = 0;
         long long off = 0;
-        auto add = [&](int f, int lo, int hi, long long elems_per_ld_unit, bool) {
-            SolveItem it;
+        auto add = [&](int f, int lo, int hi, long long elems_per_ld_unit) {
+            SolveItem it{};
             it.front = f;
             it.lo = lo;
             it.hi = hi;
             it.ldp = std::max(4, (hi - lo + 3) / 4 * 4);
             it.off = off;
+            it.k = S.k[f];
+            it.n = S.n[f];
+            it.b0 = S.node_ptr[f];
+            it.wait_parts = S.parts_f[f];
+            it.upd_off = S.upd_off[f];
+            it.fpos = S.front_ptr[f];
+            it.c0 = S.child_ptr[f];
+            it.c1 = S.child_ptr[f + 1];
+            it.parent = S.parent[f];
+            it.parent_parts = S.parent[f] >= 0 ? S.parts_b[S.parent[f]] : 0;
             const long long cnt = (long long)it.ldp * elems_per_ld_unit;
+            S.max_panel = std::max(S.max_panel, cnt);
             const int idx = (int)S.sitems.size();
             for (long long e0 = 0; e0 < cnt; e0 += 4096) S.qitems.push_back({idx, (int)e0});
             off += cnt;
@@ -158,14 +208,12 @@ std::string finish_symbolic(Symbolic& S) {
         };
         for (int f : byh) {  // forward, ascending height
             const int kk = S.k[f], mm = S.n[f] - S.k[f], P = S.parts_f[f];
-            for (int q = 0; q < P; ++q)
-                add(f, kk + (int)((long long)mm * q / P), kk + (int)((long long)mm * (q + 1) / P), kk, true);
+            for (int q = 0; q < P; ++q) add(f, kk + bound(mm, P, q), kk + bound(mm, P, q + 1), kk);
         }
         S.n_fwd_items = (int)S.sitems.size();
         for (int i = F - 1; i >= 0; --i) {  // backward, descending height
             const int f = byh[i], kk = S.k[f], P = S.parts_b[f];
-            for (int q = 0; q < P; ++q)
-                add(f, (int)((long long)kk * q / P), (int)((long long)kk * (q + 1) / P), S.n[f], false);
+            for (int q = 0; q < P; ++q) add(f, bound(kk, P, q), bound(kk, P, q + 1), S.n[f]);
         }
         S.q_size = off;
     }

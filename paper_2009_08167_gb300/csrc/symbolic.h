@@ -26,11 +26,30 @@ struct PanelItem { int front; int r0; };            // TRSM row block of a front
 struct TileItem { int front; int i0; int j0; };     // trailing-update tile
 struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
 
+// tree-solve kernel shapes: 256-thread CTAs per item (large fronts),
+// 128-thread CTAs (small fronts, few trees), one warp per item (small fronts,
+// a batch of many trees)
+enum { SOLVE_CTA256 = 0, SOLVE_CTA128 = 1, SOLVE_WARP = 2 };
+
 struct SolveItem {   // one work item of the persistent tree solve
     int front;
     int lo, hi;       // forward: border columns [lo,hi) (front numbering, k <= lo); backward: own rows [lo,hi)
     int ldp;          // panel leading dimension, multiple of 4
     long long off;    // panel offset in the Q pool (elements, multiple of 4)
+    // the front's data the item needs, packed so that one load fetches it
+    int k, n, b0;     // own / front size, first own position
+    int wait_parts;   // backward: forward parts of this front to wait for
+    long long upd_off, fpos;  // update-vector offset, index-list offset of the front
+    int c0, c1;       // forward: the front's children, records [c0, c1) of Symbolic::crec
+    int parent, parent_parts;  // backward: parent front (-1: root) and its backward parts
+};
+
+struct ChildRec {    // one child of a front, as the forward solve reads it
+    int child;       // child front
+    int parts;       // its forward parts (all must be done)
+    int m;           // its update-vector length n - k
+    int pad;
+    long long rel_off, upd_off;  // its relative indices and update vector
 };
 
 struct StepRange {   // one panel step of one level
@@ -94,6 +113,9 @@ struct Symbolic {
     //   backward part [lo,hi) of rows 0..k: column-major ldp x n panel of
     //                 [-A11^{-1} | -A11^{-1} A12] (ldp = hi-lo rounded up to 4).
     std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
+    std::vector<ChildRec> crec;       // per child_list entry
+    int solve_mode = 0;               // SOLVE_CTA256 / SOLVE_CTA128 / SOLVE_WARP (finish_symbolic)
+    long long max_panel = 0;          // largest solve-item panel (elements)
     int n_fwd_items = 0;
     std::vector<int> parts_f, parts_b;
     long long q_size = 0;

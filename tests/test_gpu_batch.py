@@ -102,6 +102,40 @@ def test_batch_eigs_shifted(R):
         assert np.max(np.abs(ev[b] - ref) / ref) <= 1e-10, b
 
 
+def _many_batch():
+    """Twenty small 2D problems: a batch wide enough for the warp-per-item
+    solve kernel (at least 16 trees)."""
+    meshes, cK = [], []
+    for b in range(20):
+        ne = 6 + (7 * b) % 11
+        m = Mesh(2, [ne, ne + b % 3], 2 + b % 2, 3 + b % 4, 3 + b % 5)
+        meshes.append(m)
+        cK.append(np.exp(normal(300 + b, m.n_elem, 0.5)))
+    return meshes, cK
+
+
+def test_batch_many_trees_solve_and_eigs(R):
+    meshes, cK = _many_batch()
+    R.assemble_batch(meshes, cK)
+    mats = _block_oracle(meshes, cK)
+    lams = [eigen.ghep_dense(K.todense(), M.todense())[0] for K, M in mats]
+    sigma = 0.5 * (np.sort(np.concatenate(lams))[100] + np.sort(np.concatenate(lams))[101])
+    assert R.factor(sigma) == int(sum(np.sum(l < sigma) for l in lams))
+    N = sum(K.n for K, _ in mats)
+    b = np.random.default_rng(21).normal(size=N)
+    x, _ = R.solve(b)
+    r0 = 0
+    for (K, M) in mats:
+        xr = np.linalg.solve(K.todense() - sigma * M.todense(), b[r0:r0 + K.n])
+        assert np.linalg.norm(x[r0:r0 + K.n] - xr) <= 1e-10 * np.linalg.norm(xr)
+        r0 += K.n
+    k = 6
+    ev, rs, nc = R.eigs_batch(k, 0.0, 1e-12)
+    assert np.all(nc == k) and np.all(rs <= 1e-10)
+    for bb, lam in enumerate(lams):
+        assert np.max(np.abs(ev[bb] - lam[:k]) / lam[:k]) <= 1e-10, bb
+
+
 def test_batch_errors(R):
     from paper_2009_08167_gb300.riga import RigaError, RIGA_EINVAL, RIGA_ESTATE
     meshes, cK = _small_batch()
