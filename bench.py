@@ -526,7 +526,10 @@ def run_kernel_mode(args, local_rank):
     prec = riga.RIGA_FP64 if args.precision == "fp64" else riga.RIGA_FP32
     cfg = workload(args.mesh)
     R = riga.Riga(local_rank, stream)
-    R.assemble(cfg["mesh"])
+    if cfg.get("batch"):
+        R.assemble_batch(cfg["meshes"], cfg["coefK"])
+    else:
+        R.assemble(cfg["mesh"])
     N = R.query()["N"]
     b = torch.randn(N, dtype=torch.float64, device="cuda")
     x = torch.empty_like(b)

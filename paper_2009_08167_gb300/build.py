@@ -68,7 +68,7 @@ def build(verbose=False, jobs=None):
         raise RuntimeError("compilation failed: " + ", ".join(failed))
     if cmds or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+        link = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"]
         p = subprocess.run(link, capture_output=True, text=True)
         if p.returncode:
             sys.stderr.write(" ".join(link) + "\n" + p.stdout + p.stderr)

@@ -87,10 +87,8 @@ __device__ void basis_span(const int* kv, double inv_ne, int p, int sp, double x
     }
 }
 
-__global__ void elem1d_kernel(int ne, int p, const int* __restrict__ kv, const int* __restrict__ elem_first,
-                              double* __restrict__ Ke, double* __restrict__ Me) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
+__device__ void elem1d_one(int e, int ne, int p, const int* __restrict__ kv, const int* __restrict__ elem_first,
+                           double* __restrict__ Ke, double* __restrict__ Me) {
     const int nq = p + 1, q = p + 1;
     double t[PMAX + 1], w[PMAX + 1];
     gauss_legendre_dev(nq, t, w);
@@ -115,13 +113,17 @@ __global__ void elem1d_kernel(int ne, int p, const int* __restrict__ kv, const i
     }
 }
 
+__global__ void elem1d_kernel(int ne, int p, const int* __restrict__ kv, const int* __restrict__ elem_first,
+                              double* __restrict__ Ke, double* __restrict__ Me) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < ne) elem1d_one(e, ne, p, kv, elem_first, Ke, Me);
+}
+
 // banded 1D matrix: B[i*(2p+1) + (j-i+p)] for DOFs i, j (after Dirichlet removal)
-__global__ void band1d_kernel(int ndof, int p, const int* __restrict__ kv, const int* __restrict__ elem_first,
-                              const double* __restrict__ Ke, const double* __restrict__ Me,
-                              double* __restrict__ Kb, double* __restrict__ Mb) {
+__device__ void band1d_one(int idx, int ndof, int p, const int* __restrict__ kv, const int* __restrict__ elem_first,
+                           const double* __restrict__ Ke, const double* __restrict__ Me, double* __restrict__ Kb,
+                           double* __restrict__ Mb) {
     const int w = 2 * p + 1, q = p + 1;
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= ndof * w) return;
     int i = idx / w, d = idx % w, j = i + d - p;
     double ks = 0.0, ms = 0.0;
     if (j >= 0 && j < ndof) {
@@ -137,6 +139,13 @@ __global__ void band1d_kernel(int ndof, int p, const int* __restrict__ kv, const
     Mb[idx] = ms;
 }
 
+__global__ void band1d_kernel(int ndof, int p, const int* __restrict__ kv, const int* __restrict__ elem_first,
+                              const double* __restrict__ Ke, const double* __restrict__ Me,
+                              double* __restrict__ Kb, double* __restrict__ Mb) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < ndof * (2 * p + 1)) band1d_one(idx, ndof, p, kv, elem_first, Ke, Me, Kb, Mb);
+}
+
 struct DirDev {
     const int* kv;
     const int* ef;
@@ -148,14 +157,11 @@ struct DirDev {
     int ne;
 };
 
-__global__ void csr_kron_kernel(int dim, int p, long long N, long long row0, long long goff,
-                                const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                const int* __restrict__ perm, DirDev X, DirDev Y, DirDev Z, double* __restrict__ Kv,
-                                double* __restrict__ Mv) {
-    const int lane = threadIdx.x & 31;
-    long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= N) return;
-    row += row0;
+// one row of the CSR (one warp), constant coefficients
+__device__ __forceinline__ void csr_kron_row(int dim, int p, long long row, long long goff, int lane,
+                                             const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                             const int* __restrict__ perm, const DirDev& X, const DirDev& Y,
+                                             const DirDev& Z, double* __restrict__ Kv, double* __restrict__ Mv) {
     const int w = 2 * p + 1;
     int g = (int)(perm[row] - goff);
     int ix = g % X.n, rem = g / X.n;
@@ -186,21 +192,27 @@ __global__ void csr_kron_kernel(int dim, int p, long long N, long long row0, lon
     }
 }
 
+__global__ void csr_kron_kernel(int dim, int p, long long N, long long row0, long long goff,
+                                const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const int* __restrict__ perm, DirDev X, DirDev Y, DirDev Z, double* __restrict__ Kv,
+                                double* __restrict__ Mv) {
+    long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row < N) csr_kron_row(dim, p, row + row0, goff, threadIdx.x & 31, rowptr, col, perm, X, Y, Z, Kv, Mv);
+}
+
 __device__ __forceinline__ void elem_range(const DirDev& D, int p, int i, int j, int& lo, int& hi) {
     int f = i + 1, g = j + 1;
     lo = max(D.kv[f], D.kv[g]);
     hi = min(D.kv[f + p + 1], D.kv[g + p + 1]);
 }
 
-__global__ void csr_coef_kernel(int dim, int p, long long N, long long row0, long long goff,
-                                const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                const int* __restrict__ perm, DirDev X, DirDev Y, DirDev Z,
-                                const double* __restrict__ cK, const double* __restrict__ cM, double* __restrict__ Kv,
-                                double* __restrict__ Mv) {
-    const int lane = threadIdx.x & 31;
-    long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= N) return;
-    row += row0;
+// one row of the CSR (one warp), per-element coefficients
+__device__ __forceinline__ void csr_coef_row(int dim, int p, long long row, long long goff, int lane,
+                                             const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                             const int* __restrict__ perm, const DirDev& X, const DirDev& Y,
+                                             const DirDev& Z, const double* __restrict__ cK,
+                                             const double* __restrict__ cM, double* __restrict__ Kv,
+                                             double* __restrict__ Mv) {
     const int q = p + 1, qq = q * q;
     int g = (int)(perm[row] - goff);
     int ix = g % X.n, rem = g / X.n;
@@ -256,11 +268,125 @@ __global__ void csr_coef_kernel(int dim, int p, long long N, long long row0, lon
     }
 }
 
-// Assembles one problem (its 1D data in P) into rows [row0, row0 + P.N) of the
-// context's CSR; goff is the problem's first global DOF.  cK / cM: device
-// coefficient arrays of the problem (NULL = constant).
-int assemble_problem(riga_ctx* c, const Symbolic& P, long long row0, long long goff, const double* cK,
-                     const double* cM) {
+__global__ void csr_coef_kernel(int dim, int p, long long N, long long row0, long long goff,
+                                const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                const int* __restrict__ perm, DirDev X, DirDev Y, DirDev Z,
+                                const double* __restrict__ cK, const double* __restrict__ cM, double* __restrict__ Kv,
+                                double* __restrict__ Mv) {
+    long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row < N)
+        csr_coef_row(dim, p, row + row0, goff, threadIdx.x & 31, rowptr, col, perm, X, Y, Z, cK, cM, Kv, Mv);
+}
+
+// ------------------------------------------------------------------ batches
+// All problems of a batch in three launches: the 1D element matrices of every
+// (problem, direction) segment, the banded 1D matrices, and the CSR rows,
+// each row finding its problem (and that problem's segments) from its
+// position.
+__device__ __forceinline__ int find_segment(const long long* __restrict__ prefix, int nseg, long long t) {
+    int lo = 0, hi = nseg;  // prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void elem1d_batch_kernel(int nseg, const long long* __restrict__ eprefix, const SegDev* __restrict__ segs,
+                                    const int* __restrict__ kv, const int* __restrict__ ef, double* __restrict__ Ke,
+                                    double* __restrict__ Me) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= eprefix[nseg]) return;
+    const int sgi = find_segment(eprefix, nseg, t);
+    const SegDev sg = segs[sgi];
+    elem1d_one((int)(t - eprefix[sgi]), sg.ne, sg.p, kv + sg.kv_off, ef + sg.ef_off, Ke + sg.ke_off, Me + sg.ke_off);
+}
+
+__global__ void band1d_batch_kernel(int nseg, const long long* __restrict__ bprefix, const SegDev* __restrict__ segs,
+                                    const int* __restrict__ kv, const int* __restrict__ ef,
+                                    const double* __restrict__ Ke, const double* __restrict__ Me,
+                                    double* __restrict__ Kb, double* __restrict__ Mb) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= bprefix[nseg]) return;
+    const int sgi = find_segment(bprefix, nseg, t);
+    const SegDev sg = segs[sgi];
+    band1d_one((int)(t - bprefix[sgi]), sg.ndof, sg.p, kv + sg.kv_off, ef + sg.ef_off, Ke + sg.ke_off,
+               Me + sg.ke_off, Kb + sg.kb_off, Mb + sg.kb_off);
+}
+
+__global__ void csr_batch_kernel(long long N, const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                 const int* __restrict__ perm, const int* __restrict__ prob_of_pos,
+                                 const ProbDev* __restrict__ probs, const SegDev* __restrict__ segs,
+                                 const int* __restrict__ kv, const int* __restrict__ ef, const double* __restrict__ Ke,
+                                 const double* __restrict__ Me, const double* __restrict__ Kb,
+                                 const double* __restrict__ Mb, const double* __restrict__ cK,
+                                 const double* __restrict__ cM, double* __restrict__ Kv, double* __restrict__ Mv) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= N) return;
+    const ProbDev pr = probs[prob_of_pos[row]];
+    DirDev d[3];
+    for (int a = 0; a < 3; ++a) {
+        d[a] = DirDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, 1};
+        if (a >= pr.dim) continue;
+        const SegDev sg = segs[pr.seg0 + a];
+        d[a] = DirDev{kv + sg.kv_off, ef + sg.ef_off, Ke + sg.ke_off, Me + sg.ke_off, Kb + sg.kb_off, Mb + sg.kb_off,
+                      sg.ndof, sg.ne};
+    }
+    const int lane = threadIdx.x & 31;
+    if (cK || cM)
+        csr_coef_row(pr.dim, pr.p, row, pr.goff, lane, rowptr, col, perm, d[0], d[1], d[2], cK ? cK + pr.e0 : nullptr,
+                     cM ? cM + pr.e0 : nullptr, Kv, Mv);
+    else
+        csr_kron_row(pr.dim, pr.p, row, pr.goff, lane, rowptr, col, perm, d[0], d[1], d[2], Kv, Mv);
+}
+
+// The batch's 1D data (knot vectors, element-to-function maps) and the
+// descriptors of its segments and problems, uploaded once per batch pattern.
+int prepare_batch_assembly(riga_ctx* c) {
+    cudaStream_t st = c->stream;
+    std::vector<int> kv, ef;
+    std::vector<SegDev> segs;
+    std::vector<ProbDev> probs;
+    std::vector<long long> ep{0}, bp{0};
+    long long ke = 0, kb = 0;
+    for (size_t b = 0; b < c->probs.size(); ++b) {
+        const Symbolic& P = c->probs[b];
+        ProbDev pd{P.dim, P.p, (int)segs.size(), 0, c->S.prob_pos[b], c->S.prob_pos[b], c->S.prob_elem[b]};
+        probs.push_back(pd);
+        const int q = P.p + 1, w = 2 * P.p + 1;
+        for (int a = 0; a < P.dim; ++a) {
+            const Dir1D& D = P.dir[a];
+            SegDev sg{D.ne, P.p, D.ndof, 0, (long long)kv.size(), (long long)ef.size(), ke, kb};
+            kv.insert(kv.end(), D.kv.begin(), D.kv.end());
+            ef.insert(ef.end(), D.elem_first.begin(), D.elem_first.end());
+            ke += (long long)D.ne * q * q;
+            kb += (long long)D.ndof * w;
+            ep.push_back(ep.back() + D.ne);
+            bp.push_back(bp.back() + (long long)D.ndof * w);
+            segs.push_back(sg);
+        }
+    }
+    c->b_nseg = (int)segs.size();
+    c->b_nelem1d = ep.back();
+    c->b_nband = bp.back();
+    RIGA_CUDA_TRY(c, c->b_kv.upload(kv, st));
+    RIGA_CUDA_TRY(c, c->b_ef.upload(ef, st));
+    RIGA_CUDA_TRY(c, c->b_segs.upload(segs, st));
+    RIGA_CUDA_TRY(c, c->b_probs.upload(probs, st));
+    RIGA_CUDA_TRY(c, c->b_eprefix.upload(ep, st));
+    RIGA_CUDA_TRY(c, c->b_bprefix.upload(bp, st));
+    RIGA_CUDA_TRY(c, c->b_Ke.alloc(ke));
+    RIGA_CUDA_TRY(c, c->b_Me.alloc(ke));
+    RIGA_CUDA_TRY(c, c->b_Kb.alloc(kb));
+    RIGA_CUDA_TRY(c, c->b_Mb.alloc(kb));
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return RIGA_OK;
+}
+
+// Assembles a single problem (its 1D data in P).  cK / cM: device
+// coefficient arrays (NULL = constant).
+int assemble_problem(riga_ctx* c, const Symbolic& P, const double* cK, const double* cM) {
     cudaStream_t st = c->stream;
     DirDev dd[3];
     for (int a = 0; a < 3; ++a) {
@@ -285,10 +411,10 @@ int assemble_problem(riga_ctx* c, const Symbolic& P, long long row0, long long g
     long long threads = P.N * 32;
     int blocks = (int)((threads + 255) / 256);
     if (!cK && !cM) {
-        { count_launch(c); csr_kron_kernel<<<blocks, 256, 0, st>>>(P.dim, P.p, P.N, row0, goff, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
+        { count_launch(c); csr_kron_kernel<<<blocks, 256, 0, st>>>(P.dim, P.p, P.N, 0, 0, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
                                                 dd[0], dd[1], dd[2], c->Kval.ptr, c->Mval.ptr); }
     } else {
-        { count_launch(c); csr_coef_kernel<<<blocks, 256, 0, st>>>(P.dim, P.p, P.N, row0, goff, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
+        { count_launch(c); csr_coef_kernel<<<blocks, 256, 0, st>>>(P.dim, P.p, P.N, 0, 0, c->rowptr.ptr, c->col.ptr, c->perm.ptr,
                                                 dd[0], dd[1], dd[2], cK, cM, c->Kval.ptr, c->Mval.ptr); }
     }
     RIGA_CUDA_TRY(c, cudaGetLastError());
@@ -311,14 +437,18 @@ int assemble_device(riga_ctx* c) {
         RIGA_CUDA_TRY(c, c->dcoefM.upload(c->coefM, st));
         cM = c->dcoefM.ptr;
     }
-    if (S.dim > 0) return assemble_problem(c, S, 0, 0, cK, cM);
-    // batch: one problem at a time into its rows of the merged CSR
-    for (size_t b = 0; b < c->probs.size(); ++b) {
-        const long long e0 = S.prob_elem[b];
-        int rc = assemble_problem(c, c->probs[b], S.prob_pos[b], S.prob_pos[b], cK ? cK + e0 : nullptr,
-                                  cM ? cM + e0 : nullptr);
-        if (rc) return rc;
-    }
+    if (S.dim > 0) return assemble_problem(c, S, cK, cM);
+    // batch: every problem in three launches
+    if (c->b_nseg < 1) return set_error(c, RIGA_ESTATE, "batch assembly data missing");
+    { count_launch(c); elem1d_batch_kernel<<<(unsigned)((c->b_nelem1d + 127) / 128), 128, 0, st>>>(
+        c->b_nseg, c->b_eprefix.ptr, c->b_segs.ptr, c->b_kv.ptr, c->b_ef.ptr, c->b_Ke.ptr, c->b_Me.ptr); }
+    { count_launch(c); band1d_batch_kernel<<<(unsigned)((c->b_nband + 127) / 128), 128, 0, st>>>(
+        c->b_nseg, c->b_bprefix.ptr, c->b_segs.ptr, c->b_kv.ptr, c->b_ef.ptr, c->b_Ke.ptr, c->b_Me.ptr, c->b_Kb.ptr,
+        c->b_Mb.ptr); }
+    { count_launch(c); csr_batch_kernel<<<(unsigned)((S.N * 32 + 255) / 256), 256, 0, st>>>(
+        S.N, c->rowptr.ptr, c->col.ptr, c->perm.ptr, c->prob_of_pos.ptr, c->b_probs.ptr, c->b_segs.ptr, c->b_kv.ptr,
+        c->b_ef.ptr, c->b_Ke.ptr, c->b_Me.ptr, c->b_Kb.ptr, c->b_Mb.ptr, cK, cM, c->Kval.ptr, c->Mval.ptr); }
+    RIGA_CUDA_TRY(c, cudaGetLastError());
     return RIGA_OK;
 }
 

@@ -11,6 +11,7 @@
 // problem in one factorization of the forest (per-position shifts), and the
 // Sylvester inertia is counted per problem.  FP64 fronts.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -399,6 +400,10 @@ int factor_batch(riga_ctx* c, const std::vector<double>& sig, bool inertia_only)
 // Outputs in c->batch_evals / batch_resid / batch_nconv (problem-major).
 int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     static const bool dbg = std::getenv("RIGA_DEBUG") != nullptr;
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    double t_checks = 0.0, t_rr = 0.0, t_start = 0.0, t_fact = 0.0;
+    const clk::time_point t_all = clk::now();
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     const int P = (int)S.prob_pos.size() - 1;
@@ -466,11 +471,13 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     std::vector<char> done(P, 0);
     std::vector<int> need(P, want);
     std::vector<double> sig0(P, sigma0);
+    clk::time_point t0 = clk::now();
     int rc = factor_batch(c, sig0, false);
+    t_fact += ms_since(t0);
     if (rc) return rc;
     std::vector<long long> nu0 = c->inertia_prob;
     uint64_t seed = c->opt_seed ? c->opt_seed : 1;
-    std::vector<double> h_alpha, h_beta, theta, zl, Zf, hv(N);
+    std::vector<double> h_alpha, h_beta, hv(N);
     int status = RIGA_OK;
     for (int run = 1; run <= 4; ++run) {
         int active = 0;
@@ -495,12 +502,14 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
                 N, Lmax, c->prob_of_pos.ptr, B.nlock.ptr, c->V.ptr, c->MV.ptr, B.ld); }
         }
         // start vectors: random on active problems, zero on the others
+        t0 = clk::now();
         for (int b = 0; b < P; ++b)
             for (long long r = S.prob_pos[b]; r < S.prob_pos[b + 1]; ++r)
                 hv[r] = done[b] ? 0.0 : ((double)(bsplitmix(seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
         if (Lmax > 0) bortho(B, Lmax, w);
         bnormalize(B, w, Mw, col0, -1, Lmax > 0 ? Lmax : 1);
+        t_start += ms_since(t0);
         int m = 0;
         for (int j = 0; j < m_max; ++j) {
             const int col = col0 + j;
@@ -523,23 +532,27 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
                 RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_beta.data(), B.ab_beta.ptr, h_beta.size() * sizeof(double),
                                                  cudaMemcpyDeviceToHost, st));
                 RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
-                bool all = true;
-                for (int b = 0; b < P && all; ++b) {
-                    if (done[b]) continue;
+                t0 = clk::now();
+                // per problem: are its wanted Ritz values converged?
+                std::vector<char> conv(P, 1);
+                parallel_for(P, [&](int b) {
+                    if (done[b]) return;
                     const double* a = h_alpha.data() + (size_t)b * m_cap;
                     const double* bt = h_beta.data() + (size_t)b * (m_cap + 1);
-                    theta.assign(m, 0.0);
-                    zl.assign(m, 0.0);
-                    tridiag_eig(m, a, bt + 1, theta.data(), zl.data(), false);
+                    std::vector<double> th(m), zz(m);
+                    tridiag_eig(m, a, bt + 1, th.data(), zz.data(), false);
                     const int wb = need[b] - nlock[b];
                     int ok = 0;
                     for (int i = m - 1; i >= 0 && ok < wb; --i) {
-                        if (!(theta[i] > 0.0)) break;
-                        if (std::fabs(bt[m] * zl[i]) <= tol_est * theta[i]) ++ok;
+                        if (!(th[i] > 0.0)) break;
+                        if (std::fabs(bt[m] * zz[i]) <= tol_est * th[i]) ++ok;
                         else break;
                     }
-                    if (ok < wb && bt[m] > 1e-300) all = false;
-                }
+                    conv[b] = !(ok < wb && bt[m] > 1e-300);
+                });
+                bool all = true;
+                for (int b = 0; b < P; ++b) all = all && conv[b];
+                t_checks += ms_since(t0);
                 if (all) break;
             }
         }
@@ -550,25 +563,26 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_alpha.data(), B.ab_alpha.ptr, h_alpha.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_beta.data(), B.ab_beta.ptr, h_beta.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        t0 = clk::now();
         const int qmax = want;
         std::vector<double> hW((size_t)P * m * qmax, 0.0), hl((size_t)P * qmax, 0.0);
         std::vector<int> nsel(P, 0);
-        for (int b = 0; b < P; ++b) {
-            if (done[b]) continue;
+        parallel_for(P, [&](int b) {
+            if (done[b]) return;
             const double* a = h_alpha.data() + (size_t)b * m_cap;
             const double* bt = h_beta.data() + (size_t)b * (m_cap + 1);
-            theta.assign(m, 0.0);
-            Zf.assign((size_t)m * m, 0.0);
-            tridiag_eig(m, a, bt + 1, theta.data(), Zf.data(), true);
+            std::vector<double> th(m), Z((size_t)m * m);
+            tridiag_eig(m, a, bt + 1, th.data(), Z.data(), true);
             const int room = std::min(qmax, lock_cap - nlock[b]);
             for (int i = m - 1; i >= 0 && nsel[b] < room; --i) {
-                if (!(theta[i] > 0.0)) break;
-                if (std::fabs(bt[m] * Zf[(size_t)i * m + m - 1]) > tol_est * theta[i]) continue;
+                if (!(th[i] > 0.0)) break;
+                if (std::fabs(bt[m] * Z[(size_t)i * m + m - 1]) > tol_est * th[i]) continue;
                 const int q = nsel[b]++;
-                for (int r = 0; r < m; ++r) hW[((size_t)b * qmax + q) * m + r] = Zf[(size_t)i * m + r];
-                hl[(size_t)b * qmax + q] = sigma0 + 1.0 / theta[i];
+                for (int r = 0; r < m; ++r) hW[((size_t)b * qmax + q) * m + r] = Z[(size_t)i * m + r];
+                hl[(size_t)b * qmax + q] = sigma0 + 1.0 / th[i];
             }
-        }
+        });
+        t_rr += ms_since(t0);
         RIGA_CUDA_TRY(c, B.W.upload(hW, st));
         RIGA_CUDA_TRY(c, B.lam.upload(hl, st));
         RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * qmax * 2));
@@ -627,7 +641,9 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
             ++checks;
         }
         if (checks > 0) {
+            t0 = clk::now();
             rc = factor_batch(c, sig_chk, true);
+            t_fact += ms_since(t0);
             if (rc) {
                 status = rc;
                 break;
@@ -642,7 +658,11 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
         }
         int nd = 0;
         for (int b = 0; b < P; ++b) nd += done[b];
-        if (dbg) std::fprintf(stderr, "[riga] batch run %d: steps=%d, problems complete %d/%d\n", run, m, nd, P);
+        if (dbg)
+            std::fprintf(stderr,
+                         "[riga] batch run %d: steps=%d, problems complete %d/%d; host ms: checks %.1f, "
+                         "tridiag RR %.1f, start %.1f, factor calls %.1f, total %.1f\n",
+                         run, m, nd, P, t_checks, t_rr, t_start, t_fact, ms_since(t_all));
         if (status) break;
     }
     // outputs: the k smallest locked eigenvalues per problem
@@ -709,6 +729,8 @@ extern "C" int riga_assemble_batch(riga_ctx* c, int nprob, const riga_mesh* mesh
         std::string err = merge_symbolic(c->S, c->probs);
         if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
         int rc0 = upload_symbolic(c);
+        if (rc0) return rc0;
+        rc0 = prepare_batch_assembly(c);
         if (rc0) return rc0;
         c->mesh_key = key;  // starts with -1: never equal to a single mesh's key
     }

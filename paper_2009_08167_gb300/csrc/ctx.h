@@ -2,8 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/riga.h"
@@ -65,6 +67,19 @@ struct Profile {
 
 }  // namespace riga
 
+namespace riga {
+// batch assembly descriptors: one segment per (problem, direction)
+struct SegDev {
+    int ne, p, ndof, pad;
+    long long kv_off, ef_off, ke_off, kb_off;  // into the concatenated 1D arrays
+};
+struct ProbDev {
+    int dim, p, seg0, pad;   // seg0: the problem's first segment
+    long long row0, goff;    // first row / first global DOF
+    long long e0;            // first element (coefficient offset)
+};
+}  // namespace riga
+
 struct riga_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -95,6 +110,14 @@ struct riga_ctx {
     riga::DevBuf<int> kv[3], elem_first[3];
     riga::DevBuf<double> Ke1[3], Me1[3], Kb1[3], Mb1[3];
     riga::DevBuf<double> dcoefK, dcoefM;
+    // batch assembly: concatenated 1D data of all problems
+    riga::DevBuf<int> b_kv, b_ef;
+    riga::DevBuf<riga::SegDev> b_segs;
+    riga::DevBuf<riga::ProbDev> b_probs;
+    riga::DevBuf<long long> b_eprefix, b_bprefix;
+    riga::DevBuf<double> b_Ke, b_Me, b_Kb, b_Mb;
+    int b_nseg = 0;
+    long long b_nelem1d = 0, b_nband = 0;
 
     // matrices in elimination order (CSR of rowptr/col)
     riga::DevBuf<double> Kval, Mval;
@@ -157,6 +180,24 @@ int set_error(riga_ctx* c, int code, const std::string& msg);
             return ::riga::set_error((ctx), RIGA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
     } while (0)
 
+// f(i) for i in [0, n) on up to 16 host threads (independent iterations)
+template <typename Fn>
+void parallel_for(int n, Fn f) {
+    int nt = (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min({nt, 16, n / 8}));
+    if (nt <= 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([=]() {
+            for (int i = t; i < n; i += nt) f(i);
+        });
+    for (std::thread& x : th) x.join();
+}
+
 // one kernel launch, attributed to the current phase
 inline void count_launch(riga_ctx* c) {
     c->prof.launches++;
@@ -194,6 +235,7 @@ struct PhaseScope {
 int upload_symbolic(riga_ctx* c);  // symbolic arrays of c->S to the device
 // assemble.cu
 int assemble_device(riga_ctx* c);
+int prepare_batch_assembly(riga_ctx* c);  // once per batch pattern
 // factor.cu
 int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
 int finish_factor(riga_ctx* c);   // sync, read flag and inertia

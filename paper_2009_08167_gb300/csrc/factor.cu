@@ -14,7 +14,7 @@
 //     diag_kernel      LDL^T of the kb x kb diagonal block in shared memory,
 //                      pivots to D and the front diagonal, breakdown flag;
 //     trsm_kernel      L21 = A21 L11^{-T} D^{-1}, one thread per row;
-//     update_kernel    A22 -= L21 D L21^T on 64x64 lower tiles of the
+//     update_kernel    A22 -= L21 D L21^T on 32x32 lower tiles of the
 //                      trailing matrix (remaining fully summed part and the
 //                      Schur complement).
 // All items of one launch span every front of the level.  The original
@@ -24,7 +24,7 @@
 namespace riga {
 
 constexpr int NB = 32;    // panel width
-constexpr int TILE = 64;  // update tile
+constexpr int TILE = 32;  // update tile
 constexpr int RB = 64;    // TRSM rows per block
 
 template <typename T>
@@ -88,13 +88,17 @@ __global__ void extend_add_kernel(const ExtItem* __restrict__ items, const int* 
     }
 }
 
-// LDL^T of one kb x kb diagonal block per front (block of 256 threads).
+// LDL^T of one kb x kb diagonal block per front (block of 128 threads).
+// Column j stays unscaled while it updates the columns to its right (with
+// the reciprocal pivot, one division per column); the columns are scaled by
+// their reciprocal pivots when the block is written back.
 template <typename T>
-__global__ void diag_kernel(const PanelItem* __restrict__ items, const int* __restrict__ kk,
-                            const int* __restrict__ nn, const long long* __restrict__ front_off,
-                            const int* __restrict__ node_ptr, T* __restrict__ pool, double* __restrict__ D,
-                            int* __restrict__ flag) {
+__global__ void __launch_bounds__(128) diag_kernel(const PanelItem* __restrict__ items, const int* __restrict__ kk,
+                                                   const int* __restrict__ nn, const long long* __restrict__ front_off,
+                                                   const int* __restrict__ node_ptr, T* __restrict__ pool,
+                                                   double* __restrict__ D, int* __restrict__ flag) {
     __shared__ T Ls[NB][NB + 1];
+    __shared__ T inv[NB];
     const PanelItem it = items[blockIdx.x];
     const int F = it.front, k = kk[F], ld = nn[F] + k, j0 = it.r0;
     const int kb = min(NB, k - j0);
@@ -105,42 +109,56 @@ __global__ void diag_kernel(const PanelItem* __restrict__ items, const int* __re
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
-        const T d = Ls[j][j];
-        if (threadIdx.x == 0 && !(d != T(0) && isfinite((double)d))) atomicOr(flag, 1);
-        // trailing update of the block: a_rc -= a_rj a_cj / d, j < c <= r
-        const int m = kb - j - 1;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            int r = j + 1 + idx % m, cc = j + 1 + idx / m;
-            if (r >= cc) Ls[r][cc] -= Ls[r][j] * Ls[cc][j] / d;
+        if (threadIdx.x == 0) {
+            const T d = Ls[j][j];
+            if (!(d != T(0) && isfinite((double)d))) atomicOr(flag, 1);
+            inv[j] = T(1) / d;
         }
         __syncthreads();
-        for (int r = j + 1 + threadIdx.x; r < kb; r += blockDim.x) Ls[r][j] /= d;
+        // a_rc -= a_rj (a_cj / d_j) over the lower triangle j < c <= r < kb
+        const T ij = inv[j];
+        const int m = kb - j - 1, tri = m * (m + 1) / 2;
+        for (int idx = threadIdx.x; idx < tri; idx += blockDim.x) {
+            int rr = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+            while ((rr + 1) * (rr + 2) / 2 <= idx) ++rr;
+            while (rr * (rr + 1) / 2 > idx) --rr;
+            const int r = j + 1 + rr, cc = j + 1 + idx - rr * (rr + 1) / 2;
+            Ls[r][cc] -= Ls[r][j] * (Ls[cc][j] * ij);
+        }
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, cc = idx / kb;
-        if (r >= cc) A[(long long)(j0 + cc) * ld + j0 + r] = Ls[r][cc];
+        if (r > cc) A[(long long)(j0 + cc) * ld + j0 + r] = Ls[r][cc] * inv[cc];
+        else if (r == cc) A[(long long)(j0 + cc) * ld + j0 + r] = Ls[r][r];
     }
     for (int t = threadIdx.x; t < kb; t += blockDim.x) D[node_ptr[F] + j0 + t] = (double)Ls[t][t];
 }
 
-// Rows r0..r0+RB-1 of the panel below the diagonal block (blockDim = RB).
+// Rows r0..r0+RB-1 of the panel below the diagonal block (blockDim = RB):
+// x_t = (a_t - sum_{u<t} x_u d_u l_tu) / d_t with the products d_u l_tu and
+// the reciprocal pivots staged in shared memory.
 template <typename T>
 __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const int* __restrict__ kk,
                             const int* __restrict__ nn, const long long* __restrict__ front_off,
                             T* __restrict__ pool, int plain) {
-    __shared__ T Ls[NB][NB + 1];
-    __shared__ T ds[NB];
+    __shared__ T LD[NB][NB + 1];
+    __shared__ T ds[NB], dinv[NB];
     const PanelItem it = items[blockIdx.x];
     const int F = it.front, k = kk[F], ld = nn[F] + k;
     const int rmax = plain ? nn[F] : ld;  // plain: skip the extra rows
     if (it.r0 >= rmax) return;
     const int kb = min(NB, k - j0);
     T* A = pool + front_off[F];
+    for (int t = threadIdx.x; t < kb; t += blockDim.x) {
+        const T d = A[(long long)(j0 + t) * ld + j0 + t];
+        ds[t] = d;
+        dinv[t] = T(1) / d;
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, cc = idx / kb;
-        if (r > cc) Ls[r][cc] = A[(long long)(j0 + cc) * ld + j0 + r];
-        if (r == cc) ds[r] = A[(long long)(j0 + cc) * ld + j0 + r];
+        if (r > cc) LD[r][cc] = A[(long long)(j0 + cc) * ld + j0 + r] * ds[cc];
     }
     __syncthreads();
     const int r = it.r0 + threadIdx.x;
@@ -154,9 +172,8 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
         if (t < kb) {
             T s = x[t];
 #pragma unroll
-            for (int u = 0; u < NB; ++u)
-                if (u < t) s -= x[u] * ds[u] * Ls[t][u];
-            x[t] = s / ds[t];
+            for (int u = 0; u < t; ++u) s -= x[u] * LD[t][u];
+            x[t] = s * dinv[t];
         }
     }
 #pragma unroll
@@ -164,13 +181,13 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
         if (t < kb) A[(long long)(j0 + t) * ld + r] = x[t];
 }
 
-// C[i0:i0+64, j0:j0+64] -= L[:, panel] D L[:, panel]^T (256 threads, 4x4 each)
+// C[i0:i0+32, j0:j0+32] -= L[:, panel] D L[:, panel]^T (64 threads, 4x4 each)
 template <typename T>
-__global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict__ items, int p0,
-                                                     const int* __restrict__ kk, const int* __restrict__ nn,
-                                                     const long long* __restrict__ front_off,
-                                                     const int* __restrict__ node_ptr, const double* __restrict__ D,
-                                                     T* __restrict__ pool, int plain) {
+__global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__ items, int p0,
+                                                    const int* __restrict__ kk, const int* __restrict__ nn,
+                                                    const long long* __restrict__ front_off,
+                                                    const int* __restrict__ node_ptr, const double* __restrict__ D,
+                                                    T* __restrict__ pool, int plain) {
     __shared__ T As[NB][TILE];
     __shared__ T Bs[NB][TILE];
     const TileItem it = items[blockIdx.x];
@@ -180,7 +197,7 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
     T* A = pool + front_off[F];
     const double* d = D + node_ptr[F] + p0;
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < NB * TILE; idx += 256) {
+    for (int idx = tid; idx < NB * TILE; idx += 64) {
         int rr = idx % TILE, t = idx / TILE;
         T a = T(0), b = T(0);
         if (t < kb) {
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
         Bs[t][rr] = b;
     }
     __syncthreads();
-    const int tx = tid % 16, ty = tid / 16;
+    const int tx = tid % 8, ty = tid / 8;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -201,9 +218,9 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
     for (int t = 0; t < kb; ++t) {
         T av[4], bv[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[t][tx + 16 * a];
+        for (int a = 0; a < 4; ++a) av[a] = As[t][tx + 8 * a];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[t][ty + 16 * b];
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[t][ty + 8 * b];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -211,11 +228,11 @@ __global__ void __launch_bounds__(256) update_kernel(const TileItem* __restrict_
     }
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        int gj = it.j0 + ty + 16 * b;
+        int gj = it.j0 + ty + 8 * b;
         if (gj >= ld) continue;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            int gi = it.i0 + tx + 16 * a;
+            int gi = it.i0 + tx + 8 * a;
             // lower triangle, plus the whole extra x extra block
             if (gi < ld && (gi >= gj || (gi >= n && gj >= n)) && !(plain && gi >= n)) A[(long long)gj * ld + gi] -= acc[a][b];
         }
@@ -300,14 +317,14 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
         for (const StepRange& R : P.steps) {
             const int j0 = R.s * NB;
             if (R.d_end > R.d_begin)
-                { count_launch(c); diag_kernel<T><<<R.d_end - R.d_begin, 256, 0, st>>>(c->pitems.ptr + R.d_begin, c->kk.ptr, c->nn.ptr,
+                { count_launch(c); diag_kernel<T><<<R.d_end - R.d_begin, 128, 0, st>>>(c->pitems.ptr + R.d_begin, c->kk.ptr, c->nn.ptr,
                                                                     c->front_off.ptr, c->node_ptr.ptr, pool, c->D.ptr,
                                                                     c->flag.ptr); }
             if (R.p_end > R.p_begin)
                 { count_launch(c); trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
                                                                    c->nn.ptr, c->front_off.ptr, pool, plain); }
             if (R.t_end > R.t_begin)
-                { count_launch(c); update_kernel<T><<<R.t_end - R.t_begin, 256, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
+                { count_launch(c); update_kernel<T><<<R.t_end - R.t_begin, 64, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
                                                                       c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr,
                                                                       c->D.ptr, pool, plain); }
         }

@@ -123,7 +123,7 @@ struct Symbolic {
     long long upd_size = 0;
 
     // factorization schedule
-    int nb = 32, tile = 64, rowblk = 64;
+    int nb = 32, tile = 32, rowblk = 64;
     std::vector<LevelPlan> levels;
     std::vector<PanelItem> pitems;
     std::vector<TileItem> titems;
