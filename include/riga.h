@@ -132,7 +132,10 @@ int riga_factor(riga_ctx* ctx, double sigma, int precision, long long* n_neg);
 /*
  * riga_solve: x = (K - sigma M)^{-1} b for nrhs right-hand sides (columns of
  * length N, x-fastest numbering) with the last factorization: forward
- * elimination, D^{-1}, backward elimination over the assembly tree.  With an
+ * elimination, D^{-1}, backward elimination over the assembly tree.  Up to
+ * four columns share one traversal of the tree (each operator panel read
+ * once for all of them); the result of a column does not depend on how the
+ * columns are grouped.  With an
  * FP32 factor (or tol > 0) the FP64 residual b - (K - sigma M) x drives
  * iterative refinement until ||r||_2 <= tol ||b||_2 (tol <= 0 with an FP32
  * factor selects 1e-13); iters_out (may be NULL) receives the refinement

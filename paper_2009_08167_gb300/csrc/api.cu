@@ -321,25 +321,33 @@ int riga_solve(riga_ctx* c, const double* b, double* x, int nrhs, double tol, in
     cudaSetDevice(c->device);
     if (!c->factored) return set_error(c, RIGA_ESTATE, "riga_factor first");
     const long long N = c->S.N;
-    for (int i = 0; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
-    double* g = c->vwork[0].ptr;
-    double* y = c->vwork[1].ptr;
+    const bool refine = (c->precision != RIGA_FP64) || tol > 0.0;
+    // all columns in one buffer: one tree traversal carries up to four of them
+    DevBuf<double> g, y;
+    RIGA_CUDA_TRY(c, g.alloc((size_t)N * nrhs));
+    RIGA_CUDA_TRY(c, y.alloc((size_t)N * nrhs));
+    for (int i = 2; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    int rc = to_device(c, b, g.ptr, (size_t)N * nrhs);
+    if (rc) return rc;
+    enqueue_permute(c, g.ptr, y.ptr, 1, nrhs);
     int status = RIGA_OK;
-    for (int col = 0; col < nrhs; ++col) {
-        int rc = to_device(c, b + (long long)col * N, g, N);
+    if (!refine) {
+        rc = enqueue_solve(c, y.ptr, nrhs);
         if (rc) return rc;
-        enqueue_permute(c, g, y, 1, 1);
-        const bool refine = (c->precision != RIGA_FP64) || tol > 0.0;
-        double t = tol > 0.0 ? tol : 1e-13;
-        int sweeps = 1;
-        rc = solve_refined(c, y, c->vwork[2].ptr, c->vwork[3].ptr, t, refine ? 30 : 1, refine ? 1 : 0, &sweeps);
-        if (rc == RIGA_EREFINE) status = rc;
-        else if (rc) return rc;
-        if (iters_out) *iters_out = sweeps;
-        enqueue_permute(c, y, g, 0, 1);
-        rc = to_user(c, g, x + (long long)col * N, N);
-        if (rc) return rc;
+        if (iters_out) *iters_out = 1;
+    } else {
+        const double t = tol > 0.0 ? tol : 1e-13;
+        for (int col = 0; col < nrhs; ++col) {
+            int sweeps = 1;
+            rc = solve_refined(c, y.ptr + (long long)col * N, c->vwork[2].ptr, c->vwork[3].ptr, t, 30, 1, &sweeps);
+            if (rc == RIGA_EREFINE) status = rc;
+            else if (rc) return rc;
+            if (iters_out) *iters_out = sweeps;
+        }
     }
+    enqueue_permute(c, y.ptr, g.ptr, 0, nrhs);
+    rc = to_user(c, g.ptr, x, (size_t)N * nrhs);
+    if (rc) return rc;
     int dflag = 0;
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));

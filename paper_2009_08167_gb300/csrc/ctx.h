@@ -240,7 +240,8 @@ int prepare_batch_assembly(riga_ctx* c);  // once per batch pattern
 int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
 int finish_factor(riga_ctx* c);   // sync, read flag and inertia
 // solve.cu
-int enqueue_solve(riga_ctx* c, double* y);  // y := A^{-1} y in permuted order (one pass)
+int enqueue_solve(riga_ctx* c, double* y, int nrhs = 1);  // y := A^{-1} y (nrhs columns, stride N), permuted order
+int solve_max_rhs(riga_ctx* c);  // right-hand sides one tree traversal can carry (1, 2 or 4)
 int enqueue_spmv(riga_ctx* c, int which, const double* x, double* y, double alpha_shift);
 void enqueue_permute(riga_ctx* c, const double* in, double* out, int to_perm, int ncols);
 int solve_refined(riga_ctx* c, double* y, double* work_x, double* work_r, double tol, int max_sweeps,

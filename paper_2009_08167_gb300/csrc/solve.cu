@@ -46,8 +46,9 @@ struct TreeArgs {
     int chunk_elems;   // elements per shared-memory chunk buffer (two buffers)
     int max_n;
     double* upd;
-    double* y;
-    double* w1;        // assembled own right-hand sides (forward -> backward)
+    double* y;         // NR right-hand sides, column r at y + r * ldy
+    long long ldy;
+    double* w1;        // assembled own right-hand sides (forward -> backward), stride ldy
     int* done_f;       // completed forward parts per front (zeroed before the launch)
     int* done_b;       // completed backward parts per front
     int* counter;      // next work item (zeroed before the launch)
@@ -121,22 +122,26 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return true;
 }
 
-// acc[q] += sum over units u = ua+g, ua+g+G, ... < ub of P[u-ua][li + NT q] * w[u]
-// for the NA output slots of this thread (an exact count: predicated-off FP64
-// instructions still occupy GB300's narrow FP64 pipe).
-template <typename T, int NA, int NT>
+// acc[q][r] += sum over units u = ua+g, ua+g+G, ... < ub of P[u-ua][l0 + li + NT q] * w_r[u]
+// for the NA output slots of this thread and the NR right-hand sides (an
+// exact count: predicated-off FP64 instructions still occupy GB300's narrow
+// FP64 pipe).  Each panel entry read from shared memory serves NR products.
+template <typename T, int NA, int NT, int NR>
 __device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ldp, int ua, int ub, int g, int G,
-                                                 int li, int cnt, const T* __restrict__ w, T* acc) {
+                                                 int l0, int li, int cnt, const T* __restrict__ w, int ldw,
+                                                 T (*acc)[NR]) {
     for (int u = ua + g; u < ub; u += G) {
-        const T* row = P + (long long)(u - ua) * ldp;
-        const T x = w[u];
-        if (NA == 1) {
-            acc[0] += row[li] * x;
-        } else {
+        const T* row = P + (long long)(u - ua) * ldp + l0;
+        T x[NR];
 #pragma unroll
-            for (int q2 = 0; q2 < NA; ++q2) {
-                const int l = li + q2 * NT;
-                if (l < cnt) acc[q2] += row[l] * x;
+        for (int r = 0; r < NR; ++r) x[r] = w[r * ldw + u];
+#pragma unroll
+        for (int q2 = 0; q2 < NA; ++q2) {
+            const int l = li + q2 * NT;
+            if (l0 + l < cnt) {
+                const T pv = row[l];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[q2][r] += pv * x[r];
             }
         }
     }
@@ -157,17 +162,21 @@ __device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ld
 // stream units (forward: rows r; backward: columns j) times a multiplier
 // (w1(r), v(j)) accumulated into the part's outputs; threads split the
 // outputs and interleave the units, then reduce through shared memory.
+// NR right-hand sides (columns of y, w1 and of each front's update vector,
+// stride a.ldy / m) go through the same items: one panel read, NR products.
 // Everything an item needs to know about its front comes packed in the item
 // (and, for its children, in one record each), so that few dependent global
 // loads separate a claim from the arithmetic.
-template <typename T, int NT>
+template <typename T, int NT, int NR>
 __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
+    constexpr int NAMAX = (NR == 1) ? 8 : (NR == 2 ? 4 : 2);  // output slots per thread per pass
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* buf[2];
     buf[0] = reinterpret_cast<T*>(smem_raw);
     buf[1] = buf[0] + a.chunk_elems;
-    T* w = buf[1] + a.chunk_elems;  // front vector (n)
-    T* red = w + a.max_n;           // NT partial sums
+    T* w = buf[1] + a.chunk_elems;  // front vectors (NR x max_n)
+    T* red = w + NR * a.max_n;      // NT x NR partial sums
+    const int ldw = a.max_n;
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_item, s_ok;
     const int tid = threadIdx.x;
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         if (item >= a.n_items) return;
         const SolveItem it = a.items[item];
         const bool fwd = item < a.n_fwd;
-        const int F = it.front, k = it.k, n = it.n, b0 = it.b0;
+        const int F = it.front, k = it.k, n = it.n, b0 = it.b0, m = n - k;
         const int lo = it.lo, cnt = it.hi - it.lo, ldp = it.ldp;
         const T* q = Q + it.off;
         const int units = fwd ? k : n;  // rows (forward) or columns (backward) of the panel
@@ -226,87 +235,127 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         }
         if (fwd) {
             // w = [b(own); 0] + children's update vectors
-            for (int i = tid; i < n; i += NT) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
+            for (int t = tid; t < NR * n; t += NT) {
+                const int r = t / n, i = t - r * n;
+                w[r * ldw + i] = (i < k) ? (T)__ldcg(&a.y[(long long)r * a.ldy + b0 + i]) : T(0);
+            }
             __syncthreads();
             for (int ci = it.c0; ci < it.c1; ++ci) {
                 const ChildRec cr = a.crec[ci];
-                const int* r = a.rel + cr.rel_off;
-                const double* u = a.upd + cr.upd_off;
-                for (int i = tid; i < cr.m; i += NT) w[r[i]] += (T)__ldcg(&u[i]);
+                const int* rl = a.rel + cr.rel_off;
+                const double* u = a.upd + cr.upd_off * NR;
+                for (int t = tid; t < NR * cr.m; t += NT) {
+                    const int r = t / cr.m, i = t - r * cr.m;
+                    w[r * ldw + rl[i]] += (T)__ldcg(&u[(long long)r * cr.m + i]);
+                }
                 __syncthreads();
             }
             if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
-                for (int i = tid; i < k; i += NT) a.w1[b0 + i] = (double)w[i];
+                for (int t = tid; t < NR * k; t += NT) {
+                    const int r = t / k, i = t - r * k;
+                    a.w1[(long long)r * a.ldy + b0 + i] = (double)w[r * ldw + i];
+                }
         } else {
             const int* idx = a.front_pos + it.fpos;
-            for (int i = tid; i < n; i += NT)
-                w[i] = (i < k) ? -(T)__ldcg(&a.w1[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
+            for (int t = tid; t < NR * n; t += NT) {
+                const int r = t / n, i = t - r * n;
+                w[r * ldw + i] = (i < k) ? -(T)__ldcg(&a.w1[(long long)r * a.ldy + b0 + i])
+                                         : (T)__ldcg(&a.y[(long long)r * a.ldy + idx[i]]);
+            }
         }
         __syncthreads();
-        // thread layout: outputs l (columns or rows of the part) x unit groups g
+        // thread layout: outputs l (columns or rows of the part) x unit groups g;
+        // outputs beyond NAMAX * NT per thread take further passes over the
+        // (then whole) panel in shared memory
         const int cp = max(1, min(cnt, NT));
         const int G = max(1, NT / cp);
         const int li = tid % cp, g = tid / cp;
         const bool active = cnt > 0 && g < G;
-        const int na = (cnt + NT - 1) / NT;  // outputs per thread when cnt > NT (G = 1)
-        T acc[8];
+        const int npass = nchunks > 1 ? 1 : max(1, (cnt + NAMAX * NT - 1) / (NAMAX * NT));
+        for (int pass = 0; pass < npass; ++pass) {
+            const int l0 = pass * NAMAX * NT;
+            const int cl = min(cnt - l0, (nchunks > 1) ? cnt : NAMAX * NT);  // outputs of this pass
+            const int na = (cl + NT - 1) / NT;
+            T acc[(NR == 1) ? 8 : NAMAX][NR];
 #pragma unroll
-        for (int q2 = 0; q2 < 8; ++q2) acc[q2] = T(0);
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            const bool good = mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
-            if (__syncthreads_or(!good)) {
-                // a copy did not complete within the budget: wait once more
-                // (bounded) for it and for the next one, then leave
-                mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
-                if (c + 1 < nchunks) mbar_wait(&mbar[b ^ 1], parity[b ^ 1], a.err, a.spin_limit);
+            for (int q2 = 0; q2 < ((NR == 1) ? 8 : NAMAX); ++q2)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[q2][r] = T(0);
+            for (int c = 0; c < nchunks; ++c) {
+                const int b = c & 1;
+                if (pass == 0) {
+                    const bool good = mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
+                    if (__syncthreads_or(!good)) {
+                        // a copy did not complete within the budget: wait once more
+                        // (bounded) for it and for the next one, then leave
+                        mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
+                        if (c + 1 < nchunks) mbar_wait(&mbar[b ^ 1], parity[b ^ 1], a.err, a.spin_limit);
+                        __syncthreads();
+                        return;
+                    }
+                    parity[b] ^= 1u;
+                }
+                const int ua = c * upc, ub = min(units, ua + upc);
+                const T* P = buf[b];
+                if (active) {
+                    if (NR == 1) {
+                        switch (na) {
+                            case 1: accumulate_chunk<T, 1, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            case 2: accumulate_chunk<T, 2, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            case 3: accumulate_chunk<T, 3, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            case 4: accumulate_chunk<T, 4, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            case 5: accumulate_chunk<T, 5, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            case 6: accumulate_chunk<T, 6, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            case 7: accumulate_chunk<T, 7, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                            default: accumulate_chunk<T, 8, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc); break;
+                        }
+                    } else if (na == 1) {
+                        accumulate_chunk<T, 1, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc);
+                    } else if (NAMAX >= 2 && na == 2) {
+                        accumulate_chunk<T, (NAMAX >= 2 ? 2 : 1), NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc);
+                    } else if (NAMAX >= 4) {
+                        if (na == 3) accumulate_chunk<T, (NAMAX >= 3 ? 3 : 1), NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc);
+                        else accumulate_chunk<T, NAMAX, NT, NR>(P, ldp, ua, ub, g, G, l0, li, cnt, w, ldw, acc);
+                    }
+                }
                 __syncthreads();
-                return;
-            }
-            parity[b] ^= 1u;
-            const int ua = c * upc, ub = min(units, ua + upc);
-            const T* P = buf[b];
-            if (active) {
-                switch (na) {
-                    case 1: accumulate_chunk<T, 1, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 2: accumulate_chunk<T, 2, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 3: accumulate_chunk<T, 3, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 4: accumulate_chunk<T, 4, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 5: accumulate_chunk<T, 5, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 6: accumulate_chunk<T, 6, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    case 7: accumulate_chunk<T, 7, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
-                    default: accumulate_chunk<T, 8, NT>(P, ldp, ua, ub, g, G, li, cnt, w, acc); break;
+                if (pass == 0 && tid == 0 && c + 2 < nchunks) {
+                    fence_proxy_async();
+                    const int u2 = (c + 2) * upc, un2 = min(upc, units - u2);
+                    bulk_load(buf[b], q + (long long)u2 * ldp, (unsigned)(un2 * ldp * sizeof(T)), &mbar[b]);
                 }
             }
-            __syncthreads();
-            if (tid == 0 && c + 2 < nchunks) {
-                fence_proxy_async();
-                const int u2 = (c + 2) * upc, un2 = min(upc, units - u2);
-                bulk_load(buf[b], q + (long long)u2 * ldp, (unsigned)(un2 * ldp * sizeof(T)), &mbar[b]);
-            }
-        }
-        if (cnt > 0) {
-            if (G > 1) {
-                if (active) red[g * cp + li] = acc[0];
-                __syncthreads();
-                if (g == 0 && li < cnt) {
-                    T s = T(0);
-                    for (int g2 = 0; g2 < G; ++g2) s += red[g2 * cp + li];
-                    acc[0] = s;
-                }
-            }
-            if (g == 0) {
+            if (cl > 0) {
+                if (G > 1) {
+                    if (active)
 #pragma unroll
-                for (int q2 = 0; q2 < 8; ++q2) {
-                    const int l = li + q2 * NT;
-                    if (q2 < na && l < cnt) {
-                        if (fwd) a.upd[it.upd_off + lo + l - k] = (double)(w[lo + l] + acc[q2]);
-                        else a.y[b0 + lo + l] = (double)acc[q2];
+                        for (int r = 0; r < NR; ++r) red[(g * cp + li) * NR + r] = acc[0][r];
+                    __syncthreads();
+                    if (g == 0 && li < cl)
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            T s2 = T(0);
+                            for (int g2 = 0; g2 < G; ++g2) s2 += red[(g2 * cp + li) * NR + r];
+                            acc[0][r] = s2;
+                        }
+                }
+                if (g == 0) {
+#pragma unroll
+                    for (int q2 = 0; q2 < ((NR == 1) ? 8 : NAMAX); ++q2) {
+                        const int l = l0 + li + q2 * NT;
+                        if (q2 < na && l < cnt) {
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) {
+                                if (fwd) a.upd[it.upd_off * NR + (long long)r * m + lo + l - k] =
+                                             (double)(w[r * ldw + lo + l] + acc[q2][r]);
+                                else a.y[(long long)r * a.ldy + b0 + lo + l] = (double)acc[q2][r];
+                            }
+                        }
                     }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
         if (tid == 0) {
             __threadfence();
             atomicAdd(fwd ? &a.done_f[F] : &a.done_b[F], 1);
@@ -318,21 +367,21 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
 // ---------------------------------------------------------------------------
 // Warp-per-item variant for batches of many small trees, where the solve is
 // bound by how many items are in flight rather than by a critical path:
-// every warp is an independent worker with its own front vector in shared
+// every warp is an independent worker with its own front vectors in shared
 // memory, so that dozens of items per SM overlap their dependency waits and
 // gathers.  The item's panel is prefetched into L2 by one bulk prefetch when
 // the item is claimed (before its dependency wait) and then read once with
-// streaming loads straight into registers.  Parts hold at most 256 outputs
-// (8 per lane), in widths that are multiples of 32.
+// streaming loads straight into registers.  Parts hold at most 128 outputs
+// (4 per lane), in widths that are multiples of 32.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-// acc[q] += sum over units u = g, g+G, ... < units of P[u][li + 32 q] * w[u];
+// acc[q][r] += sum over units u = g, g+G, ... < units of P[u][li + 32 q] * w_r[u];
 // U units per round, so that U * NA loads are in flight per lane
-template <typename T, int NA, int U>
+template <typename T, int NA, int U, int NR>
 __device__ __forceinline__ void warp_accumulate(const T* __restrict__ P, int ldp, int units, int g, int G, int li,
-                                                int cnt, const T* __restrict__ w, T* acc) {
+                                                int cnt, const T* __restrict__ w, int ldw, T (*acc)[NR]) {
     int u = g;
     for (; u + (U - 1) * G < units; u += U * G) {
         T v[U][NA];
@@ -347,29 +396,36 @@ __device__ __forceinline__ void warp_accumulate(const T* __restrict__ P, int ldp
         }
 #pragma unroll
         for (int s = 0; s < U; ++s) {
-            const T x = w[u + s * G];
 #pragma unroll
-            for (int q2 = 0; q2 < NA; ++q2)
-                if (li + 32 * q2 < cnt) acc[q2] += v[s][q2] * x;
+            for (int r = 0; r < NR; ++r) {
+                const T x = w[r * ldw + u + s * G];
+#pragma unroll
+                for (int q2 = 0; q2 < NA; ++q2)
+                    if (li + 32 * q2 < cnt) acc[q2][r] += v[s][q2] * x;
+            }
         }
     }
     for (; u < units; u += G) {
         const T* row = P + (long long)u * ldp;
-        const T x = w[u];
 #pragma unroll
         for (int q2 = 0; q2 < NA; ++q2) {
             const int l = li + 32 * q2;
-            if (l < cnt) acc[q2] += __ldcs(row + l) * x;
+            if (l < cnt) {
+                const T pv = __ldcs(row + l);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[q2][r] += pv * w[r * ldw + u];
+            }
         }
     }
 }
 
-template <typename T>
+template <typename T, int NR>
 __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restrict__ Q, TreeArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    T* w = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * a.max_n;
+    const int ldw = a.max_n;
+    T* w = reinterpret_cast<T*>(smem_raw) + (size_t)(threadIdx.x >> 5) * NR * ldw;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1);
@@ -377,7 +433,7 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
         if (item >= a.n_items) return;
         const SolveItem it = a.items[item];
         const bool fwd = item < a.n_fwd;
-        const int F = it.front, k = it.k, n = it.n, b0 = it.b0;
+        const int F = it.front, k = it.k, n = it.n, b0 = it.b0, m = n - k;
         const int lo = it.lo, cnt = it.hi - it.lo, ldp = it.ldp;
         const T* q = Q + it.off;
         const int units = fwd ? k : n;  // rows (forward) or columns (backward) of the panel
@@ -406,49 +462,65 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
         if (a.trace && lane == 0) a.trace[4 * item + 2] = global_ns();
         if (fwd) {
             // w = [b(own); 0] + children's update vectors
-            for (int i = lane; i < n; i += 32) w[i] = (i < k) ? (T)__ldcg(&a.y[b0 + i]) : T(0);
+            for (int t = lane; t < NR * n; t += 32) {
+                const int r = t / n, i = t - r * n;
+                w[r * ldw + i] = (i < k) ? (T)__ldcg(&a.y[(long long)r * a.ldy + b0 + i]) : T(0);
+            }
             __syncwarp();
             for (int ci = it.c0; ci < it.c1; ++ci) {
                 const ChildRec cr = a.crec[ci];
-                const int* r = a.rel + cr.rel_off;
-                const double* u = a.upd + cr.upd_off;
-                for (int i = lane; i < cr.m; i += 32) w[r[i]] += (T)__ldcg(&u[i]);
+                const int* rl = a.rel + cr.rel_off;
+                const double* u = a.upd + cr.upd_off * NR;
+                for (int t = lane; t < NR * cr.m; t += 32) {
+                    const int r = t / cr.m, i = t - r * cr.m;
+                    w[r * ldw + rl[i]] += (T)__ldcg(&u[(long long)r * cr.m + i]);
+                }
                 __syncwarp();
             }
             if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
-                for (int i = lane; i < k; i += 32) a.w1[b0 + i] = (double)w[i];
+                for (int t = lane; t < NR * k; t += 32) {
+                    const int r = t / k, i = t - r * k;
+                    a.w1[(long long)r * a.ldy + b0 + i] = (double)w[r * ldw + i];
+                }
         } else {
             const int* idx = a.front_pos + it.fpos;
-            for (int i = lane; i < n; i += 32)
-                w[i] = (i < k) ? -(T)__ldcg(&a.w1[b0 + i]) : (T)__ldcg(&a.y[idx[i]]);
+            for (int t = lane; t < NR * n; t += 32) {
+                const int r = t / n, i = t - r * n;
+                w[r * ldw + i] = (i < k) ? -(T)__ldcg(&a.w1[(long long)r * a.ldy + b0 + i])
+                                         : (T)__ldcg(&a.y[(long long)r * a.ldy + idx[i]]);
+            }
         }
         __syncwarp();
         // lanes: outputs li (cp per unit group) x unit groups g (G = 32 / cp)
         const int cp = cnt > 16 ? 32 : (cnt > 8 ? 16 : (cnt > 4 ? 8 : 4));
         const int G = 32 / cp, li = lane % cp, g = lane / cp;
         const int na = (cnt + 31) / 32;
-        T acc[8];
+        T acc[4][NR];
 #pragma unroll
-        for (int q2 = 0; q2 < 8; ++q2) acc[q2] = T(0);
+        for (int q2 = 0; q2 < 4; ++q2)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[q2][r] = T(0);
         if (cnt > 0) {
             switch (na) {
-                case 1: warp_accumulate<T, 1, 16>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                case 2: warp_accumulate<T, 2, 8>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                case 3: warp_accumulate<T, 3, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                case 4: warp_accumulate<T, 4, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                case 5: warp_accumulate<T, 5, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                case 6: warp_accumulate<T, 6, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                case 7: warp_accumulate<T, 7, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
-                default: warp_accumulate<T, 8, 4>(q, ldp, units, g, G, li, cnt, w, acc); break;
+                case 1: warp_accumulate<T, 1, (NR == 1 ? 16 : 8), NR>(q, ldp, units, g, G, li, cnt, w, ldw, acc); break;
+                case 2: warp_accumulate<T, 2, (NR == 1 ? 8 : 4), NR>(q, ldp, units, g, G, li, cnt, w, ldw, acc); break;
+                case 3: warp_accumulate<T, 3, 4, NR>(q, ldp, units, g, G, li, cnt, w, ldw, acc); break;
+                default: warp_accumulate<T, 4, 4, NR>(q, ldp, units, g, G, li, cnt, w, ldw, acc); break;
             }
-            for (int o = cp; o < 32; o <<= 1) acc[0] += __shfl_xor_sync(FULL, acc[0], o);
+            for (int o = cp; o < 32; o <<= 1)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[0][r] += __shfl_xor_sync(FULL, acc[0][r], o);
             if (g == 0) {
 #pragma unroll
-                for (int q2 = 0; q2 < 8; ++q2) {
+                for (int q2 = 0; q2 < 4; ++q2) {
                     const int l = li + 32 * q2;
                     if (q2 < na && l < cnt) {
-                        if (fwd) a.upd[it.upd_off + lo + l - k] = (double)(w[lo + l] + acc[q2]);
-                        else a.y[b0 + lo + l] = (double)acc[q2];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            if (fwd) a.upd[it.upd_off * NR + (long long)r * m + lo + l - k] =
+                                         (double)(w[r * ldw + lo + l] + acc[q2][r]);
+                            else a.y[(long long)r * a.ldy + b0 + lo + l] = (double)acc[q2][r];
+                        }
                     }
                 }
             }
@@ -544,37 +616,64 @@ __global__ void norm2_partial_kernel(long long N, const double* __restrict__ a, 
     }
 }
 
-template <typename T>
+// Whether the NR > 1 kernels can take this symbolic analysis: every part's
+// panel must arrive in one copy (the extra output passes re-read it from
+// shared memory), and the front vectors of NR right-hand sides must fit.
+static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out, int* nt_out) {
+    int max_n = 0, max_ldp = 0;
+    for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
+    for (const SolveItem& it : S.sitems) max_ldp = std::max(max_ldp, it.ldp);
+    const int nt = S.solve_mode == SOLVE_CTA256 ? 256 : 128;
+    // small fronts: halves of 2048..3072 elements (NR > 1: as large as the
+    // largest panel needs), so that every part's panel arrives in one copy;
+    // large fronts: two 32 KiB halves
+    long long chunk = S.solve_mode == SOLVE_CTA128
+                          ? std::max<long long>(2048, (S.max_panel + 1) / 2)
+                          : (long long)(32768 / elem);
+    if (S.solve_mode == SOLVE_CTA128 && nr == 1) chunk = std::min<long long>(chunk, 3072);
+    chunk = std::max<long long>(chunk, max_ldp);
+    chunk = (chunk + 3) / 4 * 4;
+    *chunk_out = (int)chunk;
+    *nt_out = nt;
+    if (S.solve_mode == SOLVE_WARP) return 4 * (size_t)nr * max_n * elem;
+    return (2 * (size_t)chunk + (size_t)nr * max_n + (size_t)nt * nr + 8) * elem;
+}
+
+int solve_max_rhs(riga_ctx* c) {
+    const Symbolic& S = c->S;
+    if (S.solve_mode == SOLVE_CTA256) return 1;
+    int maxopt = 0;
+    if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return 1;
+    const size_t elem = c->precision == RIGA_FP64 ? sizeof(double) : sizeof(float);
+    for (int nr : {4, 2}) {
+        int chunk = 0, nt = 0;
+        const size_t smem = solve_smem(S, nr, elem, &chunk, &nt);
+        if (smem + 256 <= (size_t)maxopt && (S.solve_mode == SOLVE_WARP || 2LL * chunk >= S.max_panel)) return nr;
+    }
+    return 1;
+}
+
+template <typename T, int NR>
 static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
-    // and the vector read and written in each sweep
-    PhaseScope scope(c, PH_SOLVE, (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * (double)S.N * sizeof(double));
-    int max_n = 0, max_ldp = 0;
+    // and the vectors read and written in each sweep
+    PhaseScope scope(c, PH_SOLVE,
+                     (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * NR * (double)S.N * sizeof(double));
+    int max_n = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
-    for (const SolveItem& it : S.sitems) max_ldp = std::max(max_ldp, it.ldp);
-    // batches of many small trees: one item per warp (tree_solve_warp_kernel);
-    // small fronts: 128 threads and a 32 KiB (FP64) panel buffer per CTA, so
-    // that many items per SM overlap their waits; large fronts: 256 threads
-    // and two 32 KiB halves
     const int n_items = (int)S.sitems.size();
-    int maxopt = 0, nsm = 0, per_sm = 0;
+    int maxopt = 0, nsm = 0, per_sm = 0, chunk = 0, nt = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    const int nt = S.solve_mode == SOLVE_CTA256 ? 256 : 128;
-    // (small: halves of 2048..3072 elements, so that every part's panel
-    // usually arrives in one copy)
-    int chunk = S.solve_mode == SOLVE_CTA128
-                    ? (int)std::min<long long>(3072, std::max<long long>(2048, (S.max_panel + 1) / 2))
-                    : (int)(32768 / sizeof(T));
-    chunk = std::max(chunk, max_ldp);
-    chunk = (chunk + 3) / 4 * 4;
+    const size_t smem = solve_smem(S, NR, sizeof(T), &chunk, &nt);
     const bool warp = S.solve_mode == SOLVE_WARP;
-    const size_t smem = warp ? 4 * (size_t)max_n * sizeof(T) : (2 * (size_t)chunk + max_n + nt + 8) * sizeof(T);
     if (smem + 256 > (size_t)maxopt) return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
-    auto kern = warp ? tree_solve_warp_kernel<T>
-                     : (S.solve_mode == SOLVE_CTA128 ? tree_solve_kernel<T, 128> : tree_solve_kernel<T, 256>);
+    if (NR > 1 && (S.solve_mode == SOLVE_CTA256 || (!warp && 2LL * chunk < S.max_panel)))
+        return set_error(c, RIGA_EINVAL, "several right-hand sides need whole-panel copies");
+    auto kern = warp ? tree_solve_warp_kernel<T, NR>
+                     : (S.solve_mode == SOLVE_CTA128 ? tree_solve_kernel<T, 128, NR> : tree_solve_kernel<T, 256, NR>);
     if (smem > 48 * 1024)
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
@@ -603,6 +702,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     a.max_n = max_n;
     a.upd = c->upd.ptr;
     a.y = y;
+    a.ldy = S.N;
     a.w1 = c->w1buf.ptr;
     a.done_f = c->solve_flags.ptr;
     a.done_b = c->solve_flags.ptr + S.n_nodes;
@@ -614,18 +714,33 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     return RIGA_OK;
 }
 
-int enqueue_solve(riga_ctx* c, double* y) {
+// y := A^{-1} y for nrhs columns (stride N) in groups of the largest
+// supported width (4, 2, 1 right-hand sides per tree traversal)
+int enqueue_solve(riga_ctx* c, double* y, int nrhs) {
     if (!c->factored) return set_error(c, RIGA_ESTATE, "no factorization");
     Symbolic& S = c->S;
-    RIGA_CUDA_TRY(c, c->upd.alloc(S.upd_size > 0 ? S.upd_size : 1));
+    const int maxr = solve_max_rhs(c);
+    const int width = std::min(std::max(1, nrhs), maxr);
+    RIGA_CUDA_TRY(c, c->upd.alloc((S.upd_size > 0 ? S.upd_size : 1) * (size_t)width));
     RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes + 1));
-    RIGA_CUDA_TRY(c, c->w1buf.alloc(S.N));
-    int rc;
-    if (c->precision == RIGA_FP64) rc = enqueue_solve_t<double>(c, c->q64.ptr, y);
-    else rc = enqueue_solve_t<float>(c, c->q32.ptr, y);
-    if (rc) return rc;
-    RIGA_CUDA_TRY(c, cudaGetLastError());
-    c->stats.n_solve++;
+    RIGA_CUDA_TRY(c, c->w1buf.alloc((size_t)S.N * width));
+    for (int c0 = 0; c0 < nrhs;) {
+        const int left = nrhs - c0;
+        const int nr = left >= 4 && maxr >= 4 ? 4 : (left >= 2 && maxr >= 2 ? 2 : 1);
+        double* yc = y + (long long)c0 * S.N;
+        int rc;
+        if (c->precision == RIGA_FP64) {
+            rc = nr == 4 ? enqueue_solve_t<double, 4>(c, c->q64.ptr, yc)
+                         : (nr == 2 ? enqueue_solve_t<double, 2>(c, c->q64.ptr, yc) : enqueue_solve_t<double, 1>(c, c->q64.ptr, yc));
+        } else {
+            rc = nr == 4 ? enqueue_solve_t<float, 4>(c, c->q32.ptr, yc)
+                         : (nr == 2 ? enqueue_solve_t<float, 2>(c, c->q32.ptr, yc) : enqueue_solve_t<float, 1>(c, c->q32.ptr, yc));
+        }
+        if (rc) return rc;
+        RIGA_CUDA_TRY(c, cudaGetLastError());
+        c->stats.n_solve += nr;
+        c0 += nr;
+    }
     return RIGA_OK;
 }
 

@@ -121,7 +121,7 @@ std::string finish_symbolic(Symbolic& S) {
 
     // ------------------------------------------------------- solve items
     // Parts of about part_fma multiply-adds each (at most 32 per sweep), of at
-    // most 8 outputs per thread of the solve CTA (per lane for the warp
+    // most 8 outputs per thread of the solve CTA (4 per lane for the warp
     // kernel).  When every front has at most SMALL_MAX_N variables (2D
     // meshes), parts are smaller, so that the fronts near the root (the
     // critical path of the solve) spread over more SMs and each part's panel
@@ -135,7 +135,7 @@ std::string finish_symbolic(Symbolic& S) {
     S.solve_mode = max_n > SMALL_MAX_N ? SOLVE_CTA256 : (n_trees >= 16 ? SOLVE_WARP : SOLVE_CTA128);
     const bool warp = S.solve_mode == SOLVE_WARP;
     const long long part_fma = S.solve_mode == SOLVE_CTA256 ? 12288 : 4096;
-    const long long max_width = warp ? 256 : (S.solve_mode == SOLVE_CTA128 ? 8 * 128 : 8 * 256);
+    const long long max_width = warp ? 128 : (S.solve_mode == SOLVE_CTA128 ? 8 * 128 : 8 * 256);
     // split `len` outputs into at least `want` parts of at most max_width
     // (warp kernel: widths a multiple of 32 except the last)
     auto split = [&](long long len, long long want) -> long long {
