@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c4"],
                     help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, "
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
+    ap.add_argument("--block", type=int, default=1, choices=[0, 1, 2, 4],
+                    help="Lanczos block size (riga_set_eig_block; 0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-front (mixed) leg")
@@ -93,7 +95,7 @@ def config_dict(args, cfg, extra=None):
     d = {
         "workload": f"laplace{m.dim}d_p{m.p}_{'x'.join(str(v) for v in m.ne)}_{'riga_bs%d' % m.bs if m.bs else 'iga'}_k{cfg['k']}_slices{cfg['k'] // cfg['slice']}",
         "dim": m.dim, "elements_per_side": m.ne[0], "degree": m.p, "block_size": m.bs, "leaf_extent": m.leaf_extent,
-        "pairs": cfg["k"], "slice": cfg["slice"], "factor_precision": args.precision,
+        "pairs": cfg["k"], "slice": cfg["slice"], "factor_precision": args.precision, "lanczos_block": args.block,
         "l2": "flushed between timed steps (512 MiB write)",
         "parallelism": f"replicas{args.gpus}",
     }
@@ -417,6 +419,7 @@ def run_riga(args, rank, world, local_rank):
     mesh, k = cfg["mesh"], cfg["k"]
     R = riga.Riga(local_rank, stream)
     R.set_eig_options(slice=cfg["slice"], precision=prec, extra=2, seed=11)
+    R.set_eig_block(args.block)
     R.assemble(mesh)  # symbolic analysis: once per pattern, untimed
     q = R.query()
     N = q["N"]

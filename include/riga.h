@@ -225,6 +225,38 @@ int riga_assemble_batch(riga_ctx* ctx, int nprob, const riga_mesh* meshes, const
 int riga_eigs_batch(riga_ctx* ctx, int k, double sigma, double tol, double* evals, double* resid, int* nconv);
 
 /*
+ * riga_band_eig: the Rayleigh-Ritz step of block Lanczos on the host (the
+ * block form of Eq. LanczosTm and Eq. RitzValues): all eigenvalues of a real
+ * symmetric band matrix, and eigenvectors for chosen ones.  Needs no context
+ * and no GPU.
+ *  T[n*n]: HOST, column-major, symmetric; entries with |i - j| > b are
+ *    ignored (taken as zero).  b >= 0 is the half-bandwidth (the Lanczos
+ *    block size).
+ *  theta[n]: HOST out, all eigenvalues ascending.
+ *  which[q]: HOST, indices into theta of the wanted eigenvectors; S[n*q]:
+ *    HOST out, column-major, orthonormal eigenvectors (sign unspecified).
+ * Band reduction to tridiagonal form by Givens rotations, implicit QL, and
+ * inverse iteration with a pivoted band LU, orthogonalised within clusters.
+ * Errors: RIGA_EINVAL (bad sizes or indices).
+ */
+int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S);
+
+/*
+ * riga_set_eig_block: Lanczos block size of riga_eigs.  1 (the default) is
+ * the single-vector recurrence of Sec. 4.1-4.2; 2 or 4 run block Lanczos:
+ * each step applies the shift-inverted operator to a block of vectors with
+ * one traversal of the factor (riga_solve's grouping), orthogonalises the
+ * block against all previous vectors (two classical Gram-Schmidt passes in
+ * the M-inner product) and M-orthonormalises it (Cholesky QR, twice); the
+ * Rayleigh-Ritz step uses the block-tridiagonal T_m (riga_band_eig).
+ * Eigenvalues of multiplicity up to the block size appear in one run.  0
+ * selects 4.  When the factor cannot carry that many right-hand sides (fronts
+ * larger than 1536), the size falls back to what it can (possibly 1).
+ * Errors: RIGA_EINVAL.
+ */
+int riga_set_eig_block(riga_ctx* ctx, int block);
+
+/*
  * riga_eig_grad: gradient of L = sum_i dL_dlambda[i] lambda_i over the k
  * eigenpairs of the last riga_eigs with respect to the log-coefficients a_e,
  * b_e (coefK[e] = exp(a_e), coefM[e] = exp(b_e) of riga_assemble):

@@ -367,6 +367,13 @@ int riga_set_eig_options(riga_ctx* c, int slice, int precision, int max_steps, i
     return RIGA_OK;
 }
 
+int riga_set_eig_block(riga_ctx* c, int block) {
+    if (!c) return RIGA_EINVAL;
+    if (block != 0 && block != 1 && block != 2 && block != 4) return set_error(c, RIGA_EINVAL, "block size must be 0, 1, 2 or 4");
+    c->opt_block = block;
+    return RIGA_OK;
+}
+
 int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, double* evecs, double* resid, int* nconv) {
     if (!c || !evals) return RIGA_EINVAL;
     if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");

@@ -1,0 +1,201 @@
+// Rayleigh-Ritz step of block Lanczos: eigenpairs of the symmetric band
+// matrix T_m (the block-tridiagonal projection of the shift-inverted operator,
+// the block form of Eq. LanczosTm and Eq. RitzValues; half-bandwidth = the
+// block size b).
+//
+// Eigenvalues: the band is reduced to tridiagonal form by Givens similarity
+// rotations, chasing the bulge each rotation creates down the band (the
+// classical Rutishauser-Schwarz band reduction, O(n^2 b)); the tridiagonal
+// eigenvalues come from the implicit QL iteration of tridiag.cpp.
+// Eigenvectors (only those asked for): inverse iteration on T - theta I with a
+// banded LU factorization with partial pivoting, the iterates of eigenvalues
+// closer than 1e-3 ||T|| orthogonalised against each other (modified
+// Gram-Schmidt), three iterations from a fixed start vector.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <numeric>
+#include <vector>
+
+#include "ctx.h"
+
+namespace riga {
+
+namespace {
+
+// similarity rotation in the (p, q) plane of a dense symmetric matrix:
+// rows p, q <- [c s; -s c] [row p; row q], and the same on the columns,
+// restricted to the index window where the band (plus one bulge) can hold
+// non-zeros
+void rotate_sym(std::vector<double>& A, int n, int b, int p, int q, double c, double s) {
+    auto at = [&](int i, int j) -> double& { return A[(size_t)j * n + i]; };
+    const int lo = std::max(0, p - b - 2), hi = std::min(n, q + b + 3);
+    for (int t = lo; t < hi; ++t) {
+        if (t == p || t == q) continue;
+        const double x = at(p, t), y = at(q, t);
+        const double nx = c * x + s * y, ny = -s * x + c * y;
+        at(p, t) = nx;
+        at(t, p) = nx;
+        at(q, t) = ny;
+        at(t, q) = ny;
+    }
+    const double app = at(p, p), aqq = at(q, q), apq = at(p, q);
+    const double npp = c * c * app + 2.0 * c * s * apq + s * s * aqq;
+    const double nqq = s * s * app - 2.0 * c * s * apq + c * c * aqq;
+    const double npq = (c * c - s * s) * apq + c * s * (aqq - app);
+    at(p, p) = npp;
+    at(q, q) = nqq;
+    at(p, q) = npq;
+    at(q, p) = npq;
+}
+
+// band LU with partial pivoting (kl = ku = b; fill up to 2b above the
+// diagonal), LAPACK band layout: A(i, j) at ab[kv + i - j + j * ldab]
+struct BandLU {
+    int n, kl, ku, kv, ldab;
+    std::vector<double> ab;
+    std::vector<int> piv;
+};
+
+void band_lu(BandLU& F, int n, int b, const double* T, double shift, double tiny) {
+    F.n = n;
+    F.kl = b;
+    F.ku = b;
+    F.kv = 2 * b;
+    F.ldab = 3 * b + 1;
+    F.ab.assign((size_t)F.ldab * n, 0.0);
+    F.piv.assign(n, 0);
+    auto AB = [&](int i, int j) -> double& { return F.ab[(size_t)F.kv + i - j + (size_t)j * F.ldab]; };
+    for (int j = 0; j < n; ++j)
+        for (int i = std::max(0, j - b); i <= std::min(n - 1, j + b); ++i)
+            AB(i, j) = T[(size_t)j * n + i] - (i == j ? shift : 0.0);
+    int ju = 0;
+    for (int j = 0; j < n; ++j) {
+        const int km = std::min(F.kl, n - 1 - j);
+        int jp = 0;
+        double best = std::fabs(AB(j, j));
+        for (int i = 1; i <= km; ++i)
+            if (std::fabs(AB(j + i, j)) > best) {
+                best = std::fabs(AB(j + i, j));
+                jp = i;
+            }
+        F.piv[j] = j + jp;
+        ju = std::max(ju, std::min(j + F.ku + jp, n - 1));
+        if (jp != 0)
+            for (int cc = j; cc <= ju; ++cc) std::swap(AB(j, cc), AB(j + jp, cc));
+        if (std::fabs(AB(j, j)) < tiny) AB(j, j) = AB(j, j) < 0.0 ? -tiny : tiny;
+        const double inv = 1.0 / AB(j, j);
+        for (int i = 1; i <= km; ++i) AB(j + i, j) *= inv;
+        for (int cc = j + 1; cc <= ju; ++cc) {
+            const double u = AB(j, cc);
+            if (u == 0.0) continue;
+            for (int i = 1; i <= km; ++i) AB(j + i, cc) -= AB(j + i, j) * u;
+        }
+    }
+}
+
+void band_solve(const BandLU& F, double* x) {
+    const int n = F.n;
+    auto AB = [&](int i, int j) -> double { return F.ab[(size_t)F.kv + i - j + (size_t)j * F.ldab]; };
+    for (int j = 0; j < n; ++j) {
+        if (F.piv[j] != j) std::swap(x[j], x[F.piv[j]]);
+        const int km = std::min(F.kl, n - 1 - j);
+        for (int i = 1; i <= km; ++i) x[j + i] -= AB(j + i, j) * x[j];
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        x[j] /= AB(j, j);
+        for (int i = std::max(0, j - F.kv); i < j; ++i) x[i] -= AB(i, j) * x[j];
+    }
+}
+
+}  // namespace
+
+void band_eigvals(int n, int b, const double* T, double* theta) {
+    if (n <= 0) return;
+    std::vector<double> A(T, T + (size_t)n * n);
+    auto at = [&](int i, int j) -> double& { return A[(size_t)j * n + i]; };
+    for (int j = 0; j + 2 < n; ++j) {
+        for (int i = std::min(j + b, n - 1); i >= j + 2; --i) {
+            const double x = at(i - 1, j), y = at(i, j);
+            if (y == 0.0) continue;
+            const double r = std::hypot(x, y);
+            rotate_sym(A, n, b, i - 1, i, x / r, y / r);
+            at(i, j) = 0.0;
+            at(j, i) = 0.0;
+            // chase the bulge at (k + b, k - 1) down the band
+            for (int k = i; k + b < n;) {
+                const int p = k + b - 1, q = k + b, col = k - 1;
+                const double x2 = at(p, col), y2 = at(q, col);
+                if (y2 == 0.0) break;
+                const double r2 = std::hypot(x2, y2);
+                rotate_sym(A, n, b, p, q, x2 / r2, y2 / r2);
+                at(q, col) = 0.0;
+                at(col, q) = 0.0;
+                k = q;
+            }
+        }
+    }
+    std::vector<double> d(n), e(n, 0.0), z(n);
+    for (int i = 0; i < n; ++i) d[i] = at(i, i);
+    for (int i = 0; i + 1 < n; ++i) e[i] = at(i + 1, i);
+    tridiag_eig(n, d.data(), e.data(), theta, z.data(), false);
+}
+
+void band_eigvecs(int n, int b, const double* T, int q, const double* th, double* S) {
+    double tnorm = 0.0;
+    for (size_t i = 0; i < (size_t)n * n; ++i) tnorm = std::max(tnorm, std::fabs(T[i]));
+    tnorm = std::max(tnorm, 1e-300);
+    const double tiny = 2.220446049250313e-16 * tnorm;
+    // process in ascending eigenvalue order so that clusters are contiguous
+    std::vector<int> ord(q);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return th[x] < th[y]; });
+    BandLU F;
+    std::vector<double> x(n);
+    int cl0 = 0;  // first member (in ord) of the current cluster
+    for (int oi = 0; oi < q; ++oi) {
+        const int qi = ord[oi];
+        if (oi > 0 && th[qi] - th[ord[oi - 1]] > 1e-3 * tnorm) cl0 = oi;
+        band_lu(F, n, b, T, th[qi], tiny);
+        // fixed start vector (deterministic), then three inverse iterations
+        uint64_t s = 0x9E3779B97F4A7C15ULL ^ (uint64_t)(oi + 1);
+        for (int i = 0; i < n; ++i) {
+            s ^= s << 13;
+            s ^= s >> 7;
+            s ^= s << 17;
+            x[i] = ((double)(s >> 11) / 9007199254740992.0) - 0.5;
+        }
+        for (int it = 0; it < 3; ++it) {
+            band_solve(F, x.data());
+            for (int pj = cl0; pj < oi; ++pj) {
+                const double* v = S + (size_t)ord[pj] * n;
+                double dot = 0.0;
+                for (int i = 0; i < n; ++i) dot += v[i] * x[i];
+                for (int i = 0; i < n; ++i) x[i] -= dot * v[i];
+            }
+            double nrm = 0.0;
+            for (int i = 0; i < n; ++i) nrm += x[i] * x[i];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0.0)) nrm = 1.0;
+            for (int i = 0; i < n; ++i) x[i] /= nrm;
+        }
+        std::copy(x.begin(), x.end(), S + (size_t)qi * n);
+    }
+}
+
+}  // namespace riga
+
+using namespace riga;
+
+extern "C" int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S) {
+    if (n < 1 || b < 0 || !T || !theta || q < 0 || (q > 0 && (!which || !S))) return RIGA_EINVAL;
+    for (int i = 0; i < q; ++i)
+        if (which[i] < 0 || which[i] >= n) return RIGA_EINVAL;
+    band_eigvals(n, std::max(b, 1), T, theta);
+    if (q > 0) {
+        std::vector<double> th(q);
+        for (int i = 0; i < q; ++i) th[i] = theta[which[i]];
+        band_eigvecs(n, std::max(b, 1), T, q, th.data(), S);
+    }
+    return RIGA_OK;
+}

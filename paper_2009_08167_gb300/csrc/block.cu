@@ -1,0 +1,670 @@
+// Block shift-and-invert Lanczos (block size B = 2 or 4) in the M-inner
+// product: the recurrence of Sec. 4.1-4.2 with B vectors per step, so that
+// one traversal of the factor's tree (a B-right-hand-side solve, solve.cu)
+// and one read of M serve B Krylov vectors, and eigenvalues of multiplicity
+// up to B appear in a single run.
+//
+// Per block step j (H = (K - sigma M)^{-1} M, V_j M-orthonormal, MV_j stored):
+//   W = H V_j                      one B-RHS solve of the stored M V_j
+//   W -= V C1, W -= V C2           two classical Gram-Schmidt passes against
+//                                  all columns so far (locked, then run)
+//   A_j = (C1 + C2)[block j rows]  diagonal block of T
+//   W = V_{j+1} B_{j+1}            M-orthonormal QR by Cholesky of W^T M W,
+//                                  twice (CholQR2), M W from one block SpMV
+// T_m is block tridiagonal (half-bandwidth B) with diagonal blocks A_j and
+// sub-diagonal blocks B_{j+1}; its eigenpairs (band.cpp) give the Ritz
+// values theta (lambda = sigma + 1/theta) and the residual estimates
+// ||B_m s_last||.  A breakdown of the QR (a numerically rank-deficient W)
+// ends the run; the converged pairs found so far are kept.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <numeric>
+
+#include "lanczos.h"
+
+namespace riga {
+
+constexpr int BLK_MAX = 4;
+
+// Partial dots out[j*B + r] = sum over this chunk's rows of B_j[row] w_r[row]
+// (the basis tile staged through shared memory as in the single-vector
+// kernels; every staged entry serves B products).
+template <int B>
+__device__ __forceinline__ void bchunk_dots(const double* __restrict__ Bm, long long ld, int J, long long r0, int rows,
+                                            const double* __restrict__ ws, double* __restrict__ Vs,
+                                            double* __restrict__ red, double* __restrict__ out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j0 = 0; j0 < J; j0 += TJ) {
+        const int jn = min(TJ, J - j0);
+#pragma unroll
+        for (int q = 0; q < TJ / 8; ++q) {
+            const int jl = warp + 8 * q;
+            if (jl < jn) {
+                const double* col = Bm + (long long)(j0 + jl) * ld + r0;
+#pragma unroll
+                for (int i = 0; i < CH / 32; ++i) {
+                    const int r = lane + 32 * i;
+                    Vs[jl * (CH + 1) + r] = (r < rows) ? col[r] : 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        double s[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) s[r] = 0.0;
+        if (lane < jn) {
+            const double* vc = Vs + lane * (CH + 1);
+#pragma unroll 4
+            for (int i = warp; i < CH; i += 8) {
+                const double v = vc[i];
+#pragma unroll
+                for (int r = 0; r < B; ++r) s[r] += v * ws[r * CH + i];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < B; ++r) red[(warp * TJ + lane) * B + r] = s[r];
+        __syncthreads();
+        if (tid < jn * B) {
+            double t = 0.0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) t += red[g * TJ * B + tid];
+            out[j0 * B + tid] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) bdots_kernel(const double* __restrict__ MV, long long ld, int J,
+                                                    const double* __restrict__ W, long long N,
+                                                    double* __restrict__ partial, int pstride) {
+    extern __shared__ double sh[];
+    double* ws = sh;                  // B * CH
+    double* red = ws + B * CH;        // 8 * TJ * B
+    double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
+    const long long r0 = (long long)blockIdx.x * CH;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < B; ++r) ws[r * CH + tid] = (r0 + tid < N) ? W[r * N + r0 + tid] : 0.0;
+    __syncthreads();
+    const int rows = (int)min((long long)CH, N - r0);
+    bchunk_dots<B>(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+}
+
+// w_r[row] -= sum_j V_j[row] C[j*B + r], the loads issued eight at a time
+template <int B>
+__device__ __forceinline__ void brow_update(const double* __restrict__ V, long long ld, int J, long long row,
+                                            const double* __restrict__ cs, double* v) {
+    int j = 0;
+    for (; j + 8 <= J; j += 8) {
+        double b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = V[(long long)(j + q) * ld + row];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int r = 0; r < B; ++r) v[r] -= b[q] * cs[(j + q) * B + r];
+    }
+    for (; j < J; ++j) {
+        const double b = V[(long long)j * ld + row];
+#pragma unroll
+        for (int r = 0; r < B; ++r) v[r] -= b * cs[j * B + r];
+    }
+}
+
+// W -= V C (this chunk), then partial dots MV^T W
+template <int B>
+__global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restrict__ V, const double* __restrict__ MV,
+                                                           long long ld, int J, const double* __restrict__ C,
+                                                           double* __restrict__ W, long long N,
+                                                           double* __restrict__ partial, int pstride) {
+    extern __shared__ double sh[];
+    double* ws = sh;                  // B * CH
+    double* red = ws + B * CH;        // 8 * TJ * B
+    double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
+    double* cs = Vs + TJ * (CH + 1);  // J * B
+    const long long r0 = (long long)blockIdx.x * CH;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < J * B; t += blockDim.x) cs[t] = C[t];
+    __syncthreads();
+    const long long row = r0 + tid;
+    double v[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) v[r] = 0.0;
+    if (row < N) {
+#pragma unroll
+        for (int r = 0; r < B; ++r) v[r] = W[r * N + row];
+        brow_update<B>(V, ld, J, row, cs, v);
+#pragma unroll
+        for (int r = 0; r < B; ++r) W[r * N + row] = v[r];
+    }
+#pragma unroll
+    for (int r = 0; r < B; ++r) ws[r * CH + tid] = v[r];
+    __syncthreads();
+    const int rows = (int)min((long long)CH, N - r0);
+    bchunk_dots<B>(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) bupdate_kernel(const double* __restrict__ V, long long ld, int J,
+                                                      const double* __restrict__ C, double* __restrict__ W, long long N) {
+    extern __shared__ double cs[];
+    for (int t = threadIdx.x; t < J * B; t += blockDim.x) cs[t] = C[t];
+    __syncthreads();
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    double v[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) v[r] = W[r * N + row];
+    brow_update<B>(V, ld, J, row, cs, v);
+#pragma unroll
+    for (int r = 0; r < B; ++r) W[r * N + row] = v[r];
+}
+
+// MW = M W (16 lanes per row, every value of M serving B products) and the
+// block's partial Gram matrix W^T M W (row-major B x B)
+template <int B>
+__global__ void __launch_bounds__(256) bspmv_gram_kernel(long long N, const long long* __restrict__ rowptr,
+                                                         const int* __restrict__ col, const double* __restrict__ Mv,
+                                                         const double* __restrict__ W, double* __restrict__ MW,
+                                                         double* __restrict__ partial) {
+    __shared__ double red[16][B * B];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long row = t / 16;
+    const int lane = (int)(t % 16), grp = threadIdx.x / 16;
+    double s[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) s[r] = 0.0;
+    if (row < N)
+        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) {
+            const double mv = Mv[e];
+            const int cc = col[e];
+#pragma unroll
+            for (int r = 0; r < B; ++r) s[r] += mv * W[r * N + cc];
+        }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < B; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o, 16);
+    if (lane == 0) {
+        if (row < N) {
+#pragma unroll
+            for (int r = 0; r < B; ++r) MW[r * N + row] = s[r];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const double wq = W[q * N + row];
+#pragma unroll
+                for (int r = 0; r < B; ++r) red[grp][q * B + r] = wq * s[r];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < B * B; ++e) red[grp][e] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < B * B) {
+        double tot = 0.0;
+        for (int g = 0; g < 16; ++g) tot += red[g][threadIdx.x];
+        partial[(long long)blockIdx.x * B * B + threadIdx.x] = tot;
+    }
+}
+
+// partial Gram matrix V^T (M V) of B columns with their stored M-products
+template <int B>
+__global__ void __launch_bounds__(256) bgram_kernel(long long N, const double* __restrict__ V, long long ld,
+                                                    const double* __restrict__ MV, double* __restrict__ partial) {
+    __shared__ double red[8][B * B];
+    double g[B * B];
+#pragma unroll
+    for (int e = 0; e < B * B; ++e) g[e] = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        double v[B], m[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            v[r] = V[r * ld + i];
+            m[r] = MV[r * ld + i];
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+#pragma unroll
+            for (int r = 0; r < B; ++r) g[q * B + r] += v[q] * m[r];
+    }
+#pragma unroll
+    for (int e = 0; e < B * B; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g[e] += __shfl_xor_sync(0xffffffffu, g[e], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int e = 0; e < B * B; ++e) red[threadIdx.x >> 5][e] = g[e];
+    __syncthreads();
+    if (threadIdx.x < B * B) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red[w][threadIdx.x];
+        partial[(long long)blockIdx.x * B * B + threadIdx.x] = tot;
+    }
+}
+
+// out[e] = sum over nb partial blocks of partial[i * count + e] (fixed order)
+__global__ void __launch_bounds__(256) bsum_small_kernel(const double* __restrict__ partial, int nb, int count,
+                                                         double* __restrict__ out) {
+    __shared__ double sh[256];
+    for (int e = 0; e < count; ++e) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[(long long)i * count + e];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[e] = sh[0];
+        __syncthreads();
+    }
+}
+
+// Cholesky G + s I = R^T R of the symmetrised B x B Gram matrix (one
+// thread), s = shift_rel * trace(G); R^{-1}; and optionally Bout = R Rprev
+// (the block's triangular factor accumulated over the QR passes).  A pivot at
+// or below 1e-24 of the largest diagonal entry is a breakdown: flag bit 0,
+// and R = I so that the step stays finite.
+template <int B>
+__global__ void bchol_kernel(const double* __restrict__ G, double shift_rel, double* __restrict__ Rinv,
+                             const double* __restrict__ Rprev, double* __restrict__ Bout, double* __restrict__ Rout,
+                             int* __restrict__ flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double g[B][B], R[B][B], Ri[B][B];
+    double dmax = 0.0, tr = 0.0;
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            g[i][j] = 0.5 * (G[i * B + j] + G[j * B + i]);
+            R[i][j] = 0.0;
+            Ri[i][j] = 0.0;
+        }
+    for (int i = 0; i < B; ++i) tr += fmax(g[i][i], 0.0);
+    for (int i = 0; i < B; ++i) g[i][i] += shift_rel * tr;
+    for (int i = 0; i < B; ++i) dmax = fmax(dmax, g[i][i]);
+    bool bad = !(dmax > 0.0);
+    for (int i = 0; i < B && !bad; ++i) {
+        double d = g[i][i];
+        for (int k = 0; k < i; ++k) d -= R[k][i] * R[k][i];
+        if (!(d > 1e-24 * dmax)) {
+            bad = true;
+            break;
+        }
+        R[i][i] = sqrt(d);
+        for (int j = i + 1; j < B; ++j) {
+            double v = g[i][j];
+            for (int k = 0; k < i; ++k) v -= R[k][i] * R[k][j];
+            R[i][j] = v / R[i][i];
+        }
+    }
+    if (bad) {
+        atomicOr(flag, 1);
+        for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j) R[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    // upper-triangular inverse
+    for (int j = 0; j < B; ++j) {
+        Ri[j][j] = 1.0 / R[j][j];
+        for (int i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j; ++k) s += R[i][k] * Ri[k][j];
+            Ri[i][j] = -s / R[i][i];
+        }
+    }
+    for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+            Rinv[i * B + j] = Ri[i][j];
+            if (Rout) Rout[i * B + j] = R[i][j];
+        }
+    if (Bout) {
+        for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < B; ++k) s += R[i][k] * (Rprev ? Rprev[k * B + j] : (k == j ? 1.0 : 0.0));
+                Bout[i * B + j] = s;
+            }
+    }
+}
+
+// X[:, l] = sum_{i <= l} Y[:, i] Rinv[i][l] for both Y = W (into V) and
+// Y = M W (into M V); in place when the output aliases the input
+template <int B>
+__global__ void bscale_kernel(long long N, const double* __restrict__ Rinv, const double* W, long long ldw,
+                              const double* MW, double* V, double* MV, long long ldv) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double ri[B * B];
+#pragma unroll
+    for (int e = 0; e < B * B; ++e) ri[e] = Rinv[e];
+    double w[B], mw[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        w[r] = W[r * ldw + i];
+        mw[r] = MW[r * ldw + i];
+    }
+#pragma unroll
+    for (int l = 0; l < B; ++l) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int r = 0; r <= l; ++r) {
+            a += w[r] * ri[r * B + l];
+            b += mw[r] * ri[r * B + l];
+        }
+        V[l * ldv + i] = a;
+        MV[l * ldv + i] = b;
+    }
+}
+
+// A_j[i][r] = C1[(cs + i) B + r] + C2[(cs + i) B + r]
+template <int B>
+__global__ void balpha_kernel(const double* __restrict__ C1, const double* __restrict__ C2, int cs,
+                              double* __restrict__ A) {
+    const int t = threadIdx.x;
+    if (t < B * B) A[t] = C1[(cs + t / B) * B + t % B] + C2[(cs + t / B) * B + t % B];
+}
+
+// --------------------------------------------------------------- host side
+namespace {
+
+struct BlockWork {
+    riga_ctx* c;
+    int B;
+    long long N, ld;
+    int nch;
+    int cap;
+    double* W;      // N x B
+    double* MW;     // N x B
+    double* C1;     // cap * B
+    double* C2;
+    double* part;   // nch * cap * B, then small partials
+    double* small;  // B*B Gram, Rinv, R scratch
+    int* flag;
+};
+
+size_t dots_smem(int B) { return (size_t)(B * CH + 8 * TJ * B + TJ * (CH + 1)) * sizeof(double); }
+
+template <int B>
+int bortho_t(BlockWork& K, int J) {
+    riga_ctx* c = K.c;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_REORTH, 4.0 * (double)K.N * J * sizeof(double));
+    const size_t sm = dots_smem(B);
+    const int pstride = K.cap * B;
+    { count_launch(c); bdots_kernel<B><<<K.nch, 256, sm, st>>>(c->MV.ptr, K.ld, J, K.W, K.N, K.part, pstride); }
+    enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C1);
+    { count_launch(c); bupdate_dots_kernel<B><<<K.nch, 256, sm + (size_t)J * B * sizeof(double), st>>>(
+        c->V.ptr, c->MV.ptr, K.ld, J, K.C1, K.W, K.N, K.part, pstride); }
+    enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C2);
+    { count_launch(c); bupdate_kernel<B><<<(unsigned)((K.N + 255) / 256), 256, (size_t)J * B * sizeof(double), st>>>(
+        c->V.ptr, K.ld, J, K.C2, K.W, K.N); }
+    return RIGA_OK;
+}
+
+// W (N x B) -> M-orthonormal columns col..col+B-1 of V and M V; Bout = the
+// triangular factor (W = V_new Bout).  Shifted Cholesky QR, then two plain
+// passes (shifted CholeskyQR3): the shift s = 11 (N B + B (B+1)) u trace(W^T M W)
+// keeps the first factorization defined however ill-conditioned W is (its
+// directions along converged Ritz vectors are tiny), the next two restore
+// M-orthonormality, and W = V Bout holds to rounding relative to ||W||.
+template <int B>
+int bnormalize_t(BlockWork& K, int col, double* Bout) {
+    riga_ctx* c = K.c;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)K.N * 8.0 * 10.0 * B);
+    const unsigned nbs = (unsigned)((K.N * 16 + 255) / 256);
+    double* G = K.small;
+    double* Rinv = G + B * B;
+    double* R1 = Rinv + B * B;
+    double* R2 = R1 + B * B;
+    double* V = c->V.ptr + (long long)col * K.ld;
+    double* MV = c->MV.ptr + (long long)col * K.ld;
+    const unsigned gb = (unsigned)((K.N + 255) / 256);
+    const double shift = 11.0 * ((double)K.N * B + (double)B * (B + 1)) * 1.1102230246251565e-16;
+    { count_launch(c); bspmv_gram_kernel<B><<<nbs, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW, K.part); }
+    c->stats.n_matvec += B;
+    { count_launch(c); bsum_small_kernel<<<1, 256, 0, st>>>(K.part, (int)nbs, B * B, G); }
+    { count_launch(c); bchol_kernel<B><<<1, 32, 0, st>>>(G, shift, Rinv, nullptr, nullptr, R1, K.flag); }
+    { count_launch(c); bscale_kernel<B><<<gb, 256, 0, st>>>(K.N, Rinv, K.W, K.N, K.MW, V, MV, K.ld); }
+    for (int pass = 0; pass < 2; ++pass) {
+        // the Gram matrix of the new columns, its Cholesky factor, and the
+        // accumulated triangular factor (R1 <- R R1, finally into Bout)
+        { count_launch(c); bgram_kernel<B><<<304, 256, 0, st>>>(K.N, V, K.ld, MV, K.part); }
+        { count_launch(c); bsum_small_kernel<<<1, 256, 0, st>>>(K.part, 304, B * B, G); }
+        double* acc = pass == 0 ? R2 : Bout;
+        const double* prev = pass == 0 ? R1 : R2;
+        { count_launch(c); bchol_kernel<B><<<1, 32, 0, st>>>(G, 0.0, Rinv, prev, acc, nullptr, K.flag); }
+        { count_launch(c); bscale_kernel<B><<<gb, 256, 0, st>>>(K.N, Rinv, V, K.ld, MV, V, MV, K.ld); }
+    }
+    return RIGA_OK;
+}
+
+int bortho(BlockWork& K, int J) {
+    if (J <= 0) return RIGA_OK;
+    return K.B == 4 ? bortho_t<4>(K, J) : bortho_t<2>(K, J);
+}
+int bnormalize(BlockWork& K, int col, double* Bout) {
+    return K.B == 4 ? bnormalize_t<4>(K, col, Bout) : bnormalize_t<2>(K, col, Bout);
+}
+
+// the block-tridiagonal T (n = m B) from the diagonal blocks A (row-major
+// B x B each, symmetrised) and the sub-diagonal blocks Bs[1..m-1]
+void build_T(int m, int B, const double* A, const double* Bs, std::vector<double>& T) {
+    const int n = m * B;
+    T.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < m; ++j) {
+        const double* a = A + (size_t)j * B * B;
+        for (int i = 0; i < B; ++i)
+            for (int l = 0; l < B; ++l) T[(size_t)(j * B + l) * n + j * B + i] = 0.5 * (a[i * B + l] + a[l * B + i]);
+        if (j + 1 < m) {
+            const double* b = Bs + (size_t)(j + 1) * B * B;  // W_j = V_{j+1} B_{j+1}
+            for (int i = 0; i < B; ++i)
+                for (int l = 0; l < B; ++l) {
+                    T[(size_t)(j * B + l) * n + (j + 1) * B + i] = b[i * B + l];  // T[(j+1)B+i][jB+l]
+                    T[(size_t)((j + 1) * B + i) * n + j * B + l] = b[i * B + l];  // symmetric
+                }
+        }
+    }
+}
+
+}  // namespace
+
+int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigma, double sigma0, double tol_est,
+              double lock_tol, int lock_cap, uint64_t& seed, std::vector<double>& lam, int* m_out, int* n_locked) {
+    static const bool dbg = std::getenv("RIGA_DEBUG") != nullptr;
+    riga_ctx* c = R.c;
+    cudaStream_t st = c->stream;
+    const long long N = R.N;
+    *m_out = 0;
+    *n_locked = 0;
+    if (B != 2 && B != 4) return set_error(c, RIGA_EINVAL, "block size must be 2 or 4");
+    const int nblk = std::max(1, m_max / B);
+    const int col0 = nlock;
+    if (col0 + (nblk + 1) * B > R.cap) return set_error(c, RIGA_ENOMEM, "Lanczos basis capacity");
+    BlockWork K;
+    K.c = c;
+    K.B = B;
+    K.N = N;
+    K.ld = R.ld;
+    K.nch = (int)((N + CH - 1) / CH);
+    K.cap = R.cap;
+    const unsigned nbs = (unsigned)((N * 16 + 255) / 256);
+    const size_t part_n = std::max<size_t>((size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B);
+    RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)2 * N * B));
+    RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
+    RIGA_CUDA_TRY(c, c->bpartial.alloc(part_n));
+    RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)5 * B * B + (size_t)(nblk + 2) * 2 * B * B));
+    RIGA_CUDA_TRY(c, c->bflag.alloc(1));
+    K.W = c->bwork.ptr;
+    K.MW = c->bwork.ptr + (size_t)N * B;
+    K.C1 = c->bcoef.ptr;
+    K.C2 = c->bcoef.ptr + (size_t)K.cap * B;
+    K.part = c->bpartial.ptr;
+    K.small = c->bsmall.ptr;
+    K.flag = c->bflag.ptr;
+    double* dA = c->bsmall.ptr + 5 * B * B;               // nblk blocks
+    double* dB = dA + (size_t)(nblk + 1) * B * B;         // nblk + 1 blocks
+    const size_t smx = dots_smem(B) + (size_t)K.cap * B * sizeof(double);
+    if (B == 4) {
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bdots_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem(4)));
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_dots_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)((size_t)K.cap * B * sizeof(double))));
+    } else {
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bdots_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem(2)));
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_dots_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx));
+        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)((size_t)K.cap * B * sizeof(double))));
+    }
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(K.flag, 0, sizeof(int), st));
+
+    // start block: B random vectors, M-orthogonal to the locked ones
+    std::vector<double> hv((size_t)N * B);
+    for (size_t i = 0; i < hv.size(); ++i) hv[i] = ((double)(splitmix(seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(K.W, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    int rc = bortho(K, nlock);
+    if (rc) return rc;
+    rc = bnormalize(K, col0, dB);
+    if (rc) return rc;
+
+    // host copies of the blocks and the check state
+    std::vector<double> hA, hB, T, theta, S;
+    const int ck = std::max(1, 8 / B);  // block steps between convergence checks
+    int m = 0;
+    bool breakdown = false;
+    auto fetch = [&](int mm) -> int {
+        hA.resize((size_t)mm * B * B);
+        hB.resize((size_t)(mm + 1) * B * B);
+        int hf = 0, dflag = 0;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hA.data(), dA, hA.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hB.data(), dB, hB.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(&hf, K.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (dflag & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+        breakdown = breakdown || (hf != 0);
+        return RIGA_OK;
+    };
+    // residual estimate ||B_m s_last|| of eigenvector s (length n = mm B)
+    auto estimate = [&](int mm, const double* s) {
+        const double* b = hB.data() + (size_t)mm * B * B;
+        const double* sl = s + (size_t)(mm - 1) * B;
+        double e2 = 0.0;
+        for (int i = 0; i < B; ++i) {
+            double v = 0.0;
+            for (int l = 0; l < B; ++l) v += b[i * B + l] * sl[l];
+            e2 += v * v;
+        }
+        return std::sqrt(e2);
+    };
+    auto acceptable = [&](double th) { return th != 0.0 && cur_sigma + 1.0 / th > sigma0; };
+
+    for (int j = 0; j < nblk; ++j) {
+        const int cj = col0 + j * B;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(K.W, c->MV.ptr + (long long)cj * R.ld, (size_t)N * B * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+        if (c->precision == RIGA_FP64) {
+            rc = enqueue_solve(c, K.W, B);
+        } else {
+            for (int r = 0; r < B && rc == RIGA_OK; ++r)
+                rc = solve_refined(c, K.W + (size_t)r * N, R.xw, R.rw, 0.0, c->ir_sweeps, 0, nullptr);
+        }
+        if (rc) return rc;
+        rc = bortho(K, cj + B);
+        if (rc) return rc;
+        {
+            count_launch(c);
+            if (B == 4) balpha_kernel<4><<<1, 32, 0, st>>>(K.C1, K.C2, cj, dA + (size_t)j * B * B);
+            else balpha_kernel<2><<<1, 32, 0, st>>>(K.C1, K.C2, cj, dA + (size_t)j * B * B);
+        }
+        rc = bnormalize(K, cj + B, dB + (size_t)(j + 1) * B * B);
+        if (rc) return rc;
+        c->stats.steps += B;
+        m = j + 1;
+        if (m * B >= want_run && (m % ck == 0 || m == nblk)) {
+            rc = fetch(m);
+            if (rc) return rc;
+            if (breakdown) break;
+            const int n = m * B;
+            build_T(m, B, hA.data(), hB.data(), T);
+            theta.assign(n, 0.0);
+            band_eigvals(n, B, T.data(), theta.data());
+            // the want_run acceptable Ritz values of largest |theta|
+            std::vector<int> ord;
+            for (int i = 0; i < n; ++i)
+                if (acceptable(theta[i])) ord.push_back(i);
+            std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+            if ((int)ord.size() < want_run) continue;
+            ord.resize(want_run);
+            std::vector<double> th(want_run);
+            for (int q = 0; q < want_run; ++q) th[q] = theta[ord[q]];
+            S.assign((size_t)n * want_run, 0.0);
+            band_eigvecs(n, B, T.data(), want_run, th.data(), S.data());
+            bool all = true;
+            for (int q = 0; q < want_run && all; ++q)
+                if (!(estimate(m, S.data() + (size_t)q * n) <= tol_est * std::fabs(th[q]))) all = false;
+            if (all) break;
+        }
+    }
+    *m_out = m * B;
+    if (m == 0) return RIGA_OK;
+    // Rayleigh-Ritz with vectors: every acceptable Ritz pair whose estimate
+    // meets the bar, largest |theta| first, up to the locking room
+    int rc2 = fetch(m);
+    if (rc2) return rc2;
+    const int n = m * B;
+    build_T(m, B, hA.data(), hB.data(), T);
+    theta.assign(n, 0.0);
+    band_eigvals(n, B, T.data(), theta.data());
+    std::vector<int> cand;
+    for (int i = 0; i < n; ++i)
+        if (acceptable(theta[i])) cand.push_back(i);
+    std::sort(cand.begin(), cand.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+    std::vector<double> th(cand.size());
+    for (size_t q = 0; q < cand.size(); ++q) th[q] = theta[cand[q]];
+    S.assign((size_t)n * cand.size(), 0.0);
+    band_eigvecs(n, B, T.data(), (int)cand.size(), th.data(), S.data());
+    const int room = lock_cap - nlock;
+    std::vector<double> Wsel, lcand;
+    for (size_t q = 0; q < cand.size() && (int)lcand.size() < room; ++q) {
+        const double* s = S.data() + q * n;
+        if (!(estimate(m, s) <= tol_est * std::fabs(th[q]))) continue;
+        Wsel.insert(Wsel.end(), s, s + n);
+        lcand.push_back(cur_sigma + 1.0 / th[q]);
+    }
+    if (dbg) {
+        std::fprintf(stderr, "[riga] block run: B=%d steps=%d (blocks %d/%d) breakdown=%d candidates=%zu\n", B, n, m,
+                     nblk, (int)breakdown, lcand.size());
+        for (size_t q = 0; q < cand.size() && q < 12; ++q)
+            std::fprintf(stderr, "[riga]   ritz %zu: lambda=%.15g est=%.3e\n", q, cur_sigma + 1.0 / th[q],
+                         estimate(m, S.data() + q * n) / std::fabs(th[q]));
+        double sym = 0.0, bmax = 0.0;
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < B; ++i)
+                for (int l = 0; l < B; ++l) {
+                    sym = std::max(sym, std::fabs(hA[(size_t)j * B * B + i * B + l] - hA[(size_t)j * B * B + l * B + i]));
+                    bmax = std::max(bmax, std::fabs(hB[(size_t)(j + 1) * B * B + i * B + l]));
+                }
+        std::fprintf(stderr, "[riga]   max asym(A)=%.3e max|B|=%.3e\n", sym, bmax);
+        if (N <= 5000) {
+            // orthogonality of [locked | run] and the projection error of T
+            const int J = col0 + n;
+            std::vector<double> hV((size_t)N * J), hM((size_t)N * J);
+            cudaMemcpy(hV.data(), c->V.ptr, hV.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            cudaMemcpy(hM.data(), c->MV.ptr, hM.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            double orth = 0.0;
+            for (int a = 0; a < J; ++a)
+                for (int b2 = 0; b2 < J; ++b2) {
+                    double d = 0.0;
+                    for (long long i = 0; i < N; ++i) d += hV[(size_t)a * N + i] * hM[(size_t)b2 * N + i];
+                    orth = std::max(orth, std::fabs(d - (a == b2 ? 1.0 : 0.0)));
+                }
+            std::fprintf(stderr, "[riga]   basis orthogonality max|V^T M V - I| = %.3e over %d columns\n", orth, J);
+        }
+    }
+    return ritz_lock(R, col0, n, Wsel, lcand, nlock, lock_tol, lam, n_locked);
+}
+
+}  // namespace riga

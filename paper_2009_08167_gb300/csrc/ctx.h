@@ -154,6 +154,9 @@ struct riga_ctx {
 
     // -------------------------------------------------------------- Lanczos
     int opt_slice = 0, opt_precision = RIGA_FP64, opt_max_steps = 0, opt_extra = 2;
+    int opt_block = 1;                 // Lanczos block size (1, 2, 4; 0 = automatic)
+    riga::DevBuf<double> bwork, bcoef, bpartial, bsmall;  // block Lanczos workspace
+    riga::DevBuf<int> bflag;
     unsigned long long opt_seed = 1;
     riga::DevBuf<double> V, MV;        // basis storage: locked vectors, then the run's vectors
     riga::DevBuf<double> coef;         // Gram-Schmidt coefficients
@@ -254,5 +257,8 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma, double tol);
 int eig_grad_device(riga_ctx* c, int k, const double* w_dev, double* ga_dev, double* gb_dev);
 // tridiag.cpp
 void tridiag_eig(int m, const double* alpha, const double* beta, double* theta, double* Z, bool vectors);
+// band.cpp: symmetric band matrix (dense n x n column-major, half-bandwidth b)
+void band_eigvals(int n, int b, const double* T, double* theta);                      // ascending
+void band_eigvecs(int n, int b, const double* T, int q, const double* th, double* S);  // S: n x q
 
 }  // namespace riga

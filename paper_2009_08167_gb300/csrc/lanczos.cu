@@ -21,13 +21,9 @@
 #include <map>
 #include <numeric>
 
-#include "ctx.h"
+#include "lanczos.h"
 
 namespace riga {
-
-constexpr int CH = 256;  // rows per chunk of the tall-skinny kernels
-
-constexpr int TJ = 32;  // basis columns per shared-memory tile
 
 // Partial dots out[j] = sum_{r in chunk} B[j][r] ws[r] for j < J over one
 // chunk of CH rows.  Each 32-column tile is staged through shared memory by
@@ -337,22 +333,10 @@ __global__ void copy_cols_kernel(long long N, int ncols, const double* __restric
 }
 
 // --------------------------------------------------------------- host side
-namespace {
-
-struct Run {
-    riga_ctx* c;
-    long long N, ld;
-    int cap;       // columns of V / MV
-    int nch;       // chunks
-    double* w;
-    double* Mw;
-    double* xw;
-    double* rw;
-    double* c1;
-    double* c2;
-    double* alpha;
-    double* beta;
-};
+void enqueue_reduce_cols(riga_ctx* c, const double* partial, int nch, int J, int pstride, double* out) {
+    count_launch(c);
+    reduce_cols_kernel<<<(J + 31) / 32, 256, 0, c->stream>>>(partial, nch, J, pstride, out);
+}
 
 uint64_t splitmix(uint64_t& s) {
     s += 0x9E3779B97F4A7C15ULL;
@@ -396,7 +380,7 @@ void normalize_into(Run& R, double* w, int col, int jslot) {
 // Numeric factorization at sigma.  An inertia-only factorization leaves the
 // packed solve operators (Q pool) untouched, so the solve state of the
 // previous factorization (shift, precision) is restored afterwards.
-int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool inertia_only = false) {
+int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool inertia_only) {
     const double keep_sigma = c->sigma;
     const int keep_prec = c->precision;
     const bool keep_factored = c->factored;
@@ -452,13 +436,61 @@ int calibrate_refinement(riga_ctx* c, uint64_t seed) {
     return factor_at(c, c->sigma, RIGA_FP64, nullptr);
 }
 
-}  // namespace
-
 static int configure_reorth(riga_ctx* c, int cap) {
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
     const size_t sm_upd = sm_dots + (size_t)cap * sizeof(double);
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(gemvT_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dots));
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(update_gemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_upd));
+    return RIGA_OK;
+}
+
+// Ritz vectors U = V[:, col0 : col0+m] W (and M U from the stored M V) for the
+// candidate pairs, their FP64 residuals ||K u - lam M u|| / (|lam| ||M u||),
+// and locking of those at most lock_tol into columns nlock, nlock+1, ... of V
+// and M V (eigenvalues appended to lam).
+int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const std::vector<double>& lcand,
+              int nlock, double lock_tol, std::vector<double>& lam, int* n_locked) {
+    riga_ctx* c = R.c;
+    cudaStream_t st = c->stream;
+    const long long N = R.N;
+    const int nsel = (int)lcand.size();
+    *n_locked = 0;
+    if (nsel == 0) return RIGA_OK;
+    // W, then candidate eigenvalues and residual partial sums (304 blocks)
+    RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel + nsel + (size_t)2 * 304 * nsel));
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, Wsel.data(), (size_t)m * nsel * sizeof(double), cudaMemcpyHostToDevice, st));
+    RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
+    double* U = c->evec_perm.ptr;
+    double* MU = c->evec_perm.ptr + (size_t)N * nsel;
+    PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * nsel) * sizeof(double));
+    dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
+    { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N); }
+    { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N); }
+    const int gx = 304;
+    double* dlam = c->Wd.ptr + (size_t)m * nsel;
+    double* dpart = dlam + nsel;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lcand.data(), nsel * sizeof(double), cudaMemcpyHostToDevice, st));
+    { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
+    std::vector<double> part((size_t)2 * gx * nsel);
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    int acc_n = 0;
+    for (int q = 0; q < nsel; ++q) {
+        double ra = 0.0, rb = 0.0;
+        for (int b = 0; b < gx; ++b) {
+            ra += part[((size_t)q * gx + b) * 2];
+            rb += part[((size_t)q * gx + b) * 2 + 1];
+        }
+        const double rho = std::sqrt(ra) / (std::fabs(lcand[q]) * std::sqrt(rb));
+        if (!(rho <= lock_tol)) continue;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->V.ptr + (long long)(nlock + acc_n) * R.ld, U + (long long)q * N,
+                                         N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->MV.ptr + (long long)(nlock + acc_n) * R.ld, MU + (long long)q * N,
+                                         N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        lam.push_back(lcand[q]);
+        ++acc_n;
+    }
+    *n_locked = acc_n;
     return RIGA_OK;
 }
 
@@ -478,11 +510,20 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     int m_cap = c->opt_max_steps > 0 ? c->opt_max_steps : std::max(4 * wmax, wmax + 60);
     m_cap = (int)std::min<long long>(m_cap, N - 1);
     const int lock_cap = k + extra + 64;
+    // block size: 2 or 4 when the solve can carry that many right-hand sides
+    int B = c->opt_block == 0 ? 4 : c->opt_block;
+    if (B > 1) B = std::min(B, solve_max_rhs(c));
+    if (B == 3) B = 2;
+    if (B < 1 || (long long)(m_cap + 2 * B) >= N) B = 1;
+    // block runs converge with the number of block steps: they get 16 more
+    // blocks than the single-vector run length (they stop early once converged)
+    const int m_extra = B > 1 ? 16 * B : 0;
+    if (B > 1 && (long long)(m_cap + m_extra + 2 * B) >= N) B = 1;
     Run R;
     R.c = c;
     R.N = N;
     R.ld = N;
-    R.cap = lock_cap + m_cap + 1;
+    R.cap = lock_cap + m_cap + (B > 1 ? 16 * B : 0) + 1 + 2 * B;
     R.nch = (int)((N + CH - 1) / CH);
     if (c->V.alloc((size_t)N * R.cap) != cudaSuccess || c->MV.alloc((size_t)N * R.cap) != cudaSuccess)
         return set_error(c, RIGA_ENOMEM, "Lanczos basis");
@@ -600,6 +641,25 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
         if (nlock + m_max + 1 > R.cap) { status = set_error(c, RIGA_ENOMEM, "Lanczos basis capacity"); break; }
         const int col0 = nlock;
         cudaEventRecord(ev0, st);
+        if (B > 1) {
+            int mb = 0, acc_n = 0;
+            const int m_blk = (int)std::min<long long>(m_max + 16 * B, N - nlock - 2 * B);
+            rc = block_run(R, B, nlock, want_run, m_blk, cur_sigma, sigma0, tol_est, lock_tol, lock_cap, seed, lam, &mb,
+                           &acc_n);
+            if (rc) { status = rc; break; }
+            nlock += acc_n;
+            if (acc_n > 0) fruitless = 0;
+            else ++fruitless;
+            if (dbg)
+                std::fprintf(stderr, "[riga] run %d: shift=%.12g want=%d block=%d steps=%d/%d locked=%d total=%d\n", runs,
+                             cur_sigma, want_run, B, mb, m_max, acc_n, nlock);
+            cudaEventRecord(ev1, st);
+            RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            c->stats.t_lanczos_ms += ms;
+            continue;
+        }
         // random start vector, M-orthogonal to the locked ones
         for (long long i = 0; i < N; ++i) {
             uint64_t u = splitmix(seed);
@@ -682,44 +742,11 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             Wsel.assign((size_t)m * nsel, 0.0);
             for (int q = 0; q < nsel; ++q)
                 for (int r = 0; r < m; ++r) Wsel[(size_t)q * m + r] = Zf[(size_t)sel[q] * m + r];
-            // W, then candidate eigenvalues and residual partial sums (304 blocks)
-            RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel + nsel + (size_t)2 * 304 * nsel));
-            RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, Wsel.data(), Wsel.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-            RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
-            double* U = c->evec_perm.ptr;
-            double* MU = c->evec_perm.ptr + (size_t)N * nsel;
-            PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * nsel) * sizeof(double));
-            dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
-            { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N); }
-            { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N); }
-            // lock only the candidates whose FP64 residual
-            // ||K u - lam M u|| / (|lam| ||M u||) meets the tolerance
             std::vector<double> lcand(nsel);
             for (int q = 0; q < nsel; ++q) lcand[q] = cur_sigma + 1.0 / theta[sel[q]];
-            const int gx = 304;
-            double* dlam = c->Wd.ptr + (size_t)m * nsel;
-            double* dpart = dlam + nsel;
-            RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lcand.data(), nsel * sizeof(double), cudaMemcpyHostToDevice, st));
-            { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
-            std::vector<double> part((size_t)2 * gx * nsel);
-            RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-            RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
             int acc_n = 0;
-            for (int q = 0; q < nsel; ++q) {
-                double ra = 0.0, rb = 0.0;
-                for (int b = 0; b < gx; ++b) {
-                    ra += part[((size_t)q * gx + b) * 2];
-                    rb += part[((size_t)q * gx + b) * 2 + 1];
-                }
-                const double rho = std::sqrt(ra) / (std::fabs(lcand[q]) * std::sqrt(rb));
-                if (!(rho <= lock_tol)) continue;
-                RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->V.ptr + (long long)(nlock + acc_n) * R.ld, U + (long long)q * N,
-                                                 N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-                RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->MV.ptr + (long long)(nlock + acc_n) * R.ld, MU + (long long)q * N,
-                                                 N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-                lam.push_back(lcand[q]);
-                ++acc_n;
-            }
+            rc = ritz_lock(R, col0, m, Wsel, lcand, nlock, lock_tol, lam, &acc_n);
+            if (rc) { status = rc; break; }
             nlock += acc_n;
             if (acc_n > 0) fruitless = 0;
             else ++fruitless;

@@ -644,7 +644,7 @@ int solve_max_rhs(riga_ctx* c) {
     if (S.solve_mode == SOLVE_CTA256) return 1;
     int maxopt = 0;
     if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return 1;
-    const size_t elem = c->precision == RIGA_FP64 ? sizeof(double) : sizeof(float);
+    const size_t elem = sizeof(double);  // the larger of the two front precisions
     for (int nr : {4, 2}) {
         int chunk = 0, nt = 0;
         const size_t smem = solve_smem(S, nr, elem, &chunk, &nt);

@@ -82,6 +82,8 @@ def load_library(path=LIB_PATH):
     lib.riga_set_eig_options.argtypes = [P, I, I, I, I, ctypes.c_ulonglong]
     lib.riga_eig_grad.argtypes = [P, I, P, P, P]
     lib.riga_assemble_batch.argtypes = [P, I, ctypes.POINTER(_MeshC), P, P]
+    lib.riga_band_eig.argtypes = [I, I, P, P, I, P, P]
+    lib.riga_set_eig_block.argtypes = [P, I]
     lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
     lib.riga_get_symbolic.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(LL), P, P, P, P, P]
@@ -261,6 +263,9 @@ class Riga:
     def set_eig_options(self, slice=0, precision=RIGA_FP64, max_steps=0, extra=2, seed=1):
         self._check(self.lib.riga_set_eig_options(self.ctx, int(slice), int(precision), int(max_steps), int(extra), int(seed)))
 
+    def set_eig_block(self, block):
+        self._check(self.lib.riga_set_eig_block(self.ctx, int(block)))
+
     # ------------------------------------------------------------ riga_eigs
     def eigs(self, k, sigma=0.0, tol=1e-10, vectors=True, device_out=False):
         N = self.query()["N"]
@@ -379,6 +384,23 @@ class Riga:
                                                   ctypes.byref(by), ctypes.byref(fl)))
             out[name] = dict(launches=la.value, calls=ca.value, ms=ms.value, bytes=by.value, flops=fl.value)
         return out
+
+
+def band_eig(T, b, which=()):
+    """Eigenvalues (ascending) of the symmetric band matrix T (half-bandwidth
+    b) and the eigenvectors of the eigenvalues with indices `which`; host
+    only."""
+    lib = load_library()
+    T = np.asfortranarray(T, dtype=np.float64)
+    n = T.shape[0]
+    theta = np.zeros(n)
+    wh = np.ascontiguousarray(which, dtype=np.int32)
+    S = np.zeros((n, max(1, wh.size)), order="F")
+    rc = lib.riga_band_eig(n, int(b), _ptr(T), _ptr(theta), int(wh.size), _ptr(wh) if wh.size else None,
+                           _ptr(S) if wh.size else None)
+    if rc != RIGA_OK:
+        raise RigaError(rc, lib.riga_strerror(rc).decode())
+    return theta, S[:, :wh.size]
 
 
 def spmv_dot_noalloc(rowptr, col, val, x, y, xy, stream=None):

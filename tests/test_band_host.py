@@ -1,0 +1,62 @@
+"""Host Rayleigh-Ritz of block Lanczos (riga_band_eig): eigenpairs of
+symmetric band matrices against numpy's dense symmetric eigensolver, with
+exact multiplicities included.  No GPU."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2009_08167_gb300 import riga
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not os.path.exists(riga.LIB_PATH):
+        from paper_2009_08167_gb300.build import build
+        build()
+
+
+def _band(n, b, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(n, n))
+    A = A + A.T
+    for i in range(n):
+        for j in range(n):
+            if abs(i - j) > b:
+                A[i, j] = 0.0
+    return A
+
+
+@pytest.mark.parametrize("n,b", [(1, 1), (7, 1), (40, 2), (120, 4), (203, 6), (64, 63)])
+def test_band_eig_vs_dense(n, b):
+    T = _band(n, b, 10 * n + b)
+    which = sorted(set(range(0, n, max(1, n // 17))) | {n - 1})
+    theta, S = riga.band_eig(T, b, which)
+    ref = np.linalg.eigvalsh(T)
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(theta - ref)) <= 1e-12 * scale
+    R = T @ S - S * theta[which]
+    assert np.max(np.abs(R)) <= 1e-11 * scale
+    assert np.max(np.abs(S.T @ S - np.eye(len(which)))) <= 1e-10
+
+
+def test_band_eig_multiplicity():
+    # block Lanczos can produce exact multiplicities: two copies of one band
+    # matrix interleaved (a permutation of a block-diagonal matrix keeps the
+    # band when the copies alternate) give every eigenvalue twice
+    n0, b0 = 30, 2
+    T0 = _band(n0, b0, 3)
+    n = 2 * n0
+    T = np.zeros((n, n))
+    for i in range(n0):
+        for j in range(n0):
+            T[2 * i, 2 * j] = T0[i, j]
+            T[2 * i + 1, 2 * j + 1] = T0[i, j]
+    b = 2 * b0
+    which = list(range(n))
+    theta, S = riga.band_eig(T, b, which)
+    ref = np.sort(np.concatenate([np.linalg.eigvalsh(T0)] * 2))
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(theta - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(T @ S - S * theta)) <= 1e-11 * scale
+    assert np.max(np.abs(S.T @ S - np.eye(n))) <= 1e-10
