@@ -235,11 +235,16 @@ int riga_eigs_batch(riga_ctx* ctx, int k, double sigma, double tol, double* eval
  *  theta[n]: HOST out, all eigenvalues ascending.
  *  which[q]: HOST, indices into theta of the wanted eigenvectors; S[n*q]:
  *    HOST out, column-major, orthonormal eigenvectors (sign unspecified).
- * Band reduction to tridiagonal form by Givens rotations, implicit QL, and
- * inverse iteration with a pivoted band LU, orthogonalised within clusters.
+ *  r, Zlast[r*n] (r may be 0, then Zlast NULL): HOST out, the last r rows of
+ *    ALL eigenvectors, column i for theta[i] (column-major r x n): what the
+ *    block Lanczos residual estimates need.
+ * Band reduction to tridiagonal form by Givens rotations (tracking the last r
+ * rows of the accumulated rotation), implicit QL, and inverse iteration with
+ * a pivoted band LU, orthogonalised within clusters.
  * Errors: RIGA_EINVAL (bad sizes or indices).
  */
-int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S);
+int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S, int r,
+                  double* Zlast);
 
 /*
  * riga_set_eig_block: Lanczos block size of riga_eigs.  1 (the default) is

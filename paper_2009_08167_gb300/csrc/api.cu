@@ -192,6 +192,7 @@ void riga_destroy(riga_ctx* c) {
     }
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->bpin) cudaFreeHost(c->bpin);
     delete c;
 }
 

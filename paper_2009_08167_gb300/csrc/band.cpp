@@ -110,16 +110,29 @@ void band_solve(const BandLU& F, double* x) {
 
 }  // namespace
 
-void band_eigvals(int n, int b, const double* T, double* theta) {
-    if (n <= 0) return;
+// Band -> tridiagonal reduction; the rotations are also applied (as Q <- Q G^T)
+// to the r x n row block qr (column-major), which starts as the last r rows of
+// the identity, so that it ends as the last r rows of Q (T = Q T_tri Q^T).
+static void band_reduce(int n, int b, const double* T, std::vector<double>& d, std::vector<double>& e, int r,
+                        std::vector<double>& qr) {
     std::vector<double> A(T, T + (size_t)n * n);
     auto at = [&](int i, int j) -> double& { return A[(size_t)j * n + i]; };
+    auto track = [&](int p, int q, double c, double s) {
+        for (int k = 0; k < r; ++k) {
+            double& a = qr[(size_t)p * r + k];
+            double& bq = qr[(size_t)q * r + k];
+            const double x = a, y = bq;
+            a = c * x + s * y;
+            bq = -s * x + c * y;
+        }
+    };
     for (int j = 0; j + 2 < n; ++j) {
         for (int i = std::min(j + b, n - 1); i >= j + 2; --i) {
             const double x = at(i - 1, j), y = at(i, j);
             if (y == 0.0) continue;
-            const double r = std::hypot(x, y);
-            rotate_sym(A, n, b, i - 1, i, x / r, y / r);
+            const double rr = std::hypot(x, y);
+            rotate_sym(A, n, b, i - 1, i, x / rr, y / rr);
+            if (r > 0) track(i - 1, i, x / rr, y / rr);
             at(i, j) = 0.0;
             at(j, i) = 0.0;
             // chase the bulge at (k + b, k - 1) down the band
@@ -129,16 +142,33 @@ void band_eigvals(int n, int b, const double* T, double* theta) {
                 if (y2 == 0.0) break;
                 const double r2 = std::hypot(x2, y2);
                 rotate_sym(A, n, b, p, q, x2 / r2, y2 / r2);
+                if (r > 0) track(p, q, x2 / r2, y2 / r2);
                 at(q, col) = 0.0;
                 at(col, q) = 0.0;
                 k = q;
             }
         }
     }
-    std::vector<double> d(n), e(n, 0.0), z(n);
+    d.assign(n, 0.0);
+    e.assign(n, 0.0);
     for (int i = 0; i < n; ++i) d[i] = at(i, i);
     for (int i = 0; i + 1 < n; ++i) e[i] = at(i + 1, i);
+}
+
+void band_eigvals(int n, int b, const double* T, double* theta) {
+    if (n <= 0) return;
+    std::vector<double> d, e, qr, z(n);
+    band_reduce(n, b, T, d, e, 0, qr);
     tridiag_eig(n, d.data(), e.data(), theta, z.data(), false);
+}
+
+void band_eig_lastrows(int n, int b, const double* T, int r, double* theta, double* Zlast) {
+    if (n <= 0) return;
+    r = std::min(r, n);
+    std::vector<double> d, e, qr((size_t)r * n, 0.0);
+    for (int k = 0; k < r; ++k) qr[(size_t)(n - r + k) * r + k] = 1.0;  // last r rows of I
+    band_reduce(n, b, T, d, e, r, qr);
+    tridiag_eig_rows(n, d.data(), e.data(), theta, r, qr.data(), Zlast);
 }
 
 void band_eigvecs(int n, int b, const double* T, int q, const double* th, double* S) {
@@ -187,11 +217,14 @@ void band_eigvecs(int n, int b, const double* T, int q, const double* th, double
 
 using namespace riga;
 
-extern "C" int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S) {
-    if (n < 1 || b < 0 || !T || !theta || q < 0 || (q > 0 && (!which || !S))) return RIGA_EINVAL;
+extern "C" int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S, int r,
+                             double* Zlast) {
+    if (n < 1 || b < 0 || !T || !theta || q < 0 || (q > 0 && (!which || !S)) || r < 0 || r > n || (r > 0 && !Zlast))
+        return RIGA_EINVAL;
     for (int i = 0; i < q; ++i)
         if (which[i] < 0 || which[i] >= n) return RIGA_EINVAL;
-    band_eigvals(n, std::max(b, 1), T, theta);
+    if (r > 0) band_eig_lastrows(n, std::max(b, 1), T, r, theta, Zlast);
+    else band_eigvals(n, std::max(b, 1), T, theta);
     if (q > 0) {
         std::vector<double> th(q);
         for (int i = 0; i < q; ++i) th[i] = theta[which[i]];

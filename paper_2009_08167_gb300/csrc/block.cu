@@ -246,35 +246,30 @@ __global__ void __launch_bounds__(256) bgram_kernel(long long N, const double* _
     }
 }
 
-// out[e] = sum over nb partial blocks of partial[i * count + e] (fixed order)
+// out[e] = sum over nb partial blocks of partial[i * count + e] (fixed
+// order), one block per entry e
 __global__ void __launch_bounds__(256) bsum_small_kernel(const double* __restrict__ partial, int nb, int count,
                                                          double* __restrict__ out) {
     __shared__ double sh[256];
-    for (int e = 0; e < count; ++e) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[(long long)i * count + e];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[e] = sh[0];
+    const int e = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[(long long)i * count + e];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
+    if (threadIdx.x == 0) out[e] = sh[0];
 }
 
-// Cholesky G + s I = R^T R of the symmetrised B x B Gram matrix (one
-// thread), s = shift_rel * trace(G); R^{-1}; and optionally Bout = R Rprev
-// (the block's triangular factor accumulated over the QR passes).  A pivot at
-// or below 1e-24 of the largest diagonal entry is a breakdown: flag bit 0,
-// and R = I so that the step stays finite.
+// Cholesky G + s I = R^T R of the symmetrised B x B Gram matrix,
+// s = shift_rel * trace(G), and R^{-1}.  A pivot at or below 1e-24 of the
+// largest diagonal entry is a breakdown (returned true) and R = I, so that
+// the step stays finite.
 template <int B>
-__global__ void bchol_kernel(const double* __restrict__ G, double shift_rel, double* __restrict__ Rinv,
-                             const double* __restrict__ Rprev, double* __restrict__ Bout, double* __restrict__ Rout,
-                             int* __restrict__ flag) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double g[B][B], R[B][B], Ri[B][B];
+__device__ bool bcholesky(const double* __restrict__ G, double shift_rel, double (*R)[B], double (*Ri)[B]) {
+    double g[B][B];
     double dmax = 0.0, tr = 0.0;
     for (int i = 0; i < B; ++i)
         for (int j = 0; j < B; ++j) {
@@ -300,13 +295,10 @@ __global__ void bchol_kernel(const double* __restrict__ G, double shift_rel, dou
             R[i][j] = v / R[i][i];
         }
     }
-    if (bad) {
-        atomicOr(flag, 1);
+    if (bad)
         for (int i = 0; i < B; ++i)
             for (int j = 0; j < B; ++j) R[i][j] = (i == j) ? 1.0 : 0.0;
-    }
-    // upper-triangular inverse
-    for (int j = 0; j < B; ++j) {
+    for (int j = 0; j < B; ++j) {  // upper-triangular inverse
         Ri[j][j] = 1.0 / R[j][j];
         for (int i = j - 1; i >= 0; --i) {
             double s = 0.0;
@@ -314,31 +306,43 @@ __global__ void bchol_kernel(const double* __restrict__ G, double shift_rel, dou
             Ri[i][j] = -s / R[i][i];
         }
     }
-    for (int i = 0; i < B; ++i)
-        for (int j = 0; j < B; ++j) {
-            Rinv[i * B + j] = Ri[i][j];
-            if (Rout) Rout[i * B + j] = R[i][j];
-        }
-    if (Bout) {
-        for (int i = 0; i < B; ++i)
-            for (int j = 0; j < B; ++j) {
-                double s = 0.0;
-                for (int k = 0; k < B; ++k) s += R[i][k] * (Rprev ? Rprev[k * B + j] : (k == j ? 1.0 : 0.0));
-                Bout[i * B + j] = s;
-            }
-    }
+    return bad;
 }
 
-// X[:, l] = sum_{i <= l} Y[:, i] Rinv[i][l] for both Y = W (into V) and
-// Y = M W (into M V); in place when the output aliases the input
+// One QR pass: every block factors the small Gram matrix itself (no separate
+// launch), then X[:, l] = sum_{i <= l} Y[:, i] R^{-1}[i][l] for Y = W (into V)
+// and Y = M W (into M V), in place when the output aliases the input.  Block
+// 0 records R (Rout), the accumulated factor Bout = R Rprev, and a breakdown
+// (flag bit 0).
 template <int B>
-__global__ void bscale_kernel(long long N, const double* __restrict__ Rinv, const double* W, long long ldw,
-                              const double* MW, double* V, double* MV, long long ldv) {
+__global__ void __launch_bounds__(256) bqr_scale_kernel(long long N, const double* __restrict__ G, double shift_rel,
+                                                        const double* __restrict__ Rprev, double* __restrict__ Bout,
+                                                        double* __restrict__ Rout, int* __restrict__ flag,
+                                                        const double* W, long long ldw, const double* MW, double* V,
+                                                        double* MV, long long ldv) {
+    __shared__ double sri[B * B];
+    if (threadIdx.x == 0) {
+        double R[B][B], Ri[B][B];
+        const bool bad = bcholesky<B>(G, shift_rel, R, Ri);
+        for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j) sri[i * B + j] = Ri[i][j];
+        if (blockIdx.x == 0) {
+            if (bad) atomicOr(flag, 1);
+            if (Rout)
+                for (int i = 0; i < B; ++i)
+                    for (int j = 0; j < B; ++j) Rout[i * B + j] = R[i][j];
+            if (Bout)
+                for (int i = 0; i < B; ++i)
+                    for (int j = 0; j < B; ++j) {
+                        double s = 0.0;
+                        for (int k = 0; k < B; ++k) s += R[i][k] * (Rprev ? Rprev[k * B + j] : (k == j ? 1.0 : 0.0));
+                        Bout[i * B + j] = s;
+                    }
+        }
+    }
+    __syncthreads();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double ri[B * B];
-#pragma unroll
-    for (int e = 0; e < B * B; ++e) ri[e] = Rinv[e];
     double w[B], mw[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) {
@@ -350,8 +354,8 @@ __global__ void bscale_kernel(long long N, const double* __restrict__ Rinv, cons
         double a = 0.0, b = 0.0;
 #pragma unroll
         for (int r = 0; r <= l; ++r) {
-            a += w[r] * ri[r * B + l];
-            b += mw[r] * ri[r * B + l];
+            a += w[r] * sri[r * B + l];
+            b += mw[r] * sri[r * B + l];
         }
         V[l * ldv + i] = a;
         MV[l * ldv + i] = b;
@@ -416,8 +420,7 @@ int bnormalize_t(BlockWork& K, int col, double* Bout) {
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)K.N * 8.0 * 10.0 * B);
     const unsigned nbs = (unsigned)((K.N * 16 + 255) / 256);
     double* G = K.small;
-    double* Rinv = G + B * B;
-    double* R1 = Rinv + B * B;
+    double* R1 = G + B * B;
     double* R2 = R1 + B * B;
     double* V = c->V.ptr + (long long)col * K.ld;
     double* MV = c->MV.ptr + (long long)col * K.ld;
@@ -425,18 +428,18 @@ int bnormalize_t(BlockWork& K, int col, double* Bout) {
     const double shift = 11.0 * ((double)K.N * B + (double)B * (B + 1)) * 1.1102230246251565e-16;
     { count_launch(c); bspmv_gram_kernel<B><<<nbs, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW, K.part); }
     c->stats.n_matvec += B;
-    { count_launch(c); bsum_small_kernel<<<1, 256, 0, st>>>(K.part, (int)nbs, B * B, G); }
-    { count_launch(c); bchol_kernel<B><<<1, 32, 0, st>>>(G, shift, Rinv, nullptr, nullptr, R1, K.flag); }
-    { count_launch(c); bscale_kernel<B><<<gb, 256, 0, st>>>(K.N, Rinv, K.W, K.N, K.MW, V, MV, K.ld); }
+    { count_launch(c); bsum_small_kernel<<<B * B, 256, 0, st>>>(K.part, (int)nbs, B * B, G); }
+    { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G, shift, nullptr, nullptr, R1, K.flag, K.W, K.N,
+                                                              K.MW, V, MV, K.ld); }
     for (int pass = 0; pass < 2; ++pass) {
-        // the Gram matrix of the new columns, its Cholesky factor, and the
-        // accumulated triangular factor (R1 <- R R1, finally into Bout)
+        // the Gram matrix of the new columns; the pass's factor accumulates
+        // into R2 = R R1, then Bout = R R2
         { count_launch(c); bgram_kernel<B><<<304, 256, 0, st>>>(K.N, V, K.ld, MV, K.part); }
-        { count_launch(c); bsum_small_kernel<<<1, 256, 0, st>>>(K.part, 304, B * B, G); }
+        { count_launch(c); bsum_small_kernel<<<B * B, 256, 0, st>>>(K.part, 304, B * B, G); }
         double* acc = pass == 0 ? R2 : Bout;
         const double* prev = pass == 0 ? R1 : R2;
-        { count_launch(c); bchol_kernel<B><<<1, 32, 0, st>>>(G, 0.0, Rinv, prev, acc, nullptr, K.flag); }
-        { count_launch(c); bscale_kernel<B><<<gb, 256, 0, st>>>(K.N, Rinv, V, K.ld, MV, V, MV, K.ld); }
+        { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G, 0.0, prev, acc, nullptr, K.flag, V, K.ld, MV,
+                                                                  V, MV, K.ld); }
     }
     return RIGA_OK;
 }
@@ -492,11 +495,19 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.cap = R.cap;
     const unsigned nbs = (unsigned)((N * 16 + 255) / 256);
     const size_t part_n = std::max<size_t>((size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B);
+    const size_t nAB = (size_t)(2 * nblk + 1) * B * B;  // the T blocks: A_0..A_{nblk-1}, B_0..B_nblk
     RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)2 * N * B));
     RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
     RIGA_CUDA_TRY(c, c->bpartial.alloc(part_n));
-    RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)5 * B * B + (size_t)(nblk + 2) * 2 * B * B));
+    RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)4 * B * B + nAB));
     RIGA_CUDA_TRY(c, c->bflag.alloc(1));
+    if (c->bpin_size < nAB + 2) {
+        if (c->bpin) cudaFreeHost(c->bpin);
+        c->bpin = nullptr;
+        c->bpin_size = 0;
+        RIGA_CUDA_TRY(c, cudaMallocHost(&c->bpin, (nAB + 2) * sizeof(double)));
+        c->bpin_size = nAB + 2;
+    }
     K.W = c->bwork.ptr;
     K.MW = c->bwork.ptr + (size_t)N * B;
     K.C1 = c->bcoef.ptr;
@@ -504,8 +515,11 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.part = c->bpartial.ptr;
     K.small = c->bsmall.ptr;
     K.flag = c->bflag.ptr;
-    double* dA = c->bsmall.ptr + 5 * B * B;               // nblk blocks
-    double* dB = dA + (size_t)(nblk + 1) * B * B;         // nblk + 1 blocks
+    double* dA = c->bsmall.ptr + 4 * B * B;  // nblk diagonal blocks, then nblk + 1 sub-diagonal blocks
+    double* dB = dA + (size_t)nblk * B * B;
+    double* hA = c->bpin;                   // pinned host copies, same layout
+    double* hB = hA + (size_t)nblk * B * B;
+    int* hflags = reinterpret_cast<int*>(hA + nAB);  // [0] QR breakdown, [1] solve wait flag
     const size_t smx = dots_smem(B) + (size_t)K.cap * B * sizeof(double);
     if (B == 4) {
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bdots_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem(4)));
@@ -529,141 +543,135 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     rc = bnormalize(K, col0, dB);
     if (rc) return rc;
 
-    // host copies of the blocks and the check state
-    std::vector<double> hA, hB, T, theta, S;
-    const int ck = std::max(1, 8 / B);  // block steps between convergence checks
-    int m = 0;
+    std::vector<double> T, theta, Zl;
     bool breakdown = false;
-    auto fetch = [&](int mm) -> int {
-        hA.resize((size_t)mm * B * B);
-        hB.resize((size_t)(mm + 1) * B * B);
-        int hf = 0, dflag = 0;
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hA.data(), dA, hA.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hB.data(), dB, hB.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(&hf, K.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
-        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
-        if (dflag & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
-        breakdown = breakdown || (hf != 0);
+    auto acceptable = [&](double th) { return th != 0.0 && cur_sigma + 1.0 / th > sigma0; };
+    // copies of the first mm diagonal and mm + 1 sub-diagonal blocks and the
+    // flags into pinned memory (asynchronous)
+    auto enqueue_fetch = [&](int mm) -> int {
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hA, dA, (size_t)mm * B * B * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hB, dB, (size_t)(mm + 1) * B * B * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hflags, K.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(hflags + 1, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
         return RIGA_OK;
     };
-    // residual estimate ||B_m s_last|| of eigenvector s (length n = mm B)
-    auto estimate = [&](int mm, const double* s) {
-        const double* b = hB.data() + (size_t)mm * B * B;
-        const double* sl = s + (size_t)(mm - 1) * B;
-        double e2 = 0.0;
-        for (int i = 0; i < B; ++i) {
-            double v = 0.0;
-            for (int l = 0; l < B; ++l) v += b[i * B + l] * sl[l];
-            e2 += v * v;
+    // Ritz values of T_mm and residual estimates ||B_mm s_last|| for all of them
+    auto ritz = [&](int mm, std::vector<double>& est) {
+        const int n = mm * B;
+        build_T(mm, B, hA, hB, T);
+        theta.assign(n, 0.0);
+        Zl.assign((size_t)B * n, 0.0);
+        band_eig_lastrows(n, B, T.data(), B, theta.data(), Zl.data());
+        const double* b = hB + (size_t)mm * B * B;
+        est.assign(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            double e2 = 0.0;
+            for (int r = 0; r < B; ++r) {
+                double v = 0.0;
+                for (int l = 0; l < B; ++l) v += b[r * B + l] * Zl[(size_t)i * B + l];
+                e2 += v * v;
+            }
+            est[i] = std::sqrt(e2);
         }
-        return std::sqrt(e2);
     };
-    auto acceptable = [&](double th) { return th != 0.0 && cur_sigma + 1.0 / th > sigma0; };
+    // converged: the want_run acceptable Ritz values of largest |theta| all
+    // have estimates below tol_est |theta|
+    auto converged = [&](int mm) {
+        std::vector<double> est;
+        ritz(mm, est);
+        std::vector<int> ord;
+        for (int i = 0; i < mm * B; ++i)
+            if (acceptable(theta[i])) ord.push_back(i);
+        if ((int)ord.size() < want_run) return false;
+        std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+        for (int q = 0; q < want_run; ++q)
+            if (!(est[ord[q]] <= tol_est * std::fabs(theta[ord[q]]))) return false;
+        return true;
+    };
 
-    for (int j = 0; j < nblk; ++j) {
+    // Checks are lagged: the block copies of step m are queued with an
+    // event, the host evaluates them while the GPU runs the next steps, and
+    // it never runs more than two block steps ahead of an unevaluated check.
+    const int ck = std::max(1, 8 / B);  // block steps between checks
+    cudaEvent_t ev;
+    RIGA_CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    int pending = -1, m = 0;
+    bool done = false;
+    for (int j = 0; j < nblk && !done; ++j) {
         const int cj = col0 + j * B;
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(K.W, c->MV.ptr + (long long)cj * R.ld, (size_t)N * B * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-        if (c->precision == RIGA_FP64) {
-            rc = enqueue_solve(c, K.W, B);
-        } else {
-            for (int r = 0; r < B && rc == RIGA_OK; ++r)
-                rc = solve_refined(c, K.W + (size_t)r * N, R.xw, R.rw, 0.0, c->ir_sweeps, 0, nullptr);
+        rc = RIGA_OK;
+        if (cudaMemcpyAsync(K.W, c->MV.ptr + (long long)cj * R.ld, (size_t)N * B * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = set_error(c, RIGA_ECUDA, "block copy");
+        if (rc == RIGA_OK) {
+            if (c->precision == RIGA_FP64) {
+                rc = enqueue_solve(c, K.W, B);
+            } else {
+                for (int r = 0; r < B && rc == RIGA_OK; ++r)
+                    rc = solve_refined(c, K.W + (size_t)r * N, R.xw, R.rw, 0.0, c->ir_sweeps, 0, nullptr);
+            }
         }
-        if (rc) return rc;
-        rc = bortho(K, cj + B);
-        if (rc) return rc;
-        {
+        if (rc == RIGA_OK) rc = bortho(K, cj + B);
+        if (rc == RIGA_OK) {
             count_launch(c);
             if (B == 4) balpha_kernel<4><<<1, 32, 0, st>>>(K.C1, K.C2, cj, dA + (size_t)j * B * B);
             else balpha_kernel<2><<<1, 32, 0, st>>>(K.C1, K.C2, cj, dA + (size_t)j * B * B);
+            rc = bnormalize(K, cj + B, dB + (size_t)(j + 1) * B * B);
         }
-        rc = bnormalize(K, cj + B, dB + (size_t)(j + 1) * B * B);
-        if (rc) return rc;
+        if (rc) {
+            cudaEventDestroy(ev);
+            return rc;
+        }
         c->stats.steps += B;
         m = j + 1;
-        if (m * B >= want_run && (m % ck == 0 || m == nblk)) {
-            rc = fetch(m);
-            if (rc) return rc;
-            if (breakdown) break;
-            const int n = m * B;
-            build_T(m, B, hA.data(), hB.data(), T);
-            theta.assign(n, 0.0);
-            band_eigvals(n, B, T.data(), theta.data());
-            // the want_run acceptable Ritz values of largest |theta|
-            std::vector<int> ord;
-            for (int i = 0; i < n; ++i)
-                if (acceptable(theta[i])) ord.push_back(i);
-            std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
-            if ((int)ord.size() < want_run) continue;
-            ord.resize(want_run);
-            std::vector<double> th(want_run);
-            for (int q = 0; q < want_run; ++q) th[q] = theta[ord[q]];
-            S.assign((size_t)n * want_run, 0.0);
-            band_eigvecs(n, B, T.data(), want_run, th.data(), S.data());
-            bool all = true;
-            for (int q = 0; q < want_run && all; ++q)
-                if (!(estimate(m, S.data() + (size_t)q * n) <= tol_est * std::fabs(th[q]))) all = false;
-            if (all) break;
+        if (pending >= 0 && (m - pending >= 2 || cudaEventQuery(ev) == cudaSuccess)) {
+            cudaEventSynchronize(ev);
+            if (hflags[1] & 2) {
+                cudaEventDestroy(ev);
+                return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+            }
+            breakdown = hflags[0] != 0;
+            done = breakdown || converged(pending);
+            pending = -1;
+        }
+        if (!done && pending < 0 && m * B >= want_run && m % ck == 0 && m < nblk) {
+            rc = enqueue_fetch(m);
+            if (rc) {
+                cudaEventDestroy(ev);
+                return rc;
+            }
+            cudaEventRecord(ev, st);
+            pending = m;
         }
     }
+    cudaEventDestroy(ev);
     *m_out = m * B;
     if (m == 0) return RIGA_OK;
     // Rayleigh-Ritz with vectors: every acceptable Ritz pair whose estimate
     // meets the bar, largest |theta| first, up to the locking room
-    int rc2 = fetch(m);
-    if (rc2) return rc2;
+    rc = enqueue_fetch(m);
+    if (rc) return rc;
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (hflags[1] & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+    breakdown = hflags[0] != 0;
     const int n = m * B;
-    build_T(m, B, hA.data(), hB.data(), T);
-    theta.assign(n, 0.0);
-    band_eigvals(n, B, T.data(), theta.data());
+    std::vector<double> est;
+    ritz(m, est);
     std::vector<int> cand;
     for (int i = 0; i < n; ++i)
-        if (acceptable(theta[i])) cand.push_back(i);
+        if (acceptable(theta[i]) && est[i] <= tol_est * std::fabs(theta[i])) cand.push_back(i);
     std::sort(cand.begin(), cand.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
-    std::vector<double> th(cand.size());
-    for (size_t q = 0; q < cand.size(); ++q) th[q] = theta[cand[q]];
-    S.assign((size_t)n * cand.size(), 0.0);
-    band_eigvecs(n, B, T.data(), (int)cand.size(), th.data(), S.data());
     const int room = lock_cap - nlock;
-    std::vector<double> Wsel, lcand;
-    for (size_t q = 0; q < cand.size() && (int)lcand.size() < room; ++q) {
-        const double* s = S.data() + q * n;
-        if (!(estimate(m, s) <= tol_est * std::fabs(th[q]))) continue;
-        Wsel.insert(Wsel.end(), s, s + n);
-        lcand.push_back(cur_sigma + 1.0 / th[q]);
+    if ((int)cand.size() > room) cand.resize(std::max(room, 0));
+    std::vector<double> th(cand.size()), Wsel((size_t)n * cand.size()), lcand(cand.size());
+    for (size_t q = 0; q < cand.size(); ++q) {
+        th[q] = theta[cand[q]];
+        lcand[q] = cur_sigma + 1.0 / th[q];
     }
-    if (dbg) {
+    band_eigvecs(n, B, T.data(), (int)cand.size(), th.data(), Wsel.data());
+    if (dbg)
         std::fprintf(stderr, "[riga] block run: B=%d steps=%d (blocks %d/%d) breakdown=%d candidates=%zu\n", B, n, m,
                      nblk, (int)breakdown, lcand.size());
-        for (size_t q = 0; q < cand.size() && q < 12; ++q)
-            std::fprintf(stderr, "[riga]   ritz %zu: lambda=%.15g est=%.3e\n", q, cur_sigma + 1.0 / th[q],
-                         estimate(m, S.data() + q * n) / std::fabs(th[q]));
-        double sym = 0.0, bmax = 0.0;
-        for (int j = 0; j < m; ++j)
-            for (int i = 0; i < B; ++i)
-                for (int l = 0; l < B; ++l) {
-                    sym = std::max(sym, std::fabs(hA[(size_t)j * B * B + i * B + l] - hA[(size_t)j * B * B + l * B + i]));
-                    bmax = std::max(bmax, std::fabs(hB[(size_t)(j + 1) * B * B + i * B + l]));
-                }
-        std::fprintf(stderr, "[riga]   max asym(A)=%.3e max|B|=%.3e\n", sym, bmax);
-        if (N <= 5000) {
-            // orthogonality of [locked | run] and the projection error of T
-            const int J = col0 + n;
-            std::vector<double> hV((size_t)N * J), hM((size_t)N * J);
-            cudaMemcpy(hV.data(), c->V.ptr, hV.size() * sizeof(double), cudaMemcpyDeviceToHost);
-            cudaMemcpy(hM.data(), c->MV.ptr, hM.size() * sizeof(double), cudaMemcpyDeviceToHost);
-            double orth = 0.0;
-            for (int a = 0; a < J; ++a)
-                for (int b2 = 0; b2 < J; ++b2) {
-                    double d = 0.0;
-                    for (long long i = 0; i < N; ++i) d += hV[(size_t)a * N + i] * hM[(size_t)b2 * N + i];
-                    orth = std::max(orth, std::fabs(d - (a == b2 ? 1.0 : 0.0)));
-                }
-            std::fprintf(stderr, "[riga]   basis orthogonality max|V^T M V - I| = %.3e over %d columns\n", orth, J);
-        }
-    }
     return ritz_lock(R, col0, n, Wsel, lcand, nlock, lock_tol, lam, n_locked);
 }
 

@@ -157,6 +157,8 @@ struct riga_ctx {
     int opt_block = 1;                 // Lanczos block size (1, 2, 4; 0 = automatic)
     riga::DevBuf<double> bwork, bcoef, bpartial, bsmall;  // block Lanczos workspace
     riga::DevBuf<int> bflag;
+    double* bpin = nullptr;            // pinned host copies of the block-tridiagonal T
+    size_t bpin_size = 0;
     unsigned long long opt_seed = 1;
     riga::DevBuf<double> V, MV;        // basis storage: locked vectors, then the run's vectors
     riga::DevBuf<double> coef;         // Gram-Schmidt coefficients
@@ -257,8 +259,12 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma, double tol);
 int eig_grad_device(riga_ctx* c, int k, const double* w_dev, double* ga_dev, double* gb_dev);
 // tridiag.cpp
 void tridiag_eig(int m, const double* alpha, const double* beta, double* theta, double* Z, bool vectors);
+void tridiag_eig_rows(int m, const double* alpha, const double* beta, double* theta, int zr, const double* z0,
+                      double* Zout);
 // band.cpp: symmetric band matrix (dense n x n column-major, half-bandwidth b)
 void band_eigvals(int n, int b, const double* T, double* theta);                      // ascending
+// eigenvalues and the last r rows of all eigenvectors (Zlast: r x n column-major)
+void band_eig_lastrows(int n, int b, const double* T, int r, double* theta, double* Zlast);
 void band_eigvecs(int n, int b, const double* T, int q, const double* th, double* S);  // S: n x q
 
 }  // namespace riga

@@ -17,18 +17,17 @@
 
 namespace riga {
 
-void tridiag_eig(int m, const double* alpha, const double* beta, double* theta, double* Z, bool vectors) {
+// General form: the rotations of the iteration are applied to the columns of
+// a zr x m row block z0 (column-major: entry (row, j) at z0[j * zr + row]);
+// Zout receives that block times the eigenvector matrix, columns in
+// ascending eigenvalue order.  z0 = I gives the eigenvectors, z0 = e_m^T
+// their last row.
+void tridiag_eig_rows(int m, const double* alpha, const double* beta, double* theta, int zr, const double* z0,
+                      double* Zout) {
     std::vector<double> d(alpha, alpha + m), e(m, 0.0);
     for (int i = 0; i + 1 < m; ++i) e[i] = beta[i];
-    const int zr = vectors ? m : 1;  // rows of Z carried along
-    std::vector<double> z((size_t)zr * m, 0.0);
-    if (vectors)
-        for (int i = 0; i < m; ++i) z[(size_t)i * m + i] = 1.0;  // column-major m x m
-    else
-        z[m - 1] = 1.0;  // row vector e_m^T (entry j = column j)
-    auto zat = [&](int row, int colj) -> double& {
-        return vectors ? z[(size_t)colj * m + row] : z[colj];
-    };
+    std::vector<double> z(z0, z0 + (size_t)zr * m);
+    auto zat = [&](int row, int colj) -> double& { return z[(size_t)colj * zr + row]; };
     const double eps = 2.220446049250313e-16;
     for (int l = 0; l < m; ++l) {
         int iter = 0;
@@ -81,12 +80,18 @@ void tridiag_eig(int m, const double* alpha, const double* beta, double* theta, 
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
     for (int i = 0; i < m; ++i) theta[i] = d[order[i]];
-    if (vectors) {
-        for (int i = 0; i < m; ++i)
-            for (int k = 0; k < m; ++k) Z[(size_t)i * m + k] = z[(size_t)order[i] * m + k];
-    } else {
-        for (int i = 0; i < m; ++i) Z[i] = z[order[i]];
-    }
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < zr; ++k) Zout[(size_t)i * zr + k] = z[(size_t)order[i] * zr + k];
+}
+
+void tridiag_eig(int m, const double* alpha, const double* beta, double* theta, double* Z, bool vectors) {
+    const int zr = vectors ? m : 1;
+    std::vector<double> z0((size_t)zr * m, 0.0);
+    if (vectors)
+        for (int i = 0; i < m; ++i) z0[(size_t)i * m + i] = 1.0;
+    else if (m > 0)
+        z0[m - 1] = 1.0;
+    tridiag_eig_rows(m, alpha, beta, theta, zr, z0.data(), Z);
 }
 
 }  // namespace riga

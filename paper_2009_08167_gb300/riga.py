@@ -82,7 +82,7 @@ def load_library(path=LIB_PATH):
     lib.riga_set_eig_options.argtypes = [P, I, I, I, I, ctypes.c_ulonglong]
     lib.riga_eig_grad.argtypes = [P, I, P, P, P]
     lib.riga_assemble_batch.argtypes = [P, I, ctypes.POINTER(_MeshC), P, P]
-    lib.riga_band_eig.argtypes = [I, I, P, P, I, P, P]
+    lib.riga_band_eig.argtypes = [I, I, P, P, I, P, P, I, P]
     lib.riga_set_eig_block.argtypes = [P, I]
     lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
@@ -386,20 +386,23 @@ class Riga:
         return out
 
 
-def band_eig(T, b, which=()):
+def band_eig(T, b, which=(), last_rows=0):
     """Eigenvalues (ascending) of the symmetric band matrix T (half-bandwidth
-    b) and the eigenvectors of the eigenvalues with indices `which`; host
-    only."""
+    b), the eigenvectors of the eigenvalues with indices `which`, and (when
+    last_rows > 0) the last rows of all eigenvectors; host only."""
     lib = load_library()
     T = np.asfortranarray(T, dtype=np.float64)
     n = T.shape[0]
     theta = np.zeros(n)
     wh = np.ascontiguousarray(which, dtype=np.int32)
     S = np.zeros((n, max(1, wh.size)), order="F")
+    Z = np.zeros((max(1, last_rows), n), order="F")
     rc = lib.riga_band_eig(n, int(b), _ptr(T), _ptr(theta), int(wh.size), _ptr(wh) if wh.size else None,
-                           _ptr(S) if wh.size else None)
+                           _ptr(S) if wh.size else None, int(last_rows), _ptr(Z) if last_rows else None)
     if rc != RIGA_OK:
         raise RigaError(rc, lib.riga_strerror(rc).decode())
+    if last_rows:
+        return theta, S[:, :wh.size], Z
     return theta, S[:, :wh.size]
 
 

@@ -60,3 +60,15 @@ def test_band_eig_multiplicity():
     assert np.max(np.abs(theta - ref)) <= 1e-12 * scale
     assert np.max(np.abs(T @ S - S * theta)) <= 1e-11 * scale
     assert np.max(np.abs(S.T @ S - np.eye(n))) <= 1e-10
+
+
+@pytest.mark.parametrize("n,b", [(30, 2), (97, 4), (160, 4)])
+def test_band_eig_last_rows(n, b):
+    T = _band(n, b, 77 + n)
+    theta, _, Z = riga.band_eig(T, b, (), last_rows=b)
+    lam, V = np.linalg.eigh(T)
+    assert np.max(np.abs(theta - lam)) <= 1e-12 * np.abs(lam).max()
+    # eigenvectors are determined up to sign (the spectrum is simple here)
+    ref = V[n - b:, :]
+    sgn = np.sign(np.sum(ref * Z, axis=0))
+    assert np.max(np.abs(Z - ref * sgn)) <= 1e-10
