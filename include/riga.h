@@ -132,9 +132,10 @@ int riga_factor(riga_ctx* ctx, double sigma, int precision, long long* n_neg);
 /*
  * riga_solve: x = (K - sigma M)^{-1} b for nrhs right-hand sides (columns of
  * length N, x-fastest numbering) with the last factorization: forward
- * elimination, D^{-1}, backward elimination over the assembly tree.  Up to
- * four columns share one traversal of the tree (each operator panel read
- * once for all of them); the result of a column does not depend on how the
+ * elimination, D^{-1}, backward elimination over the assembly tree.  Several
+ * columns share one launch (up to 8 as independent interleaved traversals,
+ * or, for batches of many problems, up to 4 per work item sharing each
+ * operator panel read); the result of a column does not depend on how the
  * columns are grouped.  With an
  * FP32 factor (or tol > 0) the FP64 residual b - (K - sigma M) x drives
  * iterative refinement until ||r||_2 <= tol ||b||_2 (tol <= 0 with an FP32
@@ -255,8 +256,8 @@ int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int
  * the M-inner product) and M-orthonormalises it (Cholesky QR, twice); the
  * Rayleigh-Ritz step uses the block-tridiagonal T_m (riga_band_eig).
  * Eigenvalues of multiplicity up to the block size appear in one run.  0
- * selects 4.  When the factor cannot carry that many right-hand sides (fronts
- * larger than 1536), the size falls back to what it can (possibly 1).
+ * selects 4.  When a batch's solve kernel cannot carry that many right-hand
+ * sides per item, the size falls back to what it can (possibly 1).
  * Errors: RIGA_EINVAL.
  */
 int riga_set_eig_block(riga_ctx* ctx, int block);

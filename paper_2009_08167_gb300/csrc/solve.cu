@@ -43,6 +43,9 @@ struct TreeArgs {
     const SolveItem* items;  // forward parts (ascending height), then backward parts
     const ChildRec* crec;    // children records (see Symbolic::crec)
     int n_items, n_fwd;
+    int nsplit;        // independent groups of NR right-hand sides, items interleaved
+    int n_fronts;      // stride of the per-group completion counters
+    long long upd_size;  // stride (per right-hand side) of the update vectors
     int chunk_elems;   // elements per shared-memory chunk buffer (two buffers)
     int max_n;
     double* upd;
@@ -190,8 +193,14 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
         __syncthreads();
-        const int item = s_item;
-        if (item >= a.n_items) return;
+        const int claimed = s_item;
+        if (claimed >= a.n_items * a.nsplit) return;
+        const int item = claimed / a.nsplit, grp = claimed - item * a.nsplit;
+        double* const y = a.y + (long long)grp * NR * a.ldy;
+        double* const w1 = a.w1 + (long long)grp * NR * a.ldy;
+        double* const upd = a.upd + (long long)grp * NR * a.upd_size;
+        int* const done_f = a.done_f + (long long)grp * a.n_fronts;
+        int* const done_b = a.done_b + (long long)grp * a.n_fronts;
         const SolveItem it = a.items[item];
         const bool fwd = item < a.n_fwd;
         const int F = it.front, k = it.k, n = it.n, b0 = it.b0, m = n - k;
@@ -205,8 +214,8 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         const int issued = min(2, nchunks);
         if (tid == 0) {
             if (a.trace) {
-                a.trace[4 * item] = sm_id();
-                a.trace[4 * item + 1] = global_ns();
+                a.trace[4 * claimed] = sm_id();
+                a.trace[4 * claimed + 1] = global_ns();
             }
             for (int c = 0; c < issued; ++c) {
                 const int ua = c * upc, un = min(upc, units - ua);
@@ -216,15 +225,15 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
             if (fwd) {
                 for (int ci = it.c0; ci < it.c1 && ok; ++ci) {
                     const ChildRec cr = a.crec[ci];
-                    ok = wait_count(&a.done_f[cr.child], cr.parts, a.err, a.spin_limit);
+                    ok = wait_count(&done_f[cr.child], cr.parts, a.err, a.spin_limit);
                 }
             } else {
-                ok = wait_count(&a.done_f[F], it.wait_parts, a.err, a.spin_limit);
-                if (ok && it.parent >= 0) ok = wait_count(&a.done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
+                ok = wait_count(&done_f[F], it.wait_parts, a.err, a.spin_limit);
+                if (ok && it.parent >= 0) ok = wait_count(&done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
             }
             __threadfence();
             s_ok = ok;
-            if (a.trace) a.trace[4 * item + 2] = global_ns();
+            if (a.trace) a.trace[4 * claimed + 2] = global_ns();
         }
         __syncthreads();
         if (!s_ok) {
@@ -235,33 +244,27 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         }
         if (fwd) {
             // w = [b(own); 0] + children's update vectors
-            for (int t = tid; t < NR * n; t += NT) {
-                const int r = t / n, i = t - r * n;
-                w[r * ldw + i] = (i < k) ? (T)__ldcg(&a.y[(long long)r * a.ldy + b0 + i]) : T(0);
-            }
+            for (int r = 0; r < NR; ++r)
+                for (int i = tid; i < n; i += NT)
+                    w[r * ldw + i] = (i < k) ? (T)__ldcg(&y[(long long)r * a.ldy + b0 + i]) : T(0);
             __syncthreads();
             for (int ci = it.c0; ci < it.c1; ++ci) {
                 const ChildRec cr = a.crec[ci];
                 const int* rl = a.rel + cr.rel_off;
-                const double* u = a.upd + cr.upd_off * NR;
-                for (int t = tid; t < NR * cr.m; t += NT) {
-                    const int r = t / cr.m, i = t - r * cr.m;
-                    w[r * ldw + rl[i]] += (T)__ldcg(&u[(long long)r * cr.m + i]);
-                }
+                const double* u = upd + cr.upd_off * NR;
+                for (int r = 0; r < NR; ++r)
+                    for (int i = tid; i < cr.m; i += NT) w[r * ldw + rl[i]] += (T)__ldcg(&u[(long long)r * cr.m + i]);
                 __syncthreads();
             }
             if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
-                for (int t = tid; t < NR * k; t += NT) {
-                    const int r = t / k, i = t - r * k;
-                    a.w1[(long long)r * a.ldy + b0 + i] = (double)w[r * ldw + i];
-                }
+                for (int r = 0; r < NR; ++r)
+                    for (int i = tid; i < k; i += NT) w1[(long long)r * a.ldy + b0 + i] = (double)w[r * ldw + i];
         } else {
             const int* idx = a.front_pos + it.fpos;
-            for (int t = tid; t < NR * n; t += NT) {
-                const int r = t / n, i = t - r * n;
-                w[r * ldw + i] = (i < k) ? -(T)__ldcg(&a.w1[(long long)r * a.ldy + b0 + i])
-                                         : (T)__ldcg(&a.y[(long long)r * a.ldy + idx[i]]);
-            }
+            for (int r = 0; r < NR; ++r)
+                for (int i = tid; i < n; i += NT)
+                    w[r * ldw + i] = (i < k) ? -(T)__ldcg(&w1[(long long)r * a.ldy + b0 + i])
+                                             : (T)__ldcg(&y[(long long)r * a.ldy + idx[i]]);
         }
         __syncthreads();
         // thread layout: outputs l (columns or rows of the part) x unit groups g;
@@ -346,9 +349,9 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
                         if (q2 < na && l < cnt) {
 #pragma unroll
                             for (int r = 0; r < NR; ++r) {
-                                if (fwd) a.upd[it.upd_off * NR + (long long)r * m + lo + l - k] =
+                                if (fwd) upd[it.upd_off * NR + (long long)r * m + lo + l - k] =
                                              (double)(w[r * ldw + lo + l] + acc[q2][r]);
-                                else a.y[(long long)r * a.ldy + b0 + lo + l] = (double)acc[q2][r];
+                                else y[(long long)r * a.ldy + b0 + lo + l] = (double)acc[q2][r];
                             }
                         }
                     }
@@ -358,8 +361,8 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         }
         if (tid == 0) {
             __threadfence();
-            atomicAdd(fwd ? &a.done_f[F] : &a.done_b[F], 1);
-            if (a.trace) a.trace[4 * item + 3] = global_ns();
+            atomicAdd(fwd ? &done_f[F] : &done_b[F], 1);
+            if (a.trace) a.trace[4 * claimed + 3] = global_ns();
         }
     }
 }
@@ -429,8 +432,15 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1);
-        item = __shfl_sync(FULL, item, 0);
-        if (item >= a.n_items) return;
+        const int claimed = __shfl_sync(FULL, item, 0);
+        if (claimed >= a.n_items * a.nsplit) return;
+        item = claimed / a.nsplit;
+        const int grp = claimed - item * a.nsplit;
+        double* const y = a.y + (long long)grp * NR * a.ldy;
+        double* const w1 = a.w1 + (long long)grp * NR * a.ldy;
+        double* const upd = a.upd + (long long)grp * NR * a.upd_size;
+        int* const done_f = a.done_f + (long long)grp * a.n_fronts;
+        int* const done_b = a.done_b + (long long)grp * a.n_fronts;
         const SolveItem it = a.items[item];
         const bool fwd = item < a.n_fwd;
         const int F = it.front, k = it.k, n = it.n, b0 = it.b0, m = n - k;
@@ -439,8 +449,8 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
         const int units = fwd ? k : n;  // rows (forward) or columns (backward) of the panel
         if (lane == 0) {
             if (a.trace) {
-                a.trace[4 * item] = sm_id();
-                a.trace[4 * item + 1] = global_ns();
+                a.trace[4 * claimed] = sm_id();
+                a.trace[4 * claimed + 1] = global_ns();
             }
             if (cnt > 0 && units > 0) bulk_prefetch_l2(q, (unsigned)((long long)units * ldp * sizeof(T)));
         }
@@ -451,44 +461,38 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
         if (fwd) {
             for (int ci = it.c0 + lane; ci < it.c1; ci += 32) {
                 const ChildRec cr = a.crec[ci];
-                ok = ok && wait_count(&a.done_f[cr.child], cr.parts, a.err, a.spin_limit);
+                ok = ok && wait_count(&done_f[cr.child], cr.parts, a.err, a.spin_limit);
             }
         } else if (lane == 0) {
-            ok = wait_count(&a.done_f[F], it.wait_parts, a.err, a.spin_limit);
-            if (ok && it.parent >= 0) ok = wait_count(&a.done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
+            ok = wait_count(&done_f[F], it.wait_parts, a.err, a.spin_limit);
+            if (ok && it.parent >= 0) ok = wait_count(&done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
         }
         if (!__all_sync(FULL, ok)) return;
         __threadfence();
-        if (a.trace && lane == 0) a.trace[4 * item + 2] = global_ns();
+        if (a.trace && lane == 0) a.trace[4 * claimed + 2] = global_ns();
         if (fwd) {
             // w = [b(own); 0] + children's update vectors
-            for (int t = lane; t < NR * n; t += 32) {
-                const int r = t / n, i = t - r * n;
-                w[r * ldw + i] = (i < k) ? (T)__ldcg(&a.y[(long long)r * a.ldy + b0 + i]) : T(0);
-            }
+            for (int r = 0; r < NR; ++r)
+                for (int i = lane; i < n; i += 32)
+                    w[r * ldw + i] = (i < k) ? (T)__ldcg(&y[(long long)r * a.ldy + b0 + i]) : T(0);
             __syncwarp();
             for (int ci = it.c0; ci < it.c1; ++ci) {
                 const ChildRec cr = a.crec[ci];
                 const int* rl = a.rel + cr.rel_off;
-                const double* u = a.upd + cr.upd_off * NR;
-                for (int t = lane; t < NR * cr.m; t += 32) {
-                    const int r = t / cr.m, i = t - r * cr.m;
-                    w[r * ldw + rl[i]] += (T)__ldcg(&u[(long long)r * cr.m + i]);
-                }
+                const double* u = upd + cr.upd_off * NR;
+                for (int r = 0; r < NR; ++r)
+                    for (int i = lane; i < cr.m; i += 32) w[r * ldw + rl[i]] += (T)__ldcg(&u[(long long)r * cr.m + i]);
                 __syncwarp();
             }
             if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
-                for (int t = lane; t < NR * k; t += 32) {
-                    const int r = t / k, i = t - r * k;
-                    a.w1[(long long)r * a.ldy + b0 + i] = (double)w[r * ldw + i];
-                }
+                for (int r = 0; r < NR; ++r)
+                    for (int i = lane; i < k; i += 32) w1[(long long)r * a.ldy + b0 + i] = (double)w[r * ldw + i];
         } else {
             const int* idx = a.front_pos + it.fpos;
-            for (int t = lane; t < NR * n; t += 32) {
-                const int r = t / n, i = t - r * n;
-                w[r * ldw + i] = (i < k) ? -(T)__ldcg(&a.w1[(long long)r * a.ldy + b0 + i])
-                                         : (T)__ldcg(&a.y[(long long)r * a.ldy + idx[i]]);
-            }
+            for (int r = 0; r < NR; ++r)
+                for (int i = lane; i < n; i += 32)
+                    w[r * ldw + i] = (i < k) ? -(T)__ldcg(&w1[(long long)r * a.ldy + b0 + i])
+                                             : (T)__ldcg(&y[(long long)r * a.ldy + idx[i]]);
         }
         __syncwarp();
         // lanes: outputs li (cp per unit group) x unit groups g (G = 32 / cp)
@@ -517,9 +521,9 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
                     if (q2 < na && l < cnt) {
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
-                            if (fwd) a.upd[it.upd_off * NR + (long long)r * m + lo + l - k] =
+                            if (fwd) upd[it.upd_off * NR + (long long)r * m + lo + l - k] =
                                          (double)(w[r * ldw + lo + l] + acc[q2][r]);
-                            else a.y[(long long)r * a.ldy + b0 + lo + l] = (double)acc[q2][r];
+                            else y[(long long)r * a.ldy + b0 + lo + l] = (double)acc[q2][r];
                         }
                     }
                 }
@@ -528,8 +532,8 @@ __global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restric
         __syncwarp();
         if (lane == 0) {
             __threadfence();
-            atomicAdd(fwd ? &a.done_f[F] : &a.done_b[F], 1);
-            if (a.trace) a.trace[4 * item + 3] = global_ns();
+            atomicAdd(fwd ? &done_f[F] : &done_b[F], 1);
+            if (a.trace) a.trace[4 * claimed + 3] = global_ns();
         }
         __syncwarp();
     }
@@ -641,7 +645,7 @@ static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out,
 
 int solve_max_rhs(riga_ctx* c) {
     const Symbolic& S = c->S;
-    if (S.solve_mode == SOLVE_CTA256) return 1;
+    if (S.solve_mode != SOLVE_WARP) return 4;  // interleaved groups: any count, up to 8 per launch
     int maxopt = 0;
     if (cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return 1;
     const size_t elem = sizeof(double);  // the larger of the two front precisions
@@ -654,13 +658,13 @@ int solve_max_rhs(riga_ctx* c) {
 }
 
 template <typename T, int NR>
-static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
+static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
     // and the vectors read and written in each sweep
     PhaseScope scope(c, PH_SOLVE,
-                     (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * NR * (double)S.N * sizeof(double));
+                     (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * NR * nsplit * (double)S.N * sizeof(double));
     int max_n = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
     const int n_items = (int)S.sitems.size();
@@ -678,8 +682,9 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
     const int per_block = warp ? 4 : 1;  // concurrent items per block
-    const int grid = std::max(1, std::min((n_items + per_block - 1) / per_block, std::max(1, per_sm) * nsm));
-    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, (2 * (size_t)S.n_nodes + 1) * sizeof(int), st));
+    const long long work = (long long)n_items * nsplit;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((work + per_block - 1) / per_block, std::max(1, per_sm) * nsm));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, (2 * (size_t)S.n_nodes * nsplit + 1) * sizeof(int), st));
     TreeArgs a;
     a.node_ptr = c->node_ptr.ptr;
     a.kk = c->kk.ptr;
@@ -704,9 +709,12 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     a.y = y;
     a.ldy = S.N;
     a.w1 = c->w1buf.ptr;
+    a.nsplit = nsplit;
+    a.n_fronts = S.n_nodes;
+    a.upd_size = S.upd_size;
     a.done_f = c->solve_flags.ptr;
-    a.done_b = c->solve_flags.ptr + S.n_nodes;
-    a.counter = c->solve_flags.ptr + 2 * S.n_nodes;
+    a.done_b = c->solve_flags.ptr + (size_t)S.n_nodes * nsplit;
+    a.counter = c->solve_flags.ptr + 2 * (size_t)S.n_nodes * nsplit;
     a.err = c->flag.ptr;
     a.spin_limit = c->wait_limit;
     a.trace = c->trace_buf;
@@ -714,32 +722,45 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y) {
     return RIGA_OK;
 }
 
-// y := A^{-1} y for nrhs columns (stride N) in groups of the largest
-// supported width (4, 2, 1 right-hand sides per tree traversal)
+// y := A^{-1} y for nrhs columns (stride N).  Trees with a critical path
+// (one or few problems): the columns run as independent groups of one
+// right-hand side interleaved in one launch (up to 8), so that each item
+// stays short and the groups share the panels in L2.  Batches of many trees
+// (bound by items in flight): up to four columns share each item and each
+// panel read.
 int enqueue_solve(riga_ctx* c, double* y, int nrhs) {
     if (!c->factored) return set_error(c, RIGA_ESTATE, "no factorization");
     Symbolic& S = c->S;
-    const int maxr = solve_max_rhs(c);
-    const int width = std::min(std::max(1, nrhs), maxr);
+    const bool split = S.solve_mode != SOLVE_WARP;
+    const int maxr = split ? 1 : solve_max_rhs(c);
+    const int width = split ? std::min(std::max(1, nrhs), 8) : std::min(std::max(1, nrhs), maxr);
     RIGA_CUDA_TRY(c, c->upd.alloc((S.upd_size > 0 ? S.upd_size : 1) * (size_t)width));
-    RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes + 1));
+    RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes * width + 1));
     RIGA_CUDA_TRY(c, c->w1buf.alloc((size_t)S.N * width));
     for (int c0 = 0; c0 < nrhs;) {
         const int left = nrhs - c0;
-        const int nr = left >= 4 && maxr >= 4 ? 4 : (left >= 2 && maxr >= 2 ? 2 : 1);
         double* yc = y + (long long)c0 * S.N;
-        int rc;
-        if (c->precision == RIGA_FP64) {
-            rc = nr == 4 ? enqueue_solve_t<double, 4>(c, c->q64.ptr, yc)
-                         : (nr == 2 ? enqueue_solve_t<double, 2>(c, c->q64.ptr, yc) : enqueue_solve_t<double, 1>(c, c->q64.ptr, yc));
+        int rc, used;
+        if (split) {
+            used = std::min(left, 8);
+            rc = c->precision == RIGA_FP64 ? enqueue_solve_t<double, 1>(c, c->q64.ptr, yc, used)
+                                           : enqueue_solve_t<float, 1>(c, c->q32.ptr, yc, used);
         } else {
-            rc = nr == 4 ? enqueue_solve_t<float, 4>(c, c->q32.ptr, yc)
-                         : (nr == 2 ? enqueue_solve_t<float, 2>(c, c->q32.ptr, yc) : enqueue_solve_t<float, 1>(c, c->q32.ptr, yc));
+            used = left >= 4 && maxr >= 4 ? 4 : (left >= 2 && maxr >= 2 ? 2 : 1);
+            if (c->precision == RIGA_FP64) {
+                rc = used == 4 ? enqueue_solve_t<double, 4>(c, c->q64.ptr, yc, 1)
+                               : (used == 2 ? enqueue_solve_t<double, 2>(c, c->q64.ptr, yc, 1)
+                                            : enqueue_solve_t<double, 1>(c, c->q64.ptr, yc, 1));
+            } else {
+                rc = used == 4 ? enqueue_solve_t<float, 4>(c, c->q32.ptr, yc, 1)
+                               : (used == 2 ? enqueue_solve_t<float, 2>(c, c->q32.ptr, yc, 1)
+                                            : enqueue_solve_t<float, 1>(c, c->q32.ptr, yc, 1));
+            }
         }
         if (rc) return rc;
         RIGA_CUDA_TRY(c, cudaGetLastError());
-        c->stats.n_solve += nr;
-        c0 += nr;
+        c->stats.n_solve += used;
+        c0 += used;
     }
     return RIGA_OK;
 }
