@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c4"],
                     help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, "
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
-    ap.add_argument("--block", type=int, default=1, choices=[0, 1, 2, 4],
+    ap.add_argument("--block", type=int, default=2, choices=[0, 1, 2, 4],
                     help="Lanczos block size (riga_set_eig_block; 0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")

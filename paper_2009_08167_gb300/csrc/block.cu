@@ -163,104 +163,90 @@ __global__ void __launch_bounds__(256) bupdate_kernel(const double* __restrict__
     for (int r = 0; r < B; ++r) W[r * N + row] = v[r];
 }
 
+// Grid-wide sum of the blocks' CNT-value partials without another launch:
+// every block stores its partial, and the last block to arrive (counted on
+// `counter`, which it resets) adds them in a fixed order (deterministic).
+template <int CNT>
+__device__ void tail_reduce(const double* __restrict__ mine, double* __restrict__ partial, int* __restrict__ counter,
+                            double* __restrict__ out) {
+    __shared__ int s_last;
+    __shared__ double sh[256];
+    if ((int)threadIdx.x < CNT) partial[(long long)blockIdx.x * CNT + threadIdx.x] = mine[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int groups = blockDim.x / CNT;  // thread t sums entry t % CNT over blocks t / CNT, t / CNT + groups, ...
+    const int e = threadIdx.x % CNT, g = threadIdx.x / CNT;
+    double acc = 0.0;
+    if (g < groups)
+#pragma unroll 8
+        for (int i = g; i < (int)gridDim.x; i += groups) acc += __ldcg(&partial[(long long)i * CNT + e]);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < CNT) {
+        double t = 0.0;
+        for (int q = 0; q < groups; ++q) t += sh[q * CNT + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0;
+}
+
 // MW = M W (16 lanes per row, every value of M serving B products) and the
-// block's partial Gram matrix W^T M W (row-major B x B)
+// Gram matrix G = W^T M W (row-major B x B, reduced by the last block)
 template <int B>
 __global__ void __launch_bounds__(256) bspmv_gram_kernel(long long N, const long long* __restrict__ rowptr,
                                                          const int* __restrict__ col, const double* __restrict__ Mv,
                                                          const double* __restrict__ W, double* __restrict__ MW,
-                                                         double* __restrict__ partial) {
+                                                         double* __restrict__ partial, int* __restrict__ counter,
+                                                         double* __restrict__ G) {
     __shared__ double red[16][B * B];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long row = t / 16;
-    const int lane = (int)(t % 16), grp = threadIdx.x / 16;
-    double s[B];
+    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    double gacc[B * B];  // lane 0 of each row group: this group's Gram contributions
 #pragma unroll
-    for (int r = 0; r < B; ++r) s[r] = 0.0;
-    if (row < N)
-        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) {
-            const double mv = Mv[e];
-            const int cc = col[e];
+    for (int e = 0; e < B * B; ++e) gacc[e] = 0.0;
+    // grid-stride over groups of 16 rows, so that few blocks hold partials
+    for (long long base = (long long)blockIdx.x * 16; base < N; base += (long long)gridDim.x * 16) {
+        const long long row = base + grp;
+        double s[B];
 #pragma unroll
-            for (int r = 0; r < B; ++r) s[r] += mv * W[r * N + cc];
-        }
+        for (int r = 0; r < B; ++r) s[r] = 0.0;
+        if (row < N)
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) {
+                const double mv = Mv[e];
+                const int cc = col[e];
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
+                for (int r = 0; r < B; ++r) s[r] += mv * W[r * N + cc];
+            }
 #pragma unroll
-        for (int r = 0; r < B; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o, 16);
-    if (lane == 0) {
-        if (row < N) {
+        for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+            for (int r = 0; r < B; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o, 16);
+        if (lane == 0 && row < N) {
 #pragma unroll
             for (int r = 0; r < B; ++r) MW[r * N + row] = s[r];
 #pragma unroll
             for (int q = 0; q < B; ++q) {
                 const double wq = W[q * N + row];
 #pragma unroll
-                for (int r = 0; r < B; ++r) red[grp][q * B + r] = wq * s[r];
+                for (int r = 0; r < B; ++r) gacc[q * B + r] += wq * s[r];
             }
-        } else {
-#pragma unroll
-            for (int e = 0; e < B * B; ++e) red[grp][e] = 0.0;
         }
     }
+    if (lane == 0)
+#pragma unroll
+        for (int e = 0; e < B * B; ++e) red[grp][e] = gacc[e];
     __syncthreads();
+    __shared__ double tot[B * B];
     if (threadIdx.x < B * B) {
-        double tot = 0.0;
-        for (int g = 0; g < 16; ++g) tot += red[g][threadIdx.x];
-        partial[(long long)blockIdx.x * B * B + threadIdx.x] = tot;
+        double t2 = 0.0;
+        for (int g = 0; g < 16; ++g) t2 += red[g][threadIdx.x];
+        tot[threadIdx.x] = t2;
     }
-}
-
-// partial Gram matrix V^T (M V) of B columns with their stored M-products
-template <int B>
-__global__ void __launch_bounds__(256) bgram_kernel(long long N, const double* __restrict__ V, long long ld,
-                                                    const double* __restrict__ MV, double* __restrict__ partial) {
-    __shared__ double red[8][B * B];
-    double g[B * B];
-#pragma unroll
-    for (int e = 0; e < B * B; ++e) g[e] = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        double v[B], m[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) {
-            v[r] = V[r * ld + i];
-            m[r] = MV[r * ld + i];
-        }
-#pragma unroll
-        for (int q = 0; q < B; ++q)
-#pragma unroll
-            for (int r = 0; r < B; ++r) g[q * B + r] += v[q] * m[r];
-    }
-#pragma unroll
-    for (int e = 0; e < B * B; ++e)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g[e] += __shfl_xor_sync(0xffffffffu, g[e], o);
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int e = 0; e < B * B; ++e) red[threadIdx.x >> 5][e] = g[e];
     __syncthreads();
-    if (threadIdx.x < B * B) {
-        double tot = 0.0;
-        for (int w = 0; w < 8; ++w) tot += red[w][threadIdx.x];
-        partial[(long long)blockIdx.x * B * B + threadIdx.x] = tot;
-    }
-}
-
-// out[e] = sum over nb partial blocks of partial[i * count + e] (fixed
-// order), one block per entry e
-__global__ void __launch_bounds__(256) bsum_small_kernel(const double* __restrict__ partial, int nb, int count,
-                                                         double* __restrict__ out) {
-    __shared__ double sh[256];
-    const int e = blockIdx.x;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[(long long)i * count + e];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[e] = sh[0];
+    tail_reduce<B * B>(tot, partial, counter, G);
 }
 
 // Cholesky G + s I = R^T R of the symmetrised B x B Gram matrix,
@@ -311,16 +297,20 @@ __device__ bool bcholesky(const double* __restrict__ G, double shift_rel, double
 
 // One QR pass: every block factors the small Gram matrix itself (no separate
 // launch), then X[:, l] = sum_{i <= l} Y[:, i] R^{-1}[i][l] for Y = W (into V)
-// and Y = M W (into M V), in place when the output aliases the input.  Block
-// 0 records R (Rout), the accumulated factor Bout = R Rprev, and a breakdown
-// (flag bit 0).
+// and Y = M W (into M V), in place when the output aliases the input, and
+// (when Gnext is given) the Gram matrix of the new columns for the next pass.
+// Block 0 records R (Rout), the accumulated factor Bout = R Rprev, and a
+// breakdown (flag bit 0).
 template <int B>
 __global__ void __launch_bounds__(256) bqr_scale_kernel(long long N, const double* __restrict__ G, double shift_rel,
                                                         const double* __restrict__ Rprev, double* __restrict__ Bout,
                                                         double* __restrict__ Rout, int* __restrict__ flag,
                                                         const double* W, long long ldw, const double* MW, double* V,
-                                                        double* MV, long long ldv) {
+                                                        double* MV, long long ldv, double* __restrict__ partial,
+                                                        int* __restrict__ counter, double* __restrict__ Gnext) {
     __shared__ double sri[B * B];
+    __shared__ double red[8][B * B];
+    __shared__ double tot[B * B];
     if (threadIdx.x == 0) {
         double R[B][B], Ri[B][B];
         const bool bad = bcholesky<B>(G, shift_rel, R, Ri);
@@ -342,24 +332,51 @@ __global__ void __launch_bounds__(256) bqr_scale_kernel(long long N, const doubl
     }
     __syncthreads();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double w[B], mw[B];
+    double v[B], mv[B];
 #pragma unroll
-    for (int r = 0; r < B; ++r) {
-        w[r] = W[r * ldw + i];
-        mw[r] = MW[r * ldw + i];
-    }
+    for (int l = 0; l < B; ++l) v[l] = mv[l] = 0.0;
+    if (i < N) {
+        double w[B], mw[B];
 #pragma unroll
-    for (int l = 0; l < B; ++l) {
-        double a = 0.0, b = 0.0;
-#pragma unroll
-        for (int r = 0; r <= l; ++r) {
-            a += w[r] * sri[r * B + l];
-            b += mw[r] * sri[r * B + l];
+        for (int r = 0; r < B; ++r) {
+            w[r] = W[r * ldw + i];
+            mw[r] = MW[r * ldw + i];
         }
-        V[l * ldv + i] = a;
-        MV[l * ldv + i] = b;
+#pragma unroll
+        for (int l = 0; l < B; ++l) {
+            double a = 0.0, b = 0.0;
+#pragma unroll
+            for (int r = 0; r <= l; ++r) {
+                a += w[r] * sri[r * B + l];
+                b += mw[r] * sri[r * B + l];
+            }
+            v[l] = a;
+            mv[l] = b;
+            V[l * ldv + i] = a;
+            MV[l * ldv + i] = b;
+        }
     }
+    if (!Gnext) return;
+    double g[B * B];
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+#pragma unroll
+        for (int r = 0; r < B; ++r) g[q * B + r] = v[q] * mv[r];
+#pragma unroll
+    for (int e = 0; e < B * B; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g[e] += __shfl_xor_sync(0xffffffffu, g[e], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int e = 0; e < B * B; ++e) red[threadIdx.x >> 5][e] = g[e];
+    __syncthreads();
+    if (threadIdx.x < B * B) {
+        double t2 = 0.0;
+        for (int w2 = 0; w2 < 8; ++w2) t2 += red[w2][threadIdx.x];
+        tot[threadIdx.x] = t2;
+    }
+    __syncthreads();
+    tail_reduce<B * B>(tot, partial, counter, Gnext);
 }
 
 // A_j[i][r] = C1[(cs + i) B + r] + C2[(cs + i) B + r]
@@ -419,28 +436,26 @@ int bnormalize_t(BlockWork& K, int col, double* Bout) {
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)K.N * 8.0 * 10.0 * B);
     const unsigned nbs = (unsigned)((K.N * 16 + 255) / 256);
-    double* G = K.small;
-    double* R1 = G + B * B;
+    double* G0 = K.small;
+    double* G1 = G0 + B * B;
+    double* R1 = G1 + B * B;
     double* R2 = R1 + B * B;
     double* V = c->V.ptr + (long long)col * K.ld;
     double* MV = c->MV.ptr + (long long)col * K.ld;
     const unsigned gb = (unsigned)((K.N + 255) / 256);
     const double shift = 11.0 * ((double)K.N * B + (double)B * (B + 1)) * 1.1102230246251565e-16;
-    { count_launch(c); bspmv_gram_kernel<B><<<nbs, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW, K.part); }
+    int* counter = K.flag + 1;
+    const unsigned nbg = std::min<unsigned>(nbs, 1216);  // 8 blocks per SM
+    { count_launch(c); bspmv_gram_kernel<B><<<nbg, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW,
+                                                               K.part, counter, G0); }
     c->stats.n_matvec += B;
-    { count_launch(c); bsum_small_kernel<<<B * B, 256, 0, st>>>(K.part, (int)nbs, B * B, G); }
-    { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G, shift, nullptr, nullptr, R1, K.flag, K.W, K.N,
-                                                              K.MW, V, MV, K.ld); }
-    for (int pass = 0; pass < 2; ++pass) {
-        // the Gram matrix of the new columns; the pass's factor accumulates
-        // into R2 = R R1, then Bout = R R2
-        { count_launch(c); bgram_kernel<B><<<304, 256, 0, st>>>(K.N, V, K.ld, MV, K.part); }
-        { count_launch(c); bsum_small_kernel<<<B * B, 256, 0, st>>>(K.part, 304, B * B, G); }
-        double* acc = pass == 0 ? R2 : Bout;
-        const double* prev = pass == 0 ? R1 : R2;
-        { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G, 0.0, prev, acc, nullptr, K.flag, V, K.ld, MV,
-                                                                  V, MV, K.ld); }
-    }
+    // shifted pass (W -> V, Gram of V into G1), then two plain passes in place
+    { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G0, shift, nullptr, nullptr, R1, K.flag, K.W, K.N,
+                                                              K.MW, V, MV, K.ld, K.part, counter, G1); }
+    { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G1, 0.0, R1, R2, nullptr, K.flag, V, K.ld, MV, V, MV,
+                                                              K.ld, K.part, counter, G0); }
+    { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G0, 0.0, R2, Bout, nullptr, K.flag, V, K.ld, MV, V,
+                                                              MV, K.ld, nullptr, nullptr, nullptr); }
     return RIGA_OK;
 }
 
@@ -500,7 +515,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
     RIGA_CUDA_TRY(c, c->bpartial.alloc(part_n));
     RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)4 * B * B + nAB));
-    RIGA_CUDA_TRY(c, c->bflag.alloc(1));
+    RIGA_CUDA_TRY(c, c->bflag.alloc(2));
     if (c->bpin_size < nAB + 2) {
         if (c->bpin) cudaFreeHost(c->bpin);
         c->bpin = nullptr;
@@ -532,7 +547,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)((size_t)K.cap * B * sizeof(double))));
     }
-    RIGA_CUDA_TRY(c, cudaMemsetAsync(K.flag, 0, sizeof(int), st));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(K.flag, 0, 2 * sizeof(int), st));  // breakdown flag, reduction counter
 
     // start block: B random vectors, M-orthogonal to the locked ones
     std::vector<double> hv((size_t)N * B);
