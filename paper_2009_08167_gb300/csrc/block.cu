@@ -467,6 +467,99 @@ int bnormalize(BlockWork& K, int col, double* Bout) {
     return K.B == 4 ? bnormalize_t<4>(K, col, Bout) : bnormalize_t<2>(K, col, Bout);
 }
 
+// Eigen-decomposition of a small symmetric c x c matrix (cyclic Jacobi):
+// eigenvalues ascending in ev, eigenvectors as the columns of U (c x c,
+// column-major).
+void jacobi_small(int c, std::vector<double> A, std::vector<double>& ev, std::vector<double>& U) {
+    U.assign((size_t)c * c, 0.0);
+    for (int i = 0; i < c; ++i) U[(size_t)i * c + i] = 1.0;
+    auto a = [&](int i, int j) -> double& { return A[(size_t)j * c + i]; };
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < c; ++i)
+            for (int j = 0; j < c; ++j) {
+                tot += a(i, j) * a(i, j);
+                if (i != j) off += a(i, j) * a(i, j);
+            }
+        if (off <= 1e-32 * tot || off == 0.0) break;
+        for (int p = 0; p < c; ++p)
+            for (int q = p + 1; q < c; ++q) {
+                if (a(p, q) == 0.0) continue;
+                const double tau = (a(q, q) - a(p, p)) / (2.0 * a(p, q));
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+                for (int k = 0; k < c; ++k) {  // A <- J^T A J
+                    const double akp = a(k, p), akq = a(k, q);
+                    a(k, p) = cs * akp - sn * akq;
+                    a(k, q) = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < c; ++k) {
+                    const double apk = a(p, k), aqk = a(q, k);
+                    a(p, k) = cs * apk - sn * aqk;
+                    a(q, k) = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < c; ++k) {
+                    const double ukp = U[(size_t)p * c + k], ukq = U[(size_t)q * c + k];
+                    U[(size_t)p * c + k] = cs * ukp - sn * ukq;
+                    U[(size_t)q * c + k] = sn * ukp + cs * ukq;
+                }
+            }
+    }
+    std::vector<int> ord(c);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return a(x, x) < a(y, y); });
+    std::vector<double> U2((size_t)c * c);
+    ev.assign(c, 0.0);
+    for (int i = 0; i < c; ++i) {
+        ev[i] = a(ord[i], ord[i]);
+        for (int k = 0; k < c; ++k) U2[(size_t)i * c + k] = U[(size_t)ord[i] * c + k];
+    }
+    U.swap(U2);
+}
+
+// Residual estimates of a cluster of (numerically) equal Ritz values: the
+// estimate of a vector s of the cluster's eigenspace is ||B_m s_last||, which
+// depends on the basis chosen inside the cluster.  With E = B_m S_last (B x c,
+// S_last the cluster's last rows), the eigenvectors of E^T E rotate the basis
+// so that the estimates become sqrt of its eigenvalues, ascending: the
+// converged directions of the cluster come first.  rot (c x c) is returned.
+void cluster_estimates(int B, int c, const double* Bm, const std::vector<double>& last /* B x c */,
+                       std::vector<double>& est, std::vector<double>& rot) {
+    std::vector<double> E((size_t)B * c, 0.0), G((size_t)c * c, 0.0);
+    for (int k = 0; k < c; ++k)
+        for (int r = 0; r < B; ++r) {
+            double v = 0.0;
+            for (int l = 0; l < B; ++l) v += Bm[r * B + l] * last[(size_t)k * B + l];
+            E[(size_t)k * B + r] = v;
+        }
+    for (int i = 0; i < c; ++i)
+        for (int j = 0; j < c; ++j) {
+            double v = 0.0;
+            for (int r = 0; r < B; ++r) v += E[(size_t)i * B + r] * E[(size_t)j * B + r];
+            G[(size_t)j * c + i] = v;
+        }
+    std::vector<double> ev;
+    jacobi_small(c, G, ev, rot);
+    est.assign(c, 0.0);
+    for (int i = 0; i < c; ++i) est[i] = std::sqrt(std::max(ev[i], 0.0));
+}
+
+// clusters of acceptable Ritz values that agree to 1e-11 relative (equal
+// for the residual tolerance), as [begin, end) ranges of ord (sorted by
+// |theta| descending)
+std::vector<std::pair<int, int>> ritz_clusters(const std::vector<int>& ord, const std::vector<double>& theta) {
+    std::vector<std::pair<int, int>> cl;
+    for (int i = 0; i < (int)ord.size();) {
+        int j = i + 1;
+        while (j < (int)ord.size() &&
+               std::fabs(theta[ord[j]] - theta[ord[i]]) <= 1e-11 * std::fabs(theta[ord[i]]))
+            ++j;
+        cl.push_back({i, j});
+        i = j;
+    }
+    return cl;
+}
+
 // the block-tridiagonal T (n = m B) from the diagonal blocks A (row-major
 // B x B each, symmetrised) and the sub-diagonal blocks Bs[1..m-1]
 void build_T(int m, int B, const double* A, const double* Bs, std::vector<double>& T) {
@@ -599,9 +692,19 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
             if (acceptable(theta[i])) ord.push_back(i);
         if ((int)ord.size() < want_run) return false;
         std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
-        for (int q = 0; q < want_run; ++q)
-            if (!(est[ord[q]] <= tol_est * std::fabs(theta[ord[q]]))) return false;
-        return true;
+        const double* bm = hB + (size_t)mm * B * B;
+        int counted = 0;
+        for (const auto& cr : ritz_clusters(ord, theta)) {
+            const int cn = cr.second - cr.first;
+            std::vector<double> last((size_t)B * cn), cest, rot;
+            for (int k = 0; k < cn; ++k)
+                for (int l = 0; l < B; ++l) last[(size_t)k * B + l] = Zl[(size_t)ord[cr.first + k] * B + l];
+            cluster_estimates(B, cn, bm, last, cest, rot);
+            for (int k = 0; k < cn && counted < want_run; ++k, ++counted)
+                if (!(cest[k] <= tol_est * std::fabs(theta[ord[cr.first]]))) return false;
+            if (counted >= want_run) break;
+        }
+        return counted >= want_run;
     };
 
     // Checks are lagged: the block copies of step m are queued with an
@@ -672,18 +775,54 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     const int n = m * B;
     std::vector<double> est;
     ritz(m, est);
-    std::vector<int> cand;
+    std::vector<int> ord;
     for (int i = 0; i < n; ++i)
-        if (acceptable(theta[i]) && est[i] <= tol_est * std::fabs(theta[i])) cand.push_back(i);
-    std::sort(cand.begin(), cand.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
-    const int room = lock_cap - nlock;
-    if ((int)cand.size() > room) cand.resize(std::max(room, 0));
-    std::vector<double> th(cand.size()), Wsel((size_t)n * cand.size()), lcand(cand.size());
-    for (size_t q = 0; q < cand.size(); ++q) {
-        th[q] = theta[cand[q]];
-        lcand[q] = cur_sigma + 1.0 / th[q];
+        if (acceptable(theta[i])) ord.push_back(i);
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+    // eigenvectors (one inverse-iteration call, so that close Ritz values get
+    // orthogonal vectors) of every cluster that may hold a converged
+    // direction; per cluster, rotated so that the converged directions
+    // separate from the others; keep those whose estimate meets the bar, up
+    // to the locking room
+    const double* bm = hB + (size_t)m * B * B;
+    const int room = std::max(lock_cap - nlock, 0);
+    const auto cls = ritz_clusters(ord, theta);
+    std::vector<int> keep;  // cluster indices
+    std::vector<double> thv;
+    for (int ci = 0; ci < (int)cls.size(); ++ci) {
+        const auto& cr = cls[ci];
+        double best = 1e300;
+        for (int k = cr.first; k < cr.second; ++k) best = std::min(best, est[ord[k]]);
+        if (cr.second - cr.first == 1 && !(best <= 1e3 * tol_est * std::fabs(theta[ord[cr.first]]))) continue;
+        keep.push_back(ci);
+        for (int k = cr.first; k < cr.second; ++k) thv.push_back(theta[ord[k]]);
     }
-    band_eigvecs(n, B, T.data(), (int)cand.size(), th.data(), Wsel.data());
+    std::vector<double> Sall((size_t)n * thv.size());
+    band_eigvecs(n, B, T.data(), (int)thv.size(), thv.data(), Sall.data());
+    std::vector<double> Wsel, lcand;
+    size_t col = 0;
+    for (int ci : keep) {
+        const auto& cr = cls[ci];
+        const int cn = cr.second - cr.first;
+        const double* Sc = Sall.data() + col * n;
+        col += cn;
+        if ((int)lcand.size() >= room) continue;
+        const double th0 = theta[ord[cr.first]];
+        std::vector<double> last((size_t)B * cn), cest, rot;
+        for (int k = 0; k < cn; ++k)
+            for (int l = 0; l < B; ++l) last[(size_t)k * B + l] = Sc[(size_t)k * n + (n - B) + l];
+        cluster_estimates(B, cn, bm, last, cest, rot);
+        for (int k = 0; k < cn && (int)lcand.size() < room; ++k) {
+            if (!(cest[k] <= tol_est * std::fabs(th0))) break;  // ascending: the rest are worse
+            std::vector<double> v(n, 0.0);
+            for (int q = 0; q < cn; ++q) {
+                const double w = rot[(size_t)k * cn + q];
+                for (int i = 0; i < n; ++i) v[i] += w * Sc[(size_t)q * n + i];
+            }
+            Wsel.insert(Wsel.end(), v.begin(), v.end());
+            lcand.push_back(cur_sigma + 1.0 / th0);
+        }
+    }
     if (dbg)
         std::fprintf(stderr, "[riga] block run: B=%d steps=%d (blocks %d/%d) breakdown=%d candidates=%zu\n", B, n, m,
                      nblk, (int)breakdown, lcand.size());

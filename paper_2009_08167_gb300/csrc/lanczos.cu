@@ -641,7 +641,9 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
         if (nlock + m_max + 1 > R.cap) { status = set_error(c, RIGA_ENOMEM, "Lanczos basis capacity"); break; }
         const int col0 = nlock;
         cudaEventRecord(ev0, st);
-        if (B > 1) {
+        // block runs that stop making progress (a cluster larger than the
+        // block, met again and again) hand over to single-vector runs
+        if (B > 1 && fruitless < 2) {
             int mb = 0, acc_n = 0;
             const int m_blk = (int)std::min<long long>(m_max + 16 * B, N - nlock - 2 * B);
             rc = block_run(R, B, nlock, want_run, m_blk, cur_sigma, sigma0, tol_est, lock_tol, lock_cap, seed, lam, &mb,
