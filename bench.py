@@ -266,6 +266,18 @@ def roofline(prof):
             "ms_per_call": pr["ms"] / max(1, pr["calls"])}
 
 
+def aggregate(ms, pairs, world, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: the slowest rank's step time (max
+    over ranks) and the pairs of all ranks (each rank solves its own copy).
+    Returns (value in pairs/s, max ms per step)."""
+    import torch
+    ms_t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    return world * pairs / (ms_max / 1e3), ms_max
+
+
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 FMA rate (2 per clock per SM at 2.07 GHz)
 FP32_PEAK_TFLOPS = 80.5   # nominal GB300 FP32 FMA rate (128 per clock per SM at 2.07 GHz)
 
@@ -348,11 +360,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
     launches = (R.launches() - launches0) // max(1, args.steps)
     pairs = int(np.sum(rs <= RESID_TOL))
     ms = statistics.mean(times)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * pairs / (ms_max / 1e3)
+    value, ms_max = aggregate(ms, pairs, world, dist, dev)
     st = R.stats()
     # end to end: host wall clock around the same public calls (coefficients
     # host -> device inside assembly, eigenvalues and residuals back)
@@ -468,11 +476,7 @@ def run_riga(args, rank, world, local_rank):
     rs_h = rs.cpu().numpy()
     pairs = int(np.sum(rs_h <= RESID_TOL))
     ms = statistics.mean(times)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * pairs / (ms_max / 1e3)
+    value, ms_max = aggregate(ms, pairs, world, dist, dev)
     st = R.stats()
 
     # end to end through the public API with host buffers: mesh description
