@@ -247,23 +247,29 @@ def run_reference(args, rank, world):
 
 def roofline(prof):
     """Roofline of the dominant phase of one profiled step (device time of
-    the phase's launches, CUDA events on the library's stream)."""
+    the phase's launches, CUDA events on the library's stream): against HBM
+    (algorithmic bytes, measured copy bandwidth) and against the FP64 pipe
+    (algorithmic flops, nominal 1.25 TFLOP/s); the bound reported is the one
+    the phase is closer to."""
     pk, pk_kind = peaks()
     dom = max(prof, key=lambda p: prof[p]["ms"])
     pr = prof[dom]
     if pr["ms"] <= 0:
         return None
-    if pr["flops"] > 0 and pr["bytes"] == 0:
-        ach = pr["flops"] / (pr["ms"] / 1e3) / 1e12
-        peak = 1.25  # FP64 FFMA: nominal GB300 FP64 rate (no measured FP64 peak in the peaks file)
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "phase": dom, "peak_source": "nominal fp64"}
-    gbs = pr["bytes"] / (pr["ms"] / 1e3) / 1e9
-    per_call = ncu_traffic(dom)
-    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
-            "traffic": per_call, "phase": dom, "peak_source": pk_kind,
-            "algorithmic_bytes_per_call": pr["bytes"] / max(1, pr["calls"]),
-            "ms_per_call": pr["ms"] / max(1, pr["calls"])}
+    t = pr["ms"] / 1e3
+    gbs = pr["bytes"] / t / 1e9
+    tfl = pr["flops"] / t / 1e12
+    f_hbm = gbs / pk["hbm_gbs"]
+    f_alu = tfl / FP64_PEAK_TFLOPS
+    calls = max(1, pr["calls"])
+    common = {"phase": dom, "ms_per_call": pr["ms"] / calls, "hbm_frac": f_hbm, "fp64_frac": f_alu}
+    if pr["flops"] > 0 and f_alu >= f_hbm:
+        return dict({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
+                     "traffic": None, "peak_source": "nominal fp64 (2 DFMA/clock/SM, 2.07 GHz)",
+                     "algorithmic_flops_per_call": pr["flops"] / calls}, **common)
+    return dict({"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
+                 "traffic": ncu_traffic(dom), "peak_source": pk_kind,
+                 "algorithmic_bytes_per_call": pr["bytes"] / calls}, **common)
 
 
 def aggregate(ms, pairs, world, dist=None, device="cpu"):

@@ -355,7 +355,7 @@ void bortho(BatchState& B, int J, double* w) {
     riga_ctx* c = B.c;
     cudaStream_t st = c->stream;
     if (J <= 0) return;
-    PhaseScope scope(c, PH_REORTH, 4.0 * (double)B.N * J * sizeof(double));
+    PhaseScope scope(c, PH_REORTH, 4.0 * (double)B.N * J * sizeof(double), 8.0 * (double)B.N * J);
     const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
     dim3 rg((J + 31) / 32, B.P);
     { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr, B.ld, J, w, B.ch, B.partial.ptr, B.cap); }

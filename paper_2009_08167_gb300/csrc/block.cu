@@ -411,7 +411,7 @@ template <int B>
 int bortho_t(BlockWork& K, int J) {
     riga_ctx* c = K.c;
     cudaStream_t st = c->stream;
-    PhaseScope scope(c, PH_REORTH, 4.0 * (double)K.N * J * sizeof(double));
+    PhaseScope scope(c, PH_REORTH, 4.0 * (double)K.N * J * sizeof(double), 8.0 * (double)K.N * J * B);
     const size_t sm = dots_smem(B);
     const int pstride = K.cap * B;
     { count_launch(c); bdots_kernel<B><<<K.nch, 256, sm, st>>>(c->MV.ptr, K.ld, J, K.W, K.N, K.part, pstride); }
@@ -445,7 +445,7 @@ int bnormalize_t(BlockWork& K, int col, double* Bout) {
     const unsigned gb = (unsigned)((K.N + 255) / 256);
     const double shift = 11.0 * ((double)K.N * B + (double)B * (B + 1)) * 1.1102230246251565e-16;
     int* counter = K.flag + 1;
-    const unsigned nbg = std::min<unsigned>(nbs, 1216);  // 8 blocks per SM
+    const unsigned nbg = nbs;  // one group of 16 lanes per row
     { count_launch(c); bspmv_gram_kernel<B><<<nbg, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW,
                                                                K.part, counter, G0); }
     c->stats.n_matvec += B;

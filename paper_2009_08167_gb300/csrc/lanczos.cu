@@ -351,7 +351,7 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
     cudaStream_t st = c->stream;
     if (J <= 0) return RIGA_OK;
     // two Gram-Schmidt passes read MV twice and V twice
-    PhaseScope scope(c, PH_REORTH, 4.0 * (double)R.N * J * sizeof(double));
+    PhaseScope scope(c, PH_REORTH, 4.0 * (double)R.N * J * sizeof(double), 8.0 * (double)R.N * J);
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
     { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }

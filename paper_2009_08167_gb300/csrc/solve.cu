@@ -663,8 +663,10 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     cudaStream_t st = c->stream;
     // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
     // and the vectors read and written in each sweep
+    // algorithmic flops: one multiply-add per operator entry and right-hand side
     PhaseScope scope(c, PH_SOLVE,
-                     (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * NR * nsplit * (double)S.N * sizeof(double));
+                     (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * NR * nsplit * (double)S.N * sizeof(double),
+                     2.0 * (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * NR * nsplit);
     int max_n = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
     const int n_items = (int)S.sitems.size();
