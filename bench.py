@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="riga", choices=["riga", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
     ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c4"],
                     help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, "
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
@@ -426,7 +426,7 @@ def run_riga(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    prec = riga.RIGA_FP64 if args.precision == "fp64" else riga.RIGA_FP32
+    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32}[args.precision]
     cfg = workload(args.mesh)
     if cfg.get("batch"):
         return run_riga_batch(args, rank, world, local_rank, cfg)
@@ -589,7 +589,7 @@ def run_kernel_mode(args, local_rank):
     from paper_2009_08167_gb300 import riga
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
-    prec = riga.RIGA_FP64 if args.precision == "fp64" else riga.RIGA_FP32
+    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32}[args.precision]
     cfg = workload(args.mesh)
     R = riga.Riga(local_rank, stream)
     if cfg.get("batch"):

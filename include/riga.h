@@ -52,6 +52,8 @@ extern "C" {
 /* ---------------------------------------------------- factor precisions */
 #define RIGA_FP64 0 /* fronts in FP64 */
 #define RIGA_FP32 1 /* fronts in FP32, solves refined to FP64 accuracy */
+#define RIGA_TF32 2 /* fronts in FP32, trailing updates on the tensor cores (TF32 head + tail
+                       products, about FP32 accuracy), solves refined to FP64 accuracy */
 
 typedef struct riga_ctx riga_ctx;
 
@@ -119,8 +121,10 @@ int riga_analyze(riga_ctx* ctx, const riga_mesh* mesh);
 /*
  * riga_factor: numeric LDL^T of A = K - sigma M in the context's elimination
  * order (Sec. 4.2 and its Remark on inertia), 1x1 pivots without pivoting.
- * precision: RIGA_FP64 or RIGA_FP32 (fronts stored and updated in FP32; the
- *   assembled A is rounded from FP64).
+ * precision: RIGA_FP64, RIGA_FP32 (fronts stored and updated in FP32; the
+ *   assembled A is rounded from FP64) or RIGA_TF32 (FP32 fronts whose Schur
+ *   updates run on the tensor cores: each operand split into a TF32 head and
+ *   tail, three products accumulated in FP32).
  * n_neg (may be NULL): receives the inertia nu(K - sigma M), the number of
  *   negative entries of D = the number of eigenvalues below sigma (Sylvester).
  * Errors: RIGA_ESTATE (no riga_assemble), RIGA_EPIVOT (a zero or non-finite
@@ -173,7 +177,7 @@ int riga_eigs(riga_ctx* ctx, int k, double sigma, double tol, double* evals, dou
  * riga_set_eig_options: options of riga_eigs and riga_eigs_batch, kept
  * separate so that their signatures stay short.
  *  slice      eigenpairs accepted per shift (0 = k, a single shift);
- *  precision  RIGA_FP64 or RIGA_FP32 factor inside riga_eigs;
+ *  precision  RIGA_FP64, RIGA_FP32 or RIGA_TF32 factor inside riga_eigs;
  *  max_steps  Lanczos steps per run (0 = automatic: min(N, max(3 w, w + 40))
  *             for w wanted pairs);
  *  extra      additional pairs computed beyond the wanted ones so that the

@@ -92,6 +92,7 @@ int upload_symbolic(riga_ctx* c) {
     c->solve_flags.release();
     RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
+    RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.tc_titems, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -302,7 +303,8 @@ int riga_factor(riga_ctx* c, double sigma, int precision, long long* n_neg) {
     c->last_error.clear();
     cudaSetDevice(c->device);
     if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
-    if (precision != RIGA_FP64 && precision != RIGA_FP32) return set_error(c, RIGA_EINVAL, "unknown precision");
+    if (precision != RIGA_FP64 && precision != RIGA_FP32 && precision != RIGA_TF32)
+        return set_error(c, RIGA_EINVAL, "unknown precision");
     if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
     c->sigma = sigma;
     c->sigma_prob.clear();
@@ -359,7 +361,8 @@ int riga_solve(riga_ctx* c, const double* b, double* x, int nrhs, double tol, in
 int riga_set_eig_options(riga_ctx* c, int slice, int precision, int max_steps, int extra, unsigned long long seed) {
     if (!c) return RIGA_EINVAL;
     if (slice < 0 || max_steps < 0 || extra < 0) return set_error(c, RIGA_EINVAL, "negative option");
-    if (precision != RIGA_FP64 && precision != RIGA_FP32) return set_error(c, RIGA_EINVAL, "unknown precision");
+    if (precision != RIGA_FP64 && precision != RIGA_FP32 && precision != RIGA_TF32)
+        return set_error(c, RIGA_EINVAL, "unknown precision");
     c->opt_slice = slice;
     c->opt_precision = precision;
     c->opt_max_steps = max_steps;

@@ -105,6 +105,7 @@ struct riga_ctx {
     std::vector<int> level_nodes_off;  // offsets of each level in level_nodes
     riga::DevBuf<riga::PanelItem> pitems;
     riga::DevBuf<riga::TileItem> titems;
+    riga::DevBuf<riga::TileItem> tcitems;  // tensor-core update tiles
     riga::DevBuf<riga::ExtItem> eitems;
     // per-direction 1D data
     riga::DevBuf<int> kv[3], elem_first[3];
@@ -241,6 +242,11 @@ int upload_symbolic(riga_ctx* c);  // symbolic arrays of c->S to the device
 // assemble.cu
 int assemble_device(riga_ctx* c);
 int prepare_batch_assembly(riga_ctx* c);  // once per batch pattern
+// tc_update.cu
+__global__ void tc_update_kernel(const TileItem* items, int p0, const int* kk, const int* nn, const long long* front_off,
+                                 const int* node_ptr, const double* D, float* pool, int plain, int* err,
+                                 long long spin_limit);
+size_t tc_update_smem();
 // factor.cu
 int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
 int finish_factor(riga_ctx* c);   // sync, read flag and inertia

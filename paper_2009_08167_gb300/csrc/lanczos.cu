@@ -627,7 +627,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             if (rc) { status = rc; break; }
             factored_sigma = cur_sigma;
         }
-        if (c->precision == RIGA_FP32 && calibrated_sigma != cur_sigma) {
+        if (c->precision != RIGA_FP64 && calibrated_sigma != cur_sigma) {
             rc = calibrate_refinement(c, seed + (uint64_t)runs);
             if (rc) { status = rc; break; }
             calibrated_sigma = cur_sigma;

@@ -223,6 +223,7 @@ std::string finish_symbolic(Symbolic& S) {
     for (int f = 0; f < F; ++f) S.levels[S.height[f]].nodes.push_back(f);
     S.pitems.clear();
     S.titems.clear();
+    S.tc_titems.clear();
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
     const int ext_cols = 32;
@@ -273,6 +274,20 @@ std::string finish_symbolic(Symbolic& S) {
             }
             R.p_end = (int)S.pitems.size();
             R.t_end = (int)S.titems.size();
+            // the same trailing update in TC_M x TC_N tiles (tensor-core kernel)
+            R.c_begin = (int)S.tc_titems.size();
+            for (int f : P.nodes) {
+                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
+                if (kf <= s * nb) continue;
+                const int c0 = s * nb + std::min(nb, kf - s * nb);
+                for (int i0 = c0; i0 < lf; i0 += TC_M)
+                    for (int j0 = c0; j0 < lf; j0 += TC_N) {
+                        const bool lower = j0 <= i0 + TC_M - 1;
+                        const bool extra = (i0 + TC_M > nf) && (j0 + TC_N > nf);
+                        if (lower || extra) S.tc_titems.push_back({f, i0, j0});
+                    }
+            }
+            R.c_end = (int)S.tc_titems.size();
             P.steps.push_back(R);
         }
     }

@@ -24,6 +24,7 @@ struct Dir1D {
 // Factorization work items (precomputed per level and panel step).
 struct PanelItem { int front; int r0; };            // TRSM row block of a front
 struct TileItem { int front; int i0; int j0; };     // trailing-update tile
+constexpr int TC_M = 128, TC_N = 64;                // tensor-core update tile (rows x columns)
 struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
 
 // tree-solve kernel shapes: 256-thread CTAs per item (large fronts),
@@ -56,6 +57,7 @@ struct StepRange {   // one panel step of one level
     int s;           // step index (panel columns s*nb .. )
     int d_begin, d_end;   // PanelItem range: one diagonal-block item per active front (r0 = s*nb)
     int p_begin, p_end;   // PanelItem range: row blocks below the diagonal block
+    int c_begin, c_end;   // TileItem range of Symbolic::tc_titems (tensor-core update tiles)
     int t_begin, t_end;   // TileItem range
 };
 
@@ -112,6 +114,7 @@ struct Symbolic {
     //                 -A11^{-1} A12 (ldp = hi-lo rounded up to 4);
     //   backward part [lo,hi) of rows 0..k: column-major ldp x n panel of
     //                 [-A11^{-1} | -A11^{-1} A12] (ldp = hi-lo rounded up to 4).
+    std::vector<TileItem> tc_titems;  // update tiles of TC_M x TC_N for the tensor-core update kernel
     std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
     std::vector<ChildRec> crec;       // per child_list entry
     int solve_mode = 0;               // SOLVE_CTA256 / SOLVE_CTA128 / SOLVE_WARP (finish_symbolic)

@@ -28,6 +28,7 @@ RIGA_ECUDA = -7
 RIGA_ENOMEM = -8
 RIGA_FP64 = 0
 RIGA_FP32 = 1
+RIGA_TF32 = 2
 
 EXPORTED = [
     "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_factor", "riga_solve", "riga_eigs",
