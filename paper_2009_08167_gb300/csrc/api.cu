@@ -77,14 +77,6 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->parts_f.upload(S.parts_f, st));
     RIGA_CUDA_TRY(c, c->parts_b.upload(S.parts_b, st));
     RIGA_CUDA_TRY(c, c->qitems.upload(S.qitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.qitems, st));
-    std::vector<int> ln;
-    c->level_nodes_off.assign(S.n_levels + 1, 0);
-    for (int l = 0; l < S.n_levels; ++l) {
-        c->level_nodes_off[l] = (int)ln.size();
-        for (int f : S.levels[l].nodes) ln.push_back(f);
-    }
-    c->level_nodes_off[S.n_levels] = (int)ln.size();
-    RIGA_CUDA_TRY(c, c->level_nodes.upload(ln, st));
     // front of each persistent-solve work item (for traces)
     std::vector<int> order;
     for (const SolveItem& it : S.sitems) order.push_back(it.front);

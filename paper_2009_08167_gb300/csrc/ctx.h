@@ -101,8 +101,7 @@ struct riga_ctx {
     riga::DevBuf<int> parts_f, parts_b;
     riga::DevBuf<riga::PanelItem> qitems;
     riga::DevBuf<long long> rowptr, front_off, front_ptr, rel_ptr, upd_off, scatter, perm_to_glob, glob_rowptr;
-    riga::DevBuf<int> col, perm, ipos, node_ptr, kk, nn, front_pos, child_ptr, child_list, rel, level_nodes, parent;
-    std::vector<int> level_nodes_off;  // offsets of each level in level_nodes
+    riga::DevBuf<int> col, perm, ipos, node_ptr, kk, nn, front_pos, child_ptr, child_list, rel, parent;
     riga::DevBuf<riga::PanelItem> pitems;
     riga::DevBuf<riga::TileItem> titems;
     riga::DevBuf<riga::TileItem> tcitems;  // tensor-core update tiles
@@ -144,12 +143,9 @@ struct riga_ctx {
     riga::DevBuf<int> solve_order;     // 2F work items of the persistent solve
     riga::DevBuf<int> solve_flags;     // per-front completed parts, forward then backward
     riga::DevBuf<double> w1buf;        // assembled own right-hand sides of the forward sweep
-    riga::DevBuf<int> solve_counter;   // work counter of the persistent solve
-    int solve_epoch = 0;
     long long wait_limit = 1LL << 24;  // device dependency-wait budget (polls)
     long long* trace_buf = nullptr;    // device trace of the next solve (riga_trace_solve)
     riga::DevBuf<double> vwork[6];     // N-vectors (permuted order)
-    riga::DevBuf<double> hostbuf_dev;  // staging for host arrays
     riga::DevBuf<double> red;          // reduction scratch
     int ir_sweeps = 4;                 // refinement sweeps per solve inside Lanczos (FP32 factor)
 
