@@ -398,6 +398,8 @@ struct BlockWork {
     int cap;
     double* W;      // N x B
     double* MW;     // N x B
+    double* X;      // N x B refinement iterate (low-precision fronts)
+    double* Rr;     // N x B refinement residual
     double* C1;     // cap * B
     double* C2;
     double* part;   // nch * cap * B, then small partials
@@ -604,7 +606,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     const unsigned nbs = (unsigned)((N * 16 + 255) / 256);
     const size_t part_n = std::max<size_t>((size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B);
     const size_t nAB = (size_t)(2 * nblk + 1) * B * B;  // the T blocks: A_0..A_{nblk-1}, B_0..B_nblk
-    RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)2 * N * B));
+    RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)4 * N * B));
     RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
     RIGA_CUDA_TRY(c, c->bpartial.alloc(part_n));
     RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)4 * B * B + nAB));
@@ -618,6 +620,8 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     }
     K.W = c->bwork.ptr;
     K.MW = c->bwork.ptr + (size_t)N * B;
+    K.X = c->bwork.ptr + (size_t)2 * N * B;
+    K.Rr = c->bwork.ptr + (size_t)3 * N * B;
     K.C1 = c->bcoef.ptr;
     K.C2 = c->bcoef.ptr + (size_t)K.cap * B;
     K.part = c->bpartial.ptr;
@@ -722,12 +726,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
                             cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             rc = set_error(c, RIGA_ECUDA, "block copy");
         if (rc == RIGA_OK) {
-            if (c->precision == RIGA_FP64) {
-                rc = enqueue_solve(c, K.W, B);
-            } else {
-                for (int r = 0; r < B && rc == RIGA_OK; ++r)
-                    rc = solve_refined(c, K.W + (size_t)r * N, R.xw, R.rw, 0.0, c->ir_sweeps, 0, nullptr);
-            }
+            rc = solve_refined_multi(c, K.W, K.X, K.Rr, B, c->ir_sweeps);
         }
         if (rc == RIGA_OK) rc = bortho(K, cj + B);
         if (rc == RIGA_OK) {

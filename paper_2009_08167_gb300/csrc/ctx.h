@@ -253,6 +253,7 @@ int enqueue_spmv(riga_ctx* c, int which, const double* x, double* y, double alph
 void enqueue_permute(riga_ctx* c, const double* in, double* out, int to_perm, int ncols);
 int solve_refined(riga_ctx* c, double* y, double* work_x, double* work_r, double tol, int max_sweeps,
                   int check, int* sweeps_out);
+int solve_refined_multi(riga_ctx* c, double* y, double* work_x, double* work_r, int nr, int sweeps);
 // lanczos.cu
 int run_eigs(riga_ctx* c, int k, double sigma, double tol, int* nconv);
 // batch.cu

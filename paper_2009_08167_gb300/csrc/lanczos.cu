@@ -414,7 +414,7 @@ int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool iner
 
 // FP32 fronts: measure how many refinement sweeps one solve needs to reach a
 // relative residual of 1e-13 (a seeded random right-hand side, residuals read
-// back after every sweep); Lanczos then runs that many plus one without host
+// back after every sweep); Lanczos then runs that many (at least two) without host
 // checks.  If refinement stalls, the shift is refactored with FP64 fronts.
 int calibrate_refinement(riga_ctx* c, uint64_t seed) {
     const long long N = c->S.N;
@@ -426,7 +426,7 @@ int calibrate_refinement(riga_ctx* c, uint64_t seed) {
     int sweeps = 0;
     int rc = solve_refined(c, c->vwork[4].ptr, c->vwork[2].ptr, c->vwork[3].ptr, 1e-13, 20, 1, &sweeps);
     if (rc == RIGA_OK) {
-        c->ir_sweeps = std::min(sweeps + 1, 20);
+        c->ir_sweeps = std::min(std::max(sweeps, 2), 20);
         c->stats.ir_sweeps = c->ir_sweeps;
         return RIGA_OK;
     }
@@ -550,8 +550,16 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     int nlock = 0;
     long long nu0 = 0, nu_chk = 0;
     std::map<double, long long> inertia_cache;
-    int rc = factor_at(c, sigma0, RIGA_FP64, &nu0, prec != RIGA_FP64);
-    if (rc) return rc;
+    // nu(K - sigma0 M): with homogeneous Dirichlet conditions K and M are
+    // symmetric positive definite, every eigenvalue is positive and the
+    // inertia at sigma0 <= 0 is 0 without a factorization; otherwise FP64
+    // fronts give it (an inertia-only factorization when the run's fronts
+    // are of lower precision)
+    int rc = RIGA_OK;
+    if (prec == RIGA_FP64 || sigma0 > 0.0) {
+        rc = factor_at(c, sigma0, RIGA_FP64, &nu0, prec != RIGA_FP64);
+        if (rc) return rc;
+    }
     inertia_cache[sigma0] = nu0;
     double cur_sigma = sigma0;
     double factored_sigma = (prec == RIGA_FP64) ? sigma0 : std::nan("");

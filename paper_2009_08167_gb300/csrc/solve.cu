@@ -807,6 +807,7 @@ int solve_refined(riga_ctx* c, double* y, double* x, double* r, double tol, int 
         int rc = enqueue_solve(c, r);  // r := A^{-1} r (correction)
         if (rc) return rc;
         { count_launch(c); axpy_kernel<<<gb, 256, 0, st>>>(N, 1.0, r, x); }
+        if (!check && sweeps == max_sweeps) break;  // the last residual is not needed
         long long threads = N * 16;
         { count_launch(c); residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
                                                                             c->Mval.ptr, c->sigma, x, y, r); }
@@ -837,6 +838,32 @@ int solve_refined(riga_ctx* c, double* y, double* x, double* r, double tol, int 
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (sweeps_out) *sweeps_out = sweeps;
     if (status) return set_error(c, status, "iterative refinement did not reach the tolerance");
+    return RIGA_OK;
+}
+
+// y := A^{-1} y for nr columns (stride N) with a low-precision factor: a
+// fixed number of refinement sweeps (x = 0, r = y; d = solve(r); x += d;
+// r = y - A x), the corrections of all columns in one solve launch per sweep
+int solve_refined_multi(riga_ctx* c, double* y, double* x, double* r, int nr, int sweeps) {
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    const long long N = S.N, NN = N * nr;
+    if (c->precision == RIGA_FP64) return enqueue_solve(c, y, nr);
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(x, 0, NN * sizeof(double), st));
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(r, y, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int s = 1; s <= sweeps; ++s) {
+        int rc = enqueue_solve(c, r, nr);
+        if (rc) return rc;
+        { count_launch(c); axpy_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, st>>>(NN, 1.0, r, x); }
+        if (s == sweeps) break;
+        const long long threads = N * 16;
+        for (int j = 0; j < nr; ++j) {
+            count_launch(c);
+            residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+                N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, c->Mval.ptr, c->sigma, x + j * N, y + j * N, r + j * N);
+        }
+    }
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(y, x, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return RIGA_OK;
 }
 
