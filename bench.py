@@ -55,7 +55,9 @@ def parse():
                     help="Lanczos block size (riga_set_eig_block; 0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-front (mixed) leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the low-precision-front (mixed) leg")
+    ap.add_argument("--mixed-precision", default="tf32", choices=["fp32", "tf32"],
+                    help="fronts of the mixed leg: tf32 (Schur updates on the tensor cores) or fp32 (FFMA)")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the phase-timing pass")
     ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor", "trace"],
                     help="eigs: the benchmark; solve / factor: a short program (one factorization and "
@@ -286,6 +288,7 @@ def aggregate(ms, pairs, world, dist=None, device="cpu"):
 
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 FMA rate (2 per clock per SM at 2.07 GHz)
 FP32_PEAK_TFLOPS = 80.5   # nominal GB300 FP32 FMA rate (128 per clock per SM at 2.07 GHz)
+TF32_PEAK_TFLOPS = 1100.0  # nominal GB300 dense TF32 tensor rate
 
 
 def fronts_rate(prof, flops_plain, n_fact, peak):
@@ -518,7 +521,8 @@ def run_riga(args, rank, world, local_rank):
     # inertia) on the same workload, same timing rules
     mixed = None
     if args.precision == "fp64" and not args.no_mixed:
-        R.set_eig_options(slice=cfg["slice"], precision=riga.RIGA_FP32, extra=2, seed=11)
+        mprec = riga.RIGA_TF32 if args.mixed_precision == "tf32" else riga.RIGA_FP32
+        R.set_eig_options(slice=cfg["slice"], precision=mprec, extra=2, seed=11)
         for _ in range(max(1, args.warmup)):
             step_device()
         mt = []
@@ -537,11 +541,13 @@ def run_riga(args, rank, world, local_rank):
         step_device()
         prof_m = R.profile_get()
         R.profile(False)
-        fronts_m = fronts_rate(prof_m, q["flops_fact"], R.stats()["n_fact"], FP32_PEAK_TFLOPS)
+        fronts_m = fronts_rate(prof_m, q["flops_fact"], R.stats()["n_fact"],
+                               TF32_PEAK_TFLOPS if args.mixed_precision == "tf32" else FP32_PEAK_TFLOPS)
         mixed = {"value": world * int(np.sum(rs_mh <= RESID_TOL)) / (statistics.mean(mt) / 1e3),
                  "unit": "eigenpairs/s", "ms_per_step": statistics.mean(mt), "converged_pairs": int(np.sum(rs_mh <= RESID_TOL)),
                  "max_resid": float(np.max(rs_mh)), "n_fact": stm["n_fact"], "lanczos_steps": stm["lanczos_steps"],
-                 "dtype": "f32 fronts, f64 refinement/Lanczos/inertia", "fronts": fronts_m,
+                 "dtype": ("f32 fronts with tf32 tensor-core updates" if args.mixed_precision == "tf32" else "f32 fronts")
+                          + ", f64 refinement/Lanczos/inertia", "fronts": fronts_m,
                  "phases_ms_one_step": {p: round(v["ms"], 3) for p, v in prof_m.items() if v["calls"]}}
         R.set_eig_options(slice=cfg["slice"], precision=prec, extra=2, seed=11)
 
