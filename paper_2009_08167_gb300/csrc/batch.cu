@@ -96,9 +96,11 @@ __device__ __forceinline__ double brow_update(const double* __restrict__ V, long
     return v;
 }
 
-// w -= V c(problem) on this chunk, then partial dots MV^T w
-__global__ void __launch_bounds__(256) bupdate_gemvT_kernel(const double* __restrict__ V, const double* __restrict__ MV,
-                                                            long long ld, int J, const double* __restrict__ coef,
+// w -= V[:, 0..Ju) c(problem) on this chunk (coefficients at coef + problem *
+// cstride), then partial dots MV[:, 0..Jd)^T w
+__global__ void __launch_bounds__(256) bupdate_gemvT_kernel(const double* __restrict__ V, int Ju,
+                                                            const double* __restrict__ coef, int cstride,
+                                                            const double* __restrict__ MV, int Jd, long long ld,
                                                             double* __restrict__ w, Chunks ch,
                                                             double* __restrict__ partial, int pstride) {
     extern __shared__ double sh[];
@@ -108,18 +110,18 @@ __global__ void __launch_bounds__(256) bupdate_gemvT_kernel(const double* __rest
     double* cs = Vs + BTJ * (BCH + 1);
     const long long r0 = ch.row0[blockIdx.x];
     const int rows = ch.rows[blockIdx.x];
-    const double* c = coef + (long long)ch.prob[blockIdx.x] * J;
-    for (int j = threadIdx.x; j < J; j += blockDim.x) cs[j] = c[j];
+    const double* c = coef + (long long)ch.prob[blockIdx.x] * cstride;
+    for (int j = threadIdx.x; j < Ju; j += blockDim.x) cs[j] = c[j];
     __syncthreads();
     double v = 0.0;
     if ((int)threadIdx.x < rows) {
         const long long r = r0 + threadIdx.x;
-        v = brow_update(V, ld, J, r, cs, w[r]);
+        v = brow_update(V, ld, Ju, r, cs, w[r]);
         w[r] = v;
     }
     ws[threadIdx.x] = v;
     __syncthreads();
-    bchunk_dots(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+    bchunk_dots(MV, ld, Jd, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
 __global__ void __launch_bounds__(256) bgemv_update_kernel(const double* __restrict__ V, long long ld, int J,
@@ -190,19 +192,27 @@ __global__ void __launch_bounds__(256) bspmv_dot_kernel(const long long* __restr
     }
 }
 
-// per problem: alpha[b][j] = c1[b][col] + c2[b][col], beta[b][j+1] = sqrt(sum of its chunk partials)
+// per problem: alpha[b][j] = c1[b s1 + col1] + c2[b J + col], beta[b][j+1] =
+// sqrt(sum of its chunk partials); with one full Gram-Schmidt pass (check),
+// bit 2 of *flag when that pass removed more than 100 x the norm left
 __global__ void bfinalize_kernel(int P, const double* __restrict__ partial, const int* __restrict__ cbeg,
-                                 const int* __restrict__ cend, const double* __restrict__ c1,
+                                 const int* __restrict__ cend, const double* __restrict__ c1, int s1, int col1,
                                  const double* __restrict__ c2, int J, int col, int j, double* __restrict__ alpha,
-                                 double* __restrict__ beta, double* __restrict__ inv, int mstride) {
+                                 double* __restrict__ beta, double* __restrict__ inv, int mstride, bool check,
+                                 int* __restrict__ flag) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= P) return;
     double s = 0.0;
     for (int c = cbeg[b]; c < cend[b]; ++c) s += partial[c];
-    const double bt = sqrt(fmax(s, 0.0));
-    if (j >= 0) alpha[(long long)b * mstride + j] = c1[(long long)b * J + col] + c2[(long long)b * J + col];
+    const double b2 = fmax(s, 0.0), bt = sqrt(b2);
+    if (j >= 0) alpha[(long long)b * mstride + j] = c1[(long long)b * s1 + col1] + c2[(long long)b * J + col];
     beta[(long long)b * (mstride + 1) + j + 1] = bt;
     inv[b] = bt > 0.0 ? 1.0 / bt : 0.0;
+    if (check) {
+        double q = 0.0;
+        for (int i = 0; i < J; ++i) q += c2[(long long)b * J + i] * c2[(long long)b * J + i];
+        if (!(q <= 1e4 * b2)) atomicOr(flag, 2);
+    }
 }
 
 __global__ void bnormalize_kernel(long long N, const int* __restrict__ prob, const double* __restrict__ inv,
@@ -347,8 +357,9 @@ struct BatchState {
     DevBuf<int> ch_rows, ch_prob, cbeg, cend;
     std::vector<int> h_cbeg, h_cend;
     DevBuf<double> c1, c2, partial, ab_alpha, ab_beta, inv, W, lam, rpart;
-    DevBuf<int> dcol, nlock;
+    DevBuf<int> dcol, nlock, rflag;
     int mcap;
+    bool cgs2 = false;  // two full Gram-Schmidt passes per step (set once one pass was not enough)
 };
 
 void bortho(BatchState& B, int J, double* w) {
@@ -361,21 +372,43 @@ void bortho(BatchState& B, int J, double* w) {
     { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr, B.ld, J, w, B.ch, B.partial.ptr, B.cap); }
     { count_launch(c); bseg_reduce_kernel<<<rg, 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, J, B.cap, B.c1.ptr); }
     { count_launch(c); bupdate_gemvT_kernel<<<B.nch, 256, sm_dots + (size_t)J * sizeof(double), st>>>(
-        c->V.ptr, c->MV.ptr, B.ld, J, B.c1.ptr, w, B.ch, B.partial.ptr, B.cap); }
+        c->V.ptr, J, B.c1.ptr, J, c->MV.ptr, J, B.ld, w, B.ch, B.partial.ptr, B.cap); }
     { count_launch(c); bseg_reduce_kernel<<<rg, 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, J, B.cap, B.c2.ptr); }
     { count_launch(c); bgemv_update_kernel<<<B.nch, 256, (size_t)J * sizeof(double), st>>>(c->V.ptr, B.ld, J, B.c2.ptr, w, B.ch); }
 }
 
-// w -> M-normalised per problem into column col of V / MV; beta slot jslot+1
-void bnormalize(BatchState& B, double* w, double* Mw, int col, int jslot, int J) {
+// Per problem, the three-term recurrence against columns u0..u0+Ju (alpha_j
+// and beta_j computed as (M v)^T w, into c1 with stride Ju), then one full
+// Gram-Schmidt pass against columns 0..J (into c2)
+void brecur(BatchState& B, int J, int u0, int Ju, double* w) {
+    riga_ctx* c = B.c;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 1.0) * (double)B.N * sizeof(double), 4.0 * (double)B.N * (J + Ju));
+    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
+    { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr + (long long)u0 * B.ld, B.ld, Ju, w, B.ch,
+                                                                 B.partial.ptr, B.cap); }
+    { count_launch(c); bseg_reduce_kernel<<<dim3(1, B.P), 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, Ju, B.cap,
+                                                                       B.c1.ptr); }
+    { count_launch(c); bupdate_gemvT_kernel<<<B.nch, 256, sm_dots + (size_t)Ju * sizeof(double), st>>>(
+        c->V.ptr + (long long)u0 * B.ld, Ju, B.c1.ptr, Ju, c->MV.ptr, J, B.ld, w, B.ch, B.partial.ptr, B.cap); }
+    dim3 rg((J + 31) / 32, B.P);
+    { count_launch(c); bseg_reduce_kernel<<<rg, 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, J, B.cap, B.c2.ptr); }
+    { count_launch(c); bgemv_update_kernel<<<B.nch, 256, (size_t)J * sizeof(double), st>>>(c->V.ptr, B.ld, J, B.c2.ptr, w, B.ch); }
+}
+
+// w -> M-normalised per problem into column col of V / MV; beta slot jslot+1.
+// Ju > 0: w came from brecur with Ju recurrence columns (alpha from c1's last
+// entry, the one-pass test evaluated)
+void bnormalize(BatchState& B, double* w, double* Mw, int col, int jslot, int J, int Ju) {
     riga_ctx* c = B.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)B.N * 8.0 * 6.0);
     { count_launch(c); bspmv_dot_kernel<<<B.nch, 256, 0, st>>>(c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, Mw, B.ch, B.partial.ptr); }
     c->stats.n_matvec++;
-    { count_launch(c); bfinalize_kernel<<<(B.P + 127) / 128, 128, 0, st>>>(B.P, B.partial.ptr, B.cbeg.ptr, B.cend.ptr, B.c1.ptr,
-                                                                       B.c2.ptr, J, col - 1, jslot, B.ab_alpha.ptr,
-                                                                       B.ab_beta.ptr, B.inv.ptr, B.mcap); }
+    const int s1 = Ju > 0 ? Ju : J, col1 = Ju > 0 ? Ju - 1 : col - 1;
+    { count_launch(c); bfinalize_kernel<<<(B.P + 127) / 128, 128, 0, st>>>(
+        B.P, B.partial.ptr, B.cbeg.ptr, B.cend.ptr, B.c1.ptr, s1, col1, B.c2.ptr, J, col - 1, jslot, B.ab_alpha.ptr,
+        B.ab_beta.ptr, B.inv.ptr, B.mcap, Ju > 0, B.rflag.ptr); }
     { count_launch(c); bnormalize_kernel<<<(unsigned)((B.N + 255) / 256), 256, 0, st>>>(
         B.N, c->prob_of_pos.ptr, B.inv.ptr, w, Mw, c->V.ptr + (long long)col * B.ld, c->MV.ptr + (long long)col * B.ld); }
 }
@@ -455,6 +488,8 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     RIGA_CUDA_TRY(c, B.ab_alpha.alloc((size_t)P * m_cap));
     RIGA_CUDA_TRY(c, B.ab_beta.alloc((size_t)P * (m_cap + 1)));
     RIGA_CUDA_TRY(c, B.inv.alloc(P));
+    RIGA_CUDA_TRY(c, B.rflag.alloc(1));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(B.rflag.ptr, 0, sizeof(int), c->stream));
     RIGA_CUDA_TRY(c, B.dcol.alloc((size_t)P * want));
     for (int i = 0; i < 2; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
     const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
@@ -508,7 +543,7 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
                 hv[r] = done[b] ? 0.0 : ((double)(bsplitmix(seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
         if (Lmax > 0) bortho(B, Lmax, w);
-        bnormalize(B, w, Mw, col0, -1, Lmax > 0 ? Lmax : 1);
+        bnormalize(B, w, Mw, col0, -1, Lmax > 0 ? Lmax : 1, 0);
         t_start += ms_since(t0);
         int m = 0;
         for (int j = 0; j < m_max; ++j) {
@@ -520,8 +555,14 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
                 status = rc;
                 break;
             }
-            bortho(B, col + 1, w);
-            bnormalize(B, w, Mw, col + 1, j, col + 1);
+            if (B.cgs2) {
+                bortho(B, col + 1, w);
+                bnormalize(B, w, Mw, col + 1, j, col + 1, 0);
+            } else {
+                const int Ju = j == 0 ? 1 : 2;
+                brecur(B, col + 1, col + 1 - Ju, Ju, w);
+                bnormalize(B, w, Mw, col + 1, j, col + 1, Ju);
+            }
             c->stats.steps++;
             m = j + 1;
             if (m % 10 == 0 || m == m_max) {
@@ -531,7 +572,10 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
                                                  cudaMemcpyDeviceToHost, st));
                 RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_beta.data(), B.ab_beta.ptr, h_beta.size() * sizeof(double),
                                                  cudaMemcpyDeviceToHost, st));
+                int rflag = 0;
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(&rflag, B.rflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
                 RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+                if (rflag & 2) B.cgs2 = true;  // two full passes from now on
                 t0 = clk::now();
                 // per problem: are its wanted Ritz values converged?
                 std::vector<char> conv(P, 1);

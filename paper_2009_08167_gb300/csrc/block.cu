@@ -6,9 +6,18 @@
 //
 // Per block step j (H = (K - sigma M)^{-1} M, V_j M-orthonormal, MV_j stored):
 //   W = H V_j                      one B-RHS solve of the stored M V_j
-//   W -= V C1, W -= V C2           two classical Gram-Schmidt passes against
+//   W -= V_{j-1,j} C1              the block three-term recurrence: the
+//                                  coefficients against the last two blocks
+//                                  (computed, not taken from T)
+//   W -= V C2                      one classical Gram-Schmidt pass against
 //                                  all columns so far (locked, then run)
 //   A_j = (C1 + C2)[block j rows]  diagonal block of T
+// The full pass removes what the recurrence leaves along older vectors
+// (rounding, loss of orthogonality, the locked vectors' residuals), which is
+// tiny next to the new block, so one pass leaves W orthogonal to working
+// accuracy.  When it removed more than 100 times the norm that remains (the
+// Daniel-Gragg-Kaufman-Stewart test with a loose bound), a flag switches the
+// solve to two full passes (CGS2) from then on.
 //   W = V_{j+1} B_{j+1}            M-orthonormal QR by Cholesky of W^T M W,
 //                                  twice (CholQR2), M W from one block SpMV
 // T_m is block tridiagonal (half-bandwidth B) with diagonal blocks A_j and
@@ -114,20 +123,21 @@ __device__ __forceinline__ void brow_update(const double* __restrict__ V, long l
     }
 }
 
-// W -= V C (this chunk), then partial dots MV^T W
+// W -= V[:, 0..Ju) C (this chunk), then partial dots MV[:, 0..Jd)^T W
 template <int B>
-__global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restrict__ V, const double* __restrict__ MV,
-                                                           long long ld, int J, const double* __restrict__ C,
+__global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restrict__ V, int Ju,
+                                                           const double* __restrict__ C,
+                                                           const double* __restrict__ MV, int Jd, long long ld,
                                                            double* __restrict__ W, long long N,
                                                            double* __restrict__ partial, int pstride) {
     extern __shared__ double sh[];
     double* ws = sh;                  // B * CH
     double* red = ws + B * CH;        // 8 * TJ * B
     double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
-    double* cs = Vs + TJ * (CH + 1);  // J * B
+    double* cs = Vs + TJ * (CH + 1);  // Ju * B
     const long long r0 = (long long)blockIdx.x * CH;
     const int tid = threadIdx.x;
-    for (int t = tid; t < J * B; t += blockDim.x) cs[t] = C[t];
+    for (int t = tid; t < Ju * B; t += blockDim.x) cs[t] = C[t];
     __syncthreads();
     const long long row = r0 + tid;
     double v[B];
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restr
     if (row < N) {
 #pragma unroll
         for (int r = 0; r < B; ++r) v[r] = W[r * N + row];
-        brow_update<B>(V, ld, J, row, cs, v);
+        brow_update<B>(V, ld, Ju, row, cs, v);
 #pragma unroll
         for (int r = 0; r < B; ++r) W[r * N + row] = v[r];
     }
@@ -144,15 +154,32 @@ __global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restr
     for (int r = 0; r < B; ++r) ws[r * CH + tid] = v[r];
     __syncthreads();
     const int rows = (int)min((long long)CH, N - r0);
-    bchunk_dots<B>(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+    bchunk_dots<B>(MV, ld, Jd, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
+// W -= V C; block 0 also stores the squared column norms of C in cn2 (when
+// given), the part of each column the pass removed
 template <int B>
 __global__ void __launch_bounds__(256) bupdate_kernel(const double* __restrict__ V, long long ld, int J,
-                                                      const double* __restrict__ C, double* __restrict__ W, long long N) {
+                                                      const double* __restrict__ C, double* __restrict__ W, long long N,
+                                                      double* __restrict__ cn2) {
     extern __shared__ double cs[];
     for (int t = threadIdx.x; t < J * B; t += blockDim.x) cs[t] = C[t];
     __syncthreads();
+    if (cn2 && blockIdx.x == 0 && threadIdx.x < 32) {
+        double q2[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) q2[r] = 0.0;
+        for (int q = threadIdx.x; q < J; q += 32)
+#pragma unroll
+            for (int r = 0; r < B; ++r) q2[r] += cs[q * B + r] * cs[q * B + r];
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q2[r] += __shfl_xor_sync(0xffffffffu, q2[r], o);
+            if (threadIdx.x == 0) cn2[r] = q2[r];
+        }
+    }
     const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= N) return;
     double v[B];
@@ -192,6 +219,48 @@ __device__ void tail_reduce(const double* __restrict__ mine, double* __restrict_
         out[threadIdx.x] = t;
     }
     if (threadIdx.x == 0) *counter = 0;
+}
+
+// Coefficients of the block three-term recurrence: out[i B + r] =
+// (M v_{u0+i})^T w_r for the JB = B or 2 B columns of the last two blocks
+// (grid-stride over rows, reduced by the last block)
+template <int B, int JB>
+__global__ void __launch_bounds__(256) blocal_dots_kernel(const double* __restrict__ MV, long long ld,
+                                                          const double* __restrict__ W, long long N,
+                                                          double* __restrict__ partial, int* __restrict__ counter,
+                                                          double* __restrict__ out) {
+    __shared__ double red[8][JB * B];
+    __shared__ double tot[JB * B];
+    double acc[JB * B];
+#pragma unroll
+    for (int e = 0; e < JB * B; ++e) acc[e] = 0.0;
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
+         row += (long long)gridDim.x * blockDim.x) {
+        double w[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) w[r] = W[r * N + row];
+#pragma unroll
+        for (int i = 0; i < JB; ++i) {
+            const double mv = MV[(long long)i * ld + row];
+#pragma unroll
+            for (int r = 0; r < B; ++r) acc[i * B + r] += mv * w[r];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < JB * B; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int e = 0; e < JB * B; ++e) red[threadIdx.x >> 5][e] = acc[e];
+    __syncthreads();
+    if (threadIdx.x < JB * B) {
+        double t = 0.0;
+        for (int g = 0; g < 8; ++g) t += red[g][threadIdx.x];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    tail_reduce<JB * B>(tot, partial, counter, out);
 }
 
 // MW = M W (16 lanes per row, every value of M serving B products) and the
@@ -307,7 +376,8 @@ __global__ void __launch_bounds__(256) bqr_scale_kernel(long long N, const doubl
                                                         double* __restrict__ Rout, int* __restrict__ flag,
                                                         const double* W, long long ldw, const double* MW, double* V,
                                                         double* MV, long long ldv, double* __restrict__ partial,
-                                                        int* __restrict__ counter, double* __restrict__ Gnext) {
+                                                        int* __restrict__ counter, double* __restrict__ Gnext,
+                                                        const double* __restrict__ cn2) {
     __shared__ double sri[B * B];
     __shared__ double red[8][B * B];
     __shared__ double tot[B * B];
@@ -318,6 +388,10 @@ __global__ void __launch_bounds__(256) bqr_scale_kernel(long long N, const doubl
             for (int j = 0; j < B; ++j) sri[i * B + j] = Ri[i][j];
         if (blockIdx.x == 0) {
             if (bad) atomicOr(flag, 1);
+            // the full Gram-Schmidt pass removed more than 100 x the norm left
+            if (cn2)
+                for (int r = 0; r < B; ++r)
+                    if (!(cn2[r] <= 1e4 * G[r * B + r])) atomicOr(flag, 2);
             if (Rout)
                 for (int i = 0; i < B; ++i)
                     for (int j = 0; j < B; ++j) Rout[i * B + j] = R[i][j];
@@ -404,11 +478,14 @@ struct BlockWork {
     double* C2;
     double* part;   // nch * cap * B, then small partials
     double* small;  // B*B Gram, Rinv, R scratch
+    double* cn2;    // B squared norms of the full pass's coefficient columns
     int* flag;
 };
 
 size_t dots_smem(int B) { return (size_t)(B * CH + 8 * TJ * B + TJ * (CH + 1)) * sizeof(double); }
 
+// Two full classical Gram-Schmidt passes of W against columns 0..J of V
+// (CGS2; the start block, and every step once the one-pass test failed)
 template <int B>
 int bortho_t(BlockWork& K, int J) {
     riga_ctx* c = K.c;
@@ -419,10 +496,37 @@ int bortho_t(BlockWork& K, int J) {
     { count_launch(c); bdots_kernel<B><<<K.nch, 256, sm, st>>>(c->MV.ptr, K.ld, J, K.W, K.N, K.part, pstride); }
     enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C1);
     { count_launch(c); bupdate_dots_kernel<B><<<K.nch, 256, sm + (size_t)J * B * sizeof(double), st>>>(
-        c->V.ptr, c->MV.ptr, K.ld, J, K.C1, K.W, K.N, K.part, pstride); }
+        c->V.ptr, J, K.C1, c->MV.ptr, J, K.ld, K.W, K.N, K.part, pstride); }
     enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C2);
     { count_launch(c); bupdate_kernel<B><<<(unsigned)((K.N + 255) / 256), 256, (size_t)J * B * sizeof(double), st>>>(
-        c->V.ptr, K.ld, J, K.C2, K.W, K.N); }
+        c->V.ptr, K.ld, J, K.C2, K.W, K.N, nullptr); }
+    return RIGA_OK;
+}
+
+// The block three-term recurrence against columns u0..u0+Ju (the last one
+// or two blocks; coefficients into C1 at their column positions), then one
+// full pass against columns 0..J (coefficients into C2, squared column
+// norms into cn2)
+template <int B>
+int brecur_t(BlockWork& K, int J, int u0, int Ju) {
+    riga_ctx* c = K.c;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 3.0 * B) * (double)K.N * sizeof(double),
+                     4.0 * (double)K.N * (J + Ju) * B);
+    const size_t sm = dots_smem(B);
+    const int pstride = K.cap * B;
+    const unsigned gl = (unsigned)std::min<long long>((K.N + 255) / 256, 4 * 152);
+    const double* MVu = c->MV.ptr + (long long)u0 * K.ld;
+    double* Cl = K.C1 + (size_t)u0 * B;
+    int* counter = K.flag + 1;
+    count_launch(c);
+    if (Ju == 2 * B) blocal_dots_kernel<B, 2 * B><<<gl, 256, 0, st>>>(MVu, K.ld, K.W, K.N, K.part, counter, Cl);
+    else blocal_dots_kernel<B, B><<<gl, 256, 0, st>>>(MVu, K.ld, K.W, K.N, K.part, counter, Cl);
+    { count_launch(c); bupdate_dots_kernel<B><<<K.nch, 256, sm + (size_t)Ju * B * sizeof(double), st>>>(
+        c->V.ptr + (long long)u0 * K.ld, Ju, Cl, c->MV.ptr, J, K.ld, K.W, K.N, K.part, pstride); }
+    enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C2);
+    { count_launch(c); bupdate_kernel<B><<<(unsigned)((K.N + 255) / 256), 256, (size_t)J * B * sizeof(double), st>>>(
+        c->V.ptr, K.ld, J, K.C2, K.W, K.N, K.cn2); }
     return RIGA_OK;
 }
 
@@ -433,7 +537,7 @@ int bortho_t(BlockWork& K, int J) {
 // directions along converged Ritz vectors are tiny), the next two restore
 // M-orthonormality, and W = V Bout holds to rounding relative to ||W||.
 template <int B>
-int bnormalize_t(BlockWork& K, int col, double* Bout) {
+int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
     riga_ctx* c = K.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)K.N * 8.0 * 10.0 * B);
@@ -453,11 +557,12 @@ int bnormalize_t(BlockWork& K, int col, double* Bout) {
     c->stats.n_matvec += B;
     // shifted pass (W -> V, Gram of V into G1), then two plain passes in place
     { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G0, shift, nullptr, nullptr, R1, K.flag, K.W, K.N,
-                                                              K.MW, V, MV, K.ld, K.part, counter, G1); }
+                                                              K.MW, V, MV, K.ld, K.part, counter, G1,
+                                                              one_pass ? K.cn2 : nullptr); }
     { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G1, 0.0, R1, R2, nullptr, K.flag, V, K.ld, MV, V, MV,
-                                                              K.ld, K.part, counter, G0); }
+                                                              K.ld, K.part, counter, G0, nullptr); }
     { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G0, 0.0, R2, Bout, nullptr, K.flag, V, K.ld, MV, V,
-                                                              MV, K.ld, nullptr, nullptr, nullptr); }
+                                                              MV, K.ld, nullptr, nullptr, nullptr, nullptr); }
     return RIGA_OK;
 }
 
@@ -465,8 +570,11 @@ int bortho(BlockWork& K, int J) {
     if (J <= 0) return RIGA_OK;
     return K.B == 4 ? bortho_t<4>(K, J) : bortho_t<2>(K, J);
 }
-int bnormalize(BlockWork& K, int col, double* Bout) {
-    return K.B == 4 ? bnormalize_t<4>(K, col, Bout) : bnormalize_t<2>(K, col, Bout);
+int brecur(BlockWork& K, int J, int u0, int Ju) {
+    return K.B == 4 ? brecur_t<4>(K, J, u0, Ju) : brecur_t<2>(K, J, u0, Ju);
+}
+int bnormalize(BlockWork& K, int col, double* Bout, bool one_pass) {
+    return K.B == 4 ? bnormalize_t<4>(K, col, Bout, one_pass) : bnormalize_t<2>(K, col, Bout, one_pass);
 }
 
 // Eigen-decomposition of a small symmetric c x c matrix (cyclic Jacobi):
@@ -604,12 +712,13 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.nch = (int)((N + CH - 1) / CH);
     K.cap = R.cap;
     const unsigned nbs = (unsigned)((N * 16 + 255) / 256);
-    const size_t part_n = std::max<size_t>((size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B);
+    const size_t part_n = std::max<size_t>({(size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B,
+                                            (size_t)4 * 152 * 2 * B * B});
     const size_t nAB = (size_t)(2 * nblk + 1) * B * B;  // the T blocks: A_0..A_{nblk-1}, B_0..B_nblk
     RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)4 * N * B));
     RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
     RIGA_CUDA_TRY(c, c->bpartial.alloc(part_n));
-    RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)4 * B * B + nAB));
+    RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)5 * B * B + nAB));
     RIGA_CUDA_TRY(c, c->bflag.alloc(2));
     if (c->bpin_size < nAB + 2) {
         if (c->bpin) cudaFreeHost(c->bpin);
@@ -627,11 +736,12 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.part = c->bpartial.ptr;
     K.small = c->bsmall.ptr;
     K.flag = c->bflag.ptr;
-    double* dA = c->bsmall.ptr + 4 * B * B;  // nblk diagonal blocks, then nblk + 1 sub-diagonal blocks
+    K.cn2 = c->bsmall.ptr + 4 * B * B;
+    double* dA = c->bsmall.ptr + 5 * B * B;  // nblk diagonal blocks, then nblk + 1 sub-diagonal blocks
     double* dB = dA + (size_t)nblk * B * B;
     double* hA = c->bpin;                   // pinned host copies, same layout
     double* hB = hA + (size_t)nblk * B * B;
-    int* hflags = reinterpret_cast<int*>(hA + nAB);  // [0] QR breakdown, [1] solve wait flag
+    int* hflags = reinterpret_cast<int*>(hA + nAB);  // [0] QR breakdown (1), one-pass test failed (2); [1] solve wait flag
     const size_t smx = dots_smem(B) + (size_t)K.cap * B * sizeof(double);
     if (B == 4) {
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bdots_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem(4)));
@@ -652,7 +762,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(K.W, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     int rc = bortho(K, nlock);
     if (rc) return rc;
-    rc = bnormalize(K, col0, dB);
+    rc = bnormalize(K, col0, dB, false);
     if (rc) return rc;
 
     std::vector<double> T, theta, Zl;
@@ -728,12 +838,13 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
         if (rc == RIGA_OK) {
             rc = solve_refined_multi(c, K.W, K.X, K.Rr, B, c->ir_sweeps);
         }
-        if (rc == RIGA_OK) rc = bortho(K, cj + B);
+        const bool one_pass = !R.cgs2;
+        if (rc == RIGA_OK) rc = one_pass ? brecur(K, cj + B, j == 0 ? cj : cj - B, j == 0 ? B : 2 * B) : bortho(K, cj + B);
         if (rc == RIGA_OK) {
             count_launch(c);
             if (B == 4) balpha_kernel<4><<<1, 32, 0, st>>>(K.C1, K.C2, cj, dA + (size_t)j * B * B);
             else balpha_kernel<2><<<1, 32, 0, st>>>(K.C1, K.C2, cj, dA + (size_t)j * B * B);
-            rc = bnormalize(K, cj + B, dB + (size_t)(j + 1) * B * B);
+            rc = bnormalize(K, cj + B, dB + (size_t)(j + 1) * B * B, one_pass);
         }
         if (rc) {
             cudaEventDestroy(ev);
@@ -747,7 +858,8 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
                 cudaEventDestroy(ev);
                 return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
             }
-            breakdown = hflags[0] != 0;
+            breakdown = (hflags[0] & 1) != 0;
+            if (hflags[0] & 2) R.cgs2 = true;  // two full passes from now on
             done = breakdown || converged(pending);
             pending = -1;
         }
@@ -770,7 +882,8 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     if (rc) return rc;
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     if (hflags[1] & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
-    breakdown = hflags[0] != 0;
+    breakdown = (hflags[0] & 1) != 0;
+    if (hflags[0] & 2) R.cgs2 = true;
     const int n = m * B;
     std::vector<double> est;
     ritz(m, est);
@@ -823,8 +936,8 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
         }
     }
     if (dbg)
-        std::fprintf(stderr, "[riga] block run: B=%d steps=%d (blocks %d/%d) breakdown=%d candidates=%zu\n", B, n, m,
-                     nblk, (int)breakdown, lcand.size());
+        std::fprintf(stderr, "[riga] block run: B=%d steps=%d (blocks %d/%d) breakdown=%d cgs2=%d candidates=%zu\n", B,
+                     n, m, nblk, (int)breakdown, (int)R.cgs2, lcand.size());
     return ritz_lock(R, col0, n, Wsel, lcand, nlock, lock_tol, lam, n_locked);
 }
 

@@ -121,30 +121,31 @@ __device__ __forceinline__ double row_update(const double* __restrict__ V, long 
     return v;
 }
 
-// w -= V c1 on this chunk, then partial dots MV^T w
-__global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restrict__ V, const double* __restrict__ MV,
-                                                           long long ld, int J, const double* __restrict__ c1,
+// w -= V[:, 0..Ju) c1 on this chunk, then partial dots MV[:, 0..Jd)^T w
+__global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restrict__ V, int Ju,
+                                                           const double* __restrict__ c1,
+                                                           const double* __restrict__ MV, int Jd, long long ld,
                                                            double* __restrict__ w, long long N,
                                                            double* __restrict__ partial, int pstride) {
     extern __shared__ double sh[];
     double* ws = sh;                    // CH
     double* red = ws + CH;              // 8 * TJ
     double* Vs = red + 8 * TJ;          // TJ * (CH + 1)
-    double* cs = Vs + TJ * (CH + 1);    // J
+    double* cs = Vs + TJ * (CH + 1);    // Ju
     const long long r0 = (long long)blockIdx.x * CH;
     const int tid = threadIdx.x;
-    for (int j = tid; j < J; j += blockDim.x) cs[j] = c1[j];
+    for (int j = tid; j < Ju; j += blockDim.x) cs[j] = c1[j];
     __syncthreads();
     const long long r = r0 + tid;
     double v = 0.0;
     if (r < N) {
-        v = row_update(V, ld, J, r, cs, w[r]);
+        v = row_update(V, ld, Ju, r, cs, w[r]);
         w[r] = v;
     }
     ws[tid] = v;
     __syncthreads();
     const int rows = (int)min((long long)CH, N - r0);
-    chunk_dots(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
+    chunk_dots(MV, ld, Jd, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
 __global__ void gemv_update_kernel(const double* __restrict__ V, long long ld, int J, const double* __restrict__ c,
@@ -185,21 +186,32 @@ __global__ void __launch_bounds__(256) spmv_dot_kernel(long long N, const long l
     }
 }
 
-__global__ void finalize_kernel(const double* __restrict__ partial, int nb, const double* __restrict__ c1,
+// beta_{j+1} = sqrt(w^T M w) from the SpMV's partials, alpha_j = c1[col1] +
+// c2[col]; with one full Gram-Schmidt pass (Jc > 0), bit 2 of *flag when that
+// pass removed more than 100 x the norm left (sum of c2[0..Jc)^2 > 1e4 beta^2)
+__global__ void finalize_kernel(const double* __restrict__ partial, int nb, const double* __restrict__ c1, int col1,
                                 const double* __restrict__ c2, int col, int j, double* __restrict__ alpha,
-                                double* __restrict__ beta) {
+                                double* __restrict__ beta, int Jc, int* __restrict__ flag) {
     __shared__ double sh[256];
-    double s = 0.0;
+    __shared__ double sq[256];
+    double s = 0.0, q = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    for (int i = threadIdx.x; i < Jc; i += blockDim.x) q += c2[i] * c2[i];
     sh[threadIdx.x] = s;
+    sq[threadIdx.x] = q;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        if ((int)threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            sq[threadIdx.x] += sq[threadIdx.x + o];
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (j >= 0) alpha[j] = c1[col] + c2[col];
-        beta[j + 1] = sqrt(fmax(sh[0], 0.0));
+        if (j >= 0) alpha[j] = c1[col1] + c2[col];
+        const double b2 = fmax(sh[0], 0.0);
+        beta[j + 1] = sqrt(b2);
+        if (Jc > 0 && !(sq[0] <= 1e4 * b2)) atomicOr(flag, 2);
     }
 }
 
@@ -346,6 +358,7 @@ uint64_t splitmix(uint64_t& s) {
     return z ^ (z >> 31);
 }
 
+// Two full Gram-Schmidt passes (CGS2) of w against columns col0..col0+J
 int ortho_pass(Run& R, int col0, int J, double* w) {
     riga_ctx* c = R.c;
     cudaStream_t st = c->stream;
@@ -356,23 +369,46 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
     { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }
     size_t sm = sm_dots + (size_t)J * sizeof(double);
-    { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, c->MV.ptr + col0 * R.ld, R.ld, J, R.c1, w,
-                                                R.N, c->partial.ptr, R.cap); }
+    { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + col0 * R.ld, J, R.c1, c->MV.ptr + col0 * R.ld, J,
+                                                                  R.ld, w, R.N, c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2); }
     { count_launch(c); gemv_update_kernel<<<(unsigned)((R.N + 255) / 256), 256, (size_t)J * sizeof(double), st>>>(
         c->V.ptr + col0 * R.ld, R.ld, J, R.c2, w, R.N); }
     return RIGA_OK;
 }
 
-// w -> M-normalised into column `col` of V / MV; beta slot receives the norm
-void normalize_into(Run& R, double* w, int col, int jslot) {
+// The three-term recurrence against columns u0..u0+Ju (alpha_j and beta_j
+// computed as (M v)^T w; coefficients into c1 at their column positions),
+// then one full Gram-Schmidt pass against columns 0..J (into c2)
+int recur_pass(Run& R, int J, int u0, int Ju, double* w) {
+    riga_ctx* c = R.c;
+    cudaStream_t st = c->stream;
+    PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 1.0) * (double)R.N * sizeof(double), 4.0 * (double)R.N * (J + Ju));
+    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
+    { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + (long long)u0 * R.ld, R.ld, Ju, w, R.N,
+                                                                        c->partial.ptr, R.cap); }
+    { count_launch(c); reduce_cols_kernel<<<1, 256, 0, st>>>(c->partial.ptr, R.nch, Ju, R.cap, R.c1 + u0); }
+    size_t sm = sm_dots + (size_t)Ju * sizeof(double);
+    { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + (long long)u0 * R.ld, Ju, R.c1 + u0, c->MV.ptr, J,
+                                                                  R.ld, w, R.N, c->partial.ptr, R.cap); }
+    { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c2); }
+    { count_launch(c); gemv_update_kernel<<<(unsigned)((R.N + 255) / 256), 256, (size_t)J * sizeof(double), st>>>(
+        c->V.ptr, R.ld, J, R.c2, w, R.N); }
+    return RIGA_OK;
+}
+
+// w -> M-normalised into column `col` of V / MV; beta slot receives the norm.
+// Jc > 0: w came from recur_pass against Jc columns (the one-pass test is
+// evaluated, bit 2 of c->bflag[0]).
+void normalize_into(Run& R, double* w, int col, int jslot, int Jc) {
     riga_ctx* c = R.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)R.N * 8.0 * 6.0);
     const unsigned nbs = (unsigned)((R.N * 16 + 255) / 256);
     { count_launch(c); spmv_dot_kernel<<<nbs, 256, 0, st>>>(R.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, R.Mw, c->red.ptr); }
     c->stats.n_matvec++;
-    { count_launch(c); finalize_kernel<<<1, 256, 0, st>>>(c->red.ptr, (int)nbs, R.c1, R.c2, col - 1, jslot, R.alpha, R.beta); }
+    { count_launch(c); finalize_kernel<<<1, 256, 0, st>>>(c->red.ptr, (int)nbs, R.c1, col - 1, R.c2, col - 1, jslot, R.alpha,
+                                                         R.beta, Jc, c->bflag.ptr); }
     { count_launch(c); normalize_kernel<<<(unsigned)((R.N + 255) / 256), 256, 0, st>>>(R.N, w, R.Mw, R.beta + jslot + 1,
                                                                      c->V.ptr + col * R.ld, c->MV.ptr + col * R.ld); }
 }
@@ -531,6 +567,8 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     RIGA_CUDA_TRY(c, c->coef.alloc(2 * (size_t)R.cap));
     RIGA_CUDA_TRY(c, c->ab.alloc(2 * (size_t)m_cap + 4));
     RIGA_CUDA_TRY(c, c->red.alloc((size_t)((N * 16 + 255) / 256) + 1024));
+    RIGA_CUDA_TRY(c, c->bflag.alloc(2));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->bflag.ptr, 0, 2 * sizeof(int), st));
     for (int i = 0; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
     R.w = c->vwork[0].ptr;
     R.Mw = c->vwork[1].ptr;
@@ -677,7 +715,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
         }
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(R.w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
         if (nlock > 0) ortho_pass(R, 0, nlock, R.w);
-        normalize_into(R, R.w, col0, -1);
+        normalize_into(R, R.w, col0, -1, 0);
         int m = 0;
         bool converged = false;
         for (int j = 0; j < m_max; ++j) {
@@ -686,21 +724,28 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
                                              cudaMemcpyDeviceToDevice, st));
             rc = solve_refined(c, R.w, R.xw, R.rw, 0.0, c->ir_sweeps, 0, nullptr);
             if (rc) { status = rc; break; }
-            ortho_pass(R, 0, col + 1, R.w);
-            normalize_into(R, R.w, col + 1, j);
+            if (R.cgs2) {
+                ortho_pass(R, 0, col + 1, R.w);
+                normalize_into(R, R.w, col + 1, j, 0);
+            } else {
+                recur_pass(R, col + 1, j == 0 ? col : col - 1, j == 0 ? 1 : 2, R.w);
+                normalize_into(R, R.w, col + 1, j, col + 1);
+            }
             c->stats.steps++;
             m = j + 1;
             if (m % 10 == 0 || m == m_max) {
                 h_ab.resize(2 * (size_t)m_cap + 4);
-                int dflag = 0;
+                int dflag = 0, rflag = 0;
                 RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_ab.data(), c->ab.ptr, h_ab.size() * sizeof(double),
                                                  cudaMemcpyDeviceToHost, st));
                 RIGA_CUDA_TRY(c, cudaMemcpyAsync(&dflag, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(&rflag, c->bflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
                 RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
                 if (dflag & 2) {
                     status = set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
                     break;
                 }
+                if (rflag & 2) R.cgs2 = true;  // two full passes from now on
                 const double* a = h_ab.data();
                 const double* b = h_ab.data() + m_cap + 2;  // b[i] = beta_i (b[0] = start norm)
                 theta.assign(m, 0.0);

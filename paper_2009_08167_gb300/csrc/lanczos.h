@@ -25,13 +25,15 @@ struct Run {
     double* c2;
     double* alpha;
     double* beta;
+    bool cgs2 = false;  // two full Gram-Schmidt passes per step (set once one pass was not enough)
 };
 
 uint64_t splitmix(uint64_t& s);
 // out[j] = sum over nch chunks of partial[c * pstride + j], j < J (fixed order)
 void enqueue_reduce_cols(riga_ctx* c, const double* partial, int nch, int J, int pstride, double* out);
 int ortho_pass(Run& R, int col0, int J, double* w);
-void normalize_into(Run& R, double* w, int col, int jslot);
+int recur_pass(Run& R, int J, int u0, int Ju, double* w);
+void normalize_into(Run& R, double* w, int col, int jslot, int Jc);
 int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool inertia_only = false);
 int calibrate_refinement(riga_ctx* c, uint64_t seed);
 int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const std::vector<double>& lcand,
