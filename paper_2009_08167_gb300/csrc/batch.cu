@@ -158,36 +158,36 @@ __global__ void __launch_bounds__(256) bseg_reduce_kernel(const double* __restri
     }
 }
 
-// y = M x over a chunk (16 lanes per row) and the chunk's partial x.y
+// y = M x over a chunk (SPMV_TPR lanes per row) and the chunk's partial x.y
 __global__ void __launch_bounds__(256) bspmv_dot_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
                                                         const double* __restrict__ Mv, const double* __restrict__ x,
                                                         double* __restrict__ y, Chunks ch,
                                                         double* __restrict__ partial) {
-    __shared__ double red[16];
+    __shared__ double red[8];
     const long long r0 = ch.row0[blockIdx.x];
     const int rows = ch.rows[blockIdx.x];
-    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
     double d = 0.0;
-    for (int base = 0; base < BCH; base += 16) {
+    for (int base = 0; base < BCH; base += SPMV_RPB) {
         const int rl = base + grp;
         double s = 0.0;
         if (rl < rows) {
             const long long row = r0 + rl;
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Mv[e] * x[col[e]];
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += Mv[e] * x[col[e]];
         }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+        s = group_sum(s);
         if (lane == 0 && rl < rows) {
             const long long row = r0 + rl;
             y[row] = s;
             d += s * x[row];
         }
     }
-    if (lane == 0) red[grp] = d;
+    d = warp_sum_groups(d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < 16; ++i) t += red[i];
+        for (int i = 0; i < 8; ++i) t += red[i];
         partial[blockIdx.x] = t;
     }
 }
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(256) bresid_kernel(const long long* __restrict
                                                      const double* __restrict__ MU, long long ld,
                                                      const double* __restrict__ lam, int qmax, Chunks ch,
                                                      double* __restrict__ partial) {
-    __shared__ double sa[16], sb[16];
+    __shared__ double sa[8], sb[8];
     const int q = blockIdx.y;
     const int b = ch.prob[blockIdx.x];
     const double l = lam[(long long)b * qmax + q];
@@ -273,17 +273,16 @@ __global__ void __launch_bounds__(256) bresid_kernel(const long long* __restrict
     const double* mu = MU + (long long)q * ld;
     const long long r0 = ch.row0[blockIdx.x];
     const int rows = ch.rows[blockIdx.x];
-    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
     double sr = 0.0, sm = 0.0;
-    for (int base = 0; base < BCH; base += 16) {
+    for (int base = 0; base < BCH; base += SPMV_RPB) {
         const int rl = base + grp;
         double s = 0.0;
         if (rl < rows) {
             const long long row = r0 + rl;
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Kv[e] * u[col[e]];
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += Kv[e] * u[col[e]];
         }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+        s = group_sum(s);
         if (lane == 0 && rl < rows) {
             const double m = mu[r0 + rl];
             const double rr = s - l * m;
@@ -291,14 +290,16 @@ __global__ void __launch_bounds__(256) bresid_kernel(const long long* __restrict
             sm += m * m;
         }
     }
-    if (lane == 0) {
-        sa[grp] = sr;
-        sb[grp] = sm;
+    sr = warp_sum_groups(sr);
+    sm = warp_sum_groups(sm);
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = sr;
+        sb[threadIdx.x >> 5] = sm;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double ta = 0.0, tb = 0.0;
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 8; ++i) {
             ta += sa[i];
             tb += sb[i];
         }

@@ -66,7 +66,7 @@ __device__ __forceinline__ void bchunk_dots(const double* __restrict__ Bm, long 
         if (lane < jn) {
             const double* vc = Vs + lane * (CH + 1);
 #pragma unroll 4
-            for (int i = warp; i < CH; i += 8) {
+            for (int i = warp; i < rows; i += 8) {
                 const double v = vc[i];
 #pragma unroll
                 for (int r = 0; r < B; ++r) s[r] += v * ws[r * CH + i];
@@ -85,6 +85,9 @@ __device__ __forceinline__ void bchunk_dots(const double* __restrict__ Bm, long 
     }
 }
 
+// The tall-skinny kernels split the rows evenly over their blocks (at most
+// CH each; the block count a multiple of the SM count), so that every SM gets
+// the same share of the FP64 work.
 template <int B>
 __global__ void __launch_bounds__(256) bdots_kernel(const double* __restrict__ MV, long long ld, int J,
                                                     const double* __restrict__ W, long long N,
@@ -93,12 +96,12 @@ __global__ void __launch_bounds__(256) bdots_kernel(const double* __restrict__ M
     double* ws = sh;                  // B * CH
     double* red = ws + B * CH;        // 8 * TJ * B
     double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
-    const long long r0 = (long long)blockIdx.x * CH;
+    const long long r0 = N * blockIdx.x / gridDim.x;
+    const int rows = (int)(N * (blockIdx.x + 1) / gridDim.x - r0);
     const int tid = threadIdx.x;
 #pragma unroll
-    for (int r = 0; r < B; ++r) ws[r * CH + tid] = (r0 + tid < N) ? W[r * N + r0 + tid] : 0.0;
+    for (int r = 0; r < B; ++r) ws[r * CH + tid] = (tid < rows) ? W[r * N + r0 + tid] : 0.0;
     __syncthreads();
-    const int rows = (int)min((long long)CH, N - r0);
     bchunk_dots<B>(MV, ld, J, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
@@ -135,7 +138,8 @@ __global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restr
     double* red = ws + B * CH;        // 8 * TJ * B
     double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
     double* cs = Vs + TJ * (CH + 1);  // Ju * B
-    const long long r0 = (long long)blockIdx.x * CH;
+    const long long r0 = N * blockIdx.x / gridDim.x;
+    const int rows = (int)(N * (blockIdx.x + 1) / gridDim.x - r0);
     const int tid = threadIdx.x;
     for (int t = tid; t < Ju * B; t += blockDim.x) cs[t] = C[t];
     __syncthreads();
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restr
     double v[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) v[r] = 0.0;
-    if (row < N) {
+    if (tid < rows) {
 #pragma unroll
         for (int r = 0; r < B; ++r) v[r] = W[r * N + row];
         brow_update<B>(V, ld, Ju, row, cs, v);
@@ -153,7 +157,6 @@ __global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restr
 #pragma unroll
     for (int r = 0; r < B; ++r) ws[r * CH + tid] = v[r];
     __syncthreads();
-    const int rows = (int)min((long long)CH, N - r0);
     bchunk_dots<B>(MV, ld, Jd, r0, rows, ws, Vs, red, partial + (long long)blockIdx.x * pstride);
 }
 
@@ -180,14 +183,15 @@ __global__ void __launch_bounds__(256) bupdate_kernel(const double* __restrict__
             if (threadIdx.x == 0) cn2[r] = q2[r];
         }
     }
-    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= N) return;
-    double v[B];
+    const long long r1 = N * (blockIdx.x + 1) / gridDim.x;
+    for (long long row = N * blockIdx.x / gridDim.x + threadIdx.x; row < r1; row += blockDim.x) {
+        double v[B];
 #pragma unroll
-    for (int r = 0; r < B; ++r) v[r] = W[r * N + row];
-    brow_update<B>(V, ld, J, row, cs, v);
+        for (int r = 0; r < B; ++r) v[r] = W[r * N + row];
+        brow_update<B>(V, ld, J, row, cs, v);
 #pragma unroll
-    for (int r = 0; r < B; ++r) W[r * N + row] = v[r];
+        for (int r = 0; r < B; ++r) W[r * N + row] = v[r];
+    }
 }
 
 // Grid-wide sum of the blocks' CNT-value partials without another launch:
@@ -263,55 +267,68 @@ __global__ void __launch_bounds__(256) blocal_dots_kernel(const double* __restri
     tail_reduce<JB * B>(tot, partial, counter, out);
 }
 
-// MW = M W (16 lanes per row, every value of M serving B products) and the
-// Gram matrix G = W^T M W (row-major B x B, reduced by the last block)
+// MW = M W (SPMV_TPR lanes per row, every value of M serving B products) and
+// the Gram matrix G = W^T M W (row-major B x B, its entries spread over the
+// lanes of the row group, reduced by the last block)
 template <int B>
 __global__ void __launch_bounds__(256) bspmv_gram_kernel(long long N, const long long* __restrict__ rowptr,
                                                          const int* __restrict__ col, const double* __restrict__ Mv,
                                                          const double* __restrict__ W, double* __restrict__ MW,
                                                          double* __restrict__ partial, int* __restrict__ counter,
                                                          double* __restrict__ G) {
-    __shared__ double red[16][B * B];
-    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
-    double gacc[B * B];  // lane 0 of each row group: this group's Gram contributions
+    constexpr int GE = (B * B + SPMV_TPR - 1) / SPMV_TPR;  // Gram entries per lane: lane + SPMV_TPR k
+    __shared__ double red[8][B * B];
+    __shared__ double tot[B * B];
+    const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
+    double gacc[GE];
 #pragma unroll
-    for (int e = 0; e < B * B; ++e) gacc[e] = 0.0;
-    // grid-stride over groups of 16 rows, so that few blocks hold partials
-    for (long long base = (long long)blockIdx.x * 16; base < N; base += (long long)gridDim.x * 16) {
+    for (int k = 0; k < GE; ++k) gacc[k] = 0.0;
+    for (long long base = (long long)blockIdx.x * SPMV_RPB; base < N; base += (long long)gridDim.x * SPMV_RPB) {
         const long long row = base + grp;
         double s[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) s[r] = 0.0;
         if (row < N)
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) {
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) {
                 const double mv = Mv[e];
                 const int cc = col[e];
 #pragma unroll
                 for (int r = 0; r < B; ++r) s[r] += mv * W[r * N + cc];
             }
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1)
+        for (int r = 0; r < B; ++r) s[r] = group_sum(s[r]);
+        if (row < N) {
 #pragma unroll
-            for (int r = 0; r < B; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o, 16);
-        if (lane == 0 && row < N) {
+            for (int r = 0; r < B; ++r)
+                if (lane == r % SPMV_TPR) MW[r * N + row] = s[r];
 #pragma unroll
-            for (int r = 0; r < B; ++r) MW[r * N + row] = s[r];
+            for (int k = 0; k < GE; ++k) {
+                const int e = lane + SPMV_TPR * k;
+                if (e < B * B) {
+                    const int q = e / B, r = e % B;
+                    double sr = s[0];
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const double wq = W[q * N + row];
-#pragma unroll
-                for (int r = 0; r < B; ++r) gacc[q * B + r] += wq * s[r];
+                    for (int rr = 1; rr < B; ++rr)
+                        if (r == rr) sr = s[rr];
+                    gacc[k] += W[q * N + row] * sr;
+                }
             }
         }
     }
-    if (lane == 0)
+    // lanes with the same index in the groups of a warp hold the same entries
 #pragma unroll
-        for (int e = 0; e < B * B; ++e) red[grp][e] = gacc[e];
+    for (int k = 0; k < GE; ++k)
+#pragma unroll
+        for (int o = SPMV_TPR; o < 32; o <<= 1) gacc[k] += __shfl_xor_sync(0xffffffffu, gacc[k], o);
+    const int wl = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (wl < SPMV_TPR)
+#pragma unroll
+        for (int k = 0; k < GE; ++k)
+            if (wl + SPMV_TPR * k < B * B) red[warp][wl + SPMV_TPR * k] = gacc[k];
     __syncthreads();
-    __shared__ double tot[B * B];
     if (threadIdx.x < B * B) {
         double t2 = 0.0;
-        for (int g = 0; g < 16; ++g) t2 += red[g][threadIdx.x];
+        for (int g = 0; g < 8; ++g) t2 += red[g][threadIdx.x];
         tot[threadIdx.x] = t2;
     }
     __syncthreads();
@@ -468,7 +485,7 @@ struct BlockWork {
     riga_ctx* c;
     int B;
     long long N, ld;
-    int nch;
+    int nch;        // row blocks of the tall-skinny kernels
     int cap;
     double* W;      // N x B
     double* MW;     // N x B
@@ -498,7 +515,7 @@ int bortho_t(BlockWork& K, int J) {
     { count_launch(c); bupdate_dots_kernel<B><<<K.nch, 256, sm + (size_t)J * B * sizeof(double), st>>>(
         c->V.ptr, J, K.C1, c->MV.ptr, J, K.ld, K.W, K.N, K.part, pstride); }
     enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C2);
-    { count_launch(c); bupdate_kernel<B><<<(unsigned)((K.N + 255) / 256), 256, (size_t)J * B * sizeof(double), st>>>(
+    { count_launch(c); bupdate_kernel<B><<<K.nch, 256, (size_t)J * B * sizeof(double), st>>>(
         c->V.ptr, K.ld, J, K.C2, K.W, K.N, nullptr); }
     return RIGA_OK;
 }
@@ -525,7 +542,7 @@ int brecur_t(BlockWork& K, int J, int u0, int Ju) {
     { count_launch(c); bupdate_dots_kernel<B><<<K.nch, 256, sm + (size_t)Ju * B * sizeof(double), st>>>(
         c->V.ptr + (long long)u0 * K.ld, Ju, Cl, c->MV.ptr, J, K.ld, K.W, K.N, K.part, pstride); }
     enqueue_reduce_cols(c, K.part, K.nch, J * B, pstride, K.C2);
-    { count_launch(c); bupdate_kernel<B><<<(unsigned)((K.N + 255) / 256), 256, (size_t)J * B * sizeof(double), st>>>(
+    { count_launch(c); bupdate_kernel<B><<<K.nch, 256, (size_t)J * B * sizeof(double), st>>>(
         c->V.ptr, K.ld, J, K.C2, K.W, K.N, K.cn2); }
     return RIGA_OK;
 }
@@ -541,7 +558,7 @@ int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
     riga_ctx* c = K.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)K.N * 8.0 * 10.0 * B);
-    const unsigned nbs = (unsigned)((K.N * 16 + 255) / 256);
+    const unsigned nbs = (unsigned)((K.N + SPMV_RPB - 1) / SPMV_RPB);
     double* G0 = K.small;
     double* G1 = G0 + B * B;
     double* R1 = G1 + B * B;
@@ -551,7 +568,7 @@ int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
     const unsigned gb = (unsigned)((K.N + 255) / 256);
     const double shift = 11.0 * ((double)K.N * B + (double)B * (B + 1)) * 1.1102230246251565e-16;
     int* counter = K.flag + 1;
-    const unsigned nbg = nbs;  // one group of 16 lanes per row
+    const unsigned nbg = nbs;  // one group of SPMV_TPR lanes per row
     { count_launch(c); bspmv_gram_kernel<B><<<nbg, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW,
                                                                K.part, counter, G0); }
     c->stats.n_matvec += B;
@@ -709,9 +726,15 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.B = B;
     K.N = N;
     K.ld = R.ld;
-    K.nch = (int)((N + CH - 1) / CH);
+    {
+        int nsm = 0;
+        RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+        nsm = std::max(nsm, 1);
+        const long long nchunk = (N + CH - 1) / CH;
+        K.nch = (int)((nchunk + nsm - 1) / nsm * nsm);  // row blocks: a multiple of the SM count, <= CH rows each
+    }
     K.cap = R.cap;
-    const unsigned nbs = (unsigned)((N * 16 + 255) / 256);
+    const unsigned nbs = (unsigned)((N + SPMV_RPB - 1) / SPMV_RPB);
     const size_t part_n = std::max<size_t>({(size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B,
                                             (size_t)4 * 152 * 2 * B * B});
     const size_t nAB = (size_t)(2 * nblk + 1) * B * B;  // the T blocks: A_0..A_{nblk-1}, B_0..B_nblk

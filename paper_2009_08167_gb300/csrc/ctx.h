@@ -13,6 +13,27 @@
 
 namespace riga {
 
+// Threads per CSR row in the SpMV kernels.  With about 50 (2D, p = 3) to 350
+// (3D) entries per row, four lanes per row keep the FP64 pipe on the
+// products: with 16 lanes the partially filled last pass and the cross-lane
+// sums (every lane adds) took most of its issue slots.
+constexpr int SPMV_TPR = 4;
+constexpr int SPMV_RPB = 256 / SPMV_TPR;  // rows per 256-thread block
+
+// Sum of a value held by the first lane of each SPMV_TPR-lane group over the
+// warp (the result in lane 0; all lanes take part)
+__device__ __forceinline__ double warp_sum_groups(double v) {
+#pragma unroll
+    for (int o = SPMV_TPR; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Sum over the SPMV_TPR lanes of a row group (the result in all of them)
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = SPMV_TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, SPMV_TPR);
+    return v;
+}
+
 // Owning device buffer (cudaMalloc/cudaFree).
 template <typename T>
 struct DevBuf {

@@ -158,30 +158,29 @@ __global__ void gemv_update_kernel(const double* __restrict__ V, long long ld, i
     w[r] = row_update(V, ld, J, r, cs, w[r]);
 }
 
-// y = M x over the permuted CSR (16 lanes per row) and per-block partial x.y
+// y = M x over the permuted CSR (SPMV_TPR lanes per row) and per-block partial x.y
 __global__ void __launch_bounds__(256) spmv_dot_kernel(long long N, const long long* __restrict__ rowptr,
                                                        const int* __restrict__ col, const double* __restrict__ Mv,
                                                        const double* __restrict__ x, double* __restrict__ y,
                                                        double* __restrict__ partial) {
-    __shared__ double red[16];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long row = t / 16;
-    const int lane = (int)(t % 16);
+    __shared__ double red[8];
+    const long long row = (long long)blockIdx.x * SPMV_RPB + threadIdx.x / SPMV_TPR;
+    const int lane = threadIdx.x & (SPMV_TPR - 1);
     double s = 0.0;
     if (row < N)
-        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Mv[e] * x[col[e]];
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += Mv[e] * x[col[e]];
+    s = group_sum(s);
     double d = 0.0;
     if (row < N && lane == 0) {
         y[row] = s;
         d = s * x[row];
     }
-    if (lane == 0) red[threadIdx.x / 16] = d;
+    d = warp_sum_groups(d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int i = 0; i < (int)(blockDim.x / 16); ++i) tot += red[i];
+        for (int i = 0; i < 8; ++i) tot += red[i];
         partial[blockIdx.x] = tot;
     }
 }
@@ -257,28 +256,26 @@ __global__ void __launch_bounds__(256) gemm_ritz_kernel(const double* __restrict
             if (i0 + q < nsel) U[(long long)(i0 + q) * ldu + r] = acc[q];
 }
 
-// Residuals of candidate Ritz pairs: for column q of U (with M U in MU),
-// partial sums of ||K u - lam_q M u||^2 and ||M u||^2 over this block's rows
-// (16 lanes per row; every thread runs the same number of iterations).
+// Residual partial sums per (block, candidate q): ||K u - lam M u||^2 and
+// ||M u||^2 (SPMV_TPR lanes per row; grid-stride over groups of rows)
 __global__ void __launch_bounds__(256) resid_cols_kernel(long long N, const long long* __restrict__ rowptr,
                                                          const int* __restrict__ col, const double* __restrict__ Kv,
                                                          const double* __restrict__ U, const double* __restrict__ MU,
                                                          long long ld, const double* __restrict__ lam,
                                                          double* __restrict__ partial) {
-    __shared__ double sa[16], sb[16];
+    __shared__ double sa[8], sb[8];
     const int q = blockIdx.y;
     const double l = lam[q];
     const double* u = U + (long long)q * ld;
     const double* mu = MU + (long long)q * ld;
-    const int lane = threadIdx.x & 15, grp = threadIdx.x >> 4;
+    const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
     double sr = 0.0, sm = 0.0;
-    for (long long it = blockIdx.x; it * 16 < N; it += gridDim.x) {
-        const long long row = it * 16 + grp;
+    for (long long it = blockIdx.x; it * SPMV_RPB < N; it += gridDim.x) {
+        const long long row = it * SPMV_RPB + grp;
         double s = 0.0;
         if (row < N)
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += Kv[e] * u[col[e]];
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += Kv[e] * u[col[e]];
+        s = group_sum(s);
         if (lane == 0 && row < N) {
             const double m = mu[row];
             const double r = s - l * m;
@@ -286,14 +283,16 @@ __global__ void __launch_bounds__(256) resid_cols_kernel(long long N, const long
             sm += m * m;
         }
     }
-    if (lane == 0) {
-        sa[grp] = sr;
-        sb[grp] = sm;
+    sr = warp_sum_groups(sr);
+    sm = warp_sum_groups(sm);
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = sr;
+        sb[threadIdx.x >> 5] = sm;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double ta = 0.0, tb = 0.0;
-        for (int i = 0; i < 16; ++i) {
+        for (int i = 0; i < 8; ++i) {
             ta += sa[i];
             tb += sb[i];
         }
@@ -404,7 +403,7 @@ void normalize_into(Run& R, double* w, int col, int jslot, int Jc) {
     riga_ctx* c = R.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_SPMV, (double)c->S.nnz * 12.0 + (double)R.N * 8.0 * 6.0);
-    const unsigned nbs = (unsigned)((R.N * 16 + 255) / 256);
+    const unsigned nbs = (unsigned)((R.N + SPMV_RPB - 1) / SPMV_RPB);
     { count_launch(c); spmv_dot_kernel<<<nbs, 256, 0, st>>>(R.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, w, R.Mw, c->red.ptr); }
     c->stats.n_matvec++;
     { count_launch(c); finalize_kernel<<<1, 256, 0, st>>>(c->red.ptr, (int)nbs, R.c1, col - 1, R.c2, col - 1, jslot, R.alpha,

@@ -548,30 +548,29 @@ __global__ void spmv_kernel(long long N, const long long* __restrict__ rowptr, c
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long row = t / LANES;
     const int lane = (int)(t % LANES);
-    if (row >= N) return;
     double s = 0.0;
-    for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += LANES) {
-        double a = which == 0 ? Mv[e] : (which == 1 ? Kv[e] : Kv[e] - shift * Mv[e]);
-        s += a * x[col[e]];
-    }
+    if (row < N)
+        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += LANES) {
+            double a = which == 0 ? Mv[e] : (which == 1 ? Kv[e] : Kv[e] - shift * Mv[e]);
+            s += a * x[col[e]];
+        }
 #pragma unroll
-    for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);
-    if (lane == 0) y[row] = s;
+    for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);  // every lane takes part
+    if (row < N && lane == 0) y[row] = s;
 }
 
-// r = b - (K - shift M) x
+// r = b - (K - shift M) x (SPMV_TPR lanes per row)
 __global__ void residual_kernel(long long N, const long long* __restrict__ rowptr, const int* __restrict__ col,
                                 const double* __restrict__ Kv, const double* __restrict__ Mv, double shift,
                                 const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ r) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long row = t / 16;
-    const int lane = (int)(t % 16);
-    if (row >= N) return;
+    const long long row = t / SPMV_TPR;
+    const int lane = (int)(t % SPMV_TPR);
     double s = 0.0;
-    for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 16) s += (Kv[e] - shift * Mv[e]) * x[col[e]];
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, 16);
-    if (lane == 0) r[row] = b[row] - s;
+    if (row < N)
+        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += (Kv[e] - shift * Mv[e]) * x[col[e]];
+    s = group_sum(s);  // every lane of the warp takes part
+    if (row < N && lane == 0) r[row] = b[row] - s;
 }
 
 // out[ipos] <-> in[g]: to_perm: out[pos] = in[perm[pos]]; else out[perm[pos]] = in[pos]
@@ -769,8 +768,8 @@ int enqueue_solve(riga_ctx* c, double* y, int nrhs) {
 
 int enqueue_spmv(riga_ctx* c, int which, const double* x, double* y, double shift) {
     Symbolic& S = c->S;
-    long long threads = S.N * 16;
-    { count_launch(c); spmv_kernel<16><<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr,
+    long long threads = S.N * SPMV_TPR;
+    { count_launch(c); spmv_kernel<SPMV_TPR><<<(unsigned)((threads + 255) / 256), 256, 0, c->stream>>>(S.N, c->rowptr.ptr, c->col.ptr,
                                                                                c->Kval.ptr, c->Mval.ptr, which, shift,
                                                                                x, y); }
     RIGA_CUDA_TRY(c, cudaGetLastError());
@@ -808,7 +807,7 @@ int solve_refined(riga_ctx* c, double* y, double* x, double* r, double tol, int 
         if (rc) return rc;
         { count_launch(c); axpy_kernel<<<gb, 256, 0, st>>>(N, 1.0, r, x); }
         if (!check && sweeps == max_sweeps) break;  // the last residual is not needed
-        long long threads = N * 16;
+        long long threads = N * SPMV_TPR;
         { count_launch(c); residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
                                                                             c->Mval.ptr, c->sigma, x, y, r); }
         if (check) {
@@ -856,7 +855,7 @@ int solve_refined_multi(riga_ctx* c, double* y, double* x, double* r, int nr, in
         if (rc) return rc;
         { count_launch(c); axpy_kernel<<<(unsigned)((NN + 255) / 256), 256, 0, st>>>(NN, 1.0, r, x); }
         if (s == sweeps) break;
-        const long long threads = N * 16;
+        const long long threads = N * SPMV_TPR;
         for (int j = 0; j < nr; ++j) {
             count_launch(c);
             residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
