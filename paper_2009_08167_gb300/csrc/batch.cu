@@ -23,6 +23,7 @@ namespace riga {
 
 constexpr int BCH = 256;  // rows per chunk
 constexpr int BTJ = 32;   // basis columns per shared-memory tile
+constexpr int BHR = 128;  // rows per shared-memory tile (a chunk is staged in BHR-row pieces)
 
 struct Chunks {
     const long long* row0;
@@ -37,24 +38,29 @@ __device__ __forceinline__ void bchunk_dots(const double* __restrict__ B, long l
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j0 = 0; j0 < J; j0 += BTJ) {
         const int jn = min(BTJ, J - j0);
+        double s = 0.0;
+        for (int h = 0; h < rows; h += BHR) {
+            const int hn = min(BHR, rows - h);
 #pragma unroll
-        for (int q = 0; q < BTJ / 8; ++q) {
-            const int jl = warp + 8 * q;
-            if (jl < jn) {
-                const double* col = B + (long long)(j0 + jl) * ld + r0;
+            for (int q = 0; q < BTJ / 8; ++q) {
+                const int jl = warp + 8 * q;
+                if (jl < jn) {
+                    const double* col = B + (long long)(j0 + jl) * ld + r0 + h;
 #pragma unroll
-                for (int i = 0; i < BCH / 32; ++i) {
-                    const int r = lane + 32 * i;
-                    Vs[jl * (BCH + 1) + r] = (r < rows) ? col[r] : 0.0;
+                    for (int i = 0; i < BHR / 32; ++i) {
+                        const int r = lane + 32 * i;
+                        if (r < hn) Vs[jl * (BHR + 1) + r] = col[r];
+                    }
                 }
             }
-        }
-        __syncthreads();
-        double s = 0.0;
-        if (lane < jn) {
-            const double* vc = Vs + lane * (BCH + 1);
-#pragma unroll 8
-            for (int r = warp; r < BCH; r += 8) s += vc[r] * ws[r];
+            __syncthreads();
+            if (lane < jn) {
+                const double* vc = Vs + lane * (BHR + 1);
+                const double* wh = ws + h;
+#pragma unroll 4
+                for (int r = warp; r < hn; r += 8) s += vc[r] * wh[r];
+            }
+            __syncthreads();
         }
         red[warp * BTJ + lane] = s;
         __syncthreads();
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(256) bupdate_gemvT_kernel(const double* __rest
     double* ws = sh;
     double* red = ws + BCH;
     double* Vs = red + 8 * BTJ;
-    double* cs = Vs + BTJ * (BCH + 1);
+    double* cs = Vs + BTJ * (BHR + 1);
     const long long r0 = ch.row0[blockIdx.x];
     const int rows = ch.rows[blockIdx.x];
     const double* c = coef + (long long)ch.prob[blockIdx.x] * cstride;
@@ -368,7 +374,7 @@ void bortho(BatchState& B, int J, double* w) {
     cudaStream_t st = c->stream;
     if (J <= 0) return;
     PhaseScope scope(c, PH_REORTH, 4.0 * (double)B.N * J * sizeof(double), 8.0 * (double)B.N * J);
-    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
+    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BHR + 1)) * sizeof(double);
     dim3 rg((J + 31) / 32, B.P);
     { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr, B.ld, J, w, B.ch, B.partial.ptr, B.cap); }
     { count_launch(c); bseg_reduce_kernel<<<rg, 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, J, B.cap, B.c1.ptr); }
@@ -385,7 +391,7 @@ void brecur(BatchState& B, int J, int u0, int Ju, double* w) {
     riga_ctx* c = B.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 1.0) * (double)B.N * sizeof(double), 4.0 * (double)B.N * (J + Ju));
-    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
+    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BHR + 1)) * sizeof(double);
     { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr + (long long)u0 * B.ld, B.ld, Ju, w, B.ch,
                                                                  B.partial.ptr, B.cap); }
     { count_launch(c); bseg_reduce_kernel<<<dim3(1, B.P), 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, Ju, B.cap,
@@ -493,7 +499,7 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     RIGA_CUDA_TRY(c, cudaMemsetAsync(B.rflag.ptr, 0, sizeof(int), c->stream));
     RIGA_CUDA_TRY(c, B.dcol.alloc((size_t)P * want));
     for (int i = 0; i < 2; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
-    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BCH + 1)) * sizeof(double);
+    const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BHR + 1)) * sizeof(double);
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bgemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dots));
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_gemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)(sm_dots + (size_t)B.cap * sizeof(double))));

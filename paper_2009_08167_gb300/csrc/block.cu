@@ -38,8 +38,8 @@ namespace riga {
 constexpr int BLK_MAX = 4;
 
 // Partial dots out[j*B + r] = sum over this chunk's rows of B_j[row] w_r[row]
-// (the basis tile staged through shared memory as in the single-vector
-// kernels; every staged entry serves B products).
+// (the basis tile staged through shared memory in HR-row pieces as in the
+// single-vector kernels; every staged entry serves B products).
 template <int B>
 __device__ __forceinline__ void bchunk_dots(const double* __restrict__ Bm, long long ld, int J, long long r0, int rows,
                                             const double* __restrict__ ws, double* __restrict__ Vs,
@@ -47,30 +47,34 @@ __device__ __forceinline__ void bchunk_dots(const double* __restrict__ Bm, long 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j0 = 0; j0 < J; j0 += TJ) {
         const int jn = min(TJ, J - j0);
-#pragma unroll
-        for (int q = 0; q < TJ / 8; ++q) {
-            const int jl = warp + 8 * q;
-            if (jl < jn) {
-                const double* col = Bm + (long long)(j0 + jl) * ld + r0;
-#pragma unroll
-                for (int i = 0; i < CH / 32; ++i) {
-                    const int r = lane + 32 * i;
-                    Vs[jl * (CH + 1) + r] = (r < rows) ? col[r] : 0.0;
-                }
-            }
-        }
-        __syncthreads();
         double s[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) s[r] = 0.0;
-        if (lane < jn) {
-            const double* vc = Vs + lane * (CH + 1);
-#pragma unroll 4
-            for (int i = warp; i < rows; i += 8) {
-                const double v = vc[i];
+        for (int h = 0; h < rows; h += HR) {
+            const int hn = min(HR, rows - h);
 #pragma unroll
-                for (int r = 0; r < B; ++r) s[r] += v * ws[r * CH + i];
+            for (int q = 0; q < TJ / 8; ++q) {
+                const int jl = warp + 8 * q;
+                if (jl < jn) {
+                    const double* col = Bm + (long long)(j0 + jl) * ld + r0 + h;
+#pragma unroll
+                    for (int i = 0; i < HR / 32; ++i) {
+                        const int r = lane + 32 * i;
+                        if (r < hn) Vs[jl * (HR + 1) + r] = col[r];
+                    }
+                }
             }
+            __syncthreads();
+            if (lane < jn) {
+                const double* vc = Vs + lane * (HR + 1);
+#pragma unroll 4
+                for (int i = warp; i < hn; i += 8) {
+                    const double v = vc[i];
+#pragma unroll
+                    for (int r = 0; r < B; ++r) s[r] += v * ws[r * CH + h + i];
+                }
+            }
+            __syncthreads();
         }
 #pragma unroll
         for (int r = 0; r < B; ++r) red[(warp * TJ + lane) * B + r] = s[r];
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(256) bdots_kernel(const double* __restrict__ M
     extern __shared__ double sh[];
     double* ws = sh;                  // B * CH
     double* red = ws + B * CH;        // 8 * TJ * B
-    double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
+    double* Vs = red + 8 * TJ * B;    // TJ * (HR + 1)
     const long long r0 = N * blockIdx.x / gridDim.x;
     const int rows = (int)(N * (blockIdx.x + 1) / gridDim.x - r0);
     const int tid = threadIdx.x;
@@ -136,8 +140,8 @@ __global__ void __launch_bounds__(256) bupdate_dots_kernel(const double* __restr
     extern __shared__ double sh[];
     double* ws = sh;                  // B * CH
     double* red = ws + B * CH;        // 8 * TJ * B
-    double* Vs = red + 8 * TJ * B;    // TJ * (CH + 1)
-    double* cs = Vs + TJ * (CH + 1);  // Ju * B
+    double* Vs = red + 8 * TJ * B;    // TJ * (HR + 1)
+    double* cs = Vs + TJ * (HR + 1);  // Ju * B
     const long long r0 = N * blockIdx.x / gridDim.x;
     const int rows = (int)(N * (blockIdx.x + 1) / gridDim.x - r0);
     const int tid = threadIdx.x;
@@ -499,7 +503,7 @@ struct BlockWork {
     int* flag;
 };
 
-size_t dots_smem(int B) { return (size_t)(B * CH + 8 * TJ * B + TJ * (CH + 1)) * sizeof(double); }
+size_t dots_smem(int B) { return (size_t)(B * CH + 8 * TJ * B + TJ * (HR + 1)) * sizeof(double); }
 
 // Two full classical Gram-Schmidt passes of W against columns 0..J of V
 // (CGS2; the start block, and every step once the one-pass test failed)

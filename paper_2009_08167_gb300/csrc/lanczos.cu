@@ -26,38 +26,43 @@
 namespace riga {
 
 // Partial dots out[j] = sum_{r in chunk} B[j][r] ws[r] for j < J over one
-// chunk of CH rows.  Each 32-column tile is staged through shared memory by
-// coalesced column loads; thread (column jl, row group g) then sums rows
-// g, g+8, ... with one FP64 FMA per element (GB300's FP64 pipe is the bound of
-// these tall-skinny products), and the 8 row groups are added through shared
-// memory.
+// chunk of at most CH rows.  Each 32-column tile is staged through shared
+// memory in HR-row pieces by coalesced column loads (the small pieces leave
+// room for six blocks per SM, whose loads overlap the others' arithmetic);
+// thread (column jl, row group g) sums rows g, g+8, ... with one FP64 FMA per
+// element (GB300's FP64 pipe is the bound of these tall-skinny products), and
+// the 8 row groups are added through shared memory.
 __device__ __forceinline__ void chunk_dots(const double* __restrict__ B, long long ld, int J, long long r0, int rows,
                                            const double* __restrict__ ws, double* __restrict__ Vs,
                                            double* __restrict__ red, double* __restrict__ out) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j0 = 0; j0 < J; j0 += TJ) {
         const int jn = min(TJ, J - j0);
+        double s = 0.0;
+        for (int h = 0; h < rows; h += HR) {
+            const int hn = min(HR, rows - h);
 #pragma unroll
-        for (int q = 0; q < TJ / 8; ++q) {
-            const int jl = warp + 8 * q;
-            if (jl < jn) {
-                const double* col = B + (long long)(j0 + jl) * ld + r0;
+            for (int q = 0; q < TJ / 8; ++q) {
+                const int jl = warp + 8 * q;
+                if (jl < jn) {
+                    const double* col = B + (long long)(j0 + jl) * ld + r0 + h;
 #pragma unroll
-                for (int i = 0; i < CH / 32; ++i) {
-                    const int r = lane + 32 * i;
-                    Vs[jl * (CH + 1) + r] = (r < rows) ? col[r] : 0.0;
+                    for (int i = 0; i < HR / 32; ++i) {
+                        const int r = lane + 32 * i;
+                        if (r < hn) Vs[jl * (HR + 1) + r] = col[r];
+                    }
                 }
             }
+            __syncthreads();
+            if (lane < jn) {
+                const double* vc = Vs + lane * (HR + 1);
+                const double* wh = ws + h;
+#pragma unroll 4
+                for (int r = warp; r < hn; r += 8) s += vc[r] * wh[r];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int jl = lane, g = warp;
-        double s = 0.0;
-        if (jl < jn) {
-            const double* vc = Vs + jl * (CH + 1);
-#pragma unroll 8
-            for (int r = g; r < CH; r += 8) s += vc[r] * ws[r];
-        }
-        red[g * TJ + jl] = s;
+        red[warp * TJ + lane] = s;
         __syncthreads();
         if (tid < jn) {
             double t = 0.0;
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(256) gemvT_partial_kernel(const double* __rest
     extern __shared__ double sh[];
     double* ws = sh;                    // CH
     double* red = ws + CH;              // 8 * TJ
-    double* Vs = red + 8 * TJ;          // TJ * (CH + 1)
+    double* Vs = red + 8 * TJ;          // TJ * (HR + 1)
     const long long r0 = (long long)blockIdx.x * CH;
     const int tid = threadIdx.x;
     ws[tid] = (r0 + tid < N) ? w[r0 + tid] : 0.0;
@@ -130,8 +135,8 @@ __global__ void __launch_bounds__(256) update_gemvT_kernel(const double* __restr
     extern __shared__ double sh[];
     double* ws = sh;                    // CH
     double* red = ws + CH;              // 8 * TJ
-    double* Vs = red + 8 * TJ;          // TJ * (CH + 1)
-    double* cs = Vs + TJ * (CH + 1);    // Ju
+    double* Vs = red + 8 * TJ;          // TJ * (HR + 1)
+    double* cs = Vs + TJ * (HR + 1);    // Ju
     const long long r0 = (long long)blockIdx.x * CH;
     const int tid = threadIdx.x;
     for (int j = tid; j < Ju; j += blockDim.x) cs[j] = c1[j];
@@ -364,7 +369,7 @@ int ortho_pass(Run& R, int col0, int J, double* w) {
     if (J <= 0) return RIGA_OK;
     // two Gram-Schmidt passes read MV twice and V twice
     PhaseScope scope(c, PH_REORTH, 4.0 * (double)R.N * J * sizeof(double), 8.0 * (double)R.N * J);
-    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
+    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
     { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + col0 * R.ld, R.ld, J, w, R.N, c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<(J + 31) / 32, 256, 0, st>>>(c->partial.ptr, R.nch, J, R.cap, R.c1); }
     size_t sm = sm_dots + (size_t)J * sizeof(double);
@@ -383,7 +388,7 @@ int recur_pass(Run& R, int J, int u0, int Ju, double* w) {
     riga_ctx* c = R.c;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 1.0) * (double)R.N * sizeof(double), 4.0 * (double)R.N * (J + Ju));
-    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
+    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
     { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + (long long)u0 * R.ld, R.ld, Ju, w, R.N,
                                                                         c->partial.ptr, R.cap); }
     { count_launch(c); reduce_cols_kernel<<<1, 256, 0, st>>>(c->partial.ptr, R.nch, Ju, R.cap, R.c1 + u0); }
@@ -472,7 +477,7 @@ int calibrate_refinement(riga_ctx* c, uint64_t seed) {
 }
 
 static int configure_reorth(riga_ctx* c, int cap) {
-    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (CH + 1)) * sizeof(double);
+    const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
     const size_t sm_upd = sm_dots + (size_t)cap * sizeof(double);
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(gemvT_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dots));
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(update_gemvT_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_upd));

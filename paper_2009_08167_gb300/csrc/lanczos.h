@@ -11,6 +11,7 @@ namespace riga {
 
 constexpr int CH = 256;  // rows per chunk of the tall-skinny kernels
 constexpr int TJ = 32;   // basis columns per shared-memory tile
+constexpr int HR = 128;  // rows per shared-memory tile (a chunk is staged in HR-row pieces)
 
 struct Run {
     riga_ctx* c;
