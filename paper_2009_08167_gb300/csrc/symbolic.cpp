@@ -120,7 +120,8 @@ std::string finish_symbolic(Symbolic& S) {
     }
 
     // ------------------------------------------------------- solve items
-    // Parts of about part_fma multiply-adds each (at most 32 per sweep), of at
+    // Parts of about part_fma multiply-adds each (at most 32 per sweep for 2D
+    // trees, 256 for large fronts), of at
     // most 8 outputs per thread of the solve CTA (4 per lane for the warp
     // kernel).  When every front has at most SMALL_MAX_N variables (2D
     // meshes), parts are smaller, so that the fronts near the root (the
@@ -146,17 +147,30 @@ std::string finish_symbolic(Symbolic& S) {
         }
         return P;
     };
+    // Large fronts (3D) near the root take up to 256 parts, so that the top
+    // separators of the tree spread over every SM; each part also gathers its
+    // front's vector (n values, plus the children's update vectors going
+    // forward), so a part keeps at least two multiply-adds per gathered value.
+    const bool large = S.solve_mode == SOLVE_CTA256;
+    const long long max_parts = large ? 256 : 32;
     S.parts_f.assign(F, 1);
     S.parts_b.assign(F, 1);
     for (int f = 0; f < F; ++f) {
         const long long kk = S.k[f], mm = S.n[f] - S.k[f], nn = S.n[f];
-        long long pf = (kk * mm + part_fma - 1) / part_fma;
-        pf = std::max(1LL, std::min({pf, 32LL, std::max(1LL, mm)}));
+        long long gat_f = nn;
+        for (int ci = S.child_ptr[f]; ci < S.child_ptr[f + 1]; ++ci) {
+            const int c = S.child_list[ci];
+            gat_f += S.n[c] - S.k[c];
+        }
+        const long long unit_f = large ? std::max(part_fma, 2 * gat_f) : part_fma;
+        const long long unit_b = large ? std::max(part_fma, 2 * nn) : part_fma;
+        long long pf = (kk * mm + unit_f - 1) / unit_f;
+        pf = std::max(1LL, std::min({pf, max_parts, std::max(1LL, mm)}));
         pf = split(mm, pf);
-        long long pb = (kk * nn + part_fma - 1) / part_fma;
-        pb = std::max(1LL, std::min({pb, 32LL, std::max(1LL, kk / 8)}));
+        long long pb = (kk * nn + unit_b - 1) / unit_b;
+        pb = std::max(1LL, std::min({pb, max_parts, std::max(1LL, kk / 8)}));
         pb = split(kk, pb);
-        if (pf > 64 || pb > 64) return "front too large for the tree solve";
+        if (pf > 4 * max_parts || pb > 4 * max_parts) return "front too large for the tree solve";
         S.parts_f[f] = (int)pf;
         S.parts_b[f] = (int)pb;
     }
