@@ -630,10 +630,11 @@ static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out,
     // small fronts: halves of 2048..3072 elements (NR > 1: as large as the
     // largest panel needs), so that every part's panel arrives in one copy;
     // large fronts: halves of up to 32 KiB, smaller when the front vectors
-    // are long, so that two CTAs fit an SM (one streams while the other
-    // computes)
+    // are long, so that three CTAs fit an SM (FP32 panels; the longer FP64
+    // front vectors leave room for two), whose copies overlap the others'
+    // arithmetic
     const long long fixed = ((long long)nr * max_n + (long long)nt * nr + 8) * (long long)elem;
-    const long long half_max = std::max<long long>(8192, std::min<long long>(32768, (112 * 1024 - fixed) / 2));
+    const long long half_max = std::max<long long>(8192, std::min<long long>(32768, (74 * 1024 - fixed) / 2));
     long long chunk = S.solve_mode == SOLVE_CTA128
                           ? std::max<long long>(2048, (S.max_panel + 1) / 2)
                           : half_max / (long long)elem;
