@@ -46,7 +46,8 @@ struct TreeArgs {
     int nsplit;        // independent groups of NR right-hand sides, items interleaved
     int n_fronts;      // stride of the per-group completion counters
     long long upd_size;  // stride (per right-hand side) of the update vectors
-    int chunk_elems;   // elements per shared-memory chunk buffer (two buffers)
+    int chunk_elems;   // elements per shared-memory chunk buffer (two per slot)
+    int nslot;         // 1, or 2: the next item's copies start while the current one runs
     int max_n;
     double* upd;
     double* y;         // NR right-hand sides, column r at y + r * ldy
@@ -174,27 +175,59 @@ template <typename T, int NT, int NR>
 __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
     constexpr int NAMAX = (NR == 1) ? 8 : (NR == 2 ? 4 : 2);  // output slots per thread per pass
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* buf[2];
-    buf[0] = reinterpret_cast<T*>(smem_raw);
-    buf[1] = buf[0] + a.chunk_elems;
-    T* w = buf[1] + a.chunk_elems;  // front vectors (NR x max_n)
-    T* red = w + NR * a.max_n;      // NT x NR partial sums
+    // a.nslot slots of two chunk halves each: slot s = halves 2s, 2s+1
+    T* const bufs = reinterpret_cast<T*>(smem_raw);
+    T* w = bufs + 2 * a.nslot * a.chunk_elems;  // front vectors (NR x max_n)
+    T* red = w + NR * a.max_n;                  // NT x NR partial sums
     const int ldw = a.max_n;
-    __shared__ __align__(8) unsigned long long mbar[2];
-    __shared__ int s_item, s_ok;
+    __shared__ __align__(8) unsigned long long mbar[4];
+    __shared__ int s_item, s_next, s_ok;
+    __shared__ int s_pend[4];  // per half: a copy issued and not yet waited for
     const int tid = threadIdx.x;
-    unsigned parity[2] = {0u, 0u};
+    const int total = a.n_items * a.nsplit;
+    unsigned par = 0u;  // bit h: parity of the next phase of mbar[h] (every thread tracks it)
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int h = 0; h < 4; ++h) {
+            mbar_init(&mbar[h], 1);
+            s_pend[h] = 0;
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    // thread 0: issue the first (up to two) chunk copies of claimed work
+    // `cw` into slot sl; an item's panel goes in one copy when it fits the
+    // slot's two halves, else in chunks through them
+    auto issue_first = [&](int cw, int sl) {
+        const SolveItem it = a.items[cw / a.nsplit];
+        const bool fw = cw / a.nsplit < a.n_fwd;
+        const int units = fw ? it.k : it.n, ldp = it.ldp, cnt = it.hi - it.lo;
+        const bool whole = (long long)units * ldp <= 2LL * a.chunk_elems;
+        const int upc = whole ? max(1, units) : max(1, a.chunk_elems / ldp);
+        const int nchunks = (cnt > 0) ? (units + upc - 1) / upc : 0;
+        const T* q = Q + it.off;
+        fence_proxy_async();  // the slot's previous contents were read by the generic proxy
+        for (int c = 0; c < min(2, nchunks); ++c) {
+            const int ua = c * upc, un = min(upc, units - ua);
+            s_pend[2 * sl + c] = 1;
+            bulk_load(bufs + (size_t)(2 * sl + c) * a.chunk_elems, q + (long long)ua * ldp, (unsigned)(un * ldp * sizeof(T)),
+                      &mbar[2 * sl + c]);
+        }
+    };
+    // bounded waits for every copy still in flight, then leave
+    auto drain = [&]() {
+        for (int h = 0; h < 2 * a.nslot; ++h)
+            if (s_pend[h]) mbar_wait(&mbar[h], (par >> h) & 1u, a.err, a.spin_limit);
         __syncthreads();
+    };
+    if (tid == 0) {
+        s_item = atomicAdd(a.counter, 1);
+        if (s_item < total) issue_first(s_item, 0);
+    }
+    int cs = 0;  // slot of the current item
+    __syncthreads();
+    for (;;) {
         const int claimed = s_item;
-        if (claimed >= a.n_items * a.nsplit) return;
+        if (claimed >= total) return;  // no copies in flight
         const int item = claimed / a.nsplit, grp = claimed - item * a.nsplit;
         double* const y = a.y + (long long)grp * NR * a.ldy;
         double* const w1 = a.w1 + (long long)grp * NR * a.ldy;
@@ -207,19 +240,21 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         const int lo = it.lo, cnt = it.hi - it.lo, ldp = it.ldp;
         const T* q = Q + it.off;
         const int units = fwd ? k : n;  // rows (forward) or columns (backward) of the panel
-        // one copy into the whole buffer, or chunks through its halves
         const bool whole = (long long)units * ldp <= 2LL * a.chunk_elems;
         const int upc = whole ? max(1, units) : max(1, a.chunk_elems / ldp);
         const int nchunks = (cnt > 0) ? (units + upc - 1) / upc : 0;
-        const int issued = min(2, nchunks);
         if (tid == 0) {
             if (a.trace) {
                 a.trace[4 * claimed] = sm_id();
                 a.trace[4 * claimed + 1] = global_ns();
             }
-            for (int c = 0; c < issued; ++c) {
-                const int ua = c * upc, un = min(upc, units - ua);
-                bulk_load(buf[c], q + (long long)ua * ldp, (unsigned)(un * ldp * sizeof(T)), &mbar[c]);
+            // two slots: the next work is claimed now and its copies overlap
+            // this item's dependency wait and arithmetic.  Work is still
+            // taken in counter order by each CTA, so every dependency of an
+            // item is held by a CTA that is running an earlier item.
+            if (a.nslot == 2) {
+                s_next = atomicAdd(a.counter, 1);
+                if (s_next < total) issue_first(s_next, cs ^ 1);
             }
             bool ok = true;
             if (fwd) {
@@ -237,9 +272,7 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
         }
         __syncthreads();
         if (!s_ok) {
-            // drain the copies in flight (bounded) before leaving
-            for (int c = 0; c < issued; ++c) mbar_wait(&mbar[c], parity[c], a.err, a.spin_limit);
-            __syncthreads();
+            drain();
             return;
         }
         if (fwd) {
@@ -285,21 +318,20 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
 #pragma unroll
                 for (int r = 0; r < NR; ++r) acc[q2][r] = T(0);
             for (int c = 0; c < nchunks; ++c) {
-                const int b = c & 1;
+                const int b = 2 * cs + (c & 1);  // half of the current slot
                 if (pass == 0) {
-                    const bool good = mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
+                    const bool good = mbar_wait(&mbar[b], (par >> b) & 1u, a.err, a.spin_limit);
                     if (__syncthreads_or(!good)) {
                         // a copy did not complete within the budget: wait once more
-                        // (bounded) for it and for the next one, then leave
-                        mbar_wait(&mbar[b], parity[b], a.err, a.spin_limit);
-                        if (c + 1 < nchunks) mbar_wait(&mbar[b ^ 1], parity[b ^ 1], a.err, a.spin_limit);
-                        __syncthreads();
+                        // (bounded) for every copy in flight, then leave
+                        drain();
                         return;
                     }
-                    parity[b] ^= 1u;
+                    par ^= 1u << b;
+                    if (tid == 0) s_pend[b] = 0;
                 }
                 const int ua = c * upc, ub = min(units, ua + upc);
-                const T* P = buf[b];
+                const T* P = bufs + (size_t)b * a.chunk_elems;
                 if (active) {
                     if (NR == 1) {
                         switch (na) {
@@ -325,7 +357,9 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
                 if (pass == 0 && tid == 0 && c + 2 < nchunks) {
                     fence_proxy_async();
                     const int u2 = (c + 2) * upc, un2 = min(upc, units - u2);
-                    bulk_load(buf[b], q + (long long)u2 * ldp, (unsigned)(un2 * ldp * sizeof(T)), &mbar[b]);
+                    s_pend[b] = 1;
+                    bulk_load(bufs + (size_t)b * a.chunk_elems, q + (long long)u2 * ldp, (unsigned)(un2 * ldp * sizeof(T)),
+                              &mbar[b]);
                 }
             }
             if (cl > 0) {
@@ -363,7 +397,15 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
             __threadfence();
             atomicAdd(fwd ? &done_f[F] : &done_b[F], 1);
             if (a.trace) a.trace[4 * claimed + 3] = global_ns();
+            if (a.nslot == 2) {
+                s_item = s_next;
+            } else {
+                s_item = atomicAdd(a.counter, 1);
+                if (s_item < total) issue_first(s_item, 0);
+            }
         }
+        if (a.nslot == 2) cs ^= 1;
+        __syncthreads();
     }
 }
 
@@ -619,22 +661,28 @@ __global__ void norm2_partial_kernel(long long N, const double* __restrict__ a, 
     }
 }
 
-// Whether the NR > 1 kernels can take this symbolic analysis: every part's
-// panel must arrive in one copy (the extra output passes re-read it from
-// shared memory), and the front vectors of NR right-hand sides must fit.
-static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out, int* nt_out) {
+
+// Shared memory of the tree solve (and its chunk size, threads, slots).  The
+// NR > 1 kernels take a symbolic analysis only when every part's panel
+// arrives in one copy (the extra output passes re-read it from shared
+// memory) and the front vectors of NR right-hand sides fit.
+static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out, int* nt_out, int* nslot_out = nullptr) {
     int max_n = 0, max_ldp = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
     for (const SolveItem& it : S.sitems) max_ldp = std::max(max_ldp, it.ldp);
     const int nt = S.solve_mode == SOLVE_CTA256 ? 256 : 128;
     // small fronts: halves of 2048..3072 elements (NR > 1: as large as the
     // largest panel needs), so that every part's panel arrives in one copy;
-    // large fronts: halves of up to 32 KiB, smaller when the front vectors
-    // are long, so that three CTAs fit an SM (FP32 panels; the longer FP64
-    // front vectors leave room for two), whose copies overlap the others'
-    // arithmetic
+    // large fronts: halves of up to 32 KiB, sized so that the CTAs of an SM
+    // fit: FP32 panels three CTAs with two slots each (the next item's
+    // copies run while the current item computes), FP64 panels (whose front
+    // vectors take twice the room) two CTAs with one slot
+    const bool large = S.solve_mode == SOLVE_CTA256;
+    const int nslot = large && elem == 4 ? 2 : 1;
+    const int ctas = large && elem == 4 ? 3 : 2;
     const long long fixed = ((long long)nr * max_n + (long long)nt * nr + 8) * (long long)elem;
-    const long long half_max = std::max<long long>(8192, std::min<long long>(32768, (74 * 1024 - fixed) / 2));
+    const long long budget = 227LL * 1024 / ctas - 2048;
+    const long long half_max = std::max<long long>(8192, std::min<long long>(32768, (budget - fixed) / (2 * nslot)));
     long long chunk = S.solve_mode == SOLVE_CTA128
                           ? std::max<long long>(2048, (S.max_panel + 1) / 2)
                           : half_max / (long long)elem;
@@ -643,8 +691,9 @@ static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out,
     chunk = (chunk + 3) / 4 * 4;
     *chunk_out = (int)chunk;
     *nt_out = nt;
+    if (nslot_out) *nslot_out = nslot;
     if (S.solve_mode == SOLVE_WARP) return 4 * (size_t)nr * max_n * elem;
-    return (2 * (size_t)chunk + (size_t)nr * max_n + (size_t)nt * nr + 8) * elem;
+    return (2 * (size_t)nslot * chunk + (size_t)nr * max_n + (size_t)nt * nr + 8) * elem;
 }
 
 int solve_max_rhs(riga_ctx* c) {
@@ -677,7 +726,8 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     int maxopt = 0, nsm = 0, per_sm = 0, chunk = 0, nt = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t smem = solve_smem(S, NR, sizeof(T), &chunk, &nt);
+    int nslot = 1;
+    const size_t smem = solve_smem(S, NR, sizeof(T), &chunk, &nt, &nslot);
     const bool warp = S.solve_mode == SOLVE_WARP;
     if (smem + 256 > (size_t)maxopt) return set_error(c, RIGA_EINVAL, "front too large for the shared-memory solve");
     if (NR > 1 && (S.solve_mode == SOLVE_CTA256 || (!warp && 2LL * chunk < S.max_panel)))
@@ -710,6 +760,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     a.n_items = n_items;
     a.n_fwd = S.n_fwd_items;
     a.chunk_elems = chunk;
+    a.nslot = nslot;
     a.max_n = max_n;
     a.upd = c->upd.ptr;
     a.y = y;
