@@ -666,6 +666,11 @@ __global__ void norm2_partial_kernel(long long N, const double* __restrict__ a, 
 // NR > 1 kernels take a symbolic analysis only when every part's panel
 // arrives in one copy (the extra output passes re-read it from shared
 // memory) and the front vectors of NR right-hand sides fit.
+// Small fronts (2D trees, 128-thread CTAs): panel slots per CTA and the
+// largest chunk half (elements) for one right-hand side.
+constexpr int SMALL_SLOTS = 1;
+constexpr long long SMALL_CHUNK = 3072;
+
 static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out, int* nt_out, int* nslot_out = nullptr) {
     int max_n = 0, max_ldp = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
@@ -678,7 +683,7 @@ static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out,
     // copies run while the current item computes), FP64 panels (whose front
     // vectors take twice the room) two CTAs with one slot
     const bool large = S.solve_mode == SOLVE_CTA256;
-    const int nslot = large && elem == 4 ? 2 : 1;
+    const int nslot = large ? (elem == 4 ? 2 : 1) : SMALL_SLOTS;
     const int ctas = large && elem == 4 ? 3 : 2;
     const long long fixed = ((long long)nr * max_n + (long long)nt * nr + 8) * (long long)elem;
     const long long budget = 227LL * 1024 / ctas - 2048;
@@ -686,7 +691,7 @@ static size_t solve_smem(const Symbolic& S, int nr, size_t elem, int* chunk_out,
     long long chunk = S.solve_mode == SOLVE_CTA128
                           ? std::max<long long>(2048, (S.max_panel + 1) / 2)
                           : half_max / (long long)elem;
-    if (S.solve_mode == SOLVE_CTA128 && nr == 1) chunk = std::min<long long>(chunk, 3072);
+    if (S.solve_mode == SOLVE_CTA128 && nr == 1) chunk = std::min<long long>(chunk, SMALL_CHUNK);
     chunk = std::max<long long>(chunk, max_ldp);
     chunk = (chunk + 3) / 4 * 4;
     *chunk_out = (int)chunk;
