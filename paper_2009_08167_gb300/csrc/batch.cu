@@ -345,6 +345,20 @@ __global__ void bzero_tail_kernel(long long N, int L, const int* __restrict__ pr
 // ------------------------------------------------------------------ host side
 namespace {
 
+// Start vectors on the device: row r of an active problem takes the
+// SplitMix64 output for counter base + r (Steele, Lea and Flood, 2014),
+// mapped to a uniform value in (-1/2, 1/2); rows of finished problems are 0.
+__global__ void bstart_kernel(long long N, const int* __restrict__ prob, const int* __restrict__ active,
+                              unsigned long long base, double* __restrict__ w) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    unsigned long long z = base + (unsigned long long)(r + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    w[r] = active[prob[r]] ? ((double)(z >> 11) + 0.5) / 9007199254740992.0 - 0.5 : 0.0;
+}
+
 uint64_t bsplitmix(uint64_t& s) {
     s += 0x9E3779B97F4A7C15ULL;
     uint64_t z = s;
@@ -364,7 +378,13 @@ struct BatchState {
     DevBuf<int> ch_rows, ch_prob, cbeg, cend;
     std::vector<int> h_cbeg, h_cend;
     DevBuf<double> c1, c2, partial, ab_alpha, ab_beta, inv, W, lam, rpart;
-    DevBuf<int> dcol, nlock, rflag;
+    DevBuf<int> dcol, nlock, rflag, active;
+    double* pin = nullptr;  // pinned host copies of alpha, beta and the flag (lagged checks)
+    cudaEvent_t ev = nullptr;  // marks those copies
+    ~BatchState() {
+        if (pin) cudaFreeHost(pin);
+        if (ev) cudaEventDestroy(ev);
+    }
     int mcap;
     bool cgs2 = false;  // two full Gram-Schmidt passes per step (set once one pass was not enough)
 };
@@ -497,6 +517,11 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     RIGA_CUDA_TRY(c, B.inv.alloc(P));
     RIGA_CUDA_TRY(c, B.rflag.alloc(1));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(B.rflag.ptr, 0, sizeof(int), c->stream));
+    RIGA_CUDA_TRY(c, B.active.alloc(P));
+    const size_t npin = (size_t)P * m_cap + (size_t)P * (m_cap + 1) + 1;
+    RIGA_CUDA_TRY(c, cudaMallocHost(&B.pin, npin * sizeof(double)));
+    RIGA_CUDA_TRY(c, cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming));
+    cudaEvent_t ev = B.ev;
     RIGA_CUDA_TRY(c, B.dcol.alloc((size_t)P * want));
     for (int i = 0; i < 2; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
     const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BHR + 1)) * sizeof(double);
@@ -519,7 +544,7 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     if (rc) return rc;
     std::vector<long long> nu0 = c->inertia_prob;
     uint64_t seed = c->opt_seed ? c->opt_seed : 1;
-    std::vector<double> h_alpha, h_beta, hv(N);
+    std::vector<double> h_alpha, h_beta;
     int status = RIGA_OK;
     for (int run = 1; run <= 4; ++run) {
         int active = 0;
@@ -545,14 +570,18 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
         }
         // start vectors: random on active problems, zero on the others
         t0 = clk::now();
-        for (int b = 0; b < P; ++b)
-            for (long long r = S.prob_pos[b]; r < S.prob_pos[b + 1]; ++r)
-                hv[r] = done[b] ? 0.0 : ((double)(bsplitmix(seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        {
+            std::vector<int> act(P);
+            for (int b = 0; b < P; ++b) act[b] = !done[b];
+            RIGA_CUDA_TRY(c, B.active.upload(act, st));
+            const unsigned long long base = bsplitmix(seed);
+            count_launch(c);
+            bstart_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, c->prob_of_pos.ptr, B.active.ptr, base, w);
+        }
         if (Lmax > 0) bortho(B, Lmax, w);
         bnormalize(B, w, Mw, col0, -1, Lmax > 0 ? Lmax : 1, 0);
         t_start += ms_since(t0);
-        int m = 0;
+        int m = 0, pending = -1;
         for (int j = 0; j < m_max; ++j) {
             const int col = col0 + j;
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, c->MV.ptr + (long long)col * B.ld, N * sizeof(double),
@@ -572,41 +601,50 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
             }
             c->stats.steps++;
             m = j + 1;
-            if (m % 10 == 0 || m == m_max) {
-                h_alpha.resize((size_t)P * m_cap);
-                h_beta.resize((size_t)P * (m_cap + 1));
-                RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_alpha.data(), B.ab_alpha.ptr, h_alpha.size() * sizeof(double),
-                                                 cudaMemcpyDeviceToHost, st));
-                RIGA_CUDA_TRY(c, cudaMemcpyAsync(h_beta.data(), B.ab_beta.ptr, h_beta.size() * sizeof(double),
-                                                 cudaMemcpyDeviceToHost, st));
-                int rflag = 0;
-                RIGA_CUDA_TRY(c, cudaMemcpyAsync(&rflag, B.rflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
-                RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
-                if (rflag & 2) B.cgs2 = true;  // two full passes from now on
+            // lagged checks: the copies of step `pending` are queued with an
+            // event, the host evaluates them while the GPU runs on, and it
+            // never runs more than two steps ahead of an unevaluated check
+            if (pending >= 0 && (m - pending >= 2 || cudaEventQuery(ev) == cudaSuccess)) {
+                cudaEventSynchronize(ev);
+                const int mc = pending;
+                pending = -1;
+                const double* pa = B.pin;
+                const double* pbeta = B.pin + (size_t)P * m_cap;
+                if (reinterpret_cast<const int*>(B.pin + npin - 1)[0] & 2) B.cgs2 = true;  // two full passes from now on
                 t0 = clk::now();
                 // per problem: are its wanted Ritz values converged?
                 std::vector<char> conv(P, 1);
                 parallel_for(P, [&](int b) {
                     if (done[b]) return;
-                    const double* a = h_alpha.data() + (size_t)b * m_cap;
-                    const double* bt = h_beta.data() + (size_t)b * (m_cap + 1);
-                    std::vector<double> th(m), zz(m);
-                    tridiag_eig(m, a, bt + 1, th.data(), zz.data(), false);
+                    const double* a = pa + (size_t)b * m_cap;
+                    const double* bt = pbeta + (size_t)b * (m_cap + 1);
+                    std::vector<double> th(mc), zz(mc);
+                    tridiag_eig(mc, a, bt + 1, th.data(), zz.data(), false);
                     const int wb = need[b] - nlock[b];
                     int ok = 0;
-                    for (int i = m - 1; i >= 0 && ok < wb; --i) {
+                    for (int i = mc - 1; i >= 0 && ok < wb; --i) {
                         if (!(th[i] > 0.0)) break;
-                        if (std::fabs(bt[m] * zz[i]) <= tol_est * th[i]) ++ok;
+                        if (std::fabs(bt[mc] * zz[i]) <= tol_est * th[i]) ++ok;
                         else break;
                     }
-                    conv[b] = !(ok < wb && bt[m] > 1e-300);
+                    conv[b] = !(ok < wb && bt[mc] > 1e-300);
                 });
                 bool all = true;
                 for (int b = 0; b < P; ++b) all = all && conv[b];
                 t_checks += ms_since(t0);
                 if (all) break;
             }
+            if (pending < 0 && m % 10 == 0 && m < m_max) {
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(B.pin, B.ab_alpha.ptr, (size_t)P * m_cap * sizeof(double),
+                                                 cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(B.pin + (size_t)P * m_cap, B.ab_beta.ptr,
+                                                 (size_t)P * (m_cap + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaMemcpyAsync(B.pin + npin - 1, B.rflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+                RIGA_CUDA_TRY(c, cudaEventRecord(ev, st));
+                pending = m;
+            }
         }
+        if (pending >= 0) cudaEventSynchronize(ev);
         if (status) break;
         // Rayleigh-Ritz per problem, candidates = converged largest theta
         h_alpha.resize((size_t)P * m_cap);
