@@ -14,7 +14,7 @@
 //     diag_kernel      LDL^T of the kb x kb diagonal block in shared memory,
 //                      pivots to D and the front diagonal, breakdown flag;
 //     trsm_kernel      L21 = A21 L11^{-T} D^{-1}, one thread per row;
-//     update_kernel    A22 -= L21 D L21^T on 32x32 lower tiles of the
+//     update_kernel    A22 -= L21 D L21^T on 32x32 (16x16) lower tiles of the
 //                      trailing matrix (remaining fully summed part and the
 //                      Schur complement).
 // All items of one launch span every front of the level.  The original
@@ -181,15 +181,17 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
         if (t < kb) A[(long long)(j0 + t) * ld + r] = x[t];
 }
 
-// C[i0:i0+32, j0:j0+32] -= L[:, panel] D L[:, panel]^T (64 threads, 4x4 each)
-template <typename T>
+// C[i0:i0+TL, j0:j0+TL] -= L[:, panel] D L[:, panel]^T (64 threads, (TL/8)^2 each;
+// TL = 32, or 16 on the small trailing blocks where 32x32 tiles pad too much)
+template <typename T, int TL>
 __global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__ items, int p0,
                                                     const int* __restrict__ kk, const int* __restrict__ nn,
                                                     const long long* __restrict__ front_off,
                                                     const int* __restrict__ node_ptr, const double* __restrict__ D,
                                                     T* __restrict__ pool, int plain) {
-    __shared__ T As[NB][TILE];
-    __shared__ T Bs[NB][TILE];
+    constexpr int R = TL / 8;  // rows and columns per thread
+    __shared__ T As[NB][TL];
+    __shared__ T Bs[NB][TL];
     const TileItem it = items[blockIdx.x];
     const int F = it.front, k = kk[F], n = nn[F], ld = n + k;
     if (plain && (it.i0 >= n || it.j0 >= n)) return;  // plain: tiles touching only extra rows
@@ -197,8 +199,8 @@ __global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__
     T* A = pool + front_off[F];
     const double* d = D + node_ptr[F] + p0;
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < NB * TILE; idx += 64) {
-        int rr = idx % TILE, t = idx / TILE;
+    for (int idx = tid; idx < NB * TL; idx += 64) {
+        int rr = idx % TL, t = idx / TL;
         T a = T(0), b = T(0);
         if (t < kb) {
             int gi = it.i0 + rr, gj = it.j0 + rr;
@@ -210,28 +212,28 @@ __global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__
     }
     __syncthreads();
     const int tx = tid % 8, ty = tid / 8;
-    T acc[4][4];
+    T acc[R][R];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < R; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+        for (int b = 0; b < R; ++b) acc[a][b] = T(0);
     for (int t = 0; t < kb; ++t) {
-        T av[4], bv[4];
+        T av[R], bv[R];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[t][tx + 8 * a];
+        for (int a = 0; a < R; ++a) av[a] = As[t][tx + 8 * a];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[t][ty + 8 * b];
+        for (int b = 0; b < R; ++b) bv[b] = Bs[t][ty + 8 * b];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < R; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+            for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
     }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < R; ++b) {
         int gj = it.j0 + ty + 8 * b;
         if (gj >= ld) continue;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < R; ++a) {
             int gi = it.i0 + tx + 8 * a;
             // lower triangle, plus the whole extra x extra block
             if (gi < ld && (gi >= gj || (gi >= n && gj >= n)) && !(plain && gi >= n)) A[(long long)gj * ld + gi] -= acc[a][b];
@@ -333,10 +335,16 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
                     { count_launch(c); tc_update_kernel<<<R.c_end - R.c_begin, 128, tc_update_smem(), st>>>(
                         c->tcitems.ptr + R.c_begin, j0, c->kk.ptr, c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr, c->D.ptr,
                         reinterpret_cast<float*>(pool), plain, c->flag.ptr, c->wait_limit); }
-            } else if (R.t_end > R.t_begin)
-                { count_launch(c); update_kernel<T><<<R.t_end - R.t_begin, 64, 0, st>>>(c->titems.ptr + R.t_begin, j0, c->kk.ptr,
-                                                                      c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr,
-                                                                      c->D.ptr, pool, plain); }
+            } else {
+                if (R.t_mid > R.t_begin)
+                    { count_launch(c); update_kernel<T, 32><<<R.t_mid - R.t_begin, 64, 0, st>>>(c->titems.ptr + R.t_begin, j0,
+                                                                       c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                                                       c->node_ptr.ptr, c->D.ptr, pool, plain); }
+                if (R.t_end > R.t_mid)
+                    { count_launch(c); update_kernel<T, 16><<<R.t_end - R.t_mid, 64, 0, st>>>(c->titems.ptr + R.t_mid, j0,
+                                                                       c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                                                       c->node_ptr.ptr, c->D.ptr, pool, plain); }
+            }
         }
     }
     if (!S.qitems.empty() && !plain)

@@ -240,6 +240,7 @@ std::string finish_symbolic(Symbolic& S) {
     S.tc_titems.clear();
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
+    const int SMALL_TRAIL = 128;
     const int ext_cols = 32;
     for (int l = 0; l < S.n_levels; ++l) {
         LevelPlan& P = S.levels[l];
@@ -267,26 +268,37 @@ std::string finish_symbolic(Symbolic& S) {
                 if (S.k[f] > s * nb) S.pitems.push_back({f, s * nb});
             R.d_end = (int)S.pitems.size();
             R.p_begin = (int)S.pitems.size();
-            R.t_begin = (int)S.titems.size();
             for (int f : P.nodes) {
-                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
+                int kf = S.k[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 int kb = std::min(nb, kf - s * nb);
                 for (int r0 = s * nb + kb; r0 < lf; r0 += rb) S.pitems.push_back({f, r0});
-                int c0 = s * nb + kb;
-                // trailing update: lower tiles of the augmented front, plus the
-                // upper tiles of the extra x extra block so that -A11^{-1} is
-                // stored in full
-                int T = (lf - c0 + tile - 1) / tile;
-                for (int bi = 0; bi < T; ++bi)
-                    for (int bj = 0; bj < T; ++bj) {
-                        int i0 = c0 + bi * tile, j0 = c0 + bj * tile;
-                        bool lower = bj <= bi;
-                        bool extra_upper = (i0 + tile > nf) && (j0 + tile > nf);
-                        if (lower || extra_upper) S.titems.push_back({f, i0, j0});
-                    }
             }
             R.p_end = (int)S.pitems.size();
+            // trailing update: lower tiles of the augmented front, plus the
+            // upper tiles of the extra x extra block so that -A11^{-1} is
+            // stored in full.  Trailing blocks of at most SMALL_TRAIL rows take
+            // 16x16 tiles (less padding on the diagonal and the edges of small
+            // fronts), larger ones 32x32 tiles.
+            R.t_begin = (int)S.titems.size();
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) R.t_mid = (int)S.titems.size();
+                for (int f : P.nodes) {
+                    int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
+                    if (kf <= s * nb) continue;
+                    const int c0 = s * nb + std::min(nb, kf - s * nb);
+                    const int tl = (lf - c0 <= SMALL_TRAIL) ? 16 : tile;
+                    if ((pass == 0) != (tl == tile)) continue;
+                    const int T = (lf - c0 + tl - 1) / tl;
+                    for (int bi = 0; bi < T; ++bi)
+                        for (int bj = 0; bj < T; ++bj) {
+                            int i0 = c0 + bi * tl, j0 = c0 + bj * tl;
+                            bool lower = bj <= bi;
+                            bool extra_upper = (i0 + tl > nf) && (j0 + tl > nf);
+                            if (lower || extra_upper) S.titems.push_back({f, i0, j0});
+                        }
+                }
+            }
             R.t_end = (int)S.titems.size();
             // the same trailing update in TC_M x TC_N tiles (tensor-core kernel)
             R.c_begin = (int)S.tc_titems.size();

@@ -58,7 +58,8 @@ struct StepRange {   // one panel step of one level
     int d_begin, d_end;   // PanelItem range: one diagonal-block item per active front (r0 = s*nb)
     int p_begin, p_end;   // PanelItem range: row blocks below the diagonal block
     int c_begin, c_end;   // TileItem range of Symbolic::tc_titems (tensor-core update tiles)
-    int t_begin, t_end;   // TileItem range
+    int t_begin, t_end;   // TileItem range: [t_begin, t_mid) 32x32 tiles, [t_mid, t_end) 16x16 tiles
+    int t_mid;
 };
 
 struct LevelPlan {
