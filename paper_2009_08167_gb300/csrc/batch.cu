@@ -36,42 +36,58 @@ __device__ __forceinline__ void bchunk_dots(const double* __restrict__ B, long l
                                             const double* __restrict__ ws, double* __restrict__ Vs,
                                             double* __restrict__ red, double* __restrict__ out) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j0 = 0; j0 < J; j0 += BTJ) {
-        const int jn = min(BTJ, J - j0);
-        double s = 0.0;
-        for (int h = 0; h < rows; h += BHR) {
-            const int hn = min(BHR, rows - h);
-#pragma unroll
-            for (int q = 0; q < BTJ / 8; ++q) {
-                const int jl = warp + 8 * q;
-                if (jl < jn) {
-                    const double* col = B + (long long)(j0 + jl) * ld + r0 + h;
-#pragma unroll
-                    for (int i = 0; i < BHR / 32; ++i) {
-                        const int r = lane + 32 * i;
-                        if (r < hn) Vs[jl * (BHR + 1) + r] = col[r];
-                    }
-                }
-            }
-            __syncthreads();
-            if (lane < jn) {
-                const double* vc = Vs + lane * (BHR + 1);
-                const double* wh = ws + h;
-#pragma unroll 4
-                for (int r = warp; r < hn; r += 8) s += vc[r] * wh[r];
-            }
-            __syncthreads();
-        }
-        red[warp * BTJ + lane] = s;
-        __syncthreads();
-        if (tid < jn) {
-            double t = 0.0;
-#pragma unroll
-            for (int gg = 0; gg < 8; ++gg) t += red[gg * BTJ + tid];
-            out[j0 + tid] = t;
-        }
-        __syncthreads();
+    if (rows <= 0) {  // no rows (the same for the whole block): zero partials
+        for (int j = tid; j < J; j += blockDim.x) out[j] = 0.0;
+        return;
     }
+    const int nh = (rows + BHR - 1) / BHR;           // row pieces per column tile
+    const int nst = ((J + BTJ - 1) / BTJ) * nh;      // stages (column tile, row piece)
+    double pre[BTJ / 8][BHR / 32];                   // the next stage, loaded while this one computes
+    auto load = [&](int st) {
+        const int j0 = (st / nh) * BTJ, h = (st % nh) * BHR;
+        const int jn = min(BTJ, J - j0), hn = min(BHR, rows - h);
+#pragma unroll
+        for (int q = 0; q < BTJ / 8; ++q) {
+            const int jl = warp + 8 * q;
+            const double* col = B + (long long)(j0 + jl) * ld + r0 + h;
+#pragma unroll
+            for (int i = 0; i < BHR / 32; ++i) {
+                const int r = lane + 32 * i;
+                pre[q][i] = (jl < jn && r < hn) ? col[r] : 0.0;
+            }
+        }
+    };
+    if (nst > 0) load(0);
+    double s = 0.0;
+    for (int st = 0; st < nst; ++st) {
+        const int j0 = (st / nh) * BTJ, h = (st % nh) * BHR;
+        const int jn = min(BTJ, J - j0), hn = min(BHR, rows - h);
+#pragma unroll
+        for (int q = 0; q < BTJ / 8; ++q)
+#pragma unroll
+            for (int i = 0; i < BHR / 32; ++i) Vs[(warp + 8 * q) * (BHR + 1) + lane + 32 * i] = pre[q][i];
+        __syncthreads();
+        if (st + 1 < nst) load(st + 1);
+        if (lane < jn) {
+            const double* vc = Vs + lane * (BHR + 1);
+            const double* wh = ws + h;
+#pragma unroll 4
+            for (int r = warp; r < hn; r += 8) s += vc[r] * wh[r];
+        }
+        __syncthreads();
+        if (st % nh == nh - 1) {  // last piece of this column tile: sum the 8 row groups
+            red[warp * BTJ + lane] = s;
+            s = 0.0;
+            __syncthreads();
+            if (tid < jn) {
+                double t = 0.0;
+#pragma unroll
+                for (int gg = 0; gg < 8; ++gg) t += red[gg * BTJ + tid];
+                out[j0 + tid] = t;
+            }
+        }
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) bgemvT_kernel(const double* __restrict__ B, long long ld, int J,
@@ -231,24 +247,27 @@ __global__ void bnormalize_kernel(long long N, const int* __restrict__ prob, con
     mv[r] = Mw[r] * s;
 }
 
-// U[r][q] = sum_j V[r][j] W_b[j][q] over a chunk of problem b (W padded to qmax columns)
+// U[r][q] = sum_j V[r][j] W_b[j][q] over a chunk of problem b (W padded to qmax
+// columns); QN outputs per thread and pass (qmax rounded up to a multiple of
+// 8, at most 32), so that each V entry read serves every candidate
+template <int QN>
 __global__ void __launch_bounds__(256) bgemm_ritz_kernel(const double* __restrict__ V, long long ld, int J,
                                                          const double* __restrict__ W, int qmax, Chunks ch,
                                                          double* __restrict__ U, long long ldu) {
-    __shared__ double Ws[128][16];
+    __shared__ double Ws[128][QN];
     const int b = ch.prob[blockIdx.x];
     const long long r = ch.row0[blockIdx.x] + threadIdx.x;
     const bool ok = (int)threadIdx.x < ch.rows[blockIdx.x];
-    const int i0 = blockIdx.y * 16;
+    const int i0 = blockIdx.y * QN;
     const double* Wb = W + (long long)b * J * qmax;  // column-major J x qmax per problem
-    double acc[16];
+    double acc[QN];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < QN; ++q) acc[q] = 0.0;
     for (int j0 = 0; j0 < J; j0 += 128) {
         const int jn = min(128, J - j0);
         __syncthreads();
-        for (int t = threadIdx.x; t < 128 * 16; t += blockDim.x) {
-            const int jj = t / 16, q = t % 16;
+        for (int t = threadIdx.x; t < 128 * QN; t += blockDim.x) {
+            const int jj = t / QN, q = t % QN;
             Ws[jj][q] = (jj < jn && i0 + q < qmax) ? Wb[(long long)(i0 + q) * J + j0 + jj] : 0.0;
         }
         __syncthreads();
@@ -256,12 +275,12 @@ __global__ void __launch_bounds__(256) bgemm_ritz_kernel(const double* __restric
             for (int jj = 0; jj < jn; ++jj) {
                 const double v = V[(long long)(j0 + jj) * ld + r];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) acc[q] += v * Ws[jj][q];
+                for (int q = 0; q < QN; ++q) acc[q] += v * Ws[jj][q];
             }
     }
     if (ok)
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
+        for (int q = 0; q < QN; ++q)
             if (i0 + q < qmax) U[(long long)(i0 + q) * ldu + r] = acc[q];
 }
 
@@ -679,9 +698,12 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
         double* MU = c->evec_perm.ptr + (size_t)N * qmax;
         {
             PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * qmax) * sizeof(double));
-            dim3 g(B.nch, (qmax + 15) / 16);
-            { count_launch(c); bgemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, U, N); }
-            { count_launch(c); bgemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, MU, N); }
+            const int qn = qmax <= 8 ? 8 : (qmax <= 16 ? 16 : (qmax <= 24 ? 24 : 32));
+            dim3 g(B.nch, (qmax + qn - 1) / qn);
+            auto kern = qn == 8 ? bgemm_ritz_kernel<8>
+                                : (qn == 16 ? bgemm_ritz_kernel<16> : (qn == 24 ? bgemm_ritz_kernel<24> : bgemm_ritz_kernel<32>));
+            { count_launch(c); kern<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, U, N); }
+            { count_launch(c); kern<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, MU, N); }
             RIGA_CUDA_TRY(c, B.rpart.alloc((size_t)2 * B.nch * qmax));
             { count_launch(c); bresid_kernel<<<dim3(B.nch, qmax), 256, 0, st>>>(c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N,
                                                                                B.lam.ptr, qmax, B.ch, B.rpart.ptr); }

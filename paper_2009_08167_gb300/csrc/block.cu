@@ -38,55 +38,74 @@ namespace riga {
 constexpr int BLK_MAX = 4;
 
 // Partial dots out[j*B + r] = sum over this chunk's rows of B_j[row] w_r[row]
-// (the basis tile staged through shared memory in HR-row pieces as in the
+// (the basis tile staged through shared memory in HR-row pieces, the next
+// piece loaded into registers while the current one is summed, as in the
 // single-vector kernels; every staged entry serves B products).
 template <int B>
 __device__ __forceinline__ void bchunk_dots(const double* __restrict__ Bm, long long ld, int J, long long r0, int rows,
                                             const double* __restrict__ ws, double* __restrict__ Vs,
                                             double* __restrict__ red, double* __restrict__ out) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j0 = 0; j0 < J; j0 += TJ) {
-        const int jn = min(TJ, J - j0);
-        double s[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) s[r] = 0.0;
-        for (int h = 0; h < rows; h += HR) {
-            const int hn = min(HR, rows - h);
-#pragma unroll
-            for (int q = 0; q < TJ / 8; ++q) {
-                const int jl = warp + 8 * q;
-                if (jl < jn) {
-                    const double* col = Bm + (long long)(j0 + jl) * ld + r0 + h;
-#pragma unroll
-                    for (int i = 0; i < HR / 32; ++i) {
-                        const int r = lane + 32 * i;
-                        if (r < hn) Vs[jl * (HR + 1) + r] = col[r];
-                    }
-                }
-            }
-            __syncthreads();
-            if (lane < jn) {
-                const double* vc = Vs + lane * (HR + 1);
-#pragma unroll 4
-                for (int i = warp; i < hn; i += 8) {
-                    const double v = vc[i];
-#pragma unroll
-                    for (int r = 0; r < B; ++r) s[r] += v * ws[r * CH + h + i];
-                }
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int r = 0; r < B; ++r) red[(warp * TJ + lane) * B + r] = s[r];
-        __syncthreads();
-        if (tid < jn * B) {
-            double t = 0.0;
-#pragma unroll
-            for (int g = 0; g < 8; ++g) t += red[g * TJ * B + tid];
-            out[j0 * B + tid] = t;
-        }
-        __syncthreads();
+    if (rows <= 0) {  // no rows (the same for the whole block): zero partials
+        for (int j = tid; j < J * B; j += blockDim.x) out[j] = 0.0;
+        return;
     }
+    const int nh = (rows + HR - 1) / HR;         // row pieces per column tile
+    const int nst = ((J + TJ - 1) / TJ) * nh;    // stages (column tile, row piece)
+    double pre[TJ / 8][HR / 32];                 // the next stage, loaded while this one computes
+    auto load = [&](int st) {
+        const int j0 = (st / nh) * TJ, h = (st % nh) * HR;
+        const int jn = min(TJ, J - j0), hn = min(HR, rows - h);
+#pragma unroll
+        for (int q = 0; q < TJ / 8; ++q) {
+            const int jl = warp + 8 * q;
+            const double* col = Bm + (long long)(j0 + jl) * ld + r0 + h;
+#pragma unroll
+            for (int i = 0; i < HR / 32; ++i) {
+                const int r = lane + 32 * i;
+                pre[q][i] = (jl < jn && r < hn) ? col[r] : 0.0;
+            }
+        }
+    };
+    load(0);
+    double s[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) s[r] = 0.0;
+    for (int st = 0; st < nst; ++st) {
+        const int j0 = (st / nh) * TJ, h = (st % nh) * HR;
+        const int jn = min(TJ, J - j0), hn = min(HR, rows - h);
+#pragma unroll
+        for (int q = 0; q < TJ / 8; ++q)
+#pragma unroll
+            for (int i = 0; i < HR / 32; ++i) Vs[(warp + 8 * q) * (HR + 1) + lane + 32 * i] = pre[q][i];
+        __syncthreads();
+        if (st + 1 < nst) load(st + 1);
+        if (lane < jn) {
+            const double* vc = Vs + lane * (HR + 1);
+#pragma unroll 4
+            for (int i = warp; i < hn; i += 8) {
+                const double v = vc[i];
+#pragma unroll
+                for (int r = 0; r < B; ++r) s[r] += v * ws[r * CH + h + i];
+            }
+        }
+        __syncthreads();
+        if (st % nh == nh - 1) {  // last piece of this column tile: sum the 8 row groups
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                red[(warp * TJ + lane) * B + r] = s[r];
+                s[r] = 0.0;
+            }
+            __syncthreads();
+            if (tid < jn * B) {
+                double t = 0.0;
+#pragma unroll
+                for (int g = 0; g < 8; ++g) t += red[g * TJ * B + tid];
+                out[j0 * B + tid] = t;
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // The tall-skinny kernels split the rows evenly over their blocks (at most

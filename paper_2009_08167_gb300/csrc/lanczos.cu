@@ -28,7 +28,8 @@ namespace riga {
 // Partial dots out[j] = sum_{r in chunk} B[j][r] ws[r] for j < J over one
 // chunk of at most CH rows.  Each 32-column tile is staged through shared
 // memory in HR-row pieces by coalesced column loads (the small pieces leave
-// room for six blocks per SM, whose loads overlap the others' arithmetic);
+// room for six blocks per SM); the next piece is loaded into registers while
+// the current one is summed;
 // thread (column jl, row group g) sums rows g, g+8, ... with one FP64 FMA per
 // element (GB300's FP64 pipe is the bound of these tall-skinny products), and
 // the 8 row groups are added through shared memory.
@@ -36,42 +37,58 @@ __device__ __forceinline__ void chunk_dots(const double* __restrict__ B, long lo
                                            const double* __restrict__ ws, double* __restrict__ Vs,
                                            double* __restrict__ red, double* __restrict__ out) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j0 = 0; j0 < J; j0 += TJ) {
-        const int jn = min(TJ, J - j0);
-        double s = 0.0;
-        for (int h = 0; h < rows; h += HR) {
-            const int hn = min(HR, rows - h);
-#pragma unroll
-            for (int q = 0; q < TJ / 8; ++q) {
-                const int jl = warp + 8 * q;
-                if (jl < jn) {
-                    const double* col = B + (long long)(j0 + jl) * ld + r0 + h;
-#pragma unroll
-                    for (int i = 0; i < HR / 32; ++i) {
-                        const int r = lane + 32 * i;
-                        if (r < hn) Vs[jl * (HR + 1) + r] = col[r];
-                    }
-                }
-            }
-            __syncthreads();
-            if (lane < jn) {
-                const double* vc = Vs + lane * (HR + 1);
-                const double* wh = ws + h;
-#pragma unroll 4
-                for (int r = warp; r < hn; r += 8) s += vc[r] * wh[r];
-            }
-            __syncthreads();
-        }
-        red[warp * TJ + lane] = s;
-        __syncthreads();
-        if (tid < jn) {
-            double t = 0.0;
-#pragma unroll
-            for (int gg = 0; gg < 8; ++gg) t += red[gg * TJ + tid];
-            out[j0 + tid] = t;
-        }
-        __syncthreads();
+    if (rows <= 0) {  // no rows (the same for the whole block): zero partials
+        for (int j = tid; j < J; j += blockDim.x) out[j] = 0.0;
+        return;
     }
+    const int nh = (rows + HR - 1) / HR;         // row pieces per column tile
+    const int nst = ((J + TJ - 1) / TJ) * nh;    // stages (column tile, row piece)
+    double pre[TJ / 8][HR / 32];                 // the next stage, loaded while this one computes
+    auto load = [&](int st) {
+        const int j0 = (st / nh) * TJ, h = (st % nh) * HR;
+        const int jn = min(TJ, J - j0), hn = min(HR, rows - h);
+#pragma unroll
+        for (int q = 0; q < TJ / 8; ++q) {
+            const int jl = warp + 8 * q;
+            const double* col = B + (long long)(j0 + jl) * ld + r0 + h;
+#pragma unroll
+            for (int i = 0; i < HR / 32; ++i) {
+                const int r = lane + 32 * i;
+                pre[q][i] = (jl < jn && r < hn) ? col[r] : 0.0;
+            }
+        }
+    };
+    if (nst > 0) load(0);
+    double s = 0.0;
+    for (int st = 0; st < nst; ++st) {
+        const int j0 = (st / nh) * TJ, h = (st % nh) * HR;
+        const int jn = min(TJ, J - j0), hn = min(HR, rows - h);
+#pragma unroll
+        for (int q = 0; q < TJ / 8; ++q)
+#pragma unroll
+            for (int i = 0; i < HR / 32; ++i) Vs[(warp + 8 * q) * (HR + 1) + lane + 32 * i] = pre[q][i];
+        __syncthreads();
+        if (st + 1 < nst) load(st + 1);
+        if (lane < jn) {
+            const double* vc = Vs + lane * (HR + 1);
+            const double* wh = ws + h;
+#pragma unroll 4
+            for (int r = warp; r < hn; r += 8) s += vc[r] * wh[r];
+        }
+        __syncthreads();
+        if (st % nh == nh - 1) {  // last piece of this column tile: sum the 8 row groups
+            red[warp * TJ + lane] = s;
+            s = 0.0;
+            __syncthreads();
+            if (tid < jn) {
+                double t = 0.0;
+#pragma unroll
+                for (int gg = 0; gg < 8; ++gg) t += red[gg * TJ + tid];
+                out[j0 + tid] = t;
+            }
+        }
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) gemvT_partial_kernel(const double* __restrict__ B, long long ld, int J,
