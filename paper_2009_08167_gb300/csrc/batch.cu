@@ -90,6 +90,40 @@ __device__ __forceinline__ void bchunk_dots(const double* __restrict__ B, long l
     __syncthreads();
 }
 
+// Partial dots of the recurrence: out[j] = sum over this chunk's rows of
+// B_j[row] w[row] for the JU = 1 or 2 columns of the last two vectors; 64
+// threads, four rows each, then the block's sum (every lane does useful
+// multiply-adds, unlike the 32-column tiles of the full pass)
+template <int JU>
+__global__ void __launch_bounds__(64) blocal_dots_kernel(const double* __restrict__ B, long long ld,
+                                                         const double* __restrict__ w, Chunks ch,
+                                                         double* __restrict__ partial, int pstride) {
+    __shared__ double red[2][JU];
+    const long long r0 = ch.row0[blockIdx.x];
+    const int rows = ch.rows[blockIdx.x];
+    double acc[JU];
+#pragma unroll
+    for (int j = 0; j < JU; ++j) acc[j] = 0.0;
+#pragma unroll
+    for (int i = 0; i < BCH / 64; ++i) {
+        const int rl = (int)threadIdx.x + 64 * i;
+        if (rl < rows) {
+            const double x = w[r0 + rl];
+#pragma unroll
+            for (int j = 0; j < JU; ++j) acc[j] += B[(long long)j * ld + r0 + rl] * x;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < JU; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < JU; ++j) red[threadIdx.x >> 5][j] = acc[j];
+    __syncthreads();
+    if ((int)threadIdx.x < JU) partial[(long long)blockIdx.x * pstride + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+}
+
 __global__ void __launch_bounds__(256) bgemvT_kernel(const double* __restrict__ B, long long ld, int J,
                                                      const double* __restrict__ w, Chunks ch,
                                                      double* __restrict__ partial, int pstride) {
@@ -431,8 +465,9 @@ void brecur(BatchState& B, int J, int u0, int Ju, double* w) {
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 1.0) * (double)B.N * sizeof(double), 4.0 * (double)B.N * (J + Ju));
     const size_t sm_dots = (size_t)(BCH + 8 * BTJ + BTJ * (BHR + 1)) * sizeof(double);
-    { count_launch(c); bgemvT_kernel<<<B.nch, 256, sm_dots, st>>>(c->MV.ptr + (long long)u0 * B.ld, B.ld, Ju, w, B.ch,
-                                                                 B.partial.ptr, B.cap); }
+    count_launch(c);
+    if (Ju == 2) blocal_dots_kernel<2><<<B.nch, 64, 0, st>>>(c->MV.ptr + (long long)u0 * B.ld, B.ld, w, B.ch, B.partial.ptr, B.cap);
+    else blocal_dots_kernel<1><<<B.nch, 64, 0, st>>>(c->MV.ptr + (long long)u0 * B.ld, B.ld, w, B.ch, B.partial.ptr, B.cap);
     { count_launch(c); bseg_reduce_kernel<<<dim3(1, B.P), 256, 0, st>>>(B.partial.ptr, B.cbeg.ptr, B.cend.ptr, Ju, B.cap,
                                                                        B.c1.ptr); }
     { count_launch(c); bupdate_gemvT_kernel<<<B.nch, 256, sm_dots + (size_t)Ju * sizeof(double), st>>>(

@@ -91,6 +91,38 @@ __device__ __forceinline__ void chunk_dots(const double* __restrict__ B, long lo
     __syncthreads();
 }
 
+// Partial dots of the recurrence over one chunk of CH rows: out[j] = sum of
+// B_j[row] w[row] for the JU = 1 or 2 columns of the last two vectors (64
+// threads, four rows each, then the block's sum)
+template <int JU>
+__global__ void __launch_bounds__(64) local_dots_kernel(const double* __restrict__ B, long long ld,
+                                                        const double* __restrict__ w, long long N,
+                                                        double* __restrict__ partial, int pstride) {
+    __shared__ double red[2][JU];
+    const long long r0 = (long long)blockIdx.x * CH;
+    double acc[JU];
+#pragma unroll
+    for (int j = 0; j < JU; ++j) acc[j] = 0.0;
+#pragma unroll
+    for (int i = 0; i < CH / 64; ++i) {
+        const long long r = r0 + threadIdx.x + 64 * i;
+        if (r < N) {
+            const double x = w[r];
+#pragma unroll
+            for (int j = 0; j < JU; ++j) acc[j] += B[(long long)j * ld + r] * x;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < JU; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int j = 0; j < JU; ++j) red[threadIdx.x >> 5][j] = acc[j];
+    __syncthreads();
+    if ((int)threadIdx.x < JU) partial[(long long)blockIdx.x * pstride + threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+}
+
 __global__ void __launch_bounds__(256) gemvT_partial_kernel(const double* __restrict__ B, long long ld, int J,
                                                             const double* __restrict__ w, long long N,
                                                             double* __restrict__ partial, int pstride) {
@@ -406,8 +438,9 @@ int recur_pass(Run& R, int J, int u0, int Ju, double* w) {
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_REORTH, (2.0 * J + 2.0 * Ju + 1.0) * (double)R.N * sizeof(double), 4.0 * (double)R.N * (J + Ju));
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
-    { count_launch(c); gemvT_partial_kernel<<<R.nch, 256, sm_dots, st>>>(c->MV.ptr + (long long)u0 * R.ld, R.ld, Ju, w, R.N,
-                                                                        c->partial.ptr, R.cap); }
+    count_launch(c);
+    if (Ju == 2) local_dots_kernel<2><<<R.nch, 64, 0, st>>>(c->MV.ptr + (long long)u0 * R.ld, R.ld, w, R.N, c->partial.ptr, R.cap);
+    else local_dots_kernel<1><<<R.nch, 64, 0, st>>>(c->MV.ptr + (long long)u0 * R.ld, R.ld, w, R.N, c->partial.ptr, R.cap);
     { count_launch(c); reduce_cols_kernel<<<1, 256, 0, st>>>(c->partial.ptr, R.nch, Ju, R.cap, R.c1 + u0); }
     size_t sm = sm_dots + (size_t)Ju * sizeof(double);
     { count_launch(c); update_gemvT_kernel<<<R.nch, 256, sm, st>>>(c->V.ptr + (long long)u0 * R.ld, Ju, R.c1 + u0, c->MV.ptr, J,
