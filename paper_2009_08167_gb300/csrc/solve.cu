@@ -464,8 +464,17 @@ __device__ __forceinline__ void warp_accumulate(const T* __restrict__ P, int ldp
     }
 }
 
+// Minimum resident blocks per SM of the warp kernel (a register budget per
+// instance): the FP64 single-column instance is held to 64 registers (8
+// blocks, 32 items per SM) without spilling; the others get the budgets they
+// fit without spilling.
 template <typename T, int NR>
-__global__ void __launch_bounds__(128) tree_solve_warp_kernel(const T* __restrict__ Q, TreeArgs a) {
+constexpr int warp_min_blocks() {
+    return sizeof(T) == 8 ? (NR == 1 ? 8 : (NR == 2 ? 5 : 4)) : (NR == 1 ? 10 : (NR == 2 ? 9 : 7));
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(128, warp_min_blocks<T, NR>()) tree_solve_warp_kernel(const T* __restrict__ Q, TreeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
