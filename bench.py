@@ -267,7 +267,7 @@ def roofline(prof):
     common = {"phase": dom, "ms_per_call": pr["ms"] / calls, "hbm_frac": f_hbm, "fp64_frac": f_alu}
     if pr["flops"] > 0 and f_alu >= f_hbm:
         return dict({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
-                     "traffic": None, "peak_source": "nominal fp64 (2 DFMA/clock/SM, 2.07 GHz)",
+                     "traffic": ncu_traffic(dom), "peak_source": "nominal fp64 (2 DFMA/clock/SM, 2.07 GHz)",
                      "algorithmic_flops_per_call": pr["flops"] / calls}, **common)
     return dict({"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
                  "traffic": ncu_traffic(dom), "peak_source": pk_kind,
