@@ -170,23 +170,32 @@ def ncu_traffic(phase):
 
 
 # ------------------------------------------------------------- oracle leg
-def oracle_sample():
+def oracle_sample(cfg):
     """The FP64 oracle as it stands (shift-invert Lanczos with banded LDL^T)
-    on a bounded sample: the same 2D p=3 rIGA family (C0 lines every 16
-    elements) at 48x48 elements, 100 eigenpairs.  Returns (pairs/s, seconds,
-    description)."""
+    on a bounded sample of the workload's family: 2D meshes at 48x48 elements
+    with the workload's degree and C0 lines (100 pairs); 3D meshes at 10^3
+    elements with the workload's degree and C0 planes (up to 50 pairs; the
+    banded 3D factorization grows too fast for larger samples).  Returns
+    (pairs/s, seconds, description)."""
     import numpy as np
     from oracle import assembly, eigen
     from paper_2009_08167_gb300.inputs import Mesh
-    m = Mesh(2, 48, 3, 16)
+    w = cfg["mesh"]
+    if w.dim == 3:
+        m, k = Mesh(3, 10, w.p, w.bs), min(int(cfg["k"]), 50)
+        shape = "10x10x10"
+    else:
+        m, k = Mesh(2, 48, w.p, w.bs), 100
+        shape = "48x48"
+    fam = f"rIGA bs{w.bs}" if w.bs else "IGA"
     t0 = time.perf_counter()
-    K, M = assembly.assemble_kron(2, m.ne, m.p, m.mults)
-    lam, U, info = eigen.lanczos_shift_invert(K, M, 100, 0.0, tol=1e-12, seed=1)
+    K, M = assembly.assemble_kron(m.dim, m.ne, m.p, m.mults)
+    lam, U, info = eigen.lanczos_shift_invert(K, M, k, 0.0, tol=1e-12, seed=1)
     rho = eigen.residual_rho(K, M, lam, U)
     dt = time.perf_counter() - t0
     ok = int(np.sum(rho <= RESID_TOL))
-    desc = (f"oracle shift-invert Lanczos + banded LDL^T, 2D p=3 rIGA bs16 at 48x48 elements (N={K.n}), "
-            f"{ok} of 100 pairs at resid<=1e-10, {dt:.1f} s, 1 thread of numpy/BLAS")
+    desc = (f"oracle shift-invert Lanczos + banded LDL^T, {m.dim}D p={m.p} {fam} at {shape} elements (N={K.n}), "
+            f"{ok} of {k} pairs at resid<=1e-10, {dt:.1f} s, 1 thread of numpy/BLAS")
     return ok / dt, dt, desc
 
 
@@ -226,7 +235,7 @@ def run_reference(args, rank, world):
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     cfg = workload(args.mesh)
-    sample = (lambda: oracle_sample_batch(cfg)) if cfg.get("batch") else oracle_sample
+    sample = (lambda: oracle_sample_batch(cfg)) if cfg.get("batch") else (lambda: oracle_sample(cfg))
     for _ in range(args.warmup):
         sample()
     vals, secs = [], []
@@ -554,7 +563,7 @@ def run_riga(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
-        v, dt, desc = oracle_sample()
+        v, dt, desc = oracle_sample(cfg)
         cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": desc}
 
     if rank == 0:
