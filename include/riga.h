@@ -256,15 +256,32 @@ int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int
  * the single-vector recurrence of Sec. 4.1-4.2; 2 or 4 run block Lanczos:
  * each step applies the shift-inverted operator to a block of vectors with
  * one traversal of the factor (riga_solve's grouping), orthogonalises the
- * block against all previous vectors (two classical Gram-Schmidt passes in
- * the M-inner product) and M-orthonormalises it (Cholesky QR, twice); the
- * Rayleigh-Ritz step uses the block-tridiagonal T_m (riga_band_eig).
+ * block against all previous vectors in the M-inner product (as set by
+ * riga_set_reorth) and M-orthonormalises it (shifted Cholesky QR, three
+ * passes); the Rayleigh-Ritz step uses the block-tridiagonal T_m
+ * (riga_band_eig).
  * Eigenvalues of multiplicity up to the block size appear in one run.  0
  * selects 4.  When a batch's solve kernel cannot carry that many right-hand
  * sides per item, the size falls back to what it can (possibly 1).
  * Errors: RIGA_EINVAL.
  */
 int riga_set_eig_block(riga_ctx* ctx, int block);
+
+/*
+ * riga_set_reorth: how riga_eigs and riga_eigs_batch orthogonalise each new
+ * Lanczos vector (block) against all stored ones, in the M-inner product
+ * (Sec. 4.2: orthogonalisation against all previously stored vectors).
+ *  passes = 1 (the default): the three-term recurrence with its
+ *    coefficients computed against the last two vectors (blocks), then one
+ *    classical Gram-Schmidt pass against every stored vector; when that pass
+ *    removes more than 100 times the norm that remains, the eigensolution
+ *    switches to passes = 2 by itself.
+ *  passes = 2: two full classical Gram-Schmidt passes (CGS2) every step
+ *    (twice the FP64 work of the orthogonalisation).
+ * The setting holds for later riga_eigs / riga_eigs_batch calls on ctx.
+ * Errors: RIGA_EINVAL (ctx NULL, passes not 1 or 2).
+ */
+int riga_set_reorth(riga_ctx* ctx, int passes);
 
 /*
  * riga_eig_grad: gradient of L = sum_i dL_dlambda[i] lambda_i over the k

@@ -370,6 +370,13 @@ int riga_set_eig_block(riga_ctx* c, int block) {
     return RIGA_OK;
 }
 
+int riga_set_reorth(riga_ctx* c, int passes) {
+    if (!c) return RIGA_EINVAL;
+    if (passes != 1 && passes != 2) return set_error(c, RIGA_EINVAL, "passes must be 1 or 2");
+    c->opt_reorth = passes;
+    return RIGA_OK;
+}
+
 int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, double* evecs, double* resid, int* nconv) {
     if (!c || !evals) return RIGA_EINVAL;
     if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");

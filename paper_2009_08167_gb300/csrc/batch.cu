@@ -538,6 +538,7 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     B.ld = N;
     B.cap = lock_cap + m_cap + 1;
     B.mcap = m_cap;
+    B.cgs2 = c->opt_reorth == 2;
     // row chunks inside problems
     std::vector<long long> r0;
     std::vector<int> rw, pb;

@@ -850,6 +850,13 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
         std::vector<int> ord;
         for (int i = 0; i < mm * B; ++i)
             if (acceptable(theta[i])) ord.push_back(i);
+        if (dbg) {  // leading acceptable Ritz values whose estimates meet the bar
+            std::vector<int> o2(ord);
+            std::sort(o2.begin(), o2.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
+            int lead = 0;
+            while (lead < (int)o2.size() && est[o2[lead]] <= tol_est * std::fabs(theta[o2[lead]])) ++lead;
+            std::fprintf(stderr, "[riga] block check: steps=%d acceptable=%zu leading converged=%d\n", mm * B, o2.size(), lead);
+        }
         if ((int)ord.size() < want_run) return false;
         std::sort(ord.begin(), ord.end(), [&](int x, int y) { return std::fabs(theta[x]) > std::fabs(theta[y]); });
         const double* bm = hB + (size_t)mm * B * B;

@@ -636,6 +636,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     }
     R.alpha = c->ab.ptr;
     R.beta = c->ab.ptr + m_cap + 2;
+    R.cgs2 = c->opt_reorth == 2;
     c->stats = Stats();
 
     std::vector<double> lam;      // locked eigenvalues, in column order of V

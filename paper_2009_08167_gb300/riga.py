@@ -85,6 +85,7 @@ def load_library(path=LIB_PATH):
     lib.riga_assemble_batch.argtypes = [P, I, ctypes.POINTER(_MeshC), P, P]
     lib.riga_band_eig.argtypes = [I, I, P, P, I, P, P, I, P]
     lib.riga_set_eig_block.argtypes = [P, I]
+    lib.riga_set_reorth.argtypes = [P, I]
     lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
     lib.riga_get_symbolic.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(LL), P, P, P, P, P]
@@ -266,6 +267,11 @@ class Riga:
 
     def set_eig_block(self, block):
         self._check(self.lib.riga_set_eig_block(self.ctx, int(block)))
+
+    def set_reorth(self, passes):
+        """1: recurrence + one full Gram-Schmidt pass (switching to 2 by itself
+        when one pass is not enough); 2: two full passes every step."""
+        self._check(self.lib.riga_set_reorth(self.ctx, int(passes)))
 
     # ------------------------------------------------------------ riga_eigs
     def eigs(self, k, sigma=0.0, tol=1e-10, vectors=True, device_out=False):
