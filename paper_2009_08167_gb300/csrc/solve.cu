@@ -799,11 +799,15 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
 // stays short and the groups share the panels in L2.  Batches of many trees
 // (bound by items in flight): up to four columns share each item and each
 // panel read.
+// Columns that share each item in the 128-thread (2D tree) solve when a
+// call carries several right-hand sides (1: interleaved groups instead).
+constexpr int SMALL_COMBINED = 1;
+
 int enqueue_solve(riga_ctx* c, double* y, int nrhs) {
     if (!c->factored) return set_error(c, RIGA_ESTATE, "no factorization");
     Symbolic& S = c->S;
-    const bool split = S.solve_mode != SOLVE_WARP;
-    const int maxr = split ? 1 : solve_max_rhs(c);
+    const bool split = S.solve_mode == SOLVE_CTA256 || (S.solve_mode == SOLVE_CTA128 && SMALL_COMBINED == 1);
+    const int maxr = split ? 1 : std::min(S.solve_mode == SOLVE_CTA128 ? SMALL_COMBINED : 4, solve_max_rhs(c));
     const int width = split ? std::min(std::max(1, nrhs), 8) : std::min(std::max(1, nrhs), maxr);
     RIGA_CUDA_TRY(c, c->upd.alloc((S.upd_size > 0 ? S.upd_size : 1) * (size_t)width));
     RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes * width + 1));
