@@ -334,6 +334,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
     R = riga.Riga(local_rank, stream)
     R.set_eig_options(extra=2, seed=11)
     R.assemble_batch(meshes, cK)  # symbolic analysis of every pattern: once, untimed
+    tuned_trail, tuned_ms = R.autotune()  # front tile shapes for this batch: once, untimed
     q = R.query()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -415,6 +416,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
             "converged_pairs": pairs, "max_resid": float(np.nanmax(rs)),
             "e2e": {"value": e2e_val, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "roofline": roof, "fronts": fronts, "phases_ms_one_step": phases,
+            "autotune": {"small_trail": tuned_trail, "factor_ms_per_candidate": dict(zip([0, 64, 128, 256, 512, 1024], tuned_ms))},
             "assembly_ms": statistics.median(asm_ms),
             "counts_per_step": {"n_fact": st["n_fact"], "n_solve": st["n_solve"], "n_matvec": st["n_matvec"],
                                 "lanczos_steps": st["lanczos_steps"]},

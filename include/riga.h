@@ -268,6 +268,25 @@ int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int
 int riga_set_eig_block(riga_ctx* ctx, int block);
 
 /*
+ * riga_autotune: choose the factorization's update-tile shapes for the
+ * assembled pattern (a single problem or a batch) by measurement.  Trailing
+ * blocks of at most T rows are updated in 16x16 tiles and larger ones in
+ * 32x32 tiles; for T in {0, 64, 128, 256, 512, 1024} the FP64 factorization at sigma = 0
+ * (with the solve operators) is run twice and timed with CUDA events on the
+ * ctx's stream, and the fastest T is kept for later factorizations of this
+ * pattern (a new pattern starts again from T = 128).  The tile shape changes
+ * no result: every entry's update sums the same products in the same order.
+ *  small_trail_out (may be NULL): HOST out, the chosen T.
+ *  ms_out[6] (may be NULL): HOST out, the second run's time for each T in
+ *    the order above.
+ * On return the ctx holds the FP64 factorization at sigma = 0 (as after
+ * riga_factor(ctx, 0, RIGA_FP64, ...)).
+ * Errors: RIGA_EINVAL (ctx NULL), RIGA_ESTATE (nothing assembled), and the
+ * errors of riga_factor.
+ */
+int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
+
+/*
  * riga_set_reorth: how riga_eigs and riga_eigs_batch orthogonalise each new
  * Lanczos vector (block) against all stored ones, in the M-inner product
  * (Sec. 4.2: orthogonalisation against all previously stored vectors).

@@ -309,6 +309,67 @@ int riga_factor(riga_ctx* c, double sigma, int precision, long long* n_neg) {
     return rc;
 }
 
+// Re-upload the factorization's level schedule (after build_schedule)
+static int upload_schedule(riga_ctx* c) {
+    Symbolic& S = c->S;
+    cudaStream_t st = c->stream;
+    RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
+    RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
+    RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.tc_titems, st));
+    RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
+    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return RIGA_OK;
+}
+
+int riga_autotune(riga_ctx* c, int* small_trail_out, double* ms_out) {
+    if (!c) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    static const int cand[6] = {0, 64, 128, 256, 512, 1024};
+    cudaEvent_t e0, e1;
+    RIGA_CUDA_TRY(c, cudaEventCreate(&e0));
+    RIGA_CUDA_TRY(c, cudaEventCreate(&e1));
+    int best = c->S.small_trail;
+    double best_ms = 1e300;
+    int rc = RIGA_OK;
+    for (int i = 0; i < 6 && rc == RIGA_OK; ++i) {
+        c->S.small_trail = cand[i];
+        build_schedule(c->S);
+        rc = upload_schedule(c);
+        double ms = 1e300;
+        for (int rep = 0; rep < 2 && rc == RIGA_OK; ++rep) {  // the first run also sizes the pools
+            c->sigma = 0.0;
+            c->sigma_prob.clear();
+            c->precision = RIGA_FP64;
+            c->inertia_only = false;
+            c->factored = false;
+            cudaEventRecord(e0, c->stream);
+            rc = enqueue_factor(c);
+            if (rc == RIGA_OK) {
+                cudaEventRecord(e1, c->stream);
+                rc = finish_factor(c);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = t;
+            }
+        }
+        if (ms_out) ms_out[i] = ms;
+        if (rc == RIGA_OK && ms < best_ms) {
+            best_ms = ms;
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->S.small_trail = best;
+    build_schedule(c->S);
+    const int rc2 = upload_schedule(c);
+    if (small_trail_out) *small_trail_out = best;
+    return rc ? rc : rc2;
+}
+
 int riga_solve(riga_ctx* c, const double* b, double* x, int nrhs, double tol, int* iters_out) {
     if (!c || !b || !x || nrhs < 1) return RIGA_EINVAL;
     if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");

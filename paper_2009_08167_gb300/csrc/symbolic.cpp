@@ -232,7 +232,15 @@ std::string finish_symbolic(Symbolic& S) {
         S.q_size = off;
     }
 
-    // ---------------------------------------------------- level schedule
+    build_schedule(S);
+    return "";
+}
+
+// Level schedule of the blocked partial LDL^T: per tree level the extend-add
+// items, and per panel step the diagonal-block, row-block and trailing-update
+// tile items (the update tiles' shape follows S.small_trail).
+void build_schedule(Symbolic& S) {
+    const int F = S.n_nodes;
     S.levels.assign(S.n_levels, LevelPlan());
     for (int f = 0; f < F; ++f) S.levels[S.height[f]].nodes.push_back(f);
     S.pitems.clear();
@@ -240,7 +248,7 @@ std::string finish_symbolic(Symbolic& S) {
     S.tc_titems.clear();
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
-    const int SMALL_TRAIL = 128;
+    const int SMALL_TRAIL = S.small_trail;
     const int ext_cols = 32;
     for (int l = 0; l < S.n_levels; ++l) {
         LevelPlan& P = S.levels[l];
@@ -277,9 +285,9 @@ std::string finish_symbolic(Symbolic& S) {
             R.p_end = (int)S.pitems.size();
             // trailing update: lower tiles of the augmented front, plus the
             // upper tiles of the extra x extra block so that -A11^{-1} is
-            // stored in full.  Trailing blocks of at most SMALL_TRAIL rows take
-            // 16x16 tiles (less padding on the diagonal and the edges of small
-            // fronts), larger ones 32x32 tiles.
+            // stored in full.  Trailing blocks of at most S.small_trail rows
+            // take 16x16 tiles (less padding on the diagonal and the edges of
+            // small fronts), larger ones 32x32 tiles.
             R.t_begin = (int)S.titems.size();
             for (int pass = 0; pass < 2; ++pass) {
                 if (pass == 1) R.t_mid = (int)S.titems.size();
@@ -317,7 +325,6 @@ std::string finish_symbolic(Symbolic& S) {
             P.steps.push_back(R);
         }
     }
-    return "";
 }
 
 std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int* const* mult,

@@ -128,6 +128,7 @@ struct Symbolic {
 
     // factorization schedule
     int nb = 32, tile = 32, rowblk = 64;
+    int small_trail = 128;            // trailing blocks of at most this many rows take 16x16 update tiles
     std::vector<LevelPlan> levels;
     std::vector<PanelItem> pitems;
     std::vector<TileItem> titems;
@@ -154,6 +155,7 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
                            int leaf_extent);
 // Heights, counts, schedule and solve items from nodes, fronts and maps.
 std::string finish_symbolic(Symbolic& S);
+void build_schedule(Symbolic& S);  // the factorization's level schedule (after finish_symbolic)
 // Merges independent problems into one forest (dim = 0 marks a batch).
 std::string merge_symbolic(Symbolic& M, const std::vector<Symbolic>& P);
 

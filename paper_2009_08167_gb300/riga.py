@@ -86,6 +86,7 @@ def load_library(path=LIB_PATH):
     lib.riga_band_eig.argtypes = [I, I, P, P, I, P, P, I, P]
     lib.riga_set_eig_block.argtypes = [P, I]
     lib.riga_set_reorth.argtypes = [P, I]
+    lib.riga_autotune.argtypes = [P, P, P]
     lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
     lib.riga_get_symbolic.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(LL), P, P, P, P, P]
@@ -267,6 +268,15 @@ class Riga:
 
     def set_eig_block(self, block):
         self._check(self.lib.riga_set_eig_block(self.ctx, int(block)))
+
+    def autotune(self):
+        """Measured choice of the factorization's update-tile shapes for the
+        assembled pattern; returns (chosen cut-off, [ms per candidate 0, 64,
+        128, 256, 512, 1024]).  Leaves the FP64 factorization at sigma = 0."""
+        t = ctypes.c_int(0)
+        ms = (ctypes.c_double * 6)()
+        self._check(self.lib.riga_autotune(self.ctx, ctypes.byref(t), ms))
+        return t.value, list(ms)
 
     def set_reorth(self, passes):
         """1: recurrence + one full Gram-Schmidt pass (switching to 2 by itself

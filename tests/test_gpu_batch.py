@@ -184,3 +184,25 @@ def test_batch_c4_full(R):
         K, M = oracle_matrices(meshes[b], cK[b], None)
         lam, _, _ = eigen.lanczos_shift_invert(K, M, k, 0.0, tol=1e-12, seed=3)
         assert np.max(np.abs(ev[b] - lam) / lam) <= 1e-10, b
+
+
+def test_autotune_tile_shapes_change_no_result(R):
+    """riga_autotune times the factorization for each tile cut-off and keeps
+    the fastest; every entry's update sums the same products in the same
+    order whatever the tile shape, so the pivots are bit-identical, and the
+    batch's eigenpairs still match the oracle."""
+    meshes, cK = _small_batch()
+    R.assemble_batch(meshes, cK)
+    R.factor(0.0)
+    D0 = R.get_factor()[0].copy()
+    t, ms = R.autotune()
+    assert t in (0, 64, 128, 256, 512, 1024)
+    assert all(m > 0.0 for m in ms)
+    assert np.array_equal(R.get_factor()[0], D0)
+    k = 8
+    ev, rs, nc = R.eigs_batch(k, 0.0, 1e-12)
+    assert np.all(nc == k)
+    assert np.all(rs <= 1e-10)
+    for b, (K, M) in enumerate(_block_oracle(meshes, cK)):
+        lam = eigen.ghep_dense(K.todense(), M.todense())[0][:k]
+        assert np.max(np.abs(ev[b] - lam) / lam) <= 1e-10, b
