@@ -272,13 +272,14 @@ int riga_set_eig_block(riga_ctx* ctx, int block);
  * assembled pattern (a single problem or a batch) by measurement.  Trailing
  * blocks of at most T rows are updated in 16x16 tiles and larger ones in
  * 32x32 tiles; for T in {0, 64, 128, 256, 512, 1024} the FP64 factorization at sigma = 0
- * (with the solve operators) is run twice and timed with CUDA events on the
- * ctx's stream, and the fastest T is kept for later factorizations of this
+ * (with the solve operators) is run four times and the last three are timed
+ * with CUDA events on the ctx's stream, and the T of the smallest median is
+ * kept for later factorizations of this
  * pattern (a new pattern starts again from T = 128).  The tile shape changes
  * no result: every entry's update sums the same products in the same order.
  *  small_trail_out (may be NULL): HOST out, the chosen T.
- *  ms_out[6] (may be NULL): HOST out, the second run's time for each T in
- *    the order above.
+ *  ms_out[6] (may be NULL): HOST out, the median time for each T in the
+ *    order above.
  * On return the ctx holds the FP64 factorization at sigma = 0 (as after
  * riga_factor(ctx, 0, RIGA_FP64, ...)).
  * Errors: RIGA_EINVAL (ctx NULL), RIGA_ESTATE (nothing assembled), and the

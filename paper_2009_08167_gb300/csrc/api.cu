@@ -88,6 +88,7 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    ++c->sched_gen;
     return RIGA_OK;
 }
 
@@ -186,6 +187,9 @@ void riga_destroy(riga_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->bpin) cudaFreeHost(c->bpin);
+    for (auto& g : c->fgraph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -318,6 +322,7 @@ static int upload_schedule(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.tc_titems, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    ++c->sched_gen;
     return RIGA_OK;
 }
 
@@ -338,8 +343,8 @@ int riga_autotune(riga_ctx* c, int* small_trail_out, double* ms_out) {
         c->S.small_trail = cand[i];
         build_schedule(c->S);
         rc = upload_schedule(c);
-        double ms = 1e300;
-        for (int rep = 0; rep < 2 && rc == RIGA_OK; ++rep) {  // the first run also sizes the pools
+        std::vector<double> t3;
+        for (int rep = 0; rep < 4 && rc == RIGA_OK; ++rep) {  // the first run also sizes the pools
             c->sigma = 0.0;
             c->sigma_prob.clear();
             c->precision = RIGA_FP64;
@@ -352,9 +357,11 @@ int riga_autotune(riga_ctx* c, int* small_trail_out, double* ms_out) {
                 rc = finish_factor(c);
                 float t = 0.f;
                 cudaEventElapsedTime(&t, e0, e1);
-                ms = t;
+                if (rep > 0) t3.push_back(t);
             }
         }
+        std::sort(t3.begin(), t3.end());
+        const double ms = t3.size() == 3 ? t3[1] : 1e300;  // median of three
         if (ms_out) ms_out[i] = ms;
         if (rc == RIGA_OK && ms < best_ms) {
             best_ms = ms;

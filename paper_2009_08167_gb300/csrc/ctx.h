@@ -156,6 +156,17 @@ struct riga_ctx {
     riga::DevBuf<long long> neg; // inertia counter(s): one, or one per problem of a batch
     riga::DevBuf<int> prob_of_pos;  // batch: problem of each position
     riga::DevBuf<double> sig_pos;   // batch: shift of each position's problem
+    // batch factorization as a CUDA graph (per-position shifts come from
+    // sig_pos, so one graph per mode serves every call): [0] with the solve
+    // operators, [1] inertia only; valid while the schedule and buffers are
+    struct FactorGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long gen = -1;
+        const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        int launches = 0;
+    } fgraph[2];
+    long long sched_gen = 0;            // bumped whenever the factorization schedule is uploaded
+    cudaStream_t cap_stream = nullptr;  // private stream for graph capture
     std::vector<long long> inertia_prob;  // batch: inertia per problem
     long long inertia = -1;
 

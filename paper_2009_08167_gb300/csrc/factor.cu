@@ -286,10 +286,61 @@ __global__ void inertia_kernel(long long N, const double* __restrict__ D, long l
 }
 
 template <typename T>
+static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st);
+
+// The factorization's launches.  A batch with per-problem shifts (read from
+// device memory) replays them as one CUDA graph per mode, captured on the
+// first call on a private stream and launched into the ctx's stream; the
+// graph is rebuilt when the schedule or a buffer it uses changes.
+template <typename T>
 static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     PhaseScope scope(c, PH_FACTOR, 0.0, c->inertia_only ? S.flops : S.flops + S.flops_aug);
+    const bool per_problem = (S.dim == 0) && !c->sigma_prob.empty();
+    if (per_problem) {
+        std::vector<double> sp(S.N);
+        for (size_t b = 0; b + 1 < S.prob_pos.size(); ++b)
+            for (long long i = S.prob_pos[b]; i < S.prob_pos[b + 1]; ++i) sp[i] = c->sigma_prob[b];
+        RIGA_CUDA_TRY(c, c->sig_pos.upload(sp, st));
+    }
+    if (!per_problem || sizeof(T) != sizeof(double)) return enqueue_factor_body<T>(c, pool, Q, st);
+    riga_ctx::FactorGraph& g = c->fgraph[c->inertia_only ? 1 : 0];
+    const void* ptrs[6] = {pool, Q, c->D.ptr, c->flag.ptr, c->neg.ptr, c->sig_pos.ptr};
+    bool valid = g.exec && g.gen == c->sched_gen;
+    for (int i = 0; i < 6 && valid; ++i) valid = g.ptrs[i] == ptrs[i];
+    if (!valid) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        if (!c->cap_stream) RIGA_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        RIGA_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = c->prof.launches;
+        int rc = enqueue_factor_body<T>(c, pool, Q, c->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (rc == RIGA_OK && e != cudaSuccess) rc = set_error(c, RIGA_ECUDA, cudaGetErrorString(e));
+        if (rc == RIGA_OK && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+            g.exec = nullptr;
+            rc = set_error(c, RIGA_ECUDA, "factorization graph");
+        }
+        if (graph) cudaGraphDestroy(graph);
+        const int launches = (int)(c->prof.launches - l0);
+        c->prof.launches = l0;  // counted when the graph runs
+        c->prof.ph[PH_FACTOR].launches -= launches;
+        if (rc) return rc;
+        g.gen = c->sched_gen;
+        for (int i = 0; i < 6; ++i) g.ptrs[i] = ptrs[i];
+        g.launches = launches;
+    }
+    RIGA_CUDA_TRY(c, cudaGraphLaunch(g.exec, st));
+    c->prof.launches += g.launches;
+    c->prof.ph[PH_FACTOR].launches += g.launches;
+    return RIGA_OK;
+}
+
+template <typename T>
+static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
+    Symbolic& S = c->S;
     RIGA_CUDA_TRY(c, cudaMemsetAsync(pool, 0, (size_t)S.pool_size * sizeof(T), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
@@ -302,10 +353,6 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
     if (!plain) { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
     const bool per_problem = (S.dim == 0) && !c->sigma_prob.empty();
     if (per_problem) {
-        std::vector<double> sp(S.N);
-        for (size_t b = 0; b + 1 < S.prob_pos.size(); ++b)
-            for (long long i = S.prob_pos[b]; i < S.prob_pos[b + 1]; ++i) sp[i] = c->sigma_prob[b];
-        RIGA_CUDA_TRY(c, c->sig_pos.upload(sp, st));
         { count_launch(c); scatter_rows_kernel<T><<<(unsigned)((S.N * 32 + 255) / 256), 256, 0, st>>>(
             S.N, c->rowptr.ptr, c->scatter.ptr, c->Kval.ptr, c->Mval.ptr, c->sig_pos.ptr, pool); }
     } else if (S.nnz > 0) {
