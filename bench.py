@@ -416,7 +416,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
             "converged_pairs": pairs, "max_resid": float(np.nanmax(rs)),
             "e2e": {"value": e2e_val, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "roofline": roof, "fronts": fronts, "phases_ms_one_step": phases,
-            "autotune": {"small_trail": tuned_trail, "factor_ms_per_candidate": dict(zip([0, 64, 128, 256, 512, 1024], tuned_ms))},
+            "autotune": {"small_trail": tuned_trail, "factor_ms_per_candidate": dict(zip([0, 128, 256, 512, 1024, 4096], tuned_ms))},
             "assembly_ms": statistics.median(asm_ms),
             "counts_per_step": {"n_fact": st["n_fact"], "n_solve": st["n_solve"], "n_matvec": st["n_matvec"],
                                 "lanczos_steps": st["lanczos_steps"]},
@@ -451,6 +451,12 @@ def run_riga(args, rank, world, local_rank):
     R.assemble(mesh)  # symbolic analysis: once per pattern, untimed
     q = R.query()
     N = q["N"]
+    # front tile shapes by measurement (untimed setup), where the factorization
+    # is cheap enough to run 24 times (2D; the 3D mesh keeps the default)
+    tuned = None
+    if q["flops_fact"] < 1e11:
+        t, tms = R.autotune()
+        tuned = {"small_trail": t, "factor_ms_per_candidate": dict(zip([0, 128, 256, 512, 1024, 4096], tms))}
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -581,6 +587,7 @@ def run_riga(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "roofline": roof,
             "fronts": fronts,
+            "autotune": tuned,
             "assembly_ms": statistics.median(asm_ms),
             "mixed_path": mixed,
             "phases_ms_one_step": phases,

@@ -332,7 +332,7 @@ int riga_autotune(riga_ctx* c, int* small_trail_out, double* ms_out) {
     c->last_error.clear();
     cudaSetDevice(c->device);
     if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
-    static const int cand[6] = {0, 64, 128, 256, 512, 1024};
+    static const int cand[6] = {0, 128, 256, 512, 1024, 4096};
     cudaEvent_t e0, e1;
     RIGA_CUDA_TRY(c, cudaEventCreate(&e0));
     RIGA_CUDA_TRY(c, cudaEventCreate(&e1));

@@ -271,8 +271,8 @@ class Riga:
 
     def autotune(self):
         """Measured choice of the factorization's update-tile shapes for the
-        assembled pattern; returns (chosen cut-off, [ms per candidate 0, 64,
-        128, 256, 512, 1024]).  Leaves the FP64 factorization at sigma = 0."""
+        assembled pattern; returns (chosen cut-off, [ms per candidate 0, 128,
+        256, 512, 1024, 4096]).  Leaves the FP64 factorization at sigma = 0."""
         t = ctypes.c_int(0)
         ms = (ctypes.c_double * 6)()
         self._check(self.lib.riga_autotune(self.ctx, ctypes.byref(t), ms))
