@@ -275,7 +275,7 @@ int riga_set_eig_block(riga_ctx* ctx, int block);
  * (with the solve operators) is run four times and the last three are timed
  * with CUDA events on the ctx's stream, and the T of the smallest median is
  * kept for later factorizations of this
- * pattern (a new pattern starts again from T = 128).  The tile shape changes
+ * pattern (a new pattern starts again from T = 1024, the default).  The tile shape changes
  * no result: every entry's update sums the same products in the same order.
  *  small_trail_out (may be NULL): HOST out, the chosen T.
  *  ms_out[6] (may be NULL): HOST out, the median time for each T in the

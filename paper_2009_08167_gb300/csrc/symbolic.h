@@ -128,7 +128,7 @@ struct Symbolic {
 
     // factorization schedule
     int nb = 32, tile = 32, rowblk = 64;
-    int small_trail = 128;            // trailing blocks of at most this many rows take 16x16 update tiles
+    int small_trail = 1024;            // trailing blocks of at most this many rows take 16x16 update tiles
     std::vector<LevelPlan> levels;
     std::vector<PanelItem> pitems;
     std::vector<TileItem> titems;
