@@ -271,11 +271,11 @@ int riga_set_eig_block(riga_ctx* ctx, int block);
  * riga_autotune: choose the factorization's update-tile shapes for the
  * assembled pattern (a single problem or a batch) by measurement.  Trailing
  * blocks of at most T rows are updated in 16x16 tiles and larger ones in
- * 32x32 tiles; for T in {0, 128, 256, 512, 1024, 4096} the FP64 factorization at sigma = 0
- * (with the solve operators) is run four times and the last three are timed
- * with CUDA events on the ctx's stream, and the T of the smallest median is
- * kept for later factorizations of this
- * pattern (a new pattern starts again from T = 1024, the default).  The tile shape changes
+ * 32x32 tiles; for T in {0, 128, 256, 512, 1024, 4096} the FP64
+ * factorization at sigma = 0 (with the solve operators) is run four times,
+ * the last three timed with CUDA events on the ctx's stream, and the T of the
+ * smallest median is kept for later factorizations of this pattern (a new
+ * pattern starts again from T = 1024, the default).  The tile shape changes
  * no result: every entry's update sums the same products in the same order.
  *  small_trail_out (may be NULL): HOST out, the chosen T.
  *  ms_out[6] (may be NULL): HOST out, the median time for each T in the
