@@ -129,3 +129,20 @@ def test_host_context_refuses_device_calls():
     with pytest.raises(RigaError) as e:
         r.factor(0.0)
     assert e.value.code == RIGA_ESTATE
+
+
+def test_host_context_options_and_autotune():
+    """riga_set_reorth validates its argument on any context; riga_autotune
+    needs a device context (RIGA_ESTATE on a host-only one)."""
+    from paper_2009_08167_gb300.riga import RigaError, RIGA_EINVAL, RIGA_ESTATE
+    r = _host_ctx()
+    r.analyze(Mesh(2, 8, 2, None))
+    r.set_reorth(1)
+    r.set_reorth(2)
+    for bad in (0, 3):
+        with pytest.raises(RigaError) as e:
+            r.set_reorth(bad)
+        assert e.value.code == RIGA_EINVAL
+    with pytest.raises(RigaError) as e:
+        r.autotune()
+    assert e.value.code == RIGA_ESTATE
