@@ -17,6 +17,21 @@
 
 namespace riga {
 
+namespace {
+// sqrt(x^2 + y^2) for the rotations: the plain formula (the library hypot
+// costs several times more and the iteration makes O(m^2) rotations), scaled
+// only when the squares could leave the double range
+inline double rot_norm(double x, double y) {
+    const double ax = std::fabs(x), ay = std::fabs(y);
+    const double mx = ax > ay ? ax : ay;
+    if (mx > 1e150 || (mx < 1e-150 && mx > 0.0)) {
+        const double a = ax / mx, b = ay / mx;
+        return mx * std::sqrt(a * a + b * b);
+    }
+    return std::sqrt(x * x + y * y);
+}
+}  // namespace
+
 // General form: the rotations of the iteration are applied to the columns of
 // a zr x m row block z0 (column-major: entry (row, j) at z0[j * zr + row]);
 // Zout receives that block times the eigenvector matrix, columns in
@@ -40,14 +55,14 @@ void tridiag_eig_rows(int m, const double* alpha, const double* beta, double* th
             if (mm == l) break;
             if (++iter > 200) break;
             double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = std::hypot(g, 1.0);
+            double r = rot_norm(g, 1.0);
             g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
             double s = 1.0, c = 1.0, p = 0.0;
             int i;
             bool early = false;
             for (i = mm - 1; i >= l; --i) {
                 double f = s * e[i], b = c * e[i];
-                r = std::hypot(f, g);
+                r = rot_norm(f, g);
                 e[i + 1] = r;
                 if (r == 0.0) {
                     d[i + 1] -= p;
@@ -55,8 +70,9 @@ void tridiag_eig_rows(int m, const double* alpha, const double* beta, double* th
                     early = true;
                     break;
                 }
-                s = f / r;
-                c = g / r;
+                const double ir = 1.0 / r;
+                s = f * ir;
+                c = g * ir;
                 g = d[i + 1] - p;
                 r = (d[i] - g) * s + 2.0 * c * b;
                 p = s * r;
