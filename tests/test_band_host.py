@@ -72,3 +72,18 @@ def test_band_eig_last_rows(n, b):
     ref = V[n - b:, :]
     sgn = np.sign(np.sum(ref * Z, axis=0))
     assert np.max(np.abs(Z - ref * sgn)) <= 1e-10
+
+
+@pytest.mark.parametrize("scale", [1e-200, 1e-150, 1.0, 1e150, 1e200])
+def test_band_eig_extreme_scales(scale):
+    """The rotations' norms are scaled where squares would leave the double
+    range: eigenvalues of s T are s times those of T (to rounding) for s far
+    from 1, and the last rows of the eigenvectors do not depend on s."""
+    n, b = 90, 2
+    T = _band(n, b, 7)
+    th1, _ = riga.band_eig(T, b, [])
+    ths, _ = riga.band_eig(scale * T, b, [])
+    ref = np.linalg.eigvalsh(T)
+    assert np.all(np.isfinite(ths))
+    assert np.max(np.abs(ths / scale - ref)) <= 1e-12 * np.abs(ref).max()
+    assert np.max(np.abs(th1 - ref)) <= 1e-12 * np.abs(ref).max()
