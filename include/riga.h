@@ -157,8 +157,9 @@ int riga_solve(riga_ctx* ctx, const double* b, double* x, int nrhs, double tol, 
  *    accepted, the next shift is placed midway between the last accepted
  *    eigenvalue and the next Ritz value (Sec. 4.1, Remark on inertia).
  *  - Each shift: factorization at `precision`, Lanczos with full
- *    reorthogonalization (two classical Gram-Schmidt passes against the
- *    basis and all locked vectors), Rayleigh-Ritz on T_m, locking of pairs
+ *    reorthogonalization against the basis and all locked vectors (the
+ *    recurrence plus one classical Gram-Schmidt pass, or two passes: see
+ *    riga_set_reorth), Rayleigh-Ritz on T_m, locking of pairs
  *    whose residual estimate is below tol, restarts from a fresh random vector
  *    M-orthogonal to the locked ones until the inertia difference between the
  *    shift and a check shift confirms the count (degenerate eigenvalues).

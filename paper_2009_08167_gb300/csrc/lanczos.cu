@@ -2,11 +2,14 @@
 // 2009.08167) on H = (K - sigma M)^{-1} M, vectors in elimination order.
 //
 // Per step j (Eq. LanczosAlphaBeta): w = H v_j = A^{-1} (M v_j) with the
-// stored M v_j; full reorthogonalization (Sec. 4.2, "with respect to all
-// previously stored Lanczos vectors") by two classical Gram-Schmidt passes in
-// the M-inner product against [Y V_j] (Y = locked eigenvectors of this and
-// earlier shifts: deflation); alpha_j = v_j^T M w (first-pass coefficient plus
-// its correction); beta_{j+1} = ||w||_M; v_{j+1} = w / beta_{j+1}; M v_{j+1}
+// stored M v_j; full reorthogonalization (Sec. 4.2: against all previously
+// stored Lanczos vectors) in the M-inner product: the three-term recurrence
+// with alpha_j and beta_j computed as inner products against v_j and
+// v_{j-1}, then one classical Gram-Schmidt pass against [Y V_j] (Y = locked
+// eigenvectors of this and earlier shifts: deflation), or two full passes
+// once that pass removed more than 100 times the norm left (or when
+// riga_set_reorth asks for them); alpha_j = the recurrence coefficient plus
+// its correction; beta_{j+1} = ||w||_M; v_{j+1} = w / beta_{j+1}; M v_{j+1}
 // stored from the same SpMV.  Rayleigh-Ritz on T_m (Eq. RitzValues) on the
 // host every few steps with the last eigenvector row only (residual
 // estimates |beta_{m+1} w_m|), Ritz vectors V_m W by a device GEMM.
