@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--mixed-precision", default="tf32", choices=["fp32", "tf32"],
                     help="fronts of the mixed leg: tf32 (Schur updates on the tensor cores) or fp32 (FFMA)")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the phase-timing pass")
+    ap.add_argument("--trace-out", default="solve_trace.npz",
+                    help="--mode trace: file for the per-item solve trace (npz)")
     ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor", "trace"],
                     help="eigs: the benchmark; solve / factor: a short program (one factorization and "
                          "--steps solves, or --steps factorizations) of the same workload, for profilers")
@@ -629,7 +631,7 @@ def run_kernel_mode(args, local_rank):
             R.solve(b, out=x)
         tr, order = R.trace_solve(b.cpu().numpy())
         sym = R.get_symbolic()
-        np.savez(os.path.join(ROOT, "gpurun_out", "solve_trace.npz"), trace=tr, order=order, parent=sym["parent"],
+        np.savez(args.trace_out, trace=tr, order=order, parent=sym["parent"],
                  node_ptr=sym["node_ptr"], front_ptr=sym["front_ptr"])
         t0 = tr[:, 1].min()
         print(json.dumps({"mode": "trace", "items": int(tr.shape[0]), "span_us": float((tr[:, 3].max() - t0) / 1e3)}))
