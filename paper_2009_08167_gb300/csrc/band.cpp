@@ -23,30 +23,40 @@ namespace riga {
 
 namespace {
 
-// similarity rotation in the (p, q) plane of a dense symmetric matrix:
+// The reduction keeps the lower triangle in band storage: column j holds
+// A(j + d, j) for d = 0 .. W-1 at L[j * W + d].  W = b + 4 covers the band,
+// the bulge (distance b + 1) and every entry the window of a rotation reads
+// (distance up to b + 3); entries beyond are zero throughout.
+struct BandSym {
+    int n, w;
+    std::vector<double> L;
+    double& at(int i, int j) {
+        if (i < j) std::swap(i, j);
+        return L[(size_t)j * w + (i - j)];
+    }
+};
+
+// similarity rotation in the (p, q) plane of the symmetric matrix:
 // rows p, q <- [c s; -s c] [row p; row q], and the same on the columns,
 // restricted to the index window where the band (plus one bulge) can hold
 // non-zeros
-void rotate_sym(std::vector<double>& A, int n, int b, int p, int q, double c, double s) {
-    auto at = [&](int i, int j) -> double& { return A[(size_t)j * n + i]; };
-    const int lo = std::max(0, p - b - 2), hi = std::min(n, q + b + 3);
+void rotate_sym(BandSym& A, int b, int p, int q, double c, double s) {
+    const int lo = std::max(0, p - b - 2), hi = std::min(A.n, q + b + 3);
     for (int t = lo; t < hi; ++t) {
         if (t == p || t == q) continue;
-        const double x = at(p, t), y = at(q, t);
-        const double nx = c * x + s * y, ny = -s * x + c * y;
-        at(p, t) = nx;
-        at(t, p) = nx;
-        at(q, t) = ny;
-        at(t, q) = ny;
+        double& xr = A.at(p, t);
+        double& yr = A.at(q, t);
+        const double x = xr, y = yr;
+        xr = c * x + s * y;
+        yr = -s * x + c * y;
     }
-    const double app = at(p, p), aqq = at(q, q), apq = at(p, q);
+    const double app = A.at(p, p), aqq = A.at(q, q), apq = A.at(p, q);
     const double npp = c * c * app + 2.0 * c * s * apq + s * s * aqq;
     const double nqq = s * s * app - 2.0 * c * s * apq + c * c * aqq;
     const double npq = (c * c - s * s) * apq + c * s * (aqq - app);
-    at(p, p) = npp;
-    at(q, q) = nqq;
-    at(p, q) = npq;
-    at(q, p) = npq;
+    A.at(p, p) = npp;
+    A.at(q, q) = nqq;
+    A.at(p, q) = npq;
 }
 
 // band LU with partial pivoting (kl = ku = b; fill up to 2b above the
@@ -115,8 +125,13 @@ void band_solve(const BandLU& F, double* x) {
 // the identity, so that it ends as the last r rows of Q (T = Q T_tri Q^T).
 static void band_reduce(int n, int b, const double* T, std::vector<double>& d, std::vector<double>& e, int r,
                         std::vector<double>& qr) {
-    std::vector<double> A(T, T + (size_t)n * n);
-    auto at = [&](int i, int j) -> double& { return A[(size_t)j * n + i]; };
+    BandSym A;
+    A.n = n;
+    A.w = b + 4;
+    A.L.assign((size_t)n * A.w, 0.0);
+    for (int j = 0; j < n; ++j)
+        for (int i = j; i <= std::min(n - 1, j + b); ++i) A.L[(size_t)j * A.w + (i - j)] = T[(size_t)j * n + i];
+    auto at = [&](int i, int j) -> double& { return A.at(i, j); };
     auto track = [&](int p, int q, double c, double s) {
         for (int k = 0; k < r; ++k) {
             double& a = qr[(size_t)p * r + k];
@@ -131,20 +146,20 @@ static void band_reduce(int n, int b, const double* T, std::vector<double>& d, s
             const double x = at(i - 1, j), y = at(i, j);
             if (y == 0.0) continue;
             const double rr = std::hypot(x, y);
-            rotate_sym(A, n, b, i - 1, i, x / rr, y / rr);
-            if (r > 0) track(i - 1, i, x / rr, y / rr);
+            const double c1 = x / rr, s1 = y / rr;
+            rotate_sym(A, b, i - 1, i, c1, s1);
+            if (r > 0) track(i - 1, i, c1, s1);
             at(i, j) = 0.0;
-            at(j, i) = 0.0;
             // chase the bulge at (k + b, k - 1) down the band
             for (int k = i; k + b < n;) {
                 const int p = k + b - 1, q = k + b, col = k - 1;
                 const double x2 = at(p, col), y2 = at(q, col);
                 if (y2 == 0.0) break;
                 const double r2 = std::hypot(x2, y2);
-                rotate_sym(A, n, b, p, q, x2 / r2, y2 / r2);
-                if (r > 0) track(p, q, x2 / r2, y2 / r2);
+                const double c2 = x2 / r2, s2 = y2 / r2;
+                rotate_sym(A, b, p, q, c2, s2);
+                if (r > 0) track(p, q, c2, s2);
                 at(q, col) = 0.0;
-                at(col, q) = 0.0;
                 k = q;
             }
         }
