@@ -70,6 +70,13 @@ CASES = [
     Mesh(3, 8, 2, 4, 8),
     Mesh(2, 10, 1, None, 4),          # p = 1: every knot is C0
     Mesh(2, 3, 4, None, 2),           # fewer elements than the degree
+    Mesh(3, [7, 9, 5], 2, 3, 4),      # 3D rIGA, ragged last blocks in every direction
+    Mesh(3, [10, 6, 8], 3, 4, 5),     # 3D rIGA p = 3, uneven extents
+    Mesh(2, [37, 23], 4, 8, 8),       # p = 4, ragged blocks
+    Mesh(2, 20, 5, 6, 12),            # p = 5, leaves larger than the blocks
+    Mesh(1, 57, 2, 5, 6),             # 1D rIGA, ragged last block
+    Mesh(2, [5, 40], 2, 16, 3),       # one direction without a C0 line
+    Mesh(3, 6, 1, None, 2),           # 3D p = 1
 ]
 
 
