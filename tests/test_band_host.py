@@ -87,3 +87,32 @@ def test_band_eig_extreme_scales(scale):
     assert np.all(np.isfinite(ths))
     assert np.max(np.abs(ths / scale - ref)) <= 1e-12 * np.abs(ref).max()
     assert np.max(np.abs(th1 - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_band_eig_rejects_bad_arguments():
+    """riga_band_eig's documented RIGA_EINVAL cases, through the C ABI."""
+    import ctypes
+    lib = riga.load_library()
+    n, b = 6, 2
+    T = np.asfortranarray(_band(n, b, 3))
+    theta = np.zeros(n)
+    S = np.zeros((n, 2), order="F")
+    Z = np.zeros((2, n), order="F")
+    P = ctypes.c_void_p
+
+    def call(nn, bb, which, r, t=T, th=theta, s=S, z=Z):
+        wh = np.ascontiguousarray(which, dtype=np.int32)
+        return lib.riga_band_eig(nn, bb, t.ctypes.data_as(P) if t is not None else None,
+                                 th.ctypes.data_as(P) if th is not None else None, int(wh.size),
+                                 wh.ctypes.data_as(P) if wh.size else None, s.ctypes.data_as(P) if s is not None else None,
+                                 r, z.ctypes.data_as(P) if z is not None else None)
+
+    assert call(n, b, [0, 5], 2) == riga.RIGA_OK
+    assert call(0, b, [], 0) == riga.RIGA_EINVAL          # n < 1
+    assert call(n, -1, [], 0) == riga.RIGA_EINVAL         # negative bandwidth
+    assert call(n, b, [0, 6], 0) == riga.RIGA_EINVAL      # index out of range
+    assert call(n, b, [-1], 0) == riga.RIGA_EINVAL
+    assert call(n, b, [], n + 1) == riga.RIGA_EINVAL      # more last rows than rows
+    assert call(n, b, [], 2, z=None) == riga.RIGA_EINVAL  # rows asked, no output
+    assert call(n, b, [], 0, t=None) == riga.RIGA_EINVAL
+    assert call(n, b, [1], 0, s=None) == riga.RIGA_EINVAL  # vectors asked, no output
