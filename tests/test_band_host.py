@@ -116,3 +116,37 @@ def test_band_eig_rejects_bad_arguments():
     assert call(n, b, [], 2, z=None) == riga.RIGA_EINVAL  # rows asked, no output
     assert call(n, b, [], 0, t=None) == riga.RIGA_EINVAL
     assert call(n, b, [1], 0, s=None) == riga.RIGA_EINVAL  # vectors asked, no output
+
+
+def _tridiag(d, e):
+    return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+
+
+@pytest.mark.parametrize("case", ["random250", "wilkinson21", "split", "graded", "constant"])
+def test_tridiagonal_qr_cases(case):
+    """The tridiagonal Rayleigh-Ritz step (implicit QR, bulge chasing) on the
+    shapes Lanczos produces and on the classical hard cases: Wilkinson's
+    W21+ (pairs of eigenvalues equal to 1e-14 relative), a matrix that
+    splits into independent blocks (zero couplings), a strongly graded one,
+    and a constant-diagonal one (every shift exact at the start)."""
+    rng = np.random.default_rng(5)
+    if case == "random250":
+        d, e = rng.normal(size=250), rng.normal(size=249)
+    elif case == "wilkinson21":
+        d, e = np.abs(np.arange(-10, 11)).astype(float), np.ones(20)
+    elif case == "split":
+        d, e = rng.normal(size=60), rng.normal(size=59)
+        e[[9, 10, 30, 58]] = 0.0
+    elif case == "graded":
+        d = 10.0 ** (-np.arange(40) / 3.0)
+        e = 0.3 * np.sqrt(d[:-1] * d[1:])
+    else:
+        d, e = np.full(50, 2.0), np.ones(49)
+    T = _tridiag(d, e)
+    n = len(d)
+    theta, S = riga.band_eig(T, 1, list(range(n)))
+    ref = np.linalg.eigvalsh(T)
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(theta - ref)) <= 1e-13 * scale * max(1.0, n / 50)
+    assert np.max(np.abs(T @ S - S * theta)) <= 1e-12 * scale * max(1.0, n / 50)
+    assert np.max(np.abs(S.T @ S - np.eye(n))) <= 1e-11
