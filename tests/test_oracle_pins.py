@@ -327,6 +327,68 @@ def test_separators_separate_and_fronts_cover_fill(ne, p, bs, le):
     assert nnz_true <= nnz_front
 
 
+@pytest.mark.parametrize("k,m", [(1, 0), (7, 0), (12, 0), (5, 3), (9, 14), (16, 1)])
+def test_front_counts_closed_forms_and_elimination_count(k, m):
+    """front_nnz_and_flops against things it does not compute itself.
+    (1) Closed forms: a dense front of n = k + m variables with k pivots holds
+    k(k+1)/2 + k m entries of L, and eliminating its k pivots costs
+    ((n^3 - n) - (m^3 - m)) / 3 flops: the full dense LDL^T of n variables,
+    sum_{j=1..n} j (j - 1) = (n^3 - n) / 3, minus that of the m-variable
+    Schur complement left over.  (2) A brute-force count: the test eliminates
+    the k pivots of a random symmetric front entry by entry on its lower
+    triangle, counts the multiply-adds it performs (2 flops each) and checks
+    that what it computed is the Schur complement A22 - A21 A11^{-1} A12.  A
+    doubled or halved formula, or one that counts the upper triangle too,
+    fails both."""
+    n = k + m
+    own, border = np.arange(k), np.arange(k, n)
+    nnz, flops = symbolic.front_nnz_and_flops([(own, border)])
+    assert nnz == k * (k + 1) // 2 + k * m
+    assert flops == ((n ** 3 - n) - (m ** 3 - m)) // 3
+    rng = np.random.default_rng(100 * k + m)
+    B = rng.normal(size=(n, n))
+    A = B @ B.T + n * np.eye(n)
+    W = A.copy()
+    madds = 0
+    for i in range(k):
+        for r in range(i + 1, n):
+            lri = W[r, i] / W[i, i]
+            for c in range(i + 1, r + 1):
+                W[r, c] -= lri * W[c, i]
+                madds += 1
+    assert 2 * madds == flops
+    schur = A[k:, k:] - A[k:, :k] @ np.linalg.solve(A[:k, :k], A[:k, k:])
+    assert np.allclose(np.tril(W[k:, k:]), np.tril(schur), rtol=1e-12, atol=1e-12 * n)
+    # additivity over fronts
+    nnz2, flops2 = symbolic.front_nnz_and_flops([(own, border), (np.arange(n, n + 3), np.empty(0, np.int64))])
+    assert nnz2 == nnz + 6 and flops2 == flops + (27 - 3) // 3
+
+
+@pytest.mark.parametrize("ne,p,bs,le", [([6, 6], 2, None, 3), ([8, 8], 3, 4, 8), ([4, 4, 4], 2, None, 2)])
+def test_column_counts_equal_numeric_factor_nnz(ne, p, bs, le):
+    """Sum of (column count + 1) from the brute-force symbolic elimination
+    equals the number of non-zeros of the numeric L of the permuted matrix
+    (dense LDL^T, random values, so no entry cancels by accident); the
+    fronts hold at least those entries and cost at least the true sparse
+    flop count sum_j c_j (c_j + 1)."""
+    K, M, n1, N, nodes, perm = _tree_case(ne, p, bs, le)
+    struct, _ = symbolic.symbolic_elimination((K.indptr, K.indices), perm)
+    rng = np.random.default_rng(11)
+    A = K.todense()
+    Ar = np.where(A != 0.0, rng.uniform(0.5, 1.0, size=A.shape), 0.0)
+    Ar = np.triu(Ar, 1)
+    Ar = Ar + Ar.T + np.diag(np.full(N, 4.0 * N))
+    P = Ar[np.ix_(perm, perm)]
+    L, d = factor.ldlt_dense(P)
+    nnz_numeric = int(np.count_nonzero(np.abs(np.tril(L)) > 1e-300))
+    counts = np.array([s.size for s in struct])
+    assert int(np.sum(counts + 1)) == nnz_numeric
+    fr = symbolic.fronts(nodes, perm, (K.indptr, K.indices))
+    nnz_front, flops_front = symbolic.front_nnz_and_flops(fr)
+    assert nnz_front >= nnz_numeric
+    assert flops_front >= int(np.sum(counts * (counts + 1)))
+
+
 def test_tree_shapes_c1_and_riga_blocks():
     # C1: 16x16 p=2 IGA, 14x14 DOFs... n1 = 16; first cut a 2-thick slab at 7
     _, _, n1, N, nodes, perm = _tree_case([16, 16], 2, None, 8)
