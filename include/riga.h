@@ -111,6 +111,16 @@ void riga_destroy(riga_ctx* ctx);
 int riga_assemble(riga_ctx* ctx, const riga_mesh* mesh, const double* coefK, const double* coefM);
 
 /*
+ * riga_assemble_log: riga_assemble with per-element LOG-coefficients,
+ * K = sum_e exp(logK[e]) K_e and M = sum_e exp(logM[e]) M_e (the
+ * parametrisation in which riga_eig_grad differentiates).  The exponentials
+ * are taken on the device.  logK, logM: n_elem values each, host or device
+ * pointers, NULL = all zeros (unit coefficients).  Errors as riga_assemble;
+ * RIGA_EINVAL also when an exponential is zero or not finite.
+ */
+int riga_assemble_log(riga_ctx* ctx, const riga_mesh* mesh, const double* logK, const double* logM);
+
+/*
  * riga_analyze: the symbolic half of riga_assemble alone (host, integer):
  * C0 DOFs, elimination order, assembly tree and fronts for `mesh`, without
  * touching a device.  Makes riga_query and riga_get_symbolic available.
@@ -428,19 +438,28 @@ int riga_trace_solve(riga_ctx* ctx, const double* b, int* n_items, long long* tr
  * pool or a fixed reservation) and forbids cudaMalloc, or a long-running
  * service that must not grow its device footprint after start-up.
  *  - rowptr[N+1] (int64), col[nnz] (int32, ascending within a row), val[nnz],
- *    x[N], y[N], xy[1]: DEVICE pointers owned by the caller; 1 <= N <= 2^20.
+ *    x[N], y[N], xy[1]: DEVICE pointers of the CURRENT device, owned by the
+ *    caller; 1 <= N <= 2^20.  Every pointer is checked
+ *    (cudaPointerGetAttributes) before anything is launched: a host pointer
+ *    or memory of another device returns RIGA_EINVAL.  Preconditions the
+ *    call cannot check without reading device memory: rowptr[0] = 0,
+ *    rowptr non-decreasing, 0 <= col[e] < N for every entry, and col and
+ *    val hold rowptr[N] entries.
  *  - The per-block partial sums live in a fixed 512 KiB array in device
  *    memory that every GPU which loads this library holds until the process
  *    exits.  The first call on a device looks that array's address up
  *    (cudaGetSymbolAddress, with the device current) and caches it: make the
- *    first call on each device before any stream capture.
+ *    first call on each device before any stream capture.  The cached
+ *    address is valid for the lifetime of the device's primary context; do
+ *    not call this function again after cudaDeviceReset in the same process.
  *  - Every call uses the same array, which keeps the last call's contents;
  *    nothing in it has to start at zero (each call writes every entry it
  *    reads).  Calls that overlap on the GPU (other streams, or host threads
  *    without ordering between them) race on it.
  *  - Work is enqueued on cuda_stream (NULL = legacy default stream); the call
  *    returns without synchronizing.
- * Errors: RIGA_EINVAL (NULL pointer, N < 1 or N > 2^20), RIGA_ECUDA.
+ * Errors: RIGA_EINVAL (NULL pointer, a pointer that is not device memory of
+ * the current device, N < 1 or N > 2^20), RIGA_ECUDA.
  */
 int riga_spmv_dot_noalloc(const long long* rowptr, const int* col, const double* val, long long N,
                           const double* x, double* y, double* xy, void* cuda_stream);

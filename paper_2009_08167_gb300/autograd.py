@@ -3,7 +3,8 @@
 EigVals(a, b) returns the k smallest eigenvalues of K(a) u = lambda M(b) u,
 K(a) = sum_e exp(a_e) K_e, M(b) = sum_e exp(b_e) M_e, as a differentiable
 function of the per-element log-coefficients a and b.  The forward pass is
-riga_assemble + riga_eigs; the backward pass is riga_eig_grad with the
+riga_assemble_log (log-coefficients in, exponentials
+taken in the library) + riga_eigs; the backward pass is riga_eig_grad with the
 incoming dL/dlambda as weights (simple eigenvalues, or symmetric functions of
 complete degenerate groups).  Marshalling only: the work runs in the library.
 """
@@ -15,9 +16,9 @@ from .riga import Riga
 class _EigVals(torch.autograd.Function):
     @staticmethod
     def forward(ctx, a, b, solver, mesh, k, tol, sigma):
-        ck = torch.exp(a.detach()).to(torch.float64).contiguous()
-        cm = torch.exp(b.detach()).to(torch.float64).contiguous()
-        solver.assemble(mesh, ck, cm)
+        la = a.detach().to(torch.float64).contiguous()
+        lb = b.detach().to(torch.float64).contiguous()
+        solver.assemble(mesh, la, lb, log=True)  # the library exponentiates
         ev, _, rs = solver.eigs(k, sigma, tol, vectors=False, device_out=a.is_cuda)
         ctx.solver = solver
         ctx.k = k

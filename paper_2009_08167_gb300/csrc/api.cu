@@ -235,7 +235,26 @@ int riga_analyze(riga_ctx* c, const riga_mesh* m) {
     return RIGA_OK;
 }
 
+namespace riga {
+// c[e] = exp(c[e]): the coefficient map of the log-coefficient form
+// K = sum_e exp(a_e) K_e, M = sum_e exp(b_e) M_e
+__global__ void exp_inplace_kernel(long long n, double* __restrict__ v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = exp(v[i]);
+}
+}  // namespace riga
+
+static int assemble_impl(riga_ctx* c, const riga_mesh* m, const double* coefK, const double* coefM, bool logs);
+
 int riga_assemble(riga_ctx* c, const riga_mesh* m, const double* coefK, const double* coefM) {
+    return assemble_impl(c, m, coefK, coefM, false);
+}
+
+int riga_assemble_log(riga_ctx* c, const riga_mesh* m, const double* logK, const double* logM) {
+    return assemble_impl(c, m, logK, logM, true);
+}
+
+static int assemble_impl(riga_ctx* c, const riga_mesh* m, const double* coefK, const double* coefM, bool logs) {
     if (!c || !m) return RIGA_EINVAL;
     c->last_error.clear();
     if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
@@ -271,6 +290,10 @@ int riga_assemble(riga_ctx* c, const riga_mesh* m, const double* coefK, const do
         RIGA_CUDA_TRY(c, tmp.alloc(ne_tot));
         int rc = to_device(c, coefK, tmp.ptr, ne_tot);
         if (rc) return rc;
+        if (logs && ne_tot > 0) {
+            count_launch(c);
+            exp_inplace_kernel<<<(unsigned)std::min<long long>((ne_tot + 255) / 256, 1024), 256, 0, c->stream>>>(ne_tot, tmp.ptr);
+        }
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->coefK.data(), tmp.ptr, ne_tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
     if (coefM) {
@@ -279,6 +302,10 @@ int riga_assemble(riga_ctx* c, const riga_mesh* m, const double* coefK, const do
         RIGA_CUDA_TRY(c, tmp.alloc(ne_tot));
         int rc = to_device(c, coefM, tmp.ptr, ne_tot);
         if (rc) return rc;
+        if (logs && ne_tot > 0) {
+            count_launch(c);
+            exp_inplace_kernel<<<(unsigned)std::min<long long>((ne_tot + 255) / 256, 1024), 256, 0, c->stream>>>(ne_tot, tmp.ptr);
+        }
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->coefM.data(), tmp.ptr, ne_tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));

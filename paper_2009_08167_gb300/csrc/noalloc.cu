@@ -86,6 +86,18 @@ int noalloc_scratch(double** out) {
     *out = g_noalloc_addr[dev];
     return RIGA_OK;
 }
+
+// true when p is device (or managed) memory of the current device
+bool on_current_device(const void* p) {
+    int dev = -1;
+    cudaPointerAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
 }  // namespace
 
 }  // namespace riga
@@ -95,6 +107,11 @@ extern "C" int riga_spmv_dot_noalloc(const long long* rowptr, const int* col, co
     using namespace riga;
     if (!rowptr || !col || !val || !x || !y || !xy || N < 1) return RIGA_EINVAL;
     if (N > NOALLOC_MAX_ROWS) return RIGA_EINVAL;
+    // every array must be device memory of the current device: a host
+    // pointer or another GPU's memory is refused before anything is launched
+    const void* ptrs[6] = {rowptr, col, val, x, y, xy};
+    for (const void* p : ptrs)
+        if (!on_current_device(p)) return RIGA_EINVAL;
     double* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;

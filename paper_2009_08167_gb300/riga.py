@@ -31,7 +31,7 @@ RIGA_FP32 = 1
 RIGA_TF32 = 2
 
 EXPORTED = [
-    "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_factor", "riga_solve", "riga_eigs",
+    "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_assemble_log", "riga_factor", "riga_solve", "riga_eigs",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
     "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_set_wait_limit",
     "riga_trace_solve", "riga_spmv_dot_noalloc", "riga_strerror",
@@ -76,6 +76,7 @@ def load_library(path=LIB_PATH):
     lib.riga_destroy.argtypes = [P]
     lib.riga_destroy.restype = None
     lib.riga_assemble.argtypes = [P, ctypes.POINTER(_MeshC), P, P]
+    lib.riga_assemble_log.argtypes = [P, ctypes.POINTER(_MeshC), P, P]
     lib.riga_analyze.argtypes = [P, ctypes.POINTER(_MeshC)]
     lib.riga_factor.argtypes = [P, D, I, ctypes.POINTER(LL)]
     lib.riga_solve.argtypes = [P, P, P, I, D, ctypes.POINTER(I)]
@@ -178,7 +179,9 @@ class Riga:
         self._check(self.lib.riga_analyze(self.ctx, ctypes.byref(m)))
         self.mesh = mesh
 
-    def assemble(self, mesh: Mesh, coefK=None, coefM=None):
+    def assemble(self, mesh: Mesh, coefK=None, coefM=None, log=False):
+        """K and M of `mesh`; coefK / coefM: per-element coefficients (or, with
+        log=True, their logarithms, exponentiated by the library)."""
         m = _MeshC()
         m.dim = mesh.dim
         for a in range(3):
@@ -195,7 +198,8 @@ class Riga:
             coefK = np.ascontiguousarray(coefK, dtype=np.float64)
         if coefM is not None and isinstance(coefM, np.ndarray):
             coefM = np.ascontiguousarray(coefM, dtype=np.float64)
-        self._check(self.lib.riga_assemble(self.ctx, ctypes.byref(m), _ptr(coefK), _ptr(coefM)))
+        fn = self.lib.riga_assemble_log if log else self.lib.riga_assemble
+        self._check(fn(self.ctx, ctypes.byref(m), _ptr(coefK), _ptr(coefM)))
         self.mesh = mesh
         self._mult_keep = keep
 
@@ -430,9 +434,25 @@ def spmv_dot_noalloc(rowptr, col, val, x, y, xy, stream=None):
     default the current one) and not synchronized."""
     import torch
     lib = load_library()
-    s = stream if stream is not None else torch.cuda.current_stream()
     n = x.numel()
-    rc = lib.riga_spmv_dot_noalloc(_ptr(rowptr), _ptr(col), _ptr(val), int(n), _ptr(x), _ptr(y), _ptr(xy),
-                                   ctypes.c_void_p(s.cuda_stream))
+    want = [("rowptr", rowptr, torch.int64, n + 1), ("col", col, torch.int32, None), ("val", val, torch.float64, None),
+            ("x", x, torch.float64, n), ("y", y, torch.float64, n), ("xy", xy, torch.float64, 1)]
+    for name, t, dt, size in want:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if size is not None and t.numel() != size:
+            raise ValueError(f"{name} must have {size} entries, got {t.numel()}")
+        if t.device != x.device:
+            raise ValueError(f"{name} is on {t.device}, x on {x.device}")
+    if col.numel() != val.numel():
+        raise ValueError("col and val must have the same length")
+    with torch.cuda.device(x.device):
+        s = stream if stream is not None else torch.cuda.current_stream(x.device)
+        rc = lib.riga_spmv_dot_noalloc(_ptr(rowptr), _ptr(col), _ptr(val), int(n), _ptr(x), _ptr(y), _ptr(xy),
+                                       ctypes.c_void_p(s.cuda_stream))
     if rc != RIGA_OK:
         raise RigaError(rc, lib.riga_strerror(rc).decode())

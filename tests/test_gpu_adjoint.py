@@ -65,3 +65,36 @@ def test_c5_gradient_fd_and_homogeneity():
     # per coordinate, with a floor for the finite-difference noise
     assert np.all(np.abs(an - fd) <= 1e-4 * np.abs(fd) + 1e-5 * np.abs(np.concatenate([ga, gb])).max())
     R.close()
+
+
+def test_assemble_log_matches_exponentiated_coefficients():
+    """riga_assemble_log(a, b) (exponentials taken on the device) gives the
+    matrices of riga_assemble(exp(a), exp(b)) up to the rounding of exp, on
+    host and on device inputs; all-zero logs give the constant-coefficient
+    (Kronecker) matrices."""
+    import torch
+
+    from paper_2009_08167_gb300.inputs import Mesh
+    from tests.gpu_helpers import riga_ctx
+
+    mesh = Mesh(2, 24, 3, 8, 8)
+    rng = np.random.default_rng(41)
+    a = 0.25 * rng.normal(size=mesh.n_elem)
+    b = 0.25 * rng.normal(size=mesh.n_elem)
+    R = riga_ctx()
+    R.assemble(mesh, np.exp(a), np.exp(b))
+    _, _, K0, M0 = R.get_matrices()
+    R.assemble(mesh, a, b, log=True)
+    _, _, K1, M1 = R.get_matrices()
+    assert np.allclose(K1, K0, rtol=1e-14, atol=0) and np.allclose(M1, M0, rtol=1e-14, atol=0)
+    dev = torch.device("cuda", 0)
+    R.assemble(mesh, torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev), log=True)
+    _, _, K2, M2 = R.get_matrices()
+    assert np.array_equal(K2, K1) and np.array_equal(M2, M1)
+    R.assemble(mesh, np.zeros(mesh.n_elem), np.zeros(mesh.n_elem), log=True)
+    _, _, K3, M3 = R.get_matrices()
+    R.assemble(mesh)
+    _, _, K4, M4 = R.get_matrices()
+    assert np.allclose(K3, K4, rtol=1e-13, atol=1e-14 * np.abs(K4).max())
+    assert np.allclose(M3, M4, rtol=1e-13, atol=1e-14 * np.abs(M4).max())
+    R.close()
