@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--mixed-precision", default="tf32", choices=["fp32", "tf32"],
                     help="fronts of the mixed leg: tf32 (Schur updates on the tensor cores) or fp32 (FFMA)")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the phase-timing pass")
+    ap.add_argument("--c3-steps", type=int, default=2,
+                    help="timed steps of the 3D 64^3 p=2 rIGA workload (50 pairs), FP64 path and mixed path, "
+                         "reported as the 'c3' object of the default run (0 = skip)")
     ap.add_argument("--trace-out", default="solve_trace.npz",
                     help="--mode trace: file for the per-item solve trace (npz)")
     ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor", "trace"],
@@ -158,16 +161,19 @@ def peaks():
 
 
 def ncu_traffic(phase):
-    """DRAM bytes per invocation of a phase from the committed ncu summary
-    (profiles/ncu_traffic.txt: '<phase> <bytes_per_call> <source commit>'),
-    or None."""
+    """DRAM bytes per launch of the phase's kernel from the committed ncu
+    summary (profiles/ncu_traffic.txt: '<phase> <bytes_per_call> <source>'),
+    as (bytes, source), or None when the file has no line for the phase (a
+    kernel changed since its counters were taken has its line removed)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
-        parts = line.split("#")[0].split()
+        body, _, note = line.partition("#")
+        parts = body.split()
         if len(parts) >= 2 and parts[0] == phase:
-            return float(parts[1])
+            src = " ".join(parts[2:]) or note.strip()
+            return float(parts[1]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/ncu_traffic.txt (" + src + ")"
     return None
 
 
@@ -258,31 +264,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def roofline(prof):
+def roofline(prof, q=None):
     """Roofline of the dominant phase of one profiled step (device time of
-    the phase's launches, CUDA events on the library's stream): against HBM
-    (algorithmic bytes, measured copy bandwidth) and against the FP64 pipe
-    (algorithmic flops, nominal 1.25 TFLOP/s); the bound reported is the one
-    the phase is closer to."""
+    the phase's launches, CUDA events on the library's stream), in the class
+    the hot-path table assigns to it: the f/b solve, the SpMVs and the
+    reorthogonalization are HBM-bound (algorithmic bytes: for the solve
+    2 nnz(L) s_f + 4 N 8 b per launch with b right-hand sides, as the library
+    records them; peak: the measured copy bandwidth, else the fallback), the
+    fronts are bound by the FP64 rate on the FP64 path.  The FP64-pipe
+    fraction of the same phase (algorithmic flops over the measured FP64
+    rate) is reported beside it, labelled as such."""
     pk, pk_kind = peaks()
     dom = max(prof, key=lambda p: prof[p]["ms"])
     pr = prof[dom]
     if pr["ms"] <= 0:
         return None
     t = pr["ms"] / 1e3
+    calls = max(1, pr["calls"])
     gbs = pr["bytes"] / t / 1e9
     tfl = pr["flops"] / t / 1e12
-    f_hbm = gbs / pk["hbm_gbs"]
-    f_alu = tfl / FP64_PEAK_TFLOPS
-    calls = max(1, pr["calls"])
-    common = {"phase": dom, "ms_per_call": pr["ms"] / calls, "hbm_frac": f_hbm, "fp64_frac": f_alu}
-    if pr["flops"] > 0 and f_alu >= f_hbm:
-        return dict({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f_alu,
-                     "traffic": ncu_traffic(dom), "peak_source": "nominal fp64 (2 DFMA/clock/SM, 2.07 GHz)",
-                     "algorithmic_flops_per_call": pr["flops"] / calls}, **common)
-    return dict({"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": f_hbm,
-                 "traffic": ncu_traffic(dom), "peak_source": pk_kind,
-                 "algorithmic_bytes_per_call": pr["bytes"] / calls}, **common)
+    out = {"phase": dom, "ms_per_call": pr["ms"] / calls, "calls": pr["calls"],
+           "fp64_pipe_frac": tfl / FP64_PEAK_TFLOPS if pr["flops"] > 0 else None,
+           "fp64_peak_tflops": FP64_PEAK_TFLOPS, "fp64_peak_source": FP64_PEAK_SOURCE}
+    tr = ncu_traffic(dom)
+    if dom == "factor":
+        out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tfl / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
+                    "algorithmic_flops_per_call": pr["flops"] / calls, "traffic": tr[0] if tr else None,
+                    "traffic_source": tr[1] if tr else None})
+        return out
+    out.update({"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                "peak_source": pk_kind + " copy bandwidth", "algorithmic_bytes_per_call": pr["bytes"] / calls,
+                "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None})
+    return out
 
 
 def aggregate(ms, pairs, world, dist=None, device="cpu"):
@@ -298,6 +312,7 @@ def aggregate(ms, pairs, world, dist=None, device="cpu"):
 
 
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 FMA rate (2 per clock per SM at 2.07 GHz)
+FP64_PEAK_SOURCE = "nominal (2 DFMA per clock per SM at 2.07 GHz)"
 FP32_PEAK_TFLOPS = 80.5   # nominal GB300 FP32 FMA rate (128 per clock per SM at 2.07 GHz)
 TF32_PEAK_TFLOPS = 1100.0  # nominal GB300 dense TF32 tensor rate
 
@@ -401,7 +416,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
         step()
     prof = R.profile_get()
     R.profile(False)
-    roof = roofline(prof)
+    roof = roofline(prof, q)
     fronts = fronts_rate(prof, q["flops_fact"], R.stats()["n_fact"], FP64_PEAK_TFLOPS)
     phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
     cpu = None
@@ -532,7 +547,7 @@ def run_riga(args, rank, world, local_rank):
         step_device()
     prof = R.profile_get()
     R.profile(False)
-    roof = roofline(prof)
+    roof = roofline(prof, q)
     fronts = fronts_rate(prof, q["flops_fact"], R.stats()["n_fact"], FP64_PEAK_TFLOPS)
     phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
 
@@ -570,6 +585,10 @@ def run_riga(args, rank, world, local_rank):
                  "phases_ms_one_step": {p: round(v["ms"], 3) for p, v in prof_m.items() if v["calls"]}}
         R.set_eig_options(slice=cfg["slice"], precision=prec, extra=2, seed=11)
 
+    c3 = None
+    if args.c3_steps > 0 and args.mesh in ("riga", "iga") and args.precision == "fp64":
+        c3 = run_c3_leg(args, local_rank, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -592,6 +611,7 @@ def run_riga(args, rank, world, local_rank):
             "autotune": tuned,
             "assembly_ms": statistics.median(asm_ms),
             "mixed_path": mixed,
+            "c3": c3,
             "phases_ms_one_step": phases,
             "counts_per_step": {"n_fact": st["n_fact"], "n_solve": st["n_solve"], "n_matvec": st["n_matvec"],
                                 "lanczos_steps": st["lanczos_steps"]},
@@ -603,6 +623,54 @@ def run_riga(args, rank, world, local_rank):
     R.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_c3_leg(args, local_rank, flush):
+    """The 3D workload (64^3 elements, p=2, C0 planes every 8 elements,
+    N = 357,911, 50 pairs, Lanczos blocks of 2) on its own context: the FP64
+    path and the mixed path (FP32 fronts with TF32 tensor-core Schur
+    updates, FP64 refinement, residuals, Lanczos and inertia), each with one
+    untimed warm-up step and args.c3_steps timed steps (CUDA events, L2
+    flushed before each step), the same metric as the headline."""
+    import numpy as np
+    import torch
+    from paper_2009_08167_gb300 import riga
+    from paper_2009_08167_gb300.inputs import config_c3
+    cfg = config_c3()
+    stream = torch.cuda.current_stream()
+    R = riga.Riga(local_rank, stream)
+    R.set_eig_block(2)
+    t0 = time.perf_counter()
+    R.assemble(cfg["mesh"])
+    setup_s = time.perf_counter() - t0
+    q = R.query()
+    out = {"workload": "laplace3d_p2_64x64x64_riga_bs8_k50", "N": q["N"], "nnz": q["nnz"], "nnzL": q["nnzL"],
+           "flops_fact": q["flops_fact"], "pairs": cfg["k"], "lanczos_block": 2, "setup_s": setup_s,
+           "l2": "flushed between timed steps (512 MiB write)"}
+    for name, prec in (("fp64", riga.RIGA_FP64), ("mixed", riga.RIGA_TF32)):
+        R.set_eig_options(slice=cfg["k"], precision=prec, extra=2, seed=11)
+        R.eigs(cfg["k"], 0.0, RESID_TOL, vectors=True, device_out=True)
+        times, rs = [], None
+        for _ in range(args.c3_steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, rs = R.eigs(cfg["k"], 0.0, RESID_TOL, vectors=True, device_out=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        rs_h = rs.cpu().numpy()
+        ok = int(np.sum(rs_h <= RESID_TOL))
+        st = R.stats()
+        out[name] = {"value": ok / (statistics.mean(times) / 1e3), "unit": "eigenpairs/s",
+                     "ms_per_step": statistics.mean(times), "steps": len(times), "converged_pairs": ok,
+                     "max_resid": float(np.max(rs_h)), "n_fact": st["n_fact"], "lanczos_steps": st["lanczos_steps"],
+                     "dtype": "f64" if prec == riga.RIGA_FP64 else
+                              "f32 fronts with tf32 tensor-core updates, f64 refinement/Lanczos/inertia"}
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    R.close()
+    return out
 
 
 def run_kernel_mode(args, local_rank):

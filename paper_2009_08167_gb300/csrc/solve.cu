@@ -728,11 +728,13 @@ template <typename T, int NR>
 static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
-    // algorithmic bytes: the solve operators (k x (n-k) forward, k x n backward)
-    // and the vectors read and written in each sweep
+    // algorithmic bytes of a forward/backward solve with b right-hand sides:
+    // the factor L read once per sweep, 2 nnz(L) s_f, plus four FP64 vector
+    // passes, 4 N 8 b (the operator panels this design reads instead hold
+    // more entries: the difference counts as overhead, not as work)
     // algorithmic flops: one multiply-add per operator entry and right-hand side
     PhaseScope scope(c, PH_SOLVE,
-                     (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * sizeof(T) + 4.0 * NR * nsplit * (double)S.N * sizeof(double),
+                     2.0 * (double)S.nnzL * sizeof(T) + 4.0 * NR * nsplit * (double)S.N * sizeof(double),
                      2.0 * (2.0 * (double)S.nnzQ - (double)S.nnzL_own2) * NR * nsplit);
     int max_n = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);

@@ -51,3 +51,51 @@ def compare_eigvecs(U_ref, U, M, lam_ref, rel=1e-8, tol=1e-9, lam_next=None):
         worst = min(worst, s.min())
     assert worst >= 1 - tol, worst
     return worst
+
+
+def kron_1d_matrices(mesh):
+    """Dense 1D stiffness and mass matrices (Dirichlet functions removed) per
+    direction, x first: the factors of Eq. 2Dmatrix."""
+    from oracle import bspline
+    return [bspline.matrices_1d(mesh.ne[a], mesh.p, mesh.mults[a], True) for a in range(mesh.dim)]
+
+
+def kron_apply(mats, U):
+    """(A_z (x) A_y (x) A_x) U for the columns of U (x fastest); mats = [A_x, A_y(, A_z)]."""
+    U = np.asarray(U)
+    dims = [A.shape[1] for A in mats]
+    cols = U.shape[1]
+    T = U.reshape(list(reversed(dims)) + [cols])  # (n_z, n_y, n_x, cols) for 3D
+    d = len(mats)
+    for a, A in enumerate(mats):
+        ax = d - 1 - a  # tensor axis of direction a
+        T = np.moveaxis(np.tensordot(A, T, axes=([1], [ax])), 0, ax)
+    return T.reshape(-1, cols)
+
+
+def kron_residuals(mesh, lam, U):
+    """rho_i = ||K u_i - lam_i M u_i|| / (|lam_i| ||M u_i||) with K and M
+    applied through their Kronecker structure (no global matrix is built):
+    K = sum_a (M (x) ... K on axis a ... (x) M), M = M (x) M (x) M."""
+    one = kron_1d_matrices(mesh)
+    Ks = [o[0] for o in one]
+    Ms = [o[1] for o in one]
+    MU = kron_apply(Ms, U)
+    KU = np.zeros_like(MU)
+    for a in range(mesh.dim):
+        mats = [Ks[b] if b == a else Ms[b] for b in range(mesh.dim)]
+        KU += kron_apply(mats, U)
+    R = KU - MU * lam[None, :]
+    return np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(MU, axis=0)), MU
+
+
+def compare_eigvecs_kron(mesh, V_ref, U, lam_ref, rel=1e-8, tol=1e-9, lam_next=None):
+    """compare_eigvecs with M applied through its Kronecker structure."""
+    one = kron_1d_matrices(mesh)
+
+    class _KM:
+        @staticmethod
+        def matvec(X):
+            return kron_apply([o[1] for o in one], X)
+
+    return compare_eigvecs(V_ref, U, _KM, lam_ref, rel=rel, tol=tol, lam_next=lam_next)
