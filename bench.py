@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="riga", choices=["riga", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c4"],
                     help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, "
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
@@ -64,7 +64,11 @@ def parse():
                          "reported as the 'c3' object of the default run (0 = skip)")
     ap.add_argument("--trace-out", default="solve_trace.npz",
                     help="--mode trace: file for the per-item solve trace (npz)")
-    ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor", "trace"],
+    ap.add_argument("--sweep-dim", type=int, default=2, help="--mode bs-sweep: 2 (256^2 p=3) or 3 (32^3 p=2)")
+    ap.add_argument("--sweep-pairs", type=int, default=100, help="--mode bs-sweep: eigenpairs per eigensolve")
+    ap.add_argument("--interval-pairs", type=int, default=1024,
+                    help="--mode interval: about this many eigenpairs (the interval [0, hi) with hi from Weyl's law)")
+    ap.add_argument("--mode", default="eigs", choices=["eigs", "solve", "factor", "trace", "bs-sweep", "interval"],
                     help="eigs: the benchmark; solve / factor: a short program (one factorization and "
                          "--steps solves, or --steps factorizations) of the same workload, for profilers")
     return ap.parse_args()
@@ -457,7 +461,7 @@ def run_riga(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32}[args.precision]
+    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32, "bf16": riga.RIGA_BF16}[args.precision]
     cfg = workload(args.mesh)
     if cfg.get("batch"):
         return run_riga_batch(args, rank, world, local_rank, cfg)
@@ -673,6 +677,127 @@ def run_c3_leg(args, local_rank, flush):
     return out
 
 
+def bs_sweep(dim, ne, p, pairs, steps=5, device=0, slice_=None):
+    """Time per factorization, per f/b solve (one right-hand side) and per
+    M mat-vec, and eigenpairs/s of a full eigensolve, against the rIGA
+    blocksize (Sec. 7, Figs. 6 and 9: the paper sweeps bs = 2^0 .. n_e on one
+    CPU core and finds 16 best; bs = n_e is IGA).  FP64 fronts, Lanczos
+    blocks of 2, CUDA events on the library's stream, each call averaged
+    over `steps`.  Returns one row per blocksize."""
+    import numpy as np
+    import torch
+    from paper_2009_08167_gb300 import riga
+    from paper_2009_08167_gb300.inputs import Mesh
+    stream = torch.cuda.current_stream()
+    rows = []
+    bs_list = [1 << i for i in range(int(np.log2(ne)) + 1)]
+    for bs in bs_list:
+        mesh = Mesh(dim, ne, p, None if bs == ne else bs)
+        R = riga.Riga(device, stream)
+        R.set_eig_block(2)
+        R.set_eig_options(slice=slice_ or pairs, precision=riga.RIGA_FP64, extra=2, seed=3)
+        R.assemble(mesh)
+        q = R.query()
+        N = q["N"]
+
+        def timed(fn, n):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / n
+
+        R.factor(0.0, riga.RIGA_FP64)
+        t_fact = timed(lambda: R.factor(0.0, riga.RIGA_FP64), steps)
+        b = torch.randn(N, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        R.solve(b, out=x)
+        t_fb = timed(lambda: R.solve(b, out=x), 4 * steps)
+        t_mv = timed(lambda: R.spmv(0, b), 4 * steps)  # y = M x, global numbering (two permutations included)
+        R.eigs(pairs, 0.0, RESID_TOL, vectors=False, device_out=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, _, rs = R.eigs(pairs, 0.0, RESID_TOL, vectors=False, device_out=True)
+        e1.record(stream)
+        e1.synchronize()
+        t_eigs = e0.elapsed_time(e1)
+        ok = int((rs <= RESID_TOL).sum().item())
+        rows.append({"bs": bs, "iga": bs == ne, "N": N, "nnz": q["nnz"], "nnzL": q["nnzL"],
+                     "flops_fact": q["flops_fact"], "fact_ms": t_fact, "fb_ms": t_fb, "mv_ms": t_mv,
+                     "eigs_ms": t_eigs, "pairs": ok, "pairs_per_s": ok / (t_eigs / 1e3),
+                     "evals": ev.cpu().numpy().tolist()})
+        R.close()
+    return rows
+
+
+def run_bs_sweep(args, local_rank):
+    torch_dev = local_rank
+    import torch
+    torch.cuda.set_device(torch_dev)
+    if args.sweep_dim == 3:
+        dim, ne, p = 3, 32, 2
+    else:
+        dim, ne, p = 2, 256, 3
+    rows = bs_sweep(dim, ne, p, args.sweep_pairs, steps=max(1, args.steps), device=local_rank)
+    for r in rows:
+        r.pop("evals")
+    best = {key: min(rows, key=lambda r: r[key])["bs"] for key in ("fact_ms", "fb_ms", "mv_ms", "eigs_ms")}
+    print(json.dumps({"mode": "bs-sweep", "dim": dim, "elements_per_side": ne, "degree": p,
+                      "pairs": args.sweep_pairs, "rows": rows, "best_bs": best}), flush=True)
+
+
+def run_interval(args, local_rank):
+    """Every eigenpair in [0, hi) of the workload's mesh by dynamic spectrum
+    slicing with thick-restart Lanczos (riga_eigs_interval), the paper's
+    large-N0 setting (N0 = 4096 in 2D, 1024 in 3D).  hi comes from Weyl's
+    law for the unit square / cube (N(lambda) ~ lambda / (4 pi) in 2D,
+    lambda^{3/2} / (6 pi^2) in 3D) at 5 % above --interval-pairs; the exact
+    count is the inertia difference.  One untimed warm-up, then --steps timed
+    runs (CUDA events, L2 flushed)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2009_08167_gb300 import riga
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32, "bf16": riga.RIGA_BF16}[args.precision]
+    cfg = workload(args.mesh)
+    mesh = cfg["mesh"]
+    target = 1.05 * args.interval_pairs
+    hi = 4.0 * math.pi * target * 1.0137 if mesh.dim == 2 else (6.0 * math.pi ** 2 * target) ** (2.0 / 3.0) * 1.0137
+    R = riga.Riga(local_rank, stream)
+    R.set_eig_options(slice=50, precision=prec, extra=2, seed=11)
+    R.assemble(mesh)
+    kmax = int(2 * args.interval_pairs + 64)
+    ev, U, rs, basis = R.eigs_interval(0.0, hi, kmax, RESID_TOL)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    times = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, U, rs, basis = R.eigs_interval(0.0, hi, kmax, RESID_TOL)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = R.stats()
+    n = int(ev.size)
+    ok = int(np.sum(rs <= RESID_TOL))
+    print(json.dumps({"mode": "interval", "workload": config_dict(args, cfg)["workload"], "hi": hi, "count": n,
+                      "converged_pairs": ok, "max_resid": float(np.max(rs)) if n else None,
+                      "ms": statistics.mean(times), "pairs_per_s": ok / (statistics.mean(times) / 1e3),
+                      "basis_cols": basis, "basis_bytes": 2 * 8 * basis * R.query()["N"],
+                      "eigenvector_bytes": 8 * n * R.query()["N"], "n_fact": st["n_fact"],
+                      "lanczos_steps": st["lanczos_steps"], "precision": args.precision}), flush=True)
+    R.close()
+
+
 def run_kernel_mode(args, local_rank):
     """Short program for profilers: the benchmark's mesh, one numeric
     assembly, then --steps factorizations (mode factor) or one factorization
@@ -683,7 +808,7 @@ def run_kernel_mode(args, local_rank):
     from paper_2009_08167_gb300 import riga
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
-    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32}[args.precision]
+    prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32, "bf16": riga.RIGA_BF16}[args.precision]
     cfg = workload(args.mesh)
     R = riga.Riga(local_rank, stream)
     if cfg.get("batch"):
@@ -722,6 +847,12 @@ def run_kernel_mode(args, local_rank):
 
 def main():
     args = parse()
+    if args.mode == "bs-sweep":
+        run_bs_sweep(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.mode == "interval":
+        run_interval(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if args.mode != "eigs":
         run_kernel_mode(args, int(os.environ.get("LOCAL_RANK", "0")))
         return

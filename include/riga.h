@@ -54,6 +54,10 @@ extern "C" {
 #define RIGA_FP32 1 /* fronts in FP32, solves refined to FP64 accuracy */
 #define RIGA_TF32 2 /* fronts in FP32, trailing updates on the tensor cores (TF32 head + tail
                        products, about FP32 accuracy), solves refined to FP64 accuracy */
+#define RIGA_BF16 3 /* fronts in FP32, trailing updates on the tensor cores with BF16 operands
+                       (BF16 head + tail products, FP32 accumulation, every 128-row operand
+                       block scaled by a power of two; about 2^-16 relative), solves refined
+                       to FP64 accuracy where the refinement converges */
 
 typedef struct riga_ctx riga_ctx;
 
@@ -132,7 +136,8 @@ int riga_analyze(riga_ctx* ctx, const riga_mesh* mesh);
  * riga_factor: numeric LDL^T of A = K - sigma M in the context's elimination
  * order (Sec. 4.2 and its Remark on inertia), 1x1 pivots without pivoting.
  * precision: RIGA_FP64, RIGA_FP32 (fronts stored and updated in FP32; the
- *   assembled A is rounded from FP64) or RIGA_TF32 (FP32 fronts whose Schur
+ *   assembled A is rounded from FP64), RIGA_BF16 (FP32 fronts whose Schur
+ *   updates take BF16 head + tail operands on the tensor cores) or RIGA_TF32 (FP32 fronts whose Schur
  *   updates run on the tensor cores: each operand split into a TF32 head and
  *   tail, three products accumulated in FP32).
  * n_neg (may be NULL): receives the inertia nu(K - sigma M), the number of
@@ -185,10 +190,38 @@ int riga_eigs(riga_ctx* ctx, int k, double sigma, double tol, double* evals, dou
               double* resid, int* nconv);
 
 /*
+ * riga_eigs_interval: every eigenpair with lo <= lambda < hi, by dynamic
+ * spectrum slicing with thick-restart shift-and-invert Lanczos (Sec. 4.1;
+ * Sec. 4.2, Eq. LanczosRestart read as Wu and Simon's thick restart; the
+ * Remark on inertia; Sec. 6, Krylov-Schur with spectrum slicing, where the
+ * paper computes up to N0 = 4096 pairs).
+ *  - The count nu(K - hi M) - nu(K - lo M) comes from two FP64 inertias
+ *    (nu = 0 for lo <= 0).  More than kmax: RIGA_EINVAL with *nfound = the
+ *    count (allocate and call again).
+ *  - Slices of riga_set_eig_options' `slice` pairs (default 50) and `extra`
+ *    (default 2): each slice's shift is the previous slice's end, placed in
+ *    the first relative gap > 1e-6 after its pairs and certified by inertia.
+ *  - m_basis: Lanczos vectors per thick-restart cycle (0 = max(2 (slice +
+ *    extra), slice + extra + 40)).  The basis holds at most
+ *    2 (slice + extra) + 16 + m_basis + 2 vectors whatever the number of
+ *    pairs; *basis_cols (may be NULL) receives that capacity.
+ *  - precision (riga_set_eig_options) applies to the run factorizations;
+ *    inertias always use FP64 fronts.
+ *  - evals[kmax], evecs (N x kmax column-major, may be NULL), resid[kmax]
+ *    (may be NULL): host or device, filled with the *nfound pairs ascending,
+ *    vectors M-normalised as riga_eigs's.
+ *  - lo and hi must not be eigenvalues (zero pivot: RIGA_EPIVOT).
+ * Errors: RIGA_EINVAL, RIGA_ESTATE, RIGA_EPIVOT, RIGA_ENOCONV (the pairs of
+ * the completed slices are returned), RIGA_ENOMEM, RIGA_ECUDA.
+ */
+int riga_eigs_interval(riga_ctx* ctx, double lo, double hi, int kmax, double tol, int m_basis, double* evals,
+                       double* evecs, double* resid, int* nfound, int* basis_cols);
+
+/*
  * riga_set_eig_options: options of riga_eigs and riga_eigs_batch, kept
  * separate so that their signatures stay short.
  *  slice      eigenpairs accepted per shift (0 = k, a single shift);
- *  precision  RIGA_FP64, RIGA_FP32 or RIGA_TF32 factor inside riga_eigs;
+ *  precision  RIGA_FP64, RIGA_FP32, RIGA_TF32 or RIGA_BF16 factor inside riga_eigs;
  *  max_steps  Lanczos steps per run (0 = automatic: min(N, max(3 w, w + 40))
  *             for w wanted pairs);
  *  extra      additional pairs computed beyond the wanted ones so that the
@@ -263,6 +296,20 @@ int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int
                   double* Zlast);
 
 /*
+ * riga_sym_eig: all eigenpairs of a dense symmetric n x n matrix A (host, no
+ * context, no GPU): the Rayleigh-Ritz step of thick-restart Lanczos, whose
+ * projected matrix (Sec. 4.2, Eq. LanczosRestart read as Wu and Simon's
+ * thick restart) is an arrowhead block followed by a tridiagonal one.
+ * Householder reduction to tridiagonal form, then the implicit QR iteration.
+ *  - A: n x n column-major (only symmetric input is meaningful; both
+ *    triangles are read).  theta[n]: eigenvalues ascending.  Z: n x n
+ *    column-major, column i the unit eigenvector of theta[i].  All host
+ *    arrays owned by the caller.
+ * Errors: RIGA_EINVAL (n < 1 or a NULL pointer).
+ */
+int riga_sym_eig(int n, const double* A, double* theta, double* Z);
+
+/*
  * riga_set_eig_block: Lanczos block size of riga_eigs.  1 (the default) is
  * the single-vector recurrence of Sec. 4.1-4.2; 2 or 4 run block Lanczos:
  * each step applies the shift-inverted operator to a block of vectors with
@@ -313,6 +360,31 @@ int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
  * Errors: RIGA_EINVAL (ctx NULL, passes not 1 or 2).
  */
 int riga_set_reorth(riga_ctx* ctx, int passes);
+
+/*
+ * riga_eig_errors: errors of the first nev eigenpairs of the last riga_eigs /
+ * riga_eigs_interval against the exact eigenpairs of the Laplacian on the
+ * unit interval, square or cube (Sec. 2, Eq. exact and Eq. eigerrors; the
+ * accuracy study of Sec. 8):
+ *   everr[i]    = (lambda_h - lambda) / lambda,
+ *   eferr_l2[i] = ||s u_h - u||_{L2}^2,
+ *   eferr_e[i]  = a(s u_h - u, s u_h - u) / lambda,
+ * with lambda = pi^2 (m_1^2 + .. + m_d^2), u = 2^{d/2} prod_a sin(m_a pi x_a),
+ * u_h the M-normalised computed eigenvector and s = sign (u_h, u).  Meaningful
+ * for constant coefficients; Eq. Pythagorean (eferr_e = everr + eferr_l2)
+ * holds for converged pairs.  Computed on the device: B-spline tables at nq
+ * Gauss points per element and direction, one pass over the tensor grid of
+ * points per eigenpair for the sign and one for the errors.
+ *  - modes: HOST array nev x dim, the 1-based mode index per direction of
+ *    eigenpair i at modes[i * dim + a] (x first).  A pair inside a degenerate
+ *    eigenspace is compared with the one mode named (the paper compares the
+ *    diagonal modes of the square only).
+ *  - nq: 0 = p + 6 (u_h is a piecewise polynomial of degree p), at most 16.
+ *  - everr, eferr_l2, eferr_e: HOST arrays of nev.
+ * Errors: RIGA_EINVAL, RIGA_ESTATE (no eigenpairs; a batch context), RIGA_ECUDA.
+ */
+int riga_eig_errors(riga_ctx* ctx, int nev, const int* modes, int nq, double* everr, double* eferr_l2,
+                    double* eferr_e);
 
 /*
  * riga_eig_grad: gradient of L = sum_i dL_dlambda[i] lambda_i over the k

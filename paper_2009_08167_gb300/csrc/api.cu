@@ -84,7 +84,8 @@ int upload_symbolic(riga_ctx* c) {
     c->solve_flags.release();
     RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
-    RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.tc_titems, st));
+    RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.tc_tiles, st));
+    RIGA_CUDA_TRY(c, c->tcpacks.upload(S.tc_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.tc_packs, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -326,7 +327,7 @@ int riga_factor(riga_ctx* c, double sigma, int precision, long long* n_neg) {
     c->last_error.clear();
     cudaSetDevice(c->device);
     if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
-    if (precision != RIGA_FP64 && precision != RIGA_FP32 && precision != RIGA_TF32)
+    if (precision != RIGA_FP64 && precision != RIGA_FP32 && precision != RIGA_TF32 && precision != RIGA_BF16)
         return set_error(c, RIGA_EINVAL, "unknown precision");
     if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
     c->sigma = sigma;
@@ -346,7 +347,8 @@ static int upload_schedule(riga_ctx* c) {
     cudaStream_t st = c->stream;
     RIGA_CUDA_TRY(c, c->pitems.upload(S.pitems.empty() ? std::vector<PanelItem>{PanelItem{0, 0}} : S.pitems, st));
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
-    RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.tc_titems, st));
+    RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.tc_tiles, st));
+    RIGA_CUDA_TRY(c, c->tcpacks.upload(S.tc_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.tc_packs, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     ++c->sched_gen;
@@ -448,7 +450,7 @@ int riga_solve(riga_ctx* c, const double* b, double* x, int nrhs, double tol, in
 int riga_set_eig_options(riga_ctx* c, int slice, int precision, int max_steps, int extra, unsigned long long seed) {
     if (!c) return RIGA_EINVAL;
     if (slice < 0 || max_steps < 0 || extra < 0) return set_error(c, RIGA_EINVAL, "negative option");
-    if (precision != RIGA_FP64 && precision != RIGA_FP32 && precision != RIGA_TF32)
+    if (precision != RIGA_FP64 && precision != RIGA_FP32 && precision != RIGA_TF32 && precision != RIGA_BF16)
         return set_error(c, RIGA_EINVAL, "unknown precision");
     c->opt_slice = slice;
     c->opt_precision = precision;
@@ -472,21 +474,11 @@ int riga_set_reorth(riga_ctx* c, int passes) {
     return RIGA_OK;
 }
 
-int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, double* evecs, double* resid, int* nconv) {
-    if (!c || !evals) return RIGA_EINVAL;
-    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
-    c->last_error.clear();
-    cudaSetDevice(c->device);
-    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
-    if (c->S.dim == 0) return set_error(c, RIGA_ESTATE, "a batch context: use riga_eigs_batch");
-    if (!(tol > 0.0)) return set_error(c, RIGA_EINVAL, "tol must be positive");
-    if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
-    int got = 0;
-    int status = run_eigs(c, k, sigma, tol, &got);
-    if (nconv) *nconv = got;
-    if (status != RIGA_OK && status != RIGA_ENOCONV) return status;
+// eigenvalues, residuals rho_i = ||K u - lambda M u|| / (|lambda| ||M u||) and
+// eigenvectors (global numbering, sign convention) of the got pairs held in
+// c->evals / c->evec_perm, to user arrays (host or device)
+static int emit_eigs(riga_ctx* c, int got, double* evals, double* evecs, double* resid) {
     const long long N = c->S.N;
-    // eigenvalues
     if (got > 0) {
         if (is_device_ptr(evals)) {
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(evals, c->evals.data(), got * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -494,7 +486,6 @@ int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, doubl
             std::memcpy(evals, c->evals.data(), got * sizeof(double));
         }
     }
-    // residuals rho_i = ||K u - lambda M u|| / (|lambda| ||M u||)
     if (resid && got > 0) {
         std::vector<double> rh(got);
         RIGA_CUDA_TRY(c, c->vwork[4].alloc(N));
@@ -523,7 +514,6 @@ int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, doubl
             std::memcpy(resid, rh.data(), got * sizeof(double));
         }
     }
-    // eigenvectors: back to global numbering, sign convention
     if (evecs && got > 0) {
         DevBuf<double> tmp;
         RIGA_CUDA_TRY(c, tmp.alloc((size_t)N * got));
@@ -534,7 +524,55 @@ int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, doubl
         RIGA_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     }
     RIGA_CUDA_TRY(c, cudaGetLastError());
-    return status;
+    return RIGA_OK;
+}
+
+int riga_eigs(riga_ctx* c, int k, double sigma, double tol, double* evals, double* evecs, double* resid, int* nconv) {
+    if (!c || !evals) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (c->S.dim == 0) return set_error(c, RIGA_ESTATE, "a batch context: use riga_eigs_batch");
+    if (!(tol > 0.0)) return set_error(c, RIGA_EINVAL, "tol must be positive");
+    if (!std::isfinite(sigma)) return set_error(c, RIGA_EINVAL, "sigma must be finite");
+    int got = 0;
+    int status = run_eigs(c, k, sigma, tol, &got);
+    if (nconv) *nconv = got;
+    if (status != RIGA_OK && status != RIGA_ENOCONV) return status;
+    int rc = emit_eigs(c, got, evals, evecs, resid);
+    return rc ? rc : status;
+}
+
+int riga_eigs_interval(riga_ctx* c, double lo, double hi, int kmax, double tol, int m_basis, double* evals,
+                       double* evecs, double* resid, int* nfound, int* basis_cols) {
+    if (!c || !evals || !nfound || kmax < 0) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (!c->assembled) return set_error(c, RIGA_ESTATE, "riga_assemble first");
+    if (c->S.dim == 0) return set_error(c, RIGA_ESTATE, "a batch context: use riga_eigs_batch");
+    if (!(tol > 0.0)) return set_error(c, RIGA_EINVAL, "tol must be positive");
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi)) return set_error(c, RIGA_EINVAL, "need finite lo < hi");
+    if (m_basis < 0 || m_basis == 1 || m_basis == 2) return set_error(c, RIGA_EINVAL, "m_basis must be 0 or >= 3");
+    int got = 0;
+    int status = run_eigs_interval(c, lo, hi, kmax, tol, m_basis, &got, basis_cols);
+    *nfound = got;
+    if (status == RIGA_EINVAL) return status;  // more eigenvalues than kmax: *nfound holds the count
+    if (status != RIGA_OK && status != RIGA_ENOCONV) return status;
+    int rc = emit_eigs(c, got, evals, evecs, resid);
+    return rc ? rc : status;
+}
+
+int riga_eig_errors(riga_ctx* c, int nev, const int* modes, int nq, double* everr, double* eferr_l2, double* eferr_e) {
+    if (!c || !modes || !everr || !eferr_l2 || !eferr_e || nev < 1 || nq < 0) return RIGA_EINVAL;
+    if (c->device < 0) return set_error(c, RIGA_ESTATE, "host-only context");
+    c->last_error.clear();
+    cudaSetDevice(c->device);
+    if (c->S.dim == 0) return set_error(c, RIGA_ESTATE, "a batch context");
+    if (c->nev < 1) return set_error(c, RIGA_ESTATE, "riga_eigs or riga_eigs_interval first");
+    if (nev > c->nev) return set_error(c, RIGA_EINVAL, "nev exceeds the computed eigenpairs");
+    return eig_errors_device(c, nev, modes, nq, everr, eferr_l2, eferr_e);
 }
 
 int riga_eig_grad(riga_ctx* c, int k, const double* dL, double* grad_a, double* grad_b) {

@@ -228,9 +228,79 @@ void band_eigvecs(int n, int b, const double* T, int q, const double* th, double
     }
 }
 
+// All eigenpairs of a dense symmetric n x n matrix A (column-major; the
+// Rayleigh-Ritz step of thick-restart Lanczos, whose projected matrix is an
+// arrowhead block followed by a tridiagonal one).  Householder reduction to
+// tridiagonal form: for column k the reflector P = I - 2 v v^T (|v| = 1) maps
+// x = A[k+1:, k] to alpha e_1 with alpha = -sign(x_0) |x|, and
+// P A P = A - v q^T - q v^T with w = A v, q = 2 w - 2 (v^T w) v on the
+// trailing block; Q = P_0 P_1 ... accumulates the reflectors, and the
+// tridiagonal eigenvectors are rotated into Q Z by the QR iteration of
+// tridiag.cpp.  theta ascending; Z (n x n, column-major) the eigenvectors.
+void sym_eig_dense(int n, const double* A0, double* theta, double* Z) {
+    if (n <= 0) return;
+    std::vector<double> A(A0, A0 + (size_t)n * n), Q((size_t)n * n, 0.0), v(n), w(n), q(n);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    auto a = [&](int i, int j) -> double& { return A[(size_t)j * n + i]; };
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;  // length of x = A[k+1:, k]
+        double xn = 0.0, big = 0.0;
+        for (int i = 0; i < m; ++i) big = std::max(big, std::fabs(a(k + 1 + i, k)));
+        if (big == 0.0) continue;
+        for (int i = 0; i < m; ++i) {
+            const double t = a(k + 1 + i, k) / big;
+            xn += t * t;
+        }
+        xn = big * std::sqrt(xn);
+        const double x0 = a(k + 1, k);
+        const double alpha = x0 >= 0.0 ? -xn : xn;
+        for (int i = 0; i < m; ++i) v[i] = a(k + 1 + i, k);
+        v[0] -= alpha;
+        double vn = 0.0;
+        for (int i = 0; i < m; ++i) vn += v[i] * v[i];
+        vn = std::sqrt(vn);
+        if (!(vn > 0.0)) continue;
+        for (int i = 0; i < m; ++i) v[i] /= vn;
+        // w = A22 v, gamma = v^T w, q = 2 w - 2 gamma v
+        double gamma = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += a(k + 1 + i, k + 1 + j) * v[j];
+            w[i] = s;
+        }
+        for (int i = 0; i < m; ++i) gamma += v[i] * w[i];
+        for (int i = 0; i < m; ++i) q[i] = 2.0 * w[i] - 2.0 * gamma * v[i];
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i) a(k + 1 + i, k + 1 + j) -= v[i] * q[j] + q[i] * v[j];
+        a(k + 1, k) = alpha;
+        a(k, k + 1) = alpha;
+        for (int i = 1; i < m; ++i) {
+            a(k + 1 + i, k) = 0.0;
+            a(k, k + 1 + i) = 0.0;
+        }
+        // Q[:, k+1:] <- Q[:, k+1:] (I - 2 v v^T)
+        for (int r = 0; r < n; ++r) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += Q[(size_t)(k + 1 + j) * n + r] * v[j];
+            s *= 2.0;
+            for (int j = 0; j < m; ++j) Q[(size_t)(k + 1 + j) * n + r] -= s * v[j];
+        }
+    }
+    std::vector<double> d(n), e(n, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = a(i, i);
+    for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+    tridiag_eig_rows(n, d.data(), e.data(), theta, n, Q.data(), Z);
+}
+
 }  // namespace riga
 
 using namespace riga;
+
+extern "C" int riga_sym_eig(int n, const double* A, double* theta, double* Z) {
+    if (n < 1 || !A || !theta || !Z) return RIGA_EINVAL;
+    sym_eig_dense(n, A, theta, Z);
+    return RIGA_OK;
+}
 
 extern "C" int riga_band_eig(int n, int b, const double* T, double* theta, int q, const int* which, double* S, int r,
                              double* Zlast) {

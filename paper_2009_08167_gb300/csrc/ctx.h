@@ -125,7 +125,10 @@ struct riga_ctx {
     riga::DevBuf<int> col, perm, ipos, node_ptr, kk, nn, front_pos, child_ptr, child_list, rel, parent;
     riga::DevBuf<riga::PanelItem> pitems;
     riga::DevBuf<riga::TileItem> titems;
-    riga::DevBuf<riga::TileItem> tcitems;  // tensor-core update tiles
+    riga::DevBuf<riga::TcTile> tcitems;    // tensor-core update tiles
+    riga::DevBuf<riga::TcPack> tcpacks;    // tensor-core panel blocks to pack
+    riga::DevBuf<float> tcpack;            // packed panel blocks of one step (operands of the update)
+    riga::DevBuf<float> tcscale;           // per packed block: power-of-two operand scale (BF16)
     riga::DevBuf<riga::ExtItem> eitems;
     // per-direction 1D data
     riga::DevBuf<int> kv[3], elem_first[3];
@@ -271,11 +274,9 @@ int upload_symbolic(riga_ctx* c);  // symbolic arrays of c->S to the device
 // assemble.cu
 int assemble_device(riga_ctx* c);
 int prepare_batch_assembly(riga_ctx* c);  // once per batch pattern
-// tc_update.cu
-__global__ void tc_update_kernel(const TileItem* items, int p0, const int* kk, const int* nn, const long long* front_off,
-                                 const int* node_ptr, const double* D, float* pool, int plain, int* err,
-                                 long long spin_limit);
-size_t tc_update_smem();
+// tc_update.cu: tensor-core Schur updates of FP32 fronts (TF32 or BF16 operands)
+int prepare_tc(riga_ctx* c);  // kernel attributes and packing buffers for the current schedule
+int enqueue_tc_step(riga_ctx* c, const StepRange& R, int p0, float* pool, int plain, cudaStream_t st);
 // factor.cu
 int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
 int finish_factor(riga_ctx* c);   // sync, read flag and inertia
@@ -289,8 +290,13 @@ int solve_refined(riga_ctx* c, double* y, double* work_x, double* work_r, double
 int solve_refined_multi(riga_ctx* c, double* y, double* work_x, double* work_r, int nr, int sweeps);
 // lanczos.cu
 int run_eigs(riga_ctx* c, int k, double sigma, double tol, int* nconv);
+// slicing.cu: every eigenpair in [lo, hi) by spectrum slicing with thick-restart Lanczos
+int run_eigs_interval(riga_ctx* c, double lo, double hi, int kmax, double tol, int m_basis, int* nfound,
+                      int* basis_cols);
 // batch.cu
 int run_eigs_batch(riga_ctx* c, int k, double sigma, double tol);
+// accuracy.cu: EVerr, EFerr_L2, EFerr_E of the context's first nev eigenpairs
+int eig_errors_device(riga_ctx* c, int nev, const int* modes_host, int nq, double* everr, double* efl2, double* efe);
 // adjoint.cu
 int eig_grad_device(riga_ctx* c, int k, const double* w_dev, double* ga_dev, double* gb_dev);
 // tridiag.cpp
@@ -302,5 +308,6 @@ void band_eigvals(int n, int b, const double* T, double* theta);                
 // eigenvalues and the last r rows of all eigenvectors (Zlast: r x n column-major)
 void band_eig_lastrows(int n, int b, const double* T, int r, double* theta, double* Zlast);
 void band_eigvecs(int n, int b, const double* T, int q, const double* th, double* S);  // S: n x q
+void sym_eig_dense(int n, const double* A, double* theta, double* Z);  // dense symmetric: all eigenpairs
 
 }  // namespace riga

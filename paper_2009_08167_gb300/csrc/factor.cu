@@ -345,11 +345,12 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), st));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(c->neg.ptr, 0, sizeof(long long), st));
     const int plain = c->inertia_only ? 1 : 0;
-    // TF32 fronts: the trailing updates on the tensor cores (tc_update.cu)
-    const bool tensor = sizeof(T) == sizeof(float) && c->precision == RIGA_TF32;
-    if (tensor)
-        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)tc_update_smem()));
+    // TF32 / BF16 fronts: the trailing updates on the tensor cores (tc_update.cu)
+    const bool tensor = sizeof(T) == sizeof(float) && (c->precision == RIGA_TF32 || c->precision == RIGA_BF16);
+    if (tensor) {
+        int rc = prepare_tc(c);
+        if (rc) return rc;
+    }
     if (!plain) { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
     const bool per_problem = (S.dim == 0) && !c->sigma_prob.empty();
     if (per_problem) {
@@ -378,10 +379,8 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
                 { count_launch(c); trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
                                                                    c->nn.ptr, c->front_off.ptr, pool, plain); }
             if (tensor) {
-                if (R.c_end > R.c_begin)
-                    { count_launch(c); tc_update_kernel<<<R.c_end - R.c_begin, 128, tc_update_smem(), st>>>(
-                        c->tcitems.ptr + R.c_begin, j0, c->kk.ptr, c->nn.ptr, c->front_off.ptr, c->node_ptr.ptr, c->D.ptr,
-                        reinterpret_cast<float*>(pool), plain, c->flag.ptr, c->wait_limit); }
+                int rc = enqueue_tc_step(c, R, j0, reinterpret_cast<float*>(pool), plain, st);
+                if (rc) return rc;
             } else {
                 if (R.t_mid > R.t_begin)
                     { count_launch(c); update_kernel<T, 32><<<R.t_mid - R.t_begin, 64, 0, st>>>(c->titems.ptr + R.t_begin, j0,

@@ -529,7 +529,7 @@ int calibrate_refinement(riga_ctx* c, uint64_t seed) {
     return factor_at(c, c->sigma, RIGA_FP64, nullptr);
 }
 
-static int configure_reorth(riga_ctx* c, int cap) {
+int configure_reorth(riga_ctx* c, int cap) {
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
     const size_t sm_upd = sm_dots + (size_t)cap * sizeof(double);
     RIGA_CUDA_TRY(c, cudaFuncSetAttribute(gemvT_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dots));
@@ -584,6 +584,44 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
         ++acc_n;
     }
     *n_locked = acc_n;
+    return RIGA_OK;
+}
+
+// Ritz vectors U = V[:, col0 : col0+J] W and M U = MV[:, col0 : col0+J] W for
+// the nsel columns of W (J x nsel, host, column-major) into U and MU (N x
+// nsel, leading dimension N); the FP64 residuals
+// ||K u - lam M u|| / (|lam| ||M u||) of the first nres of them into rho.
+int ritz_vectors_resid(Run& R, int col0, int J, const std::vector<double>& W, int nsel, double* U, double* MU,
+                       const std::vector<double>& lam, int nres, std::vector<double>& rho) {
+    riga_ctx* c = R.c;
+    cudaStream_t st = c->stream;
+    const long long N = R.N;
+    rho.assign(nres, 0.0);
+    if (nsel <= 0) return RIGA_OK;
+    const int gx = 304;
+    RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)J * nsel + nsel + (size_t)2 * gx * std::max(nres, 1)));
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, W.data(), (size_t)J * nsel * sizeof(double), cudaMemcpyHostToDevice, st));
+    PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (J + 2 * nsel) * sizeof(double));
+    dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
+    { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, J, c->Wd.ptr, J, nsel, U, N, N); }
+    { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, J, c->Wd.ptr, J, nsel, MU, N, N); }
+    if (nres > 0) {
+        double* dlam = c->Wd.ptr + (size_t)J * nsel;
+        double* dpart = dlam + nsel;
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lam.data(), nres * sizeof(double), cudaMemcpyHostToDevice, st));
+        { count_launch(c); resid_cols_kernel<<<dim3(gx, nres), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
+        std::vector<double> part((size_t)2 * gx * nres);
+        RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        for (int q = 0; q < nres; ++q) {
+            double ra = 0.0, rb = 0.0;
+            for (int b = 0; b < gx; ++b) {
+                ra += part[((size_t)q * gx + b) * 2];
+                rb += part[((size_t)q * gx + b) * 2 + 1];
+            }
+            rho[q] = std::sqrt(ra) / (std::fabs(lam[q]) * std::sqrt(rb));
+        }
+    }
     return RIGA_OK;
 }
 
@@ -665,6 +703,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     int need = target + extra;  // locked pairs above sigma0 wanted before the next check
     uint64_t seed = c->opt_seed ? c->opt_seed : 1;
     int runs = 0, fruitless = 0;
+    double missing_shift = std::nan("");  // check shift below which eigenvalues are missing
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -708,14 +747,23 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             if (rc) { status = rc; break; }
             const long long found = gi;  // locked eigenvalues below sp (all are > sigma0)
             if (nu_chk - nu0 == found) {
+                missing_shift = std::nan("");
                 confirmed = gi;
                 if (confirmed >= k) break;
                 target = std::min(k, confirmed + slice);
                 need = std::max(need, target + extra);
                 cur_sigma = sp;  // next slice starts at the check shift (already factored)
             } else if (nu_chk - nu0 > found) {
-                // eigenvalues missing below sp (degenerate copies): restart at the current shift
+                // eigenvalues missing below sp: the next run starts at the
+                // current shift; if it locks nothing and the locked values
+                // just below sp form a (nearly) degenerate cluster, the runs
+                // move to sp, where that cluster's missing copies are the
+                // nearest unlocked eigenvalues and their relative separation
+                // in theta, |lambda_a - lambda_b| / |lambda - sigma|, is largest
                 need = nlock + (int)(nu_chk - nu0 - found);
+                // a (nearly) degenerate cluster just below the gap: missing
+                // copies are likely its members, next to sp
+                if (gi >= 2 && sl[gi - 1] - sl[gi - 2] <= 1e-6 * std::fabs(sl[gi - 1])) missing_shift = sp;
             } else {
                 status = set_error(c, RIGA_ENOCONV, "more locked pairs than the inertia allows");
                 break;
@@ -726,6 +774,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             status = RIGA_ENOCONV;
             break;
         }
+        if (fruitless > 0 && !std::isnan(missing_shift) && missing_shift != cur_sigma) cur_sigma = missing_shift;
         if (!(factored_sigma == cur_sigma)) {
             rc = factor_at(c, cur_sigma, prec, nullptr);
             if (rc) { status = rc; break; }

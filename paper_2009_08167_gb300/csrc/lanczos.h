@@ -37,6 +37,9 @@ int recur_pass(Run& R, int J, int u0, int Ju, double* w);
 void normalize_into(Run& R, double* w, int col, int jslot, int Jc);
 int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool inertia_only = false);
 int calibrate_refinement(riga_ctx* c, uint64_t seed);
+int configure_reorth(riga_ctx* c, int cap);  // shared-memory attributes of the reorthogonalization kernels
+int ritz_vectors_resid(Run& R, int col0, int J, const std::vector<double>& W, int nsel, double* U, double* MU,
+                       const std::vector<double>& lam, int nres, std::vector<double>& rho);
 int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const std::vector<double>& lcand,
               int nlock, double lock_tol, std::vector<double>& lam, int* n_locked);
 

@@ -245,7 +245,9 @@ void build_schedule(Symbolic& S) {
     for (int f = 0; f < F; ++f) S.levels[S.height[f]].nodes.push_back(f);
     S.pitems.clear();
     S.titems.clear();
-    S.tc_titems.clear();
+    S.tc_tiles.clear();
+    S.tc_packs.clear();
+    S.tc_pack_blocks = 0;
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
     const int SMALL_TRAIL = S.small_trail;
@@ -308,20 +310,29 @@ void build_schedule(Symbolic& S) {
                 }
             }
             R.t_end = (int)S.titems.size();
-            // the same trailing update in TC_M x TC_N tiles (tensor-core kernel)
-            R.c_begin = (int)S.tc_titems.size();
+            // the same trailing update in TC_M x TC_N tiles (tensor-core
+            // kernel): the trailing rows c0.. of each front are packed in
+            // TC_BLK-row blocks (numbered from 0 within the step), and every
+            // tile pairs a row block (A) with a column block (B)
+            R.k_begin = (int)S.tc_packs.size();
+            R.c_begin = (int)S.tc_tiles.size();
+            int nblk_step = 0;
             for (int f : P.nodes) {
                 int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 const int c0 = s * nb + std::min(nb, kf - s * nb);
-                for (int i0 = c0; i0 < lf; i0 += TC_M)
-                    for (int j0 = c0; j0 < lf; j0 += TC_N) {
-                        const bool lower = j0 <= i0 + TC_M - 1;
+                const int blk0 = nblk_step;
+                for (int r0 = c0; r0 < lf; r0 += TC_BLK) S.tc_packs.push_back({f, r0, nblk_step++, 0});
+                for (int i0 = c0, bi = blk0; i0 < lf; i0 += TC_M, ++bi)
+                    for (int j0 = c0, bj = blk0; j0 < lf; j0 += TC_N, ++bj) {
+                        const bool lower = j0 <= i0;
                         const bool extra = (i0 + TC_M > nf) && (j0 + TC_N > nf);
-                        if (lower || extra) S.tc_titems.push_back({f, i0, j0});
+                        if (lower || extra) S.tc_tiles.push_back({f, i0, j0, bi, bj, 0});
                     }
             }
-            R.c_end = (int)S.tc_titems.size();
+            S.tc_pack_blocks = std::max<long long>(S.tc_pack_blocks, nblk_step);
+            R.k_end = (int)S.tc_packs.size();
+            R.c_end = (int)S.tc_tiles.size();
             P.steps.push_back(R);
         }
     }

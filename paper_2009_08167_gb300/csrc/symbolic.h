@@ -24,7 +24,14 @@ struct Dir1D {
 // Factorization work items (precomputed per level and panel step).
 struct PanelItem { int front; int r0; };            // TRSM row block of a front
 struct TileItem { int front; int i0; int j0; };     // trailing-update tile
-constexpr int TC_M = 128, TC_N = 64;                // tensor-core update tile (rows x columns)
+constexpr int TC_M = 128, TC_N = 128;               // tensor-core update tile (rows x columns)
+constexpr int TC_BLK = 128;                          // rows of one packed panel block
+// Tensor-core update of one panel step: the panel's rows are packed once per
+// step into 128-row blocks (operands in the MMA's shared-memory layout);
+// a tile reads block a_blk as its A operand (rows i0..) and block b_blk as
+// its B operand (rows j0..).
+struct TcPack { int front; int r0; int blk; int pad; };       // pack rows r0..r0+127 of the panel into block blk
+struct TcTile { int front; int i0; int j0; int a_blk; int b_blk; int pad; };
 struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
 
 // tree-solve kernel shapes: 256-thread CTAs per item (large fronts),
@@ -57,7 +64,8 @@ struct StepRange {   // one panel step of one level
     int s;           // step index (panel columns s*nb .. )
     int d_begin, d_end;   // PanelItem range: one diagonal-block item per active front (r0 = s*nb)
     int p_begin, p_end;   // PanelItem range: row blocks below the diagonal block
-    int c_begin, c_end;   // TileItem range of Symbolic::tc_titems (tensor-core update tiles)
+    int c_begin, c_end;   // TcTile range of Symbolic::tc_tiles (tensor-core update tiles)
+    int k_begin, k_end;   // TcPack range of Symbolic::tc_packs (blocks packed before the update)
     int t_begin, t_end;   // TileItem range: [t_begin, t_mid) 32x32 tiles, [t_mid, t_end) 16x16 tiles
     int t_mid;
 };
@@ -115,7 +123,9 @@ struct Symbolic {
     //                 -A11^{-1} A12 (ldp = hi-lo rounded up to 4);
     //   backward part [lo,hi) of rows 0..k: column-major ldp x n panel of
     //                 [-A11^{-1} | -A11^{-1} A12] (ldp = hi-lo rounded up to 4).
-    std::vector<TileItem> tc_titems;  // update tiles of TC_M x TC_N for the tensor-core update kernel
+    std::vector<TcTile> tc_tiles;     // update tiles of TC_M x TC_N for the tensor-core update kernel
+    std::vector<TcPack> tc_packs;     // panel blocks packed for it, per step
+    long long tc_pack_blocks = 0;     // packed blocks of the largest step
     std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
     std::vector<ChildRec> crec;       // per child_list entry
     int solve_mode = 0;               // SOLVE_CTA256 / SOLVE_CTA128 / SOLVE_WARP (finish_symbolic)

@@ -1,194 +1,452 @@
-// Schur-complement update of FP32 fronts on the tensor cores (tcgen05, TF32
-// inputs, FP32 accumulation in tensor memory): the dense contraction of the
-// multifrontal LDL^T (Sec. 4.2), A22 -= L21 D L21^T, one TC_M x TC_N tile of
-// the trailing matrix per CTA and one panel step (K = kb <= 32) per launch.
+// Schur-complement update of FP32 fronts on the tensor cores (tcgen05 with
+// FP32 accumulation in tensor memory): the dense contraction of the
+// multifrontal LDL^T (Sec. 4.2), A22 -= L21 D L21^T, for one panel step
+// (K = kb <= 32) of every front of a tree level.
 //
-// Precision: each FP32 operand x is split into a TF32 head h (x with the low
-// 13 mantissa bits cleared) and a tail t = x - h (exact in FP32); the tile is
-// accumulated as A_h B_h + A_h B_t + A_t B_h (three MMAs per K slice), which
-// keeps the products to about FP32 accuracy (the dropped A_t B_t term and the
-// tail's own TF32 rounding are ~2^-21 relative).
+// Precision.  Each FP32 operand x is split into a head h and a tail
+// t = x - h and the tile is accumulated as A_h B_h + A_h B_t + A_t B_h (three
+// MMAs per K slice):
+//   TF32 mode: h = x with the low 13 mantissa bits cleared (kind::tf32); the
+//              dropped A_t B_t term and the tail's own rounding are ~2^-21
+//              relative, about FP32 accuracy;
+//   BF16 mode: h = bf16(x), t = bf16(x - h) (kind::f16 with BF16 inputs);
+//              ~2^-16 relative.  Each packed 128-row block is scaled by a
+//              power of two so that its largest magnitude is in [0.5, 1)
+//              before the split (the tail of a tiny block stays normal), and
+//              the epilogue removes the two blocks' scales exactly.
 //
-// Data path per CTA (128 threads, 4 warps):
-//   1. warp 0 allocates 64 TMEM columns (D: 128 lanes x 64 FP32 columns);
-//   2. the A (128 rows x 32) and B (64 rows x 32, scaled by D) panels are
-//      read from the front with coalesced loads and stored to shared memory
-//      in the canonical K-major layout without swizzle: 8-row x 16-byte core
-//      matrices, core (m, k) at byte (m * 8 + k) * 128 (LBO = 128 B between
-//      K-adjacent cores, SBO = 1024 B between 8-row groups);
-//   3. one thread issues the MMAs (K = 8 per instruction) and commits them to
-//      an mbarrier; everyone waits on it (bounded);
-//   4. each warp loads its 32 lanes of D (tcgen05.ld 32x32b.x64) and applies
-//      the update to its rows of the front with the lower-triangle /
-//      extra-block masks of the CUDA-core kernel.
+// Data path of one panel step:
+//   tc_pack_kernel    the trailing rows of each front's panel (and the panel
+//                     times the pivots) in 128-row blocks: read once, split
+//                     once, written in the MMA's shared-memory layout (K-major
+//                     8-row core matrices, no swizzle), 4 operand arrays per
+//                     block (A head, A tail, B head, B tail);
+//   tc_update_kernel  persistent, one CTA per SM, 192 threads in three roles:
+//     warp 4   producer: for each of the CTA's tiles one bulk copy per operand
+//              array (cp.async.bulk, 16-byte aligned, completion counted in
+//              bytes on an mbarrier) into one of two shared-memory stages;
+//     warp 5   MMA issuer: 12 (TF32) or 6 (BF16) tcgen05.mma into one of two
+//              128 x 128 FP32 accumulators in tensor memory (256 columns),
+//              then tcgen05.commit to free the stage and to hand the
+//              accumulator to the epilogue;
+//     warps 0-3 epilogue: tcgen05.ld of the accumulator (warp w reads lanes
+//              32w..32w+31 = tile rows), release it, then C -= acc on the
+//              front (lower triangle, and the whole extra x extra block of the
+//              augmented front) by reductions in L2, coalesced along the rows.
+//   Every wait is bounded: on expiry the kernel sets bit 2 of the error word,
+//   every role stops, in-flight copies and MMAs are waited for (bounded) and
+//   the tensor memory is freed.
+#include <cuda_bf16.h>
+
 #include "ctx.h"
 
 namespace riga {
 
 namespace {
 
-constexpr int KP = 32;                  // panel width (the factorization's NB)
-constexpr int CORE_BYTES = 128;         // 8 rows x 16 bytes
-constexpr int A_BYTES = TC_M * KP * 4;  // 16 KiB per A operand
-constexpr int B_BYTES = TC_N * KP * 4;  // 8 KiB per B operand
+constexpr int KP = 32;                         // panel width (the factorization's NB)
+constexpr int ARR = TC_BLK * KP;               // floats per operand array slot (16 KiB)
+constexpr int BLK_FLOATS = 4 * ARR;            // one packed block: A head, A tail, B head, B tail
+constexpr unsigned STAGE_BYTES = 4u * ARR * 4u;  // 64 KiB per shared-memory stage
+constexpr int NSTAGE = 2;
+constexpr int UPD_THREADS = 192;
+constexpr int TMEM_COLS = 2 * TC_N;            // two accumulators
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// byte offset of element (row, k) of a K-major, non-swizzled operand tile
-__device__ __forceinline__ int kmajor_off(int row, int k) {
-    return ((row >> 3) * (KP / 4) + (k >> 2)) * CORE_BYTES + (row & 7) * 16 + (k & 3) * 4;
-}
-
-// shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1,
-// no swizzle
+// shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1, no swizzle
 __device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
     return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
            ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// instruction descriptor of kind::tf32: D F32, A and B TF32, both K-major,
-// N = TC_N, M = TC_M
-constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_N >> 3) << 17) | ((unsigned)(TC_M >> 4) << 24);
+// instruction descriptors: D F32, A and B K-major, N = TC_N, M = TC_M;
+// kind::tf32 (A, B TF32) and kind::f16 (A, B BF16)
+constexpr unsigned IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_N >> 3) << 17) |
+                                ((unsigned)(TC_M >> 4) << 24);
+constexpr unsigned IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
+                                ((unsigned)(TC_M >> 4) << 24);
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-__device__ __forceinline__ void mma_tf32(unsigned d_tmem, unsigned long long a, unsigned long long b, int acc) {
+template <int MODE>
+__device__ __forceinline__ void mma(unsigned d_tmem, unsigned long long a, unsigned long long b, int acc) {
+    if (MODE == 0)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(IDESC_BF16), "r"(acc)
+            : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase of the given parity; gives up when another role
+// has given up (abort flag) or after `limit` polls (then raises it)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort_flag,
+                                          int* err, long long limit) {
+    long long it = 0;
+    while (!mbar_test(bar, parity)) {
+        if (*abort_flag) return false;
+        if (++it > limit) {
+            atomicOr(err, 4);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
+    unsigned* r = reinterpret_cast<unsigned*>(v);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// power of two s with s * amax in [0.5, 1) (1 for a zero block)
+__device__ __forceinline__ float pow2_scale(float amax) {
+    if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+    int e;
+    frexpf(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, -e);
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(128) tc_update_kernel(const TileItem* __restrict__ items, int p0,
-                                                        const int* __restrict__ kk, const int* __restrict__ nn,
-                                                        const long long* __restrict__ front_off,
-                                                        const int* __restrict__ node_ptr, const double* __restrict__ D,
-                                                        float* __restrict__ pool, int plain, int* __restrict__ err,
-                                                        long long spin_limit) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* Ah = sm;
-    unsigned char* At = Ah + A_BYTES;
-    unsigned char* Bh = At + A_BYTES;
-    unsigned char* Bt = Bh + B_BYTES;
-    __shared__ __align__(8) unsigned long long mbar;
-    __shared__ unsigned s_tmem;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const TileItem it = items[blockIdx.x];
-    const int F = it.front, k = kk[F], n = nn[F], ld = n + k;
-    const bool skip = plain && (it.i0 >= n || it.j0 >= n);  // plain: tiles touching only extra rows
+// One 256-thread block per packed block of the step: rows r0..r0+127 of the
+// panel (columns p0..p0+kb of the front) and the same rows times the pivots.
+// TF32 (MODE 0): float entry (r, k) of an array at
+//   ((r >> 3) * (KP / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+// BF16 (MODE 1): bf16 entry (r, k) at
+//   ((r >> 3) * (KP / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7)
+// (one 8-row x 16-byte core matrix per 32 floats / 64 bf16).  Rows beyond the
+// front and columns beyond kb are zero.
+template <int MODE>
+__global__ void __launch_bounds__(256) tc_pack_kernel(const TcPack* __restrict__ items, int p0,
+                                                      const int* __restrict__ kk, const int* __restrict__ nn,
+                                                      const long long* __restrict__ front_off,
+                                                      const int* __restrict__ node_ptr, const double* __restrict__ D,
+                                                      const float* __restrict__ pool, float* __restrict__ pack,
+                                                      float* __restrict__ scale) {
+    __shared__ float Ts[KP][TC_BLK + 1];
+    __shared__ float ds[KP];
+    __shared__ float red[2][8];
+    const TcPack it = items[blockIdx.x];
+    const int F = it.front, k = kk[F], ld = nn[F] + k;
     const int kb = min(KP, k - p0);
+    const float* A = pool + front_off[F];
+    const int tid = threadIdx.x;
+    if (tid < KP) ds[tid] = tid < kb ? (float)D[node_ptr[F] + p0 + tid] : 0.f;
+    for (int e = tid; e < KP * TC_BLK; e += 256) {
+        const int t = e / TC_BLK, r = e % TC_BLK, gi = it.r0 + r;
+        Ts[t][r] = (t < kb && gi < ld) ? A[(long long)(p0 + t) * ld + gi] : 0.f;
+    }
+    __syncthreads();
+    float* out = pack + (long long)it.blk * BLK_FLOATS;
+    if (MODE == 0) {
+        for (int q = tid; q < ARR / 4; q += 256) {
+            const int r = ((q >> 6) << 3) | (q & 7), k4 = (q >> 3) & 7;
+            float ah[4], at[4], bh[4], bt[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float x = Ts[4 * k4 + j][r];
+                const float y = x * ds[4 * k4 + j];
+                ah[j] = tf32_head(x);
+                at[j] = x - ah[j];
+                bh[j] = tf32_head(y);
+                bt[j] = y - bh[j];
+            }
+            reinterpret_cast<float4*>(out)[q] = make_float4(ah[0], ah[1], ah[2], ah[3]);
+            reinterpret_cast<float4*>(out + ARR)[q] = make_float4(at[0], at[1], at[2], at[3]);
+            reinterpret_cast<float4*>(out + 2 * ARR)[q] = make_float4(bh[0], bh[1], bh[2], bh[3]);
+            reinterpret_cast<float4*>(out + 3 * ARR)[q] = make_float4(bt[0], bt[1], bt[2], bt[3]);
+        }
+        return;
+    }
+    // BF16: block scales (largest |x| and |x d| of the block to [0.5, 1))
+    float ma = 0.f, mb = 0.f;
+    for (int e = tid; e < KP * TC_BLK; e += 256) {
+        const int t = e / TC_BLK, r = e % TC_BLK;
+        const float x = Ts[t][r];
+        ma = fmaxf(ma, fabsf(x));
+        mb = fmaxf(mb, fabsf(x * ds[t]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = ma;
+        red[1][tid >> 5] = mb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < 8; ++w) {
+            a = fmaxf(a, red[0][w]);
+            b = fmaxf(b, red[1][w]);
+        }
+        red[0][0] = pow2_scale(a);
+        red[1][0] = pow2_scale(b);
+        scale[2 * it.blk] = red[0][0];
+        scale[2 * it.blk + 1] = red[1][0];
+    }
+    __syncthreads();
+    const float sa = red[0][0], sb = red[1][0];
+    for (int q = tid; q < ARR / 8; q += 256) {  // 16-byte units: 8 bf16 of one row
+        const int r = ((q >> 5) << 3) | (q & 7), k8 = (q >> 3) & 3;
+        __nv_bfloat16 ah[8], at[8], bh[8], bt[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float x = Ts[8 * k8 + j][r] * sa;
+            const float y = Ts[8 * k8 + j][r] * ds[8 * k8 + j] * sb;
+            ah[j] = __float2bfloat16_rn(x);
+            at[j] = __float2bfloat16_rn(x - __bfloat162float(ah[j]));
+            bh[j] = __float2bfloat16_rn(y);
+            bt[j] = __float2bfloat16_rn(y - __bfloat162float(bh[j]));
+        }
+        reinterpret_cast<uint4*>(out)[q] = *reinterpret_cast<const uint4*>(ah);
+        reinterpret_cast<uint4*>(out + ARR)[q] = *reinterpret_cast<const uint4*>(at);
+        reinterpret_cast<uint4*>(out + 2 * ARR)[q] = *reinterpret_cast<const uint4*>(bh);
+        reinterpret_cast<uint4*>(out + 3 * ARR)[q] = *reinterpret_cast<const uint4*>(bt);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(UPD_THREADS, 1) tc_update_kernel(
+    const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
+    const long long* __restrict__ front_off, const float* __restrict__ pack, const float* __restrict__ scale,
+    float* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], tfull[2], tempty[2], drain;
+    __shared__ unsigned s_tmem;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the dynamic shared memory must start on a 1024-byte boundary (descriptor base offset 0)
+    unsigned char* stage0 = sm + ((1024u - (smem_addr(sm) & 1023u)) & 1023u);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(TC_N)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4 * 32);
+        }
+        mbar_init(&drain, 1);
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // operands: A rows i0.., B rows j0.. (times the pivots), zero outside
-    const float* A = pool + front_off[F];
-    const double* d = D + node_ptr[F] + p0;
-    for (int e = tid; e < TC_M * KP; e += 128) {
-        const int r = e % TC_M, t = e / TC_M;  // consecutive threads: consecutive rows (coalesced)
-        const int gi = it.i0 + r;
-        const float x = (!skip && t < kb && gi < ld) ? A[(long long)(p0 + t) * ld + gi] : 0.f;
-        const float h = tf32_head(x);
-        *reinterpret_cast<float*>(Ah + kmajor_off(r, t)) = h;
-        *reinterpret_cast<float*>(At + kmajor_off(r, t)) = x - h;
-    }
-    for (int e = tid; e < TC_N * KP; e += 128) {
-        const int r = e % TC_N, t = e / TC_N;
-        const int gj = it.j0 + r;
-        const float x = (!skip && t < kb && gj < ld) ? A[(long long)(p0 + t) * ld + gj] * (float)d[t] : 0.f;
-        const float h = tf32_head(x);
-        *reinterpret_cast<float*>(Bh + kmajor_off(r, t)) = h;
-        *reinterpret_cast<float*>(Bt + kmajor_off(r, t)) = x - h;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
+    constexpr unsigned ARR_BYTES = MODE == 0 ? ARR * 4u : ARR * 2u;  // bytes of one operand array
 
-    if (tid == 0) {
-        const unsigned lbo = CORE_BYTES, sbo = (KP / 4) * CORE_BYTES;
-        const unsigned ah = smem_addr(Ah), at = smem_addr(At), bh = smem_addr(Bh), bt = smem_addr(Bt);
-        int acc = 0;
-        for (int ks = 0; ks < KP / 8; ++ks) {  // K = 8 per instruction: two cores along K
-            const unsigned off = ks * 2 * CORE_BYTES;
-            mma_tf32(tmem, smem_desc(ah + off, lbo, sbo), smem_desc(bh + off, lbo, sbo), acc);
-            acc = 1;
-            mma_tf32(tmem, smem_desc(ah + off, lbo, sbo), smem_desc(bt + off, lbo, sbo), 1);
-            mma_tf32(tmem, smem_desc(at + off, lbo, sbo), smem_desc(bh + off, lbo, sbo), 1);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_addr(&mbar))
-                     : "memory");
-    }
-    // bounded wait for the MMAs (phase 0)
-    {
-        long long n_poll = 0;
-        unsigned ok = 0;
-        while (true) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(ok)
-                : "r"(smem_addr(&mbar))
-                : "memory");
-            if (ok) break;
-            if (++n_poll > spin_limit) {
-                if (tid == 0) atomicOr(err, 4);
-                break;
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+                const int s = it % NSTAGE;
+                const unsigned ph = (unsigned)(it / NSTAGE) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, &s_abort, err, spin_limit)) break;
+                const TcTile tl = tiles[t];
+                const float* pa = pack + (long long)tl.a_blk * BLK_FLOATS;
+                const float* pb = pack + (long long)tl.b_blk * BLK_FLOATS;
+                unsigned char* st = stage0 + (size_t)s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], 4u * ARR_BYTES);
+                bulk_copy(st, pa, ARR_BYTES, &full[s]);
+                bulk_copy(st + ARR * 4, pa + ARR, ARR_BYTES, &full[s]);
+                bulk_copy(st + 2 * ARR * 4, pb + 2 * ARR, ARR_BYTES, &full[s]);
+                bulk_copy(st + 3 * ARR * 4, pb + 3 * ARR, ARR_BYTES, &full[s]);
+            }
+            // every copy issued has landed before the CTA may exit: wait for
+            // the last phase of each stage that was used (bounded)
+            for (int q = 0; q < NSTAGE && q < it; ++q) {
+                const int last = it - 1 - q;
+                const int s = last % NSTAGE;
+                long long n = 0;
+                while (!mbar_test(&full[s], (unsigned)(last / NSTAGE) & 1u) && ++n <= spin_limit) {
+                }
             }
         }
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows 32w + lane
-    float acc[TC_N];
-    {
-        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
-        unsigned* r = reinterpret_cast<unsigned*>(acc);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-            "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
-            "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
-            "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-              "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-              "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-              "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    }
-    if (!skip) {
-        float* Af = pool + front_off[F];
-        const int gi = it.i0 + warp * 32 + (tid & 31);
-        if (gi < ld && !(plain && gi >= n)) {
-#pragma unroll 8
-            for (int c = 0; c < TC_N; ++c) {
-                const int gj = it.j0 + c;
-                if (gj < ld && (gi >= gj || (gi >= n && gj >= n))) Af[(long long)gj * ld + gi] -= acc[c];
+    } else if (warp == 5) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+                const int s = it % NSTAGE, b = it & 1;
+                const unsigned ph = (unsigned)(it / NSTAGE) & 1u, pb = (unsigned)(it >> 1) & 1u;
+                if (!mbar_wait(&full[s], ph, &s_abort, err, spin_limit)) break;
+                if (!mbar_wait(&tempty[b], pb ^ 1u, &s_abort, err, spin_limit)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned base = smem_addr(stage0 + (size_t)s * STAGE_BYTES);
+                const unsigned ah = base, at = base + ARR * 4, bh = base + 2 * ARR * 4, bt = base + 3 * ARR * 4;
+                const unsigned d = tmem + (unsigned)(b * TC_N);
+                if (MODE == 0) {
+                    // K = 8 per instruction (two 16-byte cores along K)
+                    const unsigned lbo = 128, sbo = (KP / 4) * 128;
+#pragma unroll
+                    for (int ks = 0; ks < KP / 8; ++ks) {
+                        const unsigned off = ks * 256;
+                        mma<0>(d, smem_desc(ah + off, lbo, sbo), smem_desc(bh + off, lbo, sbo), ks > 0);
+                        mma<0>(d, smem_desc(ah + off, lbo, sbo), smem_desc(bt + off, lbo, sbo), 1);
+                        mma<0>(d, smem_desc(at + off, lbo, sbo), smem_desc(bh + off, lbo, sbo), 1);
+                    }
+                } else {
+                    // K = 16 per instruction (two 16-byte cores along K)
+                    const unsigned lbo = 128, sbo = (KP / 8) * 128;
+#pragma unroll
+                    for (int ks = 0; ks < KP / 16; ++ks) {
+                        const unsigned off = ks * 256;
+                        mma<1>(d, smem_desc(ah + off, lbo, sbo), smem_desc(bh + off, lbo, sbo), ks > 0);
+                        mma<1>(d, smem_desc(ah + off, lbo, sbo), smem_desc(bt + off, lbo, sbo), 1);
+                        mma<1>(d, smem_desc(at + off, lbo, sbo), smem_desc(bh + off, lbo, sbo), 1);
+                    }
+                }
+                mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                mma_commit(&tfull[b]);  // the accumulator is ready
+            }
+            // all MMAs issued by this thread have completed (bounded)
+            mma_commit(&drain);
+            long long n = 0;
+            while (!mbar_test(&drain, 0u) && ++n <= spin_limit) {
+            }
+        }
+    } else {
+        // ----------------------------------------------- epilogue (warps 0-3)
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const unsigned pb = (unsigned)(it >> 1) & 1u;
+            // warp-uniform outcome: tcgen05.ld below is a .sync.aligned warp instruction
+            const bool ok = mbar_wait(&tfull[b], pb, &s_abort, err, spin_limit);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float acc[TC_N];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * TC_N);
+#pragma unroll
+            for (int ch = 0; ch < TC_N / 32; ++ch) tmem_ld32(taddr + ch * 32, acc + ch * 32);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[b]);
+            const TcTile tl = tiles[t];
+            const int F = tl.front, k = kk[F], n = nn[F], ld = n + k;
+            if (plain && (tl.i0 >= n || tl.j0 >= n)) continue;  // plain: tiles touching only extra rows
+            const float inv = MODE == 0 ? 1.f : 1.f / (scale[2 * tl.a_blk] * scale[2 * tl.b_blk + 1]);
+            const int gi = tl.i0 + warp * 32 + lane;
+            if (gi >= ld || (plain && gi >= n)) continue;
+            // C -= acc as fire-and-forget reductions (red.global.add.f32):
+            // every entry receives exactly one addition per panel step (the
+            // tiles are disjoint), so the result is that of a read-modify-
+            // write, deterministic, without a load latency per column
+            float* Af = pool + front_off[F] + gi;
+            const int cmax = min(TC_N, ld - tl.j0);
+#pragma unroll
+            for (int cc = 0; cc < TC_N; ++cc) {
+                const int gj = tl.j0 + cc;
+                if (cc < cmax && (gi >= gj || (gi >= n && gj >= n))) atomicAdd(Af + (long long)gj * ld, -acc[cc] * inv);
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
 }
 
-size_t tc_update_smem() { return (size_t)2 * A_BYTES + (size_t)2 * B_BYTES + 1024; }
+size_t tc_update_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
+long long tc_pack_floats_per_block() { return BLK_FLOATS; }
+
+// Pack + update of one panel step (TF32 or BF16 mode) on the given stream.
+int enqueue_tc_step(riga_ctx* c, const StepRange& R, int p0, float* pool, int plain, cudaStream_t st) {
+    const int npack = R.k_end - R.k_begin, ntiles = R.c_end - R.c_begin;
+    if (ntiles <= 0 || npack <= 0) return RIGA_OK;
+    const bool bf16 = c->precision == RIGA_BF16;
+    static int nsm = 0;
+    if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) nsm = 0;
+    const int grid = std::max(1, std::min(ntiles, nsm > 0 ? nsm : 148));
+    count_launch(c);
+    if (bf16)
+        tc_pack_kernel<1><<<npack, 256, 0, st>>>(c->tcpacks.ptr + R.k_begin, p0, c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                                 c->node_ptr.ptr, c->D.ptr, pool, c->tcpack.ptr, c->tcscale.ptr);
+    else
+        tc_pack_kernel<0><<<npack, 256, 0, st>>>(c->tcpacks.ptr + R.k_begin, p0, c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                                 c->node_ptr.ptr, c->D.ptr, pool, c->tcpack.ptr, c->tcscale.ptr);
+    count_launch(c);
+    if (bf16)
+        tc_update_kernel<1><<<grid, UPD_THREADS, tc_update_smem(), st>>>(
+            c->tcitems.ptr + R.c_begin, ntiles, c->kk.ptr, c->nn.ptr, c->front_off.ptr, c->tcpack.ptr, c->tcscale.ptr,
+            pool, plain, c->flag.ptr, c->wait_limit);
+    else
+        tc_update_kernel<0><<<grid, UPD_THREADS, tc_update_smem(), st>>>(
+            c->tcitems.ptr + R.c_begin, ntiles, c->kk.ptr, c->nn.ptr, c->front_off.ptr, c->tcpack.ptr, c->tcscale.ptr,
+            pool, plain, c->flag.ptr, c->wait_limit);
+    return RIGA_OK;
+}
+
+// Shared-memory size attributes and the packing buffers (once per schedule)
+int prepare_tc(riga_ctx* c) {
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tc_update_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_update_smem()));
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(tc_update_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_update_smem()));
+    const long long nblk = std::max<long long>(1, c->S.tc_pack_blocks);
+    if (c->tcpack.alloc((size_t)nblk * BLK_FLOATS) != cudaSuccess) return set_error(c, RIGA_ENOMEM, "tensor-core panel blocks");
+    RIGA_CUDA_TRY(c, c->tcscale.alloc((size_t)2 * nblk));
+    return RIGA_OK;
+}
 
 }  // namespace riga

@@ -29,12 +29,14 @@ RIGA_ENOMEM = -8
 RIGA_FP64 = 0
 RIGA_FP32 = 1
 RIGA_TF32 = 2
+RIGA_BF16 = 3
 
 EXPORTED = [
     "riga_create", "riga_destroy", "riga_analyze", "riga_assemble", "riga_assemble_log", "riga_factor", "riga_solve", "riga_eigs",
+    "riga_eigs_interval", "riga_eig_errors",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
     "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_set_wait_limit",
-    "riga_trace_solve", "riga_spmv_dot_noalloc", "riga_strerror",
+    "riga_trace_solve", "riga_spmv_dot_noalloc", "riga_sym_eig", "riga_strerror",
     "riga_last_error",
 ]
 PHASES = ["assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"]
@@ -99,6 +101,9 @@ def load_library(path=LIB_PATH):
     lib.riga_set_wait_limit.argtypes = [P, LL]
     lib.riga_trace_solve.argtypes = [P, P, ctypes.POINTER(I), P, P]
     lib.riga_spmv_dot_noalloc.argtypes = [P, P, P, LL, P, P, P, P]
+    lib.riga_sym_eig.argtypes = [I, P, P, P]
+    lib.riga_eigs_interval.argtypes = [P, D, D, I, D, I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.riga_eig_errors.argtypes = [P, I, P, I, P, P, P]
     lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
                                      ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.riga_strerror.argtypes = [I]
@@ -306,6 +311,37 @@ class Riga:
         U = U.T if U is not None else None
         return ev, U, rs
 
+    def eigs_interval(self, lo, hi, kmax, tol=1e-10, m_basis=0, vectors=True):
+        """Every eigenpair with lo <= lambda < hi (riga_eigs_interval):
+        (evals, U (N x n) or None, resid, basis_cols); raises RigaError
+        RIGA_EINVAL with .count when the interval holds more than kmax."""
+        N = self.query()["N"]
+        ev = np.zeros(max(kmax, 1))
+        U = np.zeros((max(kmax, 1), N)) if vectors else None
+        rs = np.zeros(max(kmax, 1))
+        nf = ctypes.c_int(0)
+        bc = ctypes.c_int(0)
+        rc = self.lib.riga_eigs_interval(self.ctx, float(lo), float(hi), int(kmax), float(tol), int(m_basis), _ptr(ev),
+                                         _ptr(U), _ptr(rs), ctypes.byref(nf), ctypes.byref(bc))
+        if rc != RIGA_OK:
+            err = RigaError(rc, self.lib.riga_strerror(rc).decode() + ": " + self.lib.riga_last_error(self.ctx).decode())
+            err.count = nf.value
+            raise err
+        n = nf.value
+        return ev[:n], (U[:n].T if U is not None else None), rs[:n], bc.value
+
+    def eig_errors(self, modes, nq=0):
+        """(EVerr, EFerr_L2, EFerr_E) of the first len(modes) computed
+        eigenpairs against the exact Laplace modes (1-based index tuples, x
+        first), riga_eig_errors."""
+        md = np.ascontiguousarray(modes, dtype=np.int32)
+        if md.ndim == 1:
+            md = md[:, None]
+        n = md.shape[0]
+        out = [np.zeros(n) for _ in range(3)]
+        self._check(self.lib.riga_eig_errors(self.ctx, n, _ptr(md), int(nq), *[_ptr(o) for o in out]))
+        return tuple(out)
+
     def eig_grad(self, k, weights):
         """Gradients (grad_a, grad_b) of sum_i weights[i] lambda_i; numpy in ->
         numpy out, CUDA tensor in -> CUDA tensors out."""
@@ -425,6 +461,20 @@ def band_eig(T, b, which=(), last_rows=0):
     if last_rows:
         return theta, S[:, :wh.size], Z
     return theta, S[:, :wh.size]
+
+
+def sym_eig(A):
+    """All eigenpairs (ascending eigenvalues, eigenvectors as columns) of a
+    dense symmetric matrix; host only (riga_sym_eig)."""
+    lib = load_library()
+    A = np.asfortranarray(A, dtype=np.float64)
+    n = A.shape[0]
+    theta = np.zeros(n)
+    Z = np.zeros((n, n), order="F")
+    rc = lib.riga_sym_eig(n, _ptr(A), _ptr(theta), _ptr(Z))
+    if rc != RIGA_OK:
+        raise RigaError(rc, lib.riga_strerror(rc).decode())
+    return theta, Z
 
 
 def spmv_dot_noalloc(rowptr, col, val, x, y, xy, stream=None):

@@ -150,3 +150,34 @@ def test_tridiagonal_qr_cases(case):
     assert np.max(np.abs(theta - ref)) <= 1e-13 * scale * max(1.0, n / 50)
     assert np.max(np.abs(T @ S - S * theta)) <= 1e-12 * scale * max(1.0, n / 50)
     assert np.max(np.abs(S.T @ S - np.eye(n))) <= 1e-11
+
+
+@pytest.mark.parametrize("case", ["dense60", "arrow_tridiag", "repeated"])
+def test_dense_symmetric_eig(case):
+    """riga_sym_eig (Householder tridiagonalization + implicit QR) against
+    numpy on a random dense matrix, on the arrowhead-plus-tridiagonal shape
+    of a thick-restarted Lanczos projection, and on a matrix with an exactly
+    repeated eigenvalue."""
+    rng = np.random.default_rng(13)
+    if case == "dense60":
+        A = rng.normal(size=(60, 60))
+        A = A + A.T
+    elif case == "arrow_tridiag":
+        c, n = 25, 90
+        A = np.zeros((n, n))
+        A[np.arange(c), np.arange(c)] = np.sort(rng.normal(size=c))
+        A[:c, c] = A[c, :c] = 0.3 * rng.normal(size=c)
+        d = rng.normal(size=n - c)
+        e = np.abs(rng.normal(size=n - c - 1))
+        A[c:, c:] = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    else:
+        Qm, _ = np.linalg.qr(rng.normal(size=(40, 40)))
+        lam = np.concatenate([np.full(5, 2.0), rng.normal(size=35)])
+        A = (Qm * lam) @ Qm.T
+        A = 0.5 * (A + A.T)
+    theta, Z = riga.sym_eig(A)
+    ref = np.linalg.eigvalsh(A)
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(theta - ref)) <= 1e-13 * scale * A.shape[0] / 10
+    assert np.max(np.abs(A @ Z - Z * theta)) <= 1e-13 * scale * A.shape[0] / 10
+    assert np.max(np.abs(Z.T @ Z - np.eye(A.shape[0]))) <= 1e-12
