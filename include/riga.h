@@ -203,7 +203,7 @@ int riga_eigs(riga_ctx* ctx, int k, double sigma, double tol, double* evals, dou
  *    the first relative gap > 1e-6 after its pairs and certified by inertia.
  *  - m_basis: Lanczos vectors per thick-restart cycle (0 = max(2 (slice +
  *    extra), slice + extra + 40)).  The basis holds at most
- *    2 (slice + extra) + 16 + m_basis + 2 vectors whatever the number of
+ *    2 (slice + extra + 8) + 16 + m_basis + 2 vectors whatever the number of
  *    pairs; *basis_cols (may be NULL) receives that capacity.
  *  - precision (riga_set_eig_options) applies to the run factorizations;
  *    inertias always use FP64 fronts.
@@ -254,8 +254,8 @@ int riga_assemble_batch(riga_ctx* ctx, int nprob, const riga_mesh* meshes, const
 
 /*
  * riga_eigs_batch: for every problem of the batch, the k smallest eigenvalues
- * lambda > sigma of K u = lambda M u by shift-and-invert Lanczos (Sec. 4) in
- * FP64, all problems advancing together: one factorization of the forest, one
+ * lambda > sigma of K u = lambda M u by shift-and-invert Lanczos (Sec. 4),
+ * all problems advancing together: one factorization of the forest, one
  * persistent solve and one M-SpMV per Lanczos step for the whole batch, with
  * each problem's recurrence, reorthogonalisation, Rayleigh-Ritz step, locking
  * and inertia-certified completeness check (its own check shift, in one
@@ -265,8 +265,14 @@ int riga_assemble_batch(riga_ctx* ctx, int nprob, const riga_mesh* meshes, const
  *  resid[nprob * k] (may be NULL): HOST, FP64 residuals
  *    ||K u - lambda M u||_2 / (|lambda| ||M u||_2) of the accepted pairs.
  *  nconv[nprob] (may be NULL): HOST, pairs delivered per problem (k or 0).
- * Uses the slice-free options of riga_set_eig_options (max_steps, extra,
- * seed); the precision is always FP64.
+ * Uses the slice-free options of riga_set_eig_options (precision, max_steps,
+ * extra, seed).  precision RIGA_FP32 / RIGA_TF32 / RIGA_BF16: the run
+ * factorization's fronts in that precision (per-problem shifts), every
+ * Lanczos solve refined to FP64 accuracy with FP64 residuals of each
+ * problem's own shifted matrix (the number of sweeps calibrated once per
+ * factorization on a seeded right-hand side; FP64 fronts if refinement
+ * stalls); the Lanczos recurrence, reorthogonalisation, residuals and the
+ * inertia checks stay FP64.
  * Errors: RIGA_ESTATE (no riga_assemble_batch), RIGA_EINVAL (k too large for
  * the smallest problem), RIGA_ENOCONV (outputs of the converged problems
  * valid), RIGA_EPIVOT, RIGA_ENOMEM, RIGA_ECUDA.
@@ -486,6 +492,19 @@ int riga_profile_get(riga_ctx* ctx, int phase, const char** name, long long* lau
  * stays usable.  limit >= 0.  Errors: RIGA_EINVAL.
  */
 int riga_set_wait_limit(riga_ctx* ctx, long long limit);
+
+/*
+ * riga_check_copies: host check (no GPU; a host-only context after
+ * riga_analyze works) of every bulk copy the kernels issue for the current
+ * schedule: the tree solve's operator panels (cp.async.bulk: 16-byte aligned
+ * source, size a multiple of 16 bytes, inside the operator pool) and the
+ * tensor-core update's packed panel blocks (block indices inside the packing
+ * buffer and belonging to the tile's front and panel step).  *n_checked
+ * receives the number of copies and references verified.  The library runs
+ * no kernel on a schedule this check would reject (riga_assemble runs it).
+ * Errors: RIGA_EINVAL (a violation; riga_last_error names it), RIGA_ESTATE.
+ */
+int riga_check_copies(riga_ctx* ctx, long long* n_checked);
 
 /*
  * riga_trace_solve: one forward/backward elimination of b (as riga_solve with

@@ -86,6 +86,7 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
     RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.tc_tiles, st));
     RIGA_CUDA_TRY(c, c->tcpacks.upload(S.tc_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.tc_packs, st));
+    RIGA_CUDA_TRY(c, c->tcnarrow.upload(S.tc_narrow.empty() ? std::vector<TileItemL>{TileItemL{0, 0, 0, 0}} : S.tc_narrow, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -271,6 +272,8 @@ static int assemble_impl(riga_ctx* c, const riga_mesh* m, const double* coefK, c
     std::vector<int> key = mesh_key(m);
     if (key != c->mesh_key) {
         std::string err = build_symbolic(c->S, m->dim, m->ne, m->p, m->mult, m->leaf_extent);
+        long long nchk = 0;
+        if (err.empty()) err = check_bulk_copies(c->S, &nchk);  // every bulk copy aligned and in range
         if (!err.empty()) {
             c->mesh_key.clear();
             return set_error(c, RIGA_EINVAL, err);
@@ -349,6 +352,7 @@ static int upload_schedule(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->titems.upload(S.titems.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.titems, st));
     RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.tc_tiles, st));
     RIGA_CUDA_TRY(c, c->tcpacks.upload(S.tc_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.tc_packs, st));
+    RIGA_CUDA_TRY(c, c->tcnarrow.upload(S.tc_narrow.empty() ? std::vector<TileItemL>{TileItemL{0, 0, 0, 0}} : S.tc_narrow, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     ++c->sched_gen;
@@ -782,6 +786,15 @@ int riga_profile_get(riga_ctx* c, int phase, const char** name, long long* launc
 int riga_set_wait_limit(riga_ctx* c, long long limit) {
     if (!c || limit < 0) return RIGA_EINVAL;
     c->wait_limit = limit;
+    return RIGA_OK;
+}
+
+int riga_check_copies(riga_ctx* c, long long* n_checked) {
+    if (!c || !n_checked) return RIGA_EINVAL;
+    c->last_error.clear();
+    if (c->S.N <= 0) return set_error(c, RIGA_ESTATE, "riga_analyze or riga_assemble first");
+    std::string err = check_bulk_copies(c->S, n_checked);
+    if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
     return RIGA_OK;
 }
 

@@ -496,18 +496,62 @@ void bnormalize(BatchState& B, double* w, double* Mw, int col, int jslot, int J,
 
 }  // namespace
 
-int factor_batch(riga_ctx* c, const std::vector<double>& sig, bool inertia_only) {
+// Factorization of the whole forest with one shift per problem.  An
+// inertia-only factorization (FP64 fronts, no solve operators) leaves the
+// solve state of the previous one (precision, per-problem shifts and their
+// per-position copy) as it was.
+int factor_batch(riga_ctx* c, const std::vector<double>& sig, bool inertia_only, int precision = RIGA_FP64) {
+    const std::vector<double> keep_sig = c->sigma_prob;
+    const int keep_prec = c->precision;
+    const double keep_sigma = c->sigma;
     c->sigma_prob = sig;
     c->sigma = sig.empty() ? 0.0 : sig[0];
-    c->precision = RIGA_FP64;
+    c->precision = inertia_only ? RIGA_FP64 : precision;
     c->inertia_only = inertia_only;
     const bool keep = c->factored;
     int rc = enqueue_factor(c);
     if (rc == RIGA_OK) rc = finish_factor(c);
-    if (inertia_only) c->factored = keep;
+    if (inertia_only) {
+        c->factored = keep;
+        if (!keep_sig.empty()) {
+            // the shifts of the factorization the solves use
+            c->sigma_prob = keep_sig;
+            c->precision = keep_prec;
+            c->sigma = keep_sigma;
+            std::vector<double> sp(c->S.N);
+            for (size_t b = 0; b + 1 < c->S.prob_pos.size(); ++b)
+                for (long long i = c->S.prob_pos[b]; i < c->S.prob_pos[b + 1]; ++i) sp[i] = c->sigma_prob[b];
+            cudaError_t e = c->sig_pos.upload(sp, c->stream);
+            if (e != cudaSuccess && rc == RIGA_OK) rc = set_error(c, RIGA_ECUDA, cudaGetErrorString(e));
+        }
+    }
     c->inertia_only = false;
     c->stats.n_fact++;
     return rc;
+}
+
+// Refinement sweeps of a low-precision batch factorization: the sweeps one
+// seeded right-hand side over the whole forest needs to reach a relative
+// residual of 1e-13 (at least 2); if refinement stalls, the forest is
+// refactored with FP64 fronts at the same shifts.
+int calibrate_refinement_batch(riga_ctx* c, uint64_t seed, const std::vector<double>& sig) {
+    const long long N = c->S.N;
+    for (int i = 2; i < 6; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    std::vector<double> hb(N);
+    uint64_t st = seed ^ 0x5DEECE66DULL;
+    for (long long i = 0; i < N; ++i) hb[i] = ((double)(bsplitmix(st) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->vwork[4].ptr, hb.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int sweeps = 0;
+    int rc = solve_refined(c, c->vwork[4].ptr, c->vwork[2].ptr, c->vwork[3].ptr, 1e-13, 20, 1, &sweeps);
+    if (rc == RIGA_OK) {
+        c->ir_sweeps = std::min(std::max(sweeps, 2), 20);
+        c->stats.ir_sweeps = c->ir_sweeps;
+        return RIGA_OK;
+    }
+    if (rc != RIGA_EREFINE) return rc;
+    c->last_error.clear();
+    c->stats.n_fallback++;
+    return factor_batch(c, sig, false, RIGA_FP64);
 }
 
 // The k smallest eigenvalues above sigma0 of every problem of the batch.
@@ -594,10 +638,33 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     std::vector<int> need(P, want);
     std::vector<double> sig0(P, sigma0);
     clk::time_point t0 = clk::now();
-    int rc = factor_batch(c, sig0, false);
+    // the run factorization: fronts in the chosen precision.  nu(K - sigma0 M)
+    // per problem from FP64 fronts: the run factorization's own inertia on
+    // the FP64 path; 0 without a factorization for sigma0 <= 0 (K and M
+    // positive definite); an FP64 inertia-only factorization otherwise
+    const int prec = c->opt_precision;
+    std::vector<long long> nu0(P, 0);
+    int rc = RIGA_OK;
+    if (prec != RIGA_FP64 && sigma0 > 0.0) {
+        rc = factor_batch(c, sig0, true);
+        if (rc) return rc;
+        nu0 = c->inertia_prob;
+    }
+    rc = factor_batch(c, sig0, false, prec);
     t_fact += ms_since(t0);
     if (rc) return rc;
-    std::vector<long long> nu0 = c->inertia_prob;
+    if (prec == RIGA_FP64) nu0 = c->inertia_prob;
+    double* xw = nullptr;
+    double* rwk = nullptr;
+    if (prec != RIGA_FP64) {
+        // refinement sweeps per solve for this factorization (a seeded
+        // right-hand side over all problems to 1e-13); FP64 fronts if it stalls
+        for (int i = 2; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+        xw = c->vwork[2].ptr;
+        rwk = c->vwork[3].ptr;
+        rc = calibrate_refinement_batch(c, c->opt_seed ? c->opt_seed : 1, sig0);
+        if (rc) return rc;
+    }
     uint64_t seed = c->opt_seed ? c->opt_seed : 1;
     std::vector<double> h_alpha, h_beta;
     int status = RIGA_OK;
@@ -641,7 +708,8 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
             const int col = col0 + j;
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, c->MV.ptr + (long long)col * B.ld, N * sizeof(double),
                                              cudaMemcpyDeviceToDevice, st));
-            rc = enqueue_solve(c, w);
+            rc = c->precision == RIGA_FP64 ? enqueue_solve(c, w)
+                                           : solve_refined(c, w, xw, rwk, 0.0, c->ir_sweeps, 0, nullptr);
             if (rc) {
                 status = rc;
                 break;
@@ -874,6 +942,8 @@ extern "C" int riga_assemble_batch(riga_ctx* c, int nprob, const riga_mesh* mesh
             if (!err.empty()) return set_error(c, RIGA_EINVAL, "problem " + std::to_string(b) + ": " + err);
         }
         std::string err = merge_symbolic(c->S, c->probs);
+        long long nchk = 0;
+        if (err.empty()) err = check_bulk_copies(c->S, &nchk);  // every bulk copy aligned and in range
         if (!err.empty()) return set_error(c, RIGA_EINVAL, err);
         int rc0 = upload_symbolic(c);
         if (rc0) return rc0;

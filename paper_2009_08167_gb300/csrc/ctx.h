@@ -127,6 +127,7 @@ struct riga_ctx {
     riga::DevBuf<riga::TileItem> titems;
     riga::DevBuf<riga::TcTile> tcitems;    // tensor-core update tiles
     riga::DevBuf<riga::TcPack> tcpacks;    // tensor-core panel blocks to pack
+    riga::DevBuf<riga::TileItemL> tcnarrow; // within-super-panel update tiles of the tensor-core schedule
     riga::DevBuf<float> tcpack;            // packed panel blocks of one step (operands of the update)
     riga::DevBuf<float> tcscale;           // per packed block: power-of-two operand scale (BF16)
     riga::DevBuf<riga::ExtItem> eitems;
@@ -183,6 +184,7 @@ struct riga_ctx {
     riga::DevBuf<double> vwork[6];     // N-vectors (permuted order)
     riga::DevBuf<double> red;          // reduction scratch
     int ir_sweeps = 4;                 // refinement sweeps per solve inside Lanczos (FP32 factor)
+    int fp64_sweeps = 1;               // FP64 factor: sweeps per solve (1 = plain; set by a calibration, reset by a factorization)
 
     // -------------------------------------------------------------- Lanczos
     int opt_slice = 0, opt_precision = RIGA_FP64, opt_max_steps = 0, opt_extra = 2;

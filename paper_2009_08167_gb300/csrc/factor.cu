@@ -16,7 +16,9 @@
 //     trsm_kernel      L21 = A21 L11^{-T} D^{-1}, one thread per row;
 //     update_kernel    A22 -= L21 D L21^T on 32x32 (16x16) lower tiles of the
 //                      trailing matrix (remaining fully summed part and the
-//                      Schur complement).
+//                      Schur complement); with tensor-core fronts only the
+//                      columns of the panel's super-panel, the rest once per
+//                      super-panel in tc_update.cu.
 // All items of one launch span every front of the level.  The original
 // entries are scattered into all fronts once, before the first level.
 #include "ctx.h"
@@ -181,10 +183,15 @@ __global__ void trsm_kernel(const PanelItem* __restrict__ items, int j0, const i
         if (t < kb) A[(long long)(j0 + t) * ld + r] = x[t];
 }
 
+// last column (exclusive) a tile may update: the front's end, or the tile's
+// own limit (the end of the super-panel of a within-super-panel update)
+__device__ __forceinline__ int tile_col_end(const TileItem&, int ld) { return ld; }
+__device__ __forceinline__ int tile_col_end(const TileItemL& it, int ld) { return min(ld, it.jend); }
+
 // C[i0:i0+TL, j0:j0+TL] -= L[:, panel] D L[:, panel]^T (64 threads, (TL/8)^2 each;
 // TL = 32, or 16 on the small trailing blocks where 32x32 tiles pad too much)
-template <typename T, int TL>
-__global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__ items, int p0,
+template <typename T, int TL, typename Item = TileItem>
+__global__ void __launch_bounds__(64) update_kernel(const Item* __restrict__ items, int p0,
                                                     const int* __restrict__ kk, const int* __restrict__ nn,
                                                     const long long* __restrict__ front_off,
                                                     const int* __restrict__ node_ptr, const double* __restrict__ D,
@@ -192,10 +199,11 @@ __global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__
     constexpr int R = TL / 8;  // rows and columns per thread
     __shared__ T As[NB][TL];
     __shared__ T Bs[NB][TL];
-    const TileItem it = items[blockIdx.x];
+    const Item it = items[blockIdx.x];
     const int F = it.front, k = kk[F], n = nn[F], ld = n + k;
     if (plain && (it.i0 >= n || it.j0 >= n)) return;  // plain: tiles touching only extra rows
     const int kb = min(NB, k - p0);
+    const int jend = tile_col_end(it, ld);
     T* A = pool + front_off[F];
     const double* d = D + node_ptr[F] + p0;
     const int tid = threadIdx.x;
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(64) update_kernel(const TileItem* __restrict__
 #pragma unroll
     for (int b = 0; b < R; ++b) {
         int gj = it.j0 + ty + 8 * b;
-        if (gj >= ld) continue;
+        if (gj >= jend) continue;
 #pragma unroll
         for (int a = 0; a < R; ++a) {
             int gi = it.i0 + tx + 8 * a;
@@ -379,6 +387,13 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
                 { count_launch(c); trsm_kernel<T><<<R.p_end - R.p_begin, RB, 0, st>>>(c->pitems.ptr + R.p_begin, j0, c->kk.ptr,
                                                                    c->nn.ptr, c->front_off.ptr, pool, plain); }
             if (tensor) {
+                // within the super-panel: this panel's update of the super-panel's
+                // remaining columns (CUDA cores); at its last panel: the whole
+                // trailing matrix with K = the super-panel (tensor cores)
+                if (R.n_end > R.n_begin)
+                    { count_launch(c); update_kernel<T, 32, TileItemL><<<R.n_end - R.n_begin, 64, 0, st>>>(c->tcnarrow.ptr + R.n_begin, j0,
+                                                                       c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                                                       c->node_ptr.ptr, c->D.ptr, pool, plain); }
                 int rc = enqueue_tc_step(c, R, j0, reinterpret_cast<float*>(pool), plain, st);
                 if (rc) return rc;
             } else {
@@ -409,6 +424,7 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
 
 int enqueue_factor(riga_ctx* c) {
     Symbolic& S = c->S;
+    if (!c->inertia_only) c->fp64_sweeps = 1;  // a new factor: plain FP64 solves until calibrated
     if (S.nb != NB || S.tile != TILE || S.rowblk != RB) return set_error(c, RIGA_EINVAL, "schedule/kernel tile mismatch");
     RIGA_CUDA_TRY(c, c->D.alloc(S.N));
     RIGA_CUDA_TRY(c, c->flag.alloc(1));

@@ -529,6 +529,28 @@ int calibrate_refinement(riga_ctx* c, uint64_t seed) {
     return factor_at(c, c->sigma, RIGA_FP64, nullptr);
 }
 
+// FP64 fronts: one seeded solve's relative residual; at most 1e-13 -> plain
+// solves (fp64_sweeps = 1), else the sweeps refinement needs to reach it (FP64
+// residuals, FP64 corrections), used by every solve until the next factorization
+int calibrate_fp64_solve(riga_ctx* c, uint64_t seed) {
+    const long long N = c->S.N;
+    for (int i = 2; i < 6; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+    std::vector<double> hb(N);
+    uint64_t st = seed ^ 0x2545F4914F6CDD1DULL;
+    for (long long i = 0; i < N; ++i) hb[i] = ((double)(splitmix(st) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+    RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->vwork[4].ptr, hb.data(), N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int sweeps = 0;
+    int rc = solve_refined(c, c->vwork[4].ptr, c->vwork[2].ptr, c->vwork[3].ptr, 1e-13, 10, 1, &sweeps);
+    if (rc == RIGA_EREFINE) {
+        c->last_error.clear();
+        sweeps = 10;
+    } else if (rc) {
+        return rc;
+    }
+    c->fp64_sweeps = std::max(1, std::min(sweeps, 10));
+    return RIGA_OK;
+}
+
 int configure_reorth(riga_ctx* c, int cap) {
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
     const size_t sm_upd = sm_dots + (size_t)cap * sizeof(double);

@@ -37,6 +37,7 @@ int recur_pass(Run& R, int J, int u0, int Ju, double* w);
 void normalize_into(Run& R, double* w, int col, int jslot, int Jc);
 int factor_at(riga_ctx* c, double sigma, int precision, long long* nu, bool inertia_only = false);
 int calibrate_refinement(riga_ctx* c, uint64_t seed);
+int calibrate_fp64_solve(riga_ctx* c, uint64_t seed);  // refinement sweeps FP64 fronts need (1 = none)
 int configure_reorth(riga_ctx* c, int cap);  // shared-memory attributes of the reorthogonalization kernels
 int ritz_vectors_resid(Run& R, int col0, int J, const std::vector<double>& W, int nsel, double* U, double* MU,
                        const std::vector<double>& lam, int nres, std::vector<double>& rho);

@@ -10,17 +10,20 @@
 // Lanczos runs lock eigenpairs with lambda in [a, hi).  Once `slice` of them
 // (plus `extra`) are locked, the slice closes at the midpoint b of the first
 // relative gap > 1e-6 after the slice-th locked value; nu(b) - nu(a) must
-// equal the number locked in [a, b) (fewer locked: the runs continue at the
-// shift b, next to the missing ones).  The pairs below b go to the output;
+// equal the number locked in [a, b).  The pairs below b go to the output;
 // the next slice starts at a = b, whose factorization (FP64 path) already
 // carries the solve operators.  The shifts therefore follow the spectrum's
-// own density: each slice ends where its eigenvalues ran out.
+// own density: each slice ends where its eigenvalues ran out.  Missing
+// eigenvalues (copies of a degenerate eigenvalue that one Krylov sequence
+// cannot see) are searched by fresh runs that lock only eigenvalues in
+// [a, b): first at the slice's shift, then next to the missing ones, which
+// inertia counts at midpoints between the locked values locate (bisection).
 //
 // Bounded memory.  The runs orthogonalize against a window of locked
 // vectors: those of the previous slice (the eigenvalues just below a, the
 // nearest to the shift on that side) and those locked in the current slice.
 // Older slices are not kept; their eigenvalues lie below a and are never
-// locked again.  The basis therefore holds at most 2 (slice + extra) + 16
+// locked again.  The basis therefore holds at most 2 (slice + extra + 8) + 16
 // window vectors plus the m + 1 of a run, whatever the number of pairs.
 //
 // Thick restart (Wu and Simon's form of Eq. LanczosRestart).  A run builds
@@ -35,6 +38,7 @@
 // [a, hi), by decreasing |theta|.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -87,6 +91,7 @@ int put_col(riga_ctx* c, Run& R, const double* u, const double* mu, int dst) {
 // locks (into the window, at most lock_room) converged pairs with lambda in
 // [a, hi) until `want` were locked in this run.  *n_locked: pairs locked.
 int trlan_run(Slicer& L, int want, int lock_room, double sigma, double a, double hi, int max_cycles, int* n_locked) {
+    static const bool dbg = std::getenv("RIGA_DEBUG") != nullptr;
     riga_ctx* c = L.c;
     Run& R = L.R;
     cudaStream_t st = c->stream;
@@ -201,6 +206,16 @@ int trlan_run(Slicer& L, int want, int lock_room, double sigma, double a, double
         // lock the candidates that pass the FP64 residual test; the others
         // stay in the restart basis
         std::vector<int> kept_idx;  // indices into the selection (columns of U)
+        if (dbg && nl > 0) {
+            int failed = 0;
+            double worst = 0.0;
+            for (int q = 0; q < nl; ++q)
+                if (!(rho[q] <= L.lock_tol)) {
+                    ++failed;
+                    worst = std::max(worst, rho[q]);
+                }
+            if (failed) std::fprintf(stderr, "[riga] trlan: %d of %d lock candidates failed the residual test (worst %.3g)\n", failed, nl, worst);
+        }
         for (int q = 0; q < nl; ++q) {
             if (rho[q] <= L.lock_tol) {
                 int rc = put_col(c, R, U + (size_t)q * N, MU + (size_t)q * N, L.nw);
@@ -234,6 +249,60 @@ int trlan_run(Slicer& L, int want, int lock_room, double sigma, double a, double
         }
         j = ck;
     }
+    return RIGA_OK;
+}
+
+// Bisection for missing eigenvalues of [a, b): sl[0..below) are the locked
+// values in [a, b), ascending; nu(a) = nu_a.  Groups of equal locked values
+// (relative 1e-9) are the candidates; an FP64 inertia count at the midpoint
+// between two groups tells which side holds more eigenvalues than are
+// locked.  *shift: inside the narrowest sub-interval found, just above its
+// group (a tenth of the way to the next boundary), so that the missing
+// eigenvalues are the nearest unlocked ones.
+int locate_missing(riga_ctx* c, double a, double b, long long nu_a, const std::vector<double>& sl, int below,
+                   std::map<double, long long>& cache, double* shift) {
+    std::vector<double> gval;   // group values
+    std::vector<int> gend;      // locked count up to and including the group
+    for (int i = 0; i < below; ++i) {
+        if (gval.empty() || sl[i] - gval.back() > 1e-9 * std::fabs(sl[i])) gval.push_back(sl[i]);
+        else gend.pop_back();
+        gend.push_back(i + 1);
+    }
+    const int G = (int)gval.size();
+    if (G == 0) {
+        *shift = 0.5 * (a + b);
+        return RIGA_OK;
+    }
+    // invariant: missing eigenvalues in [left, right) with groups lo..hi-1 inside
+    int lo = 0, hi = G;
+    double left = a, right = b;
+    long long nu_left = nu_a;
+    int locked_left = 0;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        const double t = 0.5 * (gval[mid - 1] + gval[mid]);
+        long long nu_t = 0;
+        auto it = cache.find(t);
+        if (it != cache.end()) {
+            nu_t = it->second;
+        } else {
+            int rc = factor_at(c, t, RIGA_FP64, &nu_t, true);
+            if (rc) return rc;
+            cache[t] = nu_t;
+        }
+        const int locked_t = gend[mid - 1];
+        if (nu_t - nu_left > locked_t - locked_left) {
+            hi = mid;
+            right = t;
+        } else {
+            lo = mid;
+            left = t;
+            nu_left = nu_t;
+            locked_left = locked_t;
+        }
+    }
+    *shift = gval[lo] + 0.1 * (right - gval[lo]);
+    (void)left;
     return RIGA_OK;
 }
 
@@ -272,7 +341,7 @@ int run_eigs_interval(riga_ctx* c, double lo, double hi, int kmax, double tol, i
     Slicer L;
     L.c = c;
     L.m = (int)std::min<long long>(m_basis > 0 ? m_basis : std::max(2 * (slice + extra), slice + extra + 40), N - 2);
-    L.wcap = 2 * (slice + extra) + 16;
+    L.wcap = 2 * (slice + extra + 8) + 16;
     L.tol_est = 1e-2 * tol;
     L.lock_tol = 0.5 * tol;
     L.seed = c->opt_seed ? c->opt_seed : 1;
@@ -312,85 +381,111 @@ int run_eigs_interval(riga_ctx* c, double lo, double hi, int kmax, double tol, i
     long long found = 0;
     int runs = 0, fruitless = 0;
     int target = (int)std::min<long long>(slice, count);
+    // the slice end b once chosen, and its inertia; while it is pending the
+    // runs lock only eigenvalues in [a, b) (the missing ones)
+    bool have_b = false;
+    double b = hi;
+    long long nu_b = nu_hi;
+    std::map<double, long long> inertia_cache;  // FP64 inertia counts of the bisection
     int status = RIGA_OK;
     while (found < count) {
         const long long remaining = count - found;
+        const double ub = have_b ? b : hi;
+        // this slice's locked pairs (all >= a) sorted, and how many lie below ub
         const int this_cnt = L.nw - L.nprev;
-        const int want_slice = (int)std::min<long long>(target, remaining);
-        const int need = (int)std::min<long long>(want_slice + extra, remaining);
-        if (this_cnt >= need) {
-            std::vector<int> ord(this_cnt);
-            std::iota(ord.begin(), ord.end(), 0);
-            std::sort(ord.begin(), ord.end(), [&](int x, int y) { return L.lam_win[L.nprev + x] < L.lam_win[L.nprev + y]; });
-            std::vector<double> sl(this_cnt);
-            for (int i = 0; i < this_cnt; ++i) sl[i] = L.lam_win[L.nprev + ord[i]];
-            double b = hi;
-            long long nu_b = nu_hi;
-            int gi = this_cnt;
-            if (this_cnt < remaining) {
-                gi = -1;
-                for (int i = std::max(want_slice, 1); i < this_cnt; ++i)
-                    if (sl[i] - sl[i - 1] > gap_rel * std::fabs(sl[i])) {
-                        gi = i;
-                        break;
+        std::vector<int> ord(this_cnt);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int x, int y) { return L.lam_win[L.nprev + x] < L.lam_win[L.nprev + y]; });
+        std::vector<double> sl(this_cnt);
+        for (int i = 0; i < this_cnt; ++i) sl[i] = L.lam_win[L.nprev + ord[i]];
+        const int below = (int)(std::lower_bound(sl.begin(), sl.end(), ub) - sl.begin());
+        int want_run = 0;
+        if (!have_b) {
+            const int want_slice = (int)std::min<long long>(target, remaining);
+            const int need = (int)std::min<long long>(want_slice + extra, remaining);
+            if (this_cnt >= need) {
+                if (this_cnt >= remaining) {
+                    b = hi;
+                    nu_b = nu_hi;
+                } else {
+                    int gi = -1;
+                    for (int i = std::max(want_slice, 1); i < this_cnt; ++i)
+                        if (sl[i] - sl[i - 1] > gap_rel * std::fabs(sl[i])) {
+                            gi = i;
+                            break;
+                        }
+                    if (gi < 0) {  // no gap yet after the slice's pairs: lock more
+                        target = this_cnt + 1;
+                        continue;
                     }
-                if (gi < 0) {  // no gap yet after the slice's pairs: lock more
-                    target = this_cnt + 1;
-                    continue;
+                    b = 0.5 * (sl[gi - 1] + sl[gi]);
+                    const bool reuse = prec == RIGA_FP64;
+                    rc = factor_at(c, b, RIGA_FP64, &nu_b, !reuse);
+                    if (rc) { status = rc; break; }
+                    if (reuse) factored = b;
                 }
-                b = 0.5 * (sl[gi - 1] + sl[gi]);
-                const bool reuse = prec == RIGA_FP64;
-                rc = factor_at(c, b, RIGA_FP64, &nu_b, !reuse);
-                if (rc) { status = rc; break; }
-                if (reuse) factored = b;
+                have_b = true;
+                continue;
             }
+            want_run = need - this_cnt;
+        } else {
+            const long long expected = nu_b - nu_a;
             if (dbg)
-                std::fprintf(stderr, "[riga] slice check: a=%.12g b=%.12g locked=%d gap_index=%d inertia=%lld-%lld\n", a, b,
-                             this_cnt, gi, nu_b, nu_a);
-            if (nu_b - nu_a == gi) {
+                std::fprintf(stderr, "[riga] slice check: a=%.12g b=%.12g locked below b=%d expected=%lld\n", a, b, below,
+                             expected);
+            if (below == expected) {
                 // the slice is complete: its pairs below b to the output
-                for (int i = 0; i < gi; ++i) {
+                for (int i = 0; i < below; ++i) {
                     const int colw = L.nprev + ord[i];
                     RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->evec_perm.ptr + (long long)(found + i) * N,
                                                      c->V.ptr + (long long)colw * R.ld, N * sizeof(double),
                                                      cudaMemcpyDeviceToDevice, st));
                     c->evals.push_back(sl[i]);
                 }
-                found += gi;
-                // new window: this slice's pairs below b, then those above b
+                found += below;
+                // new window: this slice's pairs (below b), then those above b
                 const int nkeep = this_cnt;
                 RIGA_CUDA_TRY(c, hold.alloc((size_t)2 * N * std::max(nkeep, 1)));
-                std::vector<double> lw(nkeep);
                 for (int i = 0; i < nkeep; ++i) {
                     const int colw = L.nprev + ord[i];
                     RIGA_CUDA_TRY(c, cudaMemcpyAsync(hold.ptr + (size_t)i * N, c->V.ptr + (long long)colw * R.ld,
                                                      N * sizeof(double), cudaMemcpyDeviceToDevice, st));
                     RIGA_CUDA_TRY(c, cudaMemcpyAsync(hold.ptr + (size_t)(nkeep + i) * N, c->MV.ptr + (long long)colw * R.ld,
                                                      N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-                    lw[i] = sl[i];
                 }
                 for (int i = 0; i < nkeep; ++i) {
                     rc = put_col(c, R, hold.ptr + (size_t)i * N, hold.ptr + (size_t)(nkeep + i) * N, i);
                     if (rc) return rc;
                 }
-                L.nprev = gi;
+                L.nprev = below;
                 L.nw = nkeep;
-                L.lam_win = lw;
+                L.lam_win = sl;
                 a = b;
                 nu_a = nu_b;
                 sigma = b;
+                have_b = false;
+                inertia_cache.clear();
                 target = (int)std::min<long long>(slice, count - found);
                 fruitless = 0;
                 continue;
             }
-            if (nu_b - nu_a > gi) {
-                // eigenvalues missing below b: continue at the shift b
-                target = this_cnt + (int)(nu_b - nu_a - gi);
-                sigma = b;
-                continue;
+            if (below > expected) {
+                status = set_error(c, RIGA_ENOCONV, "more locked pairs than the inertia allows");
+                break;
             }
-            status = set_error(c, RIGA_ENOCONV, "more locked pairs than the inertia allows");
-            break;
+            // eigenvalues missing in [a, b) (copies of degenerate eigenvalues
+            // that a single Krylov sequence cannot see): fresh runs that lock
+            // only in [a, b); the first at the slice's shift, later ones at a
+            // shift next to the missing eigenvalues, located by bisecting
+            // the locked values with inertia counts
+            want_run = (int)(expected - below);
+            if (fruitless > 0) {
+                double sm = sigma;
+                rc = locate_missing(c, a, b, nu_a, sl, below, inertia_cache, &sm);
+                if (rc) { status = rc; break; }
+                if (dbg) std::fprintf(stderr, "[riga] slice missing %d in [%.12g, %.12g): shift %.12g\n", want_run, a, b, sm);
+                sigma = sm;
+            }
         }
         if (++runs > 400 || fruitless > 6) {
             status = set_error(c, RIGA_ENOCONV, "spectrum slicing did not converge");
@@ -401,18 +496,28 @@ int run_eigs_interval(riga_ctx* c, double lo, double hi, int kmax, double tol, i
             if (rc) { status = rc; break; }
             factored = sigma;
         }
-        if (c->precision != RIGA_FP64 && !(calibrated == sigma)) {
-            rc = calibrate_refinement(c, L.seed + (uint64_t)runs);
+        if (!(calibrated == sigma)) {
+            // sweeps per solve: low-precision fronts always refine; FP64
+            // fronts at an interior shift (an indefinite matrix factored
+            // without pivoting can lose accuracy through pivot growth) refine
+            // when one solve does not reach a relative residual of 1e-13
+            if (c->precision != RIGA_FP64) {
+                rc = calibrate_refinement(c, L.seed + (uint64_t)runs);
+            } else {
+                rc = calibrate_fp64_solve(c, L.seed + (uint64_t)runs);
+            }
             if (rc) { status = rc; break; }
             calibrated = sigma;
+            if (dbg) std::fprintf(stderr, "[riga] slice shift %.12g: %d solve sweep(s)\n", sigma,
+                                  c->precision == RIGA_FP64 ? c->fp64_sweeps : c->ir_sweeps);
         }
         int acc = 0;
-        const int want_run = std::max(need - this_cnt, 1);
-        rc = trlan_run(L, want_run, want_run + 8, sigma, a, hi, 8, &acc);
+        want_run = std::max(want_run, 1);
+        rc = trlan_run(L, want_run, want_run + 8, sigma, a, ub, 8, &acc);
         if (rc) { status = rc; break; }
         if (dbg)
-            std::fprintf(stderr, "[riga] slice run %d: shift=%.12g a=%.12g locked=%d window=%d found=%lld/%lld\n", runs,
-                         sigma, a, acc, L.nw, found, count);
+            std::fprintf(stderr, "[riga] slice run %d: shift=%.12g a=%.12g ub=%.12g locked=%d window=%d found=%lld/%lld\n",
+                         runs, sigma, a, ub, acc, L.nw, found, count);
         if (acc == 0) ++fruitless;
         else fruitless = 0;
     }

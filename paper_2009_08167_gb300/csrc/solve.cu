@@ -270,12 +270,104 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
             s_ok = ok;
             if (a.trace) a.trace[4 * claimed + 2] = global_ns();
         }
+        // Static data of the item, loaded by every thread while thread 0
+        // waits for the dependencies (one right-hand side, fronts of at most
+        // PF * NT variables, at most two children): the own right-hand side
+        // and the children's relative indices (forward), the border index
+        // list (backward).  After the wait one round of loads remains: the
+        // children's update vectors, or w1 and the ancestors' solution.
+        constexpr int PF = 4;
+        T pf_y[PF];
+        int pf_ri[2][PF], pf_m[2] = {0, 0}, pf_idx[PF];
+        long long pf_uo[2] = {0, 0};
+        bool fast = false;
+        if (NR == 1) {
+            if (fwd) {
+                const int nch = it.c1 - it.c0;
+                fast = nch <= 2 && n <= PF * NT;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (c < nch && fast) {
+                        const ChildRec cr = a.crec[it.c0 + c];
+                        pf_m[c] = cr.m;
+                        pf_uo[c] = cr.upd_off;
+                        fast = cr.m <= PF * NT;
+                        const int* rl = a.rel + cr.rel_off;
+#pragma unroll
+                        for (int q = 0; q < PF; ++q) {
+                            const int i = tid + q * NT;
+                            pf_ri[c][q] = (fast && i < cr.m) ? __ldg(rl + i) : 0;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PF; ++q) pf_ri[c][q] = 0;
+                    }
+                }
+                if (fast)
+#pragma unroll
+                    for (int q = 0; q < PF; ++q) {
+                        const int i = tid + q * NT;
+                        pf_y[q] = i < k ? (T)__ldcg(&y[b0 + i]) : T(0);
+                    }
+            } else {
+                fast = n <= PF * NT;
+                const int* idx = a.front_pos + it.fpos;
+#pragma unroll
+                for (int q = 0; q < PF; ++q) {
+                    const int i = tid + q * NT;
+                    pf_idx[q] = (fast && i >= k && i < n) ? __ldg(idx + i) : 0;
+                }
+            }
+        }
         __syncthreads();
         if (!s_ok) {
             drain();
             return;
         }
-        if (fwd) {
+        if (fast && fwd) {
+            // w = [b(own); 0], then child 0's and child 1's update vectors
+            // added in that order (as the general path below)
+            const int nch = it.c1 - it.c0;
+            T uv[2][PF];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int q = 0; q < PF; ++q) {
+                    const int i = tid + q * NT;
+                    uv[c][q] = (c < nch && i < pf_m[c]) ? (T)__ldcg(&upd[pf_uo[c] + i]) : T(0);
+                }
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int i = tid + q * NT;
+                if (i < n) w[i] = pf_y[q];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (c < nch) {
+#pragma unroll
+                    for (int q = 0; q < PF; ++q) {
+                        const int i = tid + q * NT;
+                        if (i < pf_m[c]) w[pf_ri[c][q]] += uv[c][q];
+                    }
+                    __syncthreads();
+                }
+            }
+            if (lo == k)  // the first part keeps w1 = w(own) for the backward sweep
+                for (int i = tid; i < k; i += NT) w1[b0 + i] = (double)w[i];
+        } else if (fast) {
+            T v[PF];
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int i = tid + q * NT;
+                v[q] = i < k ? -(T)__ldcg(&w1[b0 + i]) : (i < n ? (T)__ldcg(&y[pf_idx[q]]) : T(0));
+            }
+#pragma unroll
+            for (int q = 0; q < PF; ++q) {
+                const int i = tid + q * NT;
+                if (i < n) w[i] = v[q];
+            }
+        } else if (fwd) {
             // w = [b(own); 0] + children's update vectors
             for (int r = 0; r < NR; ++r)
                 for (int i = tid; i < n; i += NT)
@@ -624,6 +716,23 @@ __global__ void residual_kernel(long long N, const long long* __restrict__ rowpt
     if (row < N && lane == 0) r[row] = b[row] - s;
 }
 
+// the same residual with a shift per position (a batch: each problem of the
+// forest has its own shift; entry (row, col) shares row's problem)
+__global__ void residual_pos_kernel(long long N, const long long* __restrict__ rowptr, const int* __restrict__ col,
+                                    const double* __restrict__ Kv, const double* __restrict__ Mv,
+                                    const double* __restrict__ sig_pos, const double* __restrict__ x,
+                                    const double* __restrict__ b, double* __restrict__ r) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long row = t / SPMV_TPR;
+    const int lane = (int)(t % SPMV_TPR);
+    double s = 0.0;
+    const double shift = row < N ? sig_pos[row] : 0.0;
+    if (row < N)
+        for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += (Kv[e] - shift * Mv[e]) * x[col[e]];
+    s = group_sum(s);  // every lane of the warp takes part
+    if (row < N && lane == 0) r[row] = b[row] - s;
+}
+
 // out[ipos] <-> in[g]: to_perm: out[pos] = in[perm[pos]]; else out[perm[pos]] = in[pos]
 __global__ void permute_kernel(long long N, int ncols, const int* __restrict__ perm, const double* __restrict__ in,
                                double* __restrict__ out, int to_perm) {
@@ -868,8 +977,13 @@ int solve_refined(riga_ctx* c, double* y, double* x, double* r, double tol, int 
     const long long N = S.N;
     const unsigned gb = (unsigned)((N + 255) / 256);
     if (c->precision == RIGA_FP64 && !check) {
-        if (sweeps_out) *sweeps_out = 1;
-        return enqueue_solve(c, y);
+        // FP64 fronts: plain solves, unless a calibration of this
+        // factorization asked for refinement (an interior shift)
+        if (c->fp64_sweeps <= 1) {
+            if (sweeps_out) *sweeps_out = 1;
+            return enqueue_solve(c, y);
+        }
+        max_sweeps = c->fp64_sweeps;
     }
     RIGA_CUDA_TRY(c, c->red.alloc(2 * 304));
     RIGA_CUDA_TRY(c, cudaMemsetAsync(x, 0, N * sizeof(double), st));
@@ -884,8 +998,15 @@ int solve_refined(riga_ctx* c, double* y, double* x, double* r, double tol, int 
         { count_launch(c); axpy_kernel<<<gb, 256, 0, st>>>(N, 1.0, r, x); }
         if (!check && sweeps == max_sweeps) break;  // the last residual is not needed
         long long threads = N * SPMV_TPR;
-        { count_launch(c); residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
-                                                                            c->Mval.ptr, c->sigma, x, y, r); }
+        if (S.dim == 0 && !c->sigma_prob.empty()) {
+            count_launch(c);
+            residual_pos_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
+                                                                                 c->Mval.ptr, c->sig_pos.ptr, x, y, r);
+        } else {
+            count_launch(c);
+            residual_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr,
+                                                                             c->Mval.ptr, c->sigma, x, y, r);
+        }
         if (check) {
             { count_launch(c); norm2_partial_kernel<<<304, 256, 0, st>>>(N, r, y, c->red.ptr); }
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), c->red.ptr, 2 * 304 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -923,7 +1044,10 @@ int solve_refined_multi(riga_ctx* c, double* y, double* x, double* r, int nr, in
     Symbolic& S = c->S;
     cudaStream_t st = c->stream;
     const long long N = S.N, NN = N * nr;
-    if (c->precision == RIGA_FP64) return enqueue_solve(c, y, nr);
+    if (c->precision == RIGA_FP64) {
+        if (c->fp64_sweeps <= 1) return enqueue_solve(c, y, nr);
+        sweeps = c->fp64_sweeps;
+    }
     RIGA_CUDA_TRY(c, cudaMemsetAsync(x, 0, NN * sizeof(double), st));
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(r, y, NN * sizeof(double), cudaMemcpyDeviceToDevice, st));
     for (int s = 1; s <= sweeps; ++s) {

@@ -236,6 +236,59 @@ std::string finish_symbolic(Symbolic& S) {
     return "";
 }
 
+// Host check of every bulk copy the kernels will issue for this schedule
+// (cp.async.bulk wants 16-byte aligned source and destination and a size
+// that is a multiple of 16 bytes, for 4- and 8-byte elements alike):
+//  - tree solve: each work item's panel starts at element it.off of the Q
+//    pool and is copied in chunks of whole ldp-element rows/columns: off and
+//    ldp must be multiples of 4 and the panel (ldp x units) must end inside
+//    the pool (q_size elements);
+//  - tensor-core update: every packed block index of a step lies below the
+//    packing buffer's block count, every tile's blocks belong to its front
+//    and step, and the front rows it covers start inside the front.
+// Returns "" or a description of the first violation; *checked counts the
+// copies (and tile references) verified.
+std::string check_bulk_copies(const Symbolic& S, long long* checked) {
+    long long n = 0;
+    for (size_t i = 0; i < S.sitems.size(); ++i) {
+        const SolveItem& it = S.sitems[i];
+        const bool fwd = (int)i < S.n_fwd_items;
+        const long long units = fwd ? it.k : it.n;
+        if (it.off % 4 != 0 || it.ldp % 4 != 0 || it.ldp < it.hi - it.lo)
+            return "solve item " + std::to_string(i) + ": panel offset or width not a multiple of 4 elements";
+        if (it.off < 0 || it.off + (long long)it.ldp * units > S.q_size)
+            return "solve item " + std::to_string(i) + ": panel outside the operator pool";
+        ++n;
+    }
+    for (const LevelPlan& P : S.levels)
+        for (const StepRange& R : P.steps) {
+            std::vector<int> blk_front;
+            for (int q = R.k_begin; q < R.k_end; ++q) {
+                const TcPack& pk = S.tc_packs[q];
+                const int kw = std::min(TC_KW, S.k[pk.front] - pk.p0);
+                const int nk = (kw + 31) / 32;
+                if (kw <= 0 || pk.blk < 0 || pk.blk + nk > S.tc_pack_blocks || pk.r0 < 0 || pk.r0 >= S.ld[pk.front])
+                    return "tensor-core pack item " + std::to_string(q) + " out of range";
+                if ((int)blk_front.size() < pk.blk + nk) blk_front.resize(pk.blk + nk, -1);
+                for (int cidx = 0; cidx < nk; ++cidx) blk_front[pk.blk + cidx] = pk.front;
+                ++n;
+            }
+            for (int t = R.c_begin; t < R.c_end; ++t) {
+                const TcTile& tl = S.tc_tiles[t];
+                const int nb = (int)blk_front.size();
+                if (tl.nk < 1 || tl.nk > TC_KW / 32 || tl.a_blk < 0 || tl.b_blk < 0 || tl.a_blk + tl.nk > nb ||
+                    tl.b_blk + tl.nk > nb || tl.i0 >= S.ld[tl.front] || tl.j0 >= S.ld[tl.front])
+                    return "tensor-core tile " + std::to_string(t) + " references blocks out of range";
+                for (int cidx = 0; cidx < tl.nk; ++cidx)
+                    if (blk_front[tl.a_blk + cidx] != tl.front || blk_front[tl.b_blk + cidx] != tl.front)
+                        return "tensor-core tile " + std::to_string(t) + " references a block of another front or step";
+                ++n;
+            }
+        }
+    if (checked) *checked = n;
+    return "";
+}
+
 // Level schedule of the blocked partial LDL^T: per tree level the extend-add
 // items, and per panel step the diagonal-block, row-block and trailing-update
 // tile items (the update tiles' shape follows S.small_trail).
@@ -247,6 +300,7 @@ void build_schedule(Symbolic& S) {
     S.titems.clear();
     S.tc_tiles.clear();
     S.tc_packs.clear();
+    S.tc_narrow.clear();
     S.tc_pack_blocks = 0;
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
@@ -310,10 +364,14 @@ void build_schedule(Symbolic& S) {
                 }
             }
             R.t_end = (int)S.titems.size();
-            // the same trailing update in TC_M x TC_N tiles (tensor-core
-            // kernel): the trailing rows c0.. of each front are packed in
-            // TC_BLK-row blocks (numbered from 0 within the step), and every
-            // tile pairs a row block (A) with a column block (B)
+            // the tensor-core schedule of the same step.  Super-panels of
+            // TC_KW columns: a step that does not end its front's current
+            // super-panel updates only the super-panel's remaining columns
+            // (all rows below them), on 32x32 CUDA-core tiles; the step that
+            // ends it updates everything to the right of the super-panel at
+            // once, K = its width, in TC_M x TC_N tensor-core tiles over packed
+            // 128-row blocks (one per 32-column chunk of the super-panel)
+            R.n_begin = (int)S.tc_narrow.size();
             R.k_begin = (int)S.tc_packs.size();
             R.c_begin = (int)S.tc_tiles.size();
             int nblk_step = 0;
@@ -321,16 +379,28 @@ void build_schedule(Symbolic& S) {
                 int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 const int c0 = s * nb + std::min(nb, kf - s * nb);
+                const int S0 = (s * nb) / TC_KW * TC_KW, S1 = std::min(S0 + TC_KW, kf);
+                if (c0 < S1) {
+                    // narrow update: columns [c0, S1), rows j0..lf
+                    for (int j0 = c0; j0 < S1; j0 += nb)
+                        for (int i0 = j0; i0 < lf; i0 += nb) S.tc_narrow.push_back({f, i0, j0, S1});
+                    continue;
+                }
+                const int nk = (S1 - S0 + nb - 1) / nb;
                 const int blk0 = nblk_step;
-                for (int r0 = c0; r0 < lf; r0 += TC_BLK) S.tc_packs.push_back({f, r0, nblk_step++, 0});
-                for (int i0 = c0, bi = blk0; i0 < lf; i0 += TC_M, ++bi)
-                    for (int j0 = c0, bj = blk0; j0 < lf; j0 += TC_N, ++bj) {
+                for (int r0 = c0; r0 < lf; r0 += TC_BLK) {
+                    S.tc_packs.push_back({f, r0, nblk_step, S0});
+                    nblk_step += nk;
+                }
+                for (int i0 = c0, bi = 0; i0 < lf; i0 += TC_M, ++bi)
+                    for (int j0 = c0, bj = 0; j0 < lf; j0 += TC_N, ++bj) {
                         const bool lower = j0 <= i0;
                         const bool extra = (i0 + TC_M > nf) && (j0 + TC_N > nf);
-                        if (lower || extra) S.tc_tiles.push_back({f, i0, j0, bi, bj, 0});
+                        if (lower || extra) S.tc_tiles.push_back({f, i0, j0, blk0 + bi * nk, blk0 + bj * nk, nk});
                     }
             }
             S.tc_pack_blocks = std::max<long long>(S.tc_pack_blocks, nblk_step);
+            R.n_end = (int)S.tc_narrow.size();
             R.k_end = (int)S.tc_packs.size();
             R.c_end = (int)S.tc_tiles.size();
             P.steps.push_back(R);

@@ -24,14 +24,18 @@ struct Dir1D {
 // Factorization work items (precomputed per level and panel step).
 struct PanelItem { int front; int r0; };            // TRSM row block of a front
 struct TileItem { int front; int i0; int j0; };     // trailing-update tile
+struct TileItemL { int front; int i0; int j0; int jend; };  // tile whose columns stop at jend (exclusive)
 constexpr int TC_M = 128, TC_N = 128;               // tensor-core update tile (rows x columns)
 constexpr int TC_BLK = 128;                          // rows of one packed panel block
-// Tensor-core update of one panel step: the panel's rows are packed once per
-// step into 128-row blocks (operands in the MMA's shared-memory layout);
-// a tile reads block a_blk as its A operand (rows i0..) and block b_blk as
-// its B operand (rows j0..).
-struct TcPack { int front; int r0; int blk; int pad; };       // pack rows r0..r0+127 of the panel into block blk
-struct TcTile { int front; int i0; int j0; int a_blk; int b_blk; int pad; };
+constexpr int TC_KW = 128;                           // columns of a super-panel (K of one tensor-core update)
+// Tensor-core update of the trailing matrix once per super-panel (up to
+// TC_KW / 32 panel steps): the super-panel's columns of the trailing rows are
+// packed into 128-row blocks, one packed block per 32-column chunk (operands
+// in the MMA's shared-memory layout; the chunks of a row block are
+// consecutive block numbers).  A tile reads the nk chunk blocks starting at
+// a_blk as its A operand (rows i0..) and at b_blk as its B operand (rows j0..).
+struct TcPack { int front; int r0; int blk; int p0; };  // rows r0..r0+127, super-panel columns from p0, chunks from blk
+struct TcTile { int front; int i0; int j0; int a_blk; int b_blk; int nk; };
 struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
 
 // tree-solve kernel shapes: 256-thread CTAs per item (large fronts),
@@ -66,6 +70,8 @@ struct StepRange {   // one panel step of one level
     int p_begin, p_end;   // PanelItem range: row blocks below the diagonal block
     int c_begin, c_end;   // TcTile range of Symbolic::tc_tiles (tensor-core update tiles)
     int k_begin, k_end;   // TcPack range of Symbolic::tc_packs (blocks packed before the update)
+    int n_begin, n_end;   // TileItem range of Symbolic::tc_narrow: 32x32 tiles of the panel's update
+                          // restricted to the columns of its super-panel (tensor-core schedule)
     int t_begin, t_end;   // TileItem range: [t_begin, t_mid) 32x32 tiles, [t_mid, t_end) 16x16 tiles
     int t_mid;
 };
@@ -125,6 +131,7 @@ struct Symbolic {
     //                 [-A11^{-1} | -A11^{-1} A12] (ldp = hi-lo rounded up to 4).
     std::vector<TcTile> tc_tiles;     // update tiles of TC_M x TC_N for the tensor-core update kernel
     std::vector<TcPack> tc_packs;     // panel blocks packed for it, per step
+    std::vector<TileItemL> tc_narrow; // within-super-panel updates (CUDA cores, columns < the super-panel's end)
     long long tc_pack_blocks = 0;     // packed blocks of the largest step
     std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
     std::vector<ChildRec> crec;       // per child_list entry
@@ -166,6 +173,8 @@ std::string build_symbolic(Symbolic& S, int dim, const int* ne, int p, const int
 // Heights, counts, schedule and solve items from nodes, fronts and maps.
 std::string finish_symbolic(Symbolic& S);
 void build_schedule(Symbolic& S);  // the factorization's level schedule (after finish_symbolic)
+// Host check of the alignment and range of every bulk copy of the schedule.
+std::string check_bulk_copies(const Symbolic& S, long long* checked);
 // Merges independent problems into one forest (dim = 0 marks a batch).
 std::string merge_symbolic(Symbolic& M, const std::vector<Symbolic>& P);
 

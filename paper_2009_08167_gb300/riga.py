@@ -36,7 +36,7 @@ EXPORTED = [
     "riga_eigs_interval", "riga_eig_errors",
     "riga_set_eig_options", "riga_eig_grad", "riga_query", "riga_get_symbolic", "riga_get_matrices",
     "riga_get_factor", "riga_spmv", "riga_stats", "riga_profile", "riga_profile_get", "riga_set_wait_limit",
-    "riga_trace_solve", "riga_spmv_dot_noalloc", "riga_sym_eig", "riga_strerror",
+    "riga_trace_solve", "riga_check_copies", "riga_spmv_dot_noalloc", "riga_sym_eig", "riga_strerror",
     "riga_last_error",
 ]
 PHASES = ["assemble", "factor", "solve", "reorth", "spmv", "ritz", "other"]
@@ -102,6 +102,7 @@ def load_library(path=LIB_PATH):
     lib.riga_trace_solve.argtypes = [P, P, ctypes.POINTER(I), P, P]
     lib.riga_spmv_dot_noalloc.argtypes = [P, P, P, LL, P, P, P, P]
     lib.riga_sym_eig.argtypes = [I, P, P, P]
+    lib.riga_check_copies.argtypes = [P, ctypes.POINTER(LL)]
     lib.riga_eigs_interval.argtypes = [P, D, D, I, D, I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.riga_eig_errors.argtypes = [P, I, P, I, P, P, P]
     lib.riga_profile_get.argtypes = [P, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(LL), ctypes.POINTER(LL),
@@ -358,6 +359,13 @@ class Riga:
         return ga, gb
 
     # ------------------------------------------------------------ inspection
+    def check_copies(self):
+        """Number of bulk copies of the current schedule verified on the host
+        (riga_check_copies); raises RigaError on a violation."""
+        n = ctypes.c_longlong(0)
+        self._check(self.lib.riga_check_copies(self.ctx, ctypes.byref(n)))
+        return n.value
+
     def get_symbolic(self):
         nn = ctypes.c_int()
         tot = ctypes.c_longlong()

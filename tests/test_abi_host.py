@@ -153,3 +153,20 @@ def test_host_context_options_and_autotune():
     with pytest.raises(RigaError) as e:
         r.autotune()
     assert e.value.code == RIGA_ESTATE
+
+
+@pytest.mark.parametrize("mesh", [Mesh(2, 256, 3, 16, 8), Mesh(2, 256, 3, None, 8), Mesh(3, 64, 2, 8, 8),
+                                  Mesh(3, 32, 2, 8, 8), Mesh(1, 33, 4, 8), Mesh(2, [13, 9], 3, 4, 4)],
+                         ids=["c2_riga", "c2_iga", "c3", "3d_32", "1d", "2d_ragged"])
+def test_bulk_copies_aligned_and_in_range(lib, mesh):
+    """Host check of every bulk copy of the schedule (riga_check_copies, also
+    run by riga_assemble): the tree solve's operator panels start on
+    16-byte boundaries with sizes in whole 16-byte units inside the operator
+    pool, and every tensor-core tile's packed blocks exist and belong to its
+    own front and panel step."""
+    from paper_2009_08167_gb300 import riga
+    r = riga.Riga(-1)
+    r.analyze(mesh)
+    n = r.check_copies()
+    assert n > 0
+    r.close()

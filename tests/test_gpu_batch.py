@@ -206,3 +206,36 @@ def test_autotune_tile_shapes_change_no_result(R):
     for b, (K, M) in enumerate(_block_oracle(meshes, cK)):
         lam = eigen.ghep_dense(K.todense(), M.todense())[0][:k]
         assert np.max(np.abs(ev[b] - lam) / lam) <= 1e-10, b
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["fp32", "tf32"])
+def test_batch_c4_full_mixed(R, prec):
+    """The 512-problem batch with low-precision fronts (FP32 FFMA, or TF32
+    tensor-core Schur updates) and FP64 refinement: every pair's FP64
+    residual <= 1e-10, the eigenvalues of the FP64 batch path to 1e-10
+    relative, one forest inertia count, and the three smallest problems
+    against the oracle's shift-and-invert Lanczos."""
+    probs = config_c4()
+    meshes = [p["mesh"] for p in probs]
+    cK = [np.exp(p["a"]) for p in probs]
+    R.assemble_batch(meshes, cK)
+    k = 20
+    R.set_eig_options(slice=0, precision=0, extra=2, seed=1)
+    ev64, _, _ = R.eigs_batch(k, 0.0, 1e-10)
+    R.set_eig_options(slice=0, precision=prec, extra=2, seed=1)
+    try:
+        ev, rs, nc = R.eigs_batch(k, 0.0, 1e-10)
+    finally:
+        R.set_eig_options(slice=0, precision=0, extra=2, seed=1)
+    assert np.all(nc == k)
+    assert np.all(rs <= 1e-10)
+    assert np.max(np.abs(ev - ev64) / ev64) <= 1e-10
+    s = 0.5 * (np.min(ev[:, k - 1]) + np.min(ev[:, k - 2]))
+    cnt = int(np.sum(ev < s))
+    if np.min(np.abs(ev - s)) > 1e-8 * s:
+        assert R.factor(s) == cnt
+    order = np.argsort([m.ne[0] for m in meshes])[:3]
+    for b in order:
+        K, M = oracle_matrices(meshes[b], cK[b], None)
+        lam, _, _ = eigen.lanczos_shift_invert(K, M, k, 0.0, tol=1e-12, seed=3)
+        assert np.max(np.abs(ev[b] - lam) / lam) <= 1e-10, b

@@ -61,7 +61,7 @@ def test_interval_over_500_pairs_bounded_basis(R, oracle):
     ev, U, rs, basis = R.eigs_interval(0.0, hi, kmax=700, tol=1e-10)
     _check(MESH, lam_r, V_r, ev, U, rs, 0, count)
     m = max(2 * (50 + 2), 50 + 2 + 40)
-    assert basis == 2 * (50 + 2) + 16 + m + 2
+    assert basis == 2 * (50 + 2 + 8) + 16 + m + 2
     assert basis < count / 2  # memory bounded by the slices and m, not by the pairs
 
 
@@ -73,7 +73,7 @@ def test_interior_interval_and_explicit_basis(R, oracle):
     R.assemble(MESH)
     ev, U, rs, basis = R.eigs_interval(lo, hi, kmax=400, tol=1e-10, m_basis=48)
     _check(MESH, lam_r, V_r, ev, U, rs, i0, i1 - i0)
-    assert basis == 2 * (30 + 2) + 16 + 48 + 2
+    assert basis == 2 * (30 + 2 + 8) + 16 + 48 + 2
 
 
 def test_interval_count_above_kmax(R, oracle):
