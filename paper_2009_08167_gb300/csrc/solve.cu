@@ -73,6 +73,18 @@ __device__ __forceinline__ int sm_id() {
     return id;
 }
 
+// Publication of a completed part: the CTA's writes (ordered before by
+// __syncthreads) are released at GPU scope by an acquire-release fence, then
+// the counter is bumped by a relaxed reduction (no return value); the waiter
+// reads the counter and issues the same fence before it reads the data.
+__device__ __forceinline__ void release_add(int* p) {
+    asm volatile(
+        "fence.acq_rel.gpu;\n"
+        "red.relaxed.gpu.global.add.s32 [%0], 1;" ::"l"(p)
+        : "memory");
+}
+__device__ __forceinline__ void acquire_fence() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ bool wait_count(const int* f, int target, int* err, long long limit) {
     long long it = 0;
     while (*(volatile const int*)f < target) {
@@ -266,7 +278,7 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
                 ok = wait_count(&done_f[F], it.wait_parts, a.err, a.spin_limit);
                 if (ok && it.parent >= 0) ok = wait_count(&done_b[it.parent], it.parent_parts, a.err, a.spin_limit);
             }
-            __threadfence();
+            acquire_fence();
             s_ok = ok;
             if (a.trace) a.trace[4 * claimed + 2] = global_ns();
         }
@@ -486,8 +498,7 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
             __syncthreads();
         }
         if (tid == 0) {
-            __threadfence();
-            atomicAdd(fwd ? &done_f[F] : &done_b[F], 1);
+            release_add(fwd ? &done_f[F] : &done_b[F]);
             if (a.trace) a.trace[4 * claimed + 3] = global_ns();
             if (a.nslot == 2) {
                 s_item = s_next;

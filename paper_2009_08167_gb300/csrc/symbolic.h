@@ -27,7 +27,13 @@ struct TileItem { int front; int i0; int j0; };     // trailing-update tile
 struct TileItemL { int front; int i0; int j0; int jend; };  // tile whose columns stop at jend (exclusive)
 constexpr int TC_M = 128, TC_N = 128;               // tensor-core update tile (rows x columns)
 constexpr int TC_BLK = 128;                          // rows of one packed panel block
-constexpr int TC_KW = 128;                           // columns of a super-panel (K of one tensor-core update)
+// Columns of a super-panel (K of one tensor-core update): 64.  The TF32
+// head/tail products accumulate in the FP32 tensor-memory accumulator; at
+// K = 128 (48 MMAs per tile) the factor's error let the three calibrated
+// refinement sweeps fall short on the Lanczos vectors of the 3D mesh (800
+// Lanczos steps instead of 324), at K = 64 (24 MMAs) it does not, and the
+// tile traffic is half that of K = 32.
+constexpr int TC_KW = 64;
 // Tensor-core update of the trailing matrix once per super-panel (up to
 // TC_KW / 32 panel steps): the super-panel's columns of the trailing rows are
 // packed into 128-row blocks, one packed block per 32-column chunk (operands

@@ -1,7 +1,7 @@
 // Schur-complement update of FP32 fronts on the tensor cores (tcgen05 with
 // FP32 accumulation in tensor memory): the dense contraction of the
 // multifrontal LDL^T (Sec. 4.2), A22 -= L21 D L21^T, once per super-panel of
-// up to TC_KW = 128 columns (four panel steps accumulated in TMEM before the
+// up to TC_KW = 64 columns (two panel steps accumulated in TMEM before the
 // trailing tile is reduced once), for every front of a tree level.
 //
 // Precision.  Each FP32 operand x is split into a head h and a tail
