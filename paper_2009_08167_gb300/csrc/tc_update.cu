@@ -43,6 +43,7 @@
 #include <cuda_bf16.h>
 
 #include "ctx.h"
+#include "tc_common.cuh"
 
 namespace riga {
 
@@ -56,96 +57,17 @@ constexpr int NSTAGE = 2;
 constexpr int UPD_THREADS = 192;
 constexpr int TMEM_COLS = 2 * TC_N;            // two accumulators
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+using namespace tcx;
 
-// shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1, no swizzle
-__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
-    return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
-           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-// instruction descriptors: D F32, A and B K-major, N = TC_N, M = TC_M;
-// kind::tf32 (A, B TF32) and kind::f16 (A, B BF16)
-constexpr unsigned IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_N >> 3) << 17) |
-                                ((unsigned)(TC_M >> 4) << 24);
-constexpr unsigned IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_N >> 3) << 17) |
-                                ((unsigned)(TC_M >> 4) << 24);
+constexpr unsigned IDESC_TF32 = make_idesc(2, TC_M, TC_N);
+constexpr unsigned IDESC_BF16 = make_idesc(1, TC_M, TC_N);
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 template <int MODE>
 __device__ __forceinline__ void mma(unsigned d_tmem, unsigned long long a, unsigned long long b, int acc) {
-    if (MODE == 0)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
-            : "memory");
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(IDESC_BF16), "r"(acc)
-            : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait for the phase of the given parity; gives up when another role
-// has given up (abort flag) or after `limit` polls (then raises it)
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort_flag,
-                                          int* err, long long limit) {
-    long long it = 0;
-    while (!mbar_test(bar, parity)) {
-        if (*abort_flag) return false;
-        if (++it > limit) {
-            atomicOr(err, 4);
-            *abort_flag = 1;
-            return false;
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-                 : "memory");
-}
-
-// 32 consecutive accumulator columns of this warp's 32 lanes
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
-    unsigned* r = reinterpret_cast<unsigned*>(v);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
+    if (MODE == 0) mma_tf32(d_tmem, a, b, IDESC_TF32, acc);
+    else mma_f16(d_tmem, a, b, IDESC_BF16, acc);
 }
 
 // power of two s with s * amax in [0.5, 1) (1 for a zero block)
