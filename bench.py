@@ -53,6 +53,8 @@ def parse():
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
     ap.add_argument("--block", type=int, default=2, choices=[0, 1, 2, 4],
                     help="Lanczos block size (riga_set_eig_block; 0 = automatic)")
+    ap.add_argument("--fp64-update", default="fma", choices=["fma", "tc"],
+                    help="Schur updates of FP64 fronts: FP64 FMA on the CUDA cores, or digit slices on the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the low-precision-front (mixed) leg")
@@ -106,7 +108,7 @@ def config_dict(args, cfg, extra=None):
     d = {
         "workload": f"laplace{m.dim}d_p{m.p}_{'x'.join(str(v) for v in m.ne)}_{'riga_bs%d' % m.bs if m.bs else 'iga'}_k{cfg['k']}_slices{cfg['k'] // cfg['slice']}",
         "dim": m.dim, "elements_per_side": m.ne[0], "degree": m.p, "block_size": m.bs, "leaf_extent": m.leaf_extent,
-        "pairs": cfg["k"], "slice": cfg["slice"], "factor_precision": args.precision, "lanczos_block": args.block,
+        "pairs": cfg["k"], "slice": cfg["slice"], "factor_precision": args.precision, "fp64_update": args.fp64_update, "lanczos_block": args.block,
         "l2": "flushed between timed steps (512 MiB write)",
         "parallelism": f"replicas{args.gpus}",
     }
@@ -357,6 +359,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
     stream = torch.cuda.current_stream()
     meshes, cK, k = cfg["meshes"], cfg["coefK"], cfg["k"]
     R = riga.Riga(local_rank, stream)
+    R.set_fp64_update(1 if args.fp64_update == "tc" else 0)
     R.set_eig_options(extra=2, seed=11)
     R.assemble_batch(meshes, cK)  # symbolic analysis of every pattern: once, untimed
     tuned_trail, tuned_ms = R.autotune()  # front tile shapes for this batch: once, untimed
@@ -497,6 +500,7 @@ def run_riga(args, rank, world, local_rank):
         return run_riga_batch(args, rank, world, local_rank, cfg)
     mesh, k = cfg["mesh"], cfg["k"]
     R = riga.Riga(local_rank, stream)
+    R.set_fp64_update(1 if args.fp64_update == "tc" else 0)
     R.set_eig_options(slice=cfg["slice"], precision=prec, extra=2, seed=11)
     R.set_eig_block(args.block)
     R.assemble(mesh)  # symbolic analysis: once per pattern, untimed
@@ -675,6 +679,7 @@ def run_c3_leg(args, local_rank, flush):
     cfg = config_c3()
     stream = torch.cuda.current_stream()
     R = riga.Riga(local_rank, stream)
+    R.set_fp64_update(1 if args.fp64_update == "tc" else 0)
     R.set_eig_block(2)
     t0 = time.perf_counter()
     R.assemble(cfg["mesh"])
@@ -803,6 +808,7 @@ def run_interval(args, local_rank):
     target = 1.05 * args.interval_pairs
     hi = 4.0 * math.pi * target * 1.0137 if mesh.dim == 2 else (6.0 * math.pi ** 2 * target) ** (2.0 / 3.0) * 1.0137
     R = riga.Riga(local_rank, stream)
+    R.set_fp64_update(1 if args.fp64_update == "tc" else 0)
     R.set_eig_options(slice=50, precision=prec, extra=2, seed=11)
     R.assemble(mesh)
     kmax = int(2 * args.interval_pairs + 64)
@@ -843,6 +849,7 @@ def run_kernel_mode(args, local_rank):
     prec = {"fp64": riga.RIGA_FP64, "fp32": riga.RIGA_FP32, "tf32": riga.RIGA_TF32, "bf16": riga.RIGA_BF16}[args.precision]
     cfg = workload(args.mesh)
     R = riga.Riga(local_rank, stream)
+    R.set_fp64_update(1 if args.fp64_update == "tc" else 0)
     if cfg.get("batch"):
         R.assemble_batch(cfg["meshes"], cfg["coefK"])
     else:

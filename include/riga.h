@@ -352,6 +352,26 @@ int riga_set_eig_block(riga_ctx* ctx, int block);
 int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
 
 /*
+ * riga_set_fp64_update: where the Schur-complement updates of FP64 fronts
+ * (A22 -= L21 D L21^T of each panel step, Sec. 4.2) run, for every later
+ * FP64 factorization on ctx (riga_factor with RIGA_FP64, the factorizations
+ * and inertia checks inside riga_eigs, riga_eigs_interval and
+ * riga_eigs_batch):
+ *  mode = 0 (the default): CUDA cores, FP64 fused multiply-adds;
+ *  mode = 1: tensor cores.  Each panel's rows are scaled by a power of two
+ *    per row, rounded to 55-bit integers and split into seven balanced 8-bit
+ *    digits (BF16); the 28 digit products with weight above FP64 rounding
+ *    are accumulated exactly in FP32 tensor memory and recombined in 64-bit
+ *    integers (splitting of Ozaki, Ogita, Oishi and Rump).  The error of an
+ *    updated entry is about 2^-51 * 32 * 2^(e_i + f_j), where 2^e_i and
+ *    2^f_j bound the panel rows of L21 and L21 D: the rounding level of FP64
+ *    arithmetic, normwise per row pair instead of per product.
+ * FP32, TF32 and BF16 fronts are unaffected.
+ * Errors: RIGA_EINVAL (ctx NULL, mode not 0 or 1).
+ */
+int riga_set_fp64_update(riga_ctx* ctx, int mode);
+
+/*
  * riga_set_reorth: how riga_eigs and riga_eigs_batch orthogonalise each new
  * Lanczos vector (block) against all stored ones, in the M-inner product
  * (Sec. 4.2: orthogonalisation against all previously stored vectors).

@@ -87,6 +87,8 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.tc_tiles, st));
     RIGA_CUDA_TRY(c, c->tcpacks.upload(S.tc_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.tc_packs, st));
     RIGA_CUDA_TRY(c, c->tcnarrow.upload(S.tc_narrow.empty() ? std::vector<TileItemL>{TileItemL{0, 0, 0, 0}} : S.tc_narrow, st));
+    RIGA_CUDA_TRY(c, c->ozpacks.upload(S.oz_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.oz_packs, st));
+    RIGA_CUDA_TRY(c, c->oztiles.upload(S.oz_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.oz_tiles, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -353,6 +355,8 @@ static int upload_schedule(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->tcitems.upload(S.tc_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.tc_tiles, st));
     RIGA_CUDA_TRY(c, c->tcpacks.upload(S.tc_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.tc_packs, st));
     RIGA_CUDA_TRY(c, c->tcnarrow.upload(S.tc_narrow.empty() ? std::vector<TileItemL>{TileItemL{0, 0, 0, 0}} : S.tc_narrow, st));
+    RIGA_CUDA_TRY(c, c->ozpacks.upload(S.oz_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.oz_packs, st));
+    RIGA_CUDA_TRY(c, c->oztiles.upload(S.oz_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.oz_tiles, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     ++c->sched_gen;
@@ -468,6 +472,13 @@ int riga_set_eig_block(riga_ctx* c, int block) {
     if (!c) return RIGA_EINVAL;
     if (block != 0 && block != 1 && block != 2 && block != 4) return set_error(c, RIGA_EINVAL, "block size must be 0, 1, 2 or 4");
     c->opt_block = block;
+    return RIGA_OK;
+}
+
+int riga_set_fp64_update(riga_ctx* c, int mode) {
+    if (!c) return RIGA_EINVAL;
+    if (mode != 0 && mode != 1) return set_error(c, RIGA_EINVAL, "mode must be 0 (CUDA cores) or 1 (tensor cores)");
+    c->fp64_tc = mode;
     return RIGA_OK;
 }
 

@@ -130,6 +130,11 @@ struct riga_ctx {
     riga::DevBuf<riga::TileItemL> tcnarrow; // within-super-panel update tiles of the tensor-core schedule
     riga::DevBuf<float> tcpack;            // packed panel blocks of one step (operands of the update)
     riga::DevBuf<float> tcscale;           // per packed block: power-of-two operand scale (BF16)
+    riga::DevBuf<riga::TcPack> ozpacks;    // FP64 tensor-core schedule: blocks to pack per step
+    riga::DevBuf<riga::TcTile> oztiles;    //   its tiles
+    riga::DevBuf<unsigned char> ozpack;    //   digit-slice blocks of one step
+    riga::DevBuf<int> ozexp;               //   per block: the rows' power-of-two exponents (A, then B)
+    int fp64_tc = 0;                       // FP64 fronts: 0 CUDA-core updates, 1 tensor-core digit slices
     riga::DevBuf<riga::ExtItem> eitems;
     // per-direction 1D data
     riga::DevBuf<int> kv[3], elem_first[3];
@@ -166,7 +171,7 @@ struct riga_ctx {
     struct FactorGraph {
         cudaGraphExec_t exec = nullptr;
         long long gen = -1;
-        const void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        const void* ptrs[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         int launches = 0;
     } fgraph[2];
     long long sched_gen = 0;            // bumped whenever the factorization schedule is uploaded
@@ -279,6 +284,9 @@ int prepare_batch_assembly(riga_ctx* c);  // once per batch pattern
 // tc_update.cu: tensor-core Schur updates of FP32 fronts (TF32 or BF16 operands)
 int prepare_tc(riga_ctx* c);  // kernel attributes and packing buffers for the current schedule
 int enqueue_tc_step(riga_ctx* c, const StepRange& R, int p0, float* pool, int plain, cudaStream_t st);
+// oz_update.cu: FP64-accurate Schur updates of FP64 fronts on the tensor cores
+int prepare_oz(riga_ctx* c);
+int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, int plain, cudaStream_t st);
 // factor.cu
 int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
 int finish_factor(riga_ctx* c);   // sync, read flag and inertia

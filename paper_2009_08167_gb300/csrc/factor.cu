@@ -312,11 +312,18 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
             for (long long i = S.prob_pos[b]; i < S.prob_pos[b + 1]; ++i) sp[i] = c->sigma_prob[b];
         RIGA_CUDA_TRY(c, c->sig_pos.upload(sp, st));
     }
+    // FP64 fronts with tensor-core updates: buffers and attributes before any capture
+    const bool oz = sizeof(T) == sizeof(double) && c->fp64_tc;
+    if (oz) {
+        int rc = prepare_oz(c);
+        if (rc) return rc;
+    }
     if (!per_problem || sizeof(T) != sizeof(double)) return enqueue_factor_body<T>(c, pool, Q, st);
     riga_ctx::FactorGraph& g = c->fgraph[c->inertia_only ? 1 : 0];
-    const void* ptrs[6] = {pool, Q, c->D.ptr, c->flag.ptr, c->neg.ptr, c->sig_pos.ptr};
+    const void* ptrs[8] = {pool, Q, c->D.ptr, c->flag.ptr, c->neg.ptr, c->sig_pos.ptr,
+                           oz ? (const void*)c->ozpack.ptr : nullptr, oz ? (const void*)c->ozexp.ptr : nullptr};
     bool valid = g.exec && g.gen == c->sched_gen;
-    for (int i = 0; i < 6 && valid; ++i) valid = g.ptrs[i] == ptrs[i];
+    for (int i = 0; i < 8 && valid; ++i) valid = g.ptrs[i] == ptrs[i];
     if (!valid) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -337,7 +344,7 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
         c->prof.ph[PH_FACTOR].launches -= launches;
         if (rc) return rc;
         g.gen = c->sched_gen;
-        for (int i = 0; i < 6; ++i) g.ptrs[i] = ptrs[i];
+        for (int i = 0; i < 8; ++i) g.ptrs[i] = ptrs[i];
         g.launches = launches;
     }
     RIGA_CUDA_TRY(c, cudaGraphLaunch(g.exec, st));
@@ -359,6 +366,9 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
         int rc = prepare_tc(c);
         if (rc) return rc;
     }
+    // FP64 fronts: the trailing updates on the tensor cores from digit slices
+    // (oz_update.cu; prepared in enqueue_factor_t)
+    const bool oz = sizeof(T) == sizeof(double) && c->fp64_tc;
     if (!plain) { count_launch(c); identity_kernel<T><<<S.n_nodes, 128, 0, st>>>(S.n_nodes, c->kk.ptr, c->nn.ptr, c->front_off.ptr, pool); }
     const bool per_problem = (S.dim == 0) && !c->sigma_prob.empty();
     if (per_problem) {
@@ -395,6 +405,9 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
                                                                        c->kk.ptr, c->nn.ptr, c->front_off.ptr,
                                                                        c->node_ptr.ptr, c->D.ptr, pool, plain); }
                 int rc = enqueue_tc_step(c, R, j0, reinterpret_cast<float*>(pool), plain, st);
+                if (rc) return rc;
+            } else if (oz) {
+                int rc = enqueue_oz_step(c, R, reinterpret_cast<double*>(pool), plain, st);
                 if (rc) return rc;
             } else {
                 if (R.t_mid > R.t_begin)

@@ -1,0 +1,388 @@
+// FP64-accurate Schur-complement update of FP64 fronts on the tensor cores:
+// A22 -= L21 D L21^T of the multifrontal LDL^T (Sec. 4.2), one panel step
+// (K = 32) at a time, from exact integer products of 8-bit digit slices (the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump, here with BF16
+// operands and FP32 accumulation in tensor memory).
+//
+// Splitting.  Row i of the panel L21 (32 entries), with e_i the smallest
+// integer such that every |x_ik| < 2^e_i, becomes the integer row
+// X_ik = round(x_ik 2^(55 - e_i)), |X_ik| < 2^55, written in balanced base
+// 256: X_ik = sum_{p=0..6} a_p,ik 256^(6-p), a_0 in [-128, 128], the other
+// digits in [-128, 127].  Row j of L21 D likewise (exponent f_j, digits
+// b_q,jk).  Then
+//   (L21 D L21^T)_ij ~ 2^(e_i + f_j - 110) sum_{p,q} 256^(12-p-q) sum_k a_p,ik b_q,jk.
+// Every inner sum is an integer of magnitude at most 32 * 2^14: the BF16
+// digits are exact, so are their products, and so is their FP32
+// accumulation.  The pairs of one level l = p + q share one accumulator (at
+// most 7 pairs: |V_l| <= 7 * 2^19 < 2^22, still exact).  Levels l <= 6 (28
+// pairs) are kept.  The dropped levels (2^-53.4), the rounding of X (2^-55)
+// and the truncation of S below (2^-59) weigh together about 2^-53 of
+// 32 * 2^(e_i + f_j), the bound of the entry; an FP64 dot product of length
+// 32 carries up to 32 * 2^-53 of it.
+//
+// Recombination without FP64 arithmetic (GB300 issues FP64 at about 1/60 of
+// its FP32 rate): each level sum is read as an integer through one float add
+// (V + 1.5 * 2^23 holds V in its low mantissa bits), the seven combine in
+// 64-bit integers to S = floor(sum_l V_l 256^(6-l) / 2^8) (|S| < 2^60), and
+// the double -S 2^(e_i + f_j - 54), rounded to nearest (ties away from
+// zero), is assembled from S's leading-bit position and the two exponents
+// with integer operations, then added to the front by red.global.add.f64.
+//
+// Data path of one panel step:
+//   oz_pack_kernel    the trailing rows of each front in 128-row blocks: the
+//                     panel's 32 columns read once, the row exponents, the
+//                     7 digit slices of L21 and of L21 D written as BF16 in
+//                     the MMA's shared-memory layout (K-major 8-row core
+//                     matrices, no swizzle; 8 KiB per slice);
+//   oz_update_kernel  persistent, one CTA per SM, 192 threads:
+//     warp 4   producer: per 128 x 64 tile the A block's 7 slices and the 7
+//              slices of the B block's 64-row half (14 bulk copies, 84 KiB)
+//              into one of two shared-memory stages;
+//     warp 5   MMA issuer: 56 tcgen05.mma (28 digit pairs x K = 32 in two
+//              K = 16 instructions) into 7 level accumulators of 128 x 64
+//              FP32 (448 tensor-memory columns);
+//     warps 0-3 epilogue: tcgen05.ld of the 7 levels, 16 columns at a time,
+//              the integer recombination and the FP64 reductions (lower
+//              triangle, and the whole extra x extra block of the augmented
+//              front).
+//   Every wait is bounded: on expiry the kernel sets bit 2 of the error word,
+//   every role stops, in-flight copies and MMAs are waited for (bounded) and
+//   the tensor memory is freed.
+#include "ctx.h"
+#include "tc_common.cuh"
+
+namespace riga {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int KP = 32;                                  // panel width
+constexpr int NDIG = 7;                                 // digit slices per operand
+constexpr unsigned SLICE_BYTES = TC_BLK * KP * 2;       // one slice of a 128-row block (8 KiB of BF16)
+constexpr unsigned BLK_BYTES = 2 * NDIG * SLICE_BYTES;  // A slices, then B slices (112 KiB)
+constexpr unsigned B_BYTES = OZ_N * KP * 2;             // B slice of a tile: 64 rows (4 KiB)
+constexpr unsigned STAGE_BYTES = NDIG * (SLICE_BYTES + B_BYTES);  // 84 KiB
+constexpr int NSTAGE = 2;
+constexpr int UPD_THREADS = 192;
+constexpr int NLEV = 7;                                 // levels l = p + q = 0..6
+constexpr int TMEM_COLS = 512;                          // NLEV * OZ_N = 448, allocated as a power of two
+constexpr unsigned IDESC = make_idesc(1, OZ_M, OZ_N);   // BF16 x BF16 -> FP32, 128 x 64
+
+static_assert(NLEV * OZ_N <= TMEM_COLS, "level accumulators exceed the tensor memory");
+
+// Integer X = round(x 2^(55 - e)) for |x| < 2^e, from the bits of x (no FP64
+// arithmetic): x = m 2^(E - 1075), m = 2^52 + mantissa.  Zero and subnormal
+// x give 0 (an error below 2^-1022); *bad is set for a non-finite x.
+__device__ __forceinline__ long long to_fixed(double x, int e, bool* bad) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((u >> 52) & 0x7FF);
+    if (E == 0) return 0;
+    if (E == 0x7FF) {
+        *bad = true;
+        return 0;
+    }
+    const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = E - 1075 + 55 - e;  // X = m 2^sh, sh <= 2
+    long long X;
+    if (sh >= 0) X = (long long)(m << sh);
+    else if (sh < -54) X = 0;
+    else X = (long long)((m + (1ull << (-sh - 1))) >> (-sh));  // round half away from zero
+    return (u >> 63) ? -X : X;
+}
+
+// BF16 bits of a small integer d (|d| <= 128): the float d is exact after
+// one add (magic number 1.5 * 2^23), and its top 16 bits are its BF16 value
+__device__ __forceinline__ unsigned bf16_of_int(int d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
+}
+
+// An inertia-only factorization (plain) has no extra rows to update: its
+// tiles that start in them are skipped by all three roles alike
+__device__ __forceinline__ bool skip_tile(const TcTile& tl, const int* nn, int plain) {
+    if (!plain) return false;
+    const int n = nn[tl.front];
+    return tl.i0 >= n || tl.j0 >= n;
+}
+
+// exponent field of a double, from its bits
+__device__ __forceinline__ int exp_field(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+}  // namespace
+
+// One 512-thread block per packed row block: rows r0..r0+127 of the front,
+// panel columns p0..p0+kb (kb = min(32, k - p0)).  Thread (r, g) holds the 8
+// panel entries 8g..8g+7 of row r (one 16-byte BF16 unit per slice).
+// Slice s (0..6 for L21, 7..13 for L21 D) of block blk starts at byte
+// (blk * 14 + s) * 8192; BF16 entry (r, k) of a slice at element
+//   ((r >> 3) * 4 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7).
+// expo[256 blk + r] = e_r (L21), expo[256 blk + 128 + r] = f_r (L21 D).
+// Rows beyond the front and columns beyond kb are zero.
+__global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__ items, const int* __restrict__ kk,
+                                                      const int* __restrict__ nn,
+                                                      const long long* __restrict__ front_off,
+                                                      const int* __restrict__ node_ptr, const double* __restrict__ D,
+                                                      const double* __restrict__ pool, unsigned char* __restrict__ pack,
+                                                      int* __restrict__ expo, int* __restrict__ err) {
+    __shared__ int sexp[2][4][TC_BLK];
+    const TcPack it = items[blockIdx.x];
+    const int F = it.front, k = kk[F], ld = nn[F] + k;
+    const int kb = min(KP, k - it.p0);
+    const int r = threadIdx.x & (TC_BLK - 1), g = threadIdx.x >> 7, gi = it.r0 + r;
+    const double* A = pool + front_off[F] + gi;
+    const double* d = D + node_ptr[F] + it.p0;
+    double x[8], y[8];
+    int ea = 0, eb = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int kc = 8 * g + t;
+        const bool in = kc < kb && gi < ld;
+        x[t] = in ? A[(long long)(it.p0 + kc) * ld] : 0.0;
+        y[t] = in ? x[t] * d[kc] : 0.0;
+        ea = max(ea, exp_field(x[t]));
+        eb = max(eb, exp_field(y[t]));
+    }
+    sexp[0][g][r] = ea;
+    sexp[1][g][r] = eb;
+    __syncthreads();
+    ea = max(max(sexp[0][0][r], sexp[0][1][r]), max(sexp[0][2][r], sexp[0][3][r]));
+    eb = max(max(sexp[1][0][r], sexp[1][1][r]), max(sexp[1][2][r], sexp[1][3][r]));
+    // every |x| < 2^(E - 1022) for the largest exponent field E
+    const int e = ea - 1022, f = eb - 1022;
+    if (g == 0) {
+        expo[256 * it.blk + r] = e;
+        expo[256 * it.blk + TC_BLK + r] = f;
+    }
+    bool bad = false;
+    unsigned char* out = pack + (size_t)it.blk * BLK_BYTES + (size_t)((((r >> 3) * 4 + g) * 64 + (r & 7) * 8) * 2);
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        unsigned w[NDIG][4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            long long X = to_fixed(side == 0 ? x[t] : y[t], side == 0 ? e : f, &bad);
+            // balanced base-256 digits, least significant first
+#pragma unroll
+            for (int p = NDIG - 1; p >= 1; --p) {
+                const int dg = (int)((X + 128) & 255) - 128;
+                X = (X - dg) >> 8;
+                const unsigned b = bf16_of_int(dg);
+                if (t & 1) w[p][t >> 1] |= b << 16;
+                else w[p][t >> 1] = b;
+            }
+            const unsigned b = bf16_of_int((int)X);  // top digit, |X| <= 128
+            if (t & 1) w[0][t >> 1] |= b << 16;
+            else w[0][t >> 1] = b;
+        }
+#pragma unroll
+        for (int p = 0; p < NDIG; ++p)
+            *reinterpret_cast<uint4*>(out + (size_t)(side * NDIG + p) * SLICE_BYTES) =
+                make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
+    if (bad) atomicOr(err, 1);
+}
+
+__global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
+    const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
+    const long long* __restrict__ front_off, const unsigned char* __restrict__ pack, const int* __restrict__ expo,
+    double* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], tfull, tempty, drain;
+    __shared__ unsigned s_tmem;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* stage0 = sm + ((1024u - (smem_addr(sm) & 1023u)) & 1023u);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&tfull, 1);
+        mbar_init(&tempty, 4 * 32);
+        mbar_init(&drain, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                const TcTile tl = tiles[t];
+                if (skip_tile(tl, nn, plain)) continue;
+                const int s = it % NSTAGE;
+                if (!mbar_wait(&empty[s], ((unsigned)(it / NSTAGE) & 1u) ^ 1u, &s_abort, err, spin_limit)) break;
+                const unsigned char* pa = pack + (size_t)tl.a_blk * BLK_BYTES;
+                const unsigned char* pb = pack + (size_t)tl.b_blk * BLK_BYTES + NDIG * SLICE_BYTES + tl.nk * B_BYTES;
+                unsigned char* st = stage0 + (size_t)s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+#pragma unroll 1
+                for (int p = 0; p < NDIG; ++p) {
+                    bulk_copy(st + p * SLICE_BYTES, pa + p * SLICE_BYTES, SLICE_BYTES, &full[s]);
+                    bulk_copy(st + NDIG * SLICE_BYTES + p * B_BYTES, pb + p * SLICE_BYTES, B_BYTES, &full[s]);
+                }
+                ++it;
+            }
+            // every copy issued has landed before the CTA may exit (bounded)
+            for (int q = 0; q < NSTAGE && q < it; ++q) {
+                const int last = it - 1 - q;
+                long long n = 0;
+                while (!mbar_test(&full[last % NSTAGE], (unsigned)(last / NSTAGE) & 1u) && ++n <= spin_limit) {
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                if (skip_tile(tiles[t], nn, plain)) continue;
+                if (!mbar_wait(&tempty, ((unsigned)it & 1u) ^ 1u, &s_abort, err, spin_limit)) break;
+                const int s = it % NSTAGE;
+                if (!mbar_wait(&full[s], (unsigned)(it / NSTAGE) & 1u, &s_abort, err, spin_limit)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned a0 = smem_addr(stage0 + (size_t)s * STAGE_BYTES);
+                const unsigned b0 = a0 + NDIG * SLICE_BYTES;
+                // K-major core matrices: LBO = 128 B (next 8 columns), SBO = 512 B (next 8 rows)
+#pragma unroll 1
+                for (int p = 0; p < NDIG; ++p)
+#pragma unroll 1
+                    for (int q = 0; p + q < NLEV; ++q) {
+                        const unsigned d = tmem + (unsigned)((p + q) * OZ_N);
+#pragma unroll
+                        for (int ks = 0; ks < KP / 16; ++ks)
+                            mma_f16(d, smem_desc(a0 + p * SLICE_BYTES + ks * 256, 128, 512),
+                                    smem_desc(b0 + q * B_BYTES + ks * 256, 128, 512), IDESC, p > 0 || ks > 0);
+                    }
+                mma_commit(&empty[s]);
+                mma_commit(&tfull);
+                ++it;
+            }
+            mma_commit(&drain);
+            long long n = 0;
+            while (!mbar_test(&drain, 0u) && ++n <= spin_limit) {
+            }
+        }
+    } else {
+        // ----------------------------------------------- epilogue (warps 0-3)
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const TcTile tl = tiles[t];
+            if (skip_tile(tl, nn, plain)) continue;
+            const bool ok = mbar_wait(&tfull, (unsigned)(it++) & 1u, &s_abort, err, spin_limit);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int F = tl.front, k = kk[F], n = nn[F], ld = n + k;
+            const int gi = tl.i0 + warp * 32 + lane;
+            const bool row_ok = gi < ld && !(plain && gi >= n);
+            const int e = expo[256 * tl.a_blk + warp * 32 + lane];
+            const int* fcol = expo + 256 * tl.b_blk + TC_BLK + tl.nk * OZ_N;
+            double* Af = pool + front_off[F] + gi;
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
+#pragma unroll 1
+            for (int ch = 0; ch < OZ_N / 16; ++ch) {
+                float v[NLEV][16];
+#pragma unroll
+                for (int l = 0; l < NLEV; ++l) tmem_ld16(taddr + l * OZ_N + ch * 16, v[l]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (ch == OZ_N / 16 - 1) {
+                    // the accumulators may be overwritten by the next tile's MMAs
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&tempty);
+                }
+                if (!row_ok) continue;
+#pragma unroll
+                for (int cc = 0; cc < 16; ++cc) {
+                    const int gj = tl.j0 + ch * 16 + cc;
+                    if (gj >= ld || !(gi >= gj || (gi >= n && gj >= n))) continue;
+                    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
+                    constexpr unsigned MB = 0x4B400000u;
+                    unsigned u[NLEV];
+#pragma unroll
+                    for (int l = 0; l < NLEV; ++l) u[l] = __float_as_uint(v[l][cc] + MAGIC);
+                    // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8): the pairs
+                    // (V1, V2), (V3, V4), (V5, V6) combine exactly in 32 bits
+                    const int dd = (int)(u[0] - MB);
+                    const int c2 = (int)((u[1] << 8) + u[2] - MB * 257u);
+                    const int b2 = (int)((u[3] << 8) + u[4] - MB * 257u);
+                    const int a2 = (int)((u[5] << 8) + u[6] - MB * 257u);
+                    const long long S = ((long long)dd << 40) + ((long long)c2 << 24) + ((long long)b2 << 8) +
+                                        (long long)(a2 >> 8);
+                    if (S == 0) continue;
+                    // the value added is -S 2^E0
+                    const int E0 = e + __ldg(fcol + ch * 16 + cc) - 54;
+                    const bool pos = S > 0;
+                    unsigned long long m = pos ? (unsigned long long)S : (unsigned long long)(-S);
+                    const int lz = __clzll((long long)m);
+                    const int be = 63 - lz + E0 + 1023;  // biased exponent of the leading bit
+                    double val;
+                    if (be >= 1 && be <= 2045) {
+                        m <<= lz;  // the leading bit at 63
+                        // 53 bits rounded to nearest; a carry into bit 53 raises the exponent by one
+                        const unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
+                        const unsigned long long bits =
+                            mant + ((unsigned long long)(be - 1) << 52) + ((unsigned long long)pos << 63);
+                        val = __longlong_as_double((long long)bits);
+                    } else {
+                        val = -ldexp((double)S, E0);  // subnormal or out of range: rare, FP64 arithmetic
+                    }
+                    atomicAdd(Af + (long long)gj * ld, val);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+static size_t oz_update_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
+
+// Pack + update of one panel step of FP64 fronts on the given stream.
+int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, int plain, cudaStream_t st) {
+    const int npack = R.o_end - R.o_begin, ntiles = R.q_end - R.q_begin;
+    if (ntiles <= 0 || npack <= 0) return RIGA_OK;
+    static int nsm = 0;
+    if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) nsm = 0;
+    const int grid = std::max(1, std::min(ntiles, nsm > 0 ? nsm : 148));
+    count_launch(c);
+    oz_pack_kernel<<<npack, 512, 0, st>>>(c->ozpacks.ptr + R.o_begin, c->kk.ptr, c->nn.ptr, c->front_off.ptr,
+                                          c->node_ptr.ptr, c->D.ptr, pool, c->ozpack.ptr, c->ozexp.ptr, c->flag.ptr);
+    count_launch(c);
+    oz_update_kernel<<<grid, UPD_THREADS, oz_update_smem(), st>>>(c->oztiles.ptr + R.q_begin, ntiles, c->kk.ptr,
+                                                                  c->nn.ptr, c->front_off.ptr, c->ozpack.ptr,
+                                                                  c->ozexp.ptr, pool, plain, c->flag.ptr,
+                                                                  c->wait_limit);
+    return RIGA_OK;
+}
+
+// Shared-memory size attribute and the digit-slice buffers (once per schedule)
+int prepare_oz(riga_ctx* c) {
+    RIGA_CUDA_TRY(c, cudaFuncSetAttribute(oz_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)oz_update_smem()));
+    const long long nblk = std::max<long long>(1, c->S.oz_pack_blocks);
+    if (c->ozpack.alloc((size_t)nblk * BLK_BYTES) != cudaSuccess)
+        return set_error(c, RIGA_ENOMEM, "FP64 tensor-core digit slices");
+    RIGA_CUDA_TRY(c, c->ozexp.alloc((size_t)256 * nblk));
+    return RIGA_OK;
+}
+
+}  // namespace riga

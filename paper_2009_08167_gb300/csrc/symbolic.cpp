@@ -285,6 +285,26 @@ std::string check_bulk_copies(const Symbolic& S, long long* checked) {
                 ++n;
             }
         }
+    for (const LevelPlan& P : S.levels)
+        for (const StepRange& R : P.steps) {
+            std::vector<int> blk_front;
+            for (int q = R.o_begin; q < R.o_end; ++q) {
+                const TcPack& pk = S.oz_packs[q];
+                if (pk.blk < 0 || pk.blk >= S.oz_pack_blocks || pk.r0 < 0 || pk.r0 >= S.ld[pk.front])
+                    return "FP64 tensor-core pack item " + std::to_string(q) + " out of range";
+                if ((int)blk_front.size() <= pk.blk) blk_front.resize(pk.blk + 1, -1);
+                blk_front[pk.blk] = pk.front;
+                ++n;
+            }
+            for (int t = R.q_begin; t < R.q_end; ++t) {
+                const TcTile& tl = S.oz_tiles[t];
+                const int nb = (int)blk_front.size();
+                if (tl.a_blk < 0 || tl.b_blk < 0 || tl.a_blk >= nb || tl.b_blk >= nb || tl.nk < 0 || tl.nk > 1 ||
+                    blk_front[tl.a_blk] != tl.front || blk_front[tl.b_blk] != tl.front)
+                    return "FP64 tensor-core tile " + std::to_string(t) + " references a block of another front or step";
+                ++n;
+            }
+        }
     if (checked) *checked = n;
     return "";
 }
@@ -302,6 +322,9 @@ void build_schedule(Symbolic& S) {
     S.tc_packs.clear();
     S.tc_narrow.clear();
     S.tc_pack_blocks = 0;
+    S.oz_packs.clear();
+    S.oz_tiles.clear();
+    S.oz_pack_blocks = 0;
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
     const int SMALL_TRAIL = S.small_trail;
@@ -401,6 +424,30 @@ void build_schedule(Symbolic& S) {
             }
             S.tc_pack_blocks = std::max<long long>(S.tc_pack_blocks, nblk_step);
             R.n_end = (int)S.tc_narrow.size();
+            // the FP64 tensor-core schedule of the step: every panel step
+            // updates the whole trailing matrix (K = 32) from digit-slice
+            // blocks of the trailing rows
+            R.o_begin = (int)S.oz_packs.size();
+            R.q_begin = (int)S.oz_tiles.size();
+            int oblk = 0;
+            for (int f : P.nodes) {
+                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
+                if (kf <= s * nb) continue;
+                const int c0 = s * nb + std::min(nb, kf - s * nb);
+                const int blk0 = oblk;
+                for (int r0 = c0; r0 < lf; r0 += TC_BLK) S.oz_packs.push_back({f, r0, oblk++, s * nb});
+                for (int i0 = c0; i0 < lf; i0 += OZ_M)
+                    for (int j0 = c0; j0 < lf; j0 += OZ_N) {
+                        const bool lower = j0 <= i0 + OZ_M - 1;
+                        const bool extra = (i0 + OZ_M > nf) && (j0 + OZ_N > nf);
+                        if (!(lower || extra)) continue;
+                        const int bj = (j0 - c0) / TC_BLK, half = ((j0 - c0) % TC_BLK) / OZ_N;
+                        S.oz_tiles.push_back({f, i0, j0, blk0 + (i0 - c0) / TC_BLK, blk0 + bj, half});
+                    }
+            }
+            S.oz_pack_blocks = std::max<long long>(S.oz_pack_blocks, oblk);
+            R.o_end = (int)S.oz_packs.size();
+            R.q_end = (int)S.oz_tiles.size();
             R.k_end = (int)S.tc_packs.size();
             R.c_end = (int)S.tc_tiles.size();
             P.steps.push_back(R);

@@ -42,6 +42,10 @@ constexpr int TC_KW = 64;
 // a_blk as its A operand (rows i0..) and at b_blk as its B operand (rows j0..).
 struct TcPack { int front; int r0; int blk; int p0; };  // rows r0..r0+127, super-panel columns from p0, chunks from blk
 struct TcTile { int front; int i0; int j0; int a_blk; int b_blk; int nk; };
+// FP64-accurate tensor-core update (oz_update.cu), one panel step: trailing
+// rows packed per 128-row block as 8-bit digit slices; tiles of OZ_M x OZ_N,
+// B rows j0.. in half b_half of block b_blk (TcTile.nk holds b_half)
+constexpr int OZ_M = 128, OZ_N = 64;
 struct ExtItem { int child; int c0; int c1; };      // extend-add columns [c0,c1) of a child
 
 // tree-solve kernel shapes: 256-thread CTAs per item (large fronts),
@@ -76,6 +80,8 @@ struct StepRange {   // one panel step of one level
     int p_begin, p_end;   // PanelItem range: row blocks below the diagonal block
     int c_begin, c_end;   // TcTile range of Symbolic::tc_tiles (tensor-core update tiles)
     int k_begin, k_end;   // TcPack range of Symbolic::tc_packs (blocks packed before the update)
+    int o_begin, o_end;   // TcPack range of Symbolic::oz_packs (FP64 digit-slice blocks of this step)
+    int q_begin, q_end;   // TcTile range of Symbolic::oz_tiles
     int n_begin, n_end;   // TileItem range of Symbolic::tc_narrow: 32x32 tiles of the panel's update
                           // restricted to the columns of its super-panel (tensor-core schedule)
     int t_begin, t_end;   // TileItem range: [t_begin, t_mid) 32x32 tiles, [t_mid, t_end) 16x16 tiles
@@ -138,6 +144,9 @@ struct Symbolic {
     std::vector<TcTile> tc_tiles;     // update tiles of TC_M x TC_N for the tensor-core update kernel
     std::vector<TcPack> tc_packs;     // panel blocks packed for it, per step
     std::vector<TileItemL> tc_narrow; // within-super-panel updates (CUDA cores, columns < the super-panel's end)
+    std::vector<TcPack> oz_packs;     // FP64 tensor-core schedule: blocks packed per panel step
+    std::vector<TcTile> oz_tiles;     //   and its OZ_M x OZ_N tiles
+    long long oz_pack_blocks = 0;     //   packed blocks of the largest step
     long long tc_pack_blocks = 0;     // packed blocks of the largest step
     std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
     std::vector<ChildRec> crec;       // per child_list entry

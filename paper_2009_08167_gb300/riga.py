@@ -89,6 +89,7 @@ def load_library(path=LIB_PATH):
     lib.riga_band_eig.argtypes = [I, I, P, P, I, P, P, I, P]
     lib.riga_set_eig_block.argtypes = [P, I]
     lib.riga_set_reorth.argtypes = [P, I]
+    lib.riga_set_fp64_update.argtypes = [P, I]
     lib.riga_autotune.argtypes = [P, P, P]
     lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
@@ -287,6 +288,11 @@ class Riga:
         ms = (ctypes.c_double * 6)()
         self._check(self.lib.riga_autotune(self.ctx, ctypes.byref(t), ms))
         return t.value, list(ms)
+
+    def set_fp64_update(self, mode):
+        """Schur updates of FP64 fronts: 0 on the CUDA cores (FP64 FMA), 1 on
+        the tensor cores from exact 8-bit digit-slice products."""
+        self._check(self.lib.riga_set_fp64_update(self.ctx, int(mode)))
 
     def set_reorth(self, passes):
         """1: recurrence + one full Gram-Schmidt pass (switching to 2 by itself

@@ -64,6 +64,13 @@ FACT_CASES = [Mesh(2, 16, 2, None), Mesh(2, 24, 3, 8, 8), Mesh(3, [5, 6, 4], 2, 
 
 @pytest.mark.parametrize("mesh", FACT_CASES, ids=[repr(m) for m in FACT_CASES])
 def test_factor_and_solve_parity(R, mesh):
+    factor_parity(R, mesh)
+
+
+def factor_parity(R, mesh):
+    """FP64 factor at sigma = 0 and two shifts in gaps against the oracle's
+    dense LDL^T of the permuted matrix: inertia, pivots, L entries, the
+    componentwise backward error of the GPU factor and one solve."""
     R.assemble(mesh)
     K, M = oracle_matrices(mesh)
     Kd, Md = K.todense(), M.todense()
