@@ -365,7 +365,11 @@ int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
  *    integers (splitting of Ozaki, Ogita, Oishi and Rump).  The error of an
  *    updated entry is about 2^-51 * 32 * 2^(e_i + f_j), where 2^e_i and
  *    2^f_j bound the panel rows of L21 and L21 D: the rounding level of FP64
- *    arithmetic, normwise per row pair instead of per product.
+ *    arithmetic, normwise per row pair instead of per product.  The extra
+ *    rows of the augmented fronts (the solve operators, whose rows hold
+ *    entries of widely different size) keep FP64 fused multiply-adds, and
+ *    an inertia-only factorization has none, so it runs all its updates on
+ *    the tensor cores.
  * FP32, TF32 and BF16 fronts are unaffected.
  * Errors: RIGA_EINVAL (ctx NULL, mode not 0 or 1).
  */
