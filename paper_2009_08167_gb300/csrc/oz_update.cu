@@ -4,12 +4,22 @@
 // error-free splitting of Ozaki, Ogita, Oishi and Rump, here with BF16
 // operands and FP32 accumulation in tensor memory).
 //
-// Splitting.  Row i of the panel L21 (32 entries), with e_i the smallest
+// Balancing.  The operands are L21 |D|^(1/2) and L21 D |D|^(-1/2) rather
+// than L21 and L21 D, with |D|^(1/2) rounded to a power of two per column
+// (exact scalings whose product is 1): at a shift inside the spectrum a
+// near-zero pivot makes its column of L21 huge and leaves that of L21 D
+// moderate, and the next pivot the reverse; unbalanced, the row maxima of
+// the two operands would come from different columns and their product,
+// which sets the error below, would far exceed every product term (a first
+// version lost up to 2^9 against FP64 there).  Below, x and y denote the
+// balanced entries.
+//
+// Splitting.  Row i of the panel (32 entries), with e_i the smallest
 // integer such that every |x_ik| < 2^e_i, becomes the integer row
 // X_ik = round(x_ik 2^(55 - e_i)), |X_ik| < 2^55, written in balanced base
 // 256: X_ik = sum_{p=0..6} a_p,ik 256^(6-p), a_0 in [-128, 128], the other
-// digits in [-128, 127].  Row j of L21 D likewise (exponent f_j, digits
-// b_q,jk).  Then
+// digits in [-128, 127].  Row j of the other operand likewise (exponent f_j,
+// digits b_q,jk).  Then
 //   (L21 D L21^T)_ij ~ 2^(e_i + f_j - 110) sum_{p,q} 256^(12-p-q) sum_k a_p,ik b_q,jk.
 // Every inner sum is an integer of magnitude at most 32 * 2^14: the BF16
 // digits are exact, so are their products, and so is their FP32
@@ -76,10 +86,10 @@ constexpr unsigned IDESC = make_idesc(1, OZ_M, OZ_N);   // BF16 x BF16 -> FP32, 
 
 static_assert(NLEV * OZ_N <= TMEM_COLS, "level accumulators exceed the tensor memory");
 
-// Integer X = round(x 2^(55 - e)) for |x| < 2^e, from the bits of x (no FP64
-// arithmetic): x = m 2^(E - 1075), m = 2^52 + mantissa.  Zero and subnormal
-// x give 0 (an error below 2^-1022); *bad is set for a non-finite x.
-__device__ __forceinline__ long long to_fixed(double x, int e, bool* bad) {
+// Integer X = round(x 2^(s + 55 - e)) for |x 2^s| < 2^e, from the bits of x
+// (no FP64 arithmetic): x = m 2^(E - 1075), m = 2^52 + mantissa.  Zero and
+// subnormal x give 0 (an error below 2^-1022); *bad is set for a non-finite x.
+__device__ __forceinline__ long long to_fixed(double x, int s, int e, bool* bad) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const int E = (int)((u >> 52) & 0x7FF);
     if (E == 0) return 0;
@@ -88,7 +98,7 @@ __device__ __forceinline__ long long to_fixed(double x, int e, bool* bad) {
         return 0;
     }
     const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = E - 1075 + 55 - e;  // X = m 2^sh, sh <= 2
+    const int sh = E + s - 1075 + 55 - e;  // X = m 2^sh, sh <= 2
     long long X;
     if (sh >= 0) X = (long long)(m << sh);
     else if (sh < -54) X = 0;
@@ -103,9 +113,19 @@ __device__ __forceinline__ unsigned bf16_of_int(int d) {
     return __float_as_uint(f) >> 16;
 }
 
-// exponent field of a double, from its bits
-__device__ __forceinline__ int exp_field(double x) {
-    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+constexpr int NOEXP = -(1 << 20);  // exponent of zero (below every scaled exponent)
+
+// exponent field of x 2^s (x normal), NOEXP for zero and subnormal x
+__device__ __forceinline__ int scaled_exp(double x, int s) {
+    const int E = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+    return E == 0 ? NOEXP : E + s;
+}
+
+// floor(log2 |d| / 2): 2^s is within a factor sqrt(2) of sqrt(|d|); 0 for a
+// zero, subnormal or non-finite d (the pivot check reports those)
+__device__ __forceinline__ int half_exp(double d) {
+    const int E = (int)(((unsigned long long)__double_as_longlong(d) >> 52) & 0x7FF);
+    return (E == 0 || E == 0x7FF) ? 0 : (E - 1023) >> 1;
 }
 
 }  // namespace
@@ -132,22 +152,27 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
     const double* A = pool + front_off[F] + gi;
     const double* d = D + node_ptr[F] + it.p0;
     double x[8], y[8];
-    int ea = 0, eb = 0;
+    int sc[8];
+    int ea = NOEXP, eb = NOEXP;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int kc = 8 * g + t;
         const bool in = kc < kb && gi < ld;
+        const double dk = kc < kb ? d[kc] : 1.0;
         x[t] = in ? A[(long long)(it.p0 + kc) * ld] : 0.0;
-        y[t] = in ? x[t] * d[kc] : 0.0;
-        ea = max(ea, exp_field(x[t]));
-        eb = max(eb, exp_field(y[t]));
+        y[t] = in ? x[t] * dk : 0.0;
+        // balanced operands L |D|^(1/2) and (L D) |D|^(-1/2), both scaled by
+        // powers of two: the product of the two is unchanged
+        sc[t] = half_exp(dk);
+        ea = max(ea, scaled_exp(x[t], sc[t]));
+        eb = max(eb, scaled_exp(y[t], -sc[t]));
     }
     sexp[0][g][r] = ea;
     sexp[1][g][r] = eb;
     __syncthreads();
     ea = max(max(sexp[0][0][r], sexp[0][1][r]), max(sexp[0][2][r], sexp[0][3][r]));
     eb = max(max(sexp[1][0][r], sexp[1][1][r]), max(sexp[1][2][r], sexp[1][3][r]));
-    // every |x| < 2^(E - 1022) for the largest exponent field E
+    // every |x 2^s| < 2^(E - 1022) for the largest scaled exponent field E
     const int e = ea - 1022, f = eb - 1022;
     if (g == 0) {
         expo[256 * it.blk + r] = e;
@@ -160,7 +185,7 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
         unsigned w[NDIG][4];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-            long long X = to_fixed(side == 0 ? x[t] : y[t], side == 0 ? e : f, &bad);
+            long long X = side == 0 ? to_fixed(x[t], sc[t], e, &bad) : to_fixed(y[t], -sc[t], f, &bad);
             // balanced base-256 digits, least significant first
 #pragma unroll
             for (int p = NDIG - 1; p >= 1; --p) {

@@ -10,10 +10,11 @@ variables, whose trailing matrices span many 128 x 64 tiles and end in
 ragged ones.  The update's error is about 2^-53 of 32 2^(e_i + f_j) per
 entry and panel (2^e_i, 2^f_j the row bounds of L21 and L21 D), below an
 FP64 dot product's 32 2^-53 of the same bound, so every FP64 bar holds
-unchanged.  The extra rows of the augmented fronts (the solve operators)
-stay on FP64 FMA: with row-wise digit scaling their small entries lose
-bits (a first version with them on the tensor cores missed the 1e-10 solve
-bar at 1.5e-10 on the 24^2 p=3 mesh)."""
+unchanged.  The operands are balanced by power-of-two |D|^(1/2) column
+scalings: without them, near-zero pivots at shifts inside the spectrum put
+the row maxima of L21 and L21 D in different columns, and a first version
+missed the 1e-10 solve bar (1.5e-10 on the 24^2 p=3 mesh, about 300 times
+the FMA path's error there)."""
 import numpy as np
 import pytest
 
