@@ -358,18 +358,18 @@ int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
  * and inertia checks inside riga_eigs, riga_eigs_interval and
  * riga_eigs_batch):
  *  mode = 0 (the default): CUDA cores, FP64 fused multiply-adds;
- *  mode = 1: tensor cores.  Each panel's rows are scaled by a power of two
- *    per row, rounded to 55-bit integers and split into seven balanced 8-bit
- *    digits (BF16); the 28 digit products with weight above FP64 rounding
- *    are accumulated exactly in FP32 tensor memory and recombined in 64-bit
- *    integers (splitting of Ozaki, Ogita, Oishi and Rump).  The error of an
- *    updated entry is about 2^-51 * 32 * 2^(e_i + f_j), where 2^e_i and
- *    2^f_j bound the panel rows of L21 and L21 D: the rounding level of FP64
- *    arithmetic, normwise per row pair instead of per product.  The extra
- *    rows of the augmented fronts (the solve operators, whose rows hold
- *    entries of widely different size) keep FP64 fused multiply-adds, and
- *    an inertia-only factorization has none, so it runs all its updates on
- *    the tensor cores.
+ *  mode = 1: tensor cores.  The panel operands L21 |D|^(1/2) and
+ *    L21 D |D|^(-1/2) (|D|^(1/2) rounded to powers of two per column: exact
+ *    scalings that keep the row maxima of the two operands in the same
+ *    columns next to near-zero pivots at shifts inside the spectrum) are
+ *    scaled by a power of two per row, rounded to 55-bit integers and split
+ *    into seven balanced 8-bit digits (BF16); the 28 digit products with
+ *    weight above FP64 rounding are accumulated exactly in FP32 tensor
+ *    memory and recombined in 64-bit integers (splitting of Ozaki, Ogita,
+ *    Oishi and Rump).  The error of an updated entry is about
+ *    2^-53 * 32 * 2^(e_i + f_j), where 2^e_i and 2^f_j bound the two
+ *    operands' panel rows: the rounding level of FP64 arithmetic, normwise
+ *    per row pair instead of per product.
  * FP32, TF32 and BF16 fronts are unaffected.
  * Errors: RIGA_EINVAL (ctx NULL, mode not 0 or 1).
  */

@@ -89,7 +89,6 @@ int upload_symbolic(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->tcnarrow.upload(S.tc_narrow.empty() ? std::vector<TileItemL>{TileItemL{0, 0, 0, 0}} : S.tc_narrow, st));
     RIGA_CUDA_TRY(c, c->ozpacks.upload(S.oz_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.oz_packs, st));
     RIGA_CUDA_TRY(c, c->oztiles.upload(S.oz_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.oz_tiles, st));
-    RIGA_CUDA_TRY(c, c->ozextra.upload(S.oz_extra.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.oz_extra, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     if (S.dim == 0) RIGA_CUDA_TRY(c, c->prob_of_pos.upload(S.prob_of_pos, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -358,7 +357,6 @@ static int upload_schedule(riga_ctx* c) {
     RIGA_CUDA_TRY(c, c->tcnarrow.upload(S.tc_narrow.empty() ? std::vector<TileItemL>{TileItemL{0, 0, 0, 0}} : S.tc_narrow, st));
     RIGA_CUDA_TRY(c, c->ozpacks.upload(S.oz_packs.empty() ? std::vector<TcPack>{TcPack{0, 0, 0, 0}} : S.oz_packs, st));
     RIGA_CUDA_TRY(c, c->oztiles.upload(S.oz_tiles.empty() ? std::vector<TcTile>{TcTile{0, 0, 0, 0, 0, 0}} : S.oz_tiles, st));
-    RIGA_CUDA_TRY(c, c->ozextra.upload(S.oz_extra.empty() ? std::vector<TileItem>{TileItem{0, 0, 0}} : S.oz_extra, st));
     RIGA_CUDA_TRY(c, c->eitems.upload(S.eitems.empty() ? std::vector<ExtItem>{ExtItem{0, 0, 0}} : S.eitems, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     ++c->sched_gen;

@@ -132,7 +132,6 @@ struct riga_ctx {
     riga::DevBuf<float> tcscale;           // per packed block: power-of-two operand scale (BF16)
     riga::DevBuf<riga::TcPack> ozpacks;    // FP64 tensor-core schedule: blocks to pack per step
     riga::DevBuf<riga::TcTile> oztiles;    //   its tiles
-    riga::DevBuf<riga::TileItem> ozextra;  //   the extra rows' CUDA-core tiles
     riga::DevBuf<unsigned char> ozpack;    //   digit-slice blocks of one step
     riga::DevBuf<int> ozexp;               //   per block: the rows' power-of-two exponents (A, then B)
     int fp64_tc = 0;                       // FP64 fronts: 0 CUDA-core updates, 1 tensor-core digit slices
@@ -287,7 +286,7 @@ int prepare_tc(riga_ctx* c);  // kernel attributes and packing buffers for the c
 int enqueue_tc_step(riga_ctx* c, const StepRange& R, int p0, float* pool, int plain, cudaStream_t st);
 // oz_update.cu: FP64-accurate Schur updates of FP64 fronts on the tensor cores
 int prepare_oz(riga_ctx* c);
-int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, cudaStream_t st);
+int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, int plain, cudaStream_t st);
 // factor.cu
 int enqueue_factor(riga_ctx* c);  // enqueue numeric LDL^T (no sync)
 int finish_factor(riga_ctx* c);   // sync, read flag and inertia

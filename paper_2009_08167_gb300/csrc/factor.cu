@@ -407,14 +407,8 @@ static int enqueue_factor_body(riga_ctx* c, T* pool, T* Q, cudaStream_t st) {
                 int rc = enqueue_tc_step(c, R, j0, reinterpret_cast<float*>(pool), plain, st);
                 if (rc) return rc;
             } else if (oz) {
-                // rows below n on the tensor cores; the extra rows (solve
-                // operators, not formed by an inertia-only factorization) in FP64
-                int rc = enqueue_oz_step(c, R, reinterpret_cast<double*>(pool), st);
+                int rc = enqueue_oz_step(c, R, reinterpret_cast<double*>(pool), plain, st);
                 if (rc) return rc;
-                if (!plain && R.x_end > R.x_begin)
-                    { count_launch(c); update_kernel<T, 32><<<R.x_end - R.x_begin, 64, 0, st>>>(c->ozextra.ptr + R.x_begin, j0,
-                                                                       c->kk.ptr, c->nn.ptr, c->front_off.ptr,
-                                                                       c->node_ptr.ptr, c->D.ptr, pool, plain); }
             } else {
                 if (R.t_mid > R.t_begin)
                     { count_launch(c); update_kernel<T, 32><<<R.t_mid - R.t_begin, 64, 0, st>>>(c->titems.ptr + R.t_begin, j0,

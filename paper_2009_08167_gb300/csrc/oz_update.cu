@@ -44,13 +44,7 @@
 //                     7 digit slices of L21 and of L21 D written as BF16 in
 //                     the MMA's shared-memory layout (K-major 8-row core
 //                     matrices, no swizzle; 8 KiB per slice);
-//   oz_update_kernel  persistent, one CTA per SM, 192 threads, over the lower
-//                     tiles of the rows below n (the front's own variables;
-//                     the extra rows n..n+k of the augmented front, which
-//                     build the solve operators, are updated beside it in
-//                     FP64 on the CUDA cores: their entries span many orders
-//                     of magnitude within a row, where the error bound
-//                     relative to the row maxima is not tight enough):
+//   oz_update_kernel  persistent, one CTA per SM, 192 threads:
 //     warp 4   producer: per 128 x 64 tile the A block's 7 slices and the 7
 //              slices of the B block's 64-row half (14 bulk copies, 84 KiB)
 //              into one of two shared-memory stages;
@@ -59,7 +53,8 @@
 //              FP32 (448 tensor-memory columns);
 //     warps 0-3 epilogue: tcgen05.ld of the 7 levels, 16 columns at a time,
 //              the integer recombination and the FP64 reductions (lower
-//              triangle).
+//              triangle, and the whole extra x extra block of the augmented
+//              front).
 //   Every wait is bounded: on expiry the kernel sets bit 2 of the error word,
 //   every role stops, in-flight copies and MMAs are waited for (bounded) and
 //   the tensor memory is freed.
@@ -111,6 +106,14 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int e, bool* bad)
 __device__ __forceinline__ unsigned bf16_of_int(int d) {
     const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
     return __float_as_uint(f) >> 16;
+}
+
+// An inertia-only factorization (plain) has no extra rows to update: its
+// tiles that start in them are skipped by all three roles alike
+__device__ __forceinline__ bool skip_tile(const TcTile& tl, const int* nn, int plain) {
+    if (!plain) return false;
+    const int n = nn[tl.front];
+    return tl.i0 >= n || tl.j0 >= n;
 }
 
 constexpr int NOEXP = -(1 << 20);  // exponent of zero (below every scaled exponent)
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
 __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
     const long long* __restrict__ front_off, const unsigned char* __restrict__ pack, const int* __restrict__ expo,
-    double* __restrict__ pool, int* __restrict__ err, long long spin_limit) {
+    double* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], tfull, tempty, drain;
     __shared__ unsigned s_tmem;
@@ -246,6 +249,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             int it = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 const TcTile tl = tiles[t];
+                if (skip_tile(tl, nn, plain)) continue;
                 const int s = it % NSTAGE;
                 if (!mbar_wait(&empty[s], ((unsigned)(it / NSTAGE) & 1u) ^ 1u, &s_abort, err, spin_limit)) break;
                 const unsigned char* pa = pack + (size_t)tl.a_blk * BLK_BYTES;
@@ -272,6 +276,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
         if (lane == 0) {
             int it = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                if (skip_tile(tiles[t], nn, plain)) continue;
                 if (!mbar_wait(&tempty, ((unsigned)it & 1u) ^ 1u, &s_abort, err, spin_limit)) break;
                 const int s = it % NSTAGE;
                 if (!mbar_wait(&full[s], (unsigned)(it / NSTAGE) & 1u, &s_abort, err, spin_limit)) break;
@@ -303,12 +308,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
         int it = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const TcTile tl = tiles[t];
+            if (skip_tile(tl, nn, plain)) continue;
             const bool ok = mbar_wait(&tfull, (unsigned)(it++) & 1u, &s_abort, err, spin_limit);
             if (!__all_sync(0xffffffffu, ok)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int F = tl.front, k = kk[F], n = nn[F], ld = n + k;
             const int gi = tl.i0 + warp * 32 + lane;
-            const bool row_ok = gi < n;  // the extra rows are updated beside this kernel
+            const bool row_ok = gi < ld && !(plain && gi >= n);
             const int e = expo[256 * tl.a_blk + warp * 32 + lane];
             const int* fcol = expo + 256 * tl.b_blk + TC_BLK + tl.nk * OZ_N;
             double* Af = pool + front_off[F] + gi;
@@ -328,7 +334,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
 #pragma unroll
                 for (int cc = 0; cc < 16; ++cc) {
                     const int gj = tl.j0 + ch * 16 + cc;
-                    if (gj > gi) continue;  // lower triangle (gj <= gi < n)
+                    // lower triangle, and the whole extra x extra block
+                    if (gj >= ld || !(gi >= gj || (gi >= n && gj >= n))) continue;
                     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
                     constexpr unsigned MB = 0x4B400000u;
                     unsigned u[NLEV];
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
 static size_t oz_update_smem() { return (size_t)NSTAGE * STAGE_BYTES + 1024; }
 
 // Pack + update of one panel step of FP64 fronts on the given stream.
-int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, cudaStream_t st) {
+int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, int plain, cudaStream_t st) {
     const int npack = R.o_end - R.o_begin, ntiles = R.q_end - R.q_begin;
     if (ntiles <= 0 || npack <= 0) return RIGA_OK;
     static int nsm = 0;
@@ -388,7 +395,7 @@ int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, cudaStream_t 
     count_launch(c);
     oz_update_kernel<<<grid, UPD_THREADS, oz_update_smem(), st>>>(c->oztiles.ptr + R.q_begin, ntiles, c->kk.ptr,
                                                                   c->nn.ptr, c->front_off.ptr, c->ozpack.ptr,
-                                                                  c->ozexp.ptr, pool, c->flag.ptr,
+                                                                  c->ozexp.ptr, pool, plain, c->flag.ptr,
                                                                   c->wait_limit);
     return RIGA_OK;
 }

@@ -300,8 +300,8 @@ std::string check_bulk_copies(const Symbolic& S, long long* checked) {
                 const TcTile& tl = S.oz_tiles[t];
                 const int nb = (int)blk_front.size();
                 if (tl.a_blk < 0 || tl.b_blk < 0 || tl.a_blk >= nb || tl.b_blk >= nb || tl.nk < 0 || tl.nk > 1 ||
-                    blk_front[tl.a_blk] != tl.front || blk_front[tl.b_blk] != tl.front || tl.i0 >= S.n[tl.front] ||
-                    tl.j0 >= S.n[tl.front])
+                    blk_front[tl.a_blk] != tl.front || blk_front[tl.b_blk] != tl.front || tl.i0 >= S.ld[tl.front] ||
+                    tl.j0 >= S.ld[tl.front])
                     return "FP64 tensor-core tile " + std::to_string(t) + " references a block of another front or step";
                 ++n;
             }
@@ -325,7 +325,6 @@ void build_schedule(Symbolic& S) {
     S.tc_pack_blocks = 0;
     S.oz_packs.clear();
     S.oz_tiles.clear();
-    S.oz_extra.clear();
     S.oz_pack_blocks = 0;
     S.eitems.clear();
     const int nb = S.nb, tile = S.tile, rb = S.rowblk;
@@ -427,33 +426,29 @@ void build_schedule(Symbolic& S) {
             S.tc_pack_blocks = std::max<long long>(S.tc_pack_blocks, nblk_step);
             R.n_end = (int)S.tc_narrow.size();
             // the FP64 tensor-core schedule of the step (K = 32, the panel):
-            // the trailing matrix's rows below n from digit-slice blocks
-            // (lower 128 x 64 tiles); the extra rows n..n+k, which build the
-            // solve operators (-A11^{-1} and its products) with entries of
-            // widely different size within a row, on 32x32 CUDA-core tiles
-            // in FP64, whose error is componentwise
+            // digit-slice blocks of the trailing rows, lower 128 x 64 tiles
+            // plus those of the extra x extra block
             R.o_begin = (int)S.oz_packs.size();
             R.q_begin = (int)S.oz_tiles.size();
-            R.x_begin = (int)S.oz_extra.size();
             int oblk = 0;
             for (int f : P.nodes) {
                 int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 const int c0 = s * nb + std::min(nb, kf - s * nb);
                 const int blk0 = oblk;
-                for (int r0 = c0; r0 < nf; r0 += TC_BLK) S.oz_packs.push_back({f, r0, oblk++, s * nb});
-                for (int i0 = c0; i0 < nf; i0 += OZ_M)
-                    for (int j0 = c0; j0 < nf && j0 <= i0 + OZ_M - 1; j0 += OZ_N) {
+                for (int r0 = c0; r0 < lf; r0 += TC_BLK) S.oz_packs.push_back({f, r0, oblk++, s * nb});
+                for (int i0 = c0; i0 < lf; i0 += OZ_M)
+                    for (int j0 = c0; j0 < lf; j0 += OZ_N) {
+                        const bool lower = j0 <= i0 + OZ_M - 1;
+                        const bool extra = (i0 + OZ_M > nf) && (j0 + OZ_N > nf);
+                        if (!(lower || extra)) continue;
                         const int bj = (j0 - c0) / TC_BLK, half = ((j0 - c0) % TC_BLK) / OZ_N;
                         S.oz_tiles.push_back({f, i0, j0, blk0 + (i0 - c0) / TC_BLK, blk0 + bj, half});
                     }
-                for (int i0 = nf; i0 < lf; i0 += 32)
-                    for (int j0 = c0; j0 < lf; j0 += 32) S.oz_extra.push_back({f, i0, j0});
             }
             S.oz_pack_blocks = std::max<long long>(S.oz_pack_blocks, oblk);
             R.o_end = (int)S.oz_packs.size();
             R.q_end = (int)S.oz_tiles.size();
-            R.x_end = (int)S.oz_extra.size();
             R.k_end = (int)S.tc_packs.size();
             R.c_end = (int)S.tc_tiles.size();
             P.steps.push_back(R);

@@ -82,7 +82,6 @@ struct StepRange {   // one panel step of one level
     int k_begin, k_end;   // TcPack range of Symbolic::tc_packs (blocks packed before the update)
     int o_begin, o_end;   // TcPack range of Symbolic::oz_packs (FP64 digit-slice blocks of this step)
     int q_begin, q_end;   // TcTile range of Symbolic::oz_tiles
-    int x_begin, x_end;   // TileItem range of Symbolic::oz_extra (the extra rows' update beside them)
     int n_begin, n_end;   // TileItem range of Symbolic::tc_narrow: 32x32 tiles of the panel's update
                           // restricted to the columns of its super-panel (tensor-core schedule)
     int t_begin, t_end;   // TileItem range: [t_begin, t_mid) 32x32 tiles, [t_mid, t_end) 16x16 tiles
@@ -146,8 +145,7 @@ struct Symbolic {
     std::vector<TcPack> tc_packs;     // panel blocks packed for it, per step
     std::vector<TileItemL> tc_narrow; // within-super-panel updates (CUDA cores, columns < the super-panel's end)
     std::vector<TcPack> oz_packs;     // FP64 tensor-core schedule: blocks packed per panel step
-    std::vector<TcTile> oz_tiles;     //   and its OZ_M x OZ_N tiles (rows and columns below n)
-    std::vector<TileItem> oz_extra;   //   32x32 CUDA-core tiles of the extra rows (n..n+k)
+    std::vector<TcTile> oz_tiles;     //   and its OZ_M x OZ_N tiles
     long long oz_pack_blocks = 0;     //   packed blocks of the largest step
     long long tc_pack_blocks = 0;     // packed blocks of the largest step
     std::vector<SolveItem> sitems;    // forward items (ascending height), then backward (descending)
