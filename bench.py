@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="riga", choices=["riga", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16"])
-    ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c4"],
+    ap.add_argument("--mesh", default="riga", choices=["riga", "iga", "c3", "c3s", "c4"],
                     help="riga / iga: the 2D 256^2 p=3 meshes (100 pairs, 2 slices); c3: 3D 64^3 p=2 rIGA bs8, "
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
     ap.add_argument("--block", type=int, default=2, choices=[0, 1, 2, 4],
@@ -87,6 +87,11 @@ def workload(mesh_kind):
         cfg = config_c3()
         cfg["slice"] = cfg["k"]
         return cfg
+    if mesh_kind == "c3s":
+        # the 3D family at 32^3 elements (N = 42,875, fronts up to 1820
+        # variables): kernel profiles on a case a few GB in size
+        from paper_2009_08167_gb300.inputs import Mesh
+        return dict(mesh=Mesh(3, 32, 2, 8), k=50, sigma=0.0, slice=50)
     cfg = config_c2(riga=(mesh_kind == "riga"))
     return cfg
 
