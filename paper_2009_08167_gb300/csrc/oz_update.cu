@@ -44,14 +44,15 @@
 //                     7 digit slices of L21 and of L21 D written as BF16 in
 //                     the MMA's shared-memory layout (K-major 8-row core
 //                     matrices, no swizzle; 8 KiB per slice);
-//   oz_update_kernel  persistent, one CTA per SM, 192 threads:
-//     warp 4   producer: per 128 x 64 tile the A block's 7 slices and the 7
+//   oz_update_kernel  persistent, one CTA per SM, 320 threads:
+//     warp 8   producer: per 128 x 64 tile the A block's 7 slices and the 7
 //              slices of the B block's 64-row half (14 bulk copies, 84 KiB)
 //              into one of two shared-memory stages;
-//     warp 5   MMA issuer: 56 tcgen05.mma (28 digit pairs x K = 32 in two
+//     warp 9   MMA issuer: 56 tcgen05.mma (28 digit pairs x K = 32 in two
 //              K = 16 instructions) into 7 level accumulators of 128 x 64
 //              FP32 (448 tensor-memory columns);
-//     warps 0-3 epilogue: tcgen05.ld of the 7 levels, 16 columns at a time,
+//     warps 0-7 epilogue: tcgen05.ld of the 7 levels, 16 columns at a time
+//              (warp w: lane quarter w % 4, column half w / 4),
 //              the integer recombination and the FP64 reductions (lower
 //              triangle, and the whole extra x extra block of the augmented
 //              front).
@@ -74,7 +75,8 @@ constexpr unsigned BLK_BYTES = 2 * NDIG * SLICE_BYTES;  // A slices, then B slic
 constexpr unsigned B_BYTES = OZ_N * KP * 2;             // B slice of a tile: 64 rows (4 KiB)
 constexpr unsigned STAGE_BYTES = NDIG * (SLICE_BYTES + B_BYTES);  // 84 KiB
 constexpr int NSTAGE = 2;
-constexpr int UPD_THREADS = 192;
+constexpr int EPI_WARPS = 8;                            // epilogue warps 0..7; producer 8, MMA issuer 9
+constexpr int UPD_THREADS = 32 * (EPI_WARPS + 2);
 constexpr int NLEV = 7;                                 // levels l = p + q = 0..6
 constexpr int TMEM_COLS = 512;                          // NLEV * OZ_N = 448, allocated as a power of two
 constexpr unsigned IDESC = make_idesc(1, OZ_M, OZ_N);   // BF16 x BF16 -> FP32, 128 x 64
@@ -210,6 +212,51 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
     if (bad) atomicOr(err, 1);
 }
 
+// 16 columns of one tile row (this lane): the level sums v[l][cc] (exact
+// integers) of column cc recombined and -S 2^(e_i + f_j - 54) added to the
+// front entry c0[cc * ld].  CHECK: skip entries outside the front, the lower
+// triangle and the extra x extra block.
+template <bool CHECK>
+__device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][16], int er, int myf, int cbase, double* c0, int ld,
+                                         int gi, int gj0, int ldf, int n, int rmax) {
+    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
+    constexpr unsigned MB = 0x4B400000u;
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) {
+        const int fj = __shfl_sync(0xffffffffu, myf, cbase + cc);  // every lane: before any skip
+        if (CHECK) {
+            const int gj = gj0 + cc;
+            if (gi >= rmax || gj >= ldf || !(gi >= gj || (gi >= n && gj >= n))) continue;
+        }
+        unsigned u[NLEV];
+#pragma unroll
+        for (int l = 0; l < NLEV; ++l) u[l] = __float_as_uint(v[l][cc] + MAGIC);
+        // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8): the pairs
+        // (V1, V2), (V3, V4), (V5, V6) combine exactly in 32 bits
+        const int dd = (int)(u[0] - MB);
+        const int c2 = (int)((u[1] << 8) + u[2] - MB * 257u);
+        const int b2 = (int)((u[3] << 8) + u[4] - MB * 257u);
+        const int a2 = (int)((u[5] << 8) + u[6] - MB * 257u);
+        const long long S =
+            ((long long)dd << 40) + ((long long)c2 << 24) + ((long long)b2 << 8) + (long long)(a2 >> 8);
+        const bool pos = S > 0;
+        unsigned long long m = pos ? (unsigned long long)S : (unsigned long long)(-S);
+        const int lz = __clzll((long long)m);
+        const int be = er + fj - lz;  // biased exponent of the leading bit
+        double val;
+        if (__builtin_expect(be >= 1 && be <= 2045, 1)) {
+            m <<= lz;  // the leading bit at 63
+            // 53 bits rounded to nearest; a carry into bit 53 raises the exponent by one
+            const unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
+            val = __longlong_as_double(
+                (long long)(mant + ((unsigned long long)(be - 1) << 52) + ((unsigned long long)pos << 63)));
+        } else {
+            val = -ldexp((double)S, be + lz - 63 - 1023);  // subnormal or out of range: rare, FP64 arithmetic
+        }
+        if (S != 0) atomicAdd(c0 + (long long)cc * ld, val);
+    }
+}
+
 __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
     const long long* __restrict__ front_off, const unsigned char* __restrict__ pack, const int* __restrict__ expo,
@@ -233,7 +280,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             mbar_init(&empty[s], 1);
         }
         mbar_init(&tfull, 1);
-        mbar_init(&tempty, 4 * 32);
+        mbar_init(&tempty, EPI_WARPS * 32);
         mbar_init(&drain, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -243,7 +290,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
 
-    if (warp == 4) {
+    if (warp == EPI_WARPS) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             int it = 0;
@@ -271,7 +318,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == EPI_WARPS + 1) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
             int it = 0;
@@ -304,7 +351,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             }
         }
     } else {
-        // ----------------------------------------------- epilogue (warps 0-3)
+        // ------------------------------------------- epilogue (warps 0..7)
+        // warp w: tile rows 32 (w % 4) .. + 31 (its tensor-memory lane
+        // quarter), columns 32 (w / 4) .. + 31 in two chunks of 16
+        const int q4 = warp & 3, h = warp >> 2;
         int it = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const TcTile tl = tiles[t];
@@ -313,62 +363,32 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             if (!__all_sync(0xffffffffu, ok)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int F = tl.front, k = kk[F], n = nn[F], ld = n + k;
-            const int gi = tl.i0 + warp * 32 + lane;
-            const bool row_ok = gi < ld && !(plain && gi >= n);
-            const int e = expo[256 * tl.a_blk + warp * 32 + lane];
-            const int* fcol = expo + 256 * tl.b_blk + TC_BLK + tl.nk * OZ_N;
-            double* Af = pool + front_off[F] + gi;
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
+            const int rmax = plain ? n : ld;
+            const int gi = tl.i0 + q4 * 32 + lane;
+            const int gj0 = tl.j0 + h * 32;
+            // biased exponent of -S 2^(e_i + f_j - 54) is er + f_j - lz(S)
+            const int er = expo[256 * tl.a_blk + q4 * 32 + lane] + (1023 - 54 + 63);
+            const int myf = expo[256 * tl.b_blk + TC_BLK + tl.nk * OZ_N + h * 32 + lane];
+            // no per-entry masks when every row and column exists and every
+            // entry is in the lower triangle or the extra x extra block
+            const int r0 = tl.i0 + q4 * 32;
+            const bool fast = r0 + 32 <= rmax && gj0 + 32 <= ld && (r0 >= gj0 + 31 || (r0 >= n && gj0 >= n));
+            double* col = pool + front_off[F] + gi + (long long)gj0 * ld;
+            const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * 32);
 #pragma unroll 1
-            for (int ch = 0; ch < OZ_N / 16; ++ch) {
+            for (int ch = 0; ch < 2; ++ch) {
                 float v[NLEV][16];
 #pragma unroll
                 for (int l = 0; l < NLEV; ++l) tmem_ld16(taddr + l * OZ_N + ch * 16, v[l]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (ch == OZ_N / 16 - 1) {
+                if (ch == 1) {
                     // the accumulators may be overwritten by the next tile's MMAs
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(&tempty);
                 }
-                if (!row_ok) continue;
-#pragma unroll
-                for (int cc = 0; cc < 16; ++cc) {
-                    const int gj = tl.j0 + ch * 16 + cc;
-                    // lower triangle, and the whole extra x extra block
-                    if (gj >= ld || !(gi >= gj || (gi >= n && gj >= n))) continue;
-                    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
-                    constexpr unsigned MB = 0x4B400000u;
-                    unsigned u[NLEV];
-#pragma unroll
-                    for (int l = 0; l < NLEV; ++l) u[l] = __float_as_uint(v[l][cc] + MAGIC);
-                    // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8): the pairs
-                    // (V1, V2), (V3, V4), (V5, V6) combine exactly in 32 bits
-                    const int dd = (int)(u[0] - MB);
-                    const int c2 = (int)((u[1] << 8) + u[2] - MB * 257u);
-                    const int b2 = (int)((u[3] << 8) + u[4] - MB * 257u);
-                    const int a2 = (int)((u[5] << 8) + u[6] - MB * 257u);
-                    const long long S = ((long long)dd << 40) + ((long long)c2 << 24) + ((long long)b2 << 8) +
-                                        (long long)(a2 >> 8);
-                    if (S == 0) continue;
-                    // the value added is -S 2^E0
-                    const int E0 = e + __ldg(fcol + ch * 16 + cc) - 54;
-                    const bool pos = S > 0;
-                    unsigned long long m = pos ? (unsigned long long)S : (unsigned long long)(-S);
-                    const int lz = __clzll((long long)m);
-                    const int be = 63 - lz + E0 + 1023;  // biased exponent of the leading bit
-                    double val;
-                    if (be >= 1 && be <= 2045) {
-                        m <<= lz;  // the leading bit at 63
-                        // 53 bits rounded to nearest; a carry into bit 53 raises the exponent by one
-                        const unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
-                        const unsigned long long bits =
-                            mant + ((unsigned long long)(be - 1) << 52) + ((unsigned long long)pos << 63);
-                        val = __longlong_as_double((long long)bits);
-                    } else {
-                        val = -ldexp((double)S, E0);  // subnormal or out of range: rare, FP64 arithmetic
-                    }
-                    atomicAdd(Af + (long long)gj * ld, val);
-                }
+                double* c0 = col + (long long)(ch * 16) * ld;
+                if (fast) oz_chunk<false>(v, er, myf, ch * 16, c0, ld, gi, gj0 + ch * 16, ld, n, rmax);
+                else oz_chunk<true>(v, er, myf, ch * 16, c0, ld, gi, gj0 + ch * 16, ld, n, rmax);
             }
         }
     }

@@ -356,11 +356,17 @@ void build_schedule(Symbolic& S) {
                 if (S.k[f] > s * nb) S.pitems.push_back({f, s * nb});
             R.d_end = (int)S.pitems.size();
             R.p_begin = (int)S.pitems.size();
+            // Rows and columns of the augmented front beyond n + c0 (c0 = the
+            // end of the panel) are extra rows of pivots after the panel:
+            // they start as identity rows and stay exactly zero in every
+            // column before their own pivot, so the panel's row solve and
+            // trailing update skip them (their products are exact zeros)
             for (int f : P.nodes) {
-                int kf = S.k[f], lf = S.ld[f];
+                int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 int kb = std::min(nb, kf - s * nb);
-                for (int r0 = s * nb + kb; r0 < lf; r0 += rb) S.pitems.push_back({f, r0});
+                const int le = std::min(lf, nf + s * nb + kb);
+                for (int r0 = s * nb + kb; r0 < le; r0 += rb) S.pitems.push_back({f, r0});
             }
             R.p_end = (int)S.pitems.size();
             // trailing update: lower tiles of the augmented front, plus the
@@ -375,9 +381,10 @@ void build_schedule(Symbolic& S) {
                     int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                     if (kf <= s * nb) continue;
                     const int c0 = s * nb + std::min(nb, kf - s * nb);
-                    const int tl = (lf - c0 <= SMALL_TRAIL) ? 16 : tile;
+                    const int le = std::min(lf, nf + c0);
+                    const int tl = (le - c0 <= SMALL_TRAIL) ? 16 : tile;
                     if ((pass == 0) != (tl == tile)) continue;
-                    const int T = (lf - c0 + tl - 1) / tl;
+                    const int T = (le - c0 + tl - 1) / tl;
                     for (int bi = 0; bi < T; ++bi)
                         for (int bj = 0; bj < T; ++bj) {
                             int i0 = c0 + bi * tl, j0 = c0 + bj * tl;
@@ -403,21 +410,22 @@ void build_schedule(Symbolic& S) {
                 int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 const int c0 = s * nb + std::min(nb, kf - s * nb);
+                const int le = std::min(lf, nf + c0);
                 const int S0 = (s * nb) / TC_KW * TC_KW, S1 = std::min(S0 + TC_KW, kf);
                 if (c0 < S1) {
-                    // narrow update: columns [c0, S1), rows j0..lf
+                    // narrow update: columns [c0, S1), rows j0..le
                     for (int j0 = c0; j0 < S1; j0 += nb)
-                        for (int i0 = j0; i0 < lf; i0 += nb) S.tc_narrow.push_back({f, i0, j0, S1});
+                        for (int i0 = j0; i0 < le; i0 += nb) S.tc_narrow.push_back({f, i0, j0, S1});
                     continue;
                 }
                 const int nk = (S1 - S0 + nb - 1) / nb;
                 const int blk0 = nblk_step;
-                for (int r0 = c0; r0 < lf; r0 += TC_BLK) {
+                for (int r0 = c0; r0 < le; r0 += TC_BLK) {
                     S.tc_packs.push_back({f, r0, nblk_step, S0});
                     nblk_step += nk;
                 }
-                for (int i0 = c0, bi = 0; i0 < lf; i0 += TC_M, ++bi)
-                    for (int j0 = c0, bj = 0; j0 < lf; j0 += TC_N, ++bj) {
+                for (int i0 = c0, bi = 0; i0 < le; i0 += TC_M, ++bi)
+                    for (int j0 = c0, bj = 0; j0 < le; j0 += TC_N, ++bj) {
                         const bool lower = j0 <= i0;
                         const bool extra = (i0 + TC_M > nf) && (j0 + TC_N > nf);
                         if (lower || extra) S.tc_tiles.push_back({f, i0, j0, blk0 + bi * nk, blk0 + bj * nk, nk});
@@ -435,10 +443,11 @@ void build_schedule(Symbolic& S) {
                 int kf = S.k[f], nf = S.n[f], lf = S.ld[f];
                 if (kf <= s * nb) continue;
                 const int c0 = s * nb + std::min(nb, kf - s * nb);
+                const int le = std::min(lf, nf + c0);
                 const int blk0 = oblk;
-                for (int r0 = c0; r0 < lf; r0 += TC_BLK) S.oz_packs.push_back({f, r0, oblk++, s * nb});
-                for (int i0 = c0; i0 < lf; i0 += OZ_M)
-                    for (int j0 = c0; j0 < lf; j0 += OZ_N) {
+                for (int r0 = c0; r0 < le; r0 += TC_BLK) S.oz_packs.push_back({f, r0, oblk++, s * nb});
+                for (int i0 = c0; i0 < le; i0 += OZ_M)
+                    for (int j0 = c0; j0 < le; j0 += OZ_N) {
                         const bool lower = j0 <= i0 + OZ_M - 1;
                         const bool extra = (i0 + OZ_M > nf) && (j0 + OZ_N > nf);
                         if (!(lower || extra)) continue;
