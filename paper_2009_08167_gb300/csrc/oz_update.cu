@@ -44,15 +44,15 @@
 //                     7 digit slices of L21 and of L21 D written as BF16 in
 //                     the MMA's shared-memory layout (K-major 8-row core
 //                     matrices, no swizzle; 8 KiB per slice);
-//   oz_update_kernel  persistent, one CTA per SM, 320 threads:
-//     warp 8   producer: per 128 x 64 tile the A block's 7 slices and the 7
+//   oz_update_kernel  persistent, one CTA per SM, 576 threads:
+//     warp 16  producer: per 128 x 64 tile the A block's 7 slices and the 7
 //              slices of the B block's 64-row half (14 bulk copies, 84 KiB)
 //              into one of two shared-memory stages;
-//     warp 9   MMA issuer: 56 tcgen05.mma (28 digit pairs x K = 32 in two
+//     warp 17  MMA issuer: 56 tcgen05.mma (28 digit pairs x K = 32 in two
 //              K = 16 instructions) into 7 level accumulators of 128 x 64
 //              FP32 (448 tensor-memory columns);
-//     warps 0-7 epilogue: tcgen05.ld of the 7 levels, 16 columns at a time
-//              (warp w: lane quarter w % 4, column half w / 4),
+//     warps 0-15 epilogue: tcgen05.ld of the 7 levels, 8 columns at a time
+//              (warp w: lane quarter w % 4, columns 16 (w / 4) .. + 15),
 //              the integer recombination and the FP64 reductions (lower
 //              triangle, and the whole extra x extra block of the augmented
 //              front).
@@ -75,7 +75,8 @@ constexpr unsigned BLK_BYTES = 2 * NDIG * SLICE_BYTES;  // A slices, then B slic
 constexpr unsigned B_BYTES = OZ_N * KP * 2;             // B slice of a tile: 64 rows (4 KiB)
 constexpr unsigned STAGE_BYTES = NDIG * (SLICE_BYTES + B_BYTES);  // 84 KiB
 constexpr int NSTAGE = 2;
-constexpr int EPI_WARPS = 8;                            // epilogue warps 0..7; producer 8, MMA issuer 9
+constexpr int EPI_WARPS = 16;                           // epilogue warps 0..15; producer 16, MMA issuer 17
+constexpr int CW = 8;                                   // accumulator columns per tensor-memory load
 constexpr int UPD_THREADS = 32 * (EPI_WARPS + 2);
 constexpr int NLEV = 7;                                 // levels l = p + q = 0..6
 constexpr int TMEM_COLS = 512;                          // NLEV * OZ_N = 448, allocated as a power of two
@@ -212,17 +213,20 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
     if (bad) atomicOr(err, 1);
 }
 
-// 16 columns of one tile row (this lane): the level sums v[l][cc] (exact
+// CW columns of one tile row (this lane): the level sums v[l][cc] (exact
 // integers) of column cc recombined and -S 2^(e_i + f_j - 54) added to the
-// front entry c0[cc * ld].  CHECK: skip entries outside the front, the lower
-// triangle and the extra x extra block.
+// front entry c0[cc * ld] (no FP64 arithmetic: the double is assembled from
+// S's magnitude, leading-bit position and the exponents).  Results below the
+// normal range are flushed to zero (an error below 2^-1022).  CHECK: skip
+// entries outside the front, the lower triangle and the extra x extra block.
 template <bool CHECK>
-__device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][16], int er, int myf, int cbase, double* c0, int ld,
+__device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int myf, int cbase, double* c0, int ld,
                                          int gi, int gj0, int ldf, int n, int rmax) {
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
     constexpr unsigned MB = 0x4B400000u;
+    constexpr unsigned long long SIGN = 1ull << 63;
 #pragma unroll
-    for (int cc = 0; cc < 16; ++cc) {
+    for (int cc = 0; cc < CW; ++cc) {
         const int fj = __shfl_sync(0xffffffffu, myf, cbase + cc);  // every lane: before any skip
         if (CHECK) {
             const int gj = gj0 + cc;
@@ -234,26 +238,22 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][16], int er, int
         // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8): the pairs
         // (V1, V2), (V3, V4), (V5, V6) combine exactly in 32 bits
         const int dd = (int)(u[0] - MB);
-        const int c2 = (int)((u[1] << 8) + u[2] - MB * 257u);
-        const int b2 = (int)((u[3] << 8) + u[4] - MB * 257u);
-        const int a2 = (int)((u[5] << 8) + u[6] - MB * 257u);
+        const int c2 = (int)(u[1] * 256u + u[2] - MB * 257u);
+        const int b2 = (int)(u[3] * 256u + u[4] - MB * 257u);
+        const int a2 = (int)(u[5] * 256u + u[6] - MB * 257u);
         const long long S =
             ((long long)dd << 40) + ((long long)c2 << 24) + ((long long)b2 << 8) + (long long)(a2 >> 8);
-        const bool pos = S > 0;
-        unsigned long long m = pos ? (unsigned long long)S : (unsigned long long)(-S);
-        const int lz = __clzll((long long)m);
+        const unsigned long long sgn = (unsigned long long)(S >> 63);  // all ones when S < 0
+        const unsigned long long m0 = ((unsigned long long)S ^ sgn) - sgn;
+        const int lz = __clzll((long long)m0);
+        const unsigned long long m = m0 << (lz & 63);  // the leading bit at 63
+        // 53 bits rounded to nearest; a carry into bit 53 raises the exponent by one
+        const unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
         const int be = er + fj - lz;  // biased exponent of the leading bit
-        double val;
-        if (__builtin_expect(be >= 1 && be <= 2045, 1)) {
-            m <<= lz;  // the leading bit at 63
-            // 53 bits rounded to nearest; a carry into bit 53 raises the exponent by one
-            const unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
-            val = __longlong_as_double(
-                (long long)(mant + ((unsigned long long)(be - 1) << 52) + ((unsigned long long)pos << 63)));
-        } else {
-            val = -ldexp((double)S, be + lz - 63 - 1023);  // subnormal or out of range: rare, FP64 arithmetic
-        }
-        if (S != 0) atomicAdd(c0 + (long long)cc * ld, val);
+        const unsigned long long sbit = ~sgn & SIGN;  // -S: negative when S > 0
+        unsigned long long bits = mant + ((unsigned long long)(be - 1) << 52) + sbit;
+        if ((unsigned)(be - 1) >= 2045u) bits = be < 1 ? sbit : (sbit | 0x7FF0000000000000ull);
+        if (m0 != 0) atomicAdd(c0 + (long long)cc * ld, __longlong_as_double((long long)bits));
     }
 }
 
@@ -351,10 +351,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             }
         }
     } else {
-        // ------------------------------------------- epilogue (warps 0..7)
+        // ------------------------------------------ epilogue (warps 0..15)
         // warp w: tile rows 32 (w % 4) .. + 31 (its tensor-memory lane
-        // quarter), columns 32 (w / 4) .. + 31 in two chunks of 16
-        const int q4 = warp & 3, h = warp >> 2;
+        // quarter), columns 16 (w / 4) .. + 15 in two loads of 8
+        const int q4 = warp & 3, grp = warp >> 2;
         int it = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const TcTile tl = tiles[t];
@@ -365,30 +365,30 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             const int F = tl.front, k = kk[F], n = nn[F], ld = n + k;
             const int rmax = plain ? n : ld;
             const int gi = tl.i0 + q4 * 32 + lane;
-            const int gj0 = tl.j0 + h * 32;
+            const int gj0 = tl.j0 + grp * 16;
             // biased exponent of -S 2^(e_i + f_j - 54) is er + f_j - lz(S)
             const int er = expo[256 * tl.a_blk + q4 * 32 + lane] + (1023 - 54 + 63);
-            const int myf = expo[256 * tl.b_blk + TC_BLK + tl.nk * OZ_N + h * 32 + lane];
+            const int myf = expo[256 * tl.b_blk + TC_BLK + tl.nk * OZ_N + grp * 16 + (lane & 15)];
             // no per-entry masks when every row and column exists and every
             // entry is in the lower triangle or the extra x extra block
             const int r0 = tl.i0 + q4 * 32;
-            const bool fast = r0 + 32 <= rmax && gj0 + 32 <= ld && (r0 >= gj0 + 31 || (r0 >= n && gj0 >= n));
+            const bool fast = r0 + 32 <= rmax && gj0 + 16 <= ld && (r0 >= gj0 + 15 || (r0 >= n && gj0 >= n));
             double* col = pool + front_off[F] + gi + (long long)gj0 * ld;
-            const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * 32);
+            const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(grp * 16);
 #pragma unroll 1
             for (int ch = 0; ch < 2; ++ch) {
-                float v[NLEV][16];
+                float v[NLEV][CW];
 #pragma unroll
-                for (int l = 0; l < NLEV; ++l) tmem_ld16(taddr + l * OZ_N + ch * 16, v[l]);
+                for (int l = 0; l < NLEV; ++l) tmem_ld8(taddr + l * OZ_N + ch * CW, v[l]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (ch == 1) {
                     // the accumulators may be overwritten by the next tile's MMAs
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(&tempty);
                 }
-                double* c0 = col + (long long)(ch * 16) * ld;
-                if (fast) oz_chunk<false>(v, er, myf, ch * 16, c0, ld, gi, gj0 + ch * 16, ld, n, rmax);
-                else oz_chunk<true>(v, er, myf, ch * 16, c0, ld, gi, gj0 + ch * 16, ld, n, rmax);
+                double* c0 = col + (long long)(ch * CW) * ld;
+                if (fast) oz_chunk<false>(v, er, myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
+                else oz_chunk<true>(v, er, myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
             }
         }
     }

@@ -98,6 +98,15 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
         : "memory");
 }
 
+// 8 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
+    unsigned* r = reinterpret_cast<unsigned*>(v);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 // 16 consecutive accumulator columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
     unsigned* r = reinterpret_cast<unsigned*>(v);
