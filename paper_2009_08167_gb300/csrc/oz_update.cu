@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
 // S's magnitude, leading-bit position and the exponents).  Results below the
 // normal range are flushed to zero (an error below 2^-1022).  CHECK: skip
 // entries outside the front, the lower triangle and the extra x extra block.
-template <bool CHECK>
+// RANGE: results may fall outside the normal range (else known not to).
+template <bool CHECK, bool RANGE>
 __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int myf, int cbase, double* c0, int ld,
                                          int gi, int gj0, int ldf, int n, int rmax) {
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
@@ -252,7 +253,7 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
         const int be = er + fj - lz;  // biased exponent of the leading bit
         const unsigned long long sbit = ~sgn & SIGN;  // -S: negative when S > 0
         unsigned long long bits = mant + ((unsigned long long)(be - 1) << 52) + sbit;
-        if ((unsigned)(be - 1) >= 2045u) bits = be < 1 ? sbit : (sbit | 0x7FF0000000000000ull);
+        if (RANGE && (unsigned)(be - 1) >= 2045u) bits = be < 1 ? sbit : (sbit | 0x7FF0000000000000ull);
         if (m0 != 0) atomicAdd(c0 + (long long)cc * ld, __longlong_as_double((long long)bits));
     }
 }
@@ -353,27 +354,54 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     } else {
         // ------------------------------------------ epilogue (warps 0..15)
         // warp w: tile rows 32 (w % 4) .. + 31 (its tensor-memory lane
-        // quarter), columns 16 (w / 4) .. + 15 in two loads of 8
+        // quarter), columns 16 (w / 4) .. + 15 in two loads of 8.  The next
+        // tile's front data and exponents are loaded while the second half
+        // of the current one is computed.
         const int q4 = warp & 3, grp = warp >> 2;
-        int it = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        struct Meta {
+            int skip, n, ld, i0, j0, er, myf;
+            long long off;
+        };
+        auto load_meta = [&](int t, Meta& m) {
+            if (t >= ntiles) return;
             const TcTile tl = tiles[t];
-            if (skip_tile(tl, nn, plain)) continue;
+            const int F = tl.front;
+            m.n = nn[F];
+            m.ld = m.n + kk[F];
+            m.off = front_off[F];
+            m.i0 = tl.i0;
+            m.j0 = tl.j0;
+            m.skip = plain && (tl.i0 >= m.n || tl.j0 >= m.n);
+            // biased exponent of -S 2^(e_i + f_j - 54) is er + f_j - lz(S)
+            m.er = expo[256 * tl.a_blk + q4 * 32 + lane] + (1023 - 54 + 63);
+            m.myf = expo[256 * tl.b_blk + TC_BLK + tl.nk * OZ_N + grp * 16 + (lane & 15)];
+        };
+        Meta cur{}, nxt{};
+        load_meta(blockIdx.x, cur);
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles;) {
+            const int tn = t + gridDim.x;
+            if (cur.skip) {
+                t = tn;
+                load_meta(t, cur);
+                continue;
+            }
             const bool ok = mbar_wait(&tfull, (unsigned)(it++) & 1u, &s_abort, err, spin_limit);
             if (!__all_sync(0xffffffffu, ok)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int F = tl.front, k = kk[F], n = nn[F], ld = n + k;
+            const int n = cur.n, ld = cur.ld;
             const int rmax = plain ? n : ld;
-            const int gi = tl.i0 + q4 * 32 + lane;
-            const int gj0 = tl.j0 + grp * 16;
-            // biased exponent of -S 2^(e_i + f_j - 54) is er + f_j - lz(S)
-            const int er = expo[256 * tl.a_blk + q4 * 32 + lane] + (1023 - 54 + 63);
-            const int myf = expo[256 * tl.b_blk + TC_BLK + tl.nk * OZ_N + grp * 16 + (lane & 15)];
+            const int gi = cur.i0 + q4 * 32 + lane;
+            const int gj0 = cur.j0 + grp * 16;
             // no per-entry masks when every row and column exists and every
             // entry is in the lower triangle or the extra x extra block
-            const int r0 = tl.i0 + q4 * 32;
+            const int r0 = cur.i0 + q4 * 32;
             const bool fast = r0 + 32 <= rmax && gj0 + 16 <= ld && (r0 >= gj0 + 15 || (r0 >= n && gj0 >= n));
-            double* col = pool + front_off[F] + gi + (long long)gj0 * ld;
+            // no per-entry exponent-range selects when every possible result
+            // of the warp is a normal double (4 <= lz <= 63 as 0 < |S| < 2^60)
+            const int fmin = __reduce_min_sync(0xffffffffu, cur.myf), fmax = __reduce_max_sync(0xffffffffu, cur.myf);
+            const bool normal = __all_sync(0xffffffffu, cur.er + fmin - 63 >= 1 && cur.er + fmax - 4 <= 2045);
+            double* col = pool + cur.off + gi + (long long)gj0 * ld;
             const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(grp * 16);
 #pragma unroll 1
             for (int ch = 0; ch < 2; ++ch) {
@@ -385,11 +413,15 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
                     // the accumulators may be overwritten by the next tile's MMAs
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(&tempty);
+                    load_meta(tn, nxt);
                 }
                 double* c0 = col + (long long)(ch * CW) * ld;
-                if (fast) oz_chunk<false>(v, er, myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
-                else oz_chunk<true>(v, er, myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
+                if (fast && normal) oz_chunk<false, false>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
+                else if (fast) oz_chunk<false, true>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
+                else oz_chunk<true, true>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
             }
+            t = tn;
+            cur = nxt;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
