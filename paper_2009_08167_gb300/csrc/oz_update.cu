@@ -213,6 +213,19 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
     if (bad) atomicOr(err, 1);
 }
 
+constexpr unsigned MB = 0x4B400000u;  // float bits of 1.5 * 2^23: MB + V are the bits of V + 1.5 * 2^23
+// sum of the MB terms of S (mod 2^64): MB (2^40 + 2^32 + 2^24 + 2^16 + 2^8 + 1) + MB / 2^8
+constexpr unsigned long long KMB =
+    ((unsigned long long)MB << 40) + ((unsigned long long)MB << 32) + ((unsigned long long)MB << 24) +
+    ((unsigned long long)MB << 16) + ((unsigned long long)MB << 8) + MB + (MB >> 8);
+
+// a * b + c with a 32 x 32 -> 64-bit product (one IMAD.WIDE.U32)
+__device__ __forceinline__ unsigned long long mad_wide(unsigned a, unsigned b, unsigned long long c) {
+    unsigned long long d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
 // CW columns of one tile row (this lane): the level sums v[l][cc] (exact
 // integers) of column cc recombined and -S 2^(e_i + f_j - 54) added to the
 // front entry c0[cc * ld] (no FP64 arithmetic: the double is assembled from
@@ -224,7 +237,6 @@ template <bool CHECK, bool RANGE>
 __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int myf, int cbase, double* c0, int ld,
                                          int gi, int gj0, int ldf, int n, int rmax) {
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
-    constexpr unsigned MB = 0x4B400000u;
     constexpr unsigned long long SIGN = 1ull << 63;
 #pragma unroll
     for (int cc = 0; cc < CW; ++cc) {
@@ -236,14 +248,18 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
         unsigned u[NLEV];
 #pragma unroll
         for (int l = 0; l < NLEV; ++l) u[l] = __float_as_uint(v[l][cc] + MAGIC);
-        // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8): the pairs
-        // (V1, V2), (V3, V4), (V5, V6) combine exactly in 32 bits
-        const int dd = (int)(u[0] - MB);
-        const int c2 = (int)(u[1] * 256u + u[2] - MB * 257u);
-        const int b2 = (int)(u[3] * 256u + u[4] - MB * 257u);
-        const int a2 = (int)(u[5] * 256u + u[6] - MB * 257u);
-        const long long S =
-            ((long long)dd << 40) + ((long long)c2 << 24) + ((long long)b2 << 8) + (long long)(a2 >> 8);
+        // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8)
+        //   = sum_{l<6} V_l 2^(40-8l) + floor(V6 / 2^8),
+        // accumulated from u_l = MB + V_l by 64-bit multiply-adds (mod 2^64;
+        // MB is a multiple of 2^8, so (MB + V6) >> 8 = MB / 2^8 + floor(V6 / 2^8))
+        // and the constant sum of the MB terms taken off at the end
+        unsigned long long acc = u[6] >> 8;
+        acc = mad_wide(u[5], 1u, acc);
+        acc = mad_wide(u[4], 1u << 8, acc);
+        acc = mad_wide(u[3], 1u << 16, acc);
+        acc = mad_wide(u[2], 1u << 24, acc);
+        acc += (unsigned long long)(u[0] * 256u + u[1]) << 32;
+        const long long S = (long long)(acc - KMB);
         const unsigned long long sgn = (unsigned long long)(S >> 63);  // all ones when S < 0
         const unsigned long long m0 = ((unsigned long long)S ^ sgn) - sgn;
         const int lz = __clzll((long long)m0);
