@@ -237,7 +237,6 @@ template <bool CHECK, bool RANGE>
 __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int myf, int cbase, double* c0, int ld,
                                          int gi, int gj0, int ldf, int n, int rmax) {
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
-    constexpr unsigned long long SIGN = 1ull << 63;
 #pragma unroll
     for (int cc = 0; cc < CW; ++cc) {
         const int fj = __shfl_sync(0xffffffffu, myf, cbase + cc);  // every lane: before any skip
@@ -259,18 +258,30 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
         acc = mad_wide(u[3], 1u << 16, acc);
         acc = mad_wide(u[2], 1u << 24, acc);
         acc += (unsigned long long)(u[0] * 256u + u[1]) << 32;
-        const long long S = (long long)(acc - KMB);
-        const unsigned long long sgn = (unsigned long long)(S >> 63);  // all ones when S < 0
-        const unsigned long long m0 = ((unsigned long long)S ^ sgn) - sgn;
-        const int lz = __clzll((long long)m0);
-        const unsigned long long m = m0 << (lz & 63);  // the leading bit at 63
-        // 53 bits rounded to nearest; a carry into bit 53 raises the exponent by one
-        const unsigned long long mant = (m >> 11) + ((m >> 10) & 1ull);
+        // S = acc - KMB as two 32-bit words, then |S|, its leading-bit
+        // position and the top 53 bits, in 32-bit operations
+        unsigned lo = (unsigned)acc, hi = (unsigned)(acc >> 32);
+        asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %3;" : "+r"(lo), "+r"(hi) : "r"((unsigned)KMB), "r"((unsigned)(KMB >> 32)));
+        const unsigned sg = (unsigned)((int)hi >> 31);  // all ones when S < 0
+        lo ^= sg;
+        hi ^= sg;
+        asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %2;" : "+r"(lo), "+r"(hi) : "r"(sg));  // (hi:lo) = |S|
+        const bool big = hi != 0u;
+        const unsigned H = big ? hi : lo, L = big ? lo : 0u;  // |S| = (H:L) 2^(big ? 0 : -32)
+        const int sh = __clz(H);                              // < 32 unless S = 0
+        const int lz = big ? sh : sh + 32;
+        // (H:L) << sh: the leading bit at 63; mantissa = bits 63..11, rounded
+        // to nearest on bit 10 (a carry into bit 53 raises the exponent by one)
+        const unsigned nhi = __funnelshift_l(L, H, sh), nlo = L << (sh & 31);
+        unsigned mlo = __funnelshift_r(nlo, nhi, 11), mhi = nhi >> 11;
+        asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(mlo), "+r"(mhi) : "r"((nlo >> 10) & 1u));
         const int be = er + fj - lz;  // biased exponent of the leading bit
-        const unsigned long long sbit = ~sgn & SIGN;  // -S: negative when S > 0
-        unsigned long long bits = mant + ((unsigned long long)(be - 1) << 52) + sbit;
-        if (RANGE && (unsigned)(be - 1) >= 2045u) bits = be < 1 ? sbit : (sbit | 0x7FF0000000000000ull);
-        if (m0 != 0) atomicAdd(c0 + (long long)cc * ld, __longlong_as_double((long long)bits));
+        // -S: negative when S > 0
+        mhi += ((unsigned)(be - 1) << 20) + (~sg & 0x80000000u);
+        unsigned long long bits = ((unsigned long long)mhi << 32) | mlo;
+        if (RANGE && (unsigned)(be - 1) >= 2045u)
+            bits = (unsigned long long)(~sg & 0x80000000u) << 32 | (be < 1 ? 0ull : 0x7FF0000000000000ull);
+        if (H != 0u) atomicAdd(c0 + (long long)cc * ld, __longlong_as_double((long long)bits));
     }
 }
 
