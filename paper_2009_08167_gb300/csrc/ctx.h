@@ -134,6 +134,7 @@ struct riga_ctx {
     riga::DevBuf<riga::TcTile> oztiles;    //   its tiles
     riga::DevBuf<unsigned char> ozpack;    //   digit-slice blocks of one step
     riga::DevBuf<int> ozexp;               //   per block: the rows' power-of-two exponents (A, then B)
+    riga::DevBuf<int> ozlive;              //   per block: nonzero rows in A (bit 0), B rows 0-63 (1), 64-127 (2)
     int fp64_tc = 0;                       // FP64 fronts: 0 CUDA-core updates, 1 tensor-core digit slices
     riga::DevBuf<riga::ExtItem> eitems;
     // per-direction 1D data
@@ -171,7 +172,7 @@ struct riga_ctx {
     struct FactorGraph {
         cudaGraphExec_t exec = nullptr;
         long long gen = -1;
-        const void* ptrs[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        const void* ptrs[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         int launches = 0;
     } fgraph[2];
     long long sched_gen = 0;            // bumped whenever the factorization schedule is uploaded

@@ -320,10 +320,11 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
     }
     if (!per_problem || sizeof(T) != sizeof(double)) return enqueue_factor_body<T>(c, pool, Q, st);
     riga_ctx::FactorGraph& g = c->fgraph[c->inertia_only ? 1 : 0];
-    const void* ptrs[8] = {pool, Q, c->D.ptr, c->flag.ptr, c->neg.ptr, c->sig_pos.ptr,
-                           oz ? (const void*)c->ozpack.ptr : nullptr, oz ? (const void*)c->ozexp.ptr : nullptr};
+    const void* ptrs[9] = {pool, Q, c->D.ptr, c->flag.ptr, c->neg.ptr, c->sig_pos.ptr,
+                           oz ? (const void*)c->ozpack.ptr : nullptr, oz ? (const void*)c->ozexp.ptr : nullptr,
+                           oz ? (const void*)c->ozlive.ptr : nullptr};
     bool valid = g.exec && g.gen == c->sched_gen;
-    for (int i = 0; i < 8 && valid; ++i) valid = g.ptrs[i] == ptrs[i];
+    for (int i = 0; i < 9 && valid; ++i) valid = g.ptrs[i] == ptrs[i];
     if (!valid) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -344,7 +345,7 @@ static int enqueue_factor_t(riga_ctx* c, T* pool, T* Q) {
         c->prof.ph[PH_FACTOR].launches -= launches;
         if (rc) return rc;
         g.gen = c->sched_gen;
-        for (int i = 0; i < 8; ++i) g.ptrs[i] = ptrs[i];
+        for (int i = 0; i < 9; ++i) g.ptrs[i] = ptrs[i];
         g.launches = launches;
     }
     RIGA_CUDA_TRY(c, cudaGraphLaunch(g.exec, st));

@@ -113,7 +113,10 @@ __device__ __forceinline__ unsigned bf16_of_int(int d) {
 
 // An inertia-only factorization (plain) has no extra rows to update: its
 // tiles that start in them are skipped by all three roles alike
-__device__ __forceinline__ bool skip_tile(const TcTile& tl, const int* nn, int plain) {
+// Tiles whose A block or B half is all zero (live flags of the pack) are
+// skipped the same way.
+__device__ __forceinline__ bool skip_tile(const TcTile& tl, const int* nn, const int* live, int plain) {
+    if (!(live[tl.a_blk] & 1) || !(live[tl.b_blk] & (2 << tl.nk))) return true;
     if (!plain) return false;
     const int n = nn[tl.front];
     return tl.i0 >= n || tl.j0 >= n;
@@ -149,7 +152,8 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
                                                       const long long* __restrict__ front_off,
                                                       const int* __restrict__ node_ptr, const double* __restrict__ D,
                                                       const double* __restrict__ pool, unsigned char* __restrict__ pack,
-                                                      int* __restrict__ expo, int* __restrict__ err) {
+                                                      int* __restrict__ expo, int* __restrict__ live,
+                                                      int* __restrict__ err) {
     __shared__ int sexp[2][4][TC_BLK];
     const TcPack it = items[blockIdx.x];
     const int F = it.front, k = kk[F], ld = nn[F] + k;
@@ -184,6 +188,12 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
         expo[256 * it.blk + r] = e;
         expo[256 * it.blk + TC_BLK + r] = f;
     }
+    // rows of a front that the panel does not reach are zero: a tile whose A
+    // block or B half has no nonzero row is skipped by the update
+    const int anyA = __syncthreads_or(ea > NOEXP);
+    const int anyB0 = __syncthreads_or(eb > NOEXP && r < OZ_N);
+    const int anyB1 = __syncthreads_or(eb > NOEXP && r >= OZ_N);
+    if (threadIdx.x == 0) live[it.blk] = (anyA ? 1 : 0) | (anyB0 ? 2 : 0) | (anyB1 ? 4 : 0);
     bool bad = false;
     unsigned char* out = pack + (size_t)it.blk * BLK_BYTES + (size_t)((((r >> 3) * 4 + g) * 64 + (r & 7) * 8) * 2);
 #pragma unroll 1
@@ -288,7 +298,7 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
 __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
     const long long* __restrict__ front_off, const unsigned char* __restrict__ pack, const int* __restrict__ expo,
-    double* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
+    const int* __restrict__ live, double* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], tfull, tempty, drain;
     __shared__ unsigned s_tmem;
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             int it = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 const TcTile tl = tiles[t];
-                if (skip_tile(tl, nn, plain)) continue;
+                if (skip_tile(tl, nn, live, plain)) continue;
                 const int s = it % NSTAGE;
                 if (!mbar_wait(&empty[s], ((unsigned)(it / NSTAGE) & 1u) ^ 1u, &s_abort, err, spin_limit)) break;
                 const unsigned char* pa = pack + (size_t)tl.a_blk * BLK_BYTES;
@@ -351,7 +361,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
         if (lane == 0) {
             int it = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                if (skip_tile(tiles[t], nn, plain)) continue;
+                if (skip_tile(tiles[t], nn, live, plain)) continue;
                 if (!mbar_wait(&tempty, ((unsigned)it & 1u) ^ 1u, &s_abort, err, spin_limit)) break;
                 const int s = it % NSTAGE;
                 if (!mbar_wait(&full[s], (unsigned)(it / NSTAGE) & 1u, &s_abort, err, spin_limit)) break;
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             m.off = front_off[F];
             m.i0 = tl.i0;
             m.j0 = tl.j0;
-            m.skip = plain && (tl.i0 >= m.n || tl.j0 >= m.n);
+            m.skip = skip_tile(tl, nn, live, plain);
             // biased exponent of -S 2^(e_i + f_j - 54) is er + f_j - lz(S)
             m.er = expo[256 * tl.a_blk + q4 * 32 + lane] + (1023 - 54 + 63);
             m.myf = expo[256 * tl.b_blk + TC_BLK + tl.nk * OZ_N + grp * 16 + (lane & 15)];
@@ -442,6 +452,14 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
                     mbar_arrive(&tempty);
                     load_meta(tn, nxt);
                 }
+                // every level sum of the chunk zero (rows or columns the panel
+                // does not reach): nothing to add
+                unsigned nz = 0;
+#pragma unroll
+                for (int l = 0; l < NLEV; ++l)
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) nz |= __float_as_uint(v[l][c]) & 0x7FFFFFFFu;
+                if (!__any_sync(0xffffffffu, nz != 0u)) continue;
                 double* c0 = col + (long long)(ch * CW) * ld;
                 if (fast && normal) oz_chunk<false, false>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
                 else if (fast) oz_chunk<false, true>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
@@ -470,11 +488,12 @@ int enqueue_oz_step(riga_ctx* c, const StepRange& R, double* pool, int plain, cu
     const int grid = std::max(1, std::min(ntiles, nsm > 0 ? nsm : 148));
     count_launch(c);
     oz_pack_kernel<<<npack, 512, 0, st>>>(c->ozpacks.ptr + R.o_begin, c->kk.ptr, c->nn.ptr, c->front_off.ptr,
-                                          c->node_ptr.ptr, c->D.ptr, pool, c->ozpack.ptr, c->ozexp.ptr, c->flag.ptr);
+                                          c->node_ptr.ptr, c->D.ptr, pool, c->ozpack.ptr, c->ozexp.ptr, c->ozlive.ptr,
+                                          c->flag.ptr);
     count_launch(c);
     oz_update_kernel<<<grid, UPD_THREADS, oz_update_smem(), st>>>(c->oztiles.ptr + R.q_begin, ntiles, c->kk.ptr,
                                                                   c->nn.ptr, c->front_off.ptr, c->ozpack.ptr,
-                                                                  c->ozexp.ptr, pool, plain, c->flag.ptr,
+                                                                  c->ozexp.ptr, c->ozlive.ptr, pool, plain, c->flag.ptr,
                                                                   c->wait_limit);
     return RIGA_OK;
 }
@@ -487,6 +506,7 @@ int prepare_oz(riga_ctx* c) {
     if (c->ozpack.alloc((size_t)nblk * BLK_BYTES) != cudaSuccess)
         return set_error(c, RIGA_ENOMEM, "FP64 tensor-core digit slices");
     RIGA_CUDA_TRY(c, c->ozexp.alloc((size_t)256 * nblk));
+    RIGA_CUDA_TRY(c, c->ozlive.alloc((size_t)nblk));
     return RIGA_OK;
 }
 
