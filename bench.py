@@ -53,7 +53,7 @@ def parse():
                          "50 pairs; c4: batch of 512 2D rIGA problems with random coefficients, 20 pairs each")
     ap.add_argument("--block", type=int, default=2, choices=[0, 1, 2, 4],
                     help="Lanczos block size (riga_set_eig_block; 0 = automatic)")
-    ap.add_argument("--fp64-update", default="fma", choices=["fma", "tc"],
+    ap.add_argument("--fp64-update", default="tc", choices=["fma", "tc"],
                     help="Schur updates of FP64 fronts: FP64 FMA on the CUDA cores, or digit slices on the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")

@@ -357,8 +357,8 @@ int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
  * FP64 factorization on ctx (riga_factor with RIGA_FP64, the factorizations
  * and inertia checks inside riga_eigs, riga_eigs_interval and
  * riga_eigs_batch):
- *  mode = 0 (the default): CUDA cores, FP64 fused multiply-adds;
- *  mode = 1: tensor cores.  The panel operands L21 |D|^(1/2) and
+ *  mode = 0: CUDA cores, FP64 fused multiply-adds;
+ *  mode = 1 (the default): tensor cores.  The panel operands L21 |D|^(1/2) and
  *    L21 D |D|^(-1/2) (|D|^(1/2) rounded to powers of two per column: exact
  *    scalings that keep the row maxima of the two operands in the same
  *    columns next to near-zero pivots at shifts inside the spectrum) are

@@ -135,7 +135,7 @@ struct riga_ctx {
     riga::DevBuf<unsigned char> ozpack;    //   digit-slice blocks of one step
     riga::DevBuf<int> ozexp;               //   per block: the rows' power-of-two exponents (A, then B)
     riga::DevBuf<int> ozlive;              //   per block: nonzero rows in A (bit 0), B rows 0-63 (1), 64-127 (2)
-    int fp64_tc = 0;                       // FP64 fronts: 0 CUDA-core updates, 1 tensor-core digit slices
+    int fp64_tc = 1;                       // FP64 fronts: 0 CUDA-core updates, 1 tensor-core digit slices
     riga::DevBuf<riga::ExtItem> eitems;
     // per-direction 1D data
     riga::DevBuf<int> kv[3], elem_first[3];

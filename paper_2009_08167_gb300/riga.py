@@ -290,8 +290,8 @@ class Riga:
         return t.value, list(ms)
 
     def set_fp64_update(self, mode):
-        """Schur updates of FP64 fronts: 0 on the CUDA cores (FP64 FMA), 1 on
-        the tensor cores from exact 8-bit digit-slice products."""
+        """Schur updates of FP64 fronts: 0 on the CUDA cores (FP64 FMA), 1 (the
+        default) on the tensor cores from exact 8-bit digit-slice products."""
         self._check(self.lib.riga_set_fp64_update(self.ctx, int(mode)))
 
     def set_reorth(self, passes):

@@ -44,6 +44,16 @@ def test_fp64_tc_factor_parity(R, mesh):
     factor_parity(R, mesh)
 
 
+@pytest.mark.parametrize("mesh", CASES[1:4], ids=[repr(m) for m in CASES[1:4]])
+def test_fp64_fma_factor_parity(R, mesh):
+    """The CUDA-core FP64 update (riga_set_fp64_update(ctx, 0)) at the same bars."""
+    R.set_fp64_update(0)
+    try:
+        factor_parity(R, mesh)
+    finally:
+        R.set_fp64_update(1)
+
+
 def test_fp64_tc_large_fronts_against_fp64_fma(R):
     """Both FP64 update paths on fronts of up to 1820 variables, at sigma = 0
     (SPD: pivots within 1e-12 of each other) and sigma = 40 (indefinite,
