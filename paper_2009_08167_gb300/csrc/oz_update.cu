@@ -16,42 +16,45 @@
 //
 // Splitting.  Row i of the panel (32 entries), with e_i the smallest
 // integer such that every |x_ik| < 2^e_i, becomes the integer row
-// X_ik = round(x_ik 2^(55 - e_i)), |X_ik| < 2^55, written in balanced base
-// 256: X_ik = sum_{p=0..6} a_p,ik 256^(6-p), a_0 in [-128, 128], the other
+// X_ik = round(x_ik 2^(63 - e_i)), |X_ik| < 2^63, written in balanced base
+// 256: X_ik = sum_{p=0..7} a_p,ik 256^(7-p), a_0 in [-128, 128], the other
 // digits in [-128, 127].  Row j of the other operand likewise (exponent f_j,
 // digits b_q,jk).  Then
-//   (L21 D L21^T)_ij ~ 2^(e_i + f_j - 110) sum_{p,q} 256^(12-p-q) sum_k a_p,ik b_q,jk.
+//   (L21 D L21^T)_ij ~ 2^(e_i + f_j - 126) sum_{p,q} 256^(14-p-q) sum_k a_p,ik b_q,jk.
 // Every inner sum is an integer of magnitude at most 32 * 2^14: the BF16
 // digits are exact, so are their products, and so is their FP32
 // accumulation.  The pairs of one level l = p + q share one accumulator (at
-// most 7 pairs: |V_l| <= 7 * 2^19 < 2^22, still exact).  Levels l <= 6 (28
-// pairs) are kept.  The dropped levels (2^-53.4), the rounding of X (2^-55)
-// and the truncation of S below (2^-59) weigh together about 2^-53 of
-// 32 * 2^(e_i + f_j), the bound of the entry; an FP64 dot product of length
-// 32 carries up to 32 * 2^-53 of it.
+// most 8 pairs: |V_l| <= 8 * 2^19 = 2^22, still exact).  Levels l <= 7 (36
+// pairs) are kept.  The dropped levels, the rounding of X and the truncation
+// of S below weigh together about 2^-59 of 32 * 2^(e_i + f_j), the bound of
+// the entry (an FP64 dot product of length 32 carries up to 32 * 2^-53 of
+// it).  Eight levels of 64 columns fill the 512 tensor-memory columns; seven
+// (the first version) left 2^-56 and missed residual tolerances of 1e-12 at
+// shifts inside the spectrum that the FMA path meets.
 //
 // Recombination without FP64 arithmetic (GB300 issues FP64 at about 1/60 of
 // its FP32 rate): each level sum is read as an integer through one float add
-// (V + 1.5 * 2^23 holds V in its low mantissa bits), the seven combine in
-// 64-bit integers to S = floor(sum_l V_l 256^(6-l) / 2^8) (|S| < 2^60), and
-// the double -S 2^(e_i + f_j - 54), rounded to nearest (ties away from
-// zero), is assembled from S's leading-bit position and the two exponents
-// with integer operations, then added to the front by red.global.add.f64.
+// (V + 1.5 * 2^23 holds V in its low mantissa bits for |V| <= 2^22), the
+// eight combine in 64-bit integers to S = floor(sum_l V_l 256^(7-l) / 2^16)
+// (|S| < 2^60), and the double -S 2^(e_i + f_j - 54), rounded to nearest
+// (ties away from zero), is assembled from S's leading-bit position and the
+// two exponents with integer operations, then added to the front by
+// red.global.add.f64.
 //
 // Data path of one panel step:
 //   oz_pack_kernel    the trailing rows of each front in 128-row blocks: the
 //                     panel's 32 columns read once, the row exponents, the
-//                     7 digit slices of L21 and of L21 D written as BF16 in
+//                     8 digit slices of L21 and of L21 D written as BF16 in
 //                     the MMA's shared-memory layout (K-major 8-row core
 //                     matrices, no swizzle; 8 KiB per slice);
 //   oz_update_kernel  persistent, one CTA per SM, 576 threads:
-//     warp 16  producer: per 128 x 64 tile the A block's 7 slices and the 7
-//              slices of the B block's 64-row half (14 bulk copies, 84 KiB)
+//     warp 16  producer: per 128 x 64 tile the A block's 8 slices and the 8
+//              slices of the B block's 64-row half (16 bulk copies, 96 KiB)
 //              into one of two shared-memory stages;
-//     warp 17  MMA issuer: 56 tcgen05.mma (28 digit pairs x K = 32 in two
-//              K = 16 instructions) into 7 level accumulators of 128 x 64
-//              FP32 (448 tensor-memory columns);
-//     warps 0-15 epilogue: tcgen05.ld of the 7 levels, 8 columns at a time
+//     warp 17  MMA issuer: 72 tcgen05.mma (36 digit pairs x K = 32 in two
+//              K = 16 instructions) into 8 level accumulators of 128 x 64
+//              FP32 (all 512 tensor-memory columns);
+//     warps 0-15 epilogue: tcgen05.ld of the 8 levels, 8 columns at a time
 //              (warp w: lane quarter w % 4, columns 16 (w / 4) .. + 15),
 //              the integer recombination and the FP64 reductions (lower
 //              triangle, and the whole extra x extra block of the augmented
@@ -69,22 +72,22 @@ namespace {
 using namespace tcx;
 
 constexpr int KP = 32;                                  // panel width
-constexpr int NDIG = 7;                                 // digit slices per operand
+constexpr int NDIG = 8;                                 // digit slices per operand
 constexpr unsigned SLICE_BYTES = TC_BLK * KP * 2;       // one slice of a 128-row block (8 KiB of BF16)
-constexpr unsigned BLK_BYTES = 2 * NDIG * SLICE_BYTES;  // A slices, then B slices (112 KiB)
+constexpr unsigned BLK_BYTES = 2 * NDIG * SLICE_BYTES;  // A slices, then B slices (128 KiB)
 constexpr unsigned B_BYTES = OZ_N * KP * 2;             // B slice of a tile: 64 rows (4 KiB)
-constexpr unsigned STAGE_BYTES = NDIG * (SLICE_BYTES + B_BYTES);  // 84 KiB
+constexpr unsigned STAGE_BYTES = NDIG * (SLICE_BYTES + B_BYTES);  // 96 KiB
 constexpr int NSTAGE = 2;
 constexpr int EPI_WARPS = 16;                           // epilogue warps 0..15; producer 16, MMA issuer 17
 constexpr int CW = 8;                                   // accumulator columns per tensor-memory load
 constexpr int UPD_THREADS = 32 * (EPI_WARPS + 2);
-constexpr int NLEV = 7;                                 // levels l = p + q = 0..6
-constexpr int TMEM_COLS = 512;                          // NLEV * OZ_N = 448, allocated as a power of two
+constexpr int NLEV = 8;                                 // levels l = p + q = 0..7
+constexpr int TMEM_COLS = 512;                          // NLEV * OZ_N
 constexpr unsigned IDESC = make_idesc(1, OZ_M, OZ_N);   // BF16 x BF16 -> FP32, 128 x 64
 
 static_assert(NLEV * OZ_N <= TMEM_COLS, "level accumulators exceed the tensor memory");
 
-// Integer X = round(x 2^(s + 55 - e)) for |x 2^s| < 2^e, from the bits of x
+// Integer X = round(x 2^(s + 63 - e)) for |x 2^s| < 2^e, from the bits of x
 // (no FP64 arithmetic): x = m 2^(E - 1075), m = 2^52 + mantissa.  Zero and
 // subnormal x give 0 (an error below 2^-1022); *bad is set for a non-finite x.
 __device__ __forceinline__ long long to_fixed(double x, int s, int e, bool* bad) {
@@ -96,7 +99,7 @@ __device__ __forceinline__ long long to_fixed(double x, int s, int e, bool* bad)
         return 0;
     }
     const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = E + s - 1075 + 55 - e;  // X = m 2^sh, sh <= 2
+    const int sh = E + s - 1075 + 63 - e;  // X = m 2^sh, sh <= 10 (X < 2^63)
     long long X;
     if (sh >= 0) X = (long long)(m << sh);
     else if (sh < -54) X = 0;
@@ -224,10 +227,11 @@ __global__ void __launch_bounds__(512) oz_pack_kernel(const TcPack* __restrict__
 }
 
 constexpr unsigned MB = 0x4B400000u;  // float bits of 1.5 * 2^23: MB + V are the bits of V + 1.5 * 2^23
-// sum of the MB terms of S (mod 2^64): MB (2^40 + 2^32 + 2^24 + 2^16 + 2^8 + 1) + MB / 2^8
+// sum of the MB terms of S (mod 2^64): MB (2^40 + 2^32 + 2^24 + 2^16 + 2^8 + 1)
+// + (MB 257 mod 2^32) / 2^16 (MB 257 mod 2^32 = 0x8B400000 is a multiple of 2^16)
 constexpr unsigned long long KMB =
     ((unsigned long long)MB << 40) + ((unsigned long long)MB << 32) + ((unsigned long long)MB << 24) +
-    ((unsigned long long)MB << 16) + ((unsigned long long)MB << 8) + MB + (MB >> 8);
+    ((unsigned long long)MB << 16) + ((unsigned long long)MB << 8) + MB + ((MB * 257u) >> 16);
 
 // a * b + c with a 32 x 32 -> 64-bit product (one IMAD.WIDE.U32)
 __device__ __forceinline__ unsigned long long mad_wide(unsigned a, unsigned b, unsigned long long c) {
@@ -257,12 +261,13 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
         unsigned u[NLEV];
 #pragma unroll
         for (int l = 0; l < NLEV; ++l) u[l] = __float_as_uint(v[l][cc] + MAGIC);
-        // S = floor((V0 2^48 + V1 2^40 + ... + V6) / 2^8)
-        //   = sum_{l<6} V_l 2^(40-8l) + floor(V6 / 2^8),
+        // S = floor((V0 2^56 + V1 2^48 + ... + V7) / 2^16)
+        //   = sum_{l<6} V_l 2^(40-8l) + floor((V6 2^8 + V7) / 2^16),
         // accumulated from u_l = MB + V_l by 64-bit multiply-adds (mod 2^64;
-        // MB is a multiple of 2^8, so (MB + V6) >> 8 = MB / 2^8 + floor(V6 / 2^8))
-        // and the constant sum of the MB terms taken off at the end
-        unsigned long long acc = u[6] >> 8;
+        // u6 2^8 + u7 = MB 257 + V6 2^8 + V7 without wrap-around in 32 bits,
+        // and MB 257 mod 2^32 is a multiple of 2^16) and the constant sum of
+        // the MB terms taken off at the end
+        unsigned long long acc = (u[6] * 256u + u[7]) >> 16;
         acc = mad_wide(u[5], 1u, acc);
         acc = mad_wide(u[4], 1u << 8, acc);
         acc = mad_wide(u[3], 1u << 16, acc);
@@ -295,7 +300,7 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
     }
 }
 
-__global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
+__global__ void __maxnreg__(112) oz_update_kernel(
     const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
     const long long* __restrict__ front_off, const unsigned char* __restrict__ pack, const int* __restrict__ expo,
     const int* __restrict__ live, double* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
