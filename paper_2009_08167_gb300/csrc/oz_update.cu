@@ -54,7 +54,7 @@
 //     warp 17  MMA issuer: 72 tcgen05.mma (36 digit pairs x K = 32 in two
 //              K = 16 instructions) into 8 level accumulators of 128 x 64
 //              FP32 (all 512 tensor-memory columns);
-//     warps 0-15 epilogue: tcgen05.ld of the 8 levels, 8 columns at a time
+//     warps 0-15 epilogue: tcgen05.ld of the 8 levels, 4 columns at a time
 //              (warp w: lane quarter w % 4, columns 16 (w / 4) .. + 15),
 //              the integer recombination and the FP64 reductions (lower
 //              triangle, and the whole extra x extra block of the augmented
@@ -79,7 +79,10 @@ constexpr unsigned B_BYTES = OZ_N * KP * 2;             // B slice of a tile: 64
 constexpr unsigned STAGE_BYTES = NDIG * (SLICE_BYTES + B_BYTES);  // 96 KiB
 constexpr int NSTAGE = 2;
 constexpr int EPI_WARPS = 16;                           // epilogue warps 0..15; producer 16, MMA issuer 17
-constexpr int CW = 8;                                   // accumulator columns per tensor-memory load
+// accumulator columns per tensor-memory load: 8 levels x 4 columns in
+// registers (18 warps of 96 registers: five warps share one SM sub-partition's
+// 16K registers)
+constexpr int CW = 4;
 constexpr int UPD_THREADS = 32 * (EPI_WARPS + 2);
 constexpr int NLEV = 8;                                 // levels l = p + q = 0..7
 constexpr int TMEM_COLS = 512;                          // NLEV * OZ_N
@@ -300,7 +303,7 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
     }
 }
 
-__global__ void __maxnreg__(112) oz_update_kernel(
+__global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     const TcTile* __restrict__ tiles, int ntiles, const int* __restrict__ kk, const int* __restrict__ nn,
     const long long* __restrict__ front_off, const unsigned char* __restrict__ pack, const int* __restrict__ expo,
     const int* __restrict__ live, double* __restrict__ pool, int plain, int* __restrict__ err, long long spin_limit) {
@@ -396,7 +399,7 @@ __global__ void __maxnreg__(112) oz_update_kernel(
     } else {
         // ------------------------------------------ epilogue (warps 0..15)
         // warp w: tile rows 32 (w % 4) .. + 31 (its tensor-memory lane
-        // quarter), columns 16 (w / 4) .. + 15 in two loads of 8.  The next
+        // quarter), columns 16 (w / 4) .. + 15 in four loads of 4.  The next
         // tile's front data and exponents are loaded while the second half
         // of the current one is computed.
         const int q4 = warp & 3, grp = warp >> 2;
@@ -446,12 +449,12 @@ __global__ void __maxnreg__(112) oz_update_kernel(
             double* col = pool + cur.off + gi + (long long)gj0 * ld;
             const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(grp * 16);
 #pragma unroll 1
-            for (int ch = 0; ch < 2; ++ch) {
+            for (int ch = 0; ch < 16 / CW; ++ch) {
                 float v[NLEV][CW];
 #pragma unroll
-                for (int l = 0; l < NLEV; ++l) tmem_ld8(taddr + l * OZ_N + ch * CW, v[l]);
+                for (int l = 0; l < NLEV; ++l) tmem_ld4(taddr + l * OZ_N + ch * CW, v[l]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (ch == 1) {
+                if (ch == 16 / CW - 1) {
                     // the accumulators may be overwritten by the next tile's MMAs
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(&tempty);

@@ -98,6 +98,15 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v) {
         : "memory");
 }
 
+// 4 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld4(unsigned taddr, float* v) {
+    unsigned* r = reinterpret_cast<unsigned*>(v);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 // 8 consecutive accumulator columns of this warp's 32 lanes
 __device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
     unsigned* r = reinterpret_cast<unsigned*>(v);
