@@ -551,6 +551,19 @@ int calibrate_fp64_solve(riga_ctx* c, uint64_t seed) {
     return RIGA_OK;
 }
 
+// A run that locked nothing with FP64 fronts: its converged candidates (if
+// any) missed the true-residual bar, which the accuracy of the plain solves
+// limits (the Ritz residual cannot fall much below the solve's backward
+// error times ||K|| / lambda).  Later runs on this factorization refine each
+// solve once in FP64 (residual b - (K - sigma M) x and a correction solve),
+// which takes the solve error to the FP64 residual's rounding level.  A new
+// factorization starts again from plain solves.
+static void refine_after_fruitless(riga_ctx* c, bool dbg) {
+    if (c->precision != RIGA_FP64 || c->fp64_sweeps >= 2) return;
+    c->fp64_sweeps = 2;
+    if (dbg) std::fprintf(stderr, "[riga] fruitless run: FP64 solves refined once from now on\n");
+}
+
 int configure_reorth(riga_ctx* c, int cap) {
     const size_t sm_dots = (size_t)(CH + 8 * TJ + TJ * (HR + 1)) * sizeof(double);
     const size_t sm_upd = sm_dots + (size_t)cap * sizeof(double);
@@ -827,6 +840,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             nlock += acc_n;
             if (acc_n > 0) fruitless = 0;
             else ++fruitless;
+            if (acc_n == 0) refine_after_fruitless(c, dbg);
             if (dbg)
                 std::fprintf(stderr, "[riga] run %d: shift=%.12g want=%d block=%d steps=%d/%d locked=%d total=%d\n", runs,
                              cur_sigma, want_run, B, mb, m_max, acc_n, nlock);
@@ -934,6 +948,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             nlock += acc_n;
             if (acc_n > 0) fruitless = 0;
             else ++fruitless;
+            if (acc_n == 0) refine_after_fruitless(c, dbg);
         } else {
             ++fruitless;
         }
