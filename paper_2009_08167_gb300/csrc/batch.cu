@@ -668,6 +668,10 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
     uint64_t seed = c->opt_seed ? c->opt_seed : 1;
     std::vector<double> h_alpha, h_beta;
     int status = RIGA_OK;
+    // FP64 fronts: plain solves until a converged candidate misses the
+    // true-residual bar (the plain solve's accuracy limits the Ritz
+    // residual); from then on each solve is refined once in FP64
+    bool refine64 = false;
     for (int run = 1; run <= 4; ++run) {
         int active = 0;
         for (int b = 0; b < P; ++b) active += !done[b];
@@ -708,8 +712,8 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
             const int col = col0 + j;
             RIGA_CUDA_TRY(c, cudaMemcpyAsync(w, c->MV.ptr + (long long)col * B.ld, N * sizeof(double),
                                              cudaMemcpyDeviceToDevice, st));
-            rc = c->precision == RIGA_FP64 ? enqueue_solve(c, w)
-                                           : solve_refined(c, w, xw, rwk, 0.0, c->ir_sweeps, 0, nullptr);
+            rc = (c->precision == RIGA_FP64 && !refine64) ? enqueue_solve(c, w)
+                                                           : solve_refined(c, w, xw, rwk, 0.0, c->ir_sweeps, 0, nullptr);
             if (rc) {
                 status = rc;
                 break;
@@ -816,6 +820,7 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), B.rpart.ptr, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
         std::vector<int> dcol((size_t)P * qmax, -1);
+        bool rejected = false;
         for (int b = 0; b < P; ++b) {
             for (int q = 0; q < nsel[b]; ++q) {
                 double ra = 0.0, rb = 0.0;
@@ -825,12 +830,23 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
                 }
                 const double l = hl[(size_t)b * qmax + q];
                 const double rho = std::sqrt(ra) / (std::fabs(l) * std::sqrt(rb));
-                if (!(rho <= lock_tol)) continue;
+                if (!(rho <= lock_tol)) {
+                    rejected = true;
+                    continue;
+                }
                 dcol[(size_t)b * qmax + q] = nlock[b];
                 lam[b].push_back(l);
                 res[b].push_back(rho);
                 ++nlock[b];
             }
+        }
+        if (rejected && c->precision == RIGA_FP64 && !refine64) {
+            for (int i = 2; i < 4; ++i) RIGA_CUDA_TRY(c, c->vwork[i].alloc(N));
+            xw = c->vwork[2].ptr;
+            rwk = c->vwork[3].ptr;
+            c->fp64_sweeps = 2;
+            refine64 = true;
+            if (dbg) std::fprintf(stderr, "[riga] batch: a candidate missed the residual bar; FP64 solves refined once\n");
         }
         RIGA_CUDA_TRY(c, B.dcol.upload(dcol, st));
         { count_launch(c); bscatter_cols_kernel<<<(unsigned)((N * qmax + 255) / 256), 256, 0, st>>>(
