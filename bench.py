@@ -332,7 +332,18 @@ FP32_PEAK_TFLOPS = 73.1
 TF32_PEAK_TFLOPS = 1212.0
 
 
-def fronts_rate(prof, flops_plain, n_fact, peak):
+def fp64_front_peak(fp64_update):
+    """Ceiling of FP64 fronts' updates: the measured FP64 FMA rate on the CUDA
+    cores, or, with the digit-slice tensor-core update, the measured BF16
+    tensor rate over the 36 BF16 products one FP64 multiply-add costs there
+    (8 x 8 digit pairs down to level 7), as (TFLOP/s, source)."""
+    if fp64_update == "tc":
+        pk, kind = peaks()
+        return pk["bf16_tflops"] / 36.0, kind + " bf16 tensor rate / 36 (digit-slice emulation of FP64)"
+    return FP64_PEAK_TFLOPS, FP64_PEAK_SOURCE
+
+
+def fronts_rate(prof, flops_plain, n_fact, peak, peak_source="measured probe"):
     """Front TFLOP/s of one profiled step: the plain multifrontal flops per
     factorization (lower triangle, FMA = 2, no padding and no augmentation)
     times the factorizations, over the factor phase's device time; also with
@@ -344,7 +355,7 @@ def fronts_rate(prof, flops_plain, n_fact, peak):
     plain = flops_plain * n_fact / t / 1e12
     return {"tflops": plain, "peak": peak, "frac": plain / peak, "unit": "TFLOP/s",
             "tflops_incl_augmentation": pr["flops"] / t / 1e12, "factorizations": n_fact,
-            "factor_ms": pr["ms"], "peak_source": "measured probe"}
+            "factor_ms": pr["ms"], "peak_source": peak_source}
 
 
 # ------------------------------------------------------------------ riga leg
@@ -433,7 +444,7 @@ def run_riga_batch(args, rank, world, local_rank, cfg):
     prof = R.profile_get()
     R.profile(False)
     roof = roofline(prof, q)
-    fronts = fronts_rate(prof, q["flops_fact"], R.stats()["n_fact"], FP64_PEAK_TFLOPS)
+    fronts = fronts_rate(prof, q["flops_fact"], R.stats()["n_fact"], *fp64_front_peak(args.fp64_update))
     phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
     # the mixed path on the same batch: low-precision fronts, FP64 refinement
     mixed = None
@@ -593,7 +604,7 @@ def run_riga(args, rank, world, local_rank):
     prof = R.profile_get()
     R.profile(False)
     roof = roofline(prof, q)
-    fronts = fronts_rate(prof, q["flops_fact"], R.stats()["n_fact"], FP64_PEAK_TFLOPS)
+    fronts = fronts_rate(prof, q["flops_fact"], R.stats()["n_fact"], *fp64_front_peak(args.fp64_update))
     phases = {p: {"ms": round(v["ms"], 3), "calls": v["calls"], "launches": v["launches"]} for p, v in prof.items() if v["calls"]}
 
     # the mixed path (FP32 fronts, FP64 refinement, residuals, Lanczos and
