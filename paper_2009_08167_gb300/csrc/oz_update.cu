@@ -243,43 +243,52 @@ __device__ __forceinline__ unsigned long long mad_wide(unsigned a, unsigned b, u
     return d;
 }
 
-// CW columns of one tile row (this lane): the level sums v[l][cc] (exact
-// integers) of column cc recombined and -S 2^(e_i + f_j - 54) added to the
-// front entry c0[cc * ld] (no FP64 arithmetic: the double is assembled from
-// S's magnitude, leading-bit position and the exponents).  Results below the
-// normal range are flushed to zero (an error below 2^-1022).  CHECK: skip
-// entries outside the front, the lower triangle and the extra x extra block.
-// RANGE: results may fall outside the normal range (else known not to).
-template <bool CHECK, bool RANGE>
-__device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int myf, int cbase, double* c0, int ld,
-                                         int gi, int gj0, int ldf, int n, int rmax) {
+// Phase 1, CW columns of one tile row (this lane): the level sums v[l][cc]
+// (exact integers) of column cc combined into the signed 64-bit
+//   S = floor((V0 2^56 + V1 2^48 + ... + V7) / 2^16)
+//     = sum_{l<6} V_l 2^(40-8l) + floor((V6 2^8 + V7) / 2^16),
+// (|S| < 2^60), stored as two 32-bit words.  Accumulated from u_l = MB + V_l
+// by 64-bit multiply-adds (mod 2^64; u6 2^8 + u7 = MB 257 + V6 2^8 + V7
+// without wrap-around in 32 bits, and MB 257 mod 2^32 is a multiple of 2^16)
+// and the constant sum of the MB terms taken off at the end.
+__device__ __forceinline__ void oz_sum(const float (&v)[NLEV][CW], unsigned* slo, unsigned* shi) {
     constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
 #pragma unroll
     for (int cc = 0; cc < CW; ++cc) {
-        const int fj = __shfl_sync(0xffffffffu, myf, cbase + cc);  // every lane: before any skip
-        if (CHECK) {
-            const int gj = gj0 + cc;
-            if (gi >= rmax || gj >= ldf || !(gi >= gj || (gi >= n && gj >= n))) continue;
-        }
         unsigned u[NLEV];
 #pragma unroll
         for (int l = 0; l < NLEV; ++l) u[l] = __float_as_uint(v[l][cc] + MAGIC);
-        // S = floor((V0 2^56 + V1 2^48 + ... + V7) / 2^16)
-        //   = sum_{l<6} V_l 2^(40-8l) + floor((V6 2^8 + V7) / 2^16),
-        // accumulated from u_l = MB + V_l by 64-bit multiply-adds (mod 2^64;
-        // u6 2^8 + u7 = MB 257 + V6 2^8 + V7 without wrap-around in 32 bits,
-        // and MB 257 mod 2^32 is a multiple of 2^16) and the constant sum of
-        // the MB terms taken off at the end
         unsigned long long acc = (u[6] * 256u + u[7]) >> 16;
         acc = mad_wide(u[5], 1u, acc);
         acc = mad_wide(u[4], 1u << 8, acc);
         acc = mad_wide(u[3], 1u << 16, acc);
         acc = mad_wide(u[2], 1u << 24, acc);
         acc += (unsigned long long)(u[0] * 256u + u[1]) << 32;
-        // S = acc - KMB as two 32-bit words, then |S|, its leading-bit
-        // position and the top 53 bits, in 32-bit operations
         unsigned lo = (unsigned)acc, hi = (unsigned)(acc >> 32);
         asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %3;" : "+r"(lo), "+r"(hi) : "r"((unsigned)KMB), "r"((unsigned)(KMB >> 32)));
+        slo[cc] = lo;
+        shi[cc] = hi;
+    }
+}
+
+// Phase 2, the warp's 16 columns of one tile row (this lane): the double
+// -S 2^(e_i + f_j - 54) added to the front entry col[cc * ld], assembled
+// without FP64 arithmetic from |S|, its leading-bit position and the
+// exponents.  Results below the normal range are flushed to zero (an error
+// below 2^-1022).  CHECK: skip entries outside the front, the lower triangle
+// and the extra x extra block.  RANGE: results may fall outside the normal
+// range (else known not to).
+template <bool CHECK, bool RANGE>
+__device__ __forceinline__ void oz_emit(const unsigned (&slo)[16], const unsigned (&shi)[16], int er, int myf,
+                                        double* col, int ld, int gi, int gj0, int n, int rmax) {
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) {
+        const int fj = __shfl_sync(0xffffffffu, myf, cc);  // every lane: before any skip
+        if (CHECK) {
+            const int gj = gj0 + cc;
+            if (gi >= rmax || gj >= ld || !(gi >= gj || (gi >= n && gj >= n))) continue;
+        }
+        unsigned lo = slo[cc], hi = shi[cc];
         const unsigned sg = (unsigned)((int)hi >> 31);  // all ones when S < 0
         lo ^= sg;
         hi ^= sg;
@@ -299,7 +308,7 @@ __device__ __forceinline__ void oz_chunk(const float (&v)[NLEV][CW], int er, int
         unsigned long long bits = ((unsigned long long)mhi << 32) | mlo;
         if (RANGE && (unsigned)(be - 1) >= 2045u)
             bits = (unsigned long long)(~sg & 0x80000000u) << 32 | (be < 1 ? 0ull : 0x7FF0000000000000ull);
-        if (H != 0u) atomicAdd(c0 + (long long)cc * ld, __longlong_as_double((long long)bits));
+        if (H != 0u) atomicAdd(col + (long long)cc * ld, __longlong_as_double((long long)bits));
     }
 }
 
@@ -399,9 +408,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
     } else {
         // ------------------------------------------ epilogue (warps 0..15)
         // warp w: tile rows 32 (w % 4) .. + 31 (its tensor-memory lane
-        // quarter), columns 16 (w / 4) .. + 15 in four loads of 4.  The next
-        // tile's front data and exponents are loaded while the second half
-        // of the current one is computed.
+        // quarter), columns 16 (w / 4) .. + 15.  The next tile's front data
+        // and exponents are loaded while the current one's doubles are
+        // assembled.
         const int q4 = warp & 3, grp = warp >> 2;
         struct Meta {
             int skip, n, ld, i0, j0, er, myf;
@@ -448,30 +457,30 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) oz_update_kernel(
             const bool normal = __all_sync(0xffffffffu, cur.er + fmin - 63 >= 1 && cur.er + fmax - 4 <= 2045);
             double* col = pool + cur.off + gi + (long long)gj0 * ld;
             const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(grp * 16);
-#pragma unroll 1
+            // phase 1: the 16 columns' S from four loads of 4 columns x 8
+            // levels; the accumulators are released right after, so the next
+            // tile's MMAs run while phase 2 assembles and adds the doubles
+            unsigned slo[16], shi[16];
+#pragma unroll
             for (int ch = 0; ch < 16 / CW; ++ch) {
                 float v[NLEV][CW];
 #pragma unroll
                 for (int l = 0; l < NLEV; ++l) tmem_ld4(taddr + l * OZ_N + ch * CW, v[l]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (ch == 16 / CW - 1) {
-                    // the accumulators may be overwritten by the next tile's MMAs
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    mbar_arrive(&tempty);
-                    load_meta(tn, nxt);
-                }
-                // every level sum of the chunk zero (rows or columns the panel
-                // does not reach): nothing to add
-                unsigned nz = 0;
+                oz_sum(v, slo + ch * CW, shi + ch * CW);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty);
+            load_meta(tn, nxt);
+            // every S of the warp zero (rows or columns the panel does not
+            // reach): nothing to add
+            unsigned nz = 0;
 #pragma unroll
-                for (int l = 0; l < NLEV; ++l)
-#pragma unroll
-                    for (int c = 0; c < CW; ++c) nz |= __float_as_uint(v[l][c]) & 0x7FFFFFFFu;
-                if (!__any_sync(0xffffffffu, nz != 0u)) continue;
-                double* c0 = col + (long long)(ch * CW) * ld;
-                if (fast && normal) oz_chunk<false, false>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
-                else if (fast) oz_chunk<false, true>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
-                else oz_chunk<true, true>(v, cur.er, cur.myf, ch * CW, c0, ld, gi, gj0 + ch * CW, ld, n, rmax);
+            for (int c = 0; c < 16; ++c) nz |= slo[c] | shi[c];
+            if (__any_sync(0xffffffffu, nz != 0u)) {
+                if (fast && normal) oz_emit<false, false>(slo, shi, cur.er, cur.myf, col, ld, gi, gj0, n, rmax);
+                else if (fast) oz_emit<false, true>(slo, shi, cur.er, cur.myf, col, ld, gi, gj0, n, rmax);
+                else oz_emit<true, true>(slo, shi, cur.er, cur.myf, col, ld, gi, gj0, n, rmax);
             }
             t = tn;
             cur = nxt;
