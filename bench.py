@@ -683,9 +683,12 @@ def run_riga(args, rank, world, local_rank):
 
 def run_c3_leg(args, local_rank, flush):
     """The 3D workload (64^3 elements, p=2, C0 planes every 8 elements,
-    N = 357,911, 50 pairs, Lanczos blocks of 2) on its own context: the FP64
-    path and the mixed path (FP32 fronts with TF32 tensor-core Schur
-    updates, FP64 refinement, residuals, Lanczos and inertia), each with one
+    N = 357,911, 50 pairs, Lanczos blocks of 2) on its own context, three
+    ways: FP64 fronts with the Schur updates as exact BF16 digit-slice
+    products on the tensor cores ("fp64", the default update), FP64 fronts
+    with FP64 FMA updates on the CUDA cores ("fp64_fma", the plain FP64
+    path), and FP32 fronts with TF32 tensor-core updates plus FP64
+    refinement, residuals, Lanczos and inertia ("mixed").  Each with one
     untimed warm-up step and args.c3_steps timed steps (CUDA events, L2
     flushed before each step), the same metric as the headline."""
     import numpy as np
@@ -704,7 +707,8 @@ def run_c3_leg(args, local_rank, flush):
     out = {"workload": "laplace3d_p2_64x64x64_riga_bs8_k50", "N": q["N"], "nnz": q["nnz"], "nnzL": q["nnzL"],
            "flops_fact": q["flops_fact"], "pairs": cfg["k"], "lanczos_block": 2, "setup_s": setup_s,
            "l2": "flushed between timed steps (512 MiB write)"}
-    for name, prec in (("fp64", riga.RIGA_FP64), ("mixed", riga.RIGA_TF32)):
+    for name, prec, upd in (("fp64", riga.RIGA_FP64, 1), ("fp64_fma", riga.RIGA_FP64, 0), ("mixed", riga.RIGA_TF32, 1)):
+        R.set_fp64_update(upd)
         R.set_eig_options(slice=cfg["k"], precision=prec, extra=2, seed=11)
         R.eigs(cfg["k"], 0.0, RESID_TOL, vectors=True, device_out=True)
         times, rs = [], None
@@ -723,9 +727,13 @@ def run_c3_leg(args, local_rank, flush):
         out[name] = {"value": ok / (statistics.mean(times) / 1e3), "unit": "eigenpairs/s",
                      "ms_per_step": statistics.mean(times), "steps": len(times), "converged_pairs": ok,
                      "max_resid": float(np.max(rs_h)), "n_fact": st["n_fact"], "lanczos_steps": st["lanczos_steps"],
-                     "dtype": "f64" if prec == riga.RIGA_FP64 else
+                     "dtype": ("f64 fronts, updates as exact bf16 digit-slice products on the tensor cores"
+                               if upd else "f64 fronts, f64 fma updates") if prec == riga.RIGA_FP64 else
                               "f32 fronts with tf32 tensor-core updates, f64 refinement/Lanczos/inertia"}
+    R.set_fp64_update(1 if args.fp64_update == "tc" else 0)
     out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["fp64_over_fp64_fma"] = out["fp64"]["value"] / out["fp64_fma"]["value"]
+    out["mixed_over_fp64_fma"] = out["mixed"]["value"] / out["fp64_fma"]["value"]
     R.close()
     return out
 
