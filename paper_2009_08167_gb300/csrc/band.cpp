@@ -120,6 +120,14 @@ void band_solve(const BandLU& F, double* x) {
 
 }  // namespace
 
+// sqrt(x^2 + y^2) without overflow: one square root when the larger
+// magnitude lies in [2^-500, 2^500], else std::hypot
+static inline double norm2(double x, double y) {
+    const double big = std::fmax(std::fabs(x), std::fabs(y));
+    if (big >= 0x1p-500 && big <= 0x1p500) return std::sqrt(x * x + y * y);
+    return std::hypot(x, y);
+}
+
 // Band -> tridiagonal reduction; the rotations are also applied (as Q <- Q G^T)
 // to the r x n row block qr (column-major), which starts as the last r rows of
 // the identity, so that it ends as the last r rows of Q (T = Q T_tri Q^T).
@@ -145,7 +153,7 @@ static void band_reduce(int n, int b, const double* T, std::vector<double>& d, s
         for (int i = std::min(j + b, n - 1); i >= j + 2; --i) {
             const double x = at(i - 1, j), y = at(i, j);
             if (y == 0.0) continue;
-            const double rr = std::hypot(x, y);
+            const double rr = norm2(x, y);
             const double c1 = x / rr, s1 = y / rr;
             rotate_sym(A, b, i - 1, i, c1, s1);
             if (r > 0) track(i - 1, i, c1, s1);
@@ -155,7 +163,7 @@ static void band_reduce(int n, int b, const double* T, std::vector<double>& d, s
                 const int p = k + b - 1, q = k + b, col = k - 1;
                 const double x2 = at(p, col), y2 = at(q, col);
                 if (y2 == 0.0) break;
-                const double r2 = std::hypot(x2, y2);
+                const double r2 = norm2(x2, y2);
                 const double c2 = x2 / r2, s2 = y2 / r2;
                 rotate_sym(A, b, p, q, c2, s2);
                 if (r > 0) track(p, q, c2, s2);

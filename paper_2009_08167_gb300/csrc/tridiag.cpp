@@ -35,8 +35,11 @@ namespace riga {
 namespace {
 
 // c, s with c x + s y = r >= 0 and -s x + c y = 0 (a plane rotation that
-// takes (x, y) to (r, 0)); scaled by the larger magnitude so that neither
-// square leaves the double range
+// takes (x, y) to (r, 0)).  When the larger magnitude lies in
+// [2^-500, 2^500] the squares cannot overflow and the larger one stays
+// normal: one square root and one division; otherwise both are scaled by
+// the larger magnitude first.  (The rotations of the bulge chase form a
+// dependent chain, so their latency is the iteration's cost.)
 inline void plane_rotation(double x, double y, double& c, double& s, double& r) {
     const double ax = std::fabs(x), ay = std::fabs(y);
     if (ay == 0.0) {
@@ -52,6 +55,13 @@ inline void plane_rotation(double x, double y, double& c, double& s, double& r) 
         return;
     }
     const double big = ax > ay ? ax : ay;
+    if (big >= 0x1p-500 && big <= 0x1p500) {
+        r = std::sqrt(x * x + y * y);
+        const double inv = 1.0 / r;
+        c = x * inv;
+        s = y * inv;
+        return;
+    }
     const double xs = x / big, ys = y / big;
     const double h = std::sqrt(xs * xs + ys * ys);
     r = big * h;
