@@ -803,9 +803,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     RIGA_CUDA_TRY(c, cudaMemsetAsync(K.flag, 0, 2 * sizeof(int), st));  // breakdown flag, reduction counter
 
     // start block: B random vectors, M-orthogonal to the locked ones
-    std::vector<double> hv((size_t)N * B);
-    for (size_t i = 0; i < hv.size(); ++i) hv[i] = ((double)(splitmix(seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
-    RIGA_CUDA_TRY(c, cudaMemcpyAsync(K.W, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    enqueue_start_vector(c, (long long)N * B, seed, K.W);
     int rc = bortho(K, nlock);
     if (rc) return rc;
     rc = bnormalize(K, col0, dB, false);

@@ -414,6 +414,27 @@ uint64_t splitmix(uint64_t& s) {
     return z ^ (z >> 31);
 }
 
+// w[i] = u(splitmix draw i + 1 after seed0) - 1/2 with u in (0, 1): SplitMix64
+// is a counter-based generator (draw i mixes seed0 + (i + 1) * gamma), so the
+// device produces the host sequence of splitmix() exactly
+__global__ void start_vector_kernel(long long n, unsigned long long seed0, double* __restrict__ w) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long z = seed0 + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    w[i] = ((double)(z >> 11) + 0.5) / 9007199254740992.0 - 0.5;
+}
+
+// n pseudo-random start-vector entries on the device (the values n host
+// splitmix() draws would give), the seed advanced past them
+void enqueue_start_vector(riga_ctx* c, long long n, uint64_t& seed, double* w) {
+    count_launch(c);
+    start_vector_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, seed, w);
+    seed += (uint64_t)n * 0x9E3779B97F4A7C15ULL;
+}
+
 // Two full Gram-Schmidt passes (CGS2) of w against columns col0..col0+J
 int ortho_pass(Run& R, int col0, int J, double* w) {
     riga_ctx* c = R.c;
@@ -743,7 +764,6 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     std::vector<double> h_ab, theta, zl, Zf, Wsel;
-    std::vector<double> hv(N);
     int status = RIGA_OK;
 
     while (true) {
@@ -852,11 +872,7 @@ int run_eigs(riga_ctx* c, int k, double sigma0, double tol, int* nconv) {
             continue;
         }
         // random start vector, M-orthogonal to the locked ones
-        for (long long i = 0; i < N; ++i) {
-            uint64_t u = splitmix(seed);
-            hv[i] = ((double)(u >> 11) + 0.5) / 9007199254740992.0 - 0.5;
-        }
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(R.w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        enqueue_start_vector(c, N, seed, R.w);
         if (nlock > 0) ortho_pass(R, 0, nlock, R.w);
         normalize_into(R, R.w, col0, -1, 0);
         int m = 0;

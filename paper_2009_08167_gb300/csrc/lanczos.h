@@ -30,6 +30,7 @@ struct Run {
 };
 
 uint64_t splitmix(uint64_t& s);
+void enqueue_start_vector(riga_ctx* c, long long n, uint64_t& seed, double* w);
 // out[j] = sum over nch chunks of partial[c * pstride + j], j < J (fixed order)
 void enqueue_reduce_cols(riga_ctx* c, const double* partial, int nch, int J, int pstride, double* out);
 int ortho_pass(Run& R, int col0, int J, double* w);

@@ -99,12 +99,7 @@ int trlan_run(Slicer& L, int want, int lock_room, double sigma, double a, double
     const int m = L.m;
     *n_locked = 0;
     // fresh start vector, M-orthogonal to the window
-    {
-        std::vector<double> hv(N);
-        for (long long i = 0; i < N; ++i) hv[i] = ((double)(splitmix(L.seed) >> 11) + 0.5) / 9007199254740992.0 - 0.5;
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(R.w, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
-        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
-    }
+    enqueue_start_vector(c, N, L.seed, R.w);
     int col0 = L.nw;
     if (L.nw > 0) ortho_pass(R, 0, L.nw, R.w);
     normalize_into(R, R.w, col0, -1, 0);
