@@ -313,6 +313,83 @@ __global__ void __launch_bounds__(256) gemm_ritz_kernel(const double* __restrict
             if (i0 + q < nsel) U[(long long)(i0 + q) * ldu + r] = acc[q];
 }
 
+// Double-double arithmetic (Knuth's TwoSum, the FMA form of TwoProduct):
+// (hi, lo) represents hi + lo with |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void dd_add(double& hi, double& lo, double bh, double bl) {
+    const double s = hi + bh;
+    const double bb = s - hi;
+    double e = (hi - (s - bb)) + (bh - bb);
+    e += lo + bl;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+__device__ __forceinline__ void dd_add_prod(double& hi, double& lo, double a, double b) {
+    const double p = a * b;
+    dd_add(hi, lo, p, fma(a, b, -p));
+}
+
+// Rayleigh-quotient partial sums per (block, candidate q) in double-double:
+// u^T K u = sum_i u_i sum_j K_ij u_j and u^T M u = sum_i u_i (M u)_i, every
+// product and sum error-free transformed, so that the quotient carries the
+// rounding of the stored u, K and M only (K u cancels heavily for the low
+// eigenvalues: its plain FP64 sum would lose ||K|| / lambda ulps).  partial
+// holds (uKu_hi, uKu_lo, uMu_hi, uMu_lo) per (q, block).
+__global__ void __launch_bounds__(256) rq_cols_kernel(long long N, const long long* __restrict__ rowptr,
+                                                      const int* __restrict__ col, const double* __restrict__ Kv,
+                                                      const double* __restrict__ U, const double* __restrict__ MU,
+                                                      long long ld, double* __restrict__ partial) {
+    __shared__ double sh[4][8];
+    const int q = blockIdx.y;
+    const double* u = U + (long long)q * ld;
+    const double* mu = MU + (long long)q * ld;
+    const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
+    double kh = 0.0, kl = 0.0, mh = 0.0, ml = 0.0;
+    for (long long it = blockIdx.x; it * SPMV_RPB < N; it += gridDim.x) {
+        const long long row = it * SPMV_RPB + grp;
+        double sh_ = 0.0, sl_ = 0.0;
+        if (row < N)
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) dd_add_prod(sh_, sl_, Kv[e], u[col[e]]);
+#pragma unroll
+        for (int o = SPMV_TPR / 2; o > 0; o >>= 1) {
+            const double oh = __shfl_xor_sync(0xffffffffu, sh_, o, SPMV_TPR);
+            const double ol = __shfl_xor_sync(0xffffffffu, sl_, o, SPMV_TPR);
+            dd_add(sh_, sl_, oh, ol);
+        }
+        if (lane == 0 && row < N) {
+            const double ui = u[row];
+            const double p = ui * sh_;
+            dd_add(kh, kl, p, fma(ui, sh_, -p) + ui * sl_);
+            dd_add_prod(mh, ml, ui, mu[row]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double a = __shfl_xor_sync(0xffffffffu, kh, o), b = __shfl_xor_sync(0xffffffffu, kl, o);
+        const double c2 = __shfl_xor_sync(0xffffffffu, mh, o), d = __shfl_xor_sync(0xffffffffu, ml, o);
+        dd_add(kh, kl, a, b);
+        dd_add(mh, ml, c2, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = kh;
+        sh[1][threadIdx.x >> 5] = kl;
+        sh[2][threadIdx.x >> 5] = mh;
+        sh[3][threadIdx.x >> 5] = ml;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double th = 0.0, tl = 0.0, vh = 0.0, vl = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            dd_add(th, tl, sh[0][i], sh[1][i]);
+            dd_add(vh, vl, sh[2][i], sh[3][i]);
+        }
+        double* out = partial + ((long long)q * gridDim.x + blockIdx.x) * 4;
+        out[0] = th;
+        out[1] = tl;
+        out[2] = vh;
+        out[3] = vl;
+    }
+}
+
 // Residual partial sums per (block, candidate q): ||K u - lam M u||^2 and
 // ||M u||^2 (SPMV_TPR lanes per row; grid-stride over groups of rows)
 __global__ void __launch_bounds__(256) resid_cols_kernel(long long N, const long long* __restrict__ rowptr,
@@ -597,6 +674,16 @@ int configure_reorth(riga_ctx* c, int cap) {
 // candidate pairs, their FP64 residuals ||K u - lam M u|| / (|lam| ||M u||),
 // and locking of those at most lock_tol into columns nlock, nlock+1, ... of V
 // and M V (eigenvalues appended to lam).
+// host double-double addition (the same TwoSum as the device's dd_add)
+static void host_dd_add(double& hi, double& lo, double bh, double bl) {
+    const double s = hi + bh;
+    const double bb = s - hi;
+    double e = (hi - (s - bb)) + (bh - bb);
+    e += lo + bl;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
 int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const std::vector<double>& lcand,
               int nlock, double lock_tol, std::vector<double>& lam, int* n_locked) {
     riga_ctx* c = R.c;
@@ -605,8 +692,9 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
     const int nsel = (int)lcand.size();
     *n_locked = 0;
     if (nsel == 0) return RIGA_OK;
-    // W, then candidate eigenvalues and residual partial sums (304 blocks)
-    RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel + nsel + (size_t)2 * 304 * nsel));
+    // W, then candidate eigenvalues, residual partial sums (304 blocks) and
+    // Rayleigh-quotient partial sums (304 blocks)
+    RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)m * nsel + nsel + (size_t)6 * 304 * nsel));
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, Wsel.data(), (size_t)m * nsel * sizeof(double), cudaMemcpyHostToDevice, st));
     RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
     double* U = c->evec_perm.ptr;
@@ -619,10 +707,13 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
     double* dlam = c->Wd.ptr + (size_t)m * nsel;
     double* dpart = dlam + nsel;
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lcand.data(), nsel * sizeof(double), cudaMemcpyHostToDevice, st));
+    double* dpart_rq = dpart + (size_t)2 * gx * nsel;
     { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
-    std::vector<double> part((size_t)2 * gx * nsel);
+    { count_launch(c); rq_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dpart_rq); }
+    std::vector<double> part((size_t)6 * gx * nsel);
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+    const double* prq = part.data() + (size_t)2 * gx * nsel;
     int acc_n = 0;
     for (int q = 0; q < nsel; ++q) {
         double ra = 0.0, rb = 0.0;
@@ -632,11 +723,23 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
         }
         const double rho = std::sqrt(ra) / (std::fabs(lcand[q]) * std::sqrt(rb));
         if (!(rho <= lock_tol)) continue;
+        // the locked eigenvalue: the Rayleigh quotient u^T K u / u^T M u of the
+        // Ritz vector (its error is quadratic in the residual, and the
+        // double-double sums leave it the rounding of the data alone),
+        // rather than sigma + 1 / theta, which carries the rounding of the
+        // Lanczos recurrence
+        double kh = 0.0, kl = 0.0, mh = 0.0, ml = 0.0;
+        for (int b = 0; b < gx; ++b) {
+            const double* pb = prq + ((size_t)q * gx + b) * 4;
+            host_dd_add(kh, kl, pb[0], pb[1]);
+            host_dd_add(mh, ml, pb[2], pb[3]);
+        }
+        const double lrq = (kh + kl) / (mh + ml);
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->V.ptr + (long long)(nlock + acc_n) * R.ld, U + (long long)q * N,
                                          N * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->MV.ptr + (long long)(nlock + acc_n) * R.ld, MU + (long long)q * N,
                                          N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        lam.push_back(lcand[q]);
+        lam.push_back(std::isfinite(lrq) && mh > 0.0 ? lrq : lcand[q]);
         ++acc_n;
     }
     *n_locked = acc_n;
