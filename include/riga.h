@@ -352,6 +352,25 @@ int riga_set_eig_block(riga_ctx* ctx, int block);
 int riga_autotune(riga_ctx* ctx, int* small_trail_out, double* ms_out);
 
 /*
+ * riga_set_eig_accuracy: how riga_eigs forms the eigenvalues of the pairs it
+ * locks (Eq. RitzValues gives lambda = sigma + 1/theta).
+ *  rayleigh = 0 (the default): lambda = sigma + 1/theta of the converged Ritz
+ *    pair; it carries the rounding of the Lanczos recurrence, about 1e-15
+ *    relative for the lowest eigenvalues.
+ *  rayleigh = 1: lambda = u^T K u / u^T M u of the Ritz vector u, each sum
+ *    (including every row of K u, which cancels heavily for the low
+ *    eigenvalues) accumulated in double-double with error-free products;
+ *    the error is quadratic in the residual plus the rounding of the stored
+ *    u, K and M.  For derivative checks by finite differences at small steps
+ *    (an eigenvalue noise delta becomes delta / h).  It costs one pass over
+ *    K per locked candidate at several FP64 operations per entry (C2: about
+ *    10 ms per 50 pairs).
+ * The setting holds for later riga_eigs calls on ctx.
+ * Errors: RIGA_EINVAL (ctx NULL, rayleigh not 0 or 1).
+ */
+int riga_set_eig_accuracy(riga_ctx* ctx, int rayleigh);
+
+/*
  * riga_set_fp64_update: where the Schur-complement updates of FP64 fronts
  * (A22 -= L21 D L21^T of each panel step, Sec. 4.2) run, for every later
  * FP64 factorization on ctx (riga_factor with RIGA_FP64, the factorizations

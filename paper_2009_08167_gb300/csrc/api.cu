@@ -475,6 +475,13 @@ int riga_set_eig_block(riga_ctx* c, int block) {
     return RIGA_OK;
 }
 
+int riga_set_eig_accuracy(riga_ctx* c, int rayleigh) {
+    if (!c) return RIGA_EINVAL;
+    if (rayleigh != 0 && rayleigh != 1) return set_error(c, RIGA_EINVAL, "rayleigh must be 0 or 1");
+    c->opt_rq = rayleigh;
+    return RIGA_OK;
+}
+
 int riga_set_fp64_update(riga_ctx* c, int mode) {
     if (!c) return RIGA_EINVAL;
     if (mode != 0 && mode != 1) return set_error(c, RIGA_EINVAL, "mode must be 0 (CUDA cores) or 1 (tensor cores)");

@@ -196,6 +196,7 @@ struct riga_ctx {
     int opt_slice = 0, opt_precision = RIGA_FP64, opt_max_steps = 0, opt_extra = 2;
     int opt_block = 1;                 // Lanczos block size (1, 2, 4; 0 = automatic)
     int opt_reorth = 1;                // 1: recurrence + one full Gram-Schmidt pass; 2: two full passes
+    int opt_rq = 0;                    // 1: locked eigenvalues are double-double Rayleigh quotients
     riga::DevBuf<double> bwork, bcoef, bpartial, bsmall;  // block Lanczos workspace
     riga::DevBuf<int> bflag;
     double* bpin = nullptr;            // pinned host copies of the block-tridiagonal T

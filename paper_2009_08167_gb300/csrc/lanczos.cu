@@ -709,8 +709,9 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lcand.data(), nsel * sizeof(double), cudaMemcpyHostToDevice, st));
     double* dpart_rq = dpart + (size_t)2 * gx * nsel;
     { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
-    { count_launch(c); rq_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dpart_rq); }
-    std::vector<double> part((size_t)6 * gx * nsel);
+    const bool rq = c->opt_rq != 0;
+    if (rq) { count_launch(c); rq_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dpart_rq); }
+    std::vector<double> part((size_t)(rq ? 6 : 2) * gx * nsel);
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
     const double* prq = part.data() + (size_t)2 * gx * nsel;
@@ -723,18 +724,22 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
         }
         const double rho = std::sqrt(ra) / (std::fabs(lcand[q]) * std::sqrt(rb));
         if (!(rho <= lock_tol)) continue;
-        // the locked eigenvalue: the Rayleigh quotient u^T K u / u^T M u of the
-        // Ritz vector (its error is quadratic in the residual, and the
-        // double-double sums leave it the rounding of the data alone),
-        // rather than sigma + 1 / theta, which carries the rounding of the
-        // Lanczos recurrence
-        double kh = 0.0, kl = 0.0, mh = 0.0, ml = 0.0;
-        for (int b = 0; b < gx; ++b) {
-            const double* pb = prq + ((size_t)q * gx + b) * 4;
-            host_dd_add(kh, kl, pb[0], pb[1]);
-            host_dd_add(mh, ml, pb[2], pb[3]);
+        // the locked eigenvalue: sigma + 1 / theta, which carries the
+        // rounding of the Lanczos recurrence (about 1e-15 relative), or with
+        // the Rayleigh-quotient option u^T K u / u^T M u of the Ritz vector
+        // (its error quadratic in the residual; the double-double sums leave
+        // it the rounding of the data alone)
+        double lrq = lcand[q], mh = 1.0;
+        if (rq) {
+            double kh = 0.0, kl = 0.0, ml = 0.0;
+            mh = 0.0;
+            for (int b = 0; b < gx; ++b) {
+                const double* pb = prq + ((size_t)q * gx + b) * 4;
+                host_dd_add(kh, kl, pb[0], pb[1]);
+                host_dd_add(mh, ml, pb[2], pb[3]);
+            }
+            lrq = (kh + kl) / (mh + ml);
         }
-        const double lrq = (kh + kl) / (mh + ml);
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->V.ptr + (long long)(nlock + acc_n) * R.ld, U + (long long)q * N,
                                          N * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->MV.ptr + (long long)(nlock + acc_n) * R.ld, MU + (long long)q * N,

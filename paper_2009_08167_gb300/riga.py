@@ -90,6 +90,7 @@ def load_library(path=LIB_PATH):
     lib.riga_set_eig_block.argtypes = [P, I]
     lib.riga_set_reorth.argtypes = [P, I]
     lib.riga_set_fp64_update.argtypes = [P, I]
+    lib.riga_set_eig_accuracy.argtypes = [P, I]
     lib.riga_autotune.argtypes = [P, P, P]
     lib.riga_eigs_batch.argtypes = [P, I, D, D, P, P, P]
     lib.riga_query.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(D)]
@@ -288,6 +289,11 @@ class Riga:
         ms = (ctypes.c_double * 6)()
         self._check(self.lib.riga_autotune(self.ctx, ctypes.byref(t), ms))
         return t.value, list(ms)
+
+    def set_eig_accuracy(self, rayleigh):
+        """0: eigenvalues sigma + 1/theta (default); 1: double-double Rayleigh
+        quotients of the Ritz vectors (for finite-difference checks)."""
+        self._check(self.lib.riga_set_eig_accuracy(self.ctx, int(rayleigh)))
 
     def set_fp64_update(self, mode):
         """Schur updates of FP64 fronts: 0 on the CUDA cores (FP64 FMA), 1 (the

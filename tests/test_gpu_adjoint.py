@@ -22,6 +22,11 @@ def test_c5_gradient_fd_and_homogeneity():
     dev = torch.device("cuda", 0)
     R = riga_ctx()
     R.set_eig_options(slice=0, extra=4, seed=5)
+    # central differences at step 1e-6 turn an eigenvalue noise delta into
+    # delta / 1e-6: the eigenvalues are taken as double-double Rayleigh
+    # quotients (sigma + 1/theta carries about 1e-15 relative, which alone
+    # puts the difference quotient at the 1e-5 bar)
+    R.set_eig_accuracy(1)
     a = torch.tensor(cfg["a"], dtype=torch.float64, device=dev, requires_grad=True)
     b = torch.tensor(cfg["b"], dtype=torch.float64, device=dev, requires_grad=True)
     lam = eigvals(a, b, R, mesh, k, tol=1e-12)

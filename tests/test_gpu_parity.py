@@ -189,6 +189,27 @@ def test_eigs_3d_and_1d(R):
     _check_eigs(R, Mesh(1, 64, 3, 16, 8), 20)
 
 
+def test_eigs_rayleigh_quotient_option(R):
+    """riga_set_eig_accuracy(ctx, 1): the locked eigenvalues are double-double
+    Rayleigh quotients of the Ritz vectors.  Both forms meet the oracle bars;
+    they differ by the rounding of sigma + 1/theta (far below 1e-12), so the
+    residuals change by at most that much (r(lambda') = r(lambda) -
+    (lambda' - lambda) M u)."""
+    mesh = Mesh(2, 24, 3, 8, 8)
+    R.set_eig_options(slice=0, extra=2, seed=7)
+    ev0, _ = _check_eigs(R, mesh, 16)
+    rs0 = R.eigs(16, 0.0, 1e-10, vectors=False)[2]
+    R.set_eig_accuracy(1)
+    try:
+        ev1, _ = _check_eigs(R, mesh, 16)
+        rs1 = R.eigs(16, 0.0, 1e-10, vectors=False)[2]
+    finally:
+        R.set_eig_accuracy(0)
+    assert np.max(np.abs(ev1 - ev0) / ev0) <= 1e-12
+    assert np.all(rs1 <= rs0 + 1e-12)
+    R.set_eig_options(slice=0, extra=2, seed=1)
+
+
 def test_eigs_fp32_factor_path(R):
     R.set_eig_options(slice=0, precision=1, extra=2, seed=7)
     _check_eigs(R, Mesh(2, 24, 3, 8, 8), 16)
