@@ -104,6 +104,22 @@ void band_lu(BandLU& F, int n, int b, const double* T, double shift, double tiny
     }
 }
 
+// dot product with four independent partial sums (a fixed order; the
+// sequential form is one dependent add chain, which the compiler may not
+// reorder without fast-math)
+inline double dot4(const double* a, const double* b, int n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 3 < n; i += 4) {
+        s0 += a[i] * b[i];
+        s1 += a[i + 1] * b[i + 1];
+        s2 += a[i + 2] * b[i + 2];
+        s3 += a[i + 3] * b[i + 3];
+    }
+    for (; i < n; ++i) s0 += a[i] * b[i];
+    return (s0 + s1) + (s2 + s3);
+}
+
 void band_solve(const BandLU& F, double* x) {
     const int n = F.n;
     auto AB = [&](int i, int j) -> double { return F.ab[(size_t)F.kv + i - j + (size_t)j * F.ldab]; };
@@ -222,15 +238,13 @@ void band_eigvecs(int n, int b, const double* T, int q, const double* th, double
             band_solve(F, x.data());
             for (int pj = cl0; pj < oi; ++pj) {
                 const double* v = S + (size_t)ord[pj] * n;
-                double dot = 0.0;
-                for (int i = 0; i < n; ++i) dot += v[i] * x[i];
+                const double dot = dot4(v, x.data(), n);
                 for (int i = 0; i < n; ++i) x[i] -= dot * v[i];
             }
-            double nrm = 0.0;
-            for (int i = 0; i < n; ++i) nrm += x[i] * x[i];
-            nrm = std::sqrt(nrm);
+            double nrm = std::sqrt(dot4(x.data(), x.data(), n));
             if (!(nrm > 0.0)) nrm = 1.0;
-            for (int i = 0; i < n; ++i) x[i] /= nrm;
+            const double inv = 1.0 / nrm;
+            for (int i = 0; i < n; ++i) x[i] *= inv;
         }
         std::copy(x.begin(), x.end(), S + (size_t)qi * n);
     }

@@ -842,8 +842,8 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     };
     // converged: the want_run acceptable Ritz values of largest |theta| all
     // have estimates below tol_est |theta|
+    std::vector<double> est;  // residual estimates of the last Rayleigh-Ritz (check or final)
     auto converged = [&](int mm) {
-        std::vector<double> est;
         ritz(mm, est);
         std::vector<int> ord;
         for (int i = 0; i < mm * B; ++i)
@@ -878,7 +878,7 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     const int ck = std::max(1, 8 / B);  // block steps between checks
     cudaEvent_t ev;
     RIGA_CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    int pending = -1, m = 0;
+    int pending = -1, m = 0, m_conv = 0;
     bool done = false;
     for (int j = 0; j < nblk && !done; ++j) {
         const int cj = col0 + j * B;
@@ -911,7 +911,11 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
             }
             breakdown = (hflags[0] & 1) != 0;
             if (hflags[0] & 2) R.cgs2 = true;  // two full passes from now on
-            done = breakdown || converged(pending);
+            done = breakdown;
+            if (!done && converged(pending)) {
+                done = true;
+                m_conv = pending;  // theta, Zl, est, T and hB now hold T_pending's decomposition
+            }
             pending = -1;
         }
         if (!done && pending < 0 && m * B >= want_run && m % ck == 0 && m < nblk) {
@@ -928,16 +932,25 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     *m_out = m * B;
     if (m == 0) return RIGA_OK;
     // Rayleigh-Ritz with vectors: every acceptable Ritz pair whose estimate
-    // meets the bar, largest |theta| first, up to the locking room
-    rc = enqueue_fetch(m);
-    if (rc) return rc;
-    RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
-    if (hflags[1] & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
-    breakdown = (hflags[0] & 1) != 0;
-    if (hflags[0] & 2) R.cgs2 = true;
+    // meets the bar, largest |theta| first, up to the locking room.  A run
+    // that a check found converged uses that check's T_pending and its
+    // decomposition (the blocks V_1 .. V_pending are final; the steps issued
+    // after the check only extended the basis), so the host computes no
+    // second decomposition while the GPU idles; the flags of those later
+    // steps are read after the locking.
+    const bool reuse = m_conv > 0;
+    if (reuse) {
+        m = m_conv;
+    } else {
+        rc = enqueue_fetch(m);
+        if (rc) return rc;
+        RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (hflags[1] & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+        breakdown = (hflags[0] & 1) != 0;
+        if (hflags[0] & 2) R.cgs2 = true;
+        ritz(m, est);
+    }
     const int n = m * B;
-    std::vector<double> est;
-    ritz(m, est);
     std::vector<int> ord;
     for (int i = 0; i < n; ++i)
         if (acceptable(theta[i])) ord.push_back(i);
@@ -989,7 +1002,15 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     if (dbg)
         std::fprintf(stderr, "[riga] block run: B=%d steps=%d (blocks %d/%d) breakdown=%d cgs2=%d candidates=%zu\n", B,
                      n, m, nblk, (int)breakdown, (int)R.cgs2, lcand.size());
-    return ritz_lock(R, col0, n, Wsel, lcand, nlock, lock_tol, lam, n_locked);
+    rc = ritz_lock(R, col0, n, Wsel, lcand, nlock, lock_tol, lam, n_locked);
+    if (rc || !reuse) return rc;
+    // flags of the steps issued after the converged check (ritz_lock has
+    // synchronized the stream)
+    RIGA_CUDA_TRY(c, cudaMemcpy(hflags, K.flag, sizeof(int), cudaMemcpyDeviceToHost));
+    RIGA_CUDA_TRY(c, cudaMemcpy(hflags + 1, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hflags[1] & 2) return set_error(c, RIGA_ETIMEOUT, "a dependency wait of the tree solve gave up");
+    if (hflags[0] & 2) R.cgs2 = true;
+    return RIGA_OK;
 }
 
 }  // namespace riga
