@@ -42,6 +42,7 @@ struct TreeArgs {
     const int* parts_b;
     const SolveItem* items;  // forward parts (ascending height), then backward parts
     const ChildRec* crec;    // children records (see Symbolic::crec)
+    int item0;         // first item of this launch (items item0 .. item0 + n_items - 1)
     int n_items, n_fwd;
     int nsplit;        // independent groups of NR right-hand sides, items interleaved
     int n_fronts;      // stride of the per-group completion counters
@@ -210,8 +211,8 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
     // `cw` into slot sl; an item's panel goes in one copy when it fits the
     // slot's two halves, else in chunks through them
     auto issue_first = [&](int cw, int sl) {
-        const SolveItem it = a.items[cw / a.nsplit];
-        const bool fw = cw / a.nsplit < a.n_fwd;
+        const SolveItem it = a.items[a.item0 + cw / a.nsplit];
+        const bool fw = a.item0 + cw / a.nsplit < a.n_fwd;
         const int units = fw ? it.k : it.n, ldp = it.ldp, cnt = it.hi - it.lo;
         const bool whole = (long long)units * ldp <= 2LL * a.chunk_elems;
         const int upc = whole ? max(1, units) : max(1, a.chunk_elems / ldp);
@@ -238,8 +239,9 @@ __global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q,
     int cs = 0;  // slot of the current item
     __syncthreads();
     for (;;) {
-        const int claimed = s_item;
-        if (claimed >= total) return;  // no copies in flight
+        const int claimed_local = s_item;
+        if (claimed_local >= total) return;  // no copies in flight
+        const int claimed = a.item0 * a.nsplit + claimed_local;  // global work index (trace slot)
         const int item = claimed / a.nsplit, grp = claimed - item * a.nsplit;
         double* const y = a.y + (long long)grp * NR * a.ldy;
         double* const w1 = a.w1 + (long long)grp * NR * a.ldy;
@@ -844,6 +846,9 @@ int solve_max_rhs(riga_ctx* c) {
     return 1;
 }
 
+// chunk half (elements) of the leaf launches of large-front trees
+constexpr int LEAF_CHUNK = 1536;
+
 template <typename T, int NR>
 static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     Symbolic& S = c->S;
@@ -859,7 +864,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     int max_n = 0;
     for (int f = 0; f < S.n_nodes; ++f) max_n = std::max(max_n, S.n[f]);
     const int n_items = (int)S.sitems.size();
-    int maxopt = 0, nsm = 0, per_sm = 0, chunk = 0, nt = 0;
+    int maxopt = 0, nsm = 0, chunk = 0, nt = 0;
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     int nslot = 1;
@@ -870,13 +875,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
         return set_error(c, RIGA_EINVAL, "several right-hand sides need whole-panel copies");
     auto kern = warp ? tree_solve_warp_kernel<T, NR>
                      : (S.solve_mode == SOLVE_CTA128 ? tree_solve_kernel<T, 128, NR> : tree_solve_kernel<T, 256, NR>);
-    if (smem > 48 * 1024)
-        RIGA_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
-    const int per_block = warp ? 4 : 1;  // concurrent items per block
-    const long long work = (long long)n_items * nsplit;
-    const int grid = (int)std::max<long long>(1, std::min<long long>((work + per_block - 1) / per_block, std::max(1, per_sm) * nsm));
-    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, (2 * (size_t)S.n_nodes * nsplit + 1) * sizeof(int), st));
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(c->solve_flags.ptr, 0, (2 * (size_t)S.n_nodes * nsplit + 3) * sizeof(int), st));
     TreeArgs a;
     a.node_ptr = c->node_ptr.ptr;
     a.kk = c->kk.ptr;
@@ -893,6 +892,7 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     a.parts_b = c->parts_b.ptr;
     a.items = c->sitems.ptr;
     a.crec = c->crec.ptr;
+    a.item0 = 0;
     a.n_items = n_items;
     a.n_fwd = S.n_fwd_items;
     a.chunk_elems = chunk;
@@ -911,8 +911,55 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     a.err = c->flag.ptr;
     a.spin_limit = c->wait_limit;
     a.trace = c->trace_buf;
-    { count_launch(c); kern<<<grid, nt, smem, st>>>(Q, a); }
-    return RIGA_OK;
+    // one launch over items [i0, i0 + cnt) with the given configuration and counter
+    auto launch = [&](void (*k)(const T*, TreeArgs), int i0, int cnt, size_t sm, int ch, int ns, int mx,
+                      int ctr) -> int {
+        if (cnt <= 0) return RIGA_OK;
+        int occ = 0;
+        if (sm > 48 * 1024) RIGA_CUDA_TRY(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nt, sm));
+        const int per_block = warp ? 4 : 1;  // concurrent items per block
+        const long long work = (long long)cnt * nsplit;
+        const int grid = (int)std::max<long long>(1, std::min<long long>((work + per_block - 1) / per_block, std::max(1, occ) * nsm));
+        TreeArgs b = a;
+        b.item0 = i0;
+        b.n_items = cnt;
+        b.chunk_elems = ch;
+        b.nslot = ns;
+        b.max_n = mx;
+        b.counter = a.counter + ctr;
+        { count_launch(c); k<<<grid, nt, sm, st>>>(Q, b); }
+        return RIGA_OK;
+    };
+    // Trees of large FP64 fronts: the leaf fronts (no children: forward
+    // parts wait for nothing, backward parts only for the launch before)
+    // run in launches of their own whose short front vectors let three CTAs
+    // share an SM (registers bound it), so that one CTA's arithmetic covers
+    // another's copies, gathers and reductions; the fronts above run in
+    // between with the long front vectors, two CTAs per SM.
+    int f0 = 0, b0 = 0;
+    if (S.solve_mode == SOLVE_CTA256 && sizeof(T) == sizeof(double) && NR == 1) {
+        auto leaf = [&](int i) { return S.child_ptr[S.sitems[i].front + 1] == S.child_ptr[S.sitems[i].front]; };
+        while (f0 < S.n_fwd_items && leaf(f0)) ++f0;
+        while (b0 < n_items - S.n_fwd_items && leaf(n_items - 1 - b0)) ++b0;
+    }
+    if (f0 > 0 && b0 > 0 && f0 + b0 < n_items) {
+        int leaf_n = 0, leaf_ldp = 0;
+        for (int i = 0; i < n_items; ++i)
+            if (i < f0 || i >= n_items - b0) {
+                leaf_n = std::max(leaf_n, S.n[S.sitems[i].front]);
+                leaf_ldp = std::max(leaf_ldp, S.sitems[i].ldp);
+            }
+        const int lchunk = std::max(LEAF_CHUNK, (leaf_ldp + 3) / 4 * 4);
+        const size_t lsmem = (size_t)(2LL * lchunk + (long long)NR * leaf_n + (long long)nt * NR + 8) * sizeof(T);
+        if (lsmem + 256 <= (size_t)maxopt) {
+            int rc = launch(kern, 0, f0, lsmem, lchunk, 1, leaf_n, 0);
+            if (rc == RIGA_OK) rc = launch(kern, f0, n_items - f0 - b0, smem, chunk, nslot, max_n, 1);
+            if (rc == RIGA_OK) rc = launch(kern, n_items - b0, b0, lsmem, lchunk, 1, leaf_n, 2);
+            return rc;
+        }
+    }
+    return launch(kern, 0, n_items, smem, chunk, nslot, max_n, 0);
 }
 
 // y := A^{-1} y for nrhs columns (stride N).  Trees with a critical path
@@ -932,7 +979,7 @@ int enqueue_solve(riga_ctx* c, double* y, int nrhs) {
     const int maxr = split ? 1 : std::min(S.solve_mode == SOLVE_CTA128 ? SMALL_COMBINED : 4, solve_max_rhs(c));
     const int width = split ? std::min(std::max(1, nrhs), 8) : std::min(std::max(1, nrhs), maxr);
     RIGA_CUDA_TRY(c, c->upd.alloc((S.upd_size > 0 ? S.upd_size : 1) * (size_t)width));
-    RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes * width + 1));
+    RIGA_CUDA_TRY(c, c->solve_flags.alloc(2 * (size_t)S.n_nodes * width + 3));
     RIGA_CUDA_TRY(c, c->w1buf.alloc((size_t)S.N * width));
     for (int c0 = 0; c0 < nrhs;) {
         const int left = nrhs - c0;
