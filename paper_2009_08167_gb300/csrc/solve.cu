@@ -184,8 +184,8 @@ __device__ __forceinline__ void accumulate_chunk(const T* __restrict__ P, int ld
 // Everything an item needs to know about its front comes packed in the item
 // (and, for its children, in one record each), so that few dependent global
 // loads separate a claim from the arithmetic.
-template <typename T, int NT, int NR>
-__global__ void __launch_bounds__(NT) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
+template <typename T, int NT, int NR, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) tree_solve_kernel(const T* __restrict__ Q, TreeArgs a) {
     constexpr int NAMAX = (NR == 1) ? 8 : (NR == 2 ? 4 : 2);  // output slots per thread per pass
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // a.nslot slots of two chunk halves each: slot s = halves 2s, 2s+1
@@ -846,8 +846,10 @@ int solve_max_rhs(riga_ctx* c) {
     return 1;
 }
 
-// chunk half (elements) of the leaf launches of large-front trees
-constexpr int LEAF_CHUNK = 1536;
+// chunk half (elements) and resident CTAs per SM (a register budget) of the
+// leaf launches of large-front trees
+constexpr int LEAF_CHUNK = 2048;
+constexpr int LEAF_MINB = 4;
 
 template <typename T, int NR>
 static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
@@ -933,10 +935,13 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
     };
     // Trees of large FP64 fronts: the leaf fronts (no children: forward
     // parts wait for nothing, backward parts only for the launch before)
-    // run in launches of their own whose short front vectors let three CTAs
-    // share an SM (registers bound it), so that one CTA's arithmetic covers
-    // another's copies, gathers and reductions; the fronts above run in
-    // between with the long front vectors, two CTAs per SM.
+    // run in launches of their own whose short front vectors let four CTAs
+    // share an SM (a kernel instance held to 64 registers), so that one
+    // CTA's arithmetic covers another's copies, gathers and reductions; the
+    // fronts above run in between with the long front vectors, two CTAs per
+    // SM.  Chunk 2048 and four CTAs were the best of a sweep on the 64^3
+    // p = 2 mesh (one right-hand side: 2.58 ms, against 2.60-2.97 ms for
+    // chunks 768-2048 and three or four CTAs).
     int f0 = 0, b0 = 0;
     if (S.solve_mode == SOLVE_CTA256 && sizeof(T) == sizeof(double) && NR == 1) {
         auto leaf = [&](int i) { return S.child_ptr[S.sitems[i].front + 1] == S.child_ptr[S.sitems[i].front]; };
@@ -953,9 +958,10 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
         const int lchunk = std::max(LEAF_CHUNK, (leaf_ldp + 3) / 4 * 4);
         const size_t lsmem = (size_t)(2LL * lchunk + (long long)NR * leaf_n + (long long)nt * NR + 8) * sizeof(T);
         if (lsmem + 256 <= (size_t)maxopt) {
-            int rc = launch(kern, 0, f0, lsmem, lchunk, 1, leaf_n, 0);
+            auto lk = tree_solve_kernel<T, 256, NR, LEAF_MINB>;
+            int rc = launch(lk, 0, f0, lsmem, lchunk, 1, leaf_n, 0);
             if (rc == RIGA_OK) rc = launch(kern, f0, n_items - f0 - b0, smem, chunk, nslot, max_n, 1);
-            if (rc == RIGA_OK) rc = launch(kern, n_items - b0, b0, lsmem, lchunk, 1, leaf_n, 2);
+            if (rc == RIGA_OK) rc = launch(lk, n_items - b0, b0, lsmem, lchunk, 1, leaf_n, 2);
             return rc;
         }
     }
