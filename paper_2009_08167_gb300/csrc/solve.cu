@@ -933,37 +933,48 @@ static int enqueue_solve_t(riga_ctx* c, const T* Q, double* y, int nsplit) {
         { count_launch(c); k<<<grid, nt, sm, st>>>(Q, b); }
         return RIGA_OK;
     };
-    // Trees of large FP64 fronts: the leaf fronts (no children: forward
-    // parts wait for nothing, backward parts only for the launch before)
-    // run in launches of their own whose short front vectors let four CTAs
+    // Trees of large FP64 fronts: the fronts of the lowest levels (forward
+    // parts wait only for earlier parts of the same launch, backward parts
+    // also for the launch before) run in launches of their own whose short
+    // front vectors let four CTAs
     // share an SM (a kernel instance held to 64 registers), so that one
     // CTA's arithmetic covers another's copies, gathers and reductions; the
     // fronts above run in between with the long front vectors, two CTAs per
     // SM.  Chunk 2048 and four CTAs were the best of a sweep on the 64^3
     // p = 2 mesh (one right-hand side: 2.58 ms, against 2.60-2.97 ms for
     // chunks 768-2048 and three or four CTAs).
-    int f0 = 0, b0 = 0;
+    int f0 = 0, b0 = 0, leaf_n = 0, lchunk = 0;
+    size_t lsmem = 0;
     if (S.solve_mode == SOLVE_CTA256 && sizeof(T) == sizeof(double) && NR == 1) {
-        auto leaf = [&](int i) { return S.child_ptr[S.sitems[i].front + 1] == S.child_ptr[S.sitems[i].front]; };
-        while (f0 < S.n_fwd_items && leaf(f0)) ++f0;
-        while (b0 < n_items - S.n_fwd_items && leaf(n_items - 1 - b0)) ++b0;
+        // the lowest levels whose front vectors still let four CTAs share an SM
+        // (228 KiB of shared memory per SM, 1 KiB of it reserved per CTA)
+        const size_t cap = (size_t)228 * 1024 / LEAF_MINB - 2048;
+        for (int hs = 0; hs < S.n_levels; ++hs) {
+            int mn = 0, ml = 0;
+            for (int i = 0; i < n_items; ++i)
+                if (S.height[S.sitems[i].front] <= hs) {
+                    mn = std::max(mn, S.n[S.sitems[i].front]);
+                    ml = std::max(ml, S.sitems[i].ldp);
+                }
+            const int ch = std::max(LEAF_CHUNK, (ml + 3) / 4 * 4);
+            const size_t sm = (size_t)(2LL * ch + (long long)NR * mn + (long long)nt * NR + 8) * sizeof(T);
+            if (sm > cap) break;
+            int ff = 0, bb = 0;
+            while (ff < S.n_fwd_items && S.height[S.sitems[ff].front] <= hs) ++ff;
+            while (bb < n_items - S.n_fwd_items && S.height[S.sitems[n_items - 1 - bb].front] <= hs) ++bb;
+            f0 = ff;
+            b0 = bb;
+            leaf_n = mn;
+            lchunk = ch;
+            lsmem = sm;
+        }
     }
     if (f0 > 0 && b0 > 0 && f0 + b0 < n_items) {
-        int leaf_n = 0, leaf_ldp = 0;
-        for (int i = 0; i < n_items; ++i)
-            if (i < f0 || i >= n_items - b0) {
-                leaf_n = std::max(leaf_n, S.n[S.sitems[i].front]);
-                leaf_ldp = std::max(leaf_ldp, S.sitems[i].ldp);
-            }
-        const int lchunk = std::max(LEAF_CHUNK, (leaf_ldp + 3) / 4 * 4);
-        const size_t lsmem = (size_t)(2LL * lchunk + (long long)NR * leaf_n + (long long)nt * NR + 8) * sizeof(T);
-        if (lsmem + 256 <= (size_t)maxopt) {
-            auto lk = tree_solve_kernel<T, 256, NR, LEAF_MINB>;
-            int rc = launch(lk, 0, f0, lsmem, lchunk, 1, leaf_n, 0);
-            if (rc == RIGA_OK) rc = launch(kern, f0, n_items - f0 - b0, smem, chunk, nslot, max_n, 1);
-            if (rc == RIGA_OK) rc = launch(lk, n_items - b0, b0, lsmem, lchunk, 1, leaf_n, 2);
-            return rc;
-        }
+        auto lk = tree_solve_kernel<T, 256, NR, LEAF_MINB>;
+        int rc = launch(lk, 0, f0, lsmem, lchunk, 1, leaf_n, 0);
+        if (rc == RIGA_OK) rc = launch(kern, f0, n_items - f0 - b0, smem, chunk, nslot, max_n, 1);
+        if (rc == RIGA_OK) rc = launch(lk, n_items - b0, b0, lsmem, lchunk, 1, leaf_n, 2);
+        return rc;
     }
     return launch(kern, 0, n_items, smem, chunk, nslot, max_n, 0);
 }
