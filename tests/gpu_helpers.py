@@ -22,6 +22,25 @@ def oracle_matrices(mesh, coefK=None, coefM=None):
     return assembly.assemble_coef(mesh.dim, mesh.ne, mesh.p, mesh.mults, coefK, coefM)
 
 
+def ldlt_forward_bounds(L, d, B, eps):
+    """First-order forward-error bounds of an LDL^T factorization without
+    pivoting when the factored matrix moves by |dA| <= eps B (componentwise).
+
+    From A + dA = (L + dL)(D + dD)(L + dL)^T, the symmetric E = L^{-1} dA L^{-T}
+    equals X D + dD + D X^T to first order, X = L^{-1} dL strictly lower
+    triangular.  So dD = diag(E) and X_ij = E_ij / d_j (i > j), and with
+    G = |L^{-1}| B |L^{-T}|:
+        |dd_k| <= eps G_kk,      |dL| <= eps |L| (strict_lower(G) |D|^{-1}).
+    G measures the conditioning of each pivot and multiplier; a pivot of a
+    nearly singular leading block has a large G_kk / |d_k|.
+    Returns (pivot bounds, dense multiplier bounds)."""
+    import scipy.linalg as sla
+    n = L.shape[0]
+    Li = np.abs(sla.solve_triangular(L, np.eye(n), lower=True, unit_diagonal=True))
+    G = Li @ B @ Li.T
+    return eps * np.diag(G), eps * (np.abs(L) @ (np.tril(G, -1) / np.abs(d)[None, :]))
+
+
 def clusters(lam, rel=1e-8):
     """Index groups of (nearly) equal eigenvalues."""
     groups = [[0]]

@@ -2,10 +2,11 @@
 
 Tolerances (from the floating-point error of each step, fp64 unit roundoff
 1.1e-16): assembly 1e-13 relative to the largest entry (sums of at most
-(p+1)^d quadrature products); LDL^T pivots 1e-8 relative (rounding grows
-through small pivots of an indefinite factorization without pivoting) plus
-the componentwise backward-error bound |PAP^T - LDL^T| <= 1e-13 |L||D||L^T|;
-solves 1e-10
+(p+1)^d quadrature products); LDL^T: the componentwise backward-error bound
+|PAP^T - LDL^T| <= 1e-13 (|L||D||L^T| + |K| + |sigma||M|) for the GPU factor
+and for the oracle's, and pivots and multipliers within the forward-error
+bound that this backward error and the conditioning of each pivot imply
+(tests.gpu_helpers.ldlt_forward_bounds, first order, times 2); solves 1e-10
 relative; eigenvalues 1e-10 relative and residuals 1e-10 (the stated bar of
 the FP64 path); eigenvector subspaces 1e-9 in cosine; integer outputs
 (orders, inertia) exact.
@@ -15,7 +16,7 @@ import pytest
 
 from oracle import adjoint, assembly, bspline, eigen, factor, symbolic
 from paper_2009_08167_gb300.inputs import Mesh, normal
-from tests.gpu_helpers import compare_eigvecs, oracle_matrices, riga_ctx
+from tests.gpu_helpers import compare_eigvecs, ldlt_forward_bounds, oracle_matrices, riga_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +60,10 @@ def _gap_shifts(lam, count):
     return [0.5 * (lam[i] + lam[i + 1]) for i in pick]
 
 
+# componentwise backward-error bar of each FP64 factorization, relative to
+# |L||D||L^T| + |K| + |sigma||M|: n u with n up to a few thousand
+EPS_BWD = 1e-13
+
 FACT_CASES = [Mesh(2, 16, 2, None), Mesh(2, 24, 3, 8, 8), Mesh(3, [5, 6, 4], 2, None, 3), Mesh(1, 50, 3, 10, 8)]
 
 
@@ -86,13 +91,23 @@ def factor_parity(R, mesh):
         Ap = A[np.ix_(perm, perm)]
         L, d = factor.ldlt_dense(Ap)
         D, Lptr, Lg = R.get_factor(with_L=True)
-        # forward error of each pivot: rounding grows through small pivots of
-        # the indefinite factorization (no pivoting), hence 1e-8
-        assert np.max(np.abs(D - d) / np.abs(d)) < 1e-8
-        # L entries of each dense front (lower part of the first k columns)
         pos = np.empty(K.n, dtype=np.int64)
         pos[perm] = np.arange(K.n)
         fp, fi = sym["front_ptr"], sym["front_idx"]
+        # the GPU factors its own A = K - sigma M, whose entries differ from
+        # the oracle's by rounding of K and sigma M (cancellation), so the
+        # data term |K| + |sigma| |M| joins the backward-error bounds
+        data = (np.abs(Kd) + abs(sigma) * np.abs(Md))[np.ix_(perm, perm)]
+        # the oracle's own componentwise backward error
+        Bo = (np.abs(L) * np.abs(d)[None, :]) @ np.abs(L).T + data
+        assert np.max(np.abs(Ap - (L * d[None, :]) @ L.T) - EPS_BWD * Bo) <= 0.0
+        # both factors are exact LDL^T of matrices within EPS_BWD B of P A P^T
+        # (the GPU's bound is asserted below), so they differ by at most the
+        # forward bounds of a perturbation 2 EPS_BWD B; the factor 2 covers
+        # the second-order terms
+        dbound, Lbound = ldlt_forward_bounds(L, d, Bo, 2 * EPS_BWD)
+        assert np.all(np.abs(D - d) <= 2 * dbound)
+        # L entries of each dense front (lower part of the first k columns)
         for F in range(sym["node_ptr"].size - 1):
             idx = pos[fi[fp[F]:fp[F + 1]]]
             n = idx.size
@@ -100,9 +115,9 @@ def factor_parity(R, mesh):
             blk = Lg[Lptr[F]:Lptr[F + 1]].reshape(k, n).T  # column-major n x k
             ref = L[np.ix_(idx, idx[:k])]
             low = np.tril(np.ones((n, k), dtype=bool), -1)
-            assert np.allclose(blk[low], ref[low], rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+            assert np.all(np.abs(blk[low] - ref[low]) <= 2 * Lbound[np.ix_(idx, idx[:k])][low])
         # componentwise backward error of the GPU factor itself:
-        # |P A P^T - L D L^T| <= c u |L| |D| |L^T|  (c u = 1e-13 here)
+        # |P A P^T - L D L^T| <= c u (|L| |D| |L^T| + data), c u = EPS_BWD
         Lfull = np.eye(K.n)
         for F in range(sym["node_ptr"].size - 1):
             idx = pos[fi[fp[F]:fp[F + 1]]]
@@ -114,12 +129,8 @@ def factor_parity(R, mesh):
             sub[low] = blk[low]
             Lfull[np.ix_(idx, idx[:k])] += sub
         R_ = Ap - (Lfull * D[None, :]) @ Lfull.T
-        # the GPU factors its own A = K - sigma M, whose entries differ from
-        # the oracle's by rounding of K and sigma M (cancellation), so the
-        # data term |K| + |sigma| |M| joins the bound
-        data = (np.abs(Kd) + abs(sigma) * np.abs(Md))[np.ix_(perm, perm)]
         bound = (np.abs(Lfull) * np.abs(D)[None, :]) @ np.abs(Lfull).T + data
-        assert np.max(np.abs(R_) - 1e-13 * bound) <= 0.0
+        assert np.max(np.abs(R_) - EPS_BWD * bound) <= 0.0
         x, _ = R.solve(b)
         xr = np.linalg.solve(A, b)
         assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
