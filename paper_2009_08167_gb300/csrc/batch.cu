@@ -318,32 +318,39 @@ __global__ void __launch_bounds__(256) bgemm_ritz_kernel(const double* __restric
             if (i0 + q < qmax) U[(long long)(i0 + q) * ldu + r] = acc[q];
 }
 
-// residual partial sums per (chunk, candidate q): ||K u - lam M u||^2, ||M u||^2
+// M u of candidate q into MU (the matrix and u read once for both products)
+// and the residual partial sums per (chunk, candidate q): ||K u - lam M u||^2,
+// ||M u||^2
 __global__ void __launch_bounds__(256) bresid_kernel(const long long* __restrict__ rowptr, const int* __restrict__ col,
-                                                     const double* __restrict__ Kv, const double* __restrict__ U,
-                                                     const double* __restrict__ MU, long long ld,
-                                                     const double* __restrict__ lam, int qmax, Chunks ch,
-                                                     double* __restrict__ partial) {
+                                                     const double* __restrict__ Kv, const double* __restrict__ Mv,
+                                                     const double* __restrict__ U, double* __restrict__ MU,
+                                                     long long ld, const double* __restrict__ lam, int qmax,
+                                                     Chunks ch, double* __restrict__ partial) {
     __shared__ double sa[8], sb[8];
     const int q = blockIdx.y;
     const int b = ch.prob[blockIdx.x];
     const double l = lam[(long long)b * qmax + q];
     const double* u = U + (long long)q * ld;
-    const double* mu = MU + (long long)q * ld;
+    double* mu = MU + (long long)q * ld;
     const long long r0 = ch.row0[blockIdx.x];
     const int rows = ch.rows[blockIdx.x];
     const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
     double sr = 0.0, sm = 0.0;
     for (int base = 0; base < BCH; base += SPMV_RPB) {
         const int rl = base + grp;
-        double s = 0.0;
+        double s = 0.0, m = 0.0;
         if (rl < rows) {
             const long long row = r0 + rl;
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += Kv[e] * u[col[e]];
+            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) {
+                const double x = u[col[e]];
+                s += Kv[e] * x;
+                m += Mv[e] * x;
+            }
         }
         s = group_sum(s);
+        m = group_sum(m);
         if (lane == 0 && rl < rows) {
-            const double m = mu[r0 + rl];
+            mu[r0 + rl] = m;
             const double rr = s - l * m;
             sr += rr * rr;
             sm += m * m;
@@ -805,16 +812,18 @@ int run_eigs_batch(riga_ctx* c, int k, double sigma0, double tol) {
         double* U = c->evec_perm.ptr;
         double* MU = c->evec_perm.ptr + (size_t)N * qmax;
         {
-            PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * qmax) * sizeof(double));
+            // algorithmic bytes: V read, U written and read back, M U
+            // written, K and M (values and columns) read once
+            PhaseScope scope(c, PH_RITZ, (double)N * (m + 3 * qmax) * sizeof(double) + 20.0 * (double)S.nnz);
             const int qn = qmax <= 8 ? 8 : (qmax <= 16 ? 16 : (qmax <= 24 ? 24 : 32));
             dim3 g(B.nch, (qmax + qn - 1) / qn);
             auto kern = qn == 8 ? bgemm_ritz_kernel<8>
                                 : (qn == 16 ? bgemm_ritz_kernel<16> : (qn == 24 ? bgemm_ritz_kernel<24> : bgemm_ritz_kernel<32>));
             { count_launch(c); kern<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, U, N); }
-            { count_launch(c); kern<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * B.ld, B.ld, m, B.W.ptr, qmax, B.ch, MU, N); }
             RIGA_CUDA_TRY(c, B.rpart.alloc((size_t)2 * B.nch * qmax));
-            { count_launch(c); bresid_kernel<<<dim3(B.nch, qmax), 256, 0, st>>>(c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N,
-                                                                               B.lam.ptr, qmax, B.ch, B.rpart.ptr); }
+            // M U by the sparse product (not MV W, a dense product of m columns)
+            { count_launch(c); bresid_kernel<<<dim3(B.nch, qmax), 256, 0, st>>>(c->rowptr.ptr, c->col.ptr, c->Kval.ptr, c->Mval.ptr,
+                                                                               U, MU, N, B.lam.ptr, qmax, B.ch, B.rpart.ptr); }
         }
         std::vector<double> part((size_t)2 * B.nch * qmax);
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), B.rpart.ptr, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));

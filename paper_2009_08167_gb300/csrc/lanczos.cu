@@ -390,33 +390,48 @@ __global__ void __launch_bounds__(256) rq_cols_kernel(long long N, const long lo
     }
 }
 
-// Residual partial sums per (block, candidate q): ||K u - lam M u||^2 and
-// ||M u||^2 (SPMV_TPR lanes per row; grid-stride over groups of rows)
+// M u of every candidate q into MU (the matrix and u read once for both
+// products), and for q < nres the residual partial sums per block
+// ||K u - lam M u||^2 and ||M u||^2 (SPMV_TPR lanes per row; grid-stride
+// over groups of rows)
 __global__ void __launch_bounds__(256) resid_cols_kernel(long long N, const long long* __restrict__ rowptr,
                                                          const int* __restrict__ col, const double* __restrict__ Kv,
-                                                         const double* __restrict__ U, const double* __restrict__ MU,
-                                                         long long ld, const double* __restrict__ lam,
+                                                         const double* __restrict__ Mv, const double* __restrict__ U,
+                                                         double* __restrict__ MU, long long ld,
+                                                         const double* __restrict__ lam, int nres,
                                                          double* __restrict__ partial) {
     __shared__ double sa[8], sb[8];
     const int q = blockIdx.y;
-    const double l = lam[q];
+    const bool res = q < nres;
+    const double l = res ? lam[q] : 0.0;
     const double* u = U + (long long)q * ld;
-    const double* mu = MU + (long long)q * ld;
+    double* mu = MU + (long long)q * ld;
     const int lane = threadIdx.x & (SPMV_TPR - 1), grp = threadIdx.x / SPMV_TPR;
     double sr = 0.0, sm = 0.0;
     for (long long it = blockIdx.x; it * SPMV_RPB < N; it += gridDim.x) {
         const long long row = it * SPMV_RPB + grp;
-        double s = 0.0;
-        if (row < N)
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) s += Kv[e] * u[col[e]];
+        double s = 0.0, m = 0.0;
+        if (row < N) {
+            if (res) {
+                for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) {
+                    const double x = u[col[e]];
+                    s += Kv[e] * x;
+                    m += Mv[e] * x;
+                }
+            } else {
+                for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) m += Mv[e] * u[col[e]];
+            }
+        }
         s = group_sum(s);
+        m = group_sum(m);
         if (lane == 0 && row < N) {
-            const double m = mu[row];
+            mu[row] = m;
             const double r = s - l * m;
             sr += r * r;
             sm += m * m;
         }
     }
+    if (!res) return;
     sr = warp_sum_groups(sr);
     sm = warp_sum_groups(sm);
     if ((threadIdx.x & 31) == 0) {
@@ -699,16 +714,18 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
     RIGA_CUDA_TRY(c, c->evec_perm.alloc((size_t)N * nsel * 2));
     double* U = c->evec_perm.ptr;
     double* MU = c->evec_perm.ptr + (size_t)N * nsel;
-    PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (m + 2 * nsel) * sizeof(double));
+    // algorithmic bytes: V read, U written and read back, M U written, K
+    // and M (values and columns) read once
+    PhaseScope scope(c, PH_RITZ, (double)N * (m + 3 * nsel) * sizeof(double) + 20.0 * (double)c->S.nnz);
     dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
     { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, U, N, N); }
-    { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, m, c->Wd.ptr, m, nsel, MU, N, N); }
     const int gx = 304;
     double* dlam = c->Wd.ptr + (size_t)m * nsel;
     double* dpart = dlam + nsel;
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lcand.data(), nsel * sizeof(double), cudaMemcpyHostToDevice, st));
     double* dpart_rq = dpart + (size_t)2 * gx * nsel;
-    { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
+    // M U by the sparse product (not MV W, a dense product of m columns)
+    { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, c->Mval.ptr, U, MU, N, dlam, nsel, dpart); }
     const bool rq = c->opt_rq != 0;
     if (rq) { count_launch(c); rq_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dpart_rq); }
     std::vector<double> part((size_t)(rq ? 6 : 2) * gx * nsel);
@@ -751,7 +768,7 @@ int ritz_lock(Run& R, int col0, int m, const std::vector<double>& Wsel, const st
     return RIGA_OK;
 }
 
-// Ritz vectors U = V[:, col0 : col0+J] W and M U = MV[:, col0 : col0+J] W for
+// Ritz vectors U = V[:, col0 : col0+J] W and their sparse products M U for
 // the nsel columns of W (J x nsel, host, column-major) into U and MU (N x
 // nsel, leading dimension N); the FP64 residuals
 // ||K u - lam M u|| / (|lam| ||M u||) of the first nres of them into rho.
@@ -765,15 +782,15 @@ int ritz_vectors_resid(Run& R, int col0, int J, const std::vector<double>& W, in
     const int gx = 304;
     RIGA_CUDA_TRY(c, c->Wd.alloc((size_t)J * nsel + nsel + (size_t)2 * gx * std::max(nres, 1)));
     RIGA_CUDA_TRY(c, cudaMemcpyAsync(c->Wd.ptr, W.data(), (size_t)J * nsel * sizeof(double), cudaMemcpyHostToDevice, st));
-    PhaseScope scope(c, PH_RITZ, 2.0 * (double)N * (J + 2 * nsel) * sizeof(double));
+    PhaseScope scope(c, PH_RITZ, (double)N * (J + 3 * nsel) * sizeof(double) + 20.0 * (double)c->S.nnz);
     dim3 g((unsigned)((N + 255) / 256), (unsigned)((nsel + 15) / 16));
     { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->V.ptr + (long long)col0 * R.ld, R.ld, J, c->Wd.ptr, J, nsel, U, N, N); }
-    { count_launch(c); gemm_ritz_kernel<<<g, 256, 0, st>>>(c->MV.ptr + (long long)col0 * R.ld, R.ld, J, c->Wd.ptr, J, nsel, MU, N, N); }
+    double* dlam = c->Wd.ptr + (size_t)J * nsel;
+    double* dpart = dlam + nsel;
+    if (nres > 0) RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lam.data(), nres * sizeof(double), cudaMemcpyHostToDevice, st));
+    // M U by the sparse product, the residuals of the first nres columns
+    { count_launch(c); resid_cols_kernel<<<dim3(gx, nsel), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, c->Mval.ptr, U, MU, N, dlam, nres, dpart); }
     if (nres > 0) {
-        double* dlam = c->Wd.ptr + (size_t)J * nsel;
-        double* dpart = dlam + nsel;
-        RIGA_CUDA_TRY(c, cudaMemcpyAsync(dlam, lam.data(), nres * sizeof(double), cudaMemcpyHostToDevice, st));
-        { count_launch(c); resid_cols_kernel<<<dim3(gx, nres), 256, 0, st>>>(N, c->rowptr.ptr, c->col.ptr, c->Kval.ptr, U, MU, N, dlam, dpart); }
         std::vector<double> part((size_t)2 * gx * nres);
         RIGA_CUDA_TRY(c, cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         RIGA_CUDA_TRY(c, cudaStreamSynchronize(st));
