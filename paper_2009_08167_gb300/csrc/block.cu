@@ -311,13 +311,31 @@ __global__ void __launch_bounds__(256) bspmv_gram_kernel(long long N, const long
         double s[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) s[r] = 0.0;
-        if (row < N)
-            for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += SPMV_TPR) {
-                const double mv = Mv[e];
-                const int cc = col[e];
+        if (row < N) {
+            // four entries per lane in flight (their values and columns,
+            // then the gathers), summed in the order of the plain loop
+            const long long end = rowptr[row + 1];
+            for (long long e0 = rowptr[row] + lane; e0 < end; e0 += 4 * SPMV_TPR) {
+                double mv[4];
+                int cc[4];
 #pragma unroll
-                for (int r = 0; r < B; ++r) s[r] += mv * W[r * N + cc];
+                for (int k = 0; k < 4; ++k) {
+                    const long long e = e0 + k * SPMV_TPR;
+                    mv[k] = e < end ? Mv[e] : 0.0;
+                    cc[k] = e < end ? col[e] : -1;
+                }
+                double x[4][B];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int r = 0; r < B; ++r) x[k][r] = cc[k] >= 0 ? W[r * N + cc[k]] : 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (cc[k] >= 0)
+#pragma unroll
+                        for (int r = 0; r < B; ++r) s[r] += mv[k] * x[k][r];
             }
+        }
 #pragma unroll
         for (int r = 0; r < B; ++r) s[r] = group_sum(s[r]);
         if (row < N) {
@@ -493,6 +511,193 @@ __global__ void __launch_bounds__(256) bqr_scale_kernel(long long N, const doubl
     tail_reduce<B * B>(tot, partial, counter, Gnext);
 }
 
+// Grid-wide barrier of a cooperative launch (all blocks resident): the
+// k-th barrier waits until the arrival counter reaches k * gridDim.x.  The
+// wait is bounded: past the poll budget it sets bit 2 of err and reports
+// false (the caller returns; the host reads the flag).
+__device__ bool grid_barrier(int* arrive, int target, int* err, long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(arrive, 1);
+        long long it = 0;
+        int ok = 1;
+        while (*(volatile const int*)arrive < target) {
+            if (++it > limit) {
+                atomicOr(err, 2);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum of the per-block Gram partials part[i * B * B + e] over the grid, in
+// the same order in every block (so that every block factors bitwise the same
+// matrix); eight independent loads in flight per thread; the result in G
+// (shared).
+template <int B>
+__device__ void gram_from_partials(const double* __restrict__ part, double* __restrict__ sh, double* __restrict__ G) {
+    constexpr int E = B * B;
+    constexpr int GR = 256 / E;  // thread t sums entry t % E over blocks t / E, t / E + GR, ...
+    const int e = threadIdx.x % E, g = threadIdx.x / E;
+    const int nb = (int)gridDim.x;
+    double acc = 0.0;
+    for (int i0 = g; i0 < nb; i0 += 8 * GR) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k * GR;
+            v[k] = i < nb ? __ldcg(&part[(long long)i * E + e]) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc += v[k];
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < E) {
+        double t = 0.0;
+        for (int q = 0; q < GR; ++q) t += sh[q * E + threadIdx.x];
+        G[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// Block sum of per-thread Gram contributions g[B * B] into part[blockIdx.x]
+template <int B>
+__device__ void gram_block_partial(double* g, double (*red)[B * B], double* __restrict__ part) {
+#pragma unroll
+    for (int e = 0; e < B * B; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g[e] += __shfl_xor_sync(0xffffffffu, g[e], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int e = 0; e < B * B; ++e) red[threadIdx.x >> 5][e] = g[e];
+    __syncthreads();
+    if ((int)threadIdx.x < B * B) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+        part[(long long)blockIdx.x * B * B + threadIdx.x] = t;
+    }
+}
+
+// The three Cholesky QR passes of bnormalize in one cooperative launch (256
+// threads per block, every block resident), after the block SpMV
+// (bspmv_gram_kernel: M W and G0 = W^T M W): the per-block Gram partials of
+// the two later passes go to regions of their own, a grid barrier separates
+// the passes, and every block sums the partials itself in a fixed order and
+// factors the B x B matrix, so that no launch boundary and no last-block
+// reduction sits between them.  The same arithmetic as three
+// bqr_scale_kernel launches:
+//   R1 = chol(G0 + s I), V = W R1^{-1} (and M V); G1 = V^T M V,
+//   R2 = chol(G1), V <- V R2^{-1}; G2, R3, V <- V R3^{-1};
+//   Bout = R3 R2 R1 (W = V Bout).
+// A breakdown of any pass sets flag bit 0, the one-pass test (cn2 given) bit
+// 1.  bar[0] counts barrier arrivals, bar[1] exits; the last block to leave
+// resets both.
+template <int B>
+__global__ void __launch_bounds__(256) bqr_fused_kernel(long long N, const double* __restrict__ G0,
+                                                        const double* __restrict__ W, const double* __restrict__ MW,
+                                                        long long ldw, double* __restrict__ V, double* __restrict__ MV,
+                                                        long long ldv, double shift_rel, double* __restrict__ part,
+                                                        double* __restrict__ Bout, int* __restrict__ flag,
+                                                        const double* __restrict__ cn2, int* __restrict__ bar,
+                                                        int* __restrict__ err, long long spin_limit) {
+    constexpr int E = B * B;
+    __shared__ double red[8][E];
+    __shared__ double sh[256];
+    __shared__ double G[E];
+    __shared__ double sri[E];
+    __shared__ double Racc[E];  // R_k ... R_1 (block 0)
+    const long long gstride = (long long)gridDim.x * E;
+    for (int pass = 0; pass < 3; ++pass) {
+        if (pass == 0) {
+            if ((int)threadIdx.x < E) G[threadIdx.x] = G0[threadIdx.x];
+            __syncthreads();
+        } else {
+            if (!grid_barrier(&bar[0], pass * (int)gridDim.x, err, spin_limit)) return;
+            gram_from_partials<B>(part + (pass - 1) * gstride, sh, G);
+        }
+        if (threadIdx.x == 0) {
+            double R[B][B], Ri[B][B];
+            const bool bad = bcholesky<B>(G, pass == 0 ? shift_rel : 0.0, R, Ri);
+            for (int i = 0; i < B; ++i)
+                for (int j = 0; j < B; ++j) sri[i * B + j] = Ri[i][j];
+            if (blockIdx.x == 0) {
+                if (bad) atomicOr(flag, 1);
+                // the full Gram-Schmidt pass removed more than 100 x the norm left
+                if (pass == 0 && cn2)
+                    for (int r = 0; r < B; ++r)
+                        if (!(cn2[r] <= 1e4 * G[r * B + r])) atomicOr(flag, 2);
+                double P[B][B];
+                for (int i = 0; i < B; ++i)
+                    for (int j = 0; j < B; ++j) {
+                        double t = 0.0;
+                        for (int k = 0; k < B; ++k) t += R[i][k] * (pass ? Racc[k * B + j] : (k == j ? 1.0 : 0.0));
+                        P[i][j] = t;
+                    }
+                for (int i = 0; i < B; ++i)
+                    for (int j = 0; j < B; ++j) Racc[i * B + j] = P[i][j];
+                if (pass == 2)
+                    for (int e = 0; e < E; ++e) Bout[e] = Racc[e];
+            }
+        }
+        __syncthreads();
+        // every pass maps the same rows to the same thread, so the in-place
+        // passes read only what this thread wrote
+        const double* X = pass == 0 ? W : V;
+        const double* MX = pass == 0 ? MW : MV;
+        const long long ldx = pass == 0 ? ldw : ldv;
+        double g[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = 0.0;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+             i += (long long)gridDim.x * blockDim.x) {
+            double x[B], mx[B], v[B], mvv[B];
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                x[r] = X[r * ldx + i];
+                mx[r] = MX[r * ldx + i];
+            }
+#pragma unroll
+            for (int l = 0; l < B; ++l) {
+                double a = 0.0, b = 0.0;
+#pragma unroll
+                for (int r = 0; r <= l; ++r) {
+                    a += x[r] * sri[r * B + l];
+                    b += mx[r] * sri[r * B + l];
+                }
+                v[l] = a;
+                mvv[l] = b;
+                V[l * ldv + i] = a;
+                MV[l * ldv + i] = b;
+            }
+            if (pass < 2)
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+#pragma unroll
+                    for (int r = 0; r < B; ++r) g[q * B + r] += v[q] * mvv[r];
+        }
+        if (pass < 2) gram_block_partial<B>(g, red, part + pass * gstride);
+    }
+    // leave: the last block out resets the counters for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&bar[1], 1) == (int)gridDim.x - 1) {
+            bar[0] = 0;
+            bar[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
 // A_j[i][r] = C1[(cs + i) B + r] + C2[(cs + i) B + r]
 template <int B>
 __global__ void balpha_kernel(const double* __restrict__ C1, const double* __restrict__ C2, int cs,
@@ -595,6 +800,35 @@ int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
     { count_launch(c); bspmv_gram_kernel<B><<<nbg, 256, 0, st>>>(K.N, c->rowptr.ptr, c->col.ptr, c->Mval.ptr, K.W, K.MW,
                                                                K.part, counter, G0); }
     c->stats.n_matvec += B;
+    // the three passes in one cooperative launch where the device allows it
+    // (two blocks per SM, every block resident)
+    static int coop_blocks = -1;  // blocks per SM of the fused kernel, 0: no cooperative launch
+    if (coop_blocks < 0) {
+        int coop = 0, occ = 0;
+        RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+        RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bqr_fused_kernel<B>, 256, 0));
+        coop_blocks = coop ? std::min(occ, 2) : 0;
+    }
+    if (coop_blocks > 0) {
+        int nsm = 0;
+        RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+        long long n = K.N, ldw = K.N, ldv = K.ld;
+        const double* g0 = G0;
+        const double* w = K.W;
+        const double* mw = K.MW;
+        double* part = K.part;
+        int* flag = K.flag;
+        const double* cn2 = one_pass ? K.cn2 : nullptr;
+        int* bar = K.flag + 2;
+        int* err = c->flag.ptr;
+        long long lim = c->wait_limit;
+        double sh = shift;
+        void* args[] = {&n, &g0, &w, &mw, &ldw, &V, &MV, &ldv, &sh, &part, &Bout, &flag, &cn2, &bar, &err, &lim};
+        count_launch(c);
+        RIGA_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void*)bqr_fused_kernel<B>, dim3((unsigned)(coop_blocks * nsm)),
+                                                     dim3(256), args, 0, st));
+        return RIGA_OK;
+    }
     // shifted pass (W -> V, Gram of V into G1), then two plain passes in place
     { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G0, shift, nullptr, nullptr, R1, K.flag, K.W, K.N,
                                                               K.MW, V, MV, K.ld, K.part, counter, G1,
@@ -749,23 +983,25 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.B = B;
     K.N = N;
     K.ld = R.ld;
+    int nsm = 0;
+    RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    nsm = std::max(nsm, 1);
     {
-        int nsm = 0;
-        RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-        nsm = std::max(nsm, 1);
         const long long nchunk = (N + CH - 1) / CH;
         K.nch = (int)((nchunk + nsm - 1) / nsm * nsm);  // row blocks: a multiple of the SM count, <= CH rows each
     }
     K.cap = R.cap;
     const unsigned nbs = (unsigned)((N + SPMV_RPB - 1) / SPMV_RPB);
+    // the largest user: the dot partials, the last-block reductions, or the
+    // fused QR's two Gram regions (at most 2 blocks per SM)
     const size_t part_n = std::max<size_t>({(size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B,
-                                            (size_t)4 * 152 * 2 * B * B});
+                                            (size_t)4 * 152 * 2 * B * B, (size_t)2 * 2 * nsm * B * B});
     const size_t nAB = (size_t)(2 * nblk + 1) * B * B;  // the T blocks: A_0..A_{nblk-1}, B_0..B_nblk
     RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)4 * N * B));
     RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
     RIGA_CUDA_TRY(c, c->bpartial.alloc(part_n));
     RIGA_CUDA_TRY(c, c->bsmall.alloc((size_t)5 * B * B + nAB));
-    RIGA_CUDA_TRY(c, c->bflag.alloc(2));
+    RIGA_CUDA_TRY(c, c->bflag.alloc(4));
     if (c->bpin_size < nAB + 2) {
         if (c->bpin) cudaFreeHost(c->bpin);
         c->bpin = nullptr;
@@ -800,7 +1036,8 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
         RIGA_CUDA_TRY(c, cudaFuncSetAttribute(bupdate_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)((size_t)K.cap * B * sizeof(double))));
     }
-    RIGA_CUDA_TRY(c, cudaMemsetAsync(K.flag, 0, 2 * sizeof(int), st));  // breakdown flag, reduction counter
+    // breakdown flag, reduction counter, grid-barrier arrivals and exits
+    RIGA_CUDA_TRY(c, cudaMemsetAsync(K.flag, 0, 4 * sizeof(int), st));
 
     // start block: B random vectors, M-orthogonal to the locked ones
     enqueue_start_vector(c, (long long)N * B, seed, K.W);
