@@ -538,15 +538,77 @@ __device__ bool grid_barrier(int* arrive, int target, int* err, long long limit)
     return s_ok != 0;
 }
 
-// Sum of the per-block Gram partials part[i * B * B + e] over the grid, in
-// the same order in every block (so that every block factors bitwise the same
-// matrix); eight independent loads in flight per thread; the result in G
-// (shared).
+// The sums below keep FP64 additions few: on GB300 a warp's FP64
+// instruction holds its SM's FP64 pipe for 16 clocks whatever its active
+// lanes, so a reduction tree that adds every entry at every level costs more
+// than the data it sums.  All of them add in a fixed order, so that every
+// block obtains bitwise the same result.
+
+// Warp sum of E per-lane values (E a power of two, at most 32): a butterfly
+// whose first log2(E) steps halve the entries a lane carries (E - 1
+// additions in all), then plain steps on the one value left.  Lane l ends
+// with the warp sum of entry ((l >> log2(32 / E)) & (E - 1)); lane
+// e * (32 / E) holds entry e.
+template <int E>
+__device__ __forceinline__ double warp_sum_scatter(double (&v)[E]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int cnt = E, o = 16; cnt > 1; cnt >>= 1, o >>= 1) {
+        const int h = cnt / 2;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? v[i] : v[i + h];
+            const double keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    double t = v[0];
+#pragma unroll
+    for (int o = 32 / E / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+// Sum over the warps of a block of the per-warp sums red[w][e] (w < NW):
+// lane l adds entry l % E of the warps l / E, l / E + 32 / E, ..., then the
+// lanes of one entry combine; the result in out[e] (shared).  Called by one
+// whole warp.
+template <int E, int NW>
+__device__ __forceinline__ void warps_sum(const double (*red)[E], double* out) {
+    constexpr int G = 32 / E;
+    const int lane = threadIdx.x & 31, e = lane % E, g = lane / E;
+    double t = 0.0;
+#pragma unroll
+    for (int w = g; w < NW; w += G) t += red[w][e];
+#pragma unroll
+    for (int o = E; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < E) out[lane] = t;
+}
+
+// Block sum of the per-thread Gram contributions g[B * B] into
+// part[blockIdx.x * B * B + e]
+template <int B, int NT>
+__device__ void gram_block_partial(double (&g)[B * B], double (*red)[B * B], double* __restrict__ part,
+                                   double* __restrict__ tot) {
+    constexpr int E = B * B, G = 32 / E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double t = warp_sum_scatter<E>(g);
+    if (lane % G == 0) red[warp][lane / G] = t;
+    __syncthreads();
+    if (warp == 0) {
+        warps_sum<E, NT / 32>(red, tot);
+        __syncwarp();
+        if (lane < E) part[(long long)blockIdx.x * E + lane] = tot[lane];
+    }
+}
+
+// Sum of the per-block Gram partials part[i * B * B + e] over the grid by
+// one warp (lane l: entry l % E of the blocks l / E, l / E + 32 / E, ...,
+// eight loads in flight), into G (shared); the caller synchronizes.
 template <int B>
-__device__ void gram_from_partials(const double* __restrict__ part, double* __restrict__ sh, double* __restrict__ G) {
-    constexpr int E = B * B;
-    constexpr int GR = 256 / E;  // thread t sums entry t % E over blocks t / E, t / E + GR, ...
-    const int e = threadIdx.x % E, g = threadIdx.x / E;
+__device__ void gram_from_partials(const double* __restrict__ part, double* __restrict__ G) {
+    constexpr int E = B * B, GR = 32 / E;
+    const int lane = threadIdx.x & 31, e = lane % E, g = lane / E;
     const int nb = (int)gridDim.x;
     double acc = 0.0;
     for (int i0 = g; i0 < nb; i0 += 8 * GR) {
@@ -557,43 +619,21 @@ __device__ void gram_from_partials(const double* __restrict__ part, double* __re
             v[k] = i < nb ? __ldcg(&part[(long long)i * E + e]) : 0.0;
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc += v[k];
+        for (int k = 0; k < 8; ++k)
+            if (i0 + k * GR < nb) acc += v[k];
     }
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    if ((int)threadIdx.x < E) {
-        double t = 0.0;
-        for (int q = 0; q < GR; ++q) t += sh[q * E + threadIdx.x];
-        G[threadIdx.x] = t;
-    }
-    __syncthreads();
+#pragma unroll
+    for (int o = E; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane < E) G[lane] = acc;
 }
 
-// Block sum of per-thread Gram contributions g[B * B] into part[blockIdx.x]
-template <int B>
-__device__ void gram_block_partial(double* g, double (*red)[B * B], double* __restrict__ part) {
-#pragma unroll
-    for (int e = 0; e < B * B; ++e)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g[e] += __shfl_xor_sync(0xffffffffu, g[e], o);
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int e = 0; e < B * B; ++e) red[threadIdx.x >> 5][e] = g[e];
-    __syncthreads();
-    if ((int)threadIdx.x < B * B) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
-        part[(long long)blockIdx.x * B * B + threadIdx.x] = t;
-    }
-}
-
-// The three Cholesky QR passes of bnormalize in one cooperative launch (256
-// threads per block, every block resident), after the block SpMV
-// (bspmv_gram_kernel: M W and G0 = W^T M W): the per-block Gram partials of
-// the two later passes go to regions of their own, a grid barrier separates
-// the passes, and every block sums the partials itself in a fixed order and
-// factors the B x B matrix, so that no launch boundary and no last-block
-// reduction sits between them.  The same arithmetic as three
+// The three Cholesky QR passes of bnormalize in one cooperative launch (one
+// block of QR_THREADS threads per SM, every block resident), after the block
+// SpMV (bspmv_gram_kernel: M W and G0 = W^T M W): the per-block Gram partials
+// of the two later passes go to regions of their own, a grid barrier
+// separates the passes, and every block sums the partials itself in a fixed
+// order and factors the B x B matrix, so that no launch boundary and no
+// last-block reduction sits between them.  The same arithmetic as three
 // bqr_scale_kernel launches:
 //   R1 = chol(G0 + s I), V = W R1^{-1} (and M V); G1 = V^T M V,
 //   R2 = chol(G1), V <- V R2^{-1}; G2, R3, V <- V R3^{-1};
@@ -601,17 +641,20 @@ __device__ void gram_block_partial(double* g, double (*red)[B * B], double* __re
 // A breakdown of any pass sets flag bit 0, the one-pass test (cn2 given) bit
 // 1.  bar[0] counts barrier arrivals, bar[1] exits; the last block to leave
 // resets both.
+constexpr int QR_THREADS = 512;
 template <int B>
-__global__ void __launch_bounds__(256) bqr_fused_kernel(long long N, const double* __restrict__ G0,
-                                                        const double* __restrict__ W, const double* __restrict__ MW,
-                                                        long long ldw, double* __restrict__ V, double* __restrict__ MV,
-                                                        long long ldv, double shift_rel, double* __restrict__ part,
-                                                        double* __restrict__ Bout, int* __restrict__ flag,
-                                                        const double* __restrict__ cn2, int* __restrict__ bar,
-                                                        int* __restrict__ err, long long spin_limit) {
+__global__ void __launch_bounds__(QR_THREADS, 1) bqr_fused_kernel(long long N, const double* __restrict__ G0,
+                                                                  const double* __restrict__ W,
+                                                                  const double* __restrict__ MW, long long ldw,
+                                                                  double* __restrict__ V, double* __restrict__ MV,
+                                                                  long long ldv, double shift_rel,
+                                                                  double* __restrict__ part, double* __restrict__ Bout,
+                                                                  int* __restrict__ flag, const double* __restrict__ cn2,
+                                                                  int* __restrict__ bar, int* __restrict__ err,
+                                                                  long long spin_limit) {
     constexpr int E = B * B;
-    __shared__ double red[8][E];
-    __shared__ double sh[256];
+    __shared__ double red[QR_THREADS / 32][E];
+    __shared__ double tot[E];
     __shared__ double G[E];
     __shared__ double sri[E];
     __shared__ double Racc[E];  // R_k ... R_1 (block 0)
@@ -619,11 +662,11 @@ __global__ void __launch_bounds__(256) bqr_fused_kernel(long long N, const doubl
     for (int pass = 0; pass < 3; ++pass) {
         if (pass == 0) {
             if ((int)threadIdx.x < E) G[threadIdx.x] = G0[threadIdx.x];
-            __syncthreads();
         } else {
             if (!grid_barrier(&bar[0], pass * (int)gridDim.x, err, spin_limit)) return;
-            gram_from_partials<B>(part + (pass - 1) * gstride, sh, G);
+            if (threadIdx.x < 32) gram_from_partials<B>(part + (pass - 1) * gstride, G);
         }
+        __syncthreads();
         if (threadIdx.x == 0) {
             double R[B][B], Ri[B][B];
             const bool bad = bcholesky<B>(G, pass == 0 ? shift_rel : 0.0, R, Ri);
@@ -657,8 +700,8 @@ __global__ void __launch_bounds__(256) bqr_fused_kernel(long long N, const doubl
         double g[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) g[e] = 0.0;
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-             i += (long long)gridDim.x * blockDim.x) {
+        for (long long i = (long long)blockIdx.x * QR_THREADS + threadIdx.x; i < N;
+             i += (long long)gridDim.x * QR_THREADS) {
             double x[B], mx[B], v[B], mvv[B];
 #pragma unroll
             for (int r = 0; r < B; ++r) {
@@ -684,7 +727,7 @@ __global__ void __launch_bounds__(256) bqr_fused_kernel(long long N, const doubl
 #pragma unroll
                     for (int r = 0; r < B; ++r) g[q * B + r] += v[q] * mvv[r];
         }
-        if (pass < 2) gram_block_partial<B>(g, red, part + pass * gstride);
+        if (pass < 2) gram_block_partial<B, QR_THREADS>(g, red, part + pass * gstride, tot);
     }
     // leave: the last block out resets the counters for the next launch
     __syncthreads();
@@ -801,13 +844,13 @@ int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
                                                                K.part, counter, G0); }
     c->stats.n_matvec += B;
     // the three passes in one cooperative launch where the device allows it
-    // (two blocks per SM, every block resident)
+    // (one block per SM, every block resident)
     static int coop_blocks = -1;  // blocks per SM of the fused kernel, 0: no cooperative launch
     if (coop_blocks < 0) {
         int coop = 0, occ = 0;
         RIGA_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
-        RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bqr_fused_kernel<B>, 256, 0));
-        coop_blocks = coop ? std::min(occ, 2) : 0;
+        RIGA_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bqr_fused_kernel<B>, QR_THREADS, 0));
+        coop_blocks = coop ? std::min(occ, 1) : 0;
     }
     if (coop_blocks > 0) {
         int nsm = 0;
@@ -826,7 +869,7 @@ int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
         void* args[] = {&n, &g0, &w, &mw, &ldw, &V, &MV, &ldv, &sh, &part, &Bout, &flag, &cn2, &bar, &err, &lim};
         count_launch(c);
         RIGA_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void*)bqr_fused_kernel<B>, dim3((unsigned)(coop_blocks * nsm)),
-                                                     dim3(256), args, 0, st));
+                                                     dim3(QR_THREADS), args, 0, st));
         return RIGA_OK;
     }
     // shifted pass (W -> V, Gram of V into G1), then two plain passes in place
@@ -993,9 +1036,9 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
     K.cap = R.cap;
     const unsigned nbs = (unsigned)((N + SPMV_RPB - 1) / SPMV_RPB);
     // the largest user: the dot partials, the last-block reductions, or the
-    // fused QR's two Gram regions (at most 2 blocks per SM)
+    // fused QR's two Gram regions (one block per SM)
     const size_t part_n = std::max<size_t>({(size_t)K.nch * K.cap * B, (size_t)std::max<unsigned>(nbs, 304) * B * B,
-                                            (size_t)4 * 152 * 2 * B * B, (size_t)2 * 2 * nsm * B * B});
+                                            (size_t)4 * 152 * 2 * B * B, (size_t)2 * nsm * B * B});
     const size_t nAB = (size_t)(2 * nblk + 1) * B * B;  // the T blocks: A_0..A_{nblk-1}, B_0..B_nblk
     RIGA_CUDA_TRY(c, c->bwork.alloc((size_t)4 * N * B));
     RIGA_CUDA_TRY(c, c->bcoef.alloc((size_t)2 * K.cap * B));
@@ -1111,7 +1154,10 @@ int block_run(Run& R, int B, int nlock, int want_run, int m_max, double cur_sigm
 
     // Checks are lagged: the block copies of step m are queued with an
     // event, the host evaluates them while the GPU runs the next steps, and
-    // it never runs more than two block steps ahead of an unevaluated check.
+    // it never runs more than two block steps ahead of an unevaluated check
+    // (a converged check leaves the steps issued after it unused; three
+    // steps measured no better on the 2D benchmark: 1 ms less idle, one
+    // more block step per run).
     const int ck = std::max(1, 8 / B);  // block steps between checks
     cudaEvent_t ev;
     RIGA_CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
