@@ -30,33 +30,38 @@ namespace {
 struct BandSym {
     int n, w;
     std::vector<double> L;
-    double& at(int i, int j) {
-        if (i < j) std::swap(i, j);
-        return L[(size_t)j * w + (i - j)];
-    }
 };
 
-// similarity rotation in the (p, q) plane of the symmetric matrix:
-// rows p, q <- [c s; -s c] [row p; row q], and the same on the columns,
-// restricted to the index window where the band (plus one bulge) can hold
-// non-zeros
-void rotate_sym(BandSym& A, int b, int p, int q, double c, double s) {
+// similarity rotation in the adjacent plane (p, q = p + 1) of the symmetric
+// matrix: rows p, q <- [c s; -s c] [row p; row q], and the same on the
+// columns, restricted to the index window where the band (plus one bulge) can
+// hold non-zeros.  Left of p the two entries of a column t are neighbours in
+// its storage (t, p - t) and (t, q - t); right of q they sit in columns p and
+// q at distances t - p and t - q.
+void rotate_adj(BandSym& A, int b, int p, double c, double s) {
+    const int q = p + 1, w = A.w;
+    double* L = A.L.data();
     const int lo = std::max(0, p - b - 2), hi = std::min(A.n, q + b + 3);
-    for (int t = lo; t < hi; ++t) {
-        if (t == p || t == q) continue;
-        double& xr = A.at(p, t);
-        double& yr = A.at(q, t);
-        const double x = xr, y = yr;
-        xr = c * x + s * y;
-        yr = -s * x + c * y;
+    for (int t = lo; t < p; ++t) {
+        double* col = L + (size_t)t * w;
+        const double x = col[p - t], y = col[q - t];
+        col[p - t] = c * x + s * y;
+        col[q - t] = -s * x + c * y;
     }
-    const double app = A.at(p, p), aqq = A.at(q, q), apq = A.at(p, q);
+    double* cp = L + (size_t)p * w;
+    double* cq = L + (size_t)q * w;
+    for (int t = q + 1; t < hi; ++t) {
+        const double x = cp[t - p], y = cq[t - q];
+        cp[t - p] = c * x + s * y;
+        cq[t - q] = -s * x + c * y;
+    }
+    const double app = cp[0], aqq = cq[0], apq = cp[1];
     const double npp = c * c * app + 2.0 * c * s * apq + s * s * aqq;
     const double nqq = s * s * app - 2.0 * c * s * apq + c * c * aqq;
     const double npq = (c * c - s * s) * apq + c * s * (aqq - app);
-    A.at(p, p) = npp;
-    A.at(q, q) = nqq;
-    A.at(p, q) = npq;
+    cp[0] = npp;
+    cq[0] = nqq;
+    cp[1] = npq;
 }
 
 // band LU with partial pivoting (kl = ku = b; fill up to 2b above the
@@ -153,9 +158,12 @@ static void band_reduce(int n, int b, const double* T, std::vector<double>& d, s
     A.n = n;
     A.w = b + 4;
     A.L.assign((size_t)n * A.w, 0.0);
+    const int w = A.w;
+    double* L = A.L.data();
     for (int j = 0; j < n; ++j)
-        for (int i = j; i <= std::min(n - 1, j + b); ++i) A.L[(size_t)j * A.w + (i - j)] = T[(size_t)j * n + i];
-    auto at = [&](int i, int j) -> double& { return A.at(i, j); };
+        for (int i = j; i <= std::min(n - 1, j + b); ++i) L[(size_t)j * w + (i - j)] = T[(size_t)j * n + i];
+    // entry (i, j), i >= j, of the lower band
+    auto low = [&](int i, int j) -> double& { return L[(size_t)j * w + (i - j)]; };
     auto track = [&](int p, int q, double c, double s) {
         for (int k = 0; k < r; ++k) {
             double& a = qr[(size_t)p * r + k];
@@ -167,31 +175,31 @@ static void band_reduce(int n, int b, const double* T, std::vector<double>& d, s
     };
     for (int j = 0; j + 2 < n; ++j) {
         for (int i = std::min(j + b, n - 1); i >= j + 2; --i) {
-            const double x = at(i - 1, j), y = at(i, j);
+            const double x = low(i - 1, j), y = low(i, j);
             if (y == 0.0) continue;
             const double rr = norm2(x, y);
             const double c1 = x / rr, s1 = y / rr;
-            rotate_sym(A, b, i - 1, i, c1, s1);
+            rotate_adj(A, b, i - 1, c1, s1);
             if (r > 0) track(i - 1, i, c1, s1);
-            at(i, j) = 0.0;
+            low(i, j) = 0.0;
             // chase the bulge at (k + b, k - 1) down the band
             for (int k = i; k + b < n;) {
                 const int p = k + b - 1, q = k + b, col = k - 1;
-                const double x2 = at(p, col), y2 = at(q, col);
+                const double x2 = low(p, col), y2 = low(q, col);
                 if (y2 == 0.0) break;
                 const double r2 = norm2(x2, y2);
                 const double c2 = x2 / r2, s2 = y2 / r2;
-                rotate_sym(A, b, p, q, c2, s2);
+                rotate_adj(A, b, p, c2, s2);
                 if (r > 0) track(p, q, c2, s2);
-                at(q, col) = 0.0;
+                low(q, col) = 0.0;
                 k = q;
             }
         }
     }
     d.assign(n, 0.0);
     e.assign(n, 0.0);
-    for (int i = 0; i < n; ++i) d[i] = at(i, i);
-    for (int i = 0; i + 1 < n; ++i) e[i] = at(i + 1, i);
+    for (int i = 0; i < n; ++i) d[i] = low(i, i);
+    for (int i = 0; i + 1 < n; ++i) e[i] = low(i + 1, i);
 }
 
 void band_eigvals(int n, int b, const double* T, double* theta) {
