@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "ctx.h"
@@ -227,35 +228,72 @@ void band_eigvecs(int n, int b, const double* T, int q, const double* th, double
     std::vector<int> ord(q);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return th[x] < th[y]; });
-    BandLU F;
-    std::vector<double> x(n);
-    int cl0 = 0;  // first member (in ord) of the current cluster
-    for (int oi = 0; oi < q; ++oi) {
-        const int qi = ord[oi];
-        if (oi > 0 && th[qi] - th[ord[oi - 1]] > 1e-3 * tnorm) cl0 = oi;
-        band_lu(F, n, b, T, th[qi], tiny);
-        // fixed start vector (deterministic), then three inverse iterations
-        uint64_t s = 0x9E3779B97F4A7C15ULL ^ (uint64_t)(oi + 1);
-        for (int i = 0; i < n; ++i) {
-            s ^= s << 13;
-            s ^= s >> 7;
-            s ^= s << 17;
-            x[i] = ((double)(s >> 11) / 9007199254740992.0) - 0.5;
-        }
-        for (int it = 0; it < 3; ++it) {
-            band_solve(F, x.data());
-            for (int pj = cl0; pj < oi; ++pj) {
-                const double* v = S + (size_t)ord[pj] * n;
-                const double dot = dot4(v, x.data(), n);
-                for (int i = 0; i < n; ++i) x[i] -= dot * v[i];
+    // clusters: runs of ord whose neighbouring values are within 1e-3 ||T||
+    std::vector<int> cstart;
+    for (int oi = 0; oi < q; ++oi)
+        if (oi == 0 || th[ord[oi]] - th[ord[oi - 1]] > 1e-3 * tnorm) cstart.push_back(oi);
+    const int ncl = (int)cstart.size();
+    cstart.push_back(q);
+    // clusters [c0, c1): each member by inverse iteration from its own fixed
+    // start vector, orthogonalised against the cluster's earlier members
+    auto work = [&](int c0, int c1) {
+        BandLU F;
+        std::vector<double> x(n);
+        for (int ci = c0; ci < c1; ++ci) {
+            const int cl0 = cstart[ci];
+            for (int oi = cl0; oi < cstart[ci + 1]; ++oi) {
+                const int qi = ord[oi];
+                band_lu(F, n, b, T, th[qi], tiny);
+                // fixed start vector (deterministic), then three inverse iterations
+                uint64_t s = 0x9E3779B97F4A7C15ULL ^ (uint64_t)(oi + 1);
+                for (int i = 0; i < n; ++i) {
+                    s ^= s << 13;
+                    s ^= s >> 7;
+                    s ^= s << 17;
+                    x[i] = ((double)(s >> 11) / 9007199254740992.0) - 0.5;
+                }
+                for (int it = 0; it < 3; ++it) {
+                    band_solve(F, x.data());
+                    for (int pj = cl0; pj < oi; ++pj) {
+                        const double* v = S + (size_t)ord[pj] * n;
+                        const double dot = dot4(v, x.data(), n);
+                        for (int i = 0; i < n; ++i) x[i] -= dot * v[i];
+                    }
+                    double nrm = std::sqrt(dot4(x.data(), x.data(), n));
+                    if (!(nrm > 0.0)) nrm = 1.0;
+                    const double inv = 1.0 / nrm;
+                    for (int i = 0; i < n; ++i) x[i] *= inv;
+                }
+                std::copy(x.begin(), x.end(), S + (size_t)qi * n);
             }
-            double nrm = std::sqrt(dot4(x.data(), x.data(), n));
-            if (!(nrm > 0.0)) nrm = 1.0;
-            const double inv = 1.0 / nrm;
-            for (int i = 0; i < n; ++i) x[i] *= inv;
         }
-        std::copy(x.begin(), x.end(), S + (size_t)qi * n);
+    };
+    // clusters are independent: split them over host threads in contiguous
+    // runs of about equal member counts (each cluster's arithmetic is the
+    // same whichever thread runs it)
+    // (about 25 us per member at n = 200; starting a thread costs about
+    // 100 us, so four threads at most: 1.5 -> 0.9 ms for 60 members)
+    int nth = std::min({ncl, 4, n >= 64 ? q / 8 : 1});
+    nth = std::min(nth, (int)std::max(1u, std::thread::hardware_concurrency()));
+    if (nth <= 1) {
+        work(0, ncl);
+        return;
     }
+    std::vector<std::thread> pool;
+    int c0 = 0;
+    for (int t = 0; t < nth && c0 < ncl; ++t) {
+        const int target = (int)((long long)q * (t + 1) / nth);  // members covered after this thread
+        int c1 = c0 + 1;
+        while (c1 < ncl && cstart[c1] < target) ++c1;
+        if (t == nth - 1) c1 = ncl;
+        try {
+            pool.emplace_back(work, c0, c1);
+        } catch (...) {  // no thread to be had: this one does the run (no exception leaves the library)
+            work(c0, c1);
+        }
+        c0 = c1;
+    }
+    for (auto& th2 : pool) th2.join();
 }
 
 // All eigenpairs of a dense symmetric n x n matrix A (column-major; the
