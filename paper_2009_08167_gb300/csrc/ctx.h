@@ -238,10 +238,16 @@ void parallel_for(int n, Fn f) {
     }
     std::vector<std::thread> th;
     th.reserve(nt);
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([=]() {
+    for (int t = 0; t < nt; ++t) {
+        auto part = [=]() {
             for (int i = t; i < n; i += nt) f(i);
-        });
+        };
+        try {
+            th.emplace_back(part);
+        } catch (...) {  // no thread to be had: run this share here (no exception leaves the library)
+            part();
+        }
+    }
     for (std::thread& x : th) x.join();
 }
 
