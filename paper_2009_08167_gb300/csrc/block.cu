@@ -867,10 +867,18 @@ int bnormalize_t(BlockWork& K, int col, double* Bout, bool one_pass) {
         long long lim = c->wait_limit;
         double sh = shift;
         void* args[] = {&n, &g0, &w, &mw, &ldw, &V, &MV, &ldv, &sh, &part, &Bout, &flag, &cn2, &bar, &err, &lim};
-        count_launch(c);
-        RIGA_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void*)bqr_fused_kernel<B>, dim3((unsigned)(coop_blocks * nsm)),
-                                                     dim3(QR_THREADS), args, 0, st));
-        return RIGA_OK;
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)bqr_fused_kernel<B>,
+                                                          dim3((unsigned)(coop_blocks * nsm)), dim3(QR_THREADS), args, 0, st);
+        if (e == cudaSuccess) {
+            count_launch(c);
+            return RIGA_OK;
+        }
+        if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
+            return set_error(c, RIGA_ECUDA, std::string("cudaLaunchCooperativeKernel: ") + cudaGetErrorString(e));
+        // the blocks cannot all be resident here (another process holds SMs):
+        // the three separate passes from now on
+        cudaGetLastError();
+        coop_blocks = 0;
     }
     // shifted pass (W -> V, Gram of V into G1), then two plain passes in place
     { count_launch(c); bqr_scale_kernel<B><<<gb, 256, 0, st>>>(K.N, G0, shift, nullptr, nullptr, R1, K.flag, K.W, K.N,
