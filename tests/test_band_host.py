@@ -181,3 +181,23 @@ def test_dense_symmetric_eig(case):
     assert np.max(np.abs(theta - ref)) <= 1e-13 * scale * A.shape[0] / 10
     assert np.max(np.abs(A @ Z - Z * theta)) <= 1e-13 * scale * A.shape[0] / 10
     assert np.max(np.abs(Z.T @ Z - np.eye(A.shape[0]))) <= 1e-12
+
+
+def test_band_eigvecs_threads_deterministic_with_clusters():
+    """Many wanted vectors on a large band matrix (the case that splits the
+    clusters of Ritz values over host threads): two calls agree bit for bit,
+    the vectors are eigenvectors and orthonormal, including inside exact
+    double eigenvalues (two interleaved copies of one band matrix)."""
+    n0, b0 = 110, 2
+    T0 = _band(n0, b0, 19)
+    n, b = 2 * n0, 2 * b0
+    T = np.zeros((n, n))
+    T[0::2, 0::2] = T0
+    T[1::2, 1::2] = T0
+    which = list(range(n - 96, n))
+    th1, S1 = riga.band_eig(T, b, which)
+    th2, S2 = riga.band_eig(T, b, which)
+    assert np.array_equal(th1, th2) and np.array_equal(S1, S2)
+    scale = np.abs(th1).max()
+    assert np.max(np.abs(T @ S1 - S1 * th1[which])) <= 1e-11 * scale
+    assert np.max(np.abs(S1.T @ S1 - np.eye(len(which)))) <= 1e-10
