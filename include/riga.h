@@ -528,11 +528,13 @@ int riga_profile_get(riga_ctx* ctx, int phase, const char** name, long long* lau
                      double* ms, double* bytes, double* flops);
 
 /*
- * riga_set_wait_limit: budget of every device-side dependency wait of the
- * persistent tree solve, in polls of about 64 ns (default 2^24, about a
- * second).  A wait that exhausts it sets the context's device error word, the
- * kernel returns, and the next host check reports RIGA_ETIMEOUT; the context
- * stays usable.  limit >= 0.  Errors: RIGA_EINVAL.
+ * riga_set_wait_limit: budget of every device-side wait, in polls (default
+ * 2^24): the dependency waits of the persistent tree solve (polls of about
+ * 64 ns: about a second), the pipeline waits of the tensor-core Schur updates
+ * and the grid barriers of the block-Lanczos QR (shorter polls).  A wait that
+ * exhausts it sets the context's device error word, the kernel returns, and
+ * the next host check reports RIGA_ETIMEOUT; the context stays usable.
+ * limit >= 0.  Errors: RIGA_EINVAL.
  */
 int riga_set_wait_limit(riga_ctx* ctx, long long limit);
 
